@@ -1,0 +1,567 @@
+"""FP64 CPU oracle of the VIF approximation (Gyger, Furrer & Sigrist, 2025).
+
+TEST INFRASTRUCTURE ONLY.  Only the tests, the smoke check and the CPU-baseline
+leg of the benchmark may import this module.  The CUDA library never calls it,
+and it shares no code with the CUDA library.
+
+Every function follows the paper's formulas in the paper's own algebra, written
+out in numpy/scipy float64, with library primitives (Cholesky, triangular and
+dense solves, sparse products, sorting) as the only building blocks:
+
+* covariance functions: the half-integer Matern forms and the Gaussian (SE)
+  kernel, r = ||(s - s')/lambda|| (Sec. 2 and Eq. cov_trans_iso of Sec. 6);
+* the predictive-process low-rank part  Sigma_mn^T Sigma_m^{-1} Sigma_mn  (Sec. 2.1);
+* correlation-based causal neighbour sets with the distance d_c (Sec. 6);
+* the residual Vecchia factors A_i, D_i of Eq. D_A_Vecchia (Sec. 2.1);
+* the negative log-likelihood through M (Eq. def_M) with Woodbury and
+  Sylvester (Sec. 2.2), and the dense definitions used as pins;
+* predictive means and variances (Prop. 2.1, App. C.1);
+* Laplace mode finding for a Bernoulli-logit likelihood (Eq. one_it_newton_mode)
+  with preconditioned CG (Eq. pcls1) and the VIFDU preconditioner (Sec. 4.3, App. E.1).
+
+Readings of points the paper leaves open (all shared with the CUDA path):
+  R1 kernel forms of Rasmussen & Williams; "range" = length scale lambda.
+  R3 points are ordered as given; prediction points come after all training points.
+  R4 d_c uses Sigma without the nugget; if c_r(i,i) or c_r(j,j) <= TAU_V*sigma1^2 the
+     correlation is taken as 0; |rho| is clamped to 1; ranking key = 1 - |rho|.
+  R5 ties are broken by ascending index.
+  R7 Sigma_m += eps*sigma1^2*I (eps = 1e-8 SE, 1e-10 Matern); residual Vecchia blocks
+     get +1e-10*sigma1^2 on the diagonal when there is no nugget (latent GP).
+  R9 prediction points condition on training points only (B_p = I); their
+     neighbours are the m_v nearest training points by d_c (non-causal).
+  R10 Newton from b=0; PCG from x=0 stops at ||v - A x||_2/||v||_2 <= tol.
+"""
+from __future__ import annotations
+
+import math
+
+import numpy as np
+import scipy.linalg as sla
+import scipy.sparse as sp
+import scipy.sparse.linalg as spla
+
+SQRT3 = math.sqrt(3.0)
+SQRT5 = math.sqrt(5.0)
+TAU_V = 1e-6          # R4: residual variances below TAU_V*sigma1^2 count as zero
+LOG2PI = math.log(2.0 * math.pi)
+
+
+# ----------------------------------------------------------------------------
+# Covariance functions (Sec. 2, Eq. cov_trans_iso; reading R1)
+# ----------------------------------------------------------------------------
+def jitter_eps(theta) -> float:
+    """R7: relative jitter added to Sigma_m."""
+    return 1e-8 if theta.kind == 3 else 1e-10
+
+
+def residual_diag(theta) -> float:
+    """Diagonal added to residual Vecchia blocks: the nugget sigma^2 in the
+    Gaussian case (Sigma-tilde of Eq. cov_mat_gauss), else the R7 jitter."""
+    return theta.nugget if theta.nugget > 0 else 1e-10 * theta.variance
+
+
+def cov_of_r(r: np.ndarray, kind: int, variance: float) -> np.ndarray:
+    """c(r) for Matern-1/2, 3/2, 5/2 and the squared-exponential kernel (R1)."""
+    if kind == 0:
+        return variance * np.exp(-r)
+    if kind == 1:
+        t = SQRT3 * r
+        return variance * (1.0 + t) * np.exp(-t)
+    if kind == 2:
+        t = SQRT5 * r
+        return variance * (1.0 + t + t * t / 3.0) * np.exp(-t)
+    if kind == 3:
+        return variance * np.exp(-0.5 * r * r)
+    raise ValueError(kind)
+
+
+def scaled(X: np.ndarray, theta) -> np.ndarray:
+    """q_lambda(s) = s / lambda (Sec. 6, ARD transform)."""
+    ls = np.broadcast_to(np.asarray(theta.lengthscale, dtype=np.float64), (X.shape[1],))
+    return X / ls
+
+
+def dist(X1: np.ndarray, X2: np.ndarray) -> np.ndarray:
+    """Euclidean distances, computed from coordinate differences."""
+    diff = X1[:, None, :] - X2[None, :, :]
+    return np.sqrt((diff * diff).sum(-1))
+
+
+def cov(X1: np.ndarray, X2: np.ndarray, theta) -> np.ndarray:
+    """Cross-covariance matrix [c_theta(s_i, s'_j)] without the nugget."""
+    return cov_of_r(dist(scaled(X1, theta), scaled(X2, theta)), theta.kind, theta.variance)
+
+
+def sigma_m(Z: np.ndarray, theta) -> np.ndarray:
+    """Sigma_m with the R7 jitter."""
+    S = cov(Z, Z, theta)
+    return S + jitter_eps(theta) * theta.variance * np.eye(Z.shape[0])
+
+
+# ----------------------------------------------------------------------------
+# Low-rank part (Sec. 2.1, Eq. def_b_low)
+# ----------------------------------------------------------------------------
+class LowRank:
+    """Holds Sigma_m, its Cholesky factor and Sigma_m^{-1} Sigma_mn for the data.
+
+    lr(i, j) = Sigma_mi^T Sigma_m^{-1} Sigma_mj  (the low-rank covariance Sigma^l),
+    computed through a Cholesky solve with Sigma_m itself (the paper's algebra).
+    """
+
+    def __init__(self, X: np.ndarray, Z: np.ndarray, theta):
+        self.theta = theta
+        self.m = Z.shape[0]
+        if self.m == 0:
+            self.Smn = np.zeros((0, X.shape[0]))
+            self.SinvSmn = self.Smn
+            self.Sm = np.zeros((0, 0))
+            self.cf = None
+            return
+        self.Sm = sigma_m(Z, theta)
+        self.cf = sla.cho_factor(self.Sm, lower=True)
+        self.Smn = cov(Z, X, theta)                          # m x n
+        self.SinvSmn = sla.cho_solve(self.cf, self.Smn)      # Sigma_m^{-1} Sigma_mn
+
+    def lr(self, idx_a, idx_b) -> np.ndarray:
+        return self.Smn[:, idx_a].T @ self.SinvSmn[:, idx_b]
+
+    def lr_diag(self) -> np.ndarray:
+        return np.einsum("ij,ij->j", self.Smn, self.SinvSmn)
+
+    def logdet_Sm(self) -> float:
+        return 2.0 * float(np.log(np.diag(self.cf[0])).sum()) if self.m else 0.0
+
+
+# ----------------------------------------------------------------------------
+# Correlation-based neighbour selection (Sec. 6, distance d_c; R4, R5)
+# ----------------------------------------------------------------------------
+def residual_var(X, lowrank: LowRank, theta) -> np.ndarray:
+    """c_r(i,i) = Sigma_ii - Sigma_mi^T Sigma_m^{-1} Sigma_mi (no nugget)."""
+    return theta.variance - lowrank.lr_diag() if lowrank.m else np.full(X.shape[0], theta.variance)
+
+
+def corr_keys(q_x: np.ndarray, q_cr: float, X_c: np.ndarray, cr_c: np.ndarray, theta,
+              lr_cross: np.ndarray) -> np.ndarray:
+    """Ranking key 1 - |rho| of one query against candidates (R4).
+
+    rho = c_r(q,j) / sqrt(c_r(q,q) c_r(j,j)), c_r(q,j) = Sigma_qj - lr(q,j).
+    Since d_c = sqrt(1-|rho|) is monotone in the key, ranking by the key gives
+    the same order as ranking by d_c.
+    """
+    K = cov(q_x[None, :], X_c, theta)[0]
+    c = K - lr_cross
+    tv = TAU_V * theta.variance
+    with np.errstate(divide="ignore", invalid="ignore"):
+        rho = c / np.sqrt(q_cr * cr_c)
+    rho = np.where((q_cr <= tv) | (cr_c <= tv), 0.0, rho)
+    rho = np.clip(np.abs(rho), 0.0, 1.0)
+    return 1.0 - rho
+
+
+def causal_neighbors(X, Z, theta, mv: int, return_keys: bool = False):
+    """N(i): the min(i, m_v) predecessors j < i with the smallest (key, j)
+    (Sec. 2.1 neighbour rule; Sec. 6 distance), stored in ascending index order,
+    padded with -1.  Brute force over all j < i."""
+    n = X.shape[0]
+    lowrank = LowRank(X, Z, theta)
+    cr = residual_var(X, lowrank, theta)
+    N = -np.ones((n, mv), dtype=np.int64)
+    keys = [] if return_keys else None
+    for i in range(1, n):
+        if lowrank.m:
+            lr = lowrank.Smn[:, :i].T @ lowrank.SinvSmn[:, i]
+        else:
+            lr = np.zeros(i)
+        k = corr_keys(X[i], cr[i], X[:i], cr[:i], theta, lr)
+        q = min(i, mv)
+        order = np.lexsort((np.arange(i), k))[:q]
+        N[i, :q] = np.sort(order)
+        if return_keys:
+            keys.append(k)
+    if return_keys:
+        return N, keys, cr
+    return N
+
+
+def query_keys(i: int, X, lowrank: LowRank, cr, theta, upto: int | None = None):
+    """Keys of point i against candidates 0..upto-1 (default: its predecessors)."""
+    upto = i if upto is None else upto
+    lr = (lowrank.Smn[:, :upto].T @ lowrank.SinvSmn[:, i]) if lowrank.m else np.zeros(upto)
+    return corr_keys(X[i], cr[i], X[:upto], cr[:upto], theta, lr)
+
+
+# ----------------------------------------------------------------------------
+# Residual Vecchia factors (Sec. 2.1, Eq. D_A_Vecchia)
+# ----------------------------------------------------------------------------
+def vecchia_factors(X, Z, theta, N, lowrank: LowRank | None = None):
+    """Returns (Acoef, D): Acoef[i, :q_i] = A_i (row of -B on N(i)), D[i] = D_i.
+
+    A_i = (Sigma_iN - Sigma_mi^T Sigma_m^{-1} Sigma_mN)(Sigma~_N - Sigma_mN^T Sigma_m^{-1} Sigma_mN)^{-1}
+    D_i = Sigma~_ii - Sigma_mi^T Sigma_m^{-1} Sigma_mi - A_i (Sigma_iN^T - Sigma_mN^T Sigma_m^{-1} Sigma_mi)
+    Sigma~ carries the nugget (Gaussian) or the R7 jitter (latent GP).
+    Points with the same neighbour count are processed as one batch of solves.
+    """
+    n = X.shape[0]
+    mv = N.shape[1]
+    lowrank = lowrank or LowRank(X, Z, theta)
+    tdiag = residual_diag(theta)
+    Acoef = np.zeros((n, mv))
+    D = np.empty(n)
+    q_of = (N >= 0).sum(1)
+    Xs = scaled(X, theta)
+    for q in np.unique(q_of):
+        I = np.nonzero(q_of == q)[0]
+        for s in range(0, len(I), 4096):
+            Ib = I[s:s + 4096]
+            dii = theta.variance + tdiag
+            lrii = (lowrank.Smn[:, Ib] * lowrank.SinvSmn[:, Ib]).sum(0) if lowrank.m else 0.0
+            if q == 0:
+                D[Ib] = dii - lrii
+                continue
+            Nb = N[Ib, :q]                                        # b x q
+            xi = Xs[Ib]                                           # b x d
+            xn = Xs[Nb]                                           # b x q x d
+            r_iN = np.sqrt(((xi[:, None, :] - xn) ** 2).sum(-1))
+            S_iN = cov_of_r(r_iN, theta.kind, theta.variance)     # b x q
+            r_NN = np.sqrt(((xn[:, :, None, :] - xn[:, None, :, :]) ** 2).sum(-1))
+            S_NN = cov_of_r(r_NN, theta.kind, theta.variance) + tdiag * np.eye(q)
+            if lowrank.m:
+                Smi = lowrank.Smn[:, Ib].T                        # b x m
+                Wi = lowrank.SinvSmn[:, Ib].T                     # b x m
+                SmN = lowrank.Smn[:, Nb].transpose(1, 2, 0)       # b x q x m
+                WN = lowrank.SinvSmn[:, Nb].transpose(1, 2, 0)    # b x q x m
+                lr_iN = np.einsum("bm,bqm->bq", Smi, WN)
+                lr_NN = np.einsum("bqm,brm->bqr", SmN, WN)
+                lr_Ni = np.einsum("bqm,bm->bq", SmN, Wi)
+            else:
+                lr_iN = lr_Ni = 0.0
+                lr_NN = 0.0
+            left = S_iN - lr_iN
+            Mat = S_NN - lr_NN
+            Ai = np.linalg.solve(Mat, left[:, :, None])[:, :, 0]   # Mat symmetric
+            Acoef[Ib, :q] = Ai
+            D[Ib] = dii - lrii - (Ai * (S_iN - lr_Ni)).sum(1)
+    return Acoef, D
+
+
+def B_matrix(N, Acoef) -> sp.csr_matrix:
+    """Unit lower-triangular B with B_{i,N(i)} = -A_i (Sec. 2.1)."""
+    n, mv = N.shape
+    rows = [np.arange(n)]
+    cols = [np.arange(n)]
+    vals = [np.ones(n)]
+    mask = N >= 0
+    r = np.repeat(np.arange(n)[:, None], mv, 1)[mask]
+    rows.append(r)
+    cols.append(N[mask])
+    vals.append(-Acoef[mask])
+    return sp.csr_matrix((np.concatenate(vals), (np.concatenate(rows), np.concatenate(cols))),
+                         shape=(n, n))
+
+
+# ----------------------------------------------------------------------------
+# Negative log-likelihood (Sec. 2.1-2.2)
+# ----------------------------------------------------------------------------
+class VIF:
+    """All factors of one VIF approximation: Sigma_m, Sigma_mn, B, D, M."""
+
+    def __init__(self, X, Z, theta, N):
+        self.X, self.Z, self.theta, self.N = X, Z, theta, N
+        self.n = X.shape[0]
+        self.m = Z.shape[0]
+        self.lowrank = LowRank(X, Z, theta)
+        self.Acoef, self.D = vecchia_factors(X, Z, theta, N, self.lowrank)
+        self.B = B_matrix(N, self.Acoef)
+        self.Dinv = 1.0 / self.D
+        if self.m:
+            Smn = self.lowrank.Smn
+            # Q Sigma_mn^T with Q = B^T D^{-1} B, then M of Eq. def_M
+            self.QSnm = self.Q(Smn.T)
+            self.M = self.lowrank.Sm + Smn @ self.QSnm
+            self.Mcf = sla.cho_factor(self.M, lower=True)
+
+    def Q(self, V):
+        """Q V = B^T D^{-1} B V."""
+        BV = self.B @ V
+        if BV.ndim == 1:
+            return self.B.T @ (self.Dinv * BV)
+        return self.B.T @ (self.Dinv[:, None] * BV)
+
+    def Sigma_dagger_inv(self, v):
+        """Woodbury: Q v - Q Sigma_mn^T M^{-1} Sigma_mn Q v (Sec. 2.2)."""
+        Qv = self.Q(v)
+        if not self.m:
+            return Qv
+        return Qv - self.QSnm @ sla.cho_solve(self.Mcf, self.lowrank.Smn @ Qv)
+
+    def logdet(self) -> float:
+        """Sylvester: log det M - log det Sigma_m + log det D (Sec. 2.2)."""
+        ld = float(np.log(self.D).sum())
+        if self.m:
+            ld += 2.0 * float(np.log(np.diag(self.Mcf[0])).sum()) - self.lowrank.logdet_Sm()
+        return ld
+
+    def nll(self, y) -> float:
+        quad = float(y @ self.Sigma_dagger_inv(y))
+        return 0.5 * (self.n * LOG2PI + self.logdet() + quad)
+
+    def dense_Sigma_dagger(self) -> np.ndarray:
+        """Sigma~_dagger = Sigma^l + (B^T D^{-1} B)^{-1}, formed explicitly (small n)."""
+        Binv = np.linalg.inv(self.B.toarray())
+        S = Binv @ np.diag(self.D) @ Binv.T
+        if self.m:
+            S = S + self.lowrank.Smn.T @ self.lowrank.SinvSmn
+        return S
+
+
+def vif_nll(X, Z, theta, N, y) -> float:
+    return VIF(X, Z, theta, N).nll(y)
+
+
+def dense_nll(S: np.ndarray, y: np.ndarray) -> float:
+    """-log N(y; 0, S) by a dense Cholesky (Sec. 2, first display)."""
+    L = np.linalg.cholesky(S)
+    a = sla.solve_triangular(L, y, lower=True)
+    return 0.5 * (len(y) * LOG2PI + 2.0 * np.log(np.diag(L)).sum() + a @ a)
+
+
+def exact_cov(X, theta) -> np.ndarray:
+    """Sigma~ = Sigma + sigma^2 I (Eq. cov_mat_gauss)."""
+    return cov(X, X, theta) + theta.nugget * np.eye(X.shape[0])
+
+
+def fitc_cov(X, Z, theta) -> np.ndarray:
+    """FITC covariance: Sigma^l + diag(Sigma~ - Sigma^l) (Sec. 2.1, m_v = 0)."""
+    lr = LowRank(X, Z, theta)
+    Sl = lr.Smn.T @ lr.SinvSmn
+    Sf = exact_cov(X, theta)
+    return Sl + np.diag(np.diag(Sf) - np.diag(Sl))
+
+
+# ----------------------------------------------------------------------------
+# Prediction (Prop. 2.1, proof, App. C.1; reading R9)
+# ----------------------------------------------------------------------------
+def pred_neighbors(X, Z, theta, Xp, mv: int, lowrank: LowRank | None = None):
+    """N_p(j): the m_v training points with the smallest d_c to prediction point j."""
+    lowrank = lowrank or LowRank(X, Z, theta)
+    n = X.shape[0]
+    cr = residual_var(X, lowrank, theta)
+    lrp = LowRank(Xp, Z, theta)
+    crp = residual_var(Xp, lrp, theta)
+    Np = np.empty((Xp.shape[0], mv), dtype=np.int64)
+    for p in range(Xp.shape[0]):
+        lr = (lowrank.Smn.T @ lrp.SinvSmn[:, p]) if lowrank.m else np.zeros(n)
+        k = corr_keys(Xp[p], crp[p], X, cr, theta, lr)
+        order = np.lexsort((np.arange(n), k))[:mv]
+        Np[p] = np.sort(order)
+    return Np
+
+
+def pred_factors(X, Z, theta, Xp, Np, lowrank: LowRank):
+    """Rows of B_po (coefficients A_p on N_p) and D_p for the joint residual
+    Vecchia approximation of Eq. vecchia_pred with B_p = I (R9)."""
+    npred, mv = Np.shape
+    tdiag = residual_diag(theta)
+    lrp = LowRank(Xp, Z, theta)
+    Ap = np.zeros((npred, mv))
+    Dp = np.empty(npred)
+    for p in range(npred):
+        Nn = Np[p]
+        S_pN = cov(Xp[p:p + 1], X[Nn], theta)[0]
+        S_NN = cov(X[Nn], X[Nn], theta) + tdiag * np.eye(mv)
+        if lowrank.m:
+            lr_pN = lrp.Smn[:, p] @ lowrank.SinvSmn[:, Nn]
+            lr_NN = lowrank.Smn[:, Nn].T @ lowrank.SinvSmn[:, Nn]
+            lr_pp = lrp.Smn[:, p] @ lrp.SinvSmn[:, p]
+        else:
+            lr_pN, lr_NN, lr_pp = np.zeros(mv), 0.0, 0.0
+        c = S_pN - lr_pN
+        a = np.linalg.solve(S_NN - lr_NN, c)
+        Ap[p] = a
+        Dp[p] = theta.variance + tdiag - lr_pp - a @ c
+    return Ap, Dp, lrp
+
+
+def predict_prop21_dense(vif: VIF, y, Xp, Np):
+    """Predictive mean and covariance of Prop. 2.1 evaluated literally with
+    dense matrices (small n only).  Returns (mean, Sigma^p) for the response."""
+    X, Z, theta = vif.X, vif.Z, vif.theta
+    n = vif.n
+    Ap, Dp, lrp = pred_factors(X, Z, theta, Xp, Np, vif.lowrank)
+    npred = Xp.shape[0]
+    Bpo = np.zeros((npred, n))
+    for p in range(npred):
+        Bpo[p, Np[p]] = -Ap[p]
+    Bp_inv = np.eye(npred)
+    Bd = vif.B.toarray()
+    Prec = Bd.T @ np.diag(vif.Dinv) @ Bd            # B^T D^{-1} B
+    PrecInv = np.linalg.inv(Prec)
+    if vif.m:
+        Smn, Smnp = vif.lowrank.Smn, lrp.Smn
+        SmInv = np.linalg.inv(vif.lowrank.Sm)
+        LRpn = Smnp.T @ SmInv @ Smn                   # Sigma_mnp^T Sigma_m^-1 Sigma_mn
+        LRpp = Smnp.T @ SmInv @ Smnp
+        Minv = np.linalg.inv(vif.M)
+        SMS = Smn.T @ Minv @ Smn                      # Sigma_mn^T M^-1 Sigma_mn
+    else:
+        LRpn = np.zeros((npred, n))
+        LRpp = np.zeros((npred, npred))
+        SMS = np.zeros((n, n))
+    mu = (-Bp_inv @ Bpo @ y + LRpn @ Prec @ y - LRpn @ Prec @ SMS @ Prec @ y
+          + Bp_inv @ Bpo @ SMS @ Prec @ y)
+    Sd_inv = Prec - Prec @ SMS @ Prec                  # Sigma~_dagger^{-1}
+    left = LRpn - Bp_inv @ Bpo @ PrecInv
+    Sig = (Bp_inv @ np.diag(Dp) @ Bp_inv.T + Bp_inv @ Bpo @ PrecInv @ Bpo.T @ Bp_inv.T + LRpp
+           - left @ Sd_inv @ left.T)
+    return mu, Sig
+
+
+def predict_appC(vif: VIF, y, Xp, Np):
+    """Predictive mean (Prop. 2.1) and variances via the expansion of App. C.1,
+    using only sparse products and m x m solves.  Returns (mean, var) for the
+    response y^p; subtract the nugget for the latent process."""
+    X, Z, theta = vif.X, vif.Z, vif.theta
+    Ap, Dp, lrp = pred_factors(X, Z, theta, Xp, Np, vif.lowrank)
+    npred = Xp.shape[0]
+    rows = np.repeat(np.arange(npred), Np.shape[1])
+    Bpo = sp.csr_matrix((-Ap.ravel(), (rows, Np.ravel())), shape=(npred, vif.n))
+    Qy = vif.Q(y)
+    if not vif.m:
+        mu = -(Bpo @ y)
+        # (B^T D^-1 B)^-1 B_po^T rows are needed only for the cancelled term
+        return mu, Dp.copy()
+    Smn, Smnp = vif.lowrank.Smn, lrp.Smn
+    cfS, cfM = vif.lowrank.cf, vif.Mcf
+    SmInvSmnp = sla.cho_solve(cfS, Smnp)               # Sigma_m^-1 Sigma_mnp  (m x np)
+    SmnQy = Smn @ Qy
+    MinvSmnQy = sla.cho_solve(cfM, SmnQy)
+    # mean, Prop. 2.1 (B_p = I)
+    mu = (-(Bpo @ y) + SmInvSmnp.T @ SmnQy - SmInvSmnp.T @ (Smn @ vif.Q(Smn.T @ MinvSmnQy))
+          + Bpo @ (Smn.T @ MinvSmnQy))
+    # variances, App. C.1 (diagonal of each term)
+    T = Smn @ vif.QSnm                                  # Sigma_mn B^T D^-1 B Sigma_mn^T  (m x m)
+    U = Smn @ Bpo.T.toarray()                           # Sigma_mn B_po^T (m x np)
+    V = SmInvSmnp                                       # Sigma_m^-1 Sigma_mnp
+    MinvU = sla.cho_solve(cfM, U)
+    MinvTV = sla.cho_solve(cfM, T @ V)
+    t1 = Dp
+    t2 = (Smnp * V).sum(0)                              # Sigma_mnp^T Sigma_m^-1 Sigma_mnp
+    t3 = -(V * (T @ V)).sum(0)
+    t4 = (V * U).sum(0)                                 # Sigma_mnp^T Sigma_m^-1 Sigma_mn B_po^T
+    t5 = t4
+    t6 = (U * MinvU).sum(0)                             # B_po Sigma_mn^T M^-1 Sigma_mn B_po^T
+    t7 = -(U * MinvTV).sum(0)
+    t8 = t7
+    t9 = ((T @ V) * MinvTV).sum(0)
+    var = t1 + t2 + t3 + t4 + t5 + t6 + t7 + t8 + t9
+    return mu, var
+
+
+def exact_predict(X, y, theta, Xp):
+    """Exact GP predictive mean and variance of y^p (Sec. 2, second paragraph)."""
+    S = exact_cov(X, theta)
+    Snp = cov(X, Xp, theta)
+    L = np.linalg.cholesky(S)
+    alpha = sla.cho_solve((L, True), y)
+    mu = Snp.T @ alpha
+    Vv = sla.solve_triangular(L, Snp, lower=True)
+    var = theta.variance + theta.nugget - (Vv * Vv).sum(0)
+    return mu, var
+
+
+# ----------------------------------------------------------------------------
+# Laplace approximation for Bernoulli-logit (Sec. 3, Sec. 4)
+# ----------------------------------------------------------------------------
+def bern_grad_W(y, b):
+    """d log p(y|b)/db = y - sigmoid(b);  W_ii = sigmoid(b)(1 - sigmoid(b)) (Eq. W_diag)."""
+    p = 1.0 / (1.0 + np.exp(-b))
+    return y - p, p * (1.0 - p)
+
+
+def bern_loglik(y, b) -> float:
+    return float((y * b - np.logaddexp(0.0, b)).sum())
+
+
+class VIFDU:
+    """VIFDU preconditioner P^ = B^T W B + Sigma_dagger^{-1} applied with the
+    formula of App. E.1: B^{-1}[(W+D^{-1})^{-1} + (W+D^{-1})^{-1} D^{-1} B Sigma_mn^T
+    M_3^{-1} Sigma_mn B^T D^{-1} (W+D^{-1})^{-1}] B^{-T},
+    M_3 = M - Sigma_mn B^T D^{-1} (W+D^{-1})^{-1} D^{-1} B Sigma_mn^T."""
+
+    def __init__(self, vif: VIF, W):
+        self.vif = vif
+        self.Ginv = 1.0 / (W + vif.Dinv)
+        self.Bcsr = vif.B.tocsr()
+        self.BTcsr = vif.B.T.tocsr()
+        if vif.m:
+            DBS = vif.Dinv[:, None] * (vif.B @ vif.lowrank.Smn.T)     # D^-1 B Sigma_mn^T
+            self.DBS = DBS
+            self.M3 = vif.M - DBS.T @ (self.Ginv[:, None] * DBS)
+            self.M3cf = sla.cho_factor(self.M3, lower=True)
+
+    def apply(self, w):
+        x = spla.spsolve_triangular(self.BTcsr, w, lower=False)          # B^{-T} w
+        g = self.Ginv * x
+        if self.vif.m:
+            g = g + self.Ginv * (self.DBS @ sla.cho_solve(self.M3cf, self.DBS.T @ g))
+        return spla.spsolve_triangular(self.Bcsr, g, lower=True)          # B^{-1} (.)
+
+    def dense(self, W) -> np.ndarray:
+        B = self.vif.B.toarray()
+        n = self.vif.n
+        Sdi = np.column_stack([self.vif.Sigma_dagger_inv(e) for e in np.eye(n)])
+        return B.T @ np.diag(W) @ B + Sdi
+
+
+def pcg(matvec, precond, v, tol: float, max_iter: int):
+    """Preconditioned CG from x=0 on (W + Sigma_dagger^{-1}) x = v (Eq. pcls1);
+    stops when ||r||_2/||v||_2 <= tol (R10).  Returns (x, iterations, rel_res)."""
+    x = np.zeros_like(v)
+    r = v.copy()
+    nv = np.linalg.norm(v)
+    if nv == 0:
+        return x, 0, 0.0
+    z = precond(r)
+    p = z.copy()
+    rz = r @ z
+    for it in range(1, max_iter + 1):
+        Ap = matvec(p)
+        alpha = rz / (p @ Ap)
+        x += alpha * p
+        r -= alpha * Ap
+        rel = np.linalg.norm(r) / nv
+        if rel <= tol:
+            return x, it, rel
+        z = precond(r)
+        rz_new = r @ z
+        p = z + (rz_new / rz) * p
+        rz = rz_new
+    return x, max_iter, rel
+
+
+def laplace_mode(vif: VIF, y, tol=1e-6, max_pcg=1000, max_newton=50, psi_tol=1e-10,
+                 dense: bool = False):
+    """Newton iterations of Eq. one_it_newton_mode from b=0 (R10); each linear
+    solve uses PCG with the VIFDU preconditioner, or a dense solve if `dense`.
+    Returns (mode, newton_steps, total_pcg_iterations)."""
+    n = vif.n
+    b = np.zeros(n)
+    psi_old = None
+    tot = 0
+    Sdi_dense = None
+    if dense:
+        Sdi_dense = np.linalg.inv(vif.dense_Sigma_dagger())
+    for t in range(1, max_newton + 1):
+        g, W = bern_grad_W(y, b)
+        v = W * b + g
+        if dense:
+            b = np.linalg.solve(np.diag(W) + Sdi_dense, v)
+        else:
+            pre = VIFDU(vif, W)
+            b, it, _ = pcg(lambda w: W * w + vif.Sigma_dagger_inv(w), pre.apply, v, tol, max_pcg)
+            tot += it
+        psi = bern_loglik(y, b) - 0.5 * float(b @ vif.Sigma_dagger_inv(b))
+        if psi_old is not None and abs(psi - psi_old) <= psi_tol * abs(psi):
+            return b, t, tot
+        psi_old = psi
+    return b, max_newton, tot

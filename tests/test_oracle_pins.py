@@ -1,0 +1,251 @@
+"""Pins of the FP64 oracle against facts fixed by the paper and by mathematics
+(special cases, closed forms, library routines, invariants, hand-worked cases).
+None of them re-types the oracle's own formula.  CPU only."""
+import json
+import math
+import os
+
+import numpy as np
+import pytest
+import scipy.linalg as sla
+import scipy.special as ss
+from scipy.spatial.distance import cdist
+
+from oracle import vif_oracle as O
+from paper_2507_05064_gb300 import synth
+
+GOLD = os.path.join(os.path.dirname(__file__), "golden")
+
+
+def small_problem(n=300, d=2, m=20, mv=8, kind="matern32", nugget=0.1, seed=1, ls=0.2,
+                  likelihood="gaussian", n_pred=0, inducing="kmeans++"):
+    return synth.make_problem(n, d, m, mv, kind, 1.0, ls, nugget, seed, likelihood=likelihood,
+                              inducing=inducing, n_pred=n_pred, lloyd=3)
+
+
+# --------------------------------------------------------------------------- kernels
+@pytest.mark.parametrize("kind,nu", [(0, 0.5), (1, 1.5), (2, 2.5)])
+def test_matern_half_integer_forms_match_bessel_definition(kind, nu):
+    """General Matern: s^2 2^{1-nu}/Gamma(nu) (sqrt(2nu) r)^nu K_nu(sqrt(2nu) r)."""
+    r = np.array([1e-3, 0.05, 0.3, 1.0, 2.5, 7.0])
+    t = math.sqrt(2 * nu) * r
+    ref = 2.0 ** (1 - nu) / ss.gamma(nu) * t ** nu * ss.kv(nu, t) * 1.7
+    np.testing.assert_allclose(O.cov_of_r(r, kind, 1.7), ref, rtol=1e-12)
+    assert O.cov_of_r(np.array([0.0]), kind, 1.7)[0] == pytest.approx(1.7)
+
+
+def test_se_is_the_characteristic_function_of_its_spectral_density():
+    """Bochner: the SE kernel exp(-r^2/2) is E[cos(w r)] with w ~ N(0,1); quadrature."""
+    from scipy.integrate import quad
+    r = np.array([0.05, 0.3, 1.0, 2.0])
+    ref = [quad(lambda w, rr=rr: math.cos(w * rr) * math.exp(-0.5 * w * w) / math.sqrt(2 * math.pi),
+                -40, 40, limit=400)[0] for rr in r]
+    np.testing.assert_allclose(O.cov_of_r(r, 3, 1.0), ref, rtol=1e-10)
+
+
+def test_ard_scaling_is_coordinatewise():
+    th = synth.Theta(1, 1.0, np.array([0.1, 2.0]), 0.0)
+    X1 = np.array([[0.1, 0.5]])
+    X2 = np.array([[0.2, 0.5], [0.1, 2.5]])
+    # a 0.1 shift in dim 0 (length 0.1) equals a 2.0 shift in dim 1 (length 2.0)
+    k = O.cov(X1, X2, th)[0]
+    assert k[0] == pytest.approx(k[1], rel=1e-14)
+    assert k[0] == pytest.approx(O.cov_of_r(np.array([1.0]), 1, 1.0)[0], rel=1e-14)
+
+
+# --------------------------------------------------------------------------- low rank
+def test_lowrank_reproduces_sigma_when_inducing_points_are_the_data():
+    """Predictive process with S* = S: Sigma^l = Sigma (Sec. 2.1), up to the jitter."""
+    P = small_problem(n=60, m=0)
+    th = P.theta
+    lr = O.LowRank(P.X, P.X.copy(), th)
+    Sl = lr.Smn.T @ lr.SinvSmn
+    np.testing.assert_allclose(Sl, O.cov(P.X, P.X, th), atol=1e-8)
+
+
+def test_lowrank_is_psd_and_below_sigma():
+    P = small_problem(n=200, m=30)
+    lr = O.LowRank(P.X, P.Z, P.theta)
+    Sl = lr.Smn.T @ lr.SinvSmn
+    R = O.cov(P.X, P.X, P.theta) - Sl
+    assert np.linalg.eigvalsh(Sl).min() > -1e-9
+    assert np.linalg.eigvalsh(R).min() > -1e-9          # Cov(b_s) is PSD
+    # independent route: general LU solve instead of the Cholesky solve
+    Sl2 = lr.Smn.T @ np.linalg.solve(O.sigma_m(P.Z, P.theta), lr.Smn)
+    np.testing.assert_allclose(Sl, Sl2, atol=1e-9)
+
+
+# --------------------------------------------------------------------------- neighbours
+def test_knn_golden_line():
+    g = json.load(open(os.path.join(GOLD, "knn_line_m0.json")))
+    X = np.array(g["x"])[:, None]
+    th = synth.Theta(synth.KIND_IDS[g["kind"]], g["variance"], np.array([g["lengthscale"]]), 0.0)
+    N = O.causal_neighbors(X, np.zeros((0, 1)), th, g["mv"])
+    for i, exp in enumerate(g["neighbors"]):
+        got = [int(j) for j in N[i] if j >= 0]
+        assert got == exp, (i, got, exp)
+
+
+def test_knn_without_inducing_points_is_scaled_euclidean_knn():
+    P = small_problem(n=250, d=3, m=0, mv=7, ls=np.array([0.1, 0.3, 0.9]))
+    N = O.causal_neighbors(P.X, P.Z, P.theta, 7)
+    Dm = cdist(P.X / P.theta.lengthscale, P.X / P.theta.lengthscale)
+    for i in range(1, 250):
+        q = min(i, 7)
+        ref = np.sort(np.lexsort((np.arange(i), Dm[i, :i]))[:q])
+        assert list(N[i, :q]) == list(ref)
+
+
+def test_knn_matches_dense_residual_correlation_brute_force():
+    """Brute force from the dense residual covariance Sigma - Sigma^l and d_c itself."""
+    P = small_problem(n=180, m=15, mv=6, kind="matern52")
+    th = P.theta
+    N = O.causal_neighbors(P.X, P.Z, th, 6)
+    S = O.cov(P.X, P.X, th)
+    Sm = O.sigma_m(P.Z, th)
+    Snm = O.cov(P.X, P.Z, th)
+    R = S - Snm @ np.linalg.solve(Sm, Snm.T)
+    dgl = np.diag(R)
+    dc = np.sqrt(1.0 - np.minimum(np.abs(R / np.sqrt(np.outer(dgl, dgl))), 1.0))
+    np.testing.assert_allclose(dc, dc.T, atol=1e-12)          # d_c is symmetric
+    for i in range(1, 180):
+        q = min(i, 6)
+        ref = np.sort(np.lexsort((np.arange(i), dc[i, :i]))[:q])
+        assert list(N[i, :q]) == list(ref), i
+
+
+# --------------------------------------------------------------------------- factors
+def test_vecchia_factor_invariants():
+    P = small_problem(n=300, m=25, mv=10, nugget=0.05)
+    th = P.theta
+    N10 = O.causal_neighbors(P.X, P.Z, th, 10)
+    N4 = O.causal_neighbors(P.X, P.Z, th, 4)
+    lr = O.LowRank(P.X, P.Z, th)
+    _, D10 = O.vecchia_factors(P.X, P.Z, th, N10, lr)
+    _, D4 = O.vecchia_factors(P.X, P.Z, th, N4, lr)
+    ctilde = th.variance + th.nugget - lr.lr_diag()
+    assert (D10 > 0).all() and (D10 <= ctilde + 1e-12).all()
+    assert (D10 >= th.nugget - 1e-12).all()                 # noise is never explained away
+    # the 4 nearest are a subset of the 10 nearest, so conditioning on more can only shrink D
+    for i in range(300):
+        assert set(N4[i][N4[i] >= 0]) <= set(N10[i][N10[i] >= 0])
+    assert (D10 <= D4 + 1e-12).all()
+
+
+# --------------------------------------------------------------------------- likelihood
+def test_full_conditioning_gives_the_exact_gp_likelihood():
+    """m_v = n-1: the residual Vecchia is exact, so Sigma~_dagger = Sigma~ for any m, Z."""
+    P = small_problem(n=120, m=15, mv=119, nugget=0.1)
+    N = O.causal_neighbors(P.X, P.Z, P.theta, 119)
+    vif = O.VIF(P.X, P.Z, P.theta, N)
+    ex = O.dense_nll(O.exact_cov(P.X, P.theta), P.y)
+    assert vif.nll(P.y) == pytest.approx(ex, rel=1e-10)
+
+
+def test_full_conditioning_with_no_inducing_points_is_exact():
+    P = small_problem(n=90, m=0, mv=89, nugget=0.2, kind="matern12")
+    N = O.causal_neighbors(P.X, P.Z, P.theta, 89)
+    ex = O.dense_nll(O.exact_cov(P.X, P.theta), P.y)
+    assert O.vif_nll(P.X, P.Z, P.theta, N, P.y) == pytest.approx(ex, rel=1e-10)
+
+
+def test_zero_neighbours_is_fitc():
+    """m_v = 0: Sigma^l + diag(Sigma~ - Sigma^l) (Sec. 2.1, special case)."""
+    P = small_problem(n=200, m=20, mv=0, nugget=0.1)
+    th = P.theta
+    N = np.zeros((200, 0), dtype=np.int64)
+    Snm = O.cov(P.X, P.Z, th)
+    Sl = Snm @ np.linalg.solve(O.sigma_m(P.Z, th), Snm.T)
+    fitc = Sl + np.diag(th.variance + th.nugget - np.diag(Sl))
+    assert O.vif_nll(P.X, P.Z, th, N, P.y) == pytest.approx(O.dense_nll(fitc, P.y), rel=1e-11)
+
+
+def test_no_inducing_points_is_classical_vecchia():
+    """m = 0: Vecchia of Sigma~ itself, built densely here with textbook conditionals."""
+    P = small_problem(n=150, m=0, mv=6, nugget=0.1, kind="matern52")
+    th = P.theta
+    N = O.causal_neighbors(P.X, P.Z, th, 6)
+    S = O.exact_cov(P.X, th)
+    n = 150
+    Bd = np.eye(n)
+    Dd = np.empty(n)
+    for i in range(n):
+        nb = [j for j in N[i] if j >= 0]
+        if nb:
+            a = np.linalg.solve(S[np.ix_(nb, nb)], S[nb, i])
+            Bd[i, nb] = -a
+            Dd[i] = S[i, i] - S[i, nb] @ a
+        else:
+            Dd[i] = S[i, i]
+    Sv = np.linalg.inv(Bd.T @ np.diag(1 / Dd) @ Bd)
+    assert O.vif_nll(P.X, P.Z, th, N, P.y) == pytest.approx(O.dense_nll(Sv, P.y), rel=1e-10)
+
+
+def test_woodbury_sylvester_equals_dense_vif_likelihood():
+    P = small_problem(n=250, m=25, mv=7, nugget=0.05, kind="se", ls=np.array([0.1, 0.2]))
+    N = O.causal_neighbors(P.X, P.Z, P.theta, 7)
+    vif = O.VIF(P.X, P.Z, P.theta, N)
+    assert vif.nll(P.y) == pytest.approx(O.dense_nll(vif.dense_Sigma_dagger(), P.y), rel=1e-10)
+
+
+# --------------------------------------------------------------------------- prediction
+def test_prediction_prop21_equals_appendix_c_form():
+    P = small_problem(n=200, m=20, mv=8, nugget=0.1, n_pred=40)
+    th = P.theta
+    N = O.causal_neighbors(P.X, P.Z, th, 8)
+    vif = O.VIF(P.X, P.Z, th, N)
+    Np = O.pred_neighbors(P.X, P.Z, th, P.Xp, 8, vif.lowrank)
+    mu1, S1 = O.predict_prop21_dense(vif, P.y, P.Xp, Np)
+    mu2, v2 = O.predict_appC(vif, P.y, P.Xp, Np)
+    np.testing.assert_allclose(mu1, mu2, rtol=1e-9, atol=1e-10)
+    np.testing.assert_allclose(np.diag(S1), v2, rtol=1e-8)
+
+
+def test_prediction_with_full_conditioning_is_exact_gp_prediction():
+    P = small_problem(n=100, m=12, mv=99, nugget=0.1, n_pred=15)
+    th = P.theta
+    N = O.causal_neighbors(P.X, P.Z, th, 99)
+    vif = O.VIF(P.X, P.Z, th, N)
+    Np = np.tile(np.arange(100), (15, 1))
+    mu, var = O.predict_appC(vif, P.y, P.Xp, Np)
+    mu_e, var_e = O.exact_predict(P.X, P.y, th, P.Xp)
+    np.testing.assert_allclose(mu, mu_e, rtol=1e-7, atol=1e-9)
+    np.testing.assert_allclose(var, var_e, rtol=1e-7, atol=1e-9)
+
+
+# --------------------------------------------------------------------------- Laplace
+def test_vifdu_formula_equals_dense_definition():
+    """App. E.1: the solve formula inverts P^ = B^T W B + Sigma_dagger^{-1}."""
+    P = small_problem(n=120, m=12, mv=5, nugget=0.0, likelihood="bernoulli_logit")
+    N = O.causal_neighbors(P.X, P.Z, P.theta, 5)
+    vif = O.VIF(P.X, P.Z, P.theta, N)
+    W = np.random.default_rng(3).uniform(0.05, 0.25, 120)
+    pre = O.VIFDU(vif, W)
+    Pd = pre.dense(W)
+    w = np.random.default_rng(4).standard_normal(120)
+    np.testing.assert_allclose(pre.apply(w), np.linalg.solve(Pd, w), rtol=1e-8, atol=1e-10)
+
+
+def test_vifdu_without_neighbours_is_exact_so_pcg_takes_one_step():
+    P = small_problem(n=150, m=15, mv=0, nugget=0.0, likelihood="bernoulli_logit")
+    N = np.zeros((150, 0), dtype=np.int64)
+    vif = O.VIF(P.X, P.Z, P.theta, N)
+    W = np.random.default_rng(5).uniform(0.05, 0.25, 150)
+    pre = O.VIFDU(vif, W)
+    v = np.random.default_rng(6).standard_normal(150)
+    _, it, rel = O.pcg(lambda w: W * w + vif.Sigma_dagger_inv(w), pre.apply, v, 1e-10, 50)
+    assert it == 1 and rel < 1e-10
+
+
+def test_laplace_mode_is_stationary_and_pcg_agrees_with_dense_newton():
+    P = small_problem(n=200, m=15, mv=6, nugget=0.0, likelihood="bernoulli_logit",
+                      kind="matern32", ls=0.15)
+    N = O.causal_neighbors(P.X, P.Z, P.theta, 6)
+    vif = O.VIF(P.X, P.Z, P.theta, N)
+    b_d, _, _ = O.laplace_mode(vif, P.y, dense=True)
+    g, _ = O.bern_grad_W(P.y, b_d)
+    stat = np.linalg.norm(g - np.linalg.solve(vif.dense_Sigma_dagger(), b_d)) / np.linalg.norm(g)
+    assert stat < 1e-8
+    b_p, steps, its = O.laplace_mode(vif, P.y, tol=1e-10)
+    np.testing.assert_allclose(b_p, b_d, rtol=1e-6, atol=1e-8)
+    assert steps < 20 and its > 0
