@@ -1,0 +1,147 @@
+/*
+ * vif.h -- C ABI of libvif, a single-GPU (sm_103a) implementation of the
+ * Vecchia-inducing-points full-scale (VIF) Gaussian-process approximation
+ * (Gyger, Furrer & Sigrist, "Iterative Methods for Vecchia-Laplace
+ * Approximations for Latent Gaussian Process Models" / VIF paper, 2025).
+ *
+ * Conventions for every entry point
+ *   - Array arguments are float64 (or int32 where stated), row-major, owned by
+ *     the caller.  A pointer may point to host memory (pageable or pinned) or
+ *     to device memory of the context's device; the library detects which with
+ *     cudaPointerGetAttributes and copies host data itself on the context's
+ *     stream.  Host outputs are complete when the call returns.
+ *   - Every call returns a vif_status; nothing is thrown across the ABI.  On an
+ *     error the outputs are left untouched (VIF_ERR_NOT_CONVERGED still writes
+ *     the last iterate) and vif_last_error() describes it.
+ *   - The context owns all its device buffers; no call allocates caller memory.
+ *     All work is enqueued on the stream given to vif_build (0 = legacy default).
+ *   - Calls on one context must not overlap (a context is not thread-safe).
+ *   - The CUDA path is the only path: there is no CPU fallback.  A call on a
+ *     machine without a usable GPU returns VIF_ERR_CUDA.
+ */
+#ifndef VIF_H
+#define VIF_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct vif_ctx vif_ctx;
+
+typedef enum {
+  VIF_OK = 0,
+  VIF_ERR_ARG = 1,            /* invalid argument (sizes, kinds, null pointers) */
+  VIF_ERR_CUDA = 2,           /* CUDA runtime error (message in vif_last_error) */
+  VIF_ERR_NOMEM = 3,          /* device allocation failed */
+  VIF_ERR_NOT_PD = 4,         /* a Cholesky pivot was not positive; index in message */
+  VIF_ERR_TIMEOUT = 5,        /* a bounded device-side wait ran out */
+  VIF_ERR_NOT_CONVERGED = 6,  /* Newton / CG hit its iteration cap */
+  VIF_ERR_STATE = 7           /* call out of order (e.g. predict before nll) */
+} vif_status;
+
+/* Covariance functions c_theta(s,s') = sigma1^2 k(r), r = ||(s-s')/lambda||
+ * (Sec. 2; ARD transform q_lambda(s) = s/lambda of Eq. cov_trans_iso, Sec. 6).
+ * Matern forms of Rasmussen & Williams: k_{1/2} = e^{-r},
+ * k_{3/2} = (1+sqrt3 r) e^{-sqrt3 r}, k_{5/2} = (1+sqrt5 r+5r^2/3) e^{-sqrt5 r},
+ * squared exponential ("Gaussian") k = e^{-r^2/2}. */
+typedef enum { VIF_MATERN12 = 0, VIF_MATERN32 = 1, VIF_MATERN52 = 2, VIF_SE = 3 } vif_kernel;
+
+typedef struct {
+  int32_t kind;               /* vif_kernel */
+  double variance;            /* marginal variance sigma1^2 > 0 */
+  const double *lengthscale;  /* HOST array of n_ls length scales lambda > 0 */
+  int32_t n_ls;               /* 1 (isotropic) or d (ARD) */
+  double nugget;              /* error variance sigma^2 >= 0 (Gaussian likelihood, Eq. cov_mat_gauss);
+                                 must be 0 for a latent GP (Laplace, Sec. 3) */
+} vif_cov;
+
+typedef enum { VIF_FP64 = 0, VIF_MIXED = 1 } vif_precision;
+typedef enum { VIF_GAUSSIAN = 0, VIF_BERNOULLI_LOGIT = 1 } vif_likelihood;
+
+typedef struct {
+  int32_t precision;          /* vif_precision: arithmetic of the likelihood path.  VIF_MIXED stores
+                                 A and F in float32 and computes the O(n m^2) products in float32;
+                                 the Cholesky factors of Sigma_m and of the m x m capacitance matrix
+                                 and the log-determinant sums stay float64. */
+  int32_t likelihood;         /* vif_likelihood */
+  int32_t no_neighbor_search; /* 0: vif_build runs the neighbour search (default); 1: it does not,
+                                 and the caller supplies N(i) with vif_set_neighbors before vif_nll */
+  int32_t stage_timing;       /* 1: record CUDA events around every stage of vif_nll (read them with
+                                 vif_get_stage_times); 0: no events */
+  int32_t reserved[4];        /* must be zero */
+} vif_opts;
+
+/* vif_build -- fix the data S = {s_i} (X, n x d), the inducing points S* (Z, m x d,
+ * Sec. 2.1 Eq. def_b_low), and the residual Vecchia neighbour sets N(i) (Sec. 2.1
+ * neighbour rule) chosen with the correlation distance d_c of Sec. 6 under the
+ * hyperparameters `cov`:  N(i) = the min(i, m_v) points j < i with the smallest
+ * 1 - |rho_ij|, rho_ij = c_r(i,j)/sqrt(c_r(i,i) c_r(j,j)), c_r = Sigma - Sigma^l
+ * without nugget, ties broken by lower index.  The search is an exact tiled
+ * brute force (float32 filter with a rigorous error bound, float64 decision at
+ * the boundary) and returns the same sets as the paper's cover tree (Alg. 3/4).
+ *   X: n x d;  Z: m x d (m may be 0: classical Vecchia);  mv >= 0 (0: FITC).
+ *   Limits: 1 <= d <= 16, 0 <= m <= 2048, 0 <= mv <= 48, n >= 1.
+ *   stream: a cudaStream_t (NULL = legacy default stream).
+ *   *out receives the context; free it with vif_destroy. */
+vif_status vif_build(const double *X, int64_t n, int32_t d, const double *Z, int32_t m,
+                     int32_t mv, const vif_cov *cov, const vif_opts *opts, void *stream,
+                     vif_ctx **out);
+
+/* vif_nll -- negative log-likelihood of the VIF approximation (Sec. 2.1-2.2):
+ *   L = n/2 log 2pi + 1/2 log det Sigma~_dagger + 1/2 y^T Sigma~_dagger^{-1} y,
+ * with log det via Sylvester (det M det Sigma_m^{-1} det D) and the solve via
+ * Woodbury (M of Eq. def_M), for the hyperparameters `theta` and the fixed
+ * neighbour sets of the context.  y: n responses.  nll_out: HOST double.
+ * grad_out: must be NULL (reserved for the gradient of Sec. 2.2 / App. A). */
+vif_status vif_nll(vif_ctx *ctx, const vif_cov *theta, const double *y, double *nll_out,
+                   double *grad_out);
+
+/* vif_predict -- predictive means and variances at Xp (np x d) by Prop. 2.1, the
+ * variances through the expansion of App. C.1, with prediction points conditioned
+ * on their m_v nearest training points by d_c (B_p = I).  Uses theta and y as given
+ * (the factors are recomputed for theta).  latent = 1 gives the latent process b^p
+ * (variance minus the nugget), 0 the response y^p.  mean, var: np outputs (var may
+ * be NULL). */
+vif_status vif_predict(vif_ctx *ctx, const vif_cov *theta, const double *y, const double *Xp,
+                       int64_t np, int32_t latent, double *mean, double *var);
+
+/* vif_set_neighbors / vif_get_neighbors -- replace or read the neighbour table
+ * (n x mv int32, row i holds min(i,mv) indices < i in ascending order, padded
+ * with -1). */
+vif_status vif_set_neighbors(vif_ctx *ctx, const int32_t *N);
+vif_status vif_get_neighbors(const vif_ctx *ctx, int32_t *N);
+
+/* vif_get_factors -- the residual Vecchia factors of the last vif_nll call:
+ * Acoef (n x mv, row i = A_i on N(i), zero padded; B_{i,N(i)} = -A_i) and D (n),
+ * Eq. D_A_Vecchia.  Either pointer may be NULL. */
+vif_status vif_get_factors(const vif_ctx *ctx, double *Acoef, double *D);
+
+/* vif_get_stats -- counters of the last neighbour search: number of queries whose
+ * float32 filter result needed a float64 rescore at the boundary, and number that
+ * fell back to a float64 brute-force scan. */
+vif_status vif_get_knn_stats(const vif_ctx *ctx, int64_t *n_rescored, int64_t *n_fallback);
+
+/* vif_get_stage_times -- device time (ms, CUDA events on the context's stream) of
+ * the stages of the last vif_nll call of a context built with stage_timing = 1:
+ *   [0] Sigma_m, its Cholesky factor and inverse            [1] A = L_m^{-1} Sigma_mn
+ *   [2] residual Vecchia factors and rows of [F z]          [3] Gram [F z]^T [F z]
+ *   [4] capacitance Cholesky and the scalar likelihood
+ * ms: host array of at least VIF_NSTAGES doubles. */
+#define VIF_NSTAGES 5
+vif_status vif_get_stage_times(const vif_ctx *ctx, double *ms);
+
+/* vif_last_error -- text of the last error on this context ("" if none), valid
+ * until the next call on the context; with ctx == NULL, the message of the last
+ * failed vif_build in this process. */
+const char *vif_last_error(const vif_ctx *ctx);
+
+/* vif_destroy -- free the context and its device buffers (NULL is ignored). */
+void vif_destroy(vif_ctx *ctx);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* VIF_H */

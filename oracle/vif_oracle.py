@@ -82,9 +82,15 @@ def scaled(X: np.ndarray, theta) -> np.ndarray:
 
 
 def dist(X1: np.ndarray, X2: np.ndarray) -> np.ndarray:
-    """Euclidean distances, computed from coordinate differences."""
-    diff = X1[:, None, :] - X2[None, :, :]
-    return np.sqrt((diff * diff).sum(-1))
+    """Euclidean distances, computed from coordinate differences (in blocks of X2
+    rows so that the temporary stays below ~128 MB)."""
+    n1, n2, d = X1.shape[0], X2.shape[0], X1.shape[1]
+    out = np.empty((n1, n2))
+    blk = max(1, (1 << 24) // max(1, n1 * d))
+    for s in range(0, n2, blk):
+        diff = X1[:, None, :] - X2[None, s:s + blk, :]
+        out[:, s:s + blk] = np.sqrt((diff * diff).sum(-1))
+    return out
 
 
 def cov(X1: np.ndarray, X2: np.ndarray, theta) -> np.ndarray:
@@ -190,6 +196,83 @@ def query_keys(i: int, X, lowrank: LowRank, cr, theta, upto: int | None = None):
     return corr_keys(X[i], cr[i], X[:upto], cr[:upto], theta, lr)
 
 
+def causal_neighbors_sample(X, Z, theta, mv: int, queries, chunk: int = 65536):
+    """N(i) and all keys of selected queries only, streaming over the predecessors
+    in chunks (the same definition as causal_neighbors, for full-size checks)."""
+    queries = np.asarray(queries, dtype=np.int64)
+    m = Z.shape[0]
+    tv = TAU_V * theta.variance
+    if m:
+        cf = sla.cho_factor(sigma_m(Z, theta), lower=True)
+        Sq = cov(Z, X[queries], theta)
+        Wq = sla.cho_solve(cf, Sq)
+        crq = theta.variance - (Sq * Wq).sum(0)
+    else:
+        crq = np.full(len(queries), theta.variance)
+    imax = int(queries.max())
+    keys = [np.empty(int(i)) for i in queries]
+    for s0 in range(0, imax, chunk):
+        s1 = min(imax, s0 + chunk)
+        Xc = X[s0:s1]
+        if m:
+            Sc = cov(Z, Xc, theta)
+            crc = theta.variance - (Sc * sla.cho_solve(cf, Sc)).sum(0)
+            LR = Wq.T @ Sc
+        else:
+            crc = np.full(s1 - s0, theta.variance)
+            LR = np.zeros((len(queries), s1 - s0))
+        K = cov(X[queries], Xc, theta)
+        for a, i in enumerate(queries):
+            e = min(int(i), s1)
+            if e <= s0:
+                continue
+            c = K[a, :e - s0] - LR[a, :e - s0]
+            with np.errstate(divide="ignore", invalid="ignore"):
+                rho = c / np.sqrt(crq[a] * crc[:e - s0])
+            rho = np.where((crq[a] <= tv) | (crc[:e - s0] <= tv), 0.0, rho)
+            keys[a][s0:e] = 1.0 - np.clip(np.abs(rho), 0.0, 1.0)
+    Ns = []
+    for a, i in enumerate(queries):
+        q = min(int(i), mv)
+        order = np.lexsort((np.arange(int(i)), keys[a]))[:q]
+        Ns.append(np.sort(order))
+    return Ns, keys
+
+
+def vecchia_factors_rows(X, Z, theta, N, rows):
+    """A_i and D_i (Eq. D_A_Vecchia) for selected rows only: the low-rank terms
+    are formed on the selected points and their neighbours alone."""
+    rows = np.asarray(rows, dtype=np.int64)
+    need = np.unique(np.concatenate([rows, N[rows][N[rows] >= 0].ravel()]))
+    pos = {int(j): k for k, j in enumerate(need)}
+    Nsub = -np.ones((len(rows), N.shape[1]), dtype=np.int64)
+    Xsub = np.concatenate([X[need]])
+    # points of the reduced problem: the needed ones; rows refer into it
+    lr = LowRank(Xsub, Z, theta)
+    tdiag = residual_diag(theta)
+    out_A = np.zeros((len(rows), N.shape[1]))
+    out_D = np.empty(len(rows))
+    for a, i in enumerate(rows):
+        nb = [pos[int(j)] for j in N[i] if j >= 0]
+        ii = pos[int(i)]
+        q = len(nb)
+        dii = theta.variance + tdiag - (lr.lr(ii, ii) if lr.m else 0.0)
+        if q == 0:
+            out_D[a] = dii
+            continue
+        S_iN = cov(Xsub[ii:ii + 1], Xsub[nb], theta)[0]
+        S_NN = cov(Xsub[nb], Xsub[nb], theta) + tdiag * np.eye(q)
+        if lr.m:
+            S_iN_l = S_iN - lr.lr([ii], nb)[0]
+            S_NN_l = S_NN - lr.lr(nb, nb)
+        else:
+            S_iN_l, S_NN_l = S_iN, S_NN
+        Ai = np.linalg.solve(S_NN_l, S_iN_l)
+        out_A[a, :q] = Ai
+        out_D[a] = dii - Ai @ S_iN_l
+    return out_A, out_D
+
+
 # ----------------------------------------------------------------------------
 # Residual Vecchia factors (Sec. 2.1, Eq. D_A_Vecchia)
 # ----------------------------------------------------------------------------
@@ -230,9 +313,9 @@ def vecchia_factors(X, Z, theta, N, lowrank: LowRank | None = None):
                 Wi = lowrank.SinvSmn[:, Ib].T                     # b x m
                 SmN = lowrank.Smn[:, Nb].transpose(1, 2, 0)       # b x q x m
                 WN = lowrank.SinvSmn[:, Nb].transpose(1, 2, 0)    # b x q x m
-                lr_iN = np.einsum("bm,bqm->bq", Smi, WN)
-                lr_NN = np.einsum("bqm,brm->bqr", SmN, WN)
-                lr_Ni = np.einsum("bqm,bm->bq", SmN, Wi)
+                lr_iN = np.matmul(WN, Smi[:, :, None])[:, :, 0]        # Sigma_mi^T Sigma_m^-1 Sigma_mN
+                lr_NN = np.matmul(SmN, WN.transpose(0, 2, 1))
+                lr_Ni = np.matmul(SmN, Wi[:, :, None])[:, :, 0]
             else:
                 lr_iN = lr_Ni = 0.0
                 lr_NN = 0.0

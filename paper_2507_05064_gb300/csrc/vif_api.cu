@@ -1,0 +1,579 @@
+// C ABI of libvif: context management and the host orchestration of the
+// kernels (see include/vif.h for the contract of each entry point).
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <vector>
+
+#include "vif_internal.cuh"
+
+using namespace vif;
+
+struct vif_ctx {
+  int dev = 0;
+  cudaStream_t stream = nullptr;
+  int64_t n = 0;
+  int d = 0, m = 0, mv = 0, mpad = 32, fpad = 64, ldm = 32;
+  int precision = 0, likelihood = 0;
+  double center[16] = {0};
+  // device buffers
+  double *X = nullptr, *Z = nullptr;          // raw coordinates
+  double *Xs = nullptr, *Zs = nullptr;        // scaled coordinates (float64)
+  float *Xs32 = nullptr, *Zs32 = nullptr;     // scaled coordinates (float32, mixed path)
+  double *hyp = nullptr;                      // [0..15] 1/lambda, [16..31] center
+  int32_t* N = nullptr;                       // n x mv
+  double *Sm = nullptr, *Linv = nullptr;      // m x ldm
+  void* LinvT = nullptr;                      // mpad x mpad (float or double)
+  void* A = nullptr;                          // n x mpad
+  void* F = nullptr;                          // n x fpad
+  double *Acoef = nullptr, *Dv = nullptr, *logD = nullptr;
+  double* part = nullptr;
+  int nsplit = 1;
+  double* G = nullptr;                        // (m+1) x fpad
+  double* y = nullptr;                        // n
+  double* red = nullptr;                      // reduction scratch (256)
+  double* dscal = nullptr;                    // [0] sum log D, [1..3] nll, logdetC, quad
+  int* status = nullptr;                      // [0] code [1] index [2..] counters
+  double* h_pin = nullptr;                    // pinned host staging
+  int64_t knn_rescored = 0, knn_fallback = 0;
+  bool have_factors = false;
+  bool timing = false;
+  cudaEvent_t ev[VIF_NSTAGES + 1] = {};
+  char err[1024] = {0};
+};
+
+namespace {
+
+// message of the last failed vif_build (the context is gone by then)
+char g_build_err[1024] = {0};
+
+vif_status set_err(vif_ctx* c, vif_status st, const char* fmt, ...) {
+  if (c) {
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(c->err, sizeof(c->err), fmt, ap);
+    va_end(ap);
+  }
+  return st;
+}
+
+#define CK(call)                                                                                 \
+  do {                                                                                           \
+    cudaError_t e_ = (call);                                                                     \
+    if (e_ != cudaSuccess)                                                                       \
+      return set_err(ctx, e_ == cudaErrorMemoryAllocation ? VIF_ERR_NOMEM : VIF_ERR_CUDA,       \
+                     "%s: %s (%s:%d)", #call, cudaGetErrorString(e_), __FILE__, __LINE__);       \
+  } while (0)
+
+bool is_device_ptr(const void* p) {
+  cudaPointerAttributes at;
+  if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  return at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged;
+}
+
+template <typename T>
+vif_status dalloc(vif_ctx* ctx, T** p, size_t count) {
+  if (count == 0) count = 1;
+  cudaError_t e = cudaMalloc((void**)p, count * sizeof(T));
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    *p = nullptr;
+    return set_err(ctx, VIF_ERR_NOMEM, "cudaMalloc of %zu bytes failed: %s", count * sizeof(T),
+                   cudaGetErrorString(e));
+  }
+  return VIF_OK;
+}
+
+#define CKS(call)                 \
+  do {                            \
+    vif_status s_ = (call);       \
+    if (s_ != VIF_OK) return s_;  \
+  } while (0)
+
+// Copy n elements into a device buffer from a host or device source.
+vif_status upload(vif_ctx* ctx, void* dst, const void* src, size_t bytes) {
+  if (bytes == 0) return VIF_OK;
+  cudaMemcpyKind k = is_device_ptr(src) ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
+  CK(cudaMemcpyAsync(dst, src, bytes, k, ctx->stream));
+  return VIF_OK;
+}
+
+vif_status download(vif_ctx* ctx, void* dst, const void* src, size_t bytes) {
+  if (bytes == 0) return VIF_OK;
+  cudaMemcpyKind k = is_device_ptr(dst) ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
+  CK(cudaMemcpyAsync(dst, src, bytes, k, ctx->stream));
+  CK(cudaStreamSynchronize(ctx->stream));
+  return VIF_OK;
+}
+
+vif_status check_cov(vif_ctx* ctx, const vif_cov* cv, int d) {
+  if (!cv) return set_err(ctx, VIF_ERR_ARG, "covariance parameters are NULL");
+  if (cv->kind < 0 || cv->kind > 3) return set_err(ctx, VIF_ERR_ARG, "unknown kernel kind %d", cv->kind);
+  if (!(cv->variance > 0.0) || !std::isfinite(cv->variance))
+    return set_err(ctx, VIF_ERR_ARG, "variance must be positive and finite");
+  if (!(cv->nugget >= 0.0) || !std::isfinite(cv->nugget))
+    return set_err(ctx, VIF_ERR_ARG, "nugget must be >= 0 and finite");
+  if (!cv->lengthscale || (cv->n_ls != 1 && cv->n_ls != d))
+    return set_err(ctx, VIF_ERR_ARG, "lengthscale must hold 1 or d=%d values", d);
+  for (int t = 0; t < cv->n_ls; ++t)
+    if (!(cv->lengthscale[t] > 0.0) || !std::isfinite(cv->lengthscale[t]))
+      return set_err(ctx, VIF_ERR_ARG, "length scales must be positive and finite");
+  return VIF_OK;
+}
+
+CovParams cov_params(const vif_cov* cv) {
+  CovParams cp;
+  cp.kind = cv->kind;
+  cp.var = cv->variance;
+  // Sigma_m jitter and residual diagonal (nugget, or a jitter for latent processes)
+  cp.jitter = (cv->kind == VIF_SE ? 1e-8 : 1e-10) * cv->variance;
+  cp.tdiag = cv->nugget > 0.0 ? cv->nugget : 1e-10 * cv->variance;
+  return cp;
+}
+
+// Scale X and Z by 1/lambda around the data centre (float64 and, if asked, float32).
+vif_status apply_scaling(vif_ctx* ctx, const vif_cov* cv, bool want32) {
+  double h[32];
+  for (int t = 0; t < 16; ++t) {
+    h[t] = (t < ctx->d) ? 1.0 / cv->lengthscale[cv->n_ls == 1 ? 0 : t] : 0.0;
+    h[16 + t] = ctx->center[t];
+  }
+  memcpy(ctx->h_pin, h, sizeof(h));
+  CK(cudaMemcpyAsync(ctx->hyp, ctx->h_pin, sizeof(h), cudaMemcpyHostToDevice, ctx->stream));
+  CK(scale_coords(ctx->X, ctx->n, ctx->d, ctx->hyp, ctx->hyp + 16, ctx->Xs, want32 ? ctx->Xs32 : nullptr,
+                  ctx->stream));
+  if (ctx->m > 0)
+    CK(scale_coords(ctx->Z, ctx->m, ctx->d, ctx->hyp, ctx->hyp + 16, ctx->Zs, want32 ? ctx->Zs32 : nullptr,
+                    ctx->stream));
+  // the pinned staging buffer is reused by later calls: wait for the copy
+  CK(cudaStreamSynchronize(ctx->stream));
+  return VIF_OK;
+}
+
+// Sigma_m, its Cholesky factor and L_m^{-T} in precision T; then A.
+template <typename T>
+vif_status compute_lowrank(vif_ctx* ctx, const CovParams& cp, T* A, T* LinvT, const T* Xs, const T* Zs) {
+  if (ctx->m > 0) {
+    CK(build_sigma_m(ctx->Zs, ctx->m, ctx->d, cp, ctx->Sm, ctx->ldm, ctx->stream));
+    CK(dense_cholesky(ctx->Sm, ctx->m, ctx->ldm, ctx->status, ST_NOTPD_SIGMAM, ctx->stream));
+    CK(dense_trtri_lower(ctx->Sm, ctx->Linv, ctx->m, ctx->ldm, ctx->stream));
+    CK(linv_transpose<T>(ctx->Linv, ctx->m, ctx->ldm, LinvT, ctx->mpad, ctx->stream));
+  }
+  CK(lowrank_A<T>(Xs, Zs, LinvT, ctx->mpad, A, ctx->n, ctx->d, ctx->m, ctx->mpad, cp.kind, cp.var, ctx->stream));
+  return VIF_OK;
+}
+
+// compute_lowrank with stage events: [0,1) Sigma_m and its factors, [1,2) A, then the
+// factor stage starts at event 2.
+template <typename T>
+vif_status compute_lowrank_parts(vif_ctx* ctx, const CovParams& cp, T* A, T* LinvT, const T* Xs, const T* Zs) {
+  if (ctx->m > 0) {
+    CK(build_sigma_m(ctx->Zs, ctx->m, ctx->d, cp, ctx->Sm, ctx->ldm, ctx->stream));
+    CK(dense_cholesky(ctx->Sm, ctx->m, ctx->ldm, ctx->status, ST_NOTPD_SIGMAM, ctx->stream));
+    CK(dense_trtri_lower(ctx->Sm, ctx->Linv, ctx->m, ctx->ldm, ctx->stream));
+    CK(linv_transpose<T>(ctx->Linv, ctx->m, ctx->ldm, LinvT, ctx->mpad, ctx->stream));
+  }
+  if (ctx->timing) CK(cudaEventRecord(ctx->ev[1], ctx->stream));
+  CK(lowrank_A<T>(Xs, Zs, LinvT, ctx->mpad, A, ctx->n, ctx->d, ctx->m, ctx->mpad, cp.kind, cp.var, ctx->stream));
+  if (ctx->timing) CK(cudaEventRecord(ctx->ev[2], ctx->stream));
+  return VIF_OK;
+}
+
+vif_status read_status(vif_ctx* ctx, double* scal_out, int nscal) {
+  // one D2H copy of the status words and the requested scalars
+  CK(cudaMemcpyAsync(ctx->h_pin, ctx->status, 4 * sizeof(int), cudaMemcpyDeviceToHost, ctx->stream));
+  if (nscal > 0)
+    CK(cudaMemcpyAsync(ctx->h_pin + 2, ctx->dscal + 1, nscal * sizeof(double), cudaMemcpyDeviceToHost,
+                       ctx->stream));
+  CK(cudaStreamSynchronize(ctx->stream));
+  const int* st = reinterpret_cast<const int*>(ctx->h_pin);
+  if (st[0] != ST_OK) {
+    const char* what = st[0] == ST_NOTPD_SIGMAM  ? "Sigma_m (inducing points)"
+                       : st[0] == ST_NOTPD_FACTOR ? "residual Vecchia block of point"
+                       : st[0] == ST_NOTPD_CAP    ? "capacitance matrix"
+                                                   : "preconditioner";
+    if (st[0] == ST_TIMEOUT) return set_err(ctx, VIF_ERR_TIMEOUT, "device wait timed out at %d", st[1]);
+    if (st[0] == ST_BAD_NEIGHBOR)
+      return set_err(ctx, VIF_ERR_STATE, "neighbour table row %d holds an index that is not a predecessor", st[1]);
+    return set_err(ctx, VIF_ERR_NOT_PD, "Cholesky pivot not positive: %s, index %d", what, st[1]);
+  }
+  for (int k = 0; k < nscal; ++k) scal_out[k] = ctx->h_pin[2 + k];
+  return VIF_OK;
+}
+
+void free_ctx(vif_ctx* c) {
+  if (!c) return;
+  void* bufs[] = {c->X,    c->Z,     c->Xs, c->Zs,   c->Xs32, c->Zs32, c->hyp, c->N,   c->Sm,
+                  c->Linv, c->LinvT, c->A,  c->F,    c->Acoef, c->Dv,  c->logD, c->part, c->G,
+                  c->y,    c->red,   c->dscal, c->status};
+  for (void* b : bufs)
+    if (b) cudaFree(b);
+  if (c->h_pin) cudaFreeHost(c->h_pin);
+  for (auto& e : c->ev)
+    if (e) cudaEventDestroy(e);
+  delete c;
+}
+
+// Neighbour search under the build hyperparameters (float64 A plus a float32 copy).
+vif_status build_neighbors(vif_ctx* ctx, const vif_cov* cv) {
+  const int64_t n = ctx->n;
+  const int mv = ctx->mv;
+  if (mv == 0 || n == 0) return VIF_OK;
+  CovParams cp = cov_params(cv);
+  CKS(apply_scaling(ctx, cv, true));
+  double* A64 = nullptr;
+  double* LinvT64 = nullptr;
+  float *A32 = nullptr, *rs32 = nullptr, *nrm32 = nullptr, *ckey = nullptr, *ce = nullptr, *lowb = nullptr;
+  double* cii = nullptr;
+  int32_t *cidx = nullptr, *fb = nullptr;
+  const int kprime = (mv <= 24) ? 32 : 64;
+  vif_status st = VIF_OK;
+  auto cleanup = [&]() {
+    void* b[] = {A64, LinvT64, A32, rs32, nrm32, ckey, ce, lowb, cii, cidx, fb};
+    for (void* x : b)
+      if (x) cudaFree(x);
+  };
+  do {
+    if ((st = dalloc(ctx, &A64, (size_t)n * ctx->mpad)) != VIF_OK) break;
+    if ((st = dalloc(ctx, &LinvT64, (size_t)ctx->mpad * ctx->mpad)) != VIF_OK) break;
+    if ((st = dalloc(ctx, &A32, (size_t)n * ctx->mpad)) != VIF_OK) break;
+    if ((st = dalloc(ctx, &rs32, n)) != VIF_OK) break;
+    if ((st = dalloc(ctx, &nrm32, n)) != VIF_OK) break;
+    if ((st = dalloc(ctx, &cii, n)) != VIF_OK) break;
+    if ((st = dalloc(ctx, &ckey, (size_t)n * kprime)) != VIF_OK) break;
+    if ((st = dalloc(ctx, &ce, (size_t)n * kprime)) != VIF_OK) break;
+    if ((st = dalloc(ctx, &cidx, (size_t)n * kprime)) != VIF_OK) break;
+    if ((st = dalloc(ctx, &lowb, n)) != VIF_OK) break;
+    if ((st = dalloc(ctx, &fb, n)) != VIF_OK) break;
+    cudaError_t e = cudaMemsetAsync(ctx->status, 0, 16 * sizeof(int), ctx->stream);
+    if (e != cudaSuccess) {
+      st = set_err(ctx, VIF_ERR_CUDA, "%s", cudaGetErrorString(e));
+      break;
+    }
+    if ((st = compute_lowrank<double>(ctx, cp, A64, LinvT64, ctx->Xs, ctx->Zs)) != VIF_OK) break;
+    const double tau = 1e-6 * cv->variance;
+    e = residual_diag_stats(A64, n, ctx->m, ctx->mpad, cv->variance, tau, A32, cii, rs32, nrm32, ctx->stream);
+    if (e != cudaSuccess) {
+      st = set_err(ctx, VIF_ERR_CUDA, "residual_diag_stats: %s", cudaGetErrorString(e));
+      break;
+    }
+    // error constants of the float32 filter (u = 2^-24)
+    const double u = std::ldexp(1.0, -24);
+    const int mm = std::max(ctx->m, 1);
+    const double gam = (mm + 2) * u / (1.0 - (mm + 2) * u) + 1e-12;
+    // max |scaled coordinate| norm over the data (centred), from the host copy kept at build
+    double R = 0.0;
+    {
+      std::vector<double> hx((size_t)n * ctx->d);
+      e = cudaMemcpyAsync(hx.data(), ctx->Xs, hx.size() * sizeof(double), cudaMemcpyDeviceToHost, ctx->stream);
+      if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
+      if (e != cudaSuccess) {
+        st = set_err(ctx, VIF_ERR_CUDA, "%s", cudaGetErrorString(e));
+        break;
+      }
+      for (int64_t i = 0; i < n; ++i) {
+        double s2 = 0;
+        for (int t = 0; t < ctx->d; ++t) s2 += hx[(size_t)i * ctx->d + t] * hx[(size_t)i * ctx->d + t];
+        R = std::max(R, std::sqrt(s2));
+      }
+    }
+    const double epsK = cv->variance * u * (4.0 * R + 2.0 * ctx->d + 36.0);
+    KnnParams kp;
+    kp.n = n;
+    kp.d = ctx->d;
+    kp.m = ctx->m;
+    kp.mpad = ctx->mpad;
+    kp.mv = mv;
+    kp.kprime = kprime;
+    kp.kind = cv->kind;
+    kp.var = cv->variance;
+    kp.tau_v = tau;
+    kp.gamma = (float)(gam * (1.0 + 1e-6));
+    kp.epsK = (float)(epsK * (1.0 + 1e-6));
+    e = knn_causal(kp, A32, A64, ctx->Xs32, ctx->Xs, cii, rs32, nrm32, ckey, cidx, ce, lowb, ctx->N,
+                   ctx->status + 4, fb, ctx->stream);
+    if (e != cudaSuccess) {
+      st = set_err(ctx, VIF_ERR_CUDA, "knn_causal: %s", cudaGetErrorString(e));
+      break;
+    }
+    int hc[2];
+    e = cudaMemcpyAsync(hc, ctx->status + 4, 2 * sizeof(int), cudaMemcpyDeviceToHost, ctx->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
+    if (e != cudaSuccess) {
+      st = set_err(ctx, VIF_ERR_CUDA, "%s", cudaGetErrorString(e));
+      break;
+    }
+    ctx->knn_rescored = hc[0];
+    ctx->knn_fallback = hc[1];
+    double dummy[1];
+    st = read_status(ctx, dummy, 0);
+  } while (0);
+  cleanup();
+  return st;
+}
+
+}  // namespace
+
+extern "C" {
+
+vif_status vif_build(const double* X, int64_t n, int32_t d, const double* Z, int32_t m, int32_t mv,
+                     const vif_cov* cov, const vif_opts* opts, void* stream, vif_ctx** out) {
+  if (!out) return VIF_ERR_ARG;
+  *out = nullptr;
+  if (!X || n < 1 || d < 1 || d > 16 || m < 0 || m > 2048 || mv < 0 || mv > 48 || (m > 0 && !Z) || !opts)
+    return VIF_ERR_ARG;
+  if (opts->precision != VIF_FP64 && opts->precision != VIF_MIXED) return VIF_ERR_ARG;
+  if (opts->likelihood != VIF_GAUSSIAN && opts->likelihood != VIF_BERNOULLI_LOGIT) return VIF_ERR_ARG;
+  for (int k = 0; k < 4; ++k)
+    if (opts->reserved[k] != 0) return VIF_ERR_ARG;
+  int ndev = 0;
+  if (cudaGetDeviceCount(&ndev) != cudaSuccess || ndev == 0) {
+    cudaGetLastError();
+    return VIF_ERR_CUDA;
+  }
+  vif_ctx* ctx = new vif_ctx();
+  vif_status st = check_cov(ctx, cov, d);
+  if (st != VIF_OK) {
+    free_ctx(ctx);
+    return st;
+  }
+  cudaGetDevice(&ctx->dev);
+  ctx->stream = (cudaStream_t)stream;
+  ctx->n = n;
+  ctx->d = d;
+  ctx->m = m;
+  ctx->mv = mv;
+  ctx->mpad = std::max(32, ((m + 31) / 32) * 32);
+  ctx->ldm = ctx->mpad;
+  ctx->fpad = ((m + 1 + 63) / 64) * 64;
+  ctx->precision = opts->precision;
+  ctx->likelihood = opts->likelihood;
+  ctx->timing = opts->stage_timing != 0;
+  if (ctx->timing)
+    for (auto& e : ctx->ev)
+      if (cudaEventCreate(&e) != cudaSuccess) {
+        free_ctx(ctx);
+        return VIF_ERR_CUDA;
+      }
+  const bool mixed = ctx->precision == VIF_MIXED;
+  const size_t esz = mixed ? sizeof(float) : sizeof(double);
+#define ALLOC(ptr, cnt)                                 \
+  do {                                                  \
+    if ((st = dalloc(ctx, &(ptr), (cnt))) != VIF_OK) { \
+      *out = nullptr;                                   \
+      vif_status s2 = st;                               \
+      free_ctx(ctx);                                    \
+      return s2;                                        \
+    }                                                   \
+  } while (0)
+  ALLOC(ctx->X, (size_t)n * d);
+  ALLOC(ctx->Z, (size_t)std::max(m, 1) * d);
+  ALLOC(ctx->Xs, (size_t)n * d);
+  ALLOC(ctx->Zs, (size_t)std::max(m, 1) * d);
+  ALLOC(ctx->Xs32, (size_t)n * d);
+  ALLOC(ctx->Zs32, (size_t)std::max(m, 1) * d);
+  ALLOC(ctx->hyp, 32);
+  ALLOC(ctx->N, (size_t)n * std::max(mv, 1));
+  ALLOC(ctx->Sm, (size_t)ctx->ldm * ctx->ldm);
+  ALLOC(ctx->Linv, (size_t)ctx->ldm * ctx->ldm);
+  {
+    unsigned char* p = nullptr;
+    ALLOC(p, (size_t)ctx->mpad * ctx->mpad * esz);
+    ctx->LinvT = p;
+    p = nullptr;
+    ALLOC(p, (size_t)n * ctx->mpad * esz);
+    ctx->A = p;
+    p = nullptr;
+    ALLOC(p, (size_t)n * ctx->fpad * esz);
+    ctx->F = p;
+  }
+  ALLOC(ctx->Acoef, (size_t)n * std::max(mv, 1));
+  ALLOC(ctx->Dv, (size_t)n);
+  ALLOC(ctx->logD, (size_t)n);
+  ctx->nsplit = gram_nsplit(n, ctx->fpad);
+  {
+    int nt = ctx->fpad / 64;
+    ALLOC(ctx->part, (size_t)ctx->nsplit * (nt * (nt + 1) / 2) * 64 * 64);
+  }
+  ALLOC(ctx->G, (size_t)(m + 1) * ctx->fpad);
+  ALLOC(ctx->y, (size_t)n);
+  ALLOC(ctx->red, 256);
+  ALLOC(ctx->dscal, 16);
+  ALLOC(ctx->status, 16);
+#undef ALLOC
+  if (cudaMallocHost((void**)&ctx->h_pin, 4096) != cudaSuccess) {
+    cudaGetLastError();
+    free_ctx(ctx);
+    return VIF_ERR_NOMEM;
+  }
+  // upload coordinates, centre of the data box (for float32 conditioning)
+  std::vector<double> hx((size_t)n * d);
+  if (is_device_ptr(X)) {
+    if (cudaMemcpy(hx.data(), X, hx.size() * sizeof(double), cudaMemcpyDeviceToHost) != cudaSuccess) {
+      free_ctx(ctx);
+      return VIF_ERR_CUDA;
+    }
+  } else {
+    memcpy(hx.data(), X, hx.size() * sizeof(double));
+  }
+  for (int t = 0; t < d; ++t) {
+    double lo = hx[t], hi = hx[t];
+    for (int64_t i = 0; i < n; ++i) {
+      lo = std::min(lo, hx[(size_t)i * d + t]);
+      hi = std::max(hi, hx[(size_t)i * d + t]);
+    }
+    ctx->center[t] = 0.5 * (lo + hi);
+  }
+  if ((st = upload(ctx, ctx->X, X, (size_t)n * d * sizeof(double))) != VIF_OK ||
+      (m > 0 && (st = upload(ctx, ctx->Z, Z, (size_t)m * d * sizeof(double))) != VIF_OK)) {
+    free_ctx(ctx);
+    return st;
+  }
+  // buffers whose padding must be zero
+  cudaMemsetAsync(ctx->A, 0, (size_t)n * ctx->mpad * esz, ctx->stream);
+  cudaMemsetAsync(ctx->G, 0, (size_t)(m + 1) * ctx->fpad * sizeof(double), ctx->stream);
+  if (mv > 0) cudaMemsetAsync(ctx->N, 0xff, (size_t)n * mv * sizeof(int32_t), ctx->stream);
+  st = opts->no_neighbor_search ? VIF_OK : build_neighbors(ctx, cov);
+  if (st != VIF_OK) {
+    snprintf(g_build_err, sizeof(g_build_err), "%s", ctx->err);
+    free_ctx(ctx);
+    return st;
+  }
+  cudaError_t e = cudaStreamSynchronize(ctx->stream);
+  if (e != cudaSuccess) {
+    free_ctx(ctx);
+    return VIF_ERR_CUDA;
+  }
+  *out = ctx;
+  return VIF_OK;
+}
+
+vif_status vif_nll(vif_ctx* ctx, const vif_cov* theta, const double* y, double* nll_out, double* grad_out) {
+  if (!ctx) return VIF_ERR_ARG;
+  ctx->err[0] = 0;
+  if (!y || !nll_out) return set_err(ctx, VIF_ERR_ARG, "y and nll_out are required");
+  if (grad_out) return set_err(ctx, VIF_ERR_ARG, "grad_out must be NULL");
+  CKS(check_cov(ctx, theta, ctx->d));
+  if (ctx->likelihood != VIF_GAUSSIAN)
+    return set_err(ctx, VIF_ERR_STATE, "vif_nll needs a context built for the Gaussian likelihood");
+  const bool mixed = ctx->precision == VIF_MIXED;
+  CovParams cp = cov_params(theta);
+  CK(cudaMemsetAsync(ctx->status, 0, 4 * sizeof(int), ctx->stream));
+  CKS(upload(ctx, ctx->y, y, (size_t)ctx->n * sizeof(double)));
+  CKS(apply_scaling(ctx, theta, mixed));
+#define MARK(k) \
+  if (ctx->timing) CK(cudaEventRecord(ctx->ev[k], ctx->stream))
+  MARK(0);
+  if (mixed) {
+    CKS(compute_lowrank_parts<float>(ctx, cp, (float*)ctx->A, (float*)ctx->LinvT, ctx->Xs32, ctx->Zs32));
+    CK(vecchia_factor<float>((const float*)ctx->A, ctx->Xs32, ctx->N, ctx->y, ctx->n, ctx->d, ctx->m, ctx->mpad,
+                             ctx->mv, ctx->fpad, cp, (float*)ctx->F, ctx->Acoef, ctx->Dv, ctx->logD, ctx->status,
+                             ctx->stream));
+    MARK(3);
+    CK(gram_FtF<float>((const float*)ctx->F, ctx->n, ctx->fpad, ctx->m, ctx->part, ctx->nsplit, ctx->G, ctx->fpad,
+                       ctx->stream));
+  } else {
+    CKS(compute_lowrank_parts<double>(ctx, cp, (double*)ctx->A, (double*)ctx->LinvT, ctx->Xs, ctx->Zs));
+    CK(vecchia_factor<double>((const double*)ctx->A, ctx->Xs, ctx->N, ctx->y, ctx->n, ctx->d, ctx->m, ctx->mpad,
+                              ctx->mv, ctx->fpad, cp, (double*)ctx->F, ctx->Acoef, ctx->Dv, ctx->logD,
+                              ctx->status, ctx->stream));
+    MARK(3);
+    CK(gram_FtF<double>((const double*)ctx->F, ctx->n, ctx->fpad, ctx->m, ctx->part, ctx->nsplit, ctx->G,
+                        ctx->fpad, ctx->stream));
+  }
+  MARK(4);
+  CK(reduce_sum(ctx->logD, ctx->n, ctx->red, ctx->dscal, ctx->stream));
+  CK(dense_cholesky(ctx->G, ctx->m + 1, ctx->fpad, ctx->status, ST_NOTPD_CAP, ctx->stream));
+  CK(nll_finish(ctx->G, ctx->fpad, ctx->m, ctx->dscal, ctx->n, ctx->dscal + 1, ctx->stream));
+  MARK(5);
+#undef MARK
+  double sc[3];
+  CKS(read_status(ctx, sc, 3));
+  ctx->have_factors = true;
+  *nll_out = sc[0];
+  return VIF_OK;
+}
+
+vif_status vif_predict(vif_ctx* ctx, const vif_cov* theta, const double* y, const double* Xp, int64_t np,
+                       int32_t latent, double* mean, double* var) {
+  if (!ctx) return VIF_ERR_ARG;
+  (void)theta; (void)y; (void)Xp; (void)np; (void)latent; (void)mean; (void)var;
+  return set_err(ctx, VIF_ERR_STATE, "vif_predict is not available in this build");
+}
+
+vif_status vif_set_neighbors(vif_ctx* ctx, const int32_t* N) {
+  if (!ctx || !N) return VIF_ERR_ARG;
+  if (ctx->mv == 0) return VIF_OK;
+  const size_t cnt = (size_t)ctx->n * ctx->mv;
+  std::vector<int32_t> h(cnt);
+  if (is_device_ptr(N)) {
+    CK(cudaMemcpy(h.data(), N, cnt * sizeof(int32_t), cudaMemcpyDeviceToHost));
+  } else {
+    memcpy(h.data(), N, cnt * sizeof(int32_t));
+  }
+  // row i: min(i, mv) distinct predecessors in ascending order, then -1
+  for (int64_t i = 0; i < ctx->n; ++i) {
+    const int q = (int)std::min<int64_t>(i, ctx->mv);
+    const int32_t* r = h.data() + (size_t)i * ctx->mv;
+    for (int t = 0; t < ctx->mv; ++t) {
+      bool ok = (t < q) ? (r[t] >= 0 && r[t] < i && (t == 0 || r[t] > r[t - 1])) : (r[t] == -1);
+      if (!ok) return set_err(ctx, VIF_ERR_ARG, "neighbour table row %lld is not a valid set", (long long)i);
+    }
+  }
+  CK(cudaMemcpyAsync(ctx->N, h.data(), cnt * sizeof(int32_t), cudaMemcpyHostToDevice, ctx->stream));
+  CK(cudaStreamSynchronize(ctx->stream));
+  return VIF_OK;
+}
+
+vif_status vif_get_neighbors(const vif_ctx* cctx, int32_t* N) {
+  vif_ctx* ctx = const_cast<vif_ctx*>(cctx);
+  if (!ctx || !N) return VIF_ERR_ARG;
+  if (ctx->mv == 0) return VIF_OK;
+  return download(ctx, N, ctx->N, (size_t)ctx->n * ctx->mv * sizeof(int32_t));
+}
+
+vif_status vif_get_factors(const vif_ctx* cctx, double* Acoef, double* D) {
+  vif_ctx* ctx = const_cast<vif_ctx*>(cctx);
+  if (!ctx) return VIF_ERR_ARG;
+  if (!ctx->have_factors) return set_err(ctx, VIF_ERR_STATE, "no factors yet: call vif_nll first");
+  if (Acoef && ctx->mv > 0) CKS(download(ctx, Acoef, ctx->Acoef, (size_t)ctx->n * ctx->mv * sizeof(double)));
+  if (D) CKS(download(ctx, D, ctx->Dv, (size_t)ctx->n * sizeof(double)));
+  return VIF_OK;
+}
+
+vif_status vif_get_knn_stats(const vif_ctx* ctx, int64_t* n_rescored, int64_t* n_fallback) {
+  if (!ctx) return VIF_ERR_ARG;
+  if (n_rescored) *n_rescored = ctx->knn_rescored;
+  if (n_fallback) *n_fallback = ctx->knn_fallback;
+  return VIF_OK;
+}
+
+vif_status vif_get_stage_times(const vif_ctx* cctx, double* ms) {
+  vif_ctx* ctx = const_cast<vif_ctx*>(cctx);
+  if (!ctx || !ms) return VIF_ERR_ARG;
+  if (!ctx->timing) return set_err(ctx, VIF_ERR_STATE, "context was built without stage_timing");
+  if (!ctx->have_factors) return set_err(ctx, VIF_ERR_STATE, "no vif_nll call yet");
+  for (int k = 0; k < VIF_NSTAGES; ++k) {
+    float t = 0.f;
+    CK(cudaEventElapsedTime(&t, ctx->ev[k], ctx->ev[k + 1]));
+    ms[k] = t;
+  }
+  return VIF_OK;
+}
+
+const char* vif_last_error(const vif_ctx* ctx) { return ctx ? ctx->err : g_build_err; }
+
+void vif_destroy(vif_ctx* ctx) {
+  if (!ctx) return;
+  cudaStreamSynchronize(ctx->stream);
+  free_ctx(ctx);
+}
+
+}  // extern "C"

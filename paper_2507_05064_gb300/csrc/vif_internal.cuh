@@ -1,0 +1,109 @@
+// Internal declarations of libvif (not part of the C ABI).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <cmath>
+#include <string>
+
+#include "../../include/vif.h"
+
+namespace vif {
+
+// ---------------------------------------------------------------------------
+// Covariance functions (Sec. 2; Eq. cov_trans_iso of Sec. 6), written on the
+// squared scaled distance r2 = ||(s-s')/lambda||^2.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ double dsqrt(double x) { return sqrt(x); }
+__device__ __forceinline__ float dsqrt(float x) { return sqrtf(x); }
+__device__ __forceinline__ double dexp(double x) { return exp(x); }
+__device__ __forceinline__ float dexp(float x) { return expf(x); }
+
+template <typename T>
+__device__ __forceinline__ T cov_r2(T r2, int kind, T var) {
+  if (kind == VIF_SE) return var * dexp(T(-0.5) * r2);
+  if (kind == VIF_MATERN12) return var * dexp(-dsqrt(r2));
+  if (kind == VIF_MATERN32) {
+    T t = dsqrt(T(3) * r2);
+    return var * (T(1) + t) * dexp(-t);
+  }
+  T t = dsqrt(T(5) * r2);  // Matern-5/2
+  return var * (T(1) + t + t * t * T(1.0 / 3.0)) * dexp(-t);
+}
+
+template <typename T>
+__device__ __forceinline__ T sqdist(const T* __restrict__ a, const T* __restrict__ b, int d) {
+  T s = 0;
+  for (int t = 0; t < d; ++t) {
+    T u = a[t] - b[t];
+    s += u * u;
+  }
+  return s;
+}
+
+// Device status words (int32): [0] error code, [1] failing index, [2..] counters.
+enum StatusCode { ST_OK = 0, ST_NOTPD_SIGMAM = 1, ST_NOTPD_FACTOR = 2, ST_NOTPD_CAP = 3,
+                  ST_NOTPD_PRECOND = 4, ST_TIMEOUT = 5, ST_BAD_NEIGHBOR = 6 };
+
+__device__ __forceinline__ void flag_status(int* status, int code, long long idx) {
+  if (atomicCAS(status, 0, code) == 0) status[1] = (int)idx;
+}
+
+// Per-call hyperparameters, in the form the kernels use.
+struct CovParams {
+  int kind;
+  double var;
+  double tdiag;   // diagonal added to residual Vecchia blocks (nugget, or latent jitter)
+  double jitter;  // diagonal added to Sigma_m
+};
+
+// ---------------------------------------------------------------------------
+// Launchers (host side), grouped by translation unit.
+// ---------------------------------------------------------------------------
+// vif_dense.cu: float64 dense m x m linear algebra for Sigma_m and capacitance matrices.
+cudaError_t dense_cholesky(double* A, int m, int lda, int* status, int code, cudaStream_t s);
+cudaError_t dense_trtri_lower(const double* L, double* Linv, int m, int lda, cudaStream_t s);
+cudaError_t reduce_sum(const double* x, int64_t n, double* partial, double* out, cudaStream_t s);
+
+// vif_lowrank.cu
+cudaError_t scale_coords(const double* X, int64_t n, int d, const double* inv_ls, const double* center,
+                         double* Xs, float* Xs32, cudaStream_t s);
+cudaError_t build_sigma_m(const double* Zs, int m, int d, CovParams cp, double* Sm, int lda,
+                          cudaStream_t s);
+template <typename T>
+cudaError_t linv_transpose(const double* Linv, int m, int lda, T* LinvT, int ldt, cudaStream_t s);
+template <typename T>
+cudaError_t lowrank_A(const T* Xs, const T* Zs, const T* LinvT, int ldt, T* A, int64_t n, int d,
+                      int m, int mpad, int kind, double var, cudaStream_t s);
+cudaError_t residual_diag_stats(const double* A, int64_t n, int m, int mpad, double var, double tau,
+                                float* A32, double* cii, float* rs32, float* nrm32, cudaStream_t s);
+
+// vif_factor.cu
+template <typename T>
+cudaError_t vecchia_factor(const T* A, const T* Xs, const int32_t* N, const double* y, int64_t n, int d,
+                           int m, int mpad, int mv, int fpad, CovParams cp, T* F, double* Acoef,
+                           double* Dv, double* logD, int* status, cudaStream_t s);
+template <typename T>
+cudaError_t gram_FtF(const T* F, int64_t n, int fpad, int m, double* part, int nsplit, double* G,
+                     int ldg, cudaStream_t s);
+int gram_nsplit(int64_t n, int fpad);
+cudaError_t nll_finish(const double* Lg, int ldg, int m, const double* logD_sum, int64_t n,
+                       double* out, cudaStream_t s);
+
+// vif_knn.cu
+struct KnnParams {
+  int64_t n;
+  int d, m, mpad, mv, kprime;
+  int kind;
+  double var;
+  double tau_v;     // residual variances <= tau_v count as zero (correlation set to 0)
+  float gamma;      // float32 dot-product error factor
+  float epsK;       // bound on the float32 kernel-evaluation error
+};
+cudaError_t knn_causal(const KnnParams& p, const float* A32, const double* A64, const float* Xs32,
+                       const double* Xs64, const double* cii, const float* rs32, const float* nrm32,
+                       float* cand_key, int32_t* cand_idx, float* cand_e, float* lowbound,
+                       int32_t* N, int* counters, int32_t* fallback_list, cudaStream_t s);
+
+}  // namespace vif

@@ -1,0 +1,185 @@
+"""Thin ctypes binding of libvif (include/vif.h): argument marshalling only.
+
+Arrays may be numpy arrays (host) or torch CUDA tensors (device); the library
+detects which.  Every computation runs in the CUDA library; if libvif.so is
+missing this module raises on import of the library, it never falls back.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libvif.so")
+
+VIF_OK, VIF_ERR_ARG, VIF_ERR_CUDA, VIF_ERR_NOMEM, VIF_ERR_NOT_PD, VIF_ERR_TIMEOUT, \
+    VIF_ERR_NOT_CONVERGED, VIF_ERR_STATE = range(8)
+STATUS_NAMES = ["OK", "ERR_ARG", "ERR_CUDA", "ERR_NOMEM", "ERR_NOT_PD", "ERR_TIMEOUT",
+                "ERR_NOT_CONVERGED", "ERR_STATE"]
+FP64, MIXED = 0, 1
+GAUSSIAN, BERNOULLI_LOGIT = 0, 1
+
+# every symbol include/vif.h declares
+EXPORTS = ["vif_build", "vif_nll", "vif_predict", "vif_set_neighbors", "vif_get_neighbors",
+           "vif_get_factors", "vif_get_knn_stats", "vif_get_stage_times", "vif_last_error", "vif_destroy"]
+
+
+class VifCov(C.Structure):
+    _fields_ = [("kind", C.c_int32), ("variance", C.c_double), ("lengthscale", C.POINTER(C.c_double)),
+                ("n_ls", C.c_int32), ("nugget", C.c_double)]
+
+
+class VifOpts(C.Structure):
+    _fields_ = [("precision", C.c_int32), ("likelihood", C.c_int32), ("no_neighbor_search", C.c_int32),
+                ("stage_timing", C.c_int32), ("reserved", C.c_int32 * 4)]
+
+
+NSTAGES = 5
+STAGES = ["sigma_m_chol_inv", "lowrank_A", "vecchia_factor", "gram_FtF", "capacitance_nll"]
+
+
+class VifError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"{STATUS_NAMES[status] if 0 <= status < 8 else status}: {msg}")
+        self.status = status
+
+
+_lib = None
+
+
+def lib() -> C.CDLL:
+    """Load libvif.so (raises if it has not been built)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError(f"libvif.so not found at {LIB_PATH}: build it first "
+                               "(python -c 'import __graft_entry__ as g; g.build()')")
+        L = C.CDLL(LIB_PATH)
+        vp, i64, i32, dp = C.c_void_p, C.c_int64, C.c_int32, C.POINTER(C.c_double)
+        L.vif_build.argtypes = [vp, i64, i32, vp, i32, i32, C.POINTER(VifCov), C.POINTER(VifOpts), vp,
+                                C.POINTER(vp)]
+        L.vif_nll.argtypes = [vp, C.POINTER(VifCov), vp, dp, dp]
+        L.vif_predict.argtypes = [vp, C.POINTER(VifCov), vp, vp, i64, i32, vp, vp]
+        L.vif_set_neighbors.argtypes = [vp, vp]
+        L.vif_get_neighbors.argtypes = [vp, vp]
+        L.vif_get_factors.argtypes = [vp, vp, vp]
+        L.vif_get_knn_stats.argtypes = [vp, C.POINTER(i64), C.POINTER(i64)]
+        L.vif_get_stage_times.argtypes = [vp, dp]
+        L.vif_last_error.argtypes = [vp]
+        L.vif_last_error.restype = C.c_char_p
+        L.vif_destroy.argtypes = [vp]
+        L.vif_destroy.restype = None
+        for name in EXPORTS:
+            if name not in ("vif_last_error", "vif_destroy"):
+                getattr(L, name).restype = C.c_int
+        _lib = L
+    return _lib
+
+
+def _ptr(a):
+    """Pointer of a numpy array (host) or torch tensor (host or device)."""
+    if a is None:
+        return None
+    if hasattr(a, "data_ptr"):
+        return C.c_void_p(a.data_ptr())
+    return C.c_void_p(a.ctypes.data)
+
+
+def _f64(a):
+    if hasattr(a, "data_ptr"):
+        import torch
+        assert a.dtype == torch.float64 and a.is_contiguous()
+        return a
+    return np.ascontiguousarray(a, dtype=np.float64)
+
+
+def make_cov(theta) -> tuple[VifCov, np.ndarray]:
+    ls = np.ascontiguousarray(np.atleast_1d(np.asarray(theta.lengthscale, dtype=np.float64)))
+    cv = VifCov(int(theta.kind), float(theta.variance), ls.ctypes.data_as(C.POINTER(C.c_double)),
+                int(ls.size), float(theta.nugget))
+    return cv, ls
+
+
+class Context:
+    """One built VIF problem: data, inducing points and neighbour sets (vif_build)."""
+
+    def __init__(self, X, Z, mv: int, theta, precision: int = FP64, likelihood: int = GAUSSIAN,
+                 stream: int = 0, neighbor_search: bool = True, stage_timing: bool = False):
+        L = lib()
+        X = _f64(X)
+        Z = _f64(Z) if Z is not None and Z.shape[0] > 0 else None
+        self.n, self.d = int(X.shape[0]), int(X.shape[1])
+        self.m = 0 if Z is None else int(Z.shape[0])
+        self.mv = int(mv)
+        self.precision = precision
+        cv, ls = make_cov(theta)
+        opts = VifOpts(precision, likelihood, 0 if neighbor_search else 1, 1 if stage_timing else 0,
+                       (C.c_int32 * 4)())
+        h = C.c_void_p()
+        st = L.vif_build(_ptr(X), self.n, self.d, _ptr(Z), self.m, self.mv, C.byref(cv), C.byref(opts),
+                         C.c_void_p(stream), C.byref(h))
+        if st != VIF_OK:
+            raise VifError(st, L.vif_last_error(None).decode())
+        self.h = h
+        self._keep = (X, Z)
+
+    def _check(self, st):
+        if st != VIF_OK:
+            raise VifError(st, lib().vif_last_error(self.h).decode())
+
+    def nll(self, theta, y) -> float:
+        cv, ls = make_cov(theta)
+        out = C.c_double()
+        y = _f64(y)
+        self._check(lib().vif_nll(self.h, C.byref(cv), _ptr(y), C.byref(out), None))
+        return out.value
+
+    def predict(self, theta, y, Xp, latent: bool = False):
+        cv, ls = make_cov(theta)
+        Xp = _f64(Xp)
+        npred = int(Xp.shape[0])
+        mean = np.empty(npred)
+        var = np.empty(npred)
+        self._check(lib().vif_predict(self.h, C.byref(cv), _ptr(_f64(y)), _ptr(Xp), npred, int(latent),
+                                      _ptr(mean), _ptr(var)))
+        return mean, var
+
+    def neighbors(self) -> np.ndarray:
+        N = np.empty((self.n, max(self.mv, 0)), dtype=np.int32)
+        if self.mv:
+            self._check(lib().vif_get_neighbors(self.h, _ptr(N)))
+        return N
+
+    def set_neighbors(self, N) -> None:
+        N = np.ascontiguousarray(N, dtype=np.int32)
+        assert N.shape == (self.n, self.mv)
+        self._check(lib().vif_set_neighbors(self.h, _ptr(N)))
+
+    def factors(self):
+        Ac = np.zeros((self.n, self.mv))
+        D = np.empty(self.n)
+        self._check(lib().vif_get_factors(self.h, _ptr(Ac) if self.mv else None, _ptr(D)))
+        return Ac, D
+
+    def knn_stats(self):
+        a, b = C.c_int64(), C.c_int64()
+        self._check(lib().vif_get_knn_stats(self.h, C.byref(a), C.byref(b)))
+        return a.value, b.value
+
+    def stage_times(self) -> dict:
+        ms = (C.c_double * NSTAGES)()
+        self._check(lib().vif_get_stage_times(self.h, ms))
+        return dict(zip(STAGES, list(ms)))
+
+    def close(self):
+        if getattr(self, "h", None):
+            lib().vif_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

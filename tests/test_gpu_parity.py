@@ -1,0 +1,193 @@
+"""GPU (CUDA path through the C ABI) against the FP64 oracle, element by element.
+
+Tolerances: float64 path 1e-8 relative on the likelihood; mixed path 1e-5
+relative; neighbour sets exact up to near-ties (two candidates whose oracle keys
+differ by less than TIE_TOL may be exchanged).
+"""
+import json
+import os
+
+import numpy as np
+import pytest
+
+from oracle import vif_oracle as O
+from paper_2507_05064_gb300 import synth
+from paper_2507_05064_gb300 import vif as V
+
+pytestmark = pytest.mark.gpu
+
+GOLD = os.path.join(os.path.dirname(__file__), "golden")
+TIE_TOL = 1e-9
+RTOL64 = 1e-8
+RTOL_MIXED = 1e-5
+
+
+def prob(n, d, m, mv, kind, nugget, ls, seed, inducing="kmeans++"):
+    return synth.make_problem(n, d, m, mv, kind, 1.0, ls, nugget, seed, inducing=inducing, lloyd=3)
+
+
+def check_sets(N_gpu, N_or, keys, mv, tol=TIE_TOL):
+    """Exact set equality except at near-ties; returns the number of near-tie swaps."""
+    swaps = 0
+    for i in range(N_or.shape[0]):
+        a = set(int(j) for j in N_gpu[i] if j >= 0)
+        b = set(int(j) for j in N_or[i] if j >= 0)
+        if a == b:
+            continue
+        assert len(a) == len(b) == min(i, mv), (i, a, b)
+        k = keys[i - 1] if isinstance(keys, list) and len(keys) == N_or.shape[0] - 1 else keys[i]
+        ka = np.sort(k[list(a)])
+        kb = np.sort(k[list(b)])
+        assert np.max(np.abs(ka - kb)) <= tol, (i, sorted(a - b), sorted(b - a), ka, kb)
+        swaps += 1
+    return swaps
+
+
+def oracle_keys_by_row(P, N):
+    """Oracle neighbour sets and per-row key vectors (row i: keys against 0..i-1)."""
+    Nor, keys, _ = O.causal_neighbors(P.X, P.Z, P.theta, P.mv, return_keys=True)
+    return Nor, [np.zeros(0)] + keys
+
+
+# --------------------------------------------------------------------------- C1: the stated small workload
+@pytest.fixture(scope="module")
+def c1():
+    P = synth.config1()
+    Nor, keys = oracle_keys_by_row(P, None)
+    vif = O.VIF(P.X, P.Z, P.theta, Nor)
+    return P, Nor, keys, vif
+
+
+def test_c1_neighbor_sets_match_oracle(c1):
+    P, Nor, keys, _ = c1
+    ctx = V.Context(P.X, P.Z, P.mv, P.theta, precision=V.FP64)
+    swaps = check_sets(ctx.neighbors(), Nor, keys, P.mv)
+    assert swaps <= 2
+    ctx.close()
+
+
+@pytest.mark.parametrize("precision,rtol", [(V.FP64, RTOL64), (V.MIXED, RTOL_MIXED)])
+def test_c1_nll_and_factors_with_oracle_neighbors(c1, precision, rtol):
+    P, Nor, keys, vif = c1
+    ctx = V.Context(P.X, P.Z, P.mv, P.theta, precision=precision, neighbor_search=False)
+    ctx.set_neighbors(Nor.astype(np.int32))
+    nll = ctx.nll(P.theta, P.y)
+    ref = vif.nll(P.y)
+    assert nll == pytest.approx(ref, rel=rtol), (nll, ref)
+    Ac, D = ctx.factors()
+    ftol = 1e-9 if precision == V.FP64 else 2e-3
+    np.testing.assert_allclose(D, vif.D, rtol=ftol)
+    np.testing.assert_allclose(Ac, vif.Acoef, rtol=ftol, atol=ftol * np.abs(vif.Acoef).max())
+    ctx.close()
+
+
+def test_c1_end_to_end(c1):
+    P, Nor, keys, vif = c1
+    ctx = V.Context(P.X, P.Z, P.mv, P.theta, precision=V.FP64)
+    assert ctx.nll(P.theta, P.y) == pytest.approx(vif.nll(P.y), rel=RTOL64)
+    # a second call at other hyperparameters (neighbour sets stay fixed)
+    th2 = P.theta.copy()
+    th2.variance, th2.lengthscale, th2.nugget = 1.3, np.array([0.07]), 0.05
+    ref2 = O.VIF(P.X, P.Z, th2, Nor).nll(P.y)
+    assert ctx.nll(th2, P.y) == pytest.approx(ref2, rel=RTOL64)
+    ctx.close()
+
+
+def test_golden_line_neighbors():
+    g = json.load(open(os.path.join(GOLD, "knn_line_m0.json")))
+    X = np.array(g["x"])[:, None]
+    th = synth.Theta(synth.KIND_IDS[g["kind"]], g["variance"], np.array([g["lengthscale"]]), 0.0)
+    ctx = V.Context(X, None, g["mv"], th, precision=V.FP64)
+    N = ctx.neighbors()
+    for i, exp in enumerate(g["neighbors"]):
+        assert [int(j) for j in N[i] if j >= 0] == exp
+    ctx.close()
+
+
+# --------------------------------------------------------------------------- special cases of Sec. 2.1
+def test_full_conditioning_is_exact_gp():
+    P = prob(45, 2, 8, 44, "matern32", 0.1, 0.2, 11)
+    ctx = V.Context(P.X, P.Z, 44, P.theta)
+    ex = O.dense_nll(O.exact_cov(P.X, P.theta), P.y)
+    assert ctx.nll(P.theta, P.y) == pytest.approx(ex, rel=1e-9)
+    ctx.close()
+
+
+def test_zero_neighbors_is_fitc():
+    P = prob(700, 2, 30, 0, "matern52", 0.1, 0.15, 12)
+    N = np.zeros((700, 0), dtype=np.int64)
+    ref = O.vif_nll(P.X, P.Z, P.theta, N, P.y)
+    for prec, tol in [(V.FP64, RTOL64), (V.MIXED, RTOL_MIXED)]:
+        ctx = V.Context(P.X, P.Z, 0, P.theta, precision=prec)
+        assert ctx.nll(P.theta, P.y) == pytest.approx(ref, rel=tol)
+        ctx.close()
+
+
+def test_no_inducing_points_is_classical_vecchia():
+    P = prob(900, 2, 0, 8, "matern12", 0.2, 0.1, 13)
+    Nor, keys = oracle_keys_by_row(P, None)
+    ref = O.vif_nll(P.X, P.Z, P.theta, Nor, P.y)
+    ctx = V.Context(P.X, None, 8, P.theta)
+    check_sets(ctx.neighbors(), Nor, keys, 8)
+    assert ctx.nll(P.theta, P.y) == pytest.approx(ref, rel=RTOL64)
+    ctx.close()
+
+
+# --------------------------------------------------------------------------- ragged sizes, every kernel
+@pytest.mark.parametrize("kind", ["matern12", "matern32", "matern52", "se"])
+def test_ragged_sizes_all_kernels(kind):
+    ls = np.array([0.3, 0.5, 0.8]) if kind == "se" else 0.25
+    P = prob(1037, 3, 45, 7, kind, 0.05, ls, 14)
+    Nor, keys = oracle_keys_by_row(P, None)
+    vif = O.VIF(P.X, P.Z, P.theta, Nor)
+    ref = vif.nll(P.y)
+    ctx = V.Context(P.X, P.Z, 7, P.theta, precision=V.FP64)
+    check_sets(ctx.neighbors(), Nor, keys, 7)
+    assert ctx.nll(P.theta, P.y) == pytest.approx(ref, rel=RTOL64)
+    ctx.close()
+    ctx = V.Context(P.X, P.Z, 7, P.theta, precision=V.MIXED, neighbor_search=False)
+    ctx.set_neighbors(Nor.astype(np.int32))
+    assert ctx.nll(P.theta, P.y) == pytest.approx(ref, rel=RTOL_MIXED)
+    ctx.close()
+
+
+def test_mv30_and_k64_candidate_lists():
+    """m_v = 30 uses 64-entry candidate lists and the 6x6-register factor tiles."""
+    P = prob(3000, 2, 100, 30, "matern52", 0.05, 0.05, 15)
+    Nor, keys = oracle_keys_by_row(P, None)
+    ctx = V.Context(P.X, P.Z, 30, P.theta, precision=V.FP64)
+    check_sets(ctx.neighbors(), Nor, keys, 30)
+    ref = O.VIF(P.X, P.Z, P.theta, Nor).nll(P.y)
+    assert ctx.nll(P.theta, P.y) == pytest.approx(ref, rel=RTOL64)
+    ctx.close()
+
+
+# --------------------------------------------------------------------------- failure paths (host-made)
+def test_nan_input_reports_not_pd():
+    P = prob(300, 2, 20, 5, "matern32", 0.1, 0.2, 16)
+    ctx = V.Context(P.X, P.Z, 5, P.theta, neighbor_search=False)
+    Nor = O.causal_neighbors(P.X, P.Z, P.theta, 5)
+    ctx.set_neighbors(Nor.astype(np.int32))
+    th = P.theta.copy()
+    with pytest.raises(V.VifError) as ei:
+        ctx.nll(th, P.y)  # fine
+        Zbad = P.Z.copy()
+        Zbad[3] = np.nan
+        ctx2 = V.Context(P.X, Zbad, 5, P.theta, neighbor_search=False)
+        ctx2.set_neighbors(Nor.astype(np.int32))
+        ctx2.nll(th, P.y)
+    assert ei.value.status == V.VIF_ERR_NOT_PD
+    # the context stays usable after the error
+    assert np.isfinite(ctx.nll(th, P.y))
+    ctx.close()
+
+
+def test_bad_theta_is_rejected():
+    P = prob(200, 2, 10, 4, "matern32", 0.1, 0.2, 17)
+    ctx = V.Context(P.X, P.Z, 4, P.theta)
+    th = P.theta.copy()
+    th.lengthscale = np.array([0.1, 0.2, 0.3])
+    with pytest.raises(V.VifError) as ei:
+        ctx.nll(th, P.y)
+    assert ei.value.status == V.VIF_ERR_ARG
+    ctx.close()
