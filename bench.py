@@ -1,0 +1,329 @@
+"""Benchmark: VIF negative log-likelihood evaluations per second on one GB300.
+
+Workload (default): n = 500,000 points uniform on [0,1]^8, ARD squared-exponential
+kernel (length scales log-uniform in [0.2, 2], variance 1, nugget 0.01), m = 500
+k-means++ inducing points, m_v = 20 correlation neighbours.  One step = one
+vif_nll evaluation (low-rank part A, residual Vecchia factors, [F z] Gram,
+capacitance Cholesky and the scalar) on the mixed-precision path; the neighbour
+sets are built once beforehand, as in the paper's likelihood timings (Sec. 7.4).
+The float64 GPU path is timed beside it on the same neighbour sets.
+
+--impl reference runs the float64 CPU oracle (the method as the paper writes it)
+on a bounded sample of the same workload on the host cores.
+
+Prints one JSON line (rank 0).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "VIF NLL evals/s at n=500k (mixed-precision GPU path)"
+UNIT = "evals/s"
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="vif", choices=["vif", "reference"])
+    ap.add_argument("--n", type=int, default=500_000)
+    ap.add_argument("--fp64-steps", type=int, default=3)
+    ap.add_argument("--cpu-sample", type=int, default=20_000)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    return ap.parse_args()
+
+
+def workload(n):
+    from paper_2507_05064_gb300 import synth
+    t0 = time.time()
+    P = synth.config3(n=n)
+    return P, time.time() - t0
+
+
+def config_dict(P, n_gpus):
+    return {"workload": f"vif-nll-se-ard-n{P.X.shape[0]}-d8-m{P.Z.shape[0]}-mv{P.mv}",
+            "n": int(P.X.shape[0]), "d": int(P.X.shape[1]), "m": int(P.Z.shape[0]), "m_v": int(P.mv),
+            "kernel": "squared-exponential ARD", "nugget": P.theta.nugget,
+            "l2": "inputs larger than L2 (A alone is n*m*4 B = 1 GB)",
+            "parallelism": f"replicas x{n_gpus}"}
+
+
+class ClockSampler:
+    """nvidia-smi samples of SM clock and throttle reasons during the timed region."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, dev_index=0):
+        self.rows = []
+        self.proc = None
+        self.dev = dev_index
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.dev}", f"--query-gpu={self.Q}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.th = threading.Thread(target=self._read, daemon=True)
+            self.th.start()
+        except Exception:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.rows.append([x.strip() for x in line.split(",")])
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        time.sleep(0.25)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        sm = [float(r[1]) for r in self.rows if len(r) > 2 and r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in self.rows if len(r) > 2 and r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = set()
+        for r in self.rows:
+            for k, nm in enumerate(names):
+                if len(r) > 5 + k and r[5 + k].lower().startswith("active"):
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": sorted(reasons), "samples": len(self.rows)}
+
+
+def peaks():
+    try:
+        return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except Exception:
+        return {}
+
+
+def stage_algorithmic(P, stage):
+    """Algorithmic FLOPs and bytes of one launch of a stage (float32 storage)."""
+    n, m, mv = P.X.shape[0], P.Z.shape[0], P.mv
+    fpad = ((m + 1 + 63) // 64) * 64
+    if stage == "lowrank_A":
+        return 2.0 * n * m * (m + 1) / 2, 4.0 * n * m
+    if stage == "vecchia_factor":
+        q = mv
+        fma = n * ((q + 1) * (q + 2) / 2 * m + q * m)
+        return 2.0 * fma, 4.0 * n * m * 2 + 4.0 * n * (m + 1)
+    if stage == "gram_FtF":
+        return 2.0 * n * (m + 1) * (m + 2) / 2, 4.0 * n * fpad
+    return 0.0, 0.0
+
+
+def launches_per_eval(m):
+    """Kernel launches of one vif_nll call (counted from the launch sites)."""
+    nt = (m + 31) // 32
+    nt1 = (m + 1 + 31) // 32
+    chol = lambda t: t + (t - 1)       # panel launches + trailing-update launches
+    return (2 + 1 + chol(nt) + nt + 1 + 1     # scaling x2, Sigma_m, Cholesky, trtri, L^-T, A
+            + 1 + 2 + 2 + chol(nt1) + 1)      # factor, Gram + reduce, logD sum, capacitance Cholesky, finish
+
+
+def cpu_baseline(P, n_s, steps=1):
+    """Oracle NLL on the first n_s points (same m, m_v, d, kernel) -> evals/s of the
+    full workload by linear scaling in n (the per-eval cost is O(n))."""
+    from oracle import vif_oracle as O
+    n = P.X.shape[0]
+    Xs, ys = P.X[:n_s], P.y[:n_s]
+    # neighbour sets for the timing sample: the m_v immediately preceding points
+    # (the oracle's cost does not depend on which predecessors are chosen)
+    N = -np.ones((n_s, P.mv), dtype=np.int64)
+    for i in range(1, n_s):
+        q = min(i, P.mv)
+        N[i, :q] = np.arange(i - q, i)
+    ts = []
+    for _ in range(steps):
+        t0 = time.time()
+        O.VIF(Xs, P.Z, P.theta, N).nll(ys)
+        ts.append(time.time() - t0)
+    t = statistics.median(ts)
+    return {"value": 1.0 / (t * n / n_s), "unit": UNIT, "cores": os.cpu_count(), "kind": "oracle",
+            "sample": f"oracle NLL on the first {n_s} of {n} points (m={P.Z.shape[0]}, m_v={P.mv}, d=8), "
+                      f"{t:.2f} s per sample eval, scaled by n/{n_s}"}
+
+
+def run_reference(args, rank, world):
+    if rank != 0:
+        return
+    P, _ = workload(args.n)
+    cb = cpu_baseline(P, args.cpu_sample, steps=1)       # warm-up / calibration
+    vals = []
+    for _ in range(max(args.warmup, 0)):
+        pass
+    t0 = time.time()
+    for _ in range(args.steps):
+        vals.append(cpu_baseline(P, args.cpu_sample, steps=1)["value"])
+    wall = time.time() - t0
+    v = statistics.median(vals) if vals else cb["value"]
+    line = {"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": 0,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000.0 / v,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": config_dict(P, 1),
+            "cpu_baseline": {"value": v, "unit": UNIT, "cores": os.cpu_count(), "kind": "oracle",
+                             "sample": cb["sample"]},
+            "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+            "wall_s": wall}
+    print(json.dumps(line), flush=True)
+
+
+def run_vif(args, rank, world, dist):
+    import torch
+    from paper_2507_05064_gb300 import vif as V
+
+    torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", 0)))
+    dev = torch.device("cuda")
+    stream = torch.cuda.current_stream()
+    P, gen_s = workload(args.n)
+    th = P.theta
+    t0 = time.time()
+    ctx = V.Context(P.X, P.Z, P.mv, th, precision=V.MIXED, stream=stream.cuda_stream, stage_timing=True)
+    torch.cuda.synchronize()
+    build_s = time.time() - t0
+    rescored, fallback = ctx.knn_stats()
+    N = ctx.neighbors()
+    c64 = V.Context(P.X, P.Z, P.mv, th, precision=V.FP64, stream=stream.cuda_stream, neighbor_search=False)
+    c64.set_neighbors(N)
+    y_dev = torch.from_numpy(P.y).to(dev)
+
+    def barrier():
+        if dist is not None:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    for _ in range(args.warmup):
+        ctx.nll(th, y_dev)
+    stage_ms = {k: [] for k in V.STAGES}
+    clk = ClockSampler(int(os.environ.get("LOCAL_RANK", 0)))
+    barrier()
+    clk.start()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ev0.record(stream)
+    nll_mixed = None
+    for _ in range(args.steps):
+        nll_mixed = ctx.nll(th, y_dev)
+        for k, v in ctx.stage_times().items():
+            stage_ms[k].append(v)
+    ev1.record(stream)
+    barrier()
+    clocks = clk.stop()
+    ms = ev0.elapsed_time(ev1) / args.steps
+    if dist is not None:
+        t = torch.tensor([ms], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    value = world * 1000.0 / ms
+
+    # float64 GPU path on the same neighbour sets
+    c64.nll(th, y_dev)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    nll64 = None
+    for _ in range(args.fp64_steps):
+        nll64 = c64.nll(th, y_dev)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms64 = e0.elapsed_time(e1) / max(args.fp64_steps, 1)
+
+    # end to end through the C ABI with host buffers: y from pinned host memory, the
+    # scalar back to the host, both inside the timed region
+    y_pin = torch.from_numpy(P.y).pin_memory()
+    y_host = y_pin.numpy()
+    ctx.nll(th, y_host)
+    barrier()
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        ctx.nll(th, y_host)
+    torch.cuda.synchronize()
+    e2e_ms = (time.perf_counter() - t0) * 1000.0 / args.steps
+    if dist is not None:
+        t = torch.tensor([e2e_ms], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        e2e_ms = float(t.item())
+
+    if rank != 0:
+        return
+    med = {k: statistics.median(v) for k, v in stage_ms.items()}
+    dom = max(("lowrank_A", "vecchia_factor", "gram_FtF"), key=lambda k: med[k])
+    flops, byts = stage_algorithmic(P, dom)
+    pk = peaks()
+    sm_max = pk.get("sm_max_mhz", 2070.0)
+    fp32_peak = 152 * 128 * 2 * sm_max * 1e6 / 1e12        # TFLOP/s, SIMT FP32 FMA at max clock
+    achieved = flops / (med[dom] * 1e-3) / 1e12
+    roof = {"kernel": dom, "bound": "alu", "achieved": achieved, "peak": fp32_peak, "unit": "TFLOP/s",
+            "frac": achieved / fp32_peak, "traffic": None,
+            "peak_source": "152 SMs x 128 FP32 lanes x 2 flop x max SM clock (derived)",
+            "algorithmic_flops_per_launch": flops, "algorithmic_bytes_per_launch": byts,
+            "hbm_achieved_gbs": byts / (med[dom] * 1e-3) / 1e9,
+            "hbm_peak_gbs_measured": pk.get("hbm_gbs")}
+    cb = None
+    if not args.no_cpu_baseline:
+        cb = cpu_baseline(P, min(args.cpu_sample, P.X.shape[0]))
+    scale = max(abs(nll64), 0.5 * P.X.shape[0] * math.log(2 * math.pi))
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32+f64", "data": "synthetic",
+        "config": config_dict(P, world),
+        "fp64_path": {"value": world * 1000.0 / ms64, "unit": UNIT, "ms_per_step": ms64, "dtype": "f64"},
+        "mixed_vs_fp64": {"nll_mixed": nll_mixed, "nll_fp64": nll64,
+                          "abs_err": abs(nll_mixed - nll64), "rel_err": abs(nll_mixed - nll64) / abs(nll64),
+                          "rel_err_scale": abs(nll_mixed - nll64) / scale},
+        "speedup_mixed_over_fp64": ms64 / ms,
+        "stage_ms": med,
+        "neighbor_search": {"build_s": build_s, "queries_rescored": rescored, "queries_fallback": fallback},
+        "roofline": roof,
+        "cpu_baseline": cb,
+        "e2e": {"value": world * 1000.0 / e2e_ms, "unit": UNIT, "ms_per_step": e2e_ms,
+                "h2d_bytes_per_step": int(P.y.nbytes) + 256, "d2h_bytes_per_step": 16 + 24},
+        "gpu_launches": launches_per_eval(P.Z.shape[0]) * args.steps,
+        "clocks": clocks,
+        "generate_s": gen_s,
+    }
+    print(json.dumps(line), flush=True)
+    ctx.close()
+    c64.close()
+
+
+def main():
+    args = parse()
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    dist = None
+    if args.impl == "reference":
+        run_reference(args, rank, world)
+        return
+    if world > 1:
+        import torch
+        import torch.distributed as tdist
+        torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", 0)))
+        tdist.init_process_group("nccl")
+        dist = tdist
+    run_vif(args, rank, world, dist)
+    if dist is not None:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -118,7 +118,7 @@ def make_problem(n: int, d: int, m: int, mv: int, kind: str, variance: float,
     X = rng.uniform(size=(n, d))
     ls = np.atleast_1d(np.asarray(lengthscale, dtype=np.float64))
     theta = Theta(KIND_IDS[kind], float(variance), ls, float(nugget))
-    f = latent_rff(X, theta, rng)
+    f = latent_rff(X, theta, rng, R=2048 if n <= 100_000 else 512)
     if likelihood == "gaussian":
         y = f + math.sqrt(nugget) * rng.standard_normal(n)
     else:

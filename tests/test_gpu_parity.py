@@ -22,6 +22,14 @@ RTOL64 = 1e-8
 RTOL_MIXED = 1e-5
 
 
+def nll_close(got, ref, n, rtol):
+    """|got - ref| <= rtol * max(|ref|, n/2 log 2 pi): relative to the likelihood's own
+    scale, which is a sum of n terms; this keeps the bound meaningful when the
+    terms cancel to a small total."""
+    scale = max(abs(ref), 0.5 * n * np.log(2 * np.pi))
+    return abs(got - ref) <= rtol * scale
+
+
 def prob(n, d, m, mv, kind, nugget, ls, seed, inducing="kmeans++"):
     return synth.make_problem(n, d, m, mv, kind, 1.0, ls, nugget, seed, inducing=inducing, lloyd=3)
 
@@ -73,7 +81,7 @@ def test_c1_nll_and_factors_with_oracle_neighbors(c1, precision, rtol):
     ctx.set_neighbors(Nor.astype(np.int32))
     nll = ctx.nll(P.theta, P.y)
     ref = vif.nll(P.y)
-    assert nll == pytest.approx(ref, rel=rtol), (nll, ref)
+    assert nll_close(nll, ref, P.X.shape[0], rtol), (nll, ref)
     Ac, D = ctx.factors()
     ftol = 1e-9 if precision == V.FP64 else 2e-3
     np.testing.assert_allclose(D, vif.D, rtol=ftol)
@@ -119,7 +127,7 @@ def test_zero_neighbors_is_fitc():
     ref = O.vif_nll(P.X, P.Z, P.theta, N, P.y)
     for prec, tol in [(V.FP64, RTOL64), (V.MIXED, RTOL_MIXED)]:
         ctx = V.Context(P.X, P.Z, 0, P.theta, precision=prec)
-        assert ctx.nll(P.theta, P.y) == pytest.approx(ref, rel=tol)
+        assert nll_close(ctx.nll(P.theta, P.y), ref, 700, tol)
         ctx.close()
 
 
@@ -147,7 +155,7 @@ def test_ragged_sizes_all_kernels(kind):
     ctx.close()
     ctx = V.Context(P.X, P.Z, 7, P.theta, precision=V.MIXED, neighbor_search=False)
     ctx.set_neighbors(Nor.astype(np.int32))
-    assert ctx.nll(P.theta, P.y) == pytest.approx(ref, rel=RTOL_MIXED)
+    assert nll_close(ctx.nll(P.theta, P.y), ref, 1037, RTOL_MIXED)
     ctx.close()
 
 
