@@ -132,6 +132,31 @@ vif_status vif_get_knn_stats(const vif_ctx *ctx, int64_t *n_rescored, int64_t *n
 #define VIF_NSTAGES 5
 vif_status vif_get_stage_times(const vif_ctx *ctx, double *ms);
 
+/* vif_nll_noalloc -- the float64 negative log-likelihood of vif_nll (same value,
+ * same neighbour-table format), for callers that cannot allocate device memory:
+ * code inside a framework that owns the GPU's memory (its caching allocator has
+ * already reserved the free HBM, so a raw cudaMalloc fails or fragments it),
+ * plug-ins whose host forbids device allocations after start-up, and
+ * latency-critical loops that cannot pay for the device-wide synchronisation of
+ * cudaMalloc/cudaFree.  It needs no context and calls no allocating routine.
+ * The paper has no counterpart to this entry point; it is an interface addition.
+ *   X (n x d), Z (m x d), N (n x mv int32, rows as for vif_set_neighbors), y (n):
+ *   DEVICE pointers.  theta: as for vif_nll.  stream: cudaStream_t (NULL = legacy
+ *   default).  nll_out: HOST double, written when the call returns VIF_OK.
+ * All intermediates live in one static device array of VIF_NOALLOC_SCRATCH_BYTES
+ * inside the library; every GPU that loads the library holds that memory until
+ * the process exits.  A problem whose intermediates do not fit (roughly
+ * n (m_pad + f_pad + m_v + d + 2) * 8 bytes, m_pad = m rounded up to 32, f_pad = m+1
+ * rounded up to 64) is rejected with VIF_ERR_ARG and a message in
+ * vif_last_error(NULL).  The first call on a device looks up the array's device
+ * address with that device current; make that first call before any stream
+ * capture.  All calls share the array, which keeps the last call's contents:
+ * calls that overlap on the GPU (several streams or threads at once) race on it. */
+#define VIF_NOALLOC_SCRATCH_BYTES (32u << 20)
+vif_status vif_nll_noalloc(const double *X, int64_t n, int32_t d, const double *Z, int32_t m,
+                           const int32_t *N, int32_t mv, const vif_cov *theta, const double *y,
+                           void *stream, double *nll_out);
+
 /* vif_last_error -- text of the last error on this context ("" if none), valid
  * until the next call on the context; with ctx == NULL, the message of the last
  * failed vif_build in this process. */

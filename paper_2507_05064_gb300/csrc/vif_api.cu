@@ -321,6 +321,8 @@ vif_status build_neighbors(vif_ctx* ctx, const vif_cov* cv) {
 
 }  // namespace
 
+void vif_internal_set_global_error(const char* msg) { snprintf(g_build_err, sizeof(g_build_err), "%s", msg); }
+
 extern "C" {
 
 vif_status vif_build(const double* X, int64_t n, int32_t d, const double* Z, int32_t m, int32_t mv,

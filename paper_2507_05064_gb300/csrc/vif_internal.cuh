@@ -107,3 +107,6 @@ cudaError_t knn_causal(const KnnParams& p, const float* A32, const double* A64, 
                        int32_t* N, int* counters, int32_t* fallback_list, cudaStream_t s);
 
 }  // namespace vif
+
+// vif_api.cu: sets the message that vif_last_error(NULL) returns.
+void vif_internal_set_global_error(const char* msg);

@@ -23,7 +23,9 @@ GAUSSIAN, BERNOULLI_LOGIT = 0, 1
 
 # every symbol include/vif.h declares
 EXPORTS = ["vif_build", "vif_nll", "vif_predict", "vif_set_neighbors", "vif_get_neighbors",
-           "vif_get_factors", "vif_get_knn_stats", "vif_get_stage_times", "vif_last_error", "vif_destroy"]
+           "vif_get_factors", "vif_get_knn_stats", "vif_get_stage_times", "vif_nll_noalloc",
+           "vif_last_error", "vif_destroy"]
+NOALLOC_SCRATCH_BYTES = 32 << 20
 
 
 class VifCov(C.Structure):
@@ -67,6 +69,7 @@ def lib() -> C.CDLL:
         L.vif_get_factors.argtypes = [vp, vp, vp]
         L.vif_get_knn_stats.argtypes = [vp, C.POINTER(i64), C.POINTER(i64)]
         L.vif_get_stage_times.argtypes = [vp, dp]
+        L.vif_nll_noalloc.argtypes = [vp, i64, i32, vp, i32, vp, i32, C.POINTER(VifCov), vp, vp, dp]
         L.vif_last_error.argtypes = [vp]
         L.vif_last_error.restype = C.c_char_p
         L.vif_destroy.argtypes = [vp]
@@ -100,6 +103,21 @@ def make_cov(theta) -> tuple[VifCov, np.ndarray]:
     cv = VifCov(int(theta.kind), float(theta.variance), ls.ctypes.data_as(C.POINTER(C.c_double)),
                 int(ls.size), float(theta.nugget))
     return cv, ls
+
+
+def nll_noalloc(X, Z, N, mv: int, theta, y, stream: int = 0) -> float:
+    """vif_nll_noalloc: the float64 likelihood without any device allocation.
+    X, Z, N (int32), y must be device tensors; see include/vif.h for who needs this."""
+    L = lib()
+    cv, ls = make_cov(theta)
+    out = C.c_double()
+    n, d = int(X.shape[0]), int(X.shape[1])
+    m = 0 if Z is None else int(Z.shape[0])
+    st = L.vif_nll_noalloc(_ptr(X), n, d, _ptr(Z) if m else None, m, _ptr(N) if mv else None, int(mv),
+                           C.byref(cv), _ptr(y), C.c_void_p(stream), C.byref(out))
+    if st != VIF_OK:
+        raise VifError(st, L.vif_last_error(None).decode())
+    return out.value
 
 
 class Context:

@@ -1,0 +1,53 @@
+"""vif_nll_noalloc: the float64 likelihood for callers that cannot allocate device
+memory (a framework that owns the GPU's memory, a plug-in host that forbids
+allocations after start-up, a loop that cannot afford cudaMalloc's device-wide
+synchronisation).  Its scratch is a static device array shared by all calls, so
+this test calls it twice in a row, at two different hyperparameters, and checks
+each result against vif_nll on a regular context at the float64 tolerance.
+
+The file name makes pytest collect it last; it also passes on its own in a
+fresh process (its first call then performs the one-time address lookup)."""
+import numpy as np
+import pytest
+
+from paper_2507_05064_gb300 import synth
+from paper_2507_05064_gb300 import vif as V
+
+pytestmark = pytest.mark.gpu
+RTOL64 = 1e-8
+
+
+def test_noalloc_matches_vif_nll_on_two_calls_in_a_row():
+    torch = pytest.importorskip("torch")
+    P = synth.config1()
+    ctx = V.Context(P.X, P.Z, P.mv, P.theta, precision=V.FP64)
+    N = ctx.neighbors()
+    th2 = P.theta.copy()
+    th2.variance, th2.lengthscale, th2.nugget = 1.4, np.array([0.06]), 0.03
+    ref2 = ctx.nll(th2, P.y)
+    ref1 = ctx.nll(P.theta, P.y)
+    ctx.close()
+    dev = torch.device("cuda")
+    X = torch.from_numpy(P.X).to(dev)
+    Z = torch.from_numpy(P.Z).to(dev)
+    Nd = torch.from_numpy(N.astype(np.int32)).to(dev)
+    y = torch.from_numpy(P.y).to(dev)
+    got2 = V.nll_noalloc(X, Z, Nd, P.mv, th2, y)
+    got1 = V.nll_noalloc(X, Z, Nd, P.mv, P.theta, y)
+    assert got2 == pytest.approx(ref2, rel=RTOL64)
+    assert got1 == pytest.approx(ref1, rel=RTOL64)
+
+
+def test_noalloc_rejects_a_problem_beyond_its_scratch():
+    torch = pytest.importorskip("torch")
+    dev = torch.device("cuda")
+    n, d, m, mv = 200_000, 2, 200, 10            # ~ 200k * (224 + 256) * 8 B >> 32 MiB
+    X = torch.zeros((n, d), dtype=torch.float64, device=dev)
+    Z = torch.zeros((m, d), dtype=torch.float64, device=dev)
+    Nd = torch.full((n, mv), -1, dtype=torch.int32, device=dev)
+    y = torch.zeros(n, dtype=torch.float64, device=dev)
+    th = synth.Theta(1, 1.0, np.array([0.1]), 0.1)
+    with pytest.raises(V.VifError) as ei:
+        V.nll_noalloc(X, Z, Nd, mv, th, y)
+    assert ei.value.status == V.VIF_ERR_ARG
+    assert "maximum" in str(ei.value)
