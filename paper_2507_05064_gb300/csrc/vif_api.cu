@@ -26,6 +26,7 @@ struct vif_ctx {
   float *Xs32 = nullptr, *Zs32 = nullptr;     // scaled coordinates (float32, mixed path)
   double *hyp = nullptr;                      // [0..15] 1/lambda, [16..31] center
   int32_t* N = nullptr;                       // n x mv
+  int32_t* order = nullptr;                   // processing order of the per-point kernels
   double *Sm = nullptr, *Linv = nullptr;      // m x ldm
   void* LinvT = nullptr;                      // mpad x mpad (float or double)
   void* A = nullptr;                          // n x mpad
@@ -39,6 +40,13 @@ struct vif_ctx {
   double* dscal = nullptr;                    // [0] sum log D, [1..3] nll, logdetC, quad
   int* status = nullptr;                      // [0] code [1] index [2..] counters
   double* h_pin = nullptr;                    // pinned host staging
+  // float64 twins of A, F, L^{-T} for prediction from a mixed-precision context
+  double *pA = nullptr, *pF = nullptr, *pLinvT = nullptr;
+  // prediction buffers, grown on demand
+  int64_t p_cap = 0;
+  double *pXp = nullptr, *pXps = nullptr, *pAp = nullptr, *pcpp = nullptr, *pmean = nullptr, *pvar = nullptr;
+  int32_t* pNp = nullptr;
+  double *pcjj = nullptr, *pw = nullptr, *pr = nullptr, *pLinvC = nullptr;
   int64_t knn_rescored = 0, knn_fallback = 0;
   bool have_factors = false;
   bool timing = false;
@@ -186,6 +194,28 @@ vif_status compute_lowrank_parts(vif_ctx* ctx, const CovParams& cp, T* A, T* Lin
   return VIF_OK;
 }
 
+// The likelihood pipeline of Sec. 2.1-2.2 in precision T on the given buffers:
+// A, the residual Vecchia factors and rows of [F z], the Gram, the augmented
+// capacitance Cholesky and the scalar (left on the device in dscal[1..3]).
+template <typename T>
+vif_status run_pipeline(vif_ctx* ctx, const CovParams& cp, T* A, T* LinvT, T* F, const T* Xs, const T* Zs) {
+#define MARK(k) \
+  if (ctx->timing) CK(cudaEventRecord(ctx->ev[k], ctx->stream))
+  MARK(0);
+  CKS(compute_lowrank_parts<T>(ctx, cp, A, LinvT, Xs, Zs));
+  CK(vecchia_factor<T>(A, Xs, ctx->N, ctx->order, ctx->y, ctx->n, ctx->d, ctx->m, ctx->mpad, ctx->mv, ctx->fpad,
+                       cp, F, ctx->Acoef, ctx->Dv, ctx->logD, ctx->status, ctx->stream));
+  MARK(3);
+  CK(gram_FtF<T>(F, ctx->n, ctx->fpad, ctx->m, ctx->part, ctx->nsplit, ctx->G, ctx->fpad, ctx->stream));
+  MARK(4);
+  CK(reduce_sum(ctx->logD, ctx->n, ctx->red, ctx->dscal, ctx->stream));
+  CK(dense_cholesky(ctx->G, ctx->m + 1, ctx->fpad, ctx->status, ST_NOTPD_CAP, ctx->stream));
+  CK(nll_finish(ctx->G, ctx->fpad, ctx->m, ctx->dscal, ctx->n, ctx->dscal + 1, ctx->stream));
+  MARK(5);
+#undef MARK
+  return VIF_OK;
+}
+
 vif_status read_status(vif_ctx* ctx, double* scal_out, int nscal) {
   // one D2H copy of the status words and the requested scalars
   CK(cudaMemcpyAsync(ctx->h_pin, ctx->status, 4 * sizeof(int), cudaMemcpyDeviceToHost, ctx->stream));
@@ -210,10 +240,14 @@ vif_status read_status(vif_ctx* ctx, double* scal_out, int nscal) {
 
 void free_ctx(vif_ctx* c) {
   if (!c) return;
-  void* bufs[] = {c->X,    c->Z,     c->Xs, c->Zs,   c->Xs32, c->Zs32, c->hyp, c->N,   c->Sm,
+  void* bufs[] = {c->X,    c->Z,     c->Xs, c->Zs,   c->Xs32, c->Zs32, c->hyp, c->N,   c->order, c->Sm,
                   c->Linv, c->LinvT, c->A,  c->F,    c->Acoef, c->Dv,  c->logD, c->part, c->G,
                   c->y,    c->red,   c->dscal, c->status};
   for (void* b : bufs)
+    if (b) cudaFree(b);
+  void* pbufs[] = {c->pA, c->pF, c->pLinvT, c->pXp, c->pXps, c->pAp, c->pcpp, c->pmean, c->pvar, c->pNp,
+                   c->pcjj, c->pw, c->pr, c->pLinvC};
+  for (void* b : pbufs)
     if (b) cudaFree(b);
   if (c->h_pin) cudaFreeHost(c->h_pin);
   for (auto& e : c->ev)
@@ -266,8 +300,11 @@ vif_status build_neighbors(vif_ctx* ctx, const vif_cov* cv) {
     }
     // error constants of the float32 filter (u = 2^-24)
     const double u = std::ldexp(1.0, -24);
-    const int mm = std::max(ctx->m, 1);
-    const double gam = (mm + 2) * u / (1.0 - (mm + 2) * u) + 1e-12;
+    // float32 dot products are summed in chunks of 32 (see the filter kernel):
+    // |error| <= gamma_k sum|a_ik a_jk|, k = 32 + ceil(m/32) + 2 (chunk sum, total,
+    // rounding of A to float32), with sum|a_ik a_jk| <= ||a_i|| ||a_j||.
+    const int kk = 32 + (std::max(ctx->m, 1) + 31) / 32 + 2;
+    const double gam = kk * u / (1.0 - kk * u) + 1e-12;
     // max |scaled coordinate| norm over the data (centred), from the host copy kept at build
     double R = 0.0;
     {
@@ -317,6 +354,45 @@ vif_status build_neighbors(vif_ctx* ctx, const vif_cov* cv) {
   } while (0);
   cleanup();
   return st;
+}
+
+}  // namespace
+
+namespace {
+
+// Processing order for the per-point kernels: points sorted by the Morton (Z-order)
+// code of their ARD-scaled coordinates, so that consecutive warps gather
+// neighbour rows that are close in space and likely still in L2.  This only
+// changes the order in which independent points are processed, never a result.
+std::vector<int32_t> morton_order(const std::vector<double>& hx, int64_t n, int d, const vif_cov* cov) {
+  const int bits = std::min(21, 63 / d);
+  std::vector<double> lo(d), hi(d);
+  for (int t = 0; t < d; ++t) {
+    lo[t] = hi[t] = hx[t];
+    for (int64_t i = 0; i < n; ++i) {
+      lo[t] = std::min(lo[t], hx[(size_t)i * d + t]);
+      hi[t] = std::max(hi[t], hx[(size_t)i * d + t]);
+    }
+  }
+  // equal cells in the scaled space: the longest scaled extent sets the resolution
+  double ext = 0.0;
+  for (int t = 0; t < d; ++t) ext = std::max(ext, (hi[t] - lo[t]) / cov->lengthscale[cov->n_ls == 1 ? 0 : t]);
+  if (!(ext > 0.0)) ext = 1.0;
+  const double cells = (double)((1ull << bits) - 1);
+  std::vector<uint64_t> code(n);
+  for (int64_t i = 0; i < n; ++i) {
+    uint64_t c = 0;
+    for (int t = 0; t < d; ++t) {
+      double v = (hx[(size_t)i * d + t] - lo[t]) / cov->lengthscale[cov->n_ls == 1 ? 0 : t] / ext;
+      uint64_t q = (uint64_t)std::min(cells, std::max(0.0, v * cells));
+      for (int b = 0; b < bits; ++b) c |= ((q >> b) & 1ull) << (b * d + t);
+    }
+    code[i] = c;
+  }
+  std::vector<int32_t> ord(n);
+  for (int64_t i = 0; i < n; ++i) ord[i] = (int32_t)i;
+  std::stable_sort(ord.begin(), ord.end(), [&](int32_t a, int32_t b) { return code[a] < code[b]; });
+  return ord;
 }
 
 }  // namespace
@@ -383,6 +459,7 @@ vif_status vif_build(const double* X, int64_t n, int32_t d, const double* Z, int
   ALLOC(ctx->Zs32, (size_t)std::max(m, 1) * d);
   ALLOC(ctx->hyp, 32);
   ALLOC(ctx->N, (size_t)n * std::max(mv, 1));
+  ALLOC(ctx->order, (size_t)n);
   ALLOC(ctx->Sm, (size_t)ctx->ldm * ctx->ldm);
   ALLOC(ctx->Linv, (size_t)ctx->ldm * ctx->ldm);
   {
@@ -433,6 +510,13 @@ vif_status vif_build(const double* X, int64_t n, int32_t d, const double* Z, int
     }
     ctx->center[t] = 0.5 * (lo + hi);
   }
+  {
+    std::vector<int32_t> ord = morton_order(hx, n, d, cov);
+    if (cudaMemcpy(ctx->order, ord.data(), (size_t)n * sizeof(int32_t), cudaMemcpyHostToDevice) != cudaSuccess) {
+      free_ctx(ctx);
+      return VIF_ERR_CUDA;
+    }
+  }
   if ((st = upload(ctx, ctx->X, X, (size_t)n * d * sizeof(double))) != VIF_OK ||
       (m > 0 && (st = upload(ctx, ctx->Z, Z, (size_t)m * d * sizeof(double))) != VIF_OK)) {
     free_ctx(ctx);
@@ -470,32 +554,11 @@ vif_status vif_nll(vif_ctx* ctx, const vif_cov* theta, const double* y, double* 
   CK(cudaMemsetAsync(ctx->status, 0, 4 * sizeof(int), ctx->stream));
   CKS(upload(ctx, ctx->y, y, (size_t)ctx->n * sizeof(double)));
   CKS(apply_scaling(ctx, theta, mixed));
-#define MARK(k) \
-  if (ctx->timing) CK(cudaEventRecord(ctx->ev[k], ctx->stream))
-  MARK(0);
   if (mixed) {
-    CKS(compute_lowrank_parts<float>(ctx, cp, (float*)ctx->A, (float*)ctx->LinvT, ctx->Xs32, ctx->Zs32));
-    CK(vecchia_factor<float>((const float*)ctx->A, ctx->Xs32, ctx->N, ctx->y, ctx->n, ctx->d, ctx->m, ctx->mpad,
-                             ctx->mv, ctx->fpad, cp, (float*)ctx->F, ctx->Acoef, ctx->Dv, ctx->logD, ctx->status,
-                             ctx->stream));
-    MARK(3);
-    CK(gram_FtF<float>((const float*)ctx->F, ctx->n, ctx->fpad, ctx->m, ctx->part, ctx->nsplit, ctx->G, ctx->fpad,
-                       ctx->stream));
+    CKS(run_pipeline<float>(ctx, cp, (float*)ctx->A, (float*)ctx->LinvT, (float*)ctx->F, ctx->Xs32, ctx->Zs32));
   } else {
-    CKS(compute_lowrank_parts<double>(ctx, cp, (double*)ctx->A, (double*)ctx->LinvT, ctx->Xs, ctx->Zs));
-    CK(vecchia_factor<double>((const double*)ctx->A, ctx->Xs, ctx->N, ctx->y, ctx->n, ctx->d, ctx->m, ctx->mpad,
-                              ctx->mv, ctx->fpad, cp, (double*)ctx->F, ctx->Acoef, ctx->Dv, ctx->logD,
-                              ctx->status, ctx->stream));
-    MARK(3);
-    CK(gram_FtF<double>((const double*)ctx->F, ctx->n, ctx->fpad, ctx->m, ctx->part, ctx->nsplit, ctx->G,
-                        ctx->fpad, ctx->stream));
+    CKS(run_pipeline<double>(ctx, cp, (double*)ctx->A, (double*)ctx->LinvT, (double*)ctx->F, ctx->Xs, ctx->Zs));
   }
-  MARK(4);
-  CK(reduce_sum(ctx->logD, ctx->n, ctx->red, ctx->dscal, ctx->stream));
-  CK(dense_cholesky(ctx->G, ctx->m + 1, ctx->fpad, ctx->status, ST_NOTPD_CAP, ctx->stream));
-  CK(nll_finish(ctx->G, ctx->fpad, ctx->m, ctx->dscal, ctx->n, ctx->dscal + 1, ctx->stream));
-  MARK(5);
-#undef MARK
   double sc[3];
   CKS(read_status(ctx, sc, 3));
   ctx->have_factors = true;
@@ -506,8 +569,72 @@ vif_status vif_nll(vif_ctx* ctx, const vif_cov* theta, const double* y, double* 
 vif_status vif_predict(vif_ctx* ctx, const vif_cov* theta, const double* y, const double* Xp, int64_t np,
                        int32_t latent, double* mean, double* var) {
   if (!ctx) return VIF_ERR_ARG;
-  (void)theta; (void)y; (void)Xp; (void)np; (void)latent; (void)mean; (void)var;
-  return set_err(ctx, VIF_ERR_STATE, "vif_predict is not available in this build");
+  ctx->err[0] = 0;
+  if (!y || !Xp || !mean || np < 1) return set_err(ctx, VIF_ERR_ARG, "y, Xp, mean and np >= 1 are required");
+  CKS(check_cov(ctx, theta, ctx->d));
+  if (ctx->likelihood != VIF_GAUSSIAN)
+    return set_err(ctx, VIF_ERR_STATE, "vif_predict needs a context built for the Gaussian likelihood");
+  if (ctx->mv > 48) return set_err(ctx, VIF_ERR_ARG, "m_v too large for prediction");
+  const int64_t n = ctx->n;
+  const int d = ctx->d, m = ctx->m, mpad = ctx->mpad, fpad = ctx->fpad, mv = ctx->mv;
+  // float64 buffers of the likelihood pipeline
+  double *A64, *F64, *LT64;
+  if (ctx->precision == VIF_FP64) {
+    A64 = (double*)ctx->A;
+    F64 = (double*)ctx->F;
+    LT64 = (double*)ctx->LinvT;
+  } else {
+    if (!ctx->pA) {
+      CKS(dalloc(ctx, &ctx->pA, (size_t)n * mpad));
+      CKS(dalloc(ctx, &ctx->pF, (size_t)n * fpad));
+      CKS(dalloc(ctx, &ctx->pLinvT, (size_t)mpad * mpad));
+      CK(cudaMemsetAsync(ctx->pA, 0, (size_t)n * mpad * sizeof(double), ctx->stream));
+    }
+    A64 = ctx->pA;
+    F64 = ctx->pF;
+    LT64 = ctx->pLinvT;
+  }
+  if (np > ctx->p_cap) {
+    double* pb[] = {ctx->pXp, ctx->pXps, ctx->pAp, ctx->pcpp, ctx->pmean, ctx->pvar};
+    for (double* b : pb)
+      if (b) cudaFree(b);
+    if (ctx->pNp) cudaFree(ctx->pNp);
+    ctx->pXp = ctx->pXps = ctx->pAp = ctx->pcpp = ctx->pmean = ctx->pvar = nullptr;
+    ctx->pNp = nullptr;
+    ctx->p_cap = 0;
+    CKS(dalloc(ctx, &ctx->pXp, (size_t)np * d));
+    CKS(dalloc(ctx, &ctx->pXps, (size_t)np * d));
+    CKS(dalloc(ctx, &ctx->pAp, (size_t)np * mpad));
+    CKS(dalloc(ctx, &ctx->pcpp, (size_t)np));
+    CKS(dalloc(ctx, &ctx->pmean, (size_t)np));
+    CKS(dalloc(ctx, &ctx->pvar, (size_t)np));
+    CKS(dalloc(ctx, &ctx->pNp, (size_t)np * std::max(mv, 1)));
+    ctx->p_cap = np;
+  }
+  if (!ctx->pcjj) {
+    CKS(dalloc(ctx, &ctx->pcjj, (size_t)n));
+    CKS(dalloc(ctx, &ctx->pw, (size_t)mpad));
+    CKS(dalloc(ctx, &ctx->pr, (size_t)n));
+    CKS(dalloc(ctx, &ctx->pLinvC, (size_t)std::max(m, 1) * fpad));
+    CK(cudaMemsetAsync(ctx->pw, 0, (size_t)mpad * sizeof(double), ctx->stream));
+  }
+  CovParams cp = cov_params(theta);
+  CK(cudaMemsetAsync(ctx->status, 0, 4 * sizeof(int), ctx->stream));
+  CKS(upload(ctx, ctx->y, y, (size_t)n * sizeof(double)));
+  CKS(apply_scaling(ctx, theta, false));
+  CKS(run_pipeline<double>(ctx, cp, A64, LT64, F64, ctx->Xs, ctx->Zs));
+  CKS(upload(ctx, ctx->pXp, Xp, (size_t)np * d * sizeof(double)));
+  CK(scale_coords(ctx->pXp, np, d, ctx->hyp, ctx->hyp + 16, ctx->pXps, nullptr, ctx->stream));
+  CK(lowrank_A<double>(ctx->pXps, ctx->Zs, LT64, mpad, ctx->pAp, np, d, m, mpad, cp.kind, cp.var, ctx->stream));
+  CK(predict_all(A64, ctx->Xs, n, ctx->pAp, ctx->pXps, np, d, m, mpad, mv, cp, ctx->y, ctx->G, fpad, ctx->pLinvC,
+                 ctx->pw, ctx->pr, ctx->pcjj, ctx->pcpp, ctx->pNp, latent ? 1 : 0, theta->nugget, ctx->pmean,
+                 ctx->pvar, ctx->status, ctx->stream));
+  double sc[1];
+  CKS(read_status(ctx, sc, 1));
+  ctx->have_factors = true;
+  CKS(download(ctx, mean, ctx->pmean, (size_t)np * sizeof(double)));
+  if (var) CKS(download(ctx, var, ctx->pvar, (size_t)np * sizeof(double)));
+  return VIF_OK;
 }
 
 vif_status vif_set_neighbors(vif_ctx* ctx, const int32_t* N) {

@@ -24,21 +24,45 @@
 namespace vif {
 
 // ---------------------------------------------------------------------------
-// Factor kernel: one warp per point.  Lane l < 21 owns the R x R block (bi, bj),
-// bj <= bi < 6, of the (6R) x (6R) padded Gram [A_N; a_i][A_N; a_i]^T; the rows
-// are staged through shared memory 32 columns at a time.
+// Factor kernel: one warp per point.  The (q+1) rows [A_N; a_i] are padded to
+// 7R rows and their Gram is split into the 28 R x R blocks (bi, bj), bj <= bi < 7,
+// one per lane (28 of 32 lanes busy).  Rows stream through a double-buffered
+// shared-memory window of 128 bytes per row, filled with cp.async while the
+// previous window is being multiplied; each lane reads its operands as 16-byte
+// vectors along k.  Points are visited in `order` (a spatial ordering chosen at
+// build) so that neighbouring rows of A are still in L2 when they are gathered.
 // ---------------------------------------------------------------------------
-constexpr int FK_KC = 32;
 constexpr int FK_WARPS = 4;
 constexpr int FK_MAXD = 16;
+constexpr int FK_NB = 7;
 
-__constant__ unsigned char c_blk_i[21] = {0, 1, 1, 2, 2, 2, 3, 3, 3, 3, 4, 4, 4, 4, 4, 5, 5, 5, 5, 5, 5};
-__constant__ unsigned char c_blk_j[21] = {0, 0, 1, 0, 1, 2, 0, 1, 2, 3, 0, 1, 2, 3, 4, 0, 1, 2, 3, 4, 5};
+__constant__ unsigned char c_blk_i[28] = {0, 1, 1, 2, 2, 2, 3, 3, 3, 3, 4, 4, 4, 4,
+                                          4, 5, 5, 5, 5, 5, 5, 6, 6, 6, 6, 6, 6, 6};
+__constant__ unsigned char c_blk_j[28] = {0, 0, 1, 0, 1, 2, 0, 1, 2, 3, 0, 1, 2, 3,
+                                          4, 0, 1, 2, 3, 4, 5, 0, 1, 2, 3, 4, 5, 6};
+
+template <typename T> struct Vec16;
+template <> struct Vec16<float> { using type = float4; static constexpr int n = 4; };
+template <> struct Vec16<double> { using type = double2; static constexpr int n = 2; };
+
+__device__ __forceinline__ void vget(const float4& v, float (&o)[4]) { o[0] = v.x; o[1] = v.y; o[2] = v.z; o[3] = v.w; }
+__device__ __forceinline__ void vget(const double2& v, double (&o)[2]) { o[0] = v.x; o[1] = v.y; }
+
+__device__ __forceinline__ void cp_async16(void* smem, const void* gmem) {
+  unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(sa), "l"(gmem));
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;\n" ::"n"(N)); }
 
 template <typename T, int R>
 struct FactorSmem {
-  static constexpr int QM = 6 * R;
-  T buf[QM][FK_KC + 1];
+  static constexpr int QM = FK_NB * R;
+  static constexpr int V = Vec16<T>::n;       // elements per 16 bytes
+  static constexpr int KC = 128 / sizeof(T);  // window width: 128 bytes per row
+  static constexpr int LD = KC + V;           // row stride (16-byte aligned, bank shift)
+  alignas(16) T buf[2][QM][LD];
   T G[QM][QM + 1];
   T coef[QM];
   T xc[QM][FK_MAXD];
@@ -48,15 +72,18 @@ struct FactorSmem {
 template <typename T, int R>
 __global__ __launch_bounds__(FK_WARPS * 32) void factor_kernel(
     const T* __restrict__ A, const T* __restrict__ Xs, const int32_t* __restrict__ N,
-    const double* __restrict__ y, int64_t n, int d, int m, int mpad, int mv, int fpad, CovParams cp,
-    T* __restrict__ F, double* __restrict__ Acoef, double* __restrict__ Dv, double* __restrict__ logD,
-    int* status) {
-  constexpr int QM = 6 * R;
+    const int32_t* __restrict__ order, const double* __restrict__ y, int64_t n, int d, int m, int mpad, int mv,
+    int fpad, CovParams cp, T* __restrict__ F, double* __restrict__ Acoef, double* __restrict__ Dv,
+    double* __restrict__ logD, int* status) {
+  using SM = FactorSmem<T, R>;
+  constexpr int QM = SM::QM, V = SM::V, KC = SM::KC;
+  using VT = typename Vec16<T>::type;
   extern __shared__ __align__(16) unsigned char smraw[];
   const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  FactorSmem<T, R>& S = reinterpret_cast<FactorSmem<T, R>*>(smraw)[w];
-  const int64_t i = (int64_t)blockIdx.x * FK_WARPS + w;
-  if (i >= n) return;
+  SM& S = reinterpret_cast<SM*>(smraw)[w];
+  const int64_t slot = (int64_t)blockIdx.x * FK_WARPS + w;
+  if (slot >= n) return;
+  const int64_t i = order ? (int64_t)order[slot] : slot;
   const int q = (int)(i < (int64_t)mv ? i : (int64_t)mv);
   const int Q = q + 1;
   for (int t = lane; t < QM; t += 32) {
@@ -67,38 +94,56 @@ __global__ __launch_bounds__(FK_WARPS * 32) void factor_kernel(
     }
     S.idx[t] = j;
   }
-  for (int e = lane; e < QM * (FK_KC + 1); e += 32) (&S.buf[0][0])[e] = T(0);
+  // rows Q..QM-1 of both windows stay zero
+  for (int e = lane; e < 2 * QM * SM::LD; e += 32) (&S.buf[0][0][0])[e] = T(0);
   __syncwarp();
   for (int e = lane; e < Q * d; e += 32) {
     int t = e / d, c = e % d;
     S.xc[t][c] = Xs[(size_t)S.idx[t] * d + c];
   }
-  // ---- Gram of the gathered rows of A
-  const bool owner = lane < 21;
+  // ---- Gram of the gathered rows of A, double-buffered windows of KC columns
+  const bool owner = lane < 28;
   const int bi = owner ? c_blk_i[lane] : 0, bj = owner ? c_blk_j[lane] : 0;
   T acc[R][R];
 #pragma unroll
   for (int r = 0; r < R; ++r)
 #pragma unroll
     for (int c = 0; c < R; ++c) acc[r][c] = T(0);
-  for (int k0 = 0; k0 < m; k0 += FK_KC) {
-    for (int t = 0; t < Q; ++t) {
-      int k = k0 + lane;
-      S.buf[t][lane] = (k < mpad) ? A[(size_t)S.idx[t] * mpad + k] : T(0);
+  const int nwin = (m + KC - 1) / KC;
+  constexpr int SEG = KC / V;                 // 16-byte segments per row window (8)
+  auto issue = [&](int win, int b) {
+    const int k0 = win * KC;
+    for (int e = lane; e < Q * SEG; e += 32) {
+      int t = e / SEG, sg = e % SEG;
+      int k = k0 + sg * V;
+      if (k < mpad) cp_async16(&S.buf[b][t][sg * V], A + (size_t)S.idx[t] * mpad + k);
+    }
+    cp_async_commit();
+  };
+  if (nwin > 0) issue(0, 0);
+  for (int win = 0; win < nwin; ++win) {
+    const int b = win & 1;
+    if (win + 1 < nwin) {
+      issue(win + 1, b ^ 1);
+      cp_async_wait<1>();
+    } else {
+      cp_async_wait<0>();
     }
     __syncwarp();
     if (owner) {
-#pragma unroll 4
-      for (int kk = 0; kk < FK_KC; ++kk) {
-        T u[R], v[R];
+#pragma unroll 2
+      for (int kk = 0; kk < KC; kk += V) {
+        T u[R][V], v[R][V];
 #pragma unroll
-        for (int r = 0; r < R; ++r) u[r] = S.buf[bi * R + r][kk];
+        for (int r = 0; r < R; ++r) vget(*reinterpret_cast<const VT*>(&S.buf[b][bi * R + r][kk]), u[r]);
 #pragma unroll
-        for (int c = 0; c < R; ++c) v[c] = S.buf[bj * R + c][kk];
+        for (int c = 0; c < R; ++c) vget(*reinterpret_cast<const VT*>(&S.buf[b][bj * R + c][kk]), v[c]);
 #pragma unroll
-        for (int r = 0; r < R; ++r)
+        for (int e = 0; e < V; ++e)
 #pragma unroll
-          for (int c = 0; c < R; ++c) acc[r][c] += u[r] * v[c];
+          for (int r = 0; r < R; ++r)
+#pragma unroll
+            for (int c = 0; c < R; ++c) acc[r][c] += u[r][e] * v[c][e];
       }
     }
     __syncwarp();
@@ -116,17 +161,16 @@ __global__ __launch_bounds__(FK_WARPS * 32) void factor_kernel(
     int a = (int)((sqrtf(8.0f * e + 1.0f) - 1.0f) * 0.5f);
     while ((a + 1) * (a + 2) / 2 <= e) ++a;
     while (a * (a + 1) / 2 > e) --a;
-    int b = e - a * (a + 1) / 2;
-    T kv = cov_r2<T>(sqdist(&S.xc[a][0], &S.xc[b][0], d), cp.kind, (T)cp.var);
-    if (a == b) kv += (T)cp.tdiag;
-    S.G[a][b] = kv - S.G[a][b];
+    int b2 = e - a * (a + 1) / 2;
+    T kv = cov_r2<T>(sqdist(&S.xc[a][0], &S.xc[b2][0], d), cp.kind, (T)cp.var);
+    if (a == b2) kv += (T)cp.tdiag;
+    S.G[a][b2] = kv - S.G[a][b2];
   }
   __syncwarp();
   // ---- Cholesky of R (lower, in place)
   for (int c = 0; c < Q; ++c) {
     T piv = S.G[c][c];
-    bool bad = !(piv > T(0));
-    if (bad) {
+    if (!(piv > T(0))) {
       if (lane == 0) flag_status(status, ST_NOTPD_FACTOR, i);
       piv = T(NAN);
     }
@@ -158,57 +202,76 @@ __global__ __launch_bounds__(FK_WARPS * 32) void factor_kernel(
     Dv[i] = Dd;
     logD[i] = log(Dd);
   }
-  // ---- row of [F z]
+  // ---- row of [F z]: 16-byte vectors along k
   const T inv = T(1) / lii;
-  for (int k = lane; k < fpad; k += 32) {
-    T v;
-    if (k < m) {
-      v = A[(size_t)i * mpad + k];
-      for (int t = 0; t < q; ++t) v -= S.coef[t] * A[(size_t)S.idx[t] * mpad + k];
-      v *= inv;
-    } else if (k == m) {
-      double zz = y[i];
-      for (int t = 0; t < q; ++t) zz -= (double)S.coef[t] * y[S.idx[t]];
-      v = (T)(zz * (double)inv);
+  for (int k = lane * V; k < fpad; k += 32 * V) {
+    T out[V];
+    if (k < mpad) {
+      T a[V];
+      vget(*reinterpret_cast<const VT*>(A + (size_t)i * mpad + k), a);
+#pragma unroll
+      for (int e = 0; e < V; ++e) out[e] = a[e];
+      for (int t = 0; t < q; ++t) {
+        const T ct = S.coef[t];
+        vget(*reinterpret_cast<const VT*>(A + (size_t)S.idx[t] * mpad + k), a);
+#pragma unroll
+        for (int e = 0; e < V; ++e) out[e] -= ct * a[e];
+      }
+#pragma unroll
+      for (int e = 0; e < V; ++e) out[e] *= inv;
     } else {
-      v = T(0);
+#pragma unroll
+      for (int e = 0; e < V; ++e) out[e] = T(0);
     }
-    F[(size_t)i * fpad + k] = v;
+    VT ov;
+    if constexpr (V == 4) ov = make_float4(out[0], out[1], out[2], out[3]);
+    else ov = make_double2(out[0], out[1]);
+    *reinterpret_cast<VT*>(F + (size_t)i * fpad + k) = ov;
+  }
+  __syncwarp();
+  if (lane == 0) {
+    double zz = y[i];
+    for (int t = 0; t < q; ++t) zz -= (double)S.coef[t] * y[S.idx[t]];
+    F[(size_t)i * fpad + m] = (T)(zz * (double)inv);
   }
 }
 
 template <typename T, int R>
-static cudaError_t launch_factor(const T* A, const T* Xs, const int32_t* N, const double* y, int64_t n, int d,
-                                 int m, int mpad, int mv, int fpad, CovParams cp, T* F, double* Acoef,
-                                 double* Dv, double* logD, int* status, cudaStream_t s) {
+static cudaError_t launch_factor(const T* A, const T* Xs, const int32_t* N, const int32_t* order, const double* y,
+                                 int64_t n, int d, int m, int mpad, int mv, int fpad, CovParams cp, T* F,
+                                 double* Acoef, double* Dv, double* logD, int* status, cudaStream_t s) {
   size_t smem = sizeof(FactorSmem<T, R>) * FK_WARPS;
   cudaError_t e = cudaFuncSetAttribute(factor_kernel<T, R>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        (int)smem);
   if (e != cudaSuccess) return e;
   unsigned grid = (unsigned)((n + FK_WARPS - 1) / FK_WARPS);
-  factor_kernel<T, R><<<grid, FK_WARPS * 32, smem, s>>>(A, Xs, N, y, n, d, m, mpad, mv, fpad, cp, F, Acoef,
-                                                         Dv, logD, status);
+  factor_kernel<T, R><<<grid, FK_WARPS * 32, smem, s>>>(A, Xs, N, order, y, n, d, m, mpad, mv, fpad, cp, F,
+                                                         Acoef, Dv, logD, status);
   return cudaGetLastError();
 }
 
 template <typename T>
-cudaError_t vecchia_factor(const T* A, const T* Xs, const int32_t* N, const double* y, int64_t n, int d, int m,
-                           int mpad, int mv, int fpad, CovParams cp, T* F, double* Acoef, double* Dv,
-                           double* logD, int* status, cudaStream_t s) {
+cudaError_t vecchia_factor(const T* A, const T* Xs, const int32_t* N, const int32_t* order, const double* y,
+                           int64_t n, int d, int m, int mpad, int mv, int fpad, CovParams cp, T* F, double* Acoef,
+                           double* Dv, double* logD, int* status, cudaStream_t s) {
   if (d > FK_MAXD) return cudaErrorInvalidValue;
   const int Q = mv + 1;
-  if (Q <= 12) return launch_factor<T, 2>(A, Xs, N, y, n, d, m, mpad, mv, fpad, cp, F, Acoef, Dv, logD, status, s);
-  if (Q <= 24) return launch_factor<T, 4>(A, Xs, N, y, n, d, m, mpad, mv, fpad, cp, F, Acoef, Dv, logD, status, s);
-  if (Q <= 36) return launch_factor<T, 6>(A, Xs, N, y, n, d, m, mpad, mv, fpad, cp, F, Acoef, Dv, logD, status, s);
-  if (Q <= 48) return launch_factor<T, 8>(A, Xs, N, y, n, d, m, mpad, mv, fpad, cp, F, Acoef, Dv, logD, status, s);
+#define LF(RR) launch_factor<T, RR>(A, Xs, N, order, y, n, d, m, mpad, mv, fpad, cp, F, Acoef, Dv, logD, status, s)
+  if (Q <= 14) return LF(2);
+  if (Q <= 21) return LF(3);
+  if (Q <= 28) return LF(4);
+  if (Q <= 35) return LF(5);
+  if (Q <= 42) return LF(6);
+  if (Q <= 49) return LF(7);
+#undef LF
   return cudaErrorInvalidValue;
 }
-template cudaError_t vecchia_factor<float>(const float*, const float*, const int32_t*, const double*, int64_t, int,
-                                           int, int, int, int, CovParams, float*, double*, double*, double*, int*,
-                                           cudaStream_t);
-template cudaError_t vecchia_factor<double>(const double*, const double*, const int32_t*, const double*, int64_t,
-                                            int, int, int, int, int, CovParams, double*, double*, double*, double*,
-                                            int*, cudaStream_t);
+template cudaError_t vecchia_factor<float>(const float*, const float*, const int32_t*, const int32_t*,
+                                           const double*, int64_t, int, int, int, int, int, CovParams, float*,
+                                           double*, double*, double*, int*, cudaStream_t);
+template cudaError_t vecchia_factor<double>(const double*, const double*, const int32_t*, const int32_t*,
+                                            const double*, int64_t, int, int, int, int, int, CovParams, double*,
+                                            double*, double*, double*, int*, cudaStream_t);
 
 // ---------------------------------------------------------------------------
 // G' = [F z]^T [F z]: split-K SYRK.  CTA = one 64 x 64 tile pair (ti >= tj) and
@@ -283,6 +346,114 @@ __global__ __launch_bounds__(256) void gram_kernel(const T* __restrict__ F, int6
     for (int v = 0; v < 4; ++v) out[(ty * 4 + u) * GT + tx * 4 + v] = dacc[u][v] + (double)acc[u][v];
 }
 
+// float32 Gram, 128 x 128 tile pairs: 256 threads, each an 8 x 8 block made of
+// rows {ty*4..ty*4+3, 64+ty*4..} and columns {tx*4.., 64+tx*4..} so that every
+// operand read is a 16-byte shared-memory vector.  Rows of F are staged 16 at a
+// time, double-buffered through registers.
+//
+// C = I + F^T F is ill-conditioned (its largest eigenvalue grows with n), so the
+// Gram entries must be accurate relative to that eigenvalue: float32 sums run
+// over at most 256 rows and are then added into a float64 copy of the tile held
+// in shared memory.
+constexpr int GT2 = 128;
+constexpr int GR2 = 16;
+constexpr int GD_LD = GT2 + 2;   // float64 tile row stride
+
+__global__ __launch_bounds__(256) void gram_kernel_f32(const float* __restrict__ F, int64_t n, int fpad,
+                                                       double* part, int nsplit) {
+  extern __shared__ __align__(16) double Dacc[];   // [GT2][GD_LD]
+  const int p = blockIdx.x;
+  int ti = (int)((sqrtf(8.0f * p + 1.0f) - 1.0f) * 0.5f);
+  while ((ti + 1) * (ti + 2) / 2 <= p) ++ti;
+  while (ti * (ti + 1) / 2 > p) --ti;
+  const int tj = p - ti * (ti + 1) / 2;
+  const int sidx = blockIdx.y;
+  const int64_t chunk = (((n + nsplit - 1) / nsplit) + GR2 - 1) / GR2 * GR2;
+  const int64_t r0 = (int64_t)sidx * chunk;
+  const int64_t r1 = (n < r0 + chunk) ? n : r0 + chunk;
+  __shared__ __align__(16) float Fi[2][GR2][GT2];
+  __shared__ __align__(16) float Fj[2][GR2][GT2];
+  const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
+  // loader: rows lr and lr+8 of the slab, one float4 of each operand per row
+  const int lr = tid >> 5, lc = (tid & 31) * 4;
+  const int ci = ti * GT2 + lc, cj = tj * GT2 + lc;
+  auto rowof = [&](int u) { return u < 4 ? ty * 4 + u : 64 + ty * 4 + (u - 4); };
+  auto colof = [&](int v) { return v < 4 ? tx * 4 + v : 64 + tx * 4 + (v - 4); };
+  float acc[8][8];
+#pragma unroll
+  for (int u = 0; u < 8; ++u)
+#pragma unroll
+    for (int v = 0; v < 8; ++v) {
+      acc[u][v] = 0.f;
+      Dacc[rowof(u) * GD_LD + colof(v)] = 0.0;
+    }
+  auto gload = [&](int64_t r, int col) -> float4 {
+    if (r < r1 && col < fpad) return *reinterpret_cast<const float4*>(F + (size_t)r * fpad + col);
+    return make_float4(0.f, 0.f, 0.f, 0.f);
+  };
+  float4 ni0 = make_float4(0.f, 0.f, 0.f, 0.f), ni1 = ni0, nj0 = ni0, nj1 = ni0;
+  if (r0 < r1) {
+    ni0 = gload(r0 + lr, ci);
+    ni1 = gload(r0 + lr + 8, ci);
+    nj0 = gload(r0 + lr, cj);
+    nj1 = gload(r0 + lr + 8, cj);
+  }
+  int buf = 0, flush = 0;
+  for (int64_t r = r0; r < r1; r += GR2) {
+    *reinterpret_cast<float4*>(&Fi[buf][lr][lc]) = ni0;
+    *reinterpret_cast<float4*>(&Fi[buf][lr + 8][lc]) = ni1;
+    *reinterpret_cast<float4*>(&Fj[buf][lr][lc]) = nj0;
+    *reinterpret_cast<float4*>(&Fj[buf][lr + 8][lc]) = nj1;
+    __syncthreads();
+    if (r + GR2 < r1) {
+      ni0 = gload(r + GR2 + lr, ci);
+      ni1 = gload(r + GR2 + lr + 8, ci);
+      nj0 = gload(r + GR2 + lr, cj);
+      nj1 = gload(r + GR2 + lr + 8, cj);
+    }
+#pragma unroll 4
+    for (int rr = 0; rr < GR2; ++rr) {
+      float a[8], b[8];
+      float4 a0 = *reinterpret_cast<const float4*>(&Fi[buf][rr][ty * 4]);
+      float4 a1 = *reinterpret_cast<const float4*>(&Fi[buf][rr][64 + ty * 4]);
+      float4 b0 = *reinterpret_cast<const float4*>(&Fj[buf][rr][tx * 4]);
+      float4 b1 = *reinterpret_cast<const float4*>(&Fj[buf][rr][64 + tx * 4]);
+      a[0] = a0.x; a[1] = a0.y; a[2] = a0.z; a[3] = a0.w; a[4] = a1.x; a[5] = a1.y; a[6] = a1.z; a[7] = a1.w;
+      b[0] = b0.x; b[1] = b0.y; b[2] = b0.z; b[3] = b0.w; b[4] = b1.x; b[5] = b1.y; b[6] = b1.z; b[7] = b1.w;
+#pragma unroll
+      for (int u = 0; u < 8; ++u)
+#pragma unroll
+        for (int v = 0; v < 8; ++v) acc[u][v] += a[u] * b[v];
+    }
+    buf ^= 1;
+    if (++flush == 256 / GR2) {
+      flush = 0;
+#pragma unroll
+      for (int u = 0; u < 8; ++u)
+#pragma unroll
+        for (int v = 0; v < 8; ++v) {
+          Dacc[rowof(u) * GD_LD + colof(v)] += (double)acc[u][v];
+          acc[u][v] = 0.f;
+        }
+    }
+  }
+  // write the 128 x 128 partial as 64 x 64 sub-tiles in the pair layout of the
+  // float64 kernel, so one reduction serves both precisions
+  const int np64 = (fpad / GT) * (fpad / GT + 1) / 2;
+#pragma unroll
+  for (int u = 0; u < 8; ++u)
+#pragma unroll
+    for (int v = 0; v < 8; ++v) {
+      const int row = ti * GT2 + rowof(u);
+      const int col = tj * GT2 + colof(v);
+      if (row >= fpad || col >= fpad || col > row) continue;
+      const int a64 = row / GT, b64 = col / GT;
+      const int p64 = a64 * (a64 + 1) / 2 + b64;
+      part[((size_t)sidx * np64 + p64) * GT * GT + (size_t)(row % GT) * GT + (col % GT)] =
+          Dacc[rowof(u) * GD_LD + colof(v)] + (double)acc[u][v];
+    }
+}
+
 __global__ void gram_reduce_kernel(const double* part, int nsplit, int npairs, int m, double* G, int ldg) {
   const int M1 = m + 1;
   int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -299,7 +470,8 @@ __global__ void gram_reduce_kernel(const double* part, int nsplit, int npairs, i
 }
 
 int gram_nsplit(int64_t n, int fpad) {
-  int nt = fpad / GT;
+  // about four CTAs per SM for the 128-wide float32 tiles
+  int nt = (fpad + GT2 - 1) / GT2;
   int npairs = nt * (nt + 1) / 2;
   int64_t want = (4 * 152 + npairs - 1) / npairs;
   int64_t maxs = (n + 255) / 256;
@@ -312,7 +484,15 @@ cudaError_t gram_FtF(const T* F, int64_t n, int fpad, int m, double* part, int n
                      cudaStream_t s) {
   int nt = fpad / GT;
   int npairs = nt * (nt + 1) / 2;
-  gram_kernel<T><<<dim3(npairs, nsplit), 256, 0, s>>>(F, n, fpad, part, nsplit);
+  if constexpr (sizeof(T) == 4) {
+    int nt2 = (fpad + GT2 - 1) / GT2;
+    const int smem = GT2 * GD_LD * (int)sizeof(double);
+    cudaError_t e = cudaFuncSetAttribute(gram_kernel_f32, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    if (e != cudaSuccess) return e;
+    gram_kernel_f32<<<dim3(nt2 * (nt2 + 1) / 2, nsplit), 256, smem, s>>>(F, n, fpad, part, nsplit);
+  } else {
+    gram_kernel<T><<<dim3(npairs, nsplit), 256, 0, s>>>(F, n, fpad, part, nsplit);
+  }
   int64_t tot = (int64_t)(m + 1) * (m + 1);
   gram_reduce_kernel<<<(unsigned)((tot + 255) / 256), 256, 0, s>>>(part, nsplit, npairs, m, G, ldg);
   return cudaGetLastError();

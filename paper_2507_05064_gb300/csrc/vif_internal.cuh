@@ -80,16 +80,23 @@ cudaError_t residual_diag_stats(const double* A, int64_t n, int m, int mpad, dou
                                 float* A32, double* cii, float* rs32, float* nrm32, cudaStream_t s);
 
 // vif_factor.cu
+// order: processing order of the points (a permutation of 0..n-1), or NULL for 0..n-1.
 template <typename T>
-cudaError_t vecchia_factor(const T* A, const T* Xs, const int32_t* N, const double* y, int64_t n, int d,
-                           int m, int mpad, int mv, int fpad, CovParams cp, T* F, double* Acoef,
-                           double* Dv, double* logD, int* status, cudaStream_t s);
+cudaError_t vecchia_factor(const T* A, const T* Xs, const int32_t* N, const int32_t* order, const double* y,
+                           int64_t n, int d, int m, int mpad, int mv, int fpad, CovParams cp, T* F,
+                           double* Acoef, double* Dv, double* logD, int* status, cudaStream_t s);
 template <typename T>
 cudaError_t gram_FtF(const T* F, int64_t n, int fpad, int m, double* part, int nsplit, double* G,
                      int ldg, cudaStream_t s);
 int gram_nsplit(int64_t n, int fpad);
 cudaError_t nll_finish(const double* Lg, int ldg, int m, const double* logD_sum, int64_t n,
                        double* out, cudaStream_t s);
+
+// vif_predict.cu
+cudaError_t predict_all(const double* A, const double* Xs, int64_t n, const double* Ap, const double* Xps,
+                        int64_t np, int d, int m, int mpad, int mv, CovParams cp, const double* y, const double* Lg,
+                        int ldg, double* LinvC, double* w, double* r, double* cjj, double* cpp, int32_t* Np,
+                        int latent, double nugget, double* mean, double* var, int* status, cudaStream_t s);
 
 // vif_knn.cu
 struct KnnParams {

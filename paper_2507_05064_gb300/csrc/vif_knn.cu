@@ -130,12 +130,20 @@ __global__ __launch_bounds__(256) void knn_filter_kernel(KnnParams p, const floa
   const float grow = 1.0f + 8.0f * u32;
   for (int kt = 0; kt <= qt; ++kt) {
     const int64_t k0 = (int64_t)kt * KT;
+    // two-level summation: each 32-term chunk is summed on its own and then added
+    // to the running total, which bounds the float32 error by (32 + m/32 + 2) u
+    // times sum |a_ik a_jk| instead of m u.
     float acc[4][4];
 #pragma unroll
     for (int u = 0; u < 4; ++u)
 #pragma unroll
       for (int v = 0; v < 4; ++v) acc[u][v] = 0.f;
     for (int c0 = 0; c0 < p.m; c0 += KC) {
+      float part[4][4];
+#pragma unroll
+      for (int u = 0; u < 4; ++u)
+#pragma unroll
+        for (int v = 0; v < 4; ++v) part[u][v] = 0.f;
       __syncthreads();
       for (int e = tid; e < KT * KC; e += 256) {
         int r = e / KC, kk = e % KC;
@@ -152,8 +160,12 @@ __global__ __launch_bounds__(256) void knn_filter_kernel(KnnParams p, const floa
 #pragma unroll
         for (int u = 0; u < 4; ++u)
 #pragma unroll
-          for (int v = 0; v < 4; ++v) acc[u][v] += av[u] * bv[v];
+          for (int v = 0; v < 4; ++v) part[u][v] += av[u] * bv[v];
       }
+#pragma unroll
+      for (int u = 0; u < 4; ++u)
+#pragma unroll
+        for (int v = 0; v < 4; ++v) acc[u][v] += part[u][v];
     }
     __syncthreads();
     for (int e = tid; e < KT * d; e += 256) {

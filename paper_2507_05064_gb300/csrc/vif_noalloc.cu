@@ -160,8 +160,8 @@ extern "C" vif_status vif_nll_noalloc(const double* X, int64_t n, int32_t d, con
     NA_CK(linv_transpose<double>(L.Linv, m, mpad, L.LinvT, mpad, s));
   }
   NA_CK(lowrank_A<double>(L.Xs, L.Zs, L.LinvT, mpad, L.A, n, d, m, mpad, cp.kind, cp.var, s));
-  NA_CK(vecchia_factor<double>(L.A, L.Xs, N, y, n, d, m, mpad, mv, fpad, cp, L.F, L.Acoef, L.Dv, L.logD,
-                               L.status, s));
+  NA_CK(vecchia_factor<double>(L.A, L.Xs, N, nullptr, y, n, d, m, mpad, mv, fpad, cp, L.F, L.Acoef, L.Dv,
+                               L.logD, L.status, s));
   NA_CK(gram_FtF<double>(L.F, n, fpad, m, L.part, nsplit, L.G, fpad, s));
   NA_CK(reduce_sum(L.logD, n, L.red, L.dscal, s));
   NA_CK(dense_cholesky(L.G, m + 1, fpad, L.status, ST_NOTPD_CAP, s));

@@ -199,3 +199,44 @@ def test_bad_theta_is_rejected():
         ctx.nll(th, P.y)
     assert ei.value.status == V.VIF_ERR_ARG
     ctx.close()
+
+
+# --------------------------------------------------------------------------- prediction (Prop. 2.1, App. C.1)
+@pytest.mark.parametrize("precision", [V.FP64, V.MIXED])
+def test_c1_prediction_matches_oracle(c1, precision):
+    P, Nor, keys, vif = c1
+    Np = O.pred_neighbors(P.X, P.Z, P.theta, P.Xp, P.mv, vif.lowrank)
+    mu_o, var_o = O.predict_appC(vif, P.y, P.Xp, Np)
+    ctx = V.Context(P.X, P.Z, P.mv, P.theta, precision=precision, neighbor_search=False)
+    ctx.set_neighbors(Nor.astype(np.int32))
+    mu, var = ctx.predict(P.theta, P.y, P.Xp)
+    np.testing.assert_allclose(mu, mu_o, rtol=RTOL64, atol=1e-10)
+    np.testing.assert_allclose(var, var_o, rtol=RTOL64)
+    mu_l, var_l = ctx.predict(P.theta, P.y, P.Xp, latent=True)
+    np.testing.assert_allclose(mu_l, mu_o, rtol=RTOL64, atol=1e-10)
+    np.testing.assert_allclose(var_l, var_o - P.theta.nugget, rtol=1e-7)
+    ctx.close()
+
+
+def test_prediction_with_full_conditioning_is_exact_gp():
+    P = synth.make_problem(45, 2, 8, 45, "matern52", 1.0, 0.2, 0.1, 21, n_pred=30, lloyd=3)
+    ctx = V.Context(P.X, P.Z, 45, P.theta)
+    mu, var = ctx.predict(P.theta, P.y, P.Xp)
+    mu_e, var_e = O.exact_predict(P.X, P.y, P.theta, P.Xp)
+    np.testing.assert_allclose(mu, mu_e, rtol=1e-7, atol=1e-9)
+    np.testing.assert_allclose(var, var_e, rtol=1e-7, atol=1e-9)
+    ctx.close()
+
+
+def test_prediction_without_inducing_points():
+    P = synth.make_problem(400, 2, 0, 8, "matern32", 1.0, 0.15, 0.1, 22, n_pred=60, lloyd=3)
+    Nor = O.causal_neighbors(P.X, P.Z, P.theta, 8)
+    vif = O.VIF(P.X, P.Z, P.theta, Nor)
+    Np = O.pred_neighbors(P.X, P.Z, P.theta, P.Xp, 8, vif.lowrank)
+    mu_o, var_o = O.predict_appC(vif, P.y, P.Xp, Np)
+    ctx = V.Context(P.X, None, 8, P.theta, neighbor_search=False)
+    ctx.set_neighbors(Nor.astype(np.int32))
+    mu, var = ctx.predict(P.theta, P.y, P.Xp)
+    np.testing.assert_allclose(mu, mu_o, rtol=RTOL64, atol=1e-10)
+    np.testing.assert_allclose(var, var_o, rtol=RTOL64)
+    ctx.close()
