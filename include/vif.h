@@ -107,6 +107,39 @@ vif_status vif_nll(vif_ctx *ctx, const vif_cov *theta, const double *y, double *
 vif_status vif_predict(vif_ctx *ctx, const vif_cov *theta, const double *y, const double *Xp,
                        int64_t np, int32_t latent, double *mean, double *var);
 
+/* vif_laplace_mode -- mode b~ of the Laplace approximation for a Bernoulli-logit
+ * likelihood with the VIF prior on the latent GP (Sec. 3, Eq. LA; VIF-Laplace of
+ * Eq. log_det_VIFLA): Newton iterations b <- (W + Sigma_dagger^{-1})^{-1}(W b + grad)
+ * (Eq. one_it_newton_mode) from b = 0, each linear system solved by preconditioned CG
+ * on Eq. pcls1 with the VIFDU preconditioner P = B^T W B + Sigma_dagger^{-1} (Sec. 4.3,
+ * App. E.1).  Needs a context built with likelihood = VIF_BERNOULLI_LOGIT and theta with
+ * nugget 0.  CG starts from 0 and stops when ||v - (W + Sigma_dagger^{-1}) x||_2 <= rel_tol
+ * ||v||_2 (recursive residual); Newton stops when the objective
+ * log p(y|b) - b^T Sigma_dagger^{-1} b / 2 changes by at most 1e-10 relative.
+ *   y: n responses in {0,1}.  mode_out: n values (host or device).  stats: host, may be NULL.
+ *   precond: 0 = VIFDU; 1 = VIFDU with a learned diagonal correction c (W' = W exp(c),
+ *   c from the two-layer network whose weights mlp_weights points to, see vif_mlp_*). */
+typedef struct {
+  double rel_tol;             /* CG tolerance (e.g. 1e-6) */
+  int32_t max_pcg;            /* CG iteration cap per Newton step (e.g. 1000) */
+  int32_t max_newton;         /* Newton step cap (e.g. 50) */
+  int32_t precond;            /* 0 VIFDU, 1 VIFDU with learned diagonal correction */
+  int32_t reserved;           /* must be zero */
+  const void *mlp_weights;    /* device pointer to the packed network weights when precond = 1 */
+} vif_laplace_opts;
+
+typedef struct {
+  int32_t newton_iters;       /* Newton steps taken */
+  int32_t pcg_iters_total;    /* CG iterations summed over the Newton steps */
+  double final_rel_res;       /* relative residual of the last CG solve */
+  double ms_pcg;              /* device time of the CG solves (CUDA events) */
+  double ms_total;            /* device time of the whole call */
+  double objective;           /* log p(y|b~) - b~^T Sigma_dagger^{-1} b~ / 2 */
+} vif_laplace_stats;
+
+vif_status vif_laplace_mode(vif_ctx *ctx, const vif_cov *theta, const double *y,
+                            const vif_laplace_opts *opts, double *mode_out, vif_laplace_stats *stats);
+
 /* vif_set_neighbors / vif_get_neighbors -- replace or read the neighbour table
  * (n x mv int32, row i holds min(i,mv) indices < i in ascending order, padded
  * with -1). */

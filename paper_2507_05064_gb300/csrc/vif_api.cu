@@ -47,6 +47,16 @@ struct vif_ctx {
   double *pXp = nullptr, *pXps = nullptr, *pAp = nullptr, *pcpp = nullptr, *pmean = nullptr, *pvar = nullptr;
   int32_t* pNp = nullptr;
   double *pcjj = nullptr, *pw = nullptr, *pr = nullptr, *pLinvC = nullptr;
+  // Laplace buffers (allocated on the first vif_laplace_mode call)
+  bool lap_ready = false;
+  int32_t *ch_ptr = nullptr, *ch_row = nullptr, *ch_slot = nullptr;
+  double *l_b = nullptr, *l_W = nullptr, *l_v = nullptr, *l_Ginv = nullptr, *l_om = nullptr, *l_rsD = nullptr,
+         *l_ll = nullptr, *l_x = nullptr, *l_r = nullptr, *l_z = nullptr, *l_p = nullptr, *l_Ap = nullptr,
+         *l_t = nullptr, *l_t2 = nullptr, *l_x1 = nullptr, *l_sdi = nullptr, *l_sm = nullptr, *l_cm = nullptr,
+         *l_tm = nullptr, *l_part = nullptr, *l_LinvC = nullptr, *l_G3 = nullptr, *l_LinvC3 = nullptr,
+         *l_sc = nullptr, *l_red = nullptr, *l_corr = nullptr;
+  int *l_flags = nullptr, *l_counter = nullptr, *l_abort = nullptr;
+  int lap_epoch = 0;
   int64_t knn_rescored = 0, knn_fallback = 0;
   bool have_factors = false;
   bool timing = false;
@@ -245,8 +255,12 @@ void free_ctx(vif_ctx* c) {
                   c->y,    c->red,   c->dscal, c->status};
   for (void* b : bufs)
     if (b) cudaFree(b);
-  void* pbufs[] = {c->pA, c->pF, c->pLinvT, c->pXp, c->pXps, c->pAp, c->pcpp, c->pmean, c->pvar, c->pNp,
-                   c->pcjj, c->pw, c->pr, c->pLinvC};
+  void* pbufs[] = {c->pA,     c->pF,    c->pLinvT, c->pXp,    c->pXps,   c->pAp,    c->pcpp,   c->pmean,
+                   c->pvar,   c->pNp,   c->pcjj,   c->pw,     c->pr,     c->pLinvC, c->ch_ptr, c->ch_row,
+                   c->ch_slot, c->l_b,  c->l_W,    c->l_v,    c->l_Ginv, c->l_om,   c->l_rsD,  c->l_ll,
+                   c->l_x,    c->l_r,   c->l_z,    c->l_p,    c->l_Ap,   c->l_t,    c->l_t2,   c->l_x1,
+                   c->l_sdi,  c->l_sm,  c->l_cm,   c->l_tm,   c->l_part, c->l_LinvC, c->l_G3,  c->l_LinvC3,
+                   c->l_sc,   c->l_red, c->l_corr, c->l_flags, c->l_counter, c->l_abort};
   for (void* b : pbufs)
     if (b) cudaFree(b);
   if (c->h_pin) cudaFreeHost(c->h_pin);
@@ -566,6 +580,110 @@ vif_status vif_nll(vif_ctx* ctx, const vif_cov* theta, const double* y, double* 
   return VIF_OK;
 }
 
+namespace {
+
+// float64 buffers of the likelihood pipeline (the context's own, or float64 twins
+// allocated on first use for a mixed-precision context).
+vif_status fp64_buffers(vif_ctx* ctx, double** A64, double** F64, double** LT64) {
+  if (ctx->precision == VIF_FP64) {
+    *A64 = (double*)ctx->A;
+    *F64 = (double*)ctx->F;
+    *LT64 = (double*)ctx->LinvT;
+    return VIF_OK;
+  }
+  if (!ctx->pA) {
+    CKS(dalloc(ctx, &ctx->pA, (size_t)ctx->n * ctx->mpad));
+    CKS(dalloc(ctx, &ctx->pF, (size_t)ctx->n * ctx->fpad));
+    CKS(dalloc(ctx, &ctx->pLinvT, (size_t)ctx->mpad * ctx->mpad));
+    CK(cudaMemsetAsync(ctx->pA, 0, (size_t)ctx->n * ctx->mpad * sizeof(double), ctx->stream));
+  }
+  *A64 = ctx->pA;
+  *F64 = ctx->pF;
+  *LT64 = ctx->pLinvT;
+  return VIF_OK;
+}
+
+// Learned diagonal correction c of the VIFDU preconditioner (filled in by the
+// network of vif_mlp.cu); not available yet.
+cudaError_t mlp_correction(vif_ctx* ctx, const void* weights) {
+  (void)ctx;
+  (void)weights;
+  return cudaErrorNotSupported;
+}
+
+// Children lists of the neighbour DAG (the transpose of N, by column), for B^T.
+vif_status build_children(vif_ctx* ctx) {
+  const int64_t n = ctx->n;
+  const int mv = ctx->mv;
+  std::vector<int32_t> N((size_t)n * std::max(mv, 1), -1);
+  if (mv > 0) {
+    CK(cudaMemcpyAsync(N.data(), ctx->N, (size_t)n * mv * sizeof(int32_t), cudaMemcpyDeviceToHost, ctx->stream));
+    CK(cudaStreamSynchronize(ctx->stream));
+  }
+  std::vector<int32_t> ptr(n + 1, 0);
+  for (int64_t i = 0; i < n; ++i)
+    for (int t = 0; t < mv; ++t) {
+      int j = N[(size_t)i * mv + t];
+      if (j >= 0) ptr[j + 1]++;
+    }
+  for (int64_t j = 0; j < n; ++j) ptr[j + 1] += ptr[j];
+  const int64_t nnz = ptr[n];
+  std::vector<int32_t> row(std::max<int64_t>(nnz, 1)), slot(std::max<int64_t>(nnz, 1));
+  std::vector<int32_t> fill(ptr.begin(), ptr.end() - 1);
+  for (int64_t i = 0; i < n; ++i)
+    for (int t = 0; t < mv; ++t) {
+      int j = N[(size_t)i * mv + t];
+      if (j >= 0) {
+        row[fill[j]] = (int32_t)i;
+        slot[fill[j]] = t;
+        fill[j]++;
+      }
+    }
+  if (!ctx->ch_ptr) {
+    CKS(dalloc(ctx, &ctx->ch_ptr, (size_t)n + 1));
+  }
+  if (ctx->ch_row) cudaFree(ctx->ch_row);
+  if (ctx->ch_slot) cudaFree(ctx->ch_slot);
+  ctx->ch_row = ctx->ch_slot = nullptr;
+  CKS(dalloc(ctx, &ctx->ch_row, (size_t)std::max<int64_t>(nnz, 1)));
+  CKS(dalloc(ctx, &ctx->ch_slot, (size_t)std::max<int64_t>(nnz, 1)));
+  CK(cudaMemcpy(ctx->ch_ptr, ptr.data(), (n + 1) * sizeof(int32_t), cudaMemcpyHostToDevice));
+  CK(cudaMemcpy(ctx->ch_row, row.data(), row.size() * sizeof(int32_t), cudaMemcpyHostToDevice));
+  CK(cudaMemcpy(ctx->ch_slot, slot.data(), slot.size() * sizeof(int32_t), cudaMemcpyHostToDevice));
+  return VIF_OK;
+}
+
+vif_status lap_alloc(vif_ctx* ctx) {
+  if (ctx->lap_ready) return VIF_OK;
+  const int64_t n = ctx->n;
+  const size_t nb = (size_t)((n + 255) / 256);
+  double** vecs[] = {&ctx->l_b, &ctx->l_W,  &ctx->l_v,  &ctx->l_Ginv, &ctx->l_om, &ctx->l_rsD, &ctx->l_ll,
+                     &ctx->l_x, &ctx->l_r,  &ctx->l_z,  &ctx->l_p,    &ctx->l_Ap, &ctx->l_t,   &ctx->l_t2,
+                     &ctx->l_x1, &ctx->l_sdi, &ctx->l_corr};
+  for (double** v : vecs) CKS(dalloc(ctx, v, (size_t)n));
+  CKS(dalloc(ctx, &ctx->l_sm, (size_t)ctx->fpad));
+  CKS(dalloc(ctx, &ctx->l_cm, (size_t)ctx->fpad));
+  CKS(dalloc(ctx, &ctx->l_tm, (size_t)ctx->fpad));
+  CKS(dalloc(ctx, &ctx->l_part, nb * ctx->fpad));
+  CKS(dalloc(ctx, &ctx->l_LinvC, (size_t)std::max(ctx->m, 1) * ctx->fpad));
+  CKS(dalloc(ctx, &ctx->l_G3, (size_t)(ctx->m + 1) * ctx->fpad));
+  CKS(dalloc(ctx, &ctx->l_LinvC3, (size_t)std::max(ctx->m, 1) * ctx->fpad));
+  CKS(dalloc(ctx, &ctx->l_sc, 16));
+  CKS(dalloc(ctx, &ctx->l_red, 256));
+  CKS(dalloc(ctx, &ctx->l_flags, (size_t)n));
+  CKS(dalloc(ctx, &ctx->l_counter, 4));
+  CKS(dalloc(ctx, &ctx->l_abort, 1));
+  CK(cudaMemsetAsync(ctx->l_flags, 0, (size_t)n * sizeof(int), ctx->stream));
+  CK(cudaMemsetAsync(ctx->l_sm, 0, ctx->fpad * sizeof(double), ctx->stream));
+  CK(cudaMemsetAsync(ctx->l_cm, 0, ctx->fpad * sizeof(double), ctx->stream));
+  CK(cudaMemsetAsync(ctx->l_G3, 0, (size_t)(ctx->m + 1) * ctx->fpad * sizeof(double), ctx->stream));
+  CKS(build_children(ctx));
+  ctx->lap_ready = true;
+  return VIF_OK;
+}
+
+}  // namespace
+
 vif_status vif_predict(vif_ctx* ctx, const vif_cov* theta, const double* y, const double* Xp, int64_t np,
                        int32_t latent, double* mean, double* var) {
   if (!ctx) return VIF_ERR_ARG;
@@ -577,23 +695,8 @@ vif_status vif_predict(vif_ctx* ctx, const vif_cov* theta, const double* y, cons
   if (ctx->mv > 48) return set_err(ctx, VIF_ERR_ARG, "m_v too large for prediction");
   const int64_t n = ctx->n;
   const int d = ctx->d, m = ctx->m, mpad = ctx->mpad, fpad = ctx->fpad, mv = ctx->mv;
-  // float64 buffers of the likelihood pipeline
   double *A64, *F64, *LT64;
-  if (ctx->precision == VIF_FP64) {
-    A64 = (double*)ctx->A;
-    F64 = (double*)ctx->F;
-    LT64 = (double*)ctx->LinvT;
-  } else {
-    if (!ctx->pA) {
-      CKS(dalloc(ctx, &ctx->pA, (size_t)n * mpad));
-      CKS(dalloc(ctx, &ctx->pF, (size_t)n * fpad));
-      CKS(dalloc(ctx, &ctx->pLinvT, (size_t)mpad * mpad));
-      CK(cudaMemsetAsync(ctx->pA, 0, (size_t)n * mpad * sizeof(double), ctx->stream));
-    }
-    A64 = ctx->pA;
-    F64 = ctx->pF;
-    LT64 = ctx->pLinvT;
-  }
+  CKS(fp64_buffers(ctx, &A64, &F64, &LT64));
   if (np > ctx->p_cap) {
     double* pb[] = {ctx->pXp, ctx->pXps, ctx->pAp, ctx->pcpp, ctx->pmean, ctx->pvar};
     for (double* b : pb)
@@ -637,6 +740,181 @@ vif_status vif_predict(vif_ctx* ctx, const vif_cov* theta, const double* y, cons
   return VIF_OK;
 }
 
+vif_status vif_laplace_mode(vif_ctx* ctx, const vif_cov* theta, const double* y, const vif_laplace_opts* lo,
+                            double* mode_out, vif_laplace_stats* stats) {
+  if (!ctx) return VIF_ERR_ARG;
+  ctx->err[0] = 0;
+  if (!y || !lo || !mode_out) return set_err(ctx, VIF_ERR_ARG, "y, opts and mode_out are required");
+  CKS(check_cov(ctx, theta, ctx->d));
+  if (ctx->likelihood != VIF_BERNOULLI_LOGIT)
+    return set_err(ctx, VIF_ERR_STATE, "vif_laplace_mode needs a context built for VIF_BERNOULLI_LOGIT");
+  if (theta->nugget != 0.0) return set_err(ctx, VIF_ERR_ARG, "a latent GP has no nugget: set nugget = 0");
+  if (!(lo->rel_tol > 0.0) || lo->max_pcg < 1 || lo->max_newton < 1 || lo->reserved != 0)
+    return set_err(ctx, VIF_ERR_ARG, "invalid Laplace options");
+  if (lo->precond != 0 && lo->precond != 1) return set_err(ctx, VIF_ERR_ARG, "unknown preconditioner");
+  if (lo->precond == 1 && !lo->mlp_weights)
+    return set_err(ctx, VIF_ERR_ARG, "the learned correction needs mlp_weights");
+  const int64_t n = ctx->n;
+  const int m = ctx->m, fpad = ctx->fpad;
+  cudaStream_t s = ctx->stream;
+  double *A64, *F64, *LT64;
+  CKS(fp64_buffers(ctx, &A64, &F64, &LT64));
+  CKS(lap_alloc(ctx));
+  cudaEvent_t e0, e1, p0, p1;
+  CK(cudaEventCreate(&e0));
+  CK(cudaEventCreate(&e1));
+  CK(cudaEventCreate(&p0));
+  CK(cudaEventCreate(&p1));
+  struct EvGuard {
+    cudaEvent_t a, b, c, d;
+    ~EvGuard() {
+      cudaEventDestroy(a);
+      cudaEventDestroy(b);
+      cudaEventDestroy(c);
+      cudaEventDestroy(d);
+    }
+  } guard{e0, e1, p0, p1};
+  CK(cudaEventRecord(e0, s));
+  CovParams cp = cov_params(theta);
+  CK(cudaMemsetAsync(ctx->status, 0, 4 * sizeof(int), s));
+  CK(cudaMemsetAsync(ctx->l_abort, 0, sizeof(int), s));
+  CKS(upload(ctx, ctx->y, y, (size_t)n * sizeof(double)));
+  CKS(apply_scaling(ctx, theta, false));
+  // factors of the latent-GP VIF prior: A, B, D, F and C = I + F^T F (leading block of G')
+  CKS(run_pipeline<double>(ctx, cp, A64, LT64, F64, ctx->Xs, ctx->Zs));
+  if (m > 0) CK(dense_trtri_lower(ctx->G, ctx->l_LinvC, m, fpad, s));
+  double dummy[1];
+  CKS(read_status(ctx, dummy, 0));
+  LapOps o;
+  o.n = n;
+  o.m = m;
+  o.mv = ctx->mv;
+  o.fpad = fpad;
+  o.ldl = fpad;
+  o.N = ctx->N;
+  o.ch_ptr = ctx->ch_ptr;
+  o.ch_row = ctx->ch_row;
+  o.ch_slot = ctx->ch_slot;
+  o.Acoef = ctx->Acoef;
+  o.F = F64;
+  o.LinvC = ctx->l_LinvC;
+  o.LinvC3 = ctx->l_LinvC3;
+  o.rsD = ctx->l_rsD;
+  o.Ginv = ctx->l_Ginv;
+  o.t = ctx->l_t;
+  o.t2 = ctx->l_t2;
+  o.x1 = ctx->l_x1;
+  o.sm = ctx->l_sm;
+  o.cm = ctx->l_cm;
+  o.tmpm = ctx->l_tm;
+  o.partial = ctx->l_part;
+  o.flags = ctx->l_flags;
+  o.counter = ctx->l_counter;
+  o.abort_flag = ctx->l_abort;
+  o.status = ctx->status;
+  const double* corr = nullptr;   // learned correction: filled when precond == 1 (see vif_mlp)
+  if (lo->precond == 1) {
+    CK(mlp_correction(ctx, lo->mlp_weights));
+    corr = ctx->l_corr;
+  }
+  double* sc = ctx->l_sc;   // [0]=rz [1]=pAp [2]=alpha [3]=rr [4]=rz_new [5]=beta [6]=vv [7]=sum ll [8]=b.Sdi b
+  CK(cudaMemsetAsync(ctx->l_b, 0, n * sizeof(double), s));
+  CK(lap_pointwise(ctx->y, ctx->l_b, ctx->Dv, corr, n, ctx->l_W, ctx->l_v, ctx->l_Ginv, ctx->l_om, ctx->l_rsD,
+                   ctx->l_ll, s));
+  int newton = 0, pcg_total = 0;
+  double rel = 0.0, psi_old = 0.0, psi = 0.0, ms_pcg = 0.0;
+  bool have_old = false, converged = false, pcg_capped = false;
+  for (newton = 1; newton <= lo->max_newton; ++newton) {
+    if (lo->precond == 1) {
+      CK(mlp_correction(ctx, lo->mlp_weights));
+      CK(lap_pointwise(ctx->y, ctx->l_b, ctx->Dv, corr, n, ctx->l_W, ctx->l_v, ctx->l_Ginv, ctx->l_om,
+                       ctx->l_rsD, ctx->l_ll, s));
+    }
+    // C_3 = I + F^T diag(omega) F, its factor and inverse factor
+    if (m > 0) {
+      CK(gram_FtF<double>(F64, n, fpad, m, ctx->part, ctx->nsplit, ctx->l_G3, fpad, s, ctx->l_om));
+      CK(dense_cholesky(ctx->l_G3, m, fpad, ctx->status, ST_NOTPD_PRECOND, s));
+      CK(dense_trtri_lower(ctx->l_G3, ctx->l_LinvC3, m, fpad, s));
+    }
+    // PCG on (W + Sigma_dagger^{-1}) x = v from x = 0
+    CK(cudaEventRecord(p0, s));
+    CK(cudaMemsetAsync(ctx->l_x, 0, n * sizeof(double), s));
+    CK(cudaMemcpyAsync(ctx->l_r, ctx->l_v, n * sizeof(double), cudaMemcpyDeviceToDevice, s));
+    CK(lap_dot(ctx->l_v, ctx->l_v, n, ctx->l_red, sc + 6, s));
+    CK(lap_precond(o, ctx->l_r, ctx->l_z, &ctx->lap_epoch, s));
+    CK(cudaMemcpyAsync(ctx->l_p, ctx->l_z, n * sizeof(double), cudaMemcpyDeviceToDevice, s));
+    CK(lap_dot(ctx->l_r, ctx->l_z, n, ctx->l_red, sc + 0, s));
+    CK(cudaMemcpyAsync(ctx->h_pin + 8, sc + 6, sizeof(double), cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    const double vnorm = std::sqrt(ctx->h_pin[8]);
+    int it = 0;
+    rel = 0.0;
+    if (vnorm > 0.0) {
+      for (it = 1; it <= lo->max_pcg; ++it) {
+        CK(lap_matvec(o, ctx->l_p, ctx->l_W, ctx->l_Ap, s));
+        CK(lap_dot(ctx->l_p, ctx->l_Ap, n, ctx->l_red, sc + 1, s));
+        CK(lap_alpha(sc, s));
+        CK(lap_axpy(n, sc + 2, ctx->l_x, ctx->l_p, ctx->l_x, 0, s));
+        CK(lap_axpy(n, sc + 2, ctx->l_r, ctx->l_Ap, ctx->l_r, 1, s));
+        CK(lap_dot(ctx->l_r, ctx->l_r, n, ctx->l_red, sc + 3, s));
+        CK(cudaMemcpyAsync(ctx->h_pin + 8, sc + 3, sizeof(double), cudaMemcpyDeviceToHost, s));
+        CK(cudaMemcpyAsync(ctx->h_pin + 9, ctx->status, 4 * sizeof(int), cudaMemcpyDeviceToHost, s));
+        CK(cudaStreamSynchronize(s));
+        rel = std::sqrt(ctx->h_pin[8]) / vnorm;
+        if (reinterpret_cast<const int*>(ctx->h_pin + 9)[0] != ST_OK) break;
+        if (rel <= lo->rel_tol) break;
+        CK(lap_precond(o, ctx->l_r, ctx->l_z, &ctx->lap_epoch, s));
+        CK(lap_dot(ctx->l_r, ctx->l_z, n, ctx->l_red, sc + 4, s));
+        CK(lap_beta(sc, s));
+        CK(lap_axpy(n, sc + 5, ctx->l_z, nullptr, ctx->l_p, 2, s));
+      }
+      if (it > lo->max_pcg) {
+        it = lo->max_pcg;
+        pcg_capped = true;
+      }
+    }
+    CK(cudaEventRecord(p1, s));
+    CKS(read_status(ctx, dummy, 0));
+    float tms = 0.f;
+    CK(cudaEventElapsedTime(&tms, p0, p1));
+    ms_pcg += tms;
+    pcg_total += it;
+    CK(cudaMemcpyAsync(ctx->l_b, ctx->l_x, n * sizeof(double), cudaMemcpyDeviceToDevice, s));
+    // objective at the new b: sum log p(y|b) - b^T Sigma_dagger^{-1} b / 2
+    CK(lap_pointwise(ctx->y, ctx->l_b, ctx->Dv, corr, n, ctx->l_W, ctx->l_v, ctx->l_Ginv, ctx->l_om, ctx->l_rsD,
+                     ctx->l_ll, s));
+    CK(lap_matvec(o, ctx->l_b, nullptr, ctx->l_sdi, s));
+    CK(lap_dot(ctx->l_ll, nullptr, n, ctx->l_red, sc + 7, s));
+    CK(lap_dot(ctx->l_b, ctx->l_sdi, n, ctx->l_red, sc + 8, s));
+    CK(cudaMemcpyAsync(ctx->h_pin + 8, sc + 7, 2 * sizeof(double), cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    psi = ctx->h_pin[8] - 0.5 * ctx->h_pin[9];
+    if (have_old && std::fabs(psi - psi_old) <= 1e-10 * std::fabs(psi)) {
+      converged = true;
+      break;
+    }
+    psi_old = psi;
+    have_old = true;
+  }
+  if (newton > lo->max_newton) newton = lo->max_newton;
+  CK(cudaEventRecord(e1, s));
+  CKS(download(ctx, mode_out, ctx->l_b, (size_t)n * sizeof(double)));
+  float tot = 0.f;
+  CK(cudaEventElapsedTime(&tot, e0, e1));
+  if (stats) {
+    stats->newton_iters = newton;
+    stats->pcg_iters_total = pcg_total;
+    stats->final_rel_res = rel;
+    stats->ms_pcg = ms_pcg;
+    stats->ms_total = tot;
+    stats->objective = psi;
+  }
+  if (!converged || pcg_capped)
+    return set_err(ctx, VIF_ERR_NOT_CONVERGED, "Newton %s, CG %s", converged ? "converged" : "hit its cap",
+                   pcg_capped ? "hit its cap" : "converged");
+  return VIF_OK;
+}
+
 vif_status vif_set_neighbors(vif_ctx* ctx, const int32_t* N) {
   if (!ctx || !N) return VIF_ERR_ARG;
   if (ctx->mv == 0) return VIF_OK;
@@ -658,6 +936,7 @@ vif_status vif_set_neighbors(vif_ctx* ctx, const int32_t* N) {
   }
   CK(cudaMemcpyAsync(ctx->N, h.data(), cnt * sizeof(int32_t), cudaMemcpyHostToDevice, ctx->stream));
   CK(cudaStreamSynchronize(ctx->stream));
+  if (ctx->lap_ready) CKS(build_children(ctx));
   return VIF_OK;
 }
 

@@ -283,7 +283,7 @@ constexpr int GR = 16;
 
 template <typename T>
 __global__ __launch_bounds__(256) void gram_kernel(const T* __restrict__ F, int64_t n, int fpad, double* part,
-                                                   int nsplit) {
+                                                   int nsplit, const double* __restrict__ wrow) {
   const int p = blockIdx.x;
   int ti = (int)((sqrtf(8.0f * p + 1.0f) - 1.0f) * 0.5f);
   while ((ti + 1) * (ti + 2) / 2 <= p) ++ti;
@@ -312,7 +312,7 @@ __global__ __launch_bounds__(256) void gram_kernel(const T* __restrict__ F, int6
       int rr = e / GT, c = e % GT;
       int64_t row = r + rr;
       bool ok = row < r1;
-      Fi[rr][c] = ok ? F[(size_t)row * fpad + ti * GT + c] : T(0);
+      Fi[rr][c] = ok ? (wrow ? (T)wrow[row] : T(1)) * F[(size_t)row * fpad + ti * GT + c] : T(0);
       Fj[rr][c] = ok ? F[(size_t)row * fpad + tj * GT + c] : T(0);
     }
     __syncthreads();
@@ -481,9 +481,10 @@ int gram_nsplit(int64_t n, int fpad) {
 
 template <typename T>
 cudaError_t gram_FtF(const T* F, int64_t n, int fpad, int m, double* part, int nsplit, double* G, int ldg,
-                     cudaStream_t s) {
+                     cudaStream_t s, const double* wrow) {
   int nt = fpad / GT;
   int npairs = nt * (nt + 1) / 2;
+  if (sizeof(T) == 4 && wrow) return cudaErrorInvalidValue;   // row weights: float64 path only
   if constexpr (sizeof(T) == 4) {
     int nt2 = (fpad + GT2 - 1) / GT2;
     const int smem = GT2 * GD_LD * (int)sizeof(double);
@@ -491,14 +492,16 @@ cudaError_t gram_FtF(const T* F, int64_t n, int fpad, int m, double* part, int n
     if (e != cudaSuccess) return e;
     gram_kernel_f32<<<dim3(nt2 * (nt2 + 1) / 2, nsplit), 256, smem, s>>>(F, n, fpad, part, nsplit);
   } else {
-    gram_kernel<T><<<dim3(npairs, nsplit), 256, 0, s>>>(F, n, fpad, part, nsplit);
+    gram_kernel<T><<<dim3(npairs, nsplit), 256, 0, s>>>(F, n, fpad, part, nsplit, wrow);
   }
   int64_t tot = (int64_t)(m + 1) * (m + 1);
   gram_reduce_kernel<<<(unsigned)((tot + 255) / 256), 256, 0, s>>>(part, nsplit, npairs, m, G, ldg);
   return cudaGetLastError();
 }
-template cudaError_t gram_FtF<float>(const float*, int64_t, int, int, double*, int, double*, int, cudaStream_t);
-template cudaError_t gram_FtF<double>(const double*, int64_t, int, int, double*, int, double*, int, cudaStream_t);
+template cudaError_t gram_FtF<float>(const float*, int64_t, int, int, double*, int, double*, int, cudaStream_t,
+                                     const double*);
+template cudaError_t gram_FtF<double>(const double*, int64_t, int, int, double*, int, double*, int, cudaStream_t,
+                                      const double*);
 
 // NLL = 1/2 [ n log 2pi + sum_{k<m} 2 log L'_kk + sum_i log D_i + L'_mm^2 ],  L' = chol(G').
 __global__ void nll_finish_kernel(const double* Lg, int ldg, int m, const double* logD_sum, int64_t n,

@@ -85,9 +85,10 @@ template <typename T>
 cudaError_t vecchia_factor(const T* A, const T* Xs, const int32_t* N, const int32_t* order, const double* y,
                            int64_t n, int d, int m, int mpad, int mv, int fpad, CovParams cp, T* F,
                            double* Acoef, double* Dv, double* logD, int* status, cudaStream_t s);
+// wrow: optional row weights (NULL = 1): G = F^T diag(wrow) F (+ identity on the first m)
 template <typename T>
 cudaError_t gram_FtF(const T* F, int64_t n, int fpad, int m, double* part, int nsplit, double* G,
-                     int ldg, cudaStream_t s);
+                     int ldg, cudaStream_t s, const double* wrow = nullptr);
 int gram_nsplit(int64_t n, int fpad);
 cudaError_t nll_finish(const double* Lg, int ldg, int m, const double* logD_sum, int64_t n,
                        double* out, cudaStream_t s);
@@ -97,6 +98,28 @@ cudaError_t predict_all(const double* A, const double* Xs, int64_t n, const doub
                         int64_t np, int d, int m, int mpad, int mv, CovParams cp, const double* y, const double* Lg,
                         int ldg, double* LinvC, double* w, double* r, double* cjj, double* cpp, int32_t* Np,
                         int latent, double nugget, double* mean, double* var, int* status, cudaStream_t s);
+
+// vif_laplace.cu
+struct LapOps {
+  int64_t n;
+  int m, mv, fpad, ldl;
+  const int32_t *N, *ch_ptr, *ch_row, *ch_slot;
+  const double *Acoef, *F, *LinvC, *LinvC3;
+  double *rsD, *Ginv;          // 1/sqrt(D_i), 1/(W'_i + 1/D_i)
+  double *t, *t2, *x1;         // n-vector scratch
+  double *sm, *cm, *tmpm;      // m-vector scratch
+  double* partial;             // ceil(n/256) x fpad
+  int *flags, *counter, *abort_flag, *status;
+};
+cudaError_t lap_matvec(const LapOps& o, const double* x, const double* diagW, double* out, cudaStream_t s);
+cudaError_t lap_precond(const LapOps& o, const double* w, double* out, int* epoch, cudaStream_t s);
+cudaError_t lap_pointwise(const double* y, const double* b, const double* D, const double* corr, int64_t n, double* W,
+                          double* v, double* Ginv, double* omega, double* rsD, double* ll, cudaStream_t s);
+cudaError_t lap_dot(const double* a, const double* b, int64_t n, double* partial, double* out, cudaStream_t s);
+cudaError_t lap_axpy(int64_t n, const double* scal, const double* x, const double* y, double* out, int mode,
+                     cudaStream_t s);
+cudaError_t lap_alpha(double* sc, cudaStream_t s);
+cudaError_t lap_beta(double* sc, cudaStream_t s);
 
 // vif_knn.cu
 struct KnnParams {

@@ -22,7 +22,7 @@ FP64, MIXED = 0, 1
 GAUSSIAN, BERNOULLI_LOGIT = 0, 1
 
 # every symbol include/vif.h declares
-EXPORTS = ["vif_build", "vif_nll", "vif_predict", "vif_set_neighbors", "vif_get_neighbors",
+EXPORTS = ["vif_build", "vif_nll", "vif_predict", "vif_laplace_mode", "vif_set_neighbors", "vif_get_neighbors",
            "vif_get_factors", "vif_get_knn_stats", "vif_get_stage_times", "vif_nll_noalloc",
            "vif_last_error", "vif_destroy"]
 NOALLOC_SCRATCH_BYTES = 32 << 20
@@ -36,6 +36,16 @@ class VifCov(C.Structure):
 class VifOpts(C.Structure):
     _fields_ = [("precision", C.c_int32), ("likelihood", C.c_int32), ("no_neighbor_search", C.c_int32),
                 ("stage_timing", C.c_int32), ("reserved", C.c_int32 * 4)]
+
+
+class LaplaceOpts(C.Structure):
+    _fields_ = [("rel_tol", C.c_double), ("max_pcg", C.c_int32), ("max_newton", C.c_int32),
+                ("precond", C.c_int32), ("reserved", C.c_int32), ("mlp_weights", C.c_void_p)]
+
+
+class LaplaceStats(C.Structure):
+    _fields_ = [("newton_iters", C.c_int32), ("pcg_iters_total", C.c_int32), ("final_rel_res", C.c_double),
+                ("ms_pcg", C.c_double), ("ms_total", C.c_double), ("objective", C.c_double)]
 
 
 NSTAGES = 5
@@ -64,6 +74,8 @@ def lib() -> C.CDLL:
                                 C.POINTER(vp)]
         L.vif_nll.argtypes = [vp, C.POINTER(VifCov), vp, dp, dp]
         L.vif_predict.argtypes = [vp, C.POINTER(VifCov), vp, vp, i64, i32, vp, vp]
+        L.vif_laplace_mode.argtypes = [vp, C.POINTER(VifCov), vp, C.POINTER(LaplaceOpts), vp,
+                                       C.POINTER(LaplaceStats)]
         L.vif_set_neighbors.argtypes = [vp, vp]
         L.vif_get_neighbors.argtypes = [vp, vp]
         L.vif_get_factors.argtypes = [vp, vp, vp]
@@ -163,6 +175,21 @@ class Context:
         self._check(lib().vif_predict(self.h, C.byref(cv), _ptr(_f64(y)), _ptr(Xp), npred, int(latent),
                                       _ptr(mean), _ptr(var)))
         return mean, var
+
+    def laplace_mode(self, theta, y, rel_tol=1e-6, max_pcg=1000, max_newton=50, precond=0,
+                     mlp_weights=None, allow_not_converged=False):
+        """Laplace mode for Bernoulli-logit responses y; returns (mode, stats dict)."""
+        cv, ls = make_cov(theta)
+        opts = LaplaceOpts(float(rel_tol), int(max_pcg), int(max_newton), int(precond), 0,
+                           None if mlp_weights is None else _ptr(mlp_weights).value)
+        st = LaplaceStats()
+        mode = np.empty(self.n)
+        rc = lib().vif_laplace_mode(self.h, C.byref(cv), _ptr(_f64(y)), C.byref(opts), _ptr(mode), C.byref(st))
+        if not (rc == VIF_OK or (allow_not_converged and rc == VIF_ERR_NOT_CONVERGED)):
+            self._check(rc)
+        stats = {k: getattr(st, k) for k, _ in LaplaceStats._fields_}
+        stats["status"] = rc
+        return mode, stats
 
     def neighbors(self) -> np.ndarray:
         N = np.empty((self.n, max(self.mv, 0)), dtype=np.int32)

@@ -240,3 +240,61 @@ def test_prediction_without_inducing_points():
     np.testing.assert_allclose(mu, mu_o, rtol=RTOL64, atol=1e-10)
     np.testing.assert_allclose(var, var_o, rtol=RTOL64)
     ctx.close()
+
+
+# --------------------------------------------------------------------------- Laplace (Sec. 3-4)
+def bern(n, m, mv, seed, ls=0.1, d=2):
+    return synth.make_problem(n, d, m, mv, "matern32", 1.0, ls, 0.0, seed, likelihood="bernoulli_logit",
+                              lloyd=3)
+
+
+def test_laplace_mode_matches_oracle_newton_and_pcg():
+    P = bern(2000, 30, 10, 31)
+    Nor = O.causal_neighbors(P.X, P.Z, P.theta, 10)
+    vif = O.VIF(P.X, P.Z, P.theta, Nor)
+    b_dense, steps_d, _ = O.laplace_mode(vif, P.y, dense=True)
+    b_or, steps_o, its_o = O.laplace_mode(vif, P.y, tol=1e-6)
+    ctx = V.Context(P.X, P.Z, 10, P.theta, likelihood=V.BERNOULLI_LOGIT, neighbor_search=False)
+    ctx.set_neighbors(Nor.astype(np.int32))
+    b, st = ctx.laplace_mode(P.theta, P.y, rel_tol=1e-6)
+    assert np.linalg.norm(b - b_dense) <= 1e-5 * np.linalg.norm(b_dense)
+    assert np.linalg.norm(b - b_or) <= 1e-5 * np.linalg.norm(b_or)
+    assert abs(st["newton_iters"] - steps_o) <= 1
+    assert abs(st["pcg_iters_total"] - its_o) <= 2 * steps_o, (st, its_o)
+    # stationarity of the mode, with the oracle's own Sigma_dagger^{-1}
+    g, _ = O.bern_grad_W(P.y, b)
+    assert np.linalg.norm(g - vif.Sigma_dagger_inv(b)) <= 1e-5 * np.linalg.norm(g)
+    ctx.close()
+
+
+def test_vifdu_without_neighbors_takes_one_cg_step():
+    P = bern(1500, 25, 0, 32)
+    ctx = V.Context(P.X, P.Z, 0, P.theta, likelihood=V.BERNOULLI_LOGIT)
+    b, st = ctx.laplace_mode(P.theta, P.y, rel_tol=1e-8)
+    assert st["pcg_iters_total"] == st["newton_iters"]
+    vif = O.VIF(P.X, P.Z, P.theta, np.zeros((1500, 0), dtype=np.int64))
+    b_dense, _, _ = O.laplace_mode(vif, P.y, dense=True)
+    np.testing.assert_allclose(b, b_dense, rtol=1e-6, atol=1e-8)
+    ctx.close()
+
+
+def test_laplace_with_gpu_neighbors_and_no_inducing_points():
+    P = bern(1200, 0, 8, 33)
+    Nor = O.causal_neighbors(P.X, P.Z, P.theta, 8)
+    vif = O.VIF(P.X, P.Z, P.theta, Nor)
+    b_dense, _, _ = O.laplace_mode(vif, P.y, dense=True)
+    ctx = V.Context(P.X, None, 8, P.theta, likelihood=V.BERNOULLI_LOGIT)
+    b, st = ctx.laplace_mode(P.theta, P.y, rel_tol=1e-8)
+    assert np.linalg.norm(b - b_dense) <= 1e-6 * np.linalg.norm(b_dense)
+    ctx.close()
+
+
+def test_laplace_rejects_a_nugget():
+    P = bern(300, 10, 4, 34)
+    ctx = V.Context(P.X, P.Z, 4, P.theta, likelihood=V.BERNOULLI_LOGIT)
+    th = P.theta.copy()
+    th.nugget = 0.1
+    with pytest.raises(V.VifError) as ei:
+        ctx.laplace_mode(th, P.y)
+    assert ei.value.status == V.VIF_ERR_ARG
+    ctx.close()
