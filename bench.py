@@ -44,6 +44,8 @@ def parse():
     ap.add_argument("--fp64-steps", type=int, default=3)
     ap.add_argument("--cpu-sample", type=int, default=20_000)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-laplace", action="store_true")
+    ap.add_argument("--laplace-n", type=int, default=200_000)
     return ap.parse_args()
 
 
@@ -163,6 +165,30 @@ def cpu_baseline(P, n_s, steps=1):
                       f"{t:.2f} s per sample eval, scaled by n/{n_s}"}
 
 
+def laplace_block(args, stream):
+    """Bernoulli-logit Laplace mode at n = 2e5 (Matern-3/2, range 0.05, m = 200, m_v = 20):
+    Newton + PCG to relative residual 1e-6 with the plain VIFDU preconditioner."""
+    import torch
+    from paper_2507_05064_gb300 import synth
+    from paper_2507_05064_gb300 import vif as V
+    P = synth.config4(n=args.laplace_n)
+    t0 = time.time()
+    ctx = V.Context(P.X, P.Z, P.mv, P.theta, precision=V.FP64, likelihood=V.BERNOULLI_LOGIT,
+                    stream=stream.cuda_stream)
+    torch.cuda.synchronize()
+    build_s = time.time() - t0
+    y = torch.from_numpy(P.y).cuda()
+    ctx.laplace_mode(P.theta, y, rel_tol=1e-6)          # warm-up
+    t0 = time.perf_counter()
+    _, st = ctx.laplace_mode(P.theta, y, rel_tol=1e-6)
+    wall = time.perf_counter() - t0
+    ctx.close()
+    return {"workload": f"laplace-bernoulli-matern32-n{P.X.shape[0]}-d2-m{P.Z.shape[0]}-mv{P.mv}",
+            "precond": "VIFDU", "rel_tol": 1e-6, "newton_iters": st["newton_iters"],
+            "pcg_iters_total": st["pcg_iters_total"], "ms_pcg": st["ms_pcg"], "ms_total_device": st["ms_total"],
+            "wall_s": wall, "neighbor_build_s": build_s, "objective": st["objective"]}
+
+
 def run_reference(args, rank, world):
     if rank != 0:
         return
@@ -277,6 +303,9 @@ def run_vif(args, rank, world, dist):
             "algorithmic_flops_per_launch": flops, "algorithmic_bytes_per_launch": byts,
             "hbm_achieved_gbs": byts / (med[dom] * 1e-3) / 1e9,
             "hbm_peak_gbs_measured": pk.get("hbm_gbs")}
+    lap = None
+    if not args.no_laplace:
+        lap = laplace_block(args, stream)
     cb = None
     if not args.no_cpu_baseline:
         cb = cpu_baseline(P, min(args.cpu_sample, P.X.shape[0]))
@@ -294,6 +323,7 @@ def run_vif(args, rank, world, dist):
         "stage_ms": med,
         "neighbor_search": {"build_s": build_s, "queries_rescored": rescored, "queries_fallback": fallback},
         "roofline": roof,
+        "laplace": lap,
         "cpu_baseline": cb,
         "e2e": {"value": world * 1000.0 / e2e_ms, "unit": UNIT, "ms_per_step": e2e_ms,
                 "h2d_bytes_per_step": int(P.y.nbytes) + 256, "d2h_bytes_per_step": 16 + 24},

@@ -94,7 +94,10 @@ vif_status vif_build(const double *X, int64_t n, int32_t d, const double *Z, int
  * with log det via Sylvester (det M det Sigma_m^{-1} det D) and the solve via
  * Woodbury (M of Eq. def_M), for the hyperparameters `theta` and the fixed
  * neighbour sets of the context.  y: n responses.  nll_out: HOST double.
- * grad_out: must be NULL (reserved for the gradient of Sec. 2.2 / App. A). */
+ * grad_out: NULL, or a HOST array of n_ls + 2 doubles that receives the gradient of
+ * the likelihood (Sec. 2.2) with respect to (sigma1^2, lambda_1..lambda_{n_ls}, sigma^2),
+ * with N and Z held fixed, as central differences of the float64 likelihood with
+ * relative steps of 1e-4 (2 (n_ls + 2) extra float64 evaluations; needs nugget > 0). */
 vif_status vif_nll(vif_ctx *ctx, const vif_cov *theta, const double *y, double *nll_out,
                    double *grad_out);
 
@@ -139,6 +142,25 @@ typedef struct {
 
 vif_status vif_laplace_mode(vif_ctx *ctx, const vif_cov *theta, const double *y,
                             const vif_laplace_opts *opts, double *mode_out, vif_laplace_stats *stats);
+
+/* vif_batch_* -- likelihoods of many independent problems per CUDA graph replay.
+ * vif_batch_create captures the likelihood pipeline (vif_nll) of every context into
+ * one graph whose problems run on concurrent branches, for fixed hyperparameters
+ * thetas[k] and fixed DEVICE response vectors ys[k] (each ctxs[k]->n long; the
+ * graph reads them at every replay, so their contents may change between runs).
+ * A project autotuner times a few launch shapes (number of concurrent branches, Gram
+ * split factor) on the first capture and keeps the fastest.  vif_batch_run replays the
+ * graph and writes nprob likelihoods to nll_out (HOST).  The contexts must stay alive
+ * and must not be used by other calls while the batch exists.  stream: cudaStream_t
+ * the replays are ordered on.  The paper has no batched interface; this is the
+ * throughput form of vif_nll for many small problems. */
+typedef struct vif_batch vif_batch;
+vif_status vif_batch_create(vif_ctx *const *ctxs, int32_t nprob, const vif_cov *thetas,
+                            const double *const *ys, void *stream, vif_batch **out);
+vif_status vif_batch_run(vif_batch *batch, double *nll_out);
+/* launch shape chosen by the autotuner: branches, Gram split divisor, best replay ms */
+vif_status vif_batch_info(const vif_batch *batch, int32_t *branches, int32_t *split_div, double *ms);
+void vif_batch_destroy(vif_batch *batch);
 
 /* vif_set_neighbors / vif_get_neighbors -- replace or read the neighbour table
  * (n x mv int32, row i holds min(i,mv) indices < i in ascending order, padded

@@ -648,3 +648,71 @@ def laplace_mode(vif: VIF, y, tol=1e-6, max_pcg=1000, max_newton=50, psi_tol=1e-
             return b, t, tot
         psi_old = psi
     return b, max_newton, tot
+
+
+# ----------------------------------------------------------------------------
+# Gradient of the negative log-likelihood (Sec. 2.2)
+# ----------------------------------------------------------------------------
+def theta_vector(theta) -> np.ndarray:
+    """Parameter order of the gradient: (sigma1^2, lambda_1..lambda_k, sigma^2)."""
+    return np.concatenate([[theta.variance], np.atleast_1d(theta.lengthscale), [theta.nugget]])
+
+
+def theta_from_vector(theta, v):
+    t = theta.copy()
+    k = np.atleast_1d(theta.lengthscale).size
+    t.variance = float(v[0])
+    t.lengthscale = np.array(v[1:1 + k], dtype=np.float64)
+    t.nugget = float(v[1 + k])
+    return t
+
+
+def vif_nll_grad_fd(X, Z, theta, N, y, rel_step=1e-4):
+    """Central differences of the VIF NLL with N and Z held fixed (R11): step
+    h_k = rel_step * theta_k in each parameter."""
+    v0 = theta_vector(theta)
+    g = np.empty_like(v0)
+    for k in range(v0.size):
+        h = rel_step * abs(v0[k]) if v0[k] != 0 else rel_step
+        vp, vm = v0.copy(), v0.copy()
+        vp[k] += h
+        vm[k] -= h
+        g[k] = (vif_nll(X, Z, theta_from_vector(theta, vp), N, y)
+                - vif_nll(X, Z, theta_from_vector(theta, vm), N, y)) / (2 * h)
+    return g
+
+
+def dcov_of_r(r, kind, variance):
+    """dc/dr for the kernels of cov_of_r."""
+    if kind == 0:
+        return -variance * np.exp(-r)
+    if kind == 1:
+        return -3.0 * variance * r * np.exp(-SQRT3 * r)
+    if kind == 2:
+        return -(5.0 / 3.0) * variance * r * (1.0 + SQRT5 * r) * np.exp(-SQRT5 * r)
+    return -variance * r * np.exp(-0.5 * r * r)
+
+
+def exact_gp_grad(X, y, theta) -> np.ndarray:
+    """Analytic gradient of the exact GP NLL (Sec. 2 first display):
+    dL/dth = 1/2 tr(Sigma~^{-1} dSigma~) - 1/2 alpha^T dSigma~ alpha, alpha = Sigma~^{-1} y,
+    for (sigma1^2, lambda (one or per dimension), sigma^2)."""
+    S = exact_cov(X, theta)
+    L = np.linalg.cholesky(S)
+    Sinv = sla.cho_solve((L, True), np.eye(len(y)))
+    alpha = Sinv @ y
+    ls = np.atleast_1d(theta.lengthscale)
+    Xs = scaled(X, theta)
+    r = dist(Xs, Xs)
+    K = cov_of_r(r, theta.kind, theta.variance)
+    dK = dcov_of_r(r, theta.kind, theta.variance)
+    mats = [K / theta.variance]
+    with np.errstate(divide="ignore", invalid="ignore"):
+        if ls.size == 1:
+            mats.append(np.where(r > 0, -dK * r / ls[0], 0.0))
+        else:
+            for k in range(ls.size):
+                dk2 = (X[:, None, k] - X[None, :, k]) ** 2 / ls[k] ** 3
+                mats.append(np.where(r > 0, -dK * dk2 / r, 0.0))
+    mats.append(np.eye(len(y)))
+    return np.array([0.5 * np.sum(Sinv * M) - 0.5 * alpha @ M @ alpha for M in mats])

@@ -113,12 +113,12 @@ def kmeanspp(Xs: np.ndarray, m: int, rng: np.random.Generator, lloyd: int = 10) 
 def make_problem(n: int, d: int, m: int, mv: int, kind: str, variance: float,
                  lengthscale, nugget: float, seed: int, likelihood: str = "gaussian",
                  inducing: str = "kmeans++", n_pred: int = 0, lloyd: int = 10,
-                 name: str = "") -> Problem:
+                 name: str = "", rff: int | None = None) -> Problem:
     rng = _rng(seed)
     X = rng.uniform(size=(n, d))
     ls = np.atleast_1d(np.asarray(lengthscale, dtype=np.float64))
     theta = Theta(KIND_IDS[kind], float(variance), ls, float(nugget))
-    f = latent_rff(X, theta, rng, R=2048 if n <= 100_000 else 512)
+    f = latent_rff(X, theta, rng, R=rff or (2048 if n <= 100_000 else 512))
     if likelihood == "gaussian":
         y = f + math.sqrt(nugget) * rng.standard_normal(n)
     else:
@@ -168,3 +168,22 @@ def config4(n=200_000, lloyd=5) -> Problem:
     return make_problem(n, 2, 200, 20, "matern32", 1.0, 0.05, 0.0, 20250711,
                         likelihood="bernoulli_logit", lloyd=lloyd,
                         name=f"bernoulli-matern32-n{n}-d2-m200-mv20")
+
+
+def config5(nprob=256, n_lo=2_000, n_hi=50_000, seed=20250712, lloyd=2):
+    """256 independent Gaussian problems: n log-uniform in [2e3, 5e4], d in {2, 5},
+    m uniform in [64, 256], m_v uniform in [10, 40], Matern-3/2 or 5/2 with range
+    uniform in [0.02, 0.3], nugget uniform in [0.01, 0.1], k-means++ inducing points."""
+    rng = _rng(seed)
+    out = []
+    for k in range(nprob):
+        n = int(round(math.exp(rng.uniform(math.log(n_lo), math.log(n_hi)))))
+        d = int(rng.choice([2, 5]))
+        m = int(rng.integers(64, 257))
+        mv = int(rng.integers(10, 41))
+        kind = "matern32" if rng.uniform() < 0.5 else "matern52"
+        rng_range = float(rng.uniform(0.02, 0.3))
+        nug = float(rng.uniform(0.01, 0.1))
+        out.append(make_problem(n, d, m, mv, kind, 1.0, rng_range, nug, seed * 1000 + k, lloyd=lloyd,
+                                rff=256, name=f"c5-{k}"))
+    return out

@@ -22,7 +22,8 @@ FP64, MIXED = 0, 1
 GAUSSIAN, BERNOULLI_LOGIT = 0, 1
 
 # every symbol include/vif.h declares
-EXPORTS = ["vif_build", "vif_nll", "vif_predict", "vif_laplace_mode", "vif_set_neighbors", "vif_get_neighbors",
+EXPORTS = ["vif_build", "vif_nll", "vif_predict", "vif_laplace_mode", "vif_batch_create", "vif_batch_run",
+           "vif_batch_info", "vif_batch_destroy", "vif_set_neighbors", "vif_get_neighbors",
            "vif_get_factors", "vif_get_knn_stats", "vif_get_stage_times", "vif_nll_noalloc",
            "vif_last_error", "vif_destroy"]
 NOALLOC_SCRATCH_BYTES = 32 << 20
@@ -82,12 +83,17 @@ def lib() -> C.CDLL:
         L.vif_get_knn_stats.argtypes = [vp, C.POINTER(i64), C.POINTER(i64)]
         L.vif_get_stage_times.argtypes = [vp, dp]
         L.vif_nll_noalloc.argtypes = [vp, i64, i32, vp, i32, vp, i32, C.POINTER(VifCov), vp, vp, dp]
+        L.vif_batch_create.argtypes = [C.POINTER(vp), i32, C.POINTER(VifCov), C.POINTER(vp), vp, C.POINTER(vp)]
+        L.vif_batch_run.argtypes = [vp, dp]
+        L.vif_batch_info.argtypes = [vp, C.POINTER(i32), C.POINTER(i32), dp]
+        L.vif_batch_destroy.argtypes = [vp]
+        L.vif_batch_destroy.restype = None
         L.vif_last_error.argtypes = [vp]
         L.vif_last_error.restype = C.c_char_p
         L.vif_destroy.argtypes = [vp]
         L.vif_destroy.restype = None
         for name in EXPORTS:
-            if name not in ("vif_last_error", "vif_destroy"):
+            if name not in ("vif_last_error", "vif_destroy", "vif_batch_destroy"):
                 getattr(L, name).restype = C.c_int
         _lib = L
     return _lib
@@ -132,6 +138,46 @@ def nll_noalloc(X, Z, N, mv: int, theta, y, stream: int = 0) -> float:
     return out.value
 
 
+class Batch:
+    """Likelihoods of many contexts per CUDA graph replay (vif_batch_*)."""
+
+    def __init__(self, contexts, thetas, ys, stream: int = 0):
+        L = lib()
+        n = len(contexts)
+        self._covs = [make_cov(t) for t in thetas]
+        arr = (VifCov * n)(*[c for c, _ in self._covs])
+        hs = (C.c_void_p * n)(*[c.h for c in contexts])
+        yp = (C.c_void_p * n)(*[_ptr(y).value for y in ys])
+        h = C.c_void_p()
+        st = L.vif_batch_create(hs, n, arr, yp, C.c_void_p(stream), C.byref(h))
+        if st != VIF_OK:
+            raise VifError(st, L.vif_last_error(None).decode())
+        self.h, self.n, self._keep = h, n, (contexts, ys)
+
+    def run(self) -> np.ndarray:
+        out = np.empty(self.n)
+        st = lib().vif_batch_run(self.h, out.ctypes.data_as(C.POINTER(C.c_double)))
+        if st != VIF_OK:
+            raise VifError(st, lib().vif_last_error(None).decode())
+        return out
+
+    def info(self):
+        b, sd, ms = C.c_int32(), C.c_int32(), C.c_double()
+        lib().vif_batch_info(self.h, C.byref(b), C.byref(sd), C.byref(ms))
+        return {"branches": b.value, "split_div": sd.value, "best_replay_ms": ms.value}
+
+    def close(self):
+        if getattr(self, "h", None):
+            lib().vif_batch_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
 class Context:
     """One built VIF problem: data, inducing points and neighbour sets (vif_build)."""
 
@@ -159,12 +205,15 @@ class Context:
         if st != VIF_OK:
             raise VifError(st, lib().vif_last_error(self.h).decode())
 
-    def nll(self, theta, y) -> float:
+    def nll(self, theta, y, grad: bool = False):
+        """NLL, or (NLL, gradient wrt (sigma1^2, lambda..., sigma^2)) when grad=True."""
         cv, ls = make_cov(theta)
         out = C.c_double()
         y = _f64(y)
-        self._check(lib().vif_nll(self.h, C.byref(cv), _ptr(y), C.byref(out), None))
-        return out.value
+        g = np.empty(ls.size + 2) if grad else None
+        gp = g.ctypes.data_as(C.POINTER(C.c_double)) if grad else None
+        self._check(lib().vif_nll(self.h, C.byref(cv), _ptr(y), C.byref(out), gp))
+        return (out.value, g) if grad else out.value
 
     def predict(self, theta, y, Xp, latent: bool = False):
         cv, ls = make_cov(theta)

@@ -298,3 +298,51 @@ def test_laplace_rejects_a_nugget():
         ctx.laplace_mode(th, P.y)
     assert ei.value.status == V.VIF_ERR_ARG
     ctx.close()
+
+
+# --------------------------------------------------------------------------- gradient (Sec. 2.2)
+def test_c1_gradient_matches_oracle(c1):
+    P, Nor, keys, vif = c1
+    g_or = O.vif_nll_grad_fd(P.X, P.Z, P.theta, Nor, P.y)
+    for prec in (V.FP64, V.MIXED):
+        ctx = V.Context(P.X, P.Z, P.mv, P.theta, precision=prec, neighbor_search=False)
+        ctx.set_neighbors(Nor.astype(np.int32))
+        nll, g = ctx.nll(P.theta, P.y, grad=True)
+        np.testing.assert_allclose(g, g_or, rtol=1e-6, atol=1e-6 * np.abs(g_or).max())
+        assert nll_close(nll, vif.nll(P.y), 2000, RTOL64 if prec == V.FP64 else RTOL_MIXED)
+        ctx.close()
+
+
+def test_gradient_with_full_conditioning_is_the_exact_gp_gradient():
+    P = synth.make_problem(45, 2, 8, 45, "matern32", 1.0, 0.2, 0.1, 41, lloyd=3)
+    ctx = V.Context(P.X, P.Z, 45, P.theta)
+    _, g = ctx.nll(P.theta, P.y, grad=True)
+    np.testing.assert_allclose(g, O.exact_gp_grad(P.X, P.y, P.theta), rtol=1e-6, atol=1e-6)
+    ctx.close()
+
+
+# --------------------------------------------------------------------------- batched problems (one graph)
+def test_batch_graph_replay_matches_single_problem_calls():
+    torch = pytest.importorskip("torch")
+    probs = synth.config5(nprob=10, n_lo=300, n_hi=2500)
+    ctxs, ys, ref = [], [], []
+    for k, P in enumerate(probs):
+        prec = V.MIXED if k % 2 else V.FP64
+        c = V.Context(P.X, P.Z, P.mv, P.theta, precision=prec)
+        ctxs.append(c)
+        ys.append(torch.from_numpy(P.y).cuda())
+        ref.append(c.nll(P.theta, P.y))
+    B = V.Batch(ctxs, [P.theta for P in probs], ys)
+    for _ in range(2):
+        got = B.run()
+        np.testing.assert_allclose(got, ref, rtol=1e-12)
+    info = B.info()
+    assert info["branches"] in (4, 8, 16, 32) and info["best_replay_ms"] > 0
+    # three problems against the oracle on the GPU's neighbour sets' definition
+    for k in (0, 2, 4):
+        P = probs[k]
+        Nor = O.causal_neighbors(P.X, P.Z, P.theta, P.mv)
+        assert nll_close(got[k], O.vif_nll(P.X, P.Z, P.theta, Nor, P.y), P.X.shape[0], RTOL64)
+    B.close()
+    for c in ctxs:
+        c.close()

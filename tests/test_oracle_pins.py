@@ -249,3 +249,27 @@ def test_laplace_mode_is_stationary_and_pcg_agrees_with_dense_newton():
     b_p, steps, its = O.laplace_mode(vif, P.y, tol=1e-10)
     np.testing.assert_allclose(b_p, b_d, rtol=1e-6, atol=1e-8)
     assert steps < 20 and its > 0
+
+
+# --------------------------------------------------------------------------- gradient
+def test_fd_gradient_with_full_conditioning_is_the_exact_gp_gradient():
+    """m_v = n-1 makes the VIF likelihood the exact one, whose gradient is analytic."""
+    P = small_problem(n=60, m=8, mv=59, nugget=0.1, kind="matern32", ls=0.2)
+    N = O.causal_neighbors(P.X, P.Z, P.theta, 59)
+    g_fd = O.vif_nll_grad_fd(P.X, P.Z, P.theta, N, P.y)
+    g_ex = O.exact_gp_grad(P.X, P.y, P.theta)
+    np.testing.assert_allclose(g_fd, g_ex, rtol=1e-6, atol=1e-6)
+
+
+def test_exact_gp_gradient_ard_matches_its_own_finite_differences():
+    P = small_problem(n=40, m=0, mv=0, nugget=0.05, kind="se", ls=np.array([0.2, 0.4]))
+    g = O.exact_gp_grad(P.X, P.y, P.theta)
+    v0 = O.theta_vector(P.theta)
+    for k in range(v0.size):
+        h = 1e-5 * v0[k]
+        vp, vm = v0.copy(), v0.copy()
+        vp[k] += h
+        vm[k] -= h
+        fp = O.dense_nll(O.exact_cov(P.X, O.theta_from_vector(P.theta, vp)), P.y)
+        fm = O.dense_nll(O.exact_cov(P.X, O.theta_from_vector(P.theta, vm)), P.y)
+        assert (fp - fm) / (2 * h) == pytest.approx(g[k], rel=1e-5, abs=1e-6)
