@@ -143,6 +143,52 @@ typedef struct {
 vif_status vif_laplace_mode(vif_ctx *ctx, const vif_cov *theta, const double *y,
                             const vif_laplace_opts *opts, double *mode_out, vif_laplace_stats *stats);
 
+/* Learned diagonal correction of the VIFDU preconditioner (the paper has none):
+ * c_i = 4 tanh(o_i / 4), o_i from a tanh network 8 -> 64 -> 64 -> 1 on local features
+ * of point i, and the preconditioner uses W'_i = W_i exp(c_i).  The network lives in a
+ * caller-allocated DEVICE buffer of vif_mlp_bytes() bytes (float32 master weights, Adam
+ * moments, the float16 copy the kernels read).  Parameters are packed as W1 (64 x 8,
+ * row-major), b1 (64), W2 (64 x 64), b2 (64), w3 (64), b3 (1): VIF_MLP_NPARAM floats. */
+#define VIF_MLP_NIN 8
+#define VIF_MLP_NH 64
+#define VIF_MLP_NPARAM (VIF_MLP_NH * VIF_MLP_NIN + VIF_MLP_NH + VIF_MLP_NH * VIF_MLP_NH + VIF_MLP_NH + VIF_MLP_NH + 1)
+size_t vif_mlp_bytes(void);
+/* Glorot-uniform hidden layers and a zero output layer (c = 0: plain VIFDU). */
+vif_status vif_mlp_init(void *net, uint64_t seed, void *stream);
+/* Set / read the float32 parameters (params: VIF_MLP_NPARAM floats, host or device). */
+vif_status vif_mlp_set_params(void *net, const float *params, void *stream);
+vif_status vif_mlp_get_params(const void *net, float *params);
+/* c = network(feats) for n feature rows (DEVICE n x 8 float in, DEVICE n float out). */
+vif_status vif_mlp_forward(const void *net, const float *feats, int64_t n, float *c, void *stream);
+/* grad = d(sum_i gc_i c_i)/d(params) (DEVICE inputs, DEVICE VIF_MLP_NPARAM floats out). */
+vif_status vif_mlp_backward(const void *net, const float *feats, const float *gc, int64_t n, float *grad,
+                            void *stream);
+/* Network inputs of every point for the Laplace weights W (n, host or device), with the
+ * residual Vecchia factors of the last vif_laplace_mode / vif_mlp_train call on ctx:
+ *   0 (log W_i + 3)/2   1 (log D_i + 3)/2   2 log(1 + W_i D_i)   3 |N(i)|/m_v
+ *   4 sum_k A_i[k]^2    5 sum of A_j[k]^2 over the points j that condition on i
+ *   6 log(mean_k W_{N_k(i)} / W_i)   7 log(1 + sum_{j: N_k(j)=i} W_j A_j[k]^2 / W_i).
+ * feats: n x 8 float (host or device). */
+vif_status vif_mlp_features(vif_ctx *ctx, const double *W, float *feats);
+
+typedef struct {
+  int32_t steps_per_system;   /* Adam steps at each Newton iterate (each iterate is one system) */
+  int32_t probes;             /* Rademacher probes per step */
+  int32_t max_newton;         /* Newton iterates used as training systems */
+  float lr;                   /* Adam learning rate */
+  uint64_t seed;              /* probe generator seed */
+} vif_mlp_train_opts;
+typedef struct {
+  int32_t systems;            /* training systems visited */
+  double loss_first, loss_last;  /* probe loss ||P^{-1}Az - z||^2 / n at the first and last step */
+} vif_mlp_train_stats;
+/* Train the network on the Laplace systems of one problem (ctx built for
+ * VIF_BERNOULLI_LOGIT, theta with nugget 0, responses y in {0,1}): Newton iterates of
+ * the plain VIFDU solve (CG tolerance 1e-6) are the systems; at each, the network takes
+ * steps_per_system Adam steps on the Hutchinson estimate of ||P^{-1} A - I||_F^2. */
+vif_status vif_mlp_train(vif_ctx *ctx, const vif_cov *theta, const double *y, const vif_mlp_train_opts *opts,
+                         void *net, vif_mlp_train_stats *stats);
+
 /* vif_batch_* -- likelihoods of many independent problems per CUDA graph replay.
  * vif_batch_create captures the likelihood pipeline (vif_nll) of every context into
  * one graph whose problems run on concurrent branches, for fixed hyperparameters

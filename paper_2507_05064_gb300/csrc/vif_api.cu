@@ -56,6 +56,7 @@ struct vif_ctx {
          *l_tm = nullptr, *l_part = nullptr, *l_LinvC = nullptr, *l_G3 = nullptr, *l_LinvC3 = nullptr,
          *l_sc = nullptr, *l_red = nullptr, *l_corr = nullptr;
   int *l_flags = nullptr, *l_counter = nullptr, *l_abort = nullptr;
+  float *m_feat = nullptr, *m_gc = nullptr, *m_part = nullptr, *m_grad = nullptr;
   int lap_epoch = 0;
   int64_t knn_rescored = 0, knn_fallback = 0;
   bool have_factors = false;
@@ -260,7 +261,8 @@ void free_ctx(vif_ctx* c) {
                    c->ch_slot, c->l_b,  c->l_W,    c->l_v,    c->l_Ginv, c->l_om,   c->l_rsD,  c->l_ll,
                    c->l_x,    c->l_r,   c->l_z,    c->l_p,    c->l_Ap,   c->l_t,    c->l_t2,   c->l_x1,
                    c->l_sdi,  c->l_sm,  c->l_cm,   c->l_tm,   c->l_part, c->l_LinvC, c->l_G3,  c->l_LinvC3,
-                   c->l_sc,   c->l_red, c->l_corr, c->l_flags, c->l_counter, c->l_abort};
+                   c->l_sc,   c->l_red, c->l_corr, c->l_flags, c->l_counter, c->l_abort, c->m_feat,
+                   c->m_gc,   c->m_part, c->m_grad};
   for (void* b : pbufs)
     if (b) cudaFree(b);
   if (c->h_pin) cudaFreeHost(c->h_pin);
@@ -435,12 +437,6 @@ vif_status fp64_buffers(vif_ctx* ctx, double** A64, double** F64, double** LT64)
 }
 
 // Learned diagonal correction c of the VIFDU preconditioner (filled in by the
-// network of vif_mlp.cu); not available yet.
-cudaError_t mlp_correction(vif_ctx* ctx, const void* weights) {
-  (void)ctx;
-  (void)weights;
-  return cudaErrorNotSupported;
-}
 
 // Children lists of the neighbour DAG (the transpose of N, by column), for B^T.
 vif_status build_children(vif_ctx* ctx) {
@@ -767,6 +763,135 @@ vif_status vif_predict(vif_ctx* ctx, const vif_cov* theta, const double* y, cons
   return VIF_OK;
 }
 
+}  // extern "C"
+
+namespace {
+
+// Factors of the latent-GP VIF prior for theta (A, B, D, F, C = I + F^T F and the
+// inverse of its Cholesky factor) and the operator bundle of the Laplace kernels.
+vif_status lap_setup(vif_ctx* ctx, const vif_cov* theta, const double* y, LapOps* o) {
+  cudaStream_t s = ctx->stream;
+  double *A64, *F64, *LT64;
+  CKS(fp64_buffers(ctx, &A64, &F64, &LT64));
+  CKS(lap_alloc(ctx));
+  CovParams cp = cov_params(theta);
+  CK(cudaMemsetAsync(ctx->status, 0, 4 * sizeof(int), s));
+  CK(cudaMemsetAsync(ctx->l_abort, 0, sizeof(int), s));
+  CKS(upload(ctx, ctx->y, y, (size_t)ctx->n * sizeof(double)));
+  CKS(apply_scaling(ctx, theta, false));
+  CKS(run_pipeline<double>(ctx, cp, A64, LT64, F64, ctx->Xs, ctx->Zs));
+  if (ctx->m > 0) CK(dense_trtri_lower(ctx->G, ctx->l_LinvC, ctx->m, ctx->fpad, s));
+  double dummy[1];
+  CKS(read_status(ctx, dummy, 0));
+  o->n = ctx->n;
+  o->m = ctx->m;
+  o->mv = ctx->mv;
+  o->fpad = ctx->fpad;
+  o->ldl = ctx->fpad;
+  o->N = ctx->N;
+  o->ch_ptr = ctx->ch_ptr;
+  o->ch_row = ctx->ch_row;
+  o->ch_slot = ctx->ch_slot;
+  o->Acoef = ctx->Acoef;
+  o->F = F64;
+  o->LinvC = ctx->l_LinvC;
+  o->LinvC3 = ctx->l_LinvC3;
+  o->rsD = ctx->l_rsD;
+  o->Ginv = ctx->l_Ginv;
+  o->t = ctx->l_t;
+  o->t2 = ctx->l_t2;
+  o->x1 = ctx->l_x1;
+  o->sm = ctx->l_sm;
+  o->cm = ctx->l_cm;
+  o->tmpm = ctx->l_tm;
+  o->partial = ctx->l_part;
+  o->flags = ctx->l_flags;
+  o->counter = ctx->l_counter;
+  o->abort_flag = ctx->l_abort;
+  o->status = ctx->status;
+  return VIF_OK;
+}
+
+// C_3 = I + F^T diag(omega) F, its Cholesky factor and the inverse factor.
+vif_status lap_c3(vif_ctx* ctx, const LapOps& o) {
+  if (ctx->m == 0) return VIF_OK;
+  cudaStream_t s = ctx->stream;
+  CK(gram_FtF<double>(o.F, ctx->n, ctx->fpad, ctx->m, ctx->part, ctx->nsplit, ctx->l_G3, ctx->fpad, s, ctx->l_om));
+  CK(dense_cholesky(ctx->l_G3, ctx->m, ctx->fpad, ctx->status, ST_NOTPD_PRECOND, s));
+  CK(dense_trtri_lower(ctx->l_G3, ctx->l_LinvC3, ctx->m, ctx->fpad, s));
+  return VIF_OK;
+}
+
+// Preconditioned CG from x = 0 on (W + Sigma_dagger^{-1}) x = v (v in l_v, x in l_x).
+vif_status lap_pcg(vif_ctx* ctx, const LapOps& o, double tol, int max_it, int* iters, double* rel, bool* capped) {
+  cudaStream_t s = ctx->stream;
+  const int64_t n = ctx->n;
+  double* sc = ctx->l_sc;   // [0]=rz [1]=pAp [2]=alpha [3]=rr [4]=rz_new [5]=beta [6]=vv
+  CK(cudaMemsetAsync(ctx->l_x, 0, n * sizeof(double), s));
+  CK(cudaMemcpyAsync(ctx->l_r, ctx->l_v, n * sizeof(double), cudaMemcpyDeviceToDevice, s));
+  CK(lap_dot(ctx->l_v, ctx->l_v, n, ctx->l_red, sc + 6, s));
+  CK(lap_precond(o, ctx->l_r, ctx->l_z, &ctx->lap_epoch, s));
+  CK(cudaMemcpyAsync(ctx->l_p, ctx->l_z, n * sizeof(double), cudaMemcpyDeviceToDevice, s));
+  CK(lap_dot(ctx->l_r, ctx->l_z, n, ctx->l_red, sc + 0, s));
+  CK(cudaMemcpyAsync(ctx->h_pin + 8, sc + 6, sizeof(double), cudaMemcpyDeviceToHost, s));
+  CK(cudaStreamSynchronize(s));
+  const double vnorm = std::sqrt(ctx->h_pin[8]);
+  int it = 0;
+  *rel = 0.0;
+  *capped = false;
+  if (vnorm > 0.0) {
+    for (it = 1; it <= max_it; ++it) {
+      CK(lap_matvec(o, ctx->l_p, ctx->l_W, ctx->l_Ap, s));
+      CK(lap_dot(ctx->l_p, ctx->l_Ap, n, ctx->l_red, sc + 1, s));
+      CK(lap_alpha(sc, s));
+      CK(lap_axpy(n, sc + 2, ctx->l_x, ctx->l_p, ctx->l_x, 0, s));
+      CK(lap_axpy(n, sc + 2, ctx->l_r, ctx->l_Ap, ctx->l_r, 1, s));
+      CK(lap_dot(ctx->l_r, ctx->l_r, n, ctx->l_red, sc + 3, s));
+      CK(cudaMemcpyAsync(ctx->h_pin + 8, sc + 3, sizeof(double), cudaMemcpyDeviceToHost, s));
+      CK(cudaMemcpyAsync(ctx->h_pin + 9, ctx->status, 4 * sizeof(int), cudaMemcpyDeviceToHost, s));
+      CK(cudaStreamSynchronize(s));
+      *rel = std::sqrt(ctx->h_pin[8]) / vnorm;
+      if (reinterpret_cast<const int*>(ctx->h_pin + 9)[0] != ST_OK) break;
+      if (*rel <= tol) break;
+      CK(lap_precond(o, ctx->l_r, ctx->l_z, &ctx->lap_epoch, s));
+      CK(lap_dot(ctx->l_r, ctx->l_z, n, ctx->l_red, sc + 4, s));
+      CK(lap_beta(sc, s));
+      CK(lap_axpy(n, sc + 5, ctx->l_z, nullptr, ctx->l_p, 2, s));
+    }
+    if (it > max_it) {
+      it = max_it;
+      *capped = true;
+    }
+  }
+  double dummy[1];
+  CKS(read_status(ctx, dummy, 0));
+  *iters = it;
+  return VIF_OK;
+}
+
+// mlp scratch: features (n x 8 float), gc (n float), backward partials, gradient
+vif_status mlp_scratch(vif_ctx* ctx) {
+  if (ctx->m_feat) return VIF_OK;
+  CKS(dalloc(ctx, &ctx->m_feat, (size_t)ctx->n * VIF_MLP_NIN));
+  CKS(dalloc(ctx, &ctx->m_gc, (size_t)ctx->n));
+  CKS(dalloc(ctx, &ctx->m_part, (size_t)mlp_backward_blocks(ctx->n) * ((VIF_MLP_NPARAM + 63) / 64 * 64)));
+  CKS(dalloc(ctx, &ctx->m_grad, (size_t)VIF_MLP_NPARAM + 64));
+  return VIF_OK;
+}
+
+// c = network(features(W)) into l_corr.
+vif_status mlp_correction_c(vif_ctx* ctx, const void* net) {
+  CKS(mlp_scratch(ctx));
+  CK(mlp_features(ctx->l_W, ctx->Dv, ctx->Acoef, ctx->N, ctx->ch_ptr, ctx->ch_row, ctx->ch_slot, ctx->n, ctx->mv,
+                  ctx->m_feat, ctx->stream));
+  CK(mlp_forward_f64(net, ctx->m_feat, ctx->n, ctx->l_corr, ctx->stream));
+  return VIF_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
 vif_status vif_laplace_mode(vif_ctx* ctx, const vif_cov* theta, const double* y, const vif_laplace_opts* lo,
                             double* mode_out, vif_laplace_stats* stats) {
   if (!ctx) return VIF_ERR_ARG;
@@ -782,130 +907,52 @@ vif_status vif_laplace_mode(vif_ctx* ctx, const vif_cov* theta, const double* y,
   if (lo->precond == 1 && !lo->mlp_weights)
     return set_err(ctx, VIF_ERR_ARG, "the learned correction needs mlp_weights");
   const int64_t n = ctx->n;
-  const int m = ctx->m, fpad = ctx->fpad;
   cudaStream_t s = ctx->stream;
-  double *A64, *F64, *LT64;
-  CKS(fp64_buffers(ctx, &A64, &F64, &LT64));
-  CKS(lap_alloc(ctx));
-  cudaEvent_t e0, e1, p0, p1;
+  cudaEvent_t e0, e1;
   CK(cudaEventCreate(&e0));
   CK(cudaEventCreate(&e1));
-  CK(cudaEventCreate(&p0));
-  CK(cudaEventCreate(&p1));
   struct EvGuard {
-    cudaEvent_t a, b, c, d;
+    cudaEvent_t a, b;
     ~EvGuard() {
       cudaEventDestroy(a);
       cudaEventDestroy(b);
-      cudaEventDestroy(c);
-      cudaEventDestroy(d);
     }
-  } guard{e0, e1, p0, p1};
+  } guard{e0, e1};
   CK(cudaEventRecord(e0, s));
-  CovParams cp = cov_params(theta);
-  CK(cudaMemsetAsync(ctx->status, 0, 4 * sizeof(int), s));
-  CK(cudaMemsetAsync(ctx->l_abort, 0, sizeof(int), s));
-  CKS(upload(ctx, ctx->y, y, (size_t)n * sizeof(double)));
-  CKS(apply_scaling(ctx, theta, false));
-  // factors of the latent-GP VIF prior: A, B, D, F and C = I + F^T F (leading block of G')
-  CKS(run_pipeline<double>(ctx, cp, A64, LT64, F64, ctx->Xs, ctx->Zs));
-  if (m > 0) CK(dense_trtri_lower(ctx->G, ctx->l_LinvC, m, fpad, s));
-  double dummy[1];
-  CKS(read_status(ctx, dummy, 0));
   LapOps o;
-  o.n = n;
-  o.m = m;
-  o.mv = ctx->mv;
-  o.fpad = fpad;
-  o.ldl = fpad;
-  o.N = ctx->N;
-  o.ch_ptr = ctx->ch_ptr;
-  o.ch_row = ctx->ch_row;
-  o.ch_slot = ctx->ch_slot;
-  o.Acoef = ctx->Acoef;
-  o.F = F64;
-  o.LinvC = ctx->l_LinvC;
-  o.LinvC3 = ctx->l_LinvC3;
-  o.rsD = ctx->l_rsD;
-  o.Ginv = ctx->l_Ginv;
-  o.t = ctx->l_t;
-  o.t2 = ctx->l_t2;
-  o.x1 = ctx->l_x1;
-  o.sm = ctx->l_sm;
-  o.cm = ctx->l_cm;
-  o.tmpm = ctx->l_tm;
-  o.partial = ctx->l_part;
-  o.flags = ctx->l_flags;
-  o.counter = ctx->l_counter;
-  o.abort_flag = ctx->l_abort;
-  o.status = ctx->status;
-  const double* corr = nullptr;   // learned correction: filled when precond == 1 (see vif_mlp)
-  if (lo->precond == 1) {
-    CK(mlp_correction(ctx, lo->mlp_weights));
-    corr = ctx->l_corr;
-  }
-  double* sc = ctx->l_sc;   // [0]=rz [1]=pAp [2]=alpha [3]=rr [4]=rz_new [5]=beta [6]=vv [7]=sum ll [8]=b.Sdi b
+  CKS(lap_setup(ctx, theta, y, &o));
+  const bool learned = lo->precond == 1;
+  const double* corr = learned ? ctx->l_corr : nullptr;
   CK(cudaMemsetAsync(ctx->l_b, 0, n * sizeof(double), s));
+  CK(cudaMemsetAsync(ctx->l_corr, 0, n * sizeof(double), s));
   CK(lap_pointwise(ctx->y, ctx->l_b, ctx->Dv, corr, n, ctx->l_W, ctx->l_v, ctx->l_Ginv, ctx->l_om, ctx->l_rsD,
                    ctx->l_ll, s));
   int newton = 0, pcg_total = 0;
   double rel = 0.0, psi_old = 0.0, psi = 0.0, ms_pcg = 0.0;
   bool have_old = false, converged = false, pcg_capped = false;
+  cudaEvent_t p0, p1;
+  CK(cudaEventCreate(&p0));
+  CK(cudaEventCreate(&p1));
+  EvGuard guard2{p0, p1};
+  double* sc = ctx->l_sc;
   for (newton = 1; newton <= lo->max_newton; ++newton) {
-    if (lo->precond == 1) {
-      CK(mlp_correction(ctx, lo->mlp_weights));
+    if (learned) {
+      CKS(mlp_correction_c(ctx, lo->mlp_weights));
       CK(lap_pointwise(ctx->y, ctx->l_b, ctx->Dv, corr, n, ctx->l_W, ctx->l_v, ctx->l_Ginv, ctx->l_om,
                        ctx->l_rsD, ctx->l_ll, s));
     }
-    // C_3 = I + F^T diag(omega) F, its factor and inverse factor
-    if (m > 0) {
-      CK(gram_FtF<double>(F64, n, fpad, m, ctx->part, ctx->nsplit, ctx->l_G3, fpad, s, ctx->l_om));
-      CK(dense_cholesky(ctx->l_G3, m, fpad, ctx->status, ST_NOTPD_PRECOND, s));
-      CK(dense_trtri_lower(ctx->l_G3, ctx->l_LinvC3, m, fpad, s));
-    }
-    // PCG on (W + Sigma_dagger^{-1}) x = v from x = 0
+    CKS(lap_c3(ctx, o));
     CK(cudaEventRecord(p0, s));
-    CK(cudaMemsetAsync(ctx->l_x, 0, n * sizeof(double), s));
-    CK(cudaMemcpyAsync(ctx->l_r, ctx->l_v, n * sizeof(double), cudaMemcpyDeviceToDevice, s));
-    CK(lap_dot(ctx->l_v, ctx->l_v, n, ctx->l_red, sc + 6, s));
-    CK(lap_precond(o, ctx->l_r, ctx->l_z, &ctx->lap_epoch, s));
-    CK(cudaMemcpyAsync(ctx->l_p, ctx->l_z, n * sizeof(double), cudaMemcpyDeviceToDevice, s));
-    CK(lap_dot(ctx->l_r, ctx->l_z, n, ctx->l_red, sc + 0, s));
-    CK(cudaMemcpyAsync(ctx->h_pin + 8, sc + 6, sizeof(double), cudaMemcpyDeviceToHost, s));
-    CK(cudaStreamSynchronize(s));
-    const double vnorm = std::sqrt(ctx->h_pin[8]);
     int it = 0;
-    rel = 0.0;
-    if (vnorm > 0.0) {
-      for (it = 1; it <= lo->max_pcg; ++it) {
-        CK(lap_matvec(o, ctx->l_p, ctx->l_W, ctx->l_Ap, s));
-        CK(lap_dot(ctx->l_p, ctx->l_Ap, n, ctx->l_red, sc + 1, s));
-        CK(lap_alpha(sc, s));
-        CK(lap_axpy(n, sc + 2, ctx->l_x, ctx->l_p, ctx->l_x, 0, s));
-        CK(lap_axpy(n, sc + 2, ctx->l_r, ctx->l_Ap, ctx->l_r, 1, s));
-        CK(lap_dot(ctx->l_r, ctx->l_r, n, ctx->l_red, sc + 3, s));
-        CK(cudaMemcpyAsync(ctx->h_pin + 8, sc + 3, sizeof(double), cudaMemcpyDeviceToHost, s));
-        CK(cudaMemcpyAsync(ctx->h_pin + 9, ctx->status, 4 * sizeof(int), cudaMemcpyDeviceToHost, s));
-        CK(cudaStreamSynchronize(s));
-        rel = std::sqrt(ctx->h_pin[8]) / vnorm;
-        if (reinterpret_cast<const int*>(ctx->h_pin + 9)[0] != ST_OK) break;
-        if (rel <= lo->rel_tol) break;
-        CK(lap_precond(o, ctx->l_r, ctx->l_z, &ctx->lap_epoch, s));
-        CK(lap_dot(ctx->l_r, ctx->l_z, n, ctx->l_red, sc + 4, s));
-        CK(lap_beta(sc, s));
-        CK(lap_axpy(n, sc + 5, ctx->l_z, nullptr, ctx->l_p, 2, s));
-      }
-      if (it > lo->max_pcg) {
-        it = lo->max_pcg;
-        pcg_capped = true;
-      }
-    }
+    bool capped = false;
+    CKS(lap_pcg(ctx, o, lo->rel_tol, lo->max_pcg, &it, &rel, &capped));
     CK(cudaEventRecord(p1, s));
-    CKS(read_status(ctx, dummy, 0));
+    CK(cudaEventSynchronize(p1));
     float tms = 0.f;
     CK(cudaEventElapsedTime(&tms, p0, p1));
     ms_pcg += tms;
     pcg_total += it;
+    pcg_capped = pcg_capped || capped;
     CK(cudaMemcpyAsync(ctx->l_b, ctx->l_x, n * sizeof(double), cudaMemcpyDeviceToDevice, s));
     // objective at the new b: sum log p(y|b) - b^T Sigma_dagger^{-1} b / 2
     CK(lap_pointwise(ctx->y, ctx->l_b, ctx->Dv, corr, n, ctx->l_W, ctx->l_v, ctx->l_Ginv, ctx->l_om, ctx->l_rsD,
@@ -939,6 +986,139 @@ vif_status vif_laplace_mode(vif_ctx* ctx, const vif_cov* theta, const double* y,
   if (!converged || pcg_capped)
     return set_err(ctx, VIF_ERR_NOT_CONVERGED, "Newton %s, CG %s", converged ? "converged" : "hit its cap",
                    pcg_capped ? "hit its cap" : "converged");
+  return VIF_OK;
+}
+
+size_t vif_mlp_bytes(void) { return mlp_bytes(); }
+
+vif_status vif_mlp_init(void* net, uint64_t seed, void* stream) {
+  if (!net) return VIF_ERR_ARG;
+  if (mlp_init(net, seed, (cudaStream_t)stream) != cudaSuccess) return VIF_ERR_CUDA;
+  return cudaStreamSynchronize((cudaStream_t)stream) == cudaSuccess ? VIF_OK : VIF_ERR_CUDA;
+}
+
+vif_status vif_mlp_set_params(void* net, const float* params, void* stream) {
+  if (!net || !params) return VIF_ERR_ARG;
+  cudaStream_t s = (cudaStream_t)stream;
+  float* tmp = nullptr;
+  if (cudaMalloc((void**)&tmp, VIF_MLP_NPARAM * sizeof(float)) != cudaSuccess) return VIF_ERR_NOMEM;
+  cudaError_t e = cudaMemcpyAsync(tmp, params, VIF_MLP_NPARAM * sizeof(float), cudaMemcpyDefault, s);
+  if (e == cudaSuccess) e = mlp_set(net, tmp, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  cudaFree(tmp);
+  return e == cudaSuccess ? VIF_OK : VIF_ERR_CUDA;
+}
+
+vif_status vif_mlp_get_params(const void* net, float* params) {
+  if (!net || !params) return VIF_ERR_ARG;
+  return cudaMemcpy(params, mlp_master(net), VIF_MLP_NPARAM * sizeof(float), cudaMemcpyDefault) == cudaSuccess
+             ? VIF_OK
+             : VIF_ERR_CUDA;
+}
+
+vif_status vif_mlp_forward(const void* net, const float* feats, int64_t n, float* c, void* stream) {
+  if (!net || !feats || !c || n < 1) return VIF_ERR_ARG;
+  cudaStream_t s = (cudaStream_t)stream;
+  if (mlp_forward_f32(net, feats, n, c, s) != cudaSuccess) return VIF_ERR_CUDA;
+  return cudaStreamSynchronize(s) == cudaSuccess ? VIF_OK : VIF_ERR_CUDA;
+}
+
+vif_status vif_mlp_backward(const void* net, const float* feats, const float* gc, int64_t n, float* grad,
+                            void* stream) {
+  if (!net || !feats || !gc || !grad || n < 1) return VIF_ERR_ARG;
+  cudaStream_t s = (cudaStream_t)stream;
+  float* part = nullptr;
+  const size_t pc = (size_t)mlp_backward_blocks(n) * ((VIF_MLP_NPARAM + 63) / 64 * 64);
+  if (cudaMalloc((void**)&part, pc * sizeof(float)) != cudaSuccess) return VIF_ERR_NOMEM;
+  cudaError_t e = mlp_backward(net, feats, gc, n, part, grad, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  cudaFree(part);
+  return e == cudaSuccess ? VIF_OK : VIF_ERR_CUDA;
+}
+
+vif_status vif_mlp_features(vif_ctx* ctx, const double* W, float* feats) {
+  if (!ctx || !W || !feats) return VIF_ERR_ARG;
+  if (!ctx->lap_ready) return set_err(ctx, VIF_ERR_STATE, "call vif_laplace_mode or vif_mlp_train first");
+  CKS(mlp_scratch(ctx));
+  CKS(upload(ctx, ctx->l_t, W, (size_t)ctx->n * sizeof(double)));
+  CK(mlp_features(ctx->l_t, ctx->Dv, ctx->Acoef, ctx->N, ctx->ch_ptr, ctx->ch_row, ctx->ch_slot, ctx->n, ctx->mv,
+                  ctx->m_feat, ctx->stream));
+  return download(ctx, feats, ctx->m_feat, (size_t)ctx->n * VIF_MLP_NIN * sizeof(float));
+}
+
+vif_status vif_mlp_train(vif_ctx* ctx, const vif_cov* theta, const double* y, const vif_mlp_train_opts* to,
+                         void* net, vif_mlp_train_stats* stats) {
+  if (!ctx || !to || !net || !y) return VIF_ERR_ARG;
+  ctx->err[0] = 0;
+  CKS(check_cov(ctx, theta, ctx->d));
+  if (ctx->likelihood != VIF_BERNOULLI_LOGIT || theta->nugget != 0.0)
+    return set_err(ctx, VIF_ERR_STATE, "training needs a Bernoulli-logit context and nugget 0");
+  if (to->steps_per_system < 1 || to->probes < 1 || to->max_newton < 1 || !(to->lr > 0.f))
+    return set_err(ctx, VIF_ERR_ARG, "invalid training options");
+  const int64_t n = ctx->n;
+  cudaStream_t s = ctx->stream;
+  LapOps o;
+  CKS(lap_setup(ctx, theta, y, &o));
+  CKS(mlp_scratch(ctx));
+  double* sc = ctx->l_sc;
+  CK(cudaMemsetAsync(ctx->l_b, 0, n * sizeof(double), s));
+  double loss_first = -1.0, loss_last = 0.0;
+  int systems = 0;
+  uint64_t probe_ctr = 0;
+  const double coeff = -2.0 / to->probes;
+  for (int newton = 1; newton <= to->max_newton; ++newton) {
+    ++systems;
+    CK(lap_pointwise(ctx->y, ctx->l_b, ctx->Dv, nullptr, n, ctx->l_W, ctx->l_v, ctx->l_Ginv, ctx->l_om, ctx->l_rsD,
+                     ctx->l_ll, s));
+    for (int step = 0; step < to->steps_per_system; ++step) {
+      CKS(mlp_correction_c(ctx, net));
+      CK(lap_pointwise(ctx->y, ctx->l_b, ctx->Dv, ctx->l_corr, n, ctx->l_W, ctx->l_v, ctx->l_Ginv, ctx->l_om,
+                       ctx->l_rsD, ctx->l_ll, s));
+      CKS(lap_c3(ctx, o));
+      CK(mlp_zero(ctx->m_gc, n, s));
+      CK(cudaMemsetAsync(sc + 10, 0, sizeof(double), s));
+      double loss = 0.0;
+      for (int k = 0; k < to->probes; ++k) {
+        // z -> l_x, A z -> l_r, u = P^-1 A z -> l_z, r = u - z -> l_p, s = P^-1 r -> l_Ap
+        CK(mlp_rademacher(to->seed * 0x9E3779B97F4A7C15ull + (++probe_ctr), n, ctx->l_x, s));
+        CK(lap_matvec(o, ctx->l_x, ctx->l_W, ctx->l_r, s));
+        CK(lap_precond(o, ctx->l_r, ctx->l_z, &ctx->lap_epoch, s));
+        {
+          // r = u - z: l_p = l_z - 1 * l_x
+          double one = 1.0;
+          CK(cudaMemcpyAsync(sc + 11, &one, sizeof(double), cudaMemcpyHostToDevice, s));
+          CK(lap_axpy(n, sc + 11, ctx->l_z, ctx->l_x, ctx->l_p, 1, s));
+        }
+        CK(lap_precond(o, ctx->l_p, ctx->l_Ap, &ctx->lap_epoch, s));
+        CK(mlp_lp_grad(ctx->N, ctx->Acoef, n, ctx->mv, ctx->l_Ap, ctx->l_z, ctx->l_W, ctx->l_corr, coeff, ctx->m_gc,
+                       s));
+        CK(lap_dot(ctx->l_p, ctx->l_p, n, ctx->l_red, sc + 9, s));
+        CK(cudaMemcpyAsync(ctx->h_pin + 16, sc + 9, sizeof(double), cudaMemcpyDeviceToHost, s));
+        CK(cudaStreamSynchronize(s));
+        loss += ctx->h_pin[16];
+      }
+      loss /= (double)to->probes * (double)n;
+      if (loss_first < 0.0) loss_first = loss;
+      loss_last = loss;
+      CK(mlp_backward(net, ctx->m_feat, ctx->m_gc, n, ctx->m_part, ctx->m_grad, s));
+      CK(mlp_adam(net, ctx->m_grad, to->lr, s));
+    }
+    // next Newton iterate with the plain preconditioner
+    CK(lap_pointwise(ctx->y, ctx->l_b, ctx->Dv, nullptr, n, ctx->l_W, ctx->l_v, ctx->l_Ginv, ctx->l_om, ctx->l_rsD,
+                     ctx->l_ll, s));
+    CKS(lap_c3(ctx, o));
+    int it = 0;
+    double rel = 0.0;
+    bool capped = false;
+    CKS(lap_pcg(ctx, o, 1e-6, 1000, &it, &rel, &capped));
+    CK(cudaMemcpyAsync(ctx->l_b, ctx->l_x, n * sizeof(double), cudaMemcpyDeviceToDevice, s));
+  }
+  CK(cudaStreamSynchronize(s));
+  if (stats) {
+    stats->systems = systems;
+    stats->loss_first = loss_first;
+    stats->loss_last = loss_last;
+  }
   return VIF_OK;
 }
 

@@ -121,6 +121,25 @@ cudaError_t lap_axpy(int64_t n, const double* scal, const double* x, const doubl
 cudaError_t lap_alpha(double* sc, cudaStream_t s);
 cudaError_t lap_beta(double* sc, cudaStream_t s);
 
+// vif_mlp.cu
+size_t mlp_bytes();
+cudaError_t mlp_init(void* net, uint64_t seed, cudaStream_t s);
+cudaError_t mlp_set(void* net, const float* p, cudaStream_t s);
+cudaError_t mlp_features(const double* W, const double* D, const double* Acoef, const int32_t* N,
+                         const int32_t* ch_ptr, const int32_t* ch_row, const int32_t* ch_slot, int64_t n, int mv,
+                         float* F, cudaStream_t s);
+cudaError_t mlp_forward_f32(const void* net, const float* F, int64_t n, float* c, cudaStream_t s);
+cudaError_t mlp_forward_f64(const void* net, const float* F, int64_t n, double* c, cudaStream_t s);
+int mlp_backward_blocks(int64_t n);
+cudaError_t mlp_backward(const void* net, const float* F, const float* gc, int64_t n, float* partial, float* grad,
+                         cudaStream_t s);
+cudaError_t mlp_adam(void* net, const float* grad, float lr, cudaStream_t s);
+cudaError_t mlp_rademacher(uint64_t seed, int64_t n, double* z, cudaStream_t s);
+cudaError_t mlp_lp_grad(const int32_t* N, const double* Acoef, int64_t n, int mv, const double* sv, const double* u,
+                        const double* W, const double* corr, double coeff, float* gc, cudaStream_t s);
+cudaError_t mlp_zero(float* x, int64_t n, cudaStream_t s);
+const float* mlp_master(const void* net);
+
 // vif_knn.cu
 struct KnnParams {
   int64_t n;

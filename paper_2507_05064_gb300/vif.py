@@ -23,7 +23,8 @@ GAUSSIAN, BERNOULLI_LOGIT = 0, 1
 
 # every symbol include/vif.h declares
 EXPORTS = ["vif_build", "vif_nll", "vif_predict", "vif_laplace_mode", "vif_batch_create", "vif_batch_run",
-           "vif_batch_info", "vif_batch_destroy", "vif_set_neighbors", "vif_get_neighbors",
+           "vif_batch_info", "vif_batch_destroy", "vif_mlp_bytes", "vif_mlp_init", "vif_mlp_set_params",
+           "vif_mlp_get_params", "vif_mlp_forward", "vif_mlp_backward", "vif_mlp_features", "vif_mlp_train", "vif_set_neighbors", "vif_get_neighbors",
            "vif_get_factors", "vif_get_knn_stats", "vif_get_stage_times", "vif_nll_noalloc",
            "vif_last_error", "vif_destroy"]
 NOALLOC_SCRATCH_BYTES = 32 << 20
@@ -49,6 +50,17 @@ class LaplaceStats(C.Structure):
                 ("ms_pcg", C.c_double), ("ms_total", C.c_double), ("objective", C.c_double)]
 
 
+class MlpTrainOpts(C.Structure):
+    _fields_ = [("steps_per_system", C.c_int32), ("probes", C.c_int32), ("max_newton", C.c_int32),
+                ("lr", C.c_float), ("seed", C.c_uint64)]
+
+
+class MlpTrainStats(C.Structure):
+    _fields_ = [("systems", C.c_int32), ("loss_first", C.c_double), ("loss_last", C.c_double)]
+
+
+MLP_NIN, MLP_NH = 8, 64
+MLP_NPARAM = MLP_NH * MLP_NIN + MLP_NH + MLP_NH * MLP_NH + MLP_NH + MLP_NH + 1
 NSTAGES = 5
 STAGES = ["sigma_m_chol_inv", "lowrank_A", "vecchia_factor", "gram_FtF", "capacitance_nll"]
 
@@ -88,12 +100,22 @@ def lib() -> C.CDLL:
         L.vif_batch_info.argtypes = [vp, C.POINTER(i32), C.POINTER(i32), dp]
         L.vif_batch_destroy.argtypes = [vp]
         L.vif_batch_destroy.restype = None
+        L.vif_mlp_bytes.argtypes = []
+        L.vif_mlp_bytes.restype = C.c_size_t
+        L.vif_mlp_init.argtypes = [vp, C.c_uint64, vp]
+        L.vif_mlp_set_params.argtypes = [vp, vp, vp]
+        L.vif_mlp_get_params.argtypes = [vp, vp]
+        L.vif_mlp_forward.argtypes = [vp, vp, i64, vp, vp]
+        L.vif_mlp_backward.argtypes = [vp, vp, vp, i64, vp, vp]
+        L.vif_mlp_features.argtypes = [vp, vp, vp]
+        L.vif_mlp_train.argtypes = [vp, C.POINTER(VifCov), vp, C.POINTER(MlpTrainOpts), vp,
+                                    C.POINTER(MlpTrainStats)]
         L.vif_last_error.argtypes = [vp]
         L.vif_last_error.restype = C.c_char_p
         L.vif_destroy.argtypes = [vp]
         L.vif_destroy.restype = None
         for name in EXPORTS:
-            if name not in ("vif_last_error", "vif_destroy", "vif_batch_destroy"):
+            if name not in ("vif_last_error", "vif_destroy", "vif_batch_destroy", "vif_mlp_bytes"):
                 getattr(L, name).restype = C.c_int
         _lib = L
     return _lib
@@ -136,6 +158,45 @@ def nll_noalloc(X, Z, N, mv: int, theta, y, stream: int = 0) -> float:
     if st != VIF_OK:
         raise VifError(st, L.vif_last_error(None).decode())
     return out.value
+
+
+class Network:
+    """The learned correction's network in a device buffer (vif_mlp_*); needs torch."""
+
+    def __init__(self, seed: int = 0, params=None):
+        import torch
+        L = lib()
+        self.buf = torch.zeros(int(L.vif_mlp_bytes()), dtype=torch.uint8, device="cuda")
+        if params is None:
+            st = L.vif_mlp_init(_ptr(self.buf), int(seed), None)
+        else:
+            p = np.ascontiguousarray(params, dtype=np.float32)
+            st = L.vif_mlp_set_params(_ptr(self.buf), _ptr(p), None)
+        if st != VIF_OK:
+            raise VifError(st, "network initialisation failed")
+
+    def params(self) -> np.ndarray:
+        out = np.empty(MLP_NPARAM, dtype=np.float32)
+        if lib().vif_mlp_get_params(_ptr(self.buf), _ptr(out)) != VIF_OK:
+            raise VifError(VIF_ERR_CUDA, "reading the parameters failed")
+        return out
+
+    def forward(self, feats):
+        import torch
+        F = torch.as_tensor(np.ascontiguousarray(feats, dtype=np.float32)).cuda()
+        c = torch.empty(F.shape[0], dtype=torch.float32, device="cuda")
+        if lib().vif_mlp_forward(_ptr(self.buf), _ptr(F), F.shape[0], _ptr(c), None) != VIF_OK:
+            raise VifError(VIF_ERR_CUDA, "forward failed")
+        return c.cpu().numpy()
+
+    def backward(self, feats, gc):
+        import torch
+        F = torch.as_tensor(np.ascontiguousarray(feats, dtype=np.float32)).cuda()
+        g = torch.as_tensor(np.ascontiguousarray(gc, dtype=np.float32)).cuda()
+        out = torch.empty(MLP_NPARAM, dtype=torch.float32, device="cuda")
+        if lib().vif_mlp_backward(_ptr(self.buf), _ptr(F), _ptr(g), F.shape[0], _ptr(out), None) != VIF_OK:
+            raise VifError(VIF_ERR_CUDA, "backward failed")
+        return out.cpu().numpy()
 
 
 class Batch:
@@ -229,8 +290,8 @@ class Context:
                      mlp_weights=None, allow_not_converged=False):
         """Laplace mode for Bernoulli-logit responses y; returns (mode, stats dict)."""
         cv, ls = make_cov(theta)
-        opts = LaplaceOpts(float(rel_tol), int(max_pcg), int(max_newton), int(precond), 0,
-                           None if mlp_weights is None else _ptr(mlp_weights).value)
+        wp = None if mlp_weights is None else _ptr(getattr(mlp_weights, "buf", mlp_weights)).value
+        opts = LaplaceOpts(float(rel_tol), int(max_pcg), int(max_newton), int(precond), 0, wp)
         st = LaplaceStats()
         mode = np.empty(self.n)
         rc = lib().vif_laplace_mode(self.h, C.byref(cv), _ptr(_f64(y)), C.byref(opts), _ptr(mode), C.byref(st))
@@ -239,6 +300,19 @@ class Context:
         stats = {k: getattr(st, k) for k, _ in LaplaceStats._fields_}
         stats["status"] = rc
         return mode, stats
+
+    def mlp_features(self, W) -> np.ndarray:
+        F = np.empty((self.n, MLP_NIN), dtype=np.float32)
+        self._check(lib().vif_mlp_features(self.h, _ptr(_f64(W)), _ptr(F)))
+        return F
+
+    def mlp_train(self, theta, y, net, steps_per_system=10, probes=8, max_newton=4, lr=1e-3, seed=1):
+        cv, ls = make_cov(theta)
+        o = MlpTrainOpts(int(steps_per_system), int(probes), int(max_newton), float(lr), int(seed))
+        st = MlpTrainStats()
+        self._check(lib().vif_mlp_train(self.h, C.byref(cv), _ptr(_f64(y)), C.byref(o), _ptr(net.buf),
+                                        C.byref(st)))
+        return {"systems": st.systems, "loss_first": st.loss_first, "loss_last": st.loss_last}
 
     def neighbors(self) -> np.ndarray:
         N = np.empty((self.n, max(self.mv, 0)), dtype=np.int32)

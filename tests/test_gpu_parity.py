@@ -346,3 +346,59 @@ def test_batch_graph_replay_matches_single_problem_calls():
     B.close()
     for c in ctxs:
         c.close()
+
+
+# --------------------------------------------------------------------------- learned correction
+from oracle import mlp_oracle as MO
+
+
+def _f16(x):
+    return np.asarray(x, dtype=np.float16).astype(np.float64)
+
+
+def test_mlp_forward_and_backward_match_oracle():
+    rng = np.random.default_rng(11)
+    p = _f16(rng.normal(0, 0.3, MO.NPARAM))
+    net = V.Network(params=p.astype(np.float32))
+    F = rng.normal(0, 1, (3001, MO.NIN)).astype(np.float32).astype(np.float64)
+    np.testing.assert_allclose(net.forward(F), MO.forward(p, F), rtol=2e-5, atol=2e-5)
+    gc = rng.normal(0, 1, 3001).astype(np.float32).astype(np.float64)
+    g_gpu = net.backward(F, gc)
+    g_or = MO.backward(p, F, gc)
+    assert np.linalg.norm(g_gpu - g_or) <= 1e-4 * np.linalg.norm(g_or)
+    np.testing.assert_allclose(net.params(), p.astype(np.float32), rtol=0, atol=0)
+
+
+def test_mlp_features_match_oracle_and_untrained_network_is_plain_vifdu():
+    P = bern(1500, 30, 8, 51)
+    Nor = O.causal_neighbors(P.X, P.Z, P.theta, 8)
+    ctx = V.Context(P.X, P.Z, 8, P.theta, likelihood=V.BERNOULLI_LOGIT, neighbor_search=False)
+    ctx.set_neighbors(Nor.astype(np.int32))
+    b0, st0 = ctx.laplace_mode(P.theta, P.y, rel_tol=1e-6)
+    _, W = O.bern_grad_W(P.y, b0)
+    vif = O.VIF(P.X, P.Z, P.theta, Nor)
+    F_or = MO.features(W, vif.D, vif.Acoef, Nor, 8)
+    F_gpu = ctx.mlp_features(W)
+    np.testing.assert_allclose(F_gpu, F_or, rtol=1e-4, atol=1e-5)
+    net = V.Network(seed=3)                       # zero output layer: c = 0
+    b1, st1 = ctx.laplace_mode(P.theta, P.y, rel_tol=1e-6, precond=1, mlp_weights=net)
+    assert st1["pcg_iters_total"] == st0["pcg_iters_total"]
+    np.testing.assert_allclose(b1, b0, rtol=1e-12, atol=1e-12)
+    ctx.close()
+
+
+def test_training_lowers_the_preconditioner_loss():
+    P = bern(3000, 40, 10, 52, ls=0.05)
+    Nor = O.causal_neighbors(P.X, P.Z, P.theta, 10)
+    ctx = V.Context(P.X, P.Z, 10, P.theta, likelihood=V.BERNOULLI_LOGIT, neighbor_search=False)
+    ctx.set_neighbors(Nor.astype(np.int32))
+    net = V.Network(seed=4)
+    st = ctx.mlp_train(P.theta, P.y, net, steps_per_system=15, probes=4, max_newton=3, lr=3e-3)
+    assert st["systems"] == 3 and st["loss_last"] < st["loss_first"]
+    b, s_l = ctx.laplace_mode(P.theta, P.y, rel_tol=1e-6, precond=1, mlp_weights=net)
+    _, s_p = ctx.laplace_mode(P.theta, P.y, rel_tol=1e-6)
+    print("CG iterations plain", s_p["pcg_iters_total"], "learned", s_l["pcg_iters_total"], st)
+    g, _ = O.bern_grad_W(P.y, b)            # the learned preconditioner still reaches the mode
+    vif = O.VIF(P.X, P.Z, P.theta, Nor)
+    assert np.linalg.norm(g - vif.Sigma_dagger_inv(b)) <= 1e-5 * np.linalg.norm(g)
+    ctx.close()

@@ -273,3 +273,78 @@ def test_exact_gp_gradient_ard_matches_its_own_finite_differences():
         fp = O.dense_nll(O.exact_cov(P.X, O.theta_from_vector(P.theta, vp)), P.y)
         fm = O.dense_nll(O.exact_cov(P.X, O.theta_from_vector(P.theta, vm)), P.y)
         assert (fp - fm) / (2 * h) == pytest.approx(g[k], rel=1e-5, abs=1e-6)
+
+
+# --------------------------------------------------------------------------- learned correction (oracle side)
+from oracle import mlp_oracle as M
+
+
+def test_mlp_forward_closed_form_special_case():
+    p = np.zeros(M.NPARAM)
+    W1, b1, W2, b2, w3, b3 = M.unpack(p)      # views into p
+    W1[0, 0] = 1.0
+    W2[...] = np.eye(M.NH)
+    w3[0] = 2.0
+    F = np.array([[0.3, 5, 5, 5, 5, 5, 5, 5], [-1.2, 0, 0, 0, 0, 0, 0, 0]])
+    o = 2.0 * np.tanh(np.tanh(F[:, 0]))
+    np.testing.assert_allclose(M.forward(p, F), 4.0 * np.tanh(o / 4.0), rtol=1e-14)
+    assert np.all(M.forward(M.init_params(3), F) == 0.0)     # zero output layer: plain VIFDU
+
+
+def test_mlp_backward_matches_finite_differences():
+    rng = np.random.default_rng(5)
+    p = rng.normal(0, 0.3, M.NPARAM)
+    F = rng.normal(0, 1, (7, M.NIN))
+    gc = rng.normal(0, 1, 7)
+    g = M.backward(p, F, gc)
+    for k in rng.choice(M.NPARAM, 40, replace=False):
+        h = 1e-6
+        pp, pm = p.copy(), p.copy()
+        pp[k] += h
+        pm[k] -= h
+        fd = (gc @ M.forward(pp, F) - gc @ M.forward(pm, F)) / (2 * h)
+        assert fd == pytest.approx(g[k], rel=1e-6, abs=1e-9)
+
+
+def test_preconditioner_loss_gradient_formula_matches_dense_finite_differences():
+    """dL/dd_j = -2 (B P^-1 r)_j (B u)_j for L = ||P(d)^-1 A z - z||^2, P(d) = B^T diag(d) B + Sigma_dagger^-1."""
+    P = small_problem(n=70, m=8, mv=4, nugget=0.0, likelihood="bernoulli_logit")
+    N = O.causal_neighbors(P.X, P.Z, P.theta, 4)
+    vif = O.VIF(P.X, P.Z, P.theta, N)
+    rng = np.random.default_rng(7)
+    W = rng.uniform(0.05, 0.25, 70)
+    d = W * np.exp(rng.normal(0, 0.5, 70))
+    Sdi = np.column_stack([vif.Sigma_dagger_inv(e) for e in np.eye(70)])
+    A = np.diag(W) + Sdi
+    B = vif.B.toarray()
+    z = rng.choice([-1.0, 1.0], 70)
+
+    def loss(dd):
+        Pm = B.T @ np.diag(dd) @ B + Sdi
+        r = np.linalg.solve(Pm, A @ z) - z
+        return r @ r
+    Pm = B.T @ np.diag(d) @ B + Sdi
+    u = np.linalg.solve(Pm, A @ z)
+    r = u - z
+    g = -2.0 * (B @ np.linalg.solve(Pm, r)) * (B @ u)
+    for j in (0, 5, 33, 69):
+        h = 1e-4 * d[j]
+        dp, dm = d.copy(), d.copy()
+        dp[j] += h
+        dm[j] -= h
+        assert (loss(dp) - loss(dm)) / (2 * h) == pytest.approx(g[j], rel=1e-5, abs=1e-9)
+
+
+def test_features_hand_example():
+    # three points: 1 conditions on 0 (A=0.5), 2 conditions on 0 and 1 (A = 0.2, -0.4)
+    W = np.array([0.2, 0.1, 0.25])
+    D = np.array([1.0, 0.5, 0.25])
+    Ac = np.array([[0.0, 0.0], [0.5, 0.0], [0.2, -0.4]])
+    N = np.array([[-1, -1], [0, -1], [0, 1]])
+    F = M.features(W, D, Ac, N, 2)
+    assert F[0, 5] == pytest.approx(0.25 + 0.04)                  # A_1[0]^2 + A_2[0]^2
+    assert F[1, 5] == pytest.approx(0.16)
+    assert F[2, 4] == pytest.approx(0.04 + 0.16)
+    assert F[2, 6] == pytest.approx(np.log(0.15 / 0.25))            # mean W over {0, 1} / W_2
+    assert F[0, 7] == pytest.approx(np.log1p((0.1 * 0.25 + 0.25 * 0.04) / 0.2))
+    assert F[1, 3] == pytest.approx(0.5) and F[0, 3] == 0.0
