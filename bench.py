@@ -111,6 +111,17 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(self.rows)}
 
 
+def max_over_ranks(x: float, dist, device="cpu") -> float:
+    """Largest value over all ranks (the timing rule: max over ranks); identity
+    without a process group."""
+    if dist is None:
+        return float(x)
+    import torch
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
 def peaks():
     try:
         return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
@@ -180,13 +191,27 @@ def laplace_block(args, stream):
     y = torch.from_numpy(P.y).cuda()
     ctx.laplace_mode(P.theta, y, rel_tol=1e-6)          # warm-up
     t0 = time.perf_counter()
-    _, st = ctx.laplace_mode(P.theta, y, rel_tol=1e-6)
+    b_plain, st = ctx.laplace_mode(P.theta, y, rel_tol=1e-6)
     wall = time.perf_counter() - t0
+    out = {"workload": f"laplace-bernoulli-matern32-n{P.X.shape[0]}-d2-m{P.Z.shape[0]}-mv{P.mv}",
+           "rel_tol": 1e-6, "neighbor_build_s": build_s,
+           "plain": {"precond": "VIFDU", "newton_iters": st["newton_iters"],
+                     "pcg_iters_total": st["pcg_iters_total"], "ms_pcg": st["ms_pcg"],
+                     "ms_total_device": st["ms_total"], "wall_s": wall, "objective": st["objective"]}}
+    wpath = os.path.join(ROOT, "paper_2507_05064_gb300", "weights", "vifdu_mlp.npy")
+    if os.path.exists(wpath):
+        net = V.Network(params=np.load(wpath))
+        ctx.laplace_mode(P.theta, y, rel_tol=1e-6, precond=1, mlp_weights=net)     # warm-up
+        t0 = time.perf_counter()
+        b_l, sl = ctx.laplace_mode(P.theta, y, rel_tol=1e-6, precond=1, mlp_weights=net)
+        wall_l = time.perf_counter() - t0
+        out["learned"] = {"precond": "VIFDU + learned diagonal correction", "newton_iters": sl["newton_iters"],
+                          "pcg_iters_total": sl["pcg_iters_total"], "ms_pcg": sl["ms_pcg"],
+                          "ms_total_device": sl["ms_total"], "wall_s": wall_l, "objective": sl["objective"],
+                          "mode_rel_diff_vs_plain": float(np.linalg.norm(b_l - b_plain) / np.linalg.norm(b_plain))}
+        out["pcg_time_ratio_learned_over_plain"] = sl["ms_pcg"] / st["ms_pcg"]
     ctx.close()
-    return {"workload": f"laplace-bernoulli-matern32-n{P.X.shape[0]}-d2-m{P.Z.shape[0]}-mv{P.mv}",
-            "precond": "VIFDU", "rel_tol": 1e-6, "newton_iters": st["newton_iters"],
-            "pcg_iters_total": st["pcg_iters_total"], "ms_pcg": st["ms_pcg"], "ms_total_device": st["ms_total"],
-            "wall_s": wall, "neighbor_build_s": build_s, "objective": st["objective"]}
+    return out
 
 
 def run_reference(args, rank, world):
@@ -253,11 +278,7 @@ def run_vif(args, rank, world, dist):
     ev1.record(stream)
     barrier()
     clocks = clk.stop()
-    ms = ev0.elapsed_time(ev1) / args.steps
-    if dist is not None:
-        t = torch.tensor([ms], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
+    ms = max_over_ranks(ev0.elapsed_time(ev1) / args.steps, dist, dev)
     value = world * 1000.0 / ms
 
     # float64 GPU path on the same neighbour sets
@@ -282,11 +303,7 @@ def run_vif(args, rank, world, dist):
     for _ in range(args.steps):
         ctx.nll(th, y_host)
     torch.cuda.synchronize()
-    e2e_ms = (time.perf_counter() - t0) * 1000.0 / args.steps
-    if dist is not None:
-        t = torch.tensor([e2e_ms], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e2e_ms = float(t.item())
+    e2e_ms = max_over_ranks((time.perf_counter() - t0) * 1000.0 / args.steps, dist, dev)
 
     if rank != 0:
         return
