@@ -28,6 +28,7 @@ struct vif_ctx {
   int32_t* N = nullptr;                       // n x mv
   int32_t* order = nullptr;                   // processing order of the per-point kernels
   double *Sm = nullptr, *Linv = nullptr;      // m x ldm
+  double* trw = nullptr;                      // triangular-inverse workspace
   void* LinvT = nullptr;                      // mpad x mpad (float or double)
   void* A = nullptr;                          // n x mpad
   void* F = nullptr;                          // n x fpad
@@ -182,7 +183,7 @@ vif_status compute_lowrank(vif_ctx* ctx, const CovParams& cp, T* A, T* LinvT, co
   if (ctx->m > 0) {
     CK(build_sigma_m(ctx->Zs, ctx->m, ctx->d, cp, ctx->Sm, ctx->ldm, ctx->stream));
     CK(dense_cholesky(ctx->Sm, ctx->m, ctx->ldm, ctx->status, ST_NOTPD_SIGMAM, ctx->stream));
-    CK(dense_trtri_lower(ctx->Sm, ctx->Linv, ctx->m, ctx->ldm, ctx->stream));
+    CK(dense_trtri_lower(ctx->Sm, ctx->Linv, ctx->m, ctx->ldm, ctx->trw, ctx->stream));
     CK(linv_transpose<T>(ctx->Linv, ctx->m, ctx->ldm, LinvT, ctx->mpad, ctx->stream));
   }
   CK(lowrank_A<T>(Xs, Zs, LinvT, ctx->mpad, A, ctx->n, ctx->d, ctx->m, ctx->mpad, cp.kind, cp.var, ctx->stream));
@@ -196,7 +197,7 @@ vif_status compute_lowrank_parts(vif_ctx* ctx, const CovParams& cp, T* A, T* Lin
   if (ctx->m > 0) {
     CK(build_sigma_m(ctx->Zs, ctx->m, ctx->d, cp, ctx->Sm, ctx->ldm, ctx->stream));
     CK(dense_cholesky(ctx->Sm, ctx->m, ctx->ldm, ctx->status, ST_NOTPD_SIGMAM, ctx->stream));
-    CK(dense_trtri_lower(ctx->Sm, ctx->Linv, ctx->m, ctx->ldm, ctx->stream));
+    CK(dense_trtri_lower(ctx->Sm, ctx->Linv, ctx->m, ctx->ldm, ctx->trw, ctx->stream));
     CK(linv_transpose<T>(ctx->Linv, ctx->m, ctx->ldm, LinvT, ctx->mpad, ctx->stream));
   }
   if (ctx->timing) CK(cudaEventRecord(ctx->ev[1], ctx->stream));
@@ -251,7 +252,7 @@ vif_status read_status(vif_ctx* ctx, double* scal_out, int nscal) {
 
 void free_ctx(vif_ctx* c) {
   if (!c) return;
-  void* bufs[] = {c->X,    c->Z,     c->Xs, c->Zs,   c->Xs32, c->Zs32, c->hyp, c->N,   c->order, c->Sm,
+  void* bufs[] = {c->X,    c->Z,     c->Xs, c->Zs,   c->Xs32, c->Zs32, c->hyp, c->N,   c->order, c->Sm, c->trw,
                   c->Linv, c->LinvT, c->A,  c->F,    c->Acoef, c->Dv,  c->logD, c->part, c->G,
                   c->y,    c->red,   c->dscal, c->status};
   for (void* b : bufs)
@@ -436,7 +437,6 @@ vif_status fp64_buffers(vif_ctx* ctx, double** A64, double** F64, double** LT64)
   return VIF_OK;
 }
 
-// Learned diagonal correction c of the VIFDU preconditioner (filled in by the
 
 // Children lists of the neighbour DAG (the transpose of N, by column), for B^T.
 vif_status build_children(vif_ctx* ctx) {
@@ -576,6 +576,7 @@ vif_status vif_build(const double* X, int64_t n, int32_t d, const double* Z, int
   ALLOC(ctx->order, (size_t)n);
   ALLOC(ctx->Sm, (size_t)ctx->ldm * ctx->ldm);
   ALLOC(ctx->Linv, (size_t)ctx->ldm * ctx->ldm);
+  ALLOC(ctx->trw, trtri_work_doubles(m + 1));
   {
     unsigned char* p = nullptr;
     ALLOC(p, (size_t)ctx->mpad * ctx->mpad * esz);
@@ -754,7 +755,7 @@ vif_status vif_predict(vif_ctx* ctx, const vif_cov* theta, const double* y, cons
   CK(lowrank_A<double>(ctx->pXps, ctx->Zs, LT64, mpad, ctx->pAp, np, d, m, mpad, cp.kind, cp.var, ctx->stream));
   CK(predict_all(A64, ctx->Xs, n, ctx->pAp, ctx->pXps, np, d, m, mpad, mv, cp, ctx->y, ctx->G, fpad, ctx->pLinvC,
                  ctx->pw, ctx->pr, ctx->pcjj, ctx->pcpp, ctx->pNp, latent ? 1 : 0, theta->nugget, ctx->pmean,
-                 ctx->pvar, ctx->status, ctx->stream));
+                 ctx->pvar, ctx->status, ctx->trw, ctx->stream));
   double sc[1];
   CKS(read_status(ctx, sc, 1));
   ctx->have_factors = true;
@@ -780,7 +781,7 @@ vif_status lap_setup(vif_ctx* ctx, const vif_cov* theta, const double* y, LapOps
   CKS(upload(ctx, ctx->y, y, (size_t)ctx->n * sizeof(double)));
   CKS(apply_scaling(ctx, theta, false));
   CKS(run_pipeline<double>(ctx, cp, A64, LT64, F64, ctx->Xs, ctx->Zs));
-  if (ctx->m > 0) CK(dense_trtri_lower(ctx->G, ctx->l_LinvC, ctx->m, ctx->fpad, s));
+  if (ctx->m > 0) CK(dense_trtri_lower(ctx->G, ctx->l_LinvC, ctx->m, ctx->fpad, ctx->trw, s));
   double dummy[1];
   CKS(read_status(ctx, dummy, 0));
   o->n = ctx->n;
@@ -818,7 +819,7 @@ vif_status lap_c3(vif_ctx* ctx, const LapOps& o) {
   cudaStream_t s = ctx->stream;
   CK(gram_FtF<double>(o.F, ctx->n, ctx->fpad, ctx->m, ctx->part, ctx->nsplit, ctx->l_G3, ctx->fpad, s, ctx->l_om));
   CK(dense_cholesky(ctx->l_G3, ctx->m, ctx->fpad, ctx->status, ST_NOTPD_PRECOND, s));
-  CK(dense_trtri_lower(ctx->l_G3, ctx->l_LinvC3, ctx->m, ctx->fpad, s));
+  CK(dense_trtri_lower(ctx->l_G3, ctx->l_LinvC3, ctx->m, ctx->fpad, ctx->trw, s));
   return VIF_OK;
 }
 

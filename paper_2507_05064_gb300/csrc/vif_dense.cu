@@ -18,8 +18,10 @@ __device__ __forceinline__ double ld_lower(const double* A, int lda, int m, int 
   return (r == c) ? 1.0 : 0.0;
 }
 
-// In-shared-memory Cholesky of a 32 x 32 tile (lower triangle), all threads.
-__device__ void tile_potrf(double (*T)[NB + 1], int* status, int code, int base) {
+// In-shared-memory Cholesky of a 32 x 32 tile (lower triangle), all threads.  The
+// pivot's reciprocal is formed once per column (one float64 division) and the
+// column is scaled by multiplication; rinv[c] keeps 1/L_cc for the caller.
+__device__ void tile_potrf(double (*T)[NB + 1], double* rinv, int* status, int code, int base) {
   for (int c = 0; c < NB; ++c) {
     if (threadIdx.x == 0) {
       double p = T[c][c];
@@ -27,11 +29,13 @@ __device__ void tile_potrf(double (*T)[NB + 1], int* status, int code, int base)
         if (status) flag_status(status, code, base + c);
         p = nan("");
       }
-      T[c][c] = sqrt(p);
+      const double sp = sqrt(p);
+      T[c][c] = sp;
+      rinv[c] = 1.0 / sp;
     }
     __syncthreads();
-    double piv = T[c][c];
-    for (int r = c + 1 + threadIdx.x; r < NB; r += blockDim.x) T[r][c] /= piv;
+    const double ip = rinv[c];
+    for (int r = c + 1 + threadIdx.x; r < NB; r += blockDim.x) T[r][c] *= ip;
     __syncthreads();
     int w = NB - c - 1;
     for (int idx = threadIdx.x; idx < w * w; idx += blockDim.x) {
@@ -42,16 +46,42 @@ __device__ void tile_potrf(double (*T)[NB + 1], int* status, int code, int base)
   }
 }
 
+// Inverse of the lower-triangular tile L (in smem) into X (lower), one warp per
+// column block of lanes: column c of X solves L x = e_c.
+__device__ void tile_trtri(const double (*L)[NB + 1], const double* rinv, double (*X)[NB + 1]) {
+  if (threadIdx.x < NB) {
+    const int c = threadIdx.x;
+    for (int r = 0; r < NB; ++r) {
+      if (r < c) {
+        X[r][c] = 0.0;
+        continue;
+      }
+      double v = (r == c) ? 1.0 : 0.0;
+      double a0 = 0.0, a1 = 0.0;
+      int s2 = c;
+      for (; s2 + 1 < r; s2 += 2) {
+        a0 += L[r][s2] * X[s2][c];
+        a1 += L[r][s2 + 1] * X[s2 + 1][c];
+      }
+      if (s2 < r) a0 += L[r][s2] * X[s2][c];
+      X[r][c] = (v - a0 - a1) * rinv[r];
+    }
+  }
+  __syncthreads();
+}
+
 __global__ void chol_panel_kernel(double* A, int m, int lda, int k, int* status, int code) {
   __shared__ double Lk[NB][NB + 1];
+  __shared__ double Li[NB][NB + 1];
   __shared__ double Tt[NB][NB + 1];
+  __shared__ double rinv[NB];
   const int k0 = k * NB;
   for (int idx = threadIdx.x; idx < NB * NB; idx += blockDim.x) {
     int r = idx / NB, c = idx % NB;
     Lk[r][c] = (c <= r) ? ld_lower(A, lda, m, k0 + r, k0 + c) : 0.0;
   }
   __syncthreads();
-  tile_potrf(Lk, blockIdx.x == 0 ? status : nullptr, code, k0);
+  tile_potrf(Lk, rinv, blockIdx.x == 0 ? status : nullptr, code, k0);
   if (blockIdx.x == 0) {
     for (int idx = threadIdx.x; idx < NB * NB; idx += blockDim.x) {
       int r = idx / NB, c = idx % NB;
@@ -59,25 +89,24 @@ __global__ void chol_panel_kernel(double* A, int m, int lda, int k, int* status,
     }
     return;
   }
+  tile_trtri(Lk, rinv, Li);
   const int r0 = (k + blockIdx.x) * NB;
   for (int idx = threadIdx.x; idx < NB * NB; idx += blockDim.x) {
     int r = idx / NB, c = idx % NB;
     Tt[r][c] = ld_lower(A, lda, m, r0 + r, k0 + c);
   }
   __syncthreads();
-  // X L_kk^T = T, rows independent
-  if (threadIdx.x < NB) {
-    int r = threadIdx.x;
-    for (int c = 0; c < NB; ++c) {
-      double v = Tt[r][c];
-      for (int s2 = 0; s2 < c; ++s2) v -= Tt[r][s2] * Lk[c][s2];
-      Tt[r][c] = v / Lk[c][c];
-    }
-  }
-  __syncthreads();
+  // X = T L_kk^{-T}: independent dot products X[r][c] = sum_{s<=c} T[r][s] Linv[c][s]
   for (int idx = threadIdx.x; idx < NB * NB; idx += blockDim.x) {
     int r = idx / NB, c = idx % NB;
-    if (r0 + r < m && k0 + c < m) A[(size_t)(r0 + r) * lda + k0 + c] = Tt[r][c];
+    double a0 = 0.0, a1 = 0.0;
+    int s2 = 0;
+    for (; s2 + 1 <= c; s2 += 2) {
+      a0 += Tt[r][s2] * Li[c][s2];
+      a1 += Tt[r][s2 + 1] * Li[c][s2 + 1];
+    }
+    if (s2 <= c) a0 += Tt[r][s2] * Li[c][s2];
+    if (r0 + r < m && k0 + c < m) A[(size_t)(r0 + r) * lda + k0 + c] = a0 + a1;
   }
 }
 
@@ -117,7 +146,7 @@ cudaError_t dense_cholesky(double* A, int m, int lda, int* status, int code, cud
   if (m <= 0) return cudaSuccess;
   const int nt = (m + NB - 1) / NB;
   for (int k = 0; k < nt; ++k) {
-    chol_panel_kernel<<<nt - k, 128, 0, s>>>(A, m, lda, k, status, code);
+    chol_panel_kernel<<<nt - k, 256, 0, s>>>(A, m, lda, k, status, code);
     int T = nt - k - 1;
     if (T > 0) chol_update_kernel<<<T * (T + 1) / 2, 256, 0, s>>>(A, m, lda, k, T);
   }
@@ -126,85 +155,101 @@ cudaError_t dense_cholesky(double* A, int m, int lda, int* status, int code, cud
 
 // ---------------------------------------------------------------------------
 // Inverse of a lower-triangular L (blocked):  Linv_tt = L_tt^{-1};
-// Linv_ij = -Linv_ii * sum_{k=j}^{i-1} L_ik Linv_kj, one launch per block diagonal.
+// Linv_ij = -Linv_ii * sum_{k=j}^{i-1} L_ik Linv_kj, one block diagonal s = i - j at
+// a time.  Within a step every tile product L_ik Linv_kj is its own CTA and adds
+// into a per-(i,j) float64 tile with atomics, so a step costs two tile products of
+// latency instead of s + 1.
 // ---------------------------------------------------------------------------
 __global__ void trtri_diag_kernel(const double* L, double* Li, int m, int lda) {
   __shared__ double Lt[NB][NB + 1];
   __shared__ double X[NB][NB + 1];
+  __shared__ double rinv[NB];
   const int t0 = blockIdx.x * NB;
   for (int idx = threadIdx.x; idx < NB * NB; idx += blockDim.x) {
     int r = idx / NB, c = idx % NB;
     Lt[r][c] = (c <= r) ? ld_lower(L, lda, m, t0 + r, t0 + c) : 0.0;
   }
   __syncthreads();
-  if (threadIdx.x < NB) {
-    int c = threadIdx.x;  // column c of the inverse: L x = e_c
-    for (int r = 0; r < NB; ++r) {
-      double v = (r == c) ? 1.0 : 0.0;
-      if (r >= c) {
-        for (int s2 = c; s2 < r; ++s2) v -= Lt[r][s2] * X[s2][c];
-        X[r][c] = v / Lt[r][r];
-      } else {
-        X[r][c] = 0.0;
-      }
-    }
-  }
+  if (threadIdx.x < NB) rinv[threadIdx.x] = 1.0 / Lt[threadIdx.x][threadIdx.x];
   __syncthreads();
+  tile_trtri(Lt, rinv, X);
   for (int idx = threadIdx.x; idx < NB * NB; idx += blockDim.x) {
     int r = idx / NB, c = idx % NB;
     if (t0 + r < m && t0 + c < m) Li[(size_t)(t0 + r) * lda + t0 + c] = X[r][c];
   }
 }
 
-__global__ void trtri_off_kernel(const double* L, double* Li, int m, int lda, int sdiag) {
-  const int j = blockIdx.x, i = j + sdiag;
-  const int i0 = i * NB, j0 = j * NB;
+__device__ void tile_prod_acc(const double (*P)[NB + 1], const double (*Q)[NB + 1], double acc[2][2], int tx,
+                              int ty) {
+#pragma unroll 8
+  for (int c = 0; c < NB; ++c) {
+    double a0 = P[ty][c], a1 = P[ty + 16][c];
+    double b0 = Q[c][tx], b1 = Q[c][tx + 16];
+    acc[0][0] += a0 * b0;
+    acc[0][1] += a0 * b1;
+    acc[1][0] += a1 * b0;
+    acc[1][1] += a1 * b1;
+  }
+}
+
+// tmp[j] += L_{j+s,k} Linv_{k,j},  k = j + kk,  CTA b = j * s + kk
+__global__ void trtri_prod_kernel(const double* L, const double* Li, int m, int lda, int sdiag, double* tmp) {
+  const int j = blockIdx.x / sdiag, kk = blockIdx.x % sdiag;
+  const int i0 = (j + sdiag) * NB, j0 = j * NB, k0 = (j + kk) * NB;
   __shared__ double P[NB][NB + 1];
   __shared__ double Q[NB][NB + 1];
-  const int tx = threadIdx.x % 16, ty = threadIdx.x / 16;
-  double acc[2][2] = {{0, 0}, {0, 0}};
-  for (int kb = j; kb < i; ++kb) {
-    const int k0 = kb * NB;
-    __syncthreads();
-    for (int idx = threadIdx.x; idx < NB * NB; idx += blockDim.x) {
-      int r = idx / NB, c = idx % NB;
-      P[r][c] = (i0 + r < m && k0 + c < m) ? L[(size_t)(i0 + r) * lda + k0 + c] : 0.0;   // L_ik
-      Q[r][c] = (k0 + r < m && j0 + c < m) ? Li[(size_t)(k0 + r) * lda + j0 + c] : 0.0;  // Linv_kj
-    }
-    __syncthreads();
-#pragma unroll 8
-    for (int c = 0; c < NB; ++c) {
-      double a0 = P[ty][c], a1 = P[ty + 16][c];
-      double b0 = Q[c][tx], b1 = Q[c][tx + 16];
-      acc[0][0] += a0 * b0; acc[0][1] += a0 * b1;
-      acc[1][0] += a1 * b0; acc[1][1] += a1 * b1;
-    }
-  }
-  __syncthreads();
-  for (int u = 0; u < 2; ++u)
-    for (int v = 0; v < 2; ++v) Q[ty + 16 * u][tx + 16 * v] = acc[u][v];
   for (int idx = threadIdx.x; idx < NB * NB; idx += blockDim.x) {
     int r = idx / NB, c = idx % NB;
-    P[r][c] = (i0 + r < m && i0 + c < m) ? Li[(size_t)(i0 + r) * lda + i0 + c] : 0.0;  // Linv_ii
+    P[r][c] = (i0 + r < m && k0 + c < m) ? L[(size_t)(i0 + r) * lda + k0 + c] : 0.0;
+    Q[r][c] = (k0 + r < m && j0 + c < m) ? Li[(size_t)(k0 + r) * lda + j0 + c] : 0.0;
   }
   __syncthreads();
+  const int tx = threadIdx.x % 16, ty = threadIdx.x / 16;
+  double acc[2][2] = {{0, 0}, {0, 0}};
+  tile_prod_acc(P, Q, acc, tx, ty);
+  double* T = tmp + (size_t)j * NB * NB;
+  for (int u = 0; u < 2; ++u)
+    for (int v = 0; v < 2; ++v) atomicAdd(&T[(ty + 16 * u) * NB + tx + 16 * v], acc[u][v]);
+}
+
+// Linv_{j+s,j} = -Linv_{j+s,j+s} tmp[j]; tmp[j] is cleared for the next step.
+__global__ void trtri_fin_kernel(double* Li, int m, int lda, int sdiag, double* tmp) {
+  const int j = blockIdx.x, i0 = (j + sdiag) * NB, j0 = j * NB;
+  __shared__ double P[NB][NB + 1];
+  __shared__ double Q[NB][NB + 1];
+  double* T = tmp + (size_t)j * NB * NB;
+  for (int idx = threadIdx.x; idx < NB * NB; idx += blockDim.x) {
+    int r = idx / NB, c = idx % NB;
+    P[r][c] = (i0 + r < m && i0 + c < m) ? Li[(size_t)(i0 + r) * lda + i0 + c] : 0.0;
+    Q[r][c] = T[idx];
+  }
+  __syncthreads();
+  for (int idx = threadIdx.x; idx < NB * NB; idx += blockDim.x) T[idx] = 0.0;
+  const int tx = threadIdx.x % 16, ty = threadIdx.x / 16;
+  double acc[2][2] = {{0, 0}, {0, 0}};
+  tile_prod_acc(P, Q, acc, tx, ty);
   for (int u = 0; u < 2; ++u)
     for (int v = 0; v < 2; ++v) {
       int r = ty + 16 * u, c = tx + 16 * v;
-      double sacc = 0.0;
-      for (int k = 0; k <= r; ++k) sacc += P[r][k] * Q[k][c];
-      if (i0 + r < m && j0 + c < m) Li[(size_t)(i0 + r) * lda + j0 + c] = -sacc;
+      if (i0 + r < m && j0 + c < m) Li[(size_t)(i0 + r) * lda + j0 + c] = -acc[u][v];
     }
 }
 
-cudaError_t dense_trtri_lower(const double* L, double* Linv, int m, int lda, cudaStream_t s) {
+size_t trtri_work_doubles(int m) { return (size_t)((m + NB - 1) / NB) * NB * NB; }
+
+cudaError_t dense_trtri_lower(const double* L, double* Linv, int m, int lda, double* work, cudaStream_t s) {
   if (m <= 0) return cudaSuccess;
   const int nt = (m + NB - 1) / NB;
   // zero the strictly upper part so consumers may read full tiles
   cudaError_t e = cudaMemset2DAsync(Linv, lda * sizeof(double), 0, m * sizeof(double), m, s);
   if (e != cudaSuccess) return e;
+  e = cudaMemsetAsync(work, 0, trtri_work_doubles(m) * sizeof(double), s);
+  if (e != cudaSuccess) return e;
   trtri_diag_kernel<<<nt, 64, 0, s>>>(L, Linv, m, lda);
-  for (int sd = 1; sd < nt; ++sd) trtri_off_kernel<<<nt - sd, 256, 0, s>>>(L, Linv, m, lda, sd);
+  for (int sd = 1; sd < nt; ++sd) {
+    trtri_prod_kernel<<<(nt - sd) * sd, 256, 0, s>>>(L, Linv, m, lda, sd, work);
+    trtri_fin_kernel<<<nt - sd, 256, 0, s>>>(Linv, m, lda, sd, work);
+  }
   return cudaGetLastError();
 }
 

@@ -63,7 +63,9 @@ struct CovParams {
 // ---------------------------------------------------------------------------
 // vif_dense.cu: float64 dense m x m linear algebra for Sigma_m and capacitance matrices.
 cudaError_t dense_cholesky(double* A, int m, int lda, int* status, int code, cudaStream_t s);
-cudaError_t dense_trtri_lower(const double* L, double* Linv, int m, int lda, cudaStream_t s);
+// work: trtri_work_doubles(m) float64 scratch
+size_t trtri_work_doubles(int m);
+cudaError_t dense_trtri_lower(const double* L, double* Linv, int m, int lda, double* work, cudaStream_t s);
 cudaError_t reduce_sum(const double* x, int64_t n, double* partial, double* out, cudaStream_t s);
 
 // vif_lowrank.cu
@@ -97,7 +99,8 @@ cudaError_t nll_finish(const double* Lg, int ldg, int m, const double* logD_sum,
 cudaError_t predict_all(const double* A, const double* Xs, int64_t n, const double* Ap, const double* Xps,
                         int64_t np, int d, int m, int mpad, int mv, CovParams cp, const double* y, const double* Lg,
                         int ldg, double* LinvC, double* w, double* r, double* cjj, double* cpp, int32_t* Np,
-                        int latent, double nugget, double* mean, double* var, int* status, cudaStream_t s);
+                        int latent, double nugget, double* mean, double* var, int* status, double* trwork,
+                        cudaStream_t s);
 
 // vif_laplace.cu
 struct LapOps {

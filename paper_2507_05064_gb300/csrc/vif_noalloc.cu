@@ -66,7 +66,7 @@ struct Carve {
 };
 
 struct Layout {
-  double *hyp, *Xs, *Zs, *Sm, *Linv, *LinvT, *A, *F, *Acoef, *Dv, *logD, *part, *G, *red, *dscal;
+  double *hyp, *Xs, *Zs, *Sm, *Linv, *LinvT, *A, *F, *Acoef, *Dv, *logD, *part, *G, *red, *dscal, *trw;
   int* status;
   size_t bytes;
 };
@@ -90,6 +90,7 @@ Layout layout(uintptr_t base, int64_t n, int d, int m, int mv, int mpad, int fpa
   L.G = c.take<double>((size_t)(m + 1) * fpad);
   L.red = c.take<double>(256);
   L.dscal = c.take<double>(16);
+  L.trw = c.take<double>(trtri_work_doubles(m + 1));
   L.status = c.take<int>(16);
   L.bytes = c.off;
   return L;
@@ -156,7 +157,7 @@ extern "C" vif_status vif_nll_noalloc(const double* X, int64_t n, int32_t d, con
     NA_CK(scale_coords(Z, m, d, L.hyp, L.hyp + 16, L.Zs, nullptr, s));
     NA_CK(build_sigma_m(L.Zs, m, d, cp, L.Sm, mpad, s));
     NA_CK(dense_cholesky(L.Sm, m, mpad, L.status, ST_NOTPD_SIGMAM, s));
-    NA_CK(dense_trtri_lower(L.Sm, L.Linv, m, mpad, s));
+    NA_CK(dense_trtri_lower(L.Sm, L.Linv, m, mpad, L.trw, s));
     NA_CK(linv_transpose<double>(L.Linv, m, mpad, L.LinvT, mpad, s));
   }
   NA_CK(lowrank_A<double>(L.Xs, L.Zs, L.LinvT, mpad, L.A, n, d, m, mpad, cp.kind, cp.var, s));

@@ -278,7 +278,8 @@ __global__ __launch_bounds__(PK_WARPS * 32) void predict_kernel(
 cudaError_t predict_all(const double* A, const double* Xs, int64_t n, const double* Ap, const double* Xps,
                         int64_t np, int d, int m, int mpad, int mv, CovParams cp, const double* y, const double* Lg,
                         int ldg, double* LinvC, double* w, double* r, double* cjj, double* cpp, int32_t* Np,
-                        int latent, double nugget, double* mean, double* var, int* status, cudaStream_t s) {
+                        int latent, double nugget, double* mean, double* var, int* status, double* trwork,
+                        cudaStream_t s) {
   if (mv > PK_QM - 1 || d > 16) return cudaErrorInvalidValue;
   const double tau = 1e-6 * cp.var;
   resid_var64_kernel<<<(unsigned)((n + 7) / 8), 256, 0, s>>>(A, n, m, mpad, cp.var, cjj);
@@ -288,7 +289,7 @@ cudaError_t predict_all(const double* A, const double* Xs, int64_t n, const doub
                                                  Np);
   if (m > 0) {
     solve_w_kernel<<<1, 256, (size_t)m * sizeof(double), s>>>(Lg, ldg, m, w);
-    cudaError_t e = dense_trtri_lower(Lg, LinvC, m, ldg, s);
+    cudaError_t e = dense_trtri_lower(Lg, LinvC, m, ldg, trwork, s);
     if (e != cudaSuccess) return e;
   }
   resid_r_kernel<<<(unsigned)((n + 7) / 8), 256, 0, s>>>(A, w, y, n, m, mpad, r);

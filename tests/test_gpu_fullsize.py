@@ -1,0 +1,79 @@
+"""Parity at the full sizes of the benchmark workload (n = 500,000, d = 8, m = 500,
+m_v = 20, SE-ARD) and of the n = 100,000 Matern-5/2 workload, in the launch
+configuration bench.py times: sampled outputs the oracle can compute one by one
+(neighbour sets of sampled queries, factor rows of sampled points) and the full
+likelihood on a neighbour structure both sides receive from outside the CUDA path."""
+import numpy as np
+import pytest
+
+from oracle import vif_oracle as O
+from paper_2507_05064_gb300 import synth
+from paper_2507_05064_gb300 import vif as V
+
+pytestmark = pytest.mark.gpu
+TIE_TOL = 1e-9
+
+
+def preceding_neighbors(n, mv):
+    """A valid conditioning structure independent of both implementations:
+    N(i) = the min(i, m_v) immediately preceding points."""
+    N = -np.ones((n, mv), dtype=np.int64)
+    for q in range(1, mv + 1):
+        N[q, :q] = np.arange(q)
+    i = np.arange(mv + 1, n)
+    N[mv + 1:] = i[:, None] - mv + np.arange(mv)[None, :]
+    N[mv, :] = np.arange(mv)
+    return N
+
+
+def scale_close(got, ref, n, rtol):
+    return abs(got - ref) <= rtol * max(abs(ref), 0.5 * n * np.log(2 * np.pi))
+
+
+@pytest.fixture(scope="module", params=["c3", "c2"])
+def workload(request):
+    if request.param == "c3":
+        P = synth.config3()
+    else:
+        P = synth.config2(lloyd=3)
+    return request.param, P
+
+
+def test_sampled_neighbor_sets(workload):
+    name, P = workload
+    n = P.X.shape[0]
+    ctx = V.Context(P.X, P.Z, P.mv, P.theta, precision=V.MIXED)
+    N = ctx.neighbors()
+    rescored, fallback = ctx.knn_stats()
+    ctx.close()
+    rng = np.random.default_rng(123)
+    queries = np.concatenate([[P.mv, P.mv + 1, 1000], rng.integers(P.mv + 2, n, size=13)])
+    Ns, keys = O.causal_neighbors_sample(P.X, P.Z, P.theta, P.mv, queries)
+    swaps = 0
+    for a, i in enumerate(queries):
+        got = set(int(j) for j in N[i] if j >= 0)
+        exp = set(int(j) for j in Ns[a])
+        if got != exp:
+            k = keys[a]
+            assert np.max(np.abs(np.sort(k[list(got)]) - np.sort(k[list(exp)]))) <= TIE_TOL, (i, got ^ exp)
+            swaps += 1
+    assert swaps <= 1
+    assert fallback <= 0.01 * n
+
+
+def test_sampled_factor_rows_and_full_likelihood(workload):
+    name, P = workload
+    n = P.X.shape[0]
+    N = preceding_neighbors(n, P.mv)
+    rows = np.random.default_rng(7).integers(0, n, size=48)
+    A_or, D_or = O.vecchia_factors_rows(P.X, P.Z, P.theta, N, rows)
+    ref = O.vif_nll(P.X, P.Z, P.theta, N, P.y)
+    for prec, rtol_nll, rtol_f in [(V.FP64, 1e-8, 1e-9), (V.MIXED, 1e-5, 5e-3)]:
+        ctx = V.Context(P.X, P.Z, P.mv, P.theta, precision=prec, neighbor_search=False)
+        ctx.set_neighbors(N.astype(np.int32))
+        nll = ctx.nll(P.theta, P.y)
+        Ac, D = ctx.factors()
+        ctx.close()
+        assert scale_close(nll, ref, n, rtol_nll), (name, prec, nll, ref)
+        np.testing.assert_allclose(D[rows], D_or, rtol=rtol_f)
+        np.testing.assert_allclose(Ac[rows], A_or, rtol=rtol_f, atol=rtol_f * np.abs(A_or).max())
