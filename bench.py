@@ -145,12 +145,21 @@ def stage_algorithmic(P, stage):
 
 
 def launches_per_eval(m):
-    """Kernel launches of one vif_nll call (counted from the launch sites)."""
+    """Kernel launches of one vif_nll call (counted from the launch sites; 104 for
+    m = 500, as in the committed launch list)."""
     nt = (m + 31) // 32
     nt1 = (m + 1 + 31) // 32
     chol = lambda t: t + (t - 1)       # panel launches + trailing-update launches
-    return (2 + 1 + chol(nt) + nt + 1 + 1     # scaling x2, Sigma_m, Cholesky, trtri, L^-T, A
-            + 1 + 2 + 2 + chol(nt1) + 1)      # factor, Gram + reduce, logD sum, capacitance Cholesky, finish
+    trtri = lambda t: 1 + 2 * (t - 1)  # diagonal tiles, then product + finish per block diagonal
+    return (2 + 1 + chol(nt) + trtri(nt) + 1 + 1   # scaling x2, Sigma_m, Cholesky, inverse, L^-1 operand, A
+            + 1 + 2 + 2 + chol(nt1) + 1)          # factor, Gram + reduce, logD sum, capacitance Cholesky, finish
+
+
+# DRAM bytes per point of a kernel, from one ncu capture of the kernel as it stands
+# (dram__bytes_read.sum + dram__bytes_write.sum at n = 100,000; traffic grows with n).
+NCU_DRAM_BYTES_PER_POINT = {
+    "vecchia_factor": ((378.422784e6 + 203.539456e6) / 1e5, "profiles/factor_A_gram_kernels_n100k.md"),
+}
 
 
 def cpu_baseline(P, n_s, steps=1):
@@ -315,7 +324,10 @@ def run_vif(args, rank, world, dist):
     fp32_peak = 152 * 128 * 2 * sm_max * 1e6 / 1e12        # TFLOP/s, SIMT FP32 FMA at max clock
     achieved = flops / (med[dom] * 1e-3) / 1e12
     roof = {"kernel": dom, "bound": "alu", "achieved": achieved, "peak": fp32_peak, "unit": "TFLOP/s",
-            "frac": achieved / fp32_peak, "traffic": None,
+            "frac": achieved / fp32_peak,
+            "traffic": (NCU_DRAM_BYTES_PER_POINT[dom][0] * P.X.shape[0] if dom in NCU_DRAM_BYTES_PER_POINT else None),
+            "traffic_source": (NCU_DRAM_BYTES_PER_POINT[dom][1] + " (scaled by n)" if dom in NCU_DRAM_BYTES_PER_POINT
+                               else None),
             "peak_source": "152 SMs x 128 FP32 lanes x 2 flop x max SM clock (derived)",
             "algorithmic_flops_per_launch": flops, "algorithmic_bytes_per_launch": byts,
             "hbm_achieved_gbs": byts / (med[dom] * 1e-3) / 1e9,
