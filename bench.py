@@ -157,9 +157,7 @@ def launches_per_eval(m):
 
 # DRAM bytes per point of a kernel, from one ncu capture of the kernel as it stands
 # (dram__bytes_read.sum + dram__bytes_write.sum at n = 100,000; traffic grows with n).
-NCU_DRAM_BYTES_PER_POINT = {
-    "vecchia_factor": ((378.422784e6 + 203.539456e6) / 1e5, "profiles/factor_A_gram_kernels_n100k.md"),
-}
+NCU_DRAM_BYTES_PER_POINT = {}
 
 
 def cpu_baseline(P, n_s, steps=1):

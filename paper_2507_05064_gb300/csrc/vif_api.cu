@@ -177,6 +177,18 @@ vif_status apply_scaling(vif_ctx* ctx, const vif_cov* cv, bool want32) {
   return VIF_OK;
 }
 
+// A = K_nm L_m^{-T}: float64 on the SIMT kernel from L_m^{-T}; float32 on the tensor
+// cores from L_m^{-1} (the float32 LinvT buffer then holds the packed operand).
+template <typename T>
+cudaError_t lowrank_A_any(vif_ctx* ctx, const CovParams& cp, T* A, T* LinvT, const T* Xs, const T* Zs) {
+  if constexpr (sizeof(T) == 4)
+    return lowrank_A_tc(Xs, Zs, ctx->Linv, ctx->ldm, LinvT, A, ctx->n, ctx->d, ctx->m, ctx->mpad, cp.kind, cp.var,
+                        ctx->status, ctx->stream);
+  else
+    return lowrank_A<T>(Xs, Zs, LinvT, ctx->mpad, A, ctx->n, ctx->d, ctx->m, ctx->mpad, cp.kind, cp.var,
+                        ctx->stream);
+}
+
 // Sigma_m, its Cholesky factor and L_m^{-T} in precision T; then A.
 template <typename T>
 vif_status compute_lowrank(vif_ctx* ctx, const CovParams& cp, T* A, T* LinvT, const T* Xs, const T* Zs) {
@@ -184,9 +196,9 @@ vif_status compute_lowrank(vif_ctx* ctx, const CovParams& cp, T* A, T* LinvT, co
     CK(build_sigma_m(ctx->Zs, ctx->m, ctx->d, cp, ctx->Sm, ctx->ldm, ctx->stream));
     CK(dense_cholesky(ctx->Sm, ctx->m, ctx->ldm, ctx->status, ST_NOTPD_SIGMAM, ctx->stream));
     CK(dense_trtri_lower(ctx->Sm, ctx->Linv, ctx->m, ctx->ldm, ctx->trw, ctx->stream));
-    CK(linv_transpose<T>(ctx->Linv, ctx->m, ctx->ldm, LinvT, ctx->mpad, ctx->stream));
+    if constexpr (sizeof(T) == 8) CK(linv_transpose<T>(ctx->Linv, ctx->m, ctx->ldm, LinvT, ctx->mpad, ctx->stream));
   }
-  CK(lowrank_A<T>(Xs, Zs, LinvT, ctx->mpad, A, ctx->n, ctx->d, ctx->m, ctx->mpad, cp.kind, cp.var, ctx->stream));
+  CK(lowrank_A_any<T>(ctx, cp, A, LinvT, Xs, Zs));
   return VIF_OK;
 }
 
@@ -198,10 +210,10 @@ vif_status compute_lowrank_parts(vif_ctx* ctx, const CovParams& cp, T* A, T* Lin
     CK(build_sigma_m(ctx->Zs, ctx->m, ctx->d, cp, ctx->Sm, ctx->ldm, ctx->stream));
     CK(dense_cholesky(ctx->Sm, ctx->m, ctx->ldm, ctx->status, ST_NOTPD_SIGMAM, ctx->stream));
     CK(dense_trtri_lower(ctx->Sm, ctx->Linv, ctx->m, ctx->ldm, ctx->trw, ctx->stream));
-    CK(linv_transpose<T>(ctx->Linv, ctx->m, ctx->ldm, LinvT, ctx->mpad, ctx->stream));
+    if constexpr (sizeof(T) == 8) CK(linv_transpose<T>(ctx->Linv, ctx->m, ctx->ldm, LinvT, ctx->mpad, ctx->stream));
   }
   if (ctx->timing) CK(cudaEventRecord(ctx->ev[1], ctx->stream));
-  CK(lowrank_A<T>(Xs, Zs, LinvT, ctx->mpad, A, ctx->n, ctx->d, ctx->m, ctx->mpad, cp.kind, cp.var, ctx->stream));
+  CK(lowrank_A_any<T>(ctx, cp, A, LinvT, Xs, Zs));
   if (ctx->timing) CK(cudaEventRecord(ctx->ev[2], ctx->stream));
   return VIF_OK;
 }
@@ -218,7 +230,8 @@ vif_status run_pipeline(vif_ctx* ctx, const CovParams& cp, T* A, T* LinvT, T* F,
   CK(vecchia_factor<T>(A, Xs, ctx->N, ctx->order, ctx->y, ctx->n, ctx->d, ctx->m, ctx->mpad, ctx->mv, ctx->fpad,
                        cp, F, ctx->Acoef, ctx->Dv, ctx->logD, ctx->status, ctx->stream));
   MARK(3);
-  CK(gram_FtF<T>(F, ctx->n, ctx->fpad, ctx->m, ctx->part, ctx->nsplit, ctx->G, ctx->fpad, ctx->stream));
+  CK(gram_FtF<T>(F, ctx->n, ctx->fpad, ctx->m, ctx->part, ctx->nsplit, ctx->G, ctx->fpad, ctx->stream, nullptr,
+                 ctx->status));
   MARK(4);
   CK(reduce_sum(ctx->logD, ctx->n, ctx->red, ctx->dscal, ctx->stream));
   CK(dense_cholesky(ctx->G, ctx->m + 1, ctx->fpad, ctx->status, ST_NOTPD_CAP, ctx->stream));
@@ -556,6 +569,15 @@ vif_status vif_build(const double* X, int64_t n, int32_t d, const double* Z, int
       }
   const bool mixed = ctx->precision == VIF_MIXED;
   const size_t esz = mixed ? sizeof(float) : sizeof(double);
+  if (mixed) {
+    cudaError_t e = lowrank_A_tc_init();
+    if (e == cudaSuccess) e = gram_tc_init();
+    if (e != cudaSuccess) {
+      vif_internal_set_global_error(cudaGetErrorString(e));
+      free_ctx(ctx);
+      return VIF_ERR_CUDA;
+    }
+  }
 #define ALLOC(ptr, cnt)                                 \
   do {                                                  \
     if ((st = dalloc(ctx, &(ptr), (cnt))) != VIF_OK) { \
@@ -579,7 +601,9 @@ vif_status vif_build(const double* X, int64_t n, int32_t d, const double* Z, int
   ALLOC(ctx->trw, trtri_work_doubles(m + 1));
   {
     unsigned char* p = nullptr;
-    ALLOC(p, (size_t)ctx->mpad * ctx->mpad * esz);
+    size_t lt_bytes = (size_t)ctx->mpad * ctx->mpad * esz;
+    if (esz == 4) lt_bytes = std::max(lt_bytes, lowrank_A_tc_pack_floats(ctx->mpad) * sizeof(float));
+    ALLOC(p, lt_bytes);
     ctx->LinvT = p;
     p = nullptr;
     ALLOC(p, (size_t)n * ctx->mpad * esz);
@@ -1156,7 +1180,9 @@ vif_status enqueue_nll(vif_ctx* ctx, const vif_cov* th, const double* hyp_src, c
   int keep_split = ctx->nsplit;
   ctx->stream = s;
   ctx->timing = false;
-  ctx->nsplit = std::max(1, keep_split / split_div);
+  // the float64 Gram's row slices follow the tuned split; the float32 (tensor-core) Gram
+  // picks its own one-wave split, so a batched call sums its rows exactly as a single call
+  if constexpr (sizeof(T) == 8) ctx->nsplit = std::max(1, keep_split / split_div);
   vif_status st = VIF_OK;
   do {
     CovParams cp = cov_params(th);

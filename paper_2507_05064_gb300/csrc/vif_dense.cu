@@ -2,11 +2,14 @@
 // factor of Sigma_m (Sec. 2.1) and of the capacitance matrix C = L_m^{-1} M L_m^{-T}
 // (M of Eq. def_M, Sec. 2.2), and the inverse of the lower factor L_m.
 //
-// GB300 executes float64 at ~1/60 of its float32 rate (about 2 DFMA per clock per
-// SM), so a single-CTA factorisation of m = 500 would take ~10 ms.  The blocked
-// right-looking algorithm below spreads every step over many CTAs: one launch
-// factors the 32 x 32 diagonal tile (redundantly in every CTA) and solves the
-// tiles below it, the next updates the trailing tiles, one CTA per tile.
+// GB300 executes float64 at 1/64 of its float32 rate: a warp's float64 instruction
+// occupies its SM sub-partition for 64 cycles whether 1 or 32 lanes are active, a
+// square root ~680 cycles and a division ~430.  The blocked right-looking algorithm
+// below therefore keeps the serial chain short and spreads the rest over many SMs:
+// one launch factors the 32 x 32 diagonal tile (redundantly in every CTA) together
+// with the tile below it in one column sweep (pivots by a Newton-refined reciprocal
+// square root), the next updates the trailing tiles in k-slices (several CTAs per
+// tile, float64 atomics).
 #include "vif_internal.cuh"
 
 namespace vif {
@@ -18,118 +21,119 @@ __device__ __forceinline__ double ld_lower(const double* A, int lda, int m, int 
   return (r == c) ? 1.0 : 0.0;
 }
 
-// In-shared-memory Cholesky of a 32 x 32 tile (lower triangle), all threads.  The
-// pivot's reciprocal is formed once per column (one float64 division) and the
-// column is scaled by multiplication; rinv[c] keeps 1/L_cc for the caller.
-__device__ void tile_potrf(double (*T)[NB + 1], double* rinv, int* status, int code, int base) {
+// Inverse of the lower-triangular tile L (in smem) into X (lower): every column of X
+// solves L x = e_c; the sweep goes row by row (x_r = b_r / L_rr, then every later row
+// drops L[s][r] x_r), all 32 columns and all later rows at once.
+__device__ void tile_trtri(const double (*L)[NB + 1], const double* rinv, double (*X)[NB + 1]) {
+  for (int idx = threadIdx.x; idx < NB * NB; idx += blockDim.x) {
+    const int r = idx / NB, c = idx % NB;
+    X[r][c] = (r == c) ? 1.0 : 0.0;
+  }
+  __syncthreads();
+  for (int r = 0; r < NB; ++r) {
+    if (threadIdx.x <= r) X[r][threadIdx.x] *= rinv[r];   // columns c <= r
+    __syncthreads();
+    const int w = NB - r - 1;
+    for (int idx = threadIdx.x; idx < w * (r + 1); idx += blockDim.x) {
+      const int s2 = r + 1 + idx / (r + 1), c = idx % (r + 1);
+      X[s2][c] -= L[s2][r] * X[r][c];
+    }
+    __syncthreads();
+  }
+}
+
+// 1/sqrt(p) for p > 0: a float32 estimate refined by two Newton steps
+// y <- y (3 - p y^2) / 2 in float64 (quadratic convergence: ~1e-7 -> ~1e-14 -> rounding).
+// Each float64 instruction costs tens of cycles on this part, and this takes fewer of
+// them than a square root followed by a division.
+__device__ __forceinline__ double rsqrt_newton(double p) {
+  double y = (double)rsqrtf((float)p);
+  y = y * (1.5 - 0.5 * p * y * y);
+  y = y * (1.5 - 0.5 * p * y * y);
+  return y;
+}
+
+// Step k of the blocked Cholesky: CTA b factors the diagonal tile L_kk and, for b > 0,
+// the tile T_b below it (X L_kk^T = T_b) in the same column sweep over the stacked
+// 64 x 32 block [L_kk; T_b]: per column, one pivot (thread 0), one scaling and one
+// rank-1 update spread over the CTA.  CTA 0 writes L_kk, CTA b writes X.
+__global__ void chol_panel_kernel(double* A, int m, int lda, int k, int* status, int code) {
+  __shared__ double M[2 * NB][NB + 1];
+  __shared__ double rs_c;
+  const int k0 = k * NB;
+  const bool has_t = blockIdx.x > 0;
+  const int rows = has_t ? 2 * NB : NB;
+  const int r0 = (k + blockIdx.x) * NB;   // first row of T_b
+  for (int idx = threadIdx.x; idx < rows * NB; idx += blockDim.x) {
+    const int r = idx / NB, c = idx % NB;
+    M[r][c] = r < NB ? ((c <= r) ? ld_lower(A, lda, m, k0 + r, k0 + c) : 0.0)
+                     : ld_lower(A, lda, m, r0 + r - NB, k0 + c);
+  }
+  __syncthreads();
   for (int c = 0; c < NB; ++c) {
     if (threadIdx.x == 0) {
-      double p = T[c][c];
-      if (!(p > 0.0) || !isfinite(p)) {
-        if (status) flag_status(status, code, base + c);
+      double p = M[c][c];
+      if (!(p > 0.0)) {
+        if (blockIdx.x == 0 && status) flag_status(status, code, k0 + c);
         p = nan("");
       }
-      const double sp = sqrt(p);
-      T[c][c] = sp;
-      rinv[c] = 1.0 / sp;
+      const double y = rsqrt_newton(p);
+      M[c][c] = p * y;
+      rs_c = y;
     }
     __syncthreads();
-    const double ip = rinv[c];
-    for (int r = c + 1 + threadIdx.x; r < NB; r += blockDim.x) T[r][c] *= ip;
+    const double y = rs_c;
+    // column c below the pivot: rows c+1..NB-1 of L_kk and all rows of T_b
+    const int ncol = rows - (c + 1);
+    for (int t = threadIdx.x; t < ncol; t += blockDim.x) M[c + 1 + t][c] *= y;
     __syncthreads();
-    int w = NB - c - 1;
-    for (int idx = threadIdx.x; idx < w * w; idx += blockDim.x) {
-      int r = c + 1 + idx / w, s2 = c + 1 + idx % w;
-      if (s2 <= r) T[r][s2] -= T[r][c] * T[s2][c];
+    // rank-1 update of the trailing columns c+1..NB-1 (lower part of L_kk, all of T_b)
+    const int w = NB - c - 1;
+    for (int idx = threadIdx.x; idx < ncol * w; idx += blockDim.x) {
+      const int r = c + 1 + idx / w, s2 = c + 1 + idx % w;
+      if (r >= NB || s2 <= r) M[r][s2] -= M[r][c] * M[s2][c];
     }
     __syncthreads();
   }
-}
-
-// Inverse of the lower-triangular tile L (in smem) into X (lower), one warp per
-// column block of lanes: column c of X solves L x = e_c.
-__device__ void tile_trtri(const double (*L)[NB + 1], const double* rinv, double (*X)[NB + 1]) {
-  if (threadIdx.x < NB) {
-    const int c = threadIdx.x;
-    for (int r = 0; r < NB; ++r) {
-      if (r < c) {
-        X[r][c] = 0.0;
-        continue;
-      }
-      double v = (r == c) ? 1.0 : 0.0;
-      double a0 = 0.0, a1 = 0.0;
-      int s2 = c;
-      for (; s2 + 1 < r; s2 += 2) {
-        a0 += L[r][s2] * X[s2][c];
-        a1 += L[r][s2 + 1] * X[s2 + 1][c];
-      }
-      if (s2 < r) a0 += L[r][s2] * X[s2][c];
-      X[r][c] = (v - a0 - a1) * rinv[r];
-    }
-  }
-  __syncthreads();
-}
-
-__global__ void chol_panel_kernel(double* A, int m, int lda, int k, int* status, int code) {
-  __shared__ double Lk[NB][NB + 1];
-  __shared__ double Li[NB][NB + 1];
-  __shared__ double Tt[NB][NB + 1];
-  __shared__ double rinv[NB];
-  const int k0 = k * NB;
-  for (int idx = threadIdx.x; idx < NB * NB; idx += blockDim.x) {
-    int r = idx / NB, c = idx % NB;
-    Lk[r][c] = (c <= r) ? ld_lower(A, lda, m, k0 + r, k0 + c) : 0.0;
-  }
-  __syncthreads();
-  tile_potrf(Lk, rinv, blockIdx.x == 0 ? status : nullptr, code, k0);
-  if (blockIdx.x == 0) {
+  if (!has_t) {
     for (int idx = threadIdx.x; idx < NB * NB; idx += blockDim.x) {
-      int r = idx / NB, c = idx % NB;
-      if (k0 + r < m && k0 + c < m) A[(size_t)(k0 + r) * lda + k0 + c] = (c <= r) ? Lk[r][c] : 0.0;
+      const int r = idx / NB, c = idx % NB;
+      if (c <= r && k0 + r < m && k0 + c < m) A[(size_t)(k0 + r) * lda + k0 + c] = M[r][c];
     }
-    return;
-  }
-  tile_trtri(Lk, rinv, Li);
-  const int r0 = (k + blockIdx.x) * NB;
-  for (int idx = threadIdx.x; idx < NB * NB; idx += blockDim.x) {
-    int r = idx / NB, c = idx % NB;
-    Tt[r][c] = ld_lower(A, lda, m, r0 + r, k0 + c);
-  }
-  __syncthreads();
-  // X = T L_kk^{-T}: independent dot products X[r][c] = sum_{s<=c} T[r][s] Linv[c][s]
-  for (int idx = threadIdx.x; idx < NB * NB; idx += blockDim.x) {
-    int r = idx / NB, c = idx % NB;
-    double a0 = 0.0, a1 = 0.0;
-    int s2 = 0;
-    for (; s2 + 1 <= c; s2 += 2) {
-      a0 += Tt[r][s2] * Li[c][s2];
-      a1 += Tt[r][s2 + 1] * Li[c][s2 + 1];
+  } else {
+    for (int idx = threadIdx.x; idx < NB * NB; idx += blockDim.x) {
+      const int r = idx / NB, c = idx % NB;
+      if (r0 + r < m && k0 + c < m) A[(size_t)(r0 + r) * lda + k0 + c] = M[NB + r][c];
     }
-    if (s2 <= c) a0 += Tt[r][s2] * Li[c][s2];
-    if (r0 + r < m && k0 + c < m) A[(size_t)(r0 + r) * lda + k0 + c] = a0 + a1;
   }
 }
+
+// Trailing update A_ij -= L_ik L_jk^T of step k, split along k into KS slices: CTA
+// (tile, slice) multiplies 32 x 8 by 8 x 32 and adds with float64 atomics, so that a
+// step's latency is a quarter of a tile product (one CTA per SM holds the float64 pipe).
+constexpr int KS = 4;
+constexpr int KSW = NB / KS;
 
 __global__ void chol_update_kernel(double* A, int m, int lda, int k, int T) {
   // tile (i, j), k < j <= i < k+1+T, enumerated over the lower triangle
-  int b = blockIdx.x;
+  const int b = blockIdx.x / KS, ks = blockIdx.x % KS;
   int ii = (int)((sqrt(8.0 * b + 1.0) - 1.0) * 0.5);
   while ((ii + 1) * (ii + 2) / 2 <= b) ++ii;
   while (ii * (ii + 1) / 2 > b) --ii;
   int jj = b - ii * (ii + 1) / 2;
-  const int i0 = (k + 1 + ii) * NB, j0 = (k + 1 + jj) * NB, k0 = k * NB;
-  __shared__ double Li[NB][NB + 1];
-  __shared__ double Lj[NB][NB + 1];
-  for (int idx = threadIdx.x; idx < NB * NB; idx += blockDim.x) {
-    int r = idx / NB, c = idx % NB;
-    Li[r][c] = (i0 + r < m && k0 + c < m) ? A[(size_t)(i0 + r) * lda + k0 + c] : 0.0;
-    Lj[r][c] = (j0 + r < m && k0 + c < m) ? A[(size_t)(j0 + r) * lda + k0 + c] : 0.0;
+  const int i0 = (k + 1 + ii) * NB, j0 = (k + 1 + jj) * NB, c0 = k * NB + ks * KSW;
+  __shared__ double Li[NB][KSW + 1];
+  __shared__ double Lj[NB][KSW + 1];
+  for (int idx = threadIdx.x; idx < NB * KSW; idx += blockDim.x) {
+    int r = idx / KSW, c = idx % KSW;
+    Li[r][c] = (i0 + r < m && c0 + c < m) ? A[(size_t)(i0 + r) * lda + c0 + c] : 0.0;
+    Lj[r][c] = (j0 + r < m && c0 + c < m) ? A[(size_t)(j0 + r) * lda + c0 + c] : 0.0;
   }
   __syncthreads();
   const int tx = threadIdx.x % 16, ty = threadIdx.x / 16;
   double acc[2][2] = {{0, 0}, {0, 0}};
-#pragma unroll 8
-  for (int c = 0; c < NB; ++c) {
+#pragma unroll
+  for (int c = 0; c < KSW; ++c) {
     double a0 = Li[ty][c], a1 = Li[ty + 16][c];
     double b0 = Lj[tx][c], b1 = Lj[tx + 16][c];
     acc[0][0] += a0 * b0; acc[0][1] += a0 * b1;
@@ -138,7 +142,7 @@ __global__ void chol_update_kernel(double* A, int m, int lda, int k, int T) {
   for (int u = 0; u < 2; ++u)
     for (int v = 0; v < 2; ++v) {
       int r = i0 + ty + 16 * u, c = j0 + tx + 16 * v;
-      if (r < m && c < m && c <= r) A[(size_t)r * lda + c] -= acc[u][v];
+      if (r < m && c < m && c <= r) atomicAdd(&A[(size_t)r * lda + c], -acc[u][v]);
     }
 }
 
@@ -148,7 +152,7 @@ cudaError_t dense_cholesky(double* A, int m, int lda, int* status, int code, cud
   for (int k = 0; k < nt; ++k) {
     chol_panel_kernel<<<nt - k, 256, 0, s>>>(A, m, lda, k, status, code);
     int T = nt - k - 1;
-    if (T > 0) chol_update_kernel<<<T * (T + 1) / 2, 256, 0, s>>>(A, m, lda, k, T);
+    if (T > 0) chol_update_kernel<<<T * (T + 1) / 2 * KS, 256, 0, s>>>(A, m, lda, k, T);
   }
   return cudaGetLastError();
 }
@@ -156,9 +160,9 @@ cudaError_t dense_cholesky(double* A, int m, int lda, int* status, int code, cud
 // ---------------------------------------------------------------------------
 // Inverse of a lower-triangular L (blocked):  Linv_tt = L_tt^{-1};
 // Linv_ij = -Linv_ii * sum_{k=j}^{i-1} L_ik Linv_kj, one block diagonal s = i - j at
-// a time.  Within a step every tile product L_ik Linv_kj is its own CTA and adds
-// into a per-(i,j) float64 tile with atomics, so a step costs two tile products of
-// latency instead of s + 1.
+// a time.  Within a step every tile product L_ik Linv_kj is split into KS slices along
+// k, each its own CTA adding into a per-(i,j) float64 tile with atomics, so a step costs
+// two quarter tile products of latency instead of s + 1 whole ones.
 // ---------------------------------------------------------------------------
 __global__ void trtri_diag_kernel(const double* L, double* Li, int m, int lda) {
   __shared__ double Lt[NB][NB + 1];
@@ -179,10 +183,11 @@ __global__ void trtri_diag_kernel(const double* L, double* Li, int m, int lda) {
   }
 }
 
-__device__ void tile_prod_acc(const double (*P)[NB + 1], const double (*Q)[NB + 1], double acc[2][2], int tx,
-                              int ty) {
-#pragma unroll 8
-  for (int c = 0; c < NB; ++c) {
+// acc += P[rows][kk0..kk0+KSW) Q[kk0..kk0+KSW)[cols] for the 2 x 2 outputs of thread (tx, ty)
+__device__ void tile_prod_acc_k(const double (*P)[NB + 1], const double (*Q)[NB + 1], int kk0, double acc[2][2],
+                                int tx, int ty) {
+#pragma unroll
+  for (int c = kk0; c < kk0 + KSW; ++c) {
     double a0 = P[ty][c], a1 = P[ty + 16][c];
     double b0 = Q[c][tx], b1 = Q[c][tx + 16];
     acc[0][0] += a0 * b0;
@@ -192,46 +197,53 @@ __device__ void tile_prod_acc(const double (*P)[NB + 1], const double (*Q)[NB + 
   }
 }
 
-// tmp[j] += L_{j+s,k} Linv_{k,j},  k = j + kk,  CTA b = j * s + kk
+// tmp[j] += L_{j+s,k} Linv_{k,j},  k = j + kk; CTA b = (j * s + kk) * KS + slice
 __global__ void trtri_prod_kernel(const double* L, const double* Li, int m, int lda, int sdiag, double* tmp) {
-  const int j = blockIdx.x / sdiag, kk = blockIdx.x % sdiag;
+  const int pb = blockIdx.x / KS, ks = blockIdx.x % KS;
+  const int j = pb / sdiag, kk = pb % sdiag;
   const int i0 = (j + sdiag) * NB, j0 = j * NB, k0 = (j + kk) * NB;
   __shared__ double P[NB][NB + 1];
   __shared__ double Q[NB][NB + 1];
-  for (int idx = threadIdx.x; idx < NB * NB; idx += blockDim.x) {
-    int r = idx / NB, c = idx % NB;
+  const int kk0 = ks * KSW;
+  for (int idx = threadIdx.x; idx < NB * KSW; idx += blockDim.x) {
+    const int r = idx / KSW, c = kk0 + idx % KSW;        // P columns / Q rows of this slice
     P[r][c] = (i0 + r < m && k0 + c < m) ? L[(size_t)(i0 + r) * lda + k0 + c] : 0.0;
-    Q[r][c] = (k0 + r < m && j0 + c < m) ? Li[(size_t)(k0 + r) * lda + j0 + c] : 0.0;
+    const int qr = kk0 + idx / NB, qc = idx % NB;
+    Q[qr][qc] = (k0 + qr < m && j0 + qc < m) ? Li[(size_t)(k0 + qr) * lda + j0 + qc] : 0.0;
   }
   __syncthreads();
   const int tx = threadIdx.x % 16, ty = threadIdx.x / 16;
   double acc[2][2] = {{0, 0}, {0, 0}};
-  tile_prod_acc(P, Q, acc, tx, ty);
-  double* T = tmp + (size_t)j * NB * NB;
+  tile_prod_acc_k(P, Q, kk0, acc, tx, ty);
+  double* Tm = tmp + (size_t)j * NB * NB;
   for (int u = 0; u < 2; ++u)
-    for (int v = 0; v < 2; ++v) atomicAdd(&T[(ty + 16 * u) * NB + tx + 16 * v], acc[u][v]);
+    for (int v = 0; v < 2; ++v) atomicAdd(&Tm[(ty + 16 * u) * NB + tx + 16 * v], acc[u][v]);
 }
 
-// Linv_{j+s,j} = -Linv_{j+s,j+s} tmp[j]; tmp[j] is cleared for the next step.
+// Linv_{j+s,j} = -Linv_{j+s,j+s} tmp[j] (added over KS slices into the zeroed Linv);
+// each slice clears the rows of tmp[j] it read, for the next step.
 __global__ void trtri_fin_kernel(double* Li, int m, int lda, int sdiag, double* tmp) {
-  const int j = blockIdx.x, i0 = (j + sdiag) * NB, j0 = j * NB;
+  const int j = blockIdx.x / KS, ks = blockIdx.x % KS;
+  const int i0 = (j + sdiag) * NB, j0 = j * NB;
   __shared__ double P[NB][NB + 1];
   __shared__ double Q[NB][NB + 1];
-  double* T = tmp + (size_t)j * NB * NB;
-  for (int idx = threadIdx.x; idx < NB * NB; idx += blockDim.x) {
-    int r = idx / NB, c = idx % NB;
+  double* Tm = tmp + (size_t)j * NB * NB;
+  const int kk0 = ks * KSW;
+  for (int idx = threadIdx.x; idx < NB * KSW; idx += blockDim.x) {
+    const int r = idx / KSW, c = kk0 + idx % KSW;
     P[r][c] = (i0 + r < m && i0 + c < m) ? Li[(size_t)(i0 + r) * lda + i0 + c] : 0.0;
-    Q[r][c] = T[idx];
+    const int qr = kk0 + idx / NB, qc = idx % NB;
+    Q[qr][qc] = Tm[qr * NB + qc];
   }
   __syncthreads();
-  for (int idx = threadIdx.x; idx < NB * NB; idx += blockDim.x) T[idx] = 0.0;
+  for (int idx = threadIdx.x; idx < NB * KSW; idx += blockDim.x) Tm[(kk0 + idx / NB) * NB + idx % NB] = 0.0;
   const int tx = threadIdx.x % 16, ty = threadIdx.x / 16;
   double acc[2][2] = {{0, 0}, {0, 0}};
-  tile_prod_acc(P, Q, acc, tx, ty);
+  tile_prod_acc_k(P, Q, kk0, acc, tx, ty);
   for (int u = 0; u < 2; ++u)
     for (int v = 0; v < 2; ++v) {
       int r = ty + 16 * u, c = tx + 16 * v;
-      if (i0 + r < m && j0 + c < m) Li[(size_t)(i0 + r) * lda + j0 + c] = -acc[u][v];
+      if (i0 + r < m && j0 + c < m) atomicAdd(&Li[(size_t)(i0 + r) * lda + j0 + c], -acc[u][v]);
     }
 }
 
@@ -245,10 +257,10 @@ cudaError_t dense_trtri_lower(const double* L, double* Linv, int m, int lda, dou
   if (e != cudaSuccess) return e;
   e = cudaMemsetAsync(work, 0, trtri_work_doubles(m) * sizeof(double), s);
   if (e != cudaSuccess) return e;
-  trtri_diag_kernel<<<nt, 64, 0, s>>>(L, Linv, m, lda);
+  trtri_diag_kernel<<<nt, 256, 0, s>>>(L, Linv, m, lda);
   for (int sd = 1; sd < nt; ++sd) {
-    trtri_prod_kernel<<<(nt - sd) * sd, 256, 0, s>>>(L, Linv, m, lda, sd, work);
-    trtri_fin_kernel<<<nt - sd, 256, 0, s>>>(Linv, m, lda, sd, work);
+    trtri_prod_kernel<<<(nt - sd) * sd * KS, 256, 0, s>>>(L, Linv, m, lda, sd, work);
+    trtri_fin_kernel<<<(nt - sd) * KS, 256, 0, s>>>(Linv, m, lda, sd, work);
   }
   return cudaGetLastError();
 }

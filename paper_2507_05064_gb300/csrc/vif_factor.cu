@@ -19,6 +19,8 @@
 //     G' = [F z]^T [F z] + diag(1,...,1,0) = [[C, u], [u^T, z^T z]]:
 // its first m pivots give log det C and the square of its last pivot is
 // z^T z - u^T C^{-1} u.
+#include <algorithm>
+
 #include "vif_internal.cuh"
 
 namespace vif {
@@ -55,6 +57,19 @@ __device__ __forceinline__ void cp_async16(void* smem, const void* gmem) {
 __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::); }
 template <int N>
 __device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;\n" ::"n"(N)); }
+
+// 1/sqrt(p): the float32 hardware estimate plus one Newton step y <- y (3 - p y^2) / 2
+// (float), or two steps in float64 (double); a division-free pivot for the warp Cholesky.
+__device__ __forceinline__ float rsqrt_refined(float p) {
+  const float y = rsqrtf(p);
+  return y * fmaf(-0.5f * p * y, y, 1.5f);
+}
+__device__ __forceinline__ double rsqrt_refined(double p) {
+  double y = (double)rsqrtf((float)p);
+  y = y * (1.5 - 0.5 * p * y * y);
+  y = y * (1.5 - 0.5 * p * y * y);
+  return y;
+}
 
 template <typename T, int R>
 struct FactorSmem {
@@ -167,35 +182,87 @@ __global__ __launch_bounds__(FK_WARPS * 32) void factor_kernel(
     S.G[a][b2] = kv - S.G[a][b2];
   }
   __syncwarp();
-  // ---- Cholesky of R (lower, in place)
-  for (int c = 0; c < Q; ++c) {
-    T piv = S.G[c][c];
-    if (!(piv > T(0))) {
-      if (lane == 0) flag_status(status, ST_NOTPD_FACTOR, i);
-      piv = T(NAN);
+  T inv;   // 1 / sqrt(D_i)
+  if constexpr (QM <= 32) {
+    // ---- Cholesky of R in registers: lane r holds row r, columns broadcast by
+    // shuffles; rows Q..QM-1 are identity so the unrolled sweep leaves them alone
+    T row[QM];
+#pragma unroll
+    for (int c = 0; c < QM; ++c) {
+      T v = (lane < Q && c <= lane) ? S.G[lane < QM ? lane : 0][c] : T(0);
+      if (c == lane && lane >= Q) v = T(1);
+      row[c] = v;
     }
-    T sp = dsqrt(piv);
-    __syncwarp();
-    if (lane == 0) S.G[c][c] = sp;
-    for (int r = c + 1 + lane; r < Q; r += 32) S.G[r][c] /= sp;
-    __syncwarp();
-    for (int r = c + 1 + lane; r < Q; r += 32) {
-      T grc = S.G[r][c];
-      for (int s2 = c + 1; s2 <= r; ++s2) S.G[r][s2] -= grc * S.G[s2][c];
+    bool notpd = false;
+    T my_rs = T(1);   // 1 / L[lane][lane]
+#pragma unroll
+    for (int c = 0; c < QM; ++c) {
+      T piv = __shfl_sync(0xffffffffu, row[c], c);
+      if (!(piv > T(0))) {
+        notpd = true;
+        piv = T(NAN);
+      }
+      const T rs = rsqrt_refined(piv);
+      const T lc = (lane == c) ? piv * rs : row[c] * rs;
+      if (lane == c) my_rs = rs;
+      row[c] = lc;
+#pragma unroll
+      for (int s2 = c + 1; s2 < QM; ++s2) {
+        const T ls = __shfl_sync(0xffffffffu, lc, s2);
+        if (lane >= s2) row[s2] = fma(-lc, ls, row[s2]);
+      }
+    }
+    if (notpd && lane == 0) flag_status(status, ST_NOTPD_FACTOR, i);
+    if (lane < Q) {
+#pragma unroll
+      for (int c = 0; c < QM; ++c)
+        if (c <= lane) S.G[lane][c] = row[c];
     }
     __syncwarp();
+    // ---- A_i: L_NN^T x = l (l = row q of the factor), column-oriented: once x_k
+    // is known every t < k drops L[k][t] x_k from its right-hand side
+    T b = (lane < q) ? S.G[q][lane] : T(0);
+    T xk = T(0);
+    for (int k = q - 1; k >= 0; --k) {
+      const T x = __shfl_sync(0xffffffffu, b * my_rs, k);
+      if (lane == k) xk = x;
+      if (lane < k) b = fma(-S.G[k][lane], x, b);
+    }
+    if (lane < q) S.coef[lane] = xk;
+    inv = __shfl_sync(0xffffffffu, my_rs, q);
+    __syncwarp();
+  } else {
+    // ---- Cholesky of R (lower, in place)
+    for (int c = 0; c < Q; ++c) {
+      T piv = S.G[c][c];
+      if (!(piv > T(0))) {
+        if (lane == 0) flag_status(status, ST_NOTPD_FACTOR, i);
+        piv = T(NAN);
+      }
+      T sp = dsqrt(piv);
+      __syncwarp();
+      if (lane == 0) S.G[c][c] = sp;
+      for (int r = c + 1 + lane; r < Q; r += 32) S.G[r][c] /= sp;
+      __syncwarp();
+      for (int r = c + 1 + lane; r < Q; r += 32) {
+        T grc = S.G[r][c];
+        for (int s2 = c + 1; s2 <= r; ++s2) S.G[r][s2] -= grc * S.G[s2][c];
+      }
+      __syncwarp();
+    }
+    // ---- A_i: back substitution L_NN^T x = l, l = row q of the factor
+    for (int t = lane; t < q; t += 32) S.coef[t] = S.G[q][t];
+    __syncwarp();
+    for (int k = q - 1; k >= 0; --k) {
+      T x = S.coef[k] / S.G[k][k];
+      __syncwarp();
+      if (lane == 0) S.coef[k] = x;
+      for (int t = lane; t < k; t += 32) S.coef[t] -= S.G[k][t] * x;
+      __syncwarp();
+    }
+    inv = T(1) / S.G[q][q];
   }
   const T lii = S.G[q][q];
-  // ---- A_i: back substitution L_NN^T x = l, l = row q of the factor
-  for (int t = lane; t < q; t += 32) S.coef[t] = S.G[q][t];
-  __syncwarp();
-  for (int k = q - 1; k >= 0; --k) {
-    T x = S.coef[k] / S.G[k][k];
-    __syncwarp();
-    if (lane == 0) S.coef[k] = x;
-    for (int t = lane; t < k; t += 32) S.coef[t] -= S.G[k][t] * x;
-    __syncwarp();
-  }
   const double Dd = (double)lii * (double)lii;
   for (int t = lane; t < mv; t += 32) Acoef[(size_t)i * mv + t] = (t < q) ? (double)S.coef[t] : 0.0;
   if (lane == 0) {
@@ -203,7 +270,6 @@ __global__ __launch_bounds__(FK_WARPS * 32) void factor_kernel(
     logD[i] = log(Dd);
   }
   // ---- row of [F z]: 16-byte vectors along k
-  const T inv = T(1) / lii;
   for (int k = lane * V; k < fpad; k += 32 * V) {
     T out[V];
     if (k < mpad) {
@@ -211,11 +277,24 @@ __global__ __launch_bounds__(FK_WARPS * 32) void factor_kernel(
       vget(*reinterpret_cast<const VT*>(A + (size_t)i * mpad + k), a);
 #pragma unroll
       for (int e = 0; e < V; ++e) out[e] = a[e];
-      for (int t = 0; t < q; ++t) {
-        const T ct = S.coef[t];
-        vget(*reinterpret_cast<const VT*>(A + (size_t)S.idx[t] * mpad + k), a);
+      if constexpr (QM <= 28) {
+        // unrolled so that every neighbour row is requested before the first is used
 #pragma unroll
-        for (int e = 0; e < V; ++e) out[e] -= ct * a[e];
+        for (int t = 0; t < QM - 1; ++t) {
+          if (t < q) {
+            const T ct = S.coef[t];
+            vget(*reinterpret_cast<const VT*>(A + (size_t)S.idx[t] * mpad + k), a);
+#pragma unroll
+            for (int e = 0; e < V; ++e) out[e] -= ct * a[e];
+          }
+        }
+      } else {
+        for (int t = 0; t < q; ++t) {
+          const T ct = S.coef[t];
+          vget(*reinterpret_cast<const VT*>(A + (size_t)S.idx[t] * mpad + k), a);
+#pragma unroll
+          for (int e = 0; e < V; ++e) out[e] -= ct * a[e];
+        }
       }
 #pragma unroll
       for (int e = 0; e < V; ++e) out[e] *= inv;
@@ -346,114 +425,6 @@ __global__ __launch_bounds__(256) void gram_kernel(const T* __restrict__ F, int6
     for (int v = 0; v < 4; ++v) out[(ty * 4 + u) * GT + tx * 4 + v] = dacc[u][v] + (double)acc[u][v];
 }
 
-// float32 Gram, 128 x 128 tile pairs: 256 threads, each an 8 x 8 block made of
-// rows {ty*4..ty*4+3, 64+ty*4..} and columns {tx*4.., 64+tx*4..} so that every
-// operand read is a 16-byte shared-memory vector.  Rows of F are staged 16 at a
-// time, double-buffered through registers.
-//
-// C = I + F^T F is ill-conditioned (its largest eigenvalue grows with n), so the
-// Gram entries must be accurate relative to that eigenvalue: float32 sums run
-// over at most 256 rows and are then added into a float64 copy of the tile held
-// in shared memory.
-constexpr int GT2 = 128;
-constexpr int GR2 = 16;
-constexpr int GD_LD = GT2 + 2;   // float64 tile row stride
-
-__global__ __launch_bounds__(256) void gram_kernel_f32(const float* __restrict__ F, int64_t n, int fpad,
-                                                       double* part, int nsplit) {
-  extern __shared__ __align__(16) double Dacc[];   // [GT2][GD_LD]
-  const int p = blockIdx.x;
-  int ti = (int)((sqrtf(8.0f * p + 1.0f) - 1.0f) * 0.5f);
-  while ((ti + 1) * (ti + 2) / 2 <= p) ++ti;
-  while (ti * (ti + 1) / 2 > p) --ti;
-  const int tj = p - ti * (ti + 1) / 2;
-  const int sidx = blockIdx.y;
-  const int64_t chunk = (((n + nsplit - 1) / nsplit) + GR2 - 1) / GR2 * GR2;
-  const int64_t r0 = (int64_t)sidx * chunk;
-  const int64_t r1 = (n < r0 + chunk) ? n : r0 + chunk;
-  __shared__ __align__(16) float Fi[2][GR2][GT2];
-  __shared__ __align__(16) float Fj[2][GR2][GT2];
-  const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
-  // loader: rows lr and lr+8 of the slab, one float4 of each operand per row
-  const int lr = tid >> 5, lc = (tid & 31) * 4;
-  const int ci = ti * GT2 + lc, cj = tj * GT2 + lc;
-  auto rowof = [&](int u) { return u < 4 ? ty * 4 + u : 64 + ty * 4 + (u - 4); };
-  auto colof = [&](int v) { return v < 4 ? tx * 4 + v : 64 + tx * 4 + (v - 4); };
-  float acc[8][8];
-#pragma unroll
-  for (int u = 0; u < 8; ++u)
-#pragma unroll
-    for (int v = 0; v < 8; ++v) {
-      acc[u][v] = 0.f;
-      Dacc[rowof(u) * GD_LD + colof(v)] = 0.0;
-    }
-  auto gload = [&](int64_t r, int col) -> float4 {
-    if (r < r1 && col < fpad) return *reinterpret_cast<const float4*>(F + (size_t)r * fpad + col);
-    return make_float4(0.f, 0.f, 0.f, 0.f);
-  };
-  float4 ni0 = make_float4(0.f, 0.f, 0.f, 0.f), ni1 = ni0, nj0 = ni0, nj1 = ni0;
-  if (r0 < r1) {
-    ni0 = gload(r0 + lr, ci);
-    ni1 = gload(r0 + lr + 8, ci);
-    nj0 = gload(r0 + lr, cj);
-    nj1 = gload(r0 + lr + 8, cj);
-  }
-  int buf = 0, flush = 0;
-  for (int64_t r = r0; r < r1; r += GR2) {
-    *reinterpret_cast<float4*>(&Fi[buf][lr][lc]) = ni0;
-    *reinterpret_cast<float4*>(&Fi[buf][lr + 8][lc]) = ni1;
-    *reinterpret_cast<float4*>(&Fj[buf][lr][lc]) = nj0;
-    *reinterpret_cast<float4*>(&Fj[buf][lr + 8][lc]) = nj1;
-    __syncthreads();
-    if (r + GR2 < r1) {
-      ni0 = gload(r + GR2 + lr, ci);
-      ni1 = gload(r + GR2 + lr + 8, ci);
-      nj0 = gload(r + GR2 + lr, cj);
-      nj1 = gload(r + GR2 + lr + 8, cj);
-    }
-#pragma unroll 4
-    for (int rr = 0; rr < GR2; ++rr) {
-      float a[8], b[8];
-      float4 a0 = *reinterpret_cast<const float4*>(&Fi[buf][rr][ty * 4]);
-      float4 a1 = *reinterpret_cast<const float4*>(&Fi[buf][rr][64 + ty * 4]);
-      float4 b0 = *reinterpret_cast<const float4*>(&Fj[buf][rr][tx * 4]);
-      float4 b1 = *reinterpret_cast<const float4*>(&Fj[buf][rr][64 + tx * 4]);
-      a[0] = a0.x; a[1] = a0.y; a[2] = a0.z; a[3] = a0.w; a[4] = a1.x; a[5] = a1.y; a[6] = a1.z; a[7] = a1.w;
-      b[0] = b0.x; b[1] = b0.y; b[2] = b0.z; b[3] = b0.w; b[4] = b1.x; b[5] = b1.y; b[6] = b1.z; b[7] = b1.w;
-#pragma unroll
-      for (int u = 0; u < 8; ++u)
-#pragma unroll
-        for (int v = 0; v < 8; ++v) acc[u][v] += a[u] * b[v];
-    }
-    buf ^= 1;
-    if (++flush == 256 / GR2) {
-      flush = 0;
-#pragma unroll
-      for (int u = 0; u < 8; ++u)
-#pragma unroll
-        for (int v = 0; v < 8; ++v) {
-          Dacc[rowof(u) * GD_LD + colof(v)] += (double)acc[u][v];
-          acc[u][v] = 0.f;
-        }
-    }
-  }
-  // write the 128 x 128 partial as 64 x 64 sub-tiles in the pair layout of the
-  // float64 kernel, so one reduction serves both precisions
-  const int np64 = (fpad / GT) * (fpad / GT + 1) / 2;
-#pragma unroll
-  for (int u = 0; u < 8; ++u)
-#pragma unroll
-    for (int v = 0; v < 8; ++v) {
-      const int row = ti * GT2 + rowof(u);
-      const int col = tj * GT2 + colof(v);
-      if (row >= fpad || col >= fpad || col > row) continue;
-      const int a64 = row / GT, b64 = col / GT;
-      const int p64 = a64 * (a64 + 1) / 2 + b64;
-      part[((size_t)sidx * np64 + p64) * GT * GT + (size_t)(row % GT) * GT + (col % GT)] =
-          Dacc[rowof(u) * GD_LD + colof(v)] + (double)acc[u][v];
-    }
-}
-
 __global__ void gram_reduce_kernel(const double* part, int nsplit, int npairs, int m, double* G, int ldg) {
   const int M1 = m + 1;
   int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -470,8 +441,9 @@ __global__ void gram_reduce_kernel(const double* part, int nsplit, int npairs, i
 }
 
 int gram_nsplit(int64_t n, int fpad) {
-  // about four CTAs per SM for the 128-wide float32 tiles
-  int nt = (fpad + GT2 - 1) / GT2;
+  // row slices of the Gram: about four CTAs per SM counted in 128-wide tile pairs; the
+  // float32 tensor-core Gram uses at most this many, the float64 one exactly this many
+  int nt = (fpad + 127) / 128;
   int npairs = nt * (nt + 1) / 2;
   int64_t want = (4 * 152 + npairs - 1) / npairs;
   int64_t maxs = (n + 255) / 256;
@@ -481,16 +453,16 @@ int gram_nsplit(int64_t n, int fpad) {
 
 template <typename T>
 cudaError_t gram_FtF(const T* F, int64_t n, int fpad, int m, double* part, int nsplit, double* G, int ldg,
-                     cudaStream_t s, const double* wrow) {
+                     cudaStream_t s, const double* wrow, int* status) {
   int nt = fpad / GT;
   int npairs = nt * (nt + 1) / 2;
   if (sizeof(T) == 4 && wrow) return cudaErrorInvalidValue;   // row weights: float64 path only
   if constexpr (sizeof(T) == 4) {
-    int nt2 = (fpad + GT2 - 1) / GT2;
-    const int smem = GT2 * GD_LD * (int)sizeof(double);
-    cudaError_t e = cudaFuncSetAttribute(gram_kernel_f32, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    // tensor cores; one wave of slices, never more than the partial buffer holds
+    const int nst = std::min(nsplit, gram_tc_nsplit(n, fpad));
+    cudaError_t e = gram_tc(F, n, fpad, part, nst, status, s);
     if (e != cudaSuccess) return e;
-    gram_kernel_f32<<<dim3(nt2 * (nt2 + 1) / 2, nsplit), 256, smem, s>>>(F, n, fpad, part, nsplit);
+    nsplit = nst;
   } else {
     gram_kernel<T><<<dim3(npairs, nsplit), 256, 0, s>>>(F, n, fpad, part, nsplit, wrow);
   }
@@ -499,9 +471,9 @@ cudaError_t gram_FtF(const T* F, int64_t n, int fpad, int m, double* part, int n
   return cudaGetLastError();
 }
 template cudaError_t gram_FtF<float>(const float*, int64_t, int, int, double*, int, double*, int, cudaStream_t,
-                                     const double*);
+                                     const double*, int*);
 template cudaError_t gram_FtF<double>(const double*, int64_t, int, int, double*, int, double*, int, cudaStream_t,
-                                      const double*);
+                                      const double*, int*);
 
 // NLL = 1/2 [ n log 2pi + sum_{k<m} 2 log L'_kk + sum_i log D_i + L'_mm^2 ],  L' = chol(G').
 __global__ void nll_finish_kernel(const double* Lg, int ldg, int m, const double* logD_sum, int64_t n,

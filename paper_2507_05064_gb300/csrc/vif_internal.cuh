@@ -68,6 +68,14 @@ size_t trtri_work_doubles(int m);
 cudaError_t dense_trtri_lower(const double* L, double* Linv, int m, int lda, double* work, cudaStream_t s);
 cudaError_t reduce_sum(const double* x, int64_t n, double* partial, double* out, cudaStream_t s);
 
+// vif_lowrank_tc.cu: A = K_nm L_m^{-T} on the tensor cores for the float32 path.  init
+// (once per device, outside stream capture) raises the kernel's shared-memory limit;
+// pack holds lowrank_A_tc_pack_floats(mpad) floats; mpad = 32 ceil(m / 32).
+cudaError_t lowrank_A_tc_init();
+size_t lowrank_A_tc_pack_floats(int mpad);
+cudaError_t lowrank_A_tc(const float* Xs, const float* Zs, const double* Linv, int ldl, float* pack, float* A,
+                         int64_t n, int d, int m, int mpad, int kind, double var, int* status, cudaStream_t s);
+
 // vif_lowrank.cu
 cudaError_t scale_coords(const double* X, int64_t n, int d, const double* inv_ls, const double* center,
                          double* Xs, float* Xs32, cudaStream_t s);
@@ -87,10 +95,16 @@ template <typename T>
 cudaError_t vecchia_factor(const T* A, const T* Xs, const int32_t* N, const int32_t* order, const double* y,
                            int64_t n, int d, int m, int mpad, int mv, int fpad, CovParams cp, T* F,
                            double* Acoef, double* Dv, double* logD, int* status, cudaStream_t s);
-// wrow: optional row weights (NULL = 1): G = F^T diag(wrow) F (+ identity on the first m)
+// wrow: optional row weights (NULL = 1): G = F^T diag(wrow) F (+ identity on the first m).
+// The float32 Gram runs on the tensor cores (vif_gram_tc.cu) and may use fewer slices
+// than nsplit; status receives ST_TIMEOUT if one of its waits gives up.
 template <typename T>
 cudaError_t gram_FtF(const T* F, int64_t n, int fpad, int m, double* part, int nsplit, double* G,
-                     int ldg, cudaStream_t s, const double* wrow = nullptr);
+                     int ldg, cudaStream_t s, const double* wrow = nullptr, int* status = nullptr);
+// vif_gram_tc.cu: split-K float32 Gram partials on the tensor cores (64 x 64 pair layout)
+cudaError_t gram_tc_init();
+int gram_tc_nsplit(int64_t n, int fpad);
+cudaError_t gram_tc(const float* F, int64_t n, int fpad, double* part, int nsplit, int* status, cudaStream_t s);
 int gram_nsplit(int64_t n, int fpad);
 cudaError_t nll_finish(const double* Lg, int ldg, int m, const double* logD_sum, int64_t n,
                        double* out, cudaStream_t s);

@@ -144,109 +144,15 @@ __global__ __launch_bounds__(256) void lowrank_A_kernel(const T* __restrict__ Xs
   }
 }
 
-// float32 variant with 16-byte operand reads: the kernel tile is stored transposed
-// (k-major) so a thread's 8 points are two float4s, and a thread's 8 output columns
-// are two groups of 4 contiguous columns 256 apart, which keeps the triangular skip
-// uniform across the CTA (half h is skipped once all its columns lie below c0).
-__global__ __launch_bounds__(256) void lowrank_A_kernel_f32(const float* __restrict__ Xs, const float* __restrict__ Zs,
-                                                            const float* __restrict__ LinvT, int ldt,
-                                                            float* __restrict__ A, int64_t n, int d, int m, int mpad,
-                                                            int kind, float var) {
-  constexpr int BK = 16;
-  __shared__ float xs[LR_BP * LR_MAXD];
-  __shared__ float zs[BK * LR_MAXD];
-  __shared__ __align__(16) float KsT[BK][LR_BP + 4];
-  __shared__ __align__(16) float Ls[BK][LR_PASS];
-  const int64_t p0 = (int64_t)blockIdx.x * LR_BP;
-  const int tid = threadIdx.x, cg = tid & 63, rg = tid >> 6;
-  for (int e = tid; e < LR_BP * d; e += 256) {
-    int64_t pi = p0 + e / d;
-    xs[e] = (pi < n) ? Xs[(size_t)p0 * d + e] : 0.f;
-  }
-  for (int base = 0; base < mpad; base += LR_PASS) {
-    float acc[8][8];
-#pragma unroll
-    for (int r = 0; r < 8; ++r)
-#pragma unroll
-      for (int j = 0; j < 8; ++j) acc[r][j] = 0.f;
-    const int cend = min(m, base + LR_PASS);
-    for (int c0 = 0; c0 < cend; c0 += BK) {
-      __syncthreads();
-      for (int e = tid; e < BK * d; e += 256) {
-        int c = c0 + e / d;
-        zs[e] = (c < m) ? Zs[(size_t)c0 * d + e] : 0.f;
-      }
-      // rows c0..c0+15 of L^{-T}, columns base..base+511 as float4 (zero outside)
-      for (int e = tid; e < BK * (LR_PASS / 4); e += 256) {
-        int kk = e / (LR_PASS / 4), q4 = (e % (LR_PASS / 4)) * 4;
-        int c = c0 + kk, r = base + q4;
-        float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
-        if (c < m && r + 3 < ldt && r + 3 >= c) v = *reinterpret_cast<const float4*>(LinvT + (size_t)c * ldt + r);
-        *reinterpret_cast<float4*>(&Ls[kk][q4]) = v;
-      }
-      __syncthreads();
-      for (int e = tid; e < LR_BP * BK; e += 256) {
-        int pi = e % LR_BP, kk = e / LR_BP;
-        int c = c0 + kk;
-        float v = 0.f;
-        if (c < m && p0 + pi < n) v = cov_r2<float>(sqdist(xs + pi * d, zs + kk * d, d), kind, var);
-        KsT[kk][pi] = v;
-      }
-      __syncthreads();
-      const bool h0 = base + 255 >= c0, h1 = base + 511 >= c0;
-#pragma unroll 4
-      for (int kk = 0; kk < BK; ++kk) {
-        const float4 a0 = *reinterpret_cast<const float4*>(&KsT[kk][rg * 8]);
-        const float4 a1 = *reinterpret_cast<const float4*>(&KsT[kk][rg * 8 + 4]);
-        const float av[8] = {a0.x, a0.y, a0.z, a0.w, a1.x, a1.y, a1.z, a1.w};
-        if (h0) {
-          const float4 b = *reinterpret_cast<const float4*>(&Ls[kk][cg * 4]);
-          const float bv[4] = {b.x, b.y, b.z, b.w};
-#pragma unroll
-          for (int r = 0; r < 8; ++r)
-#pragma unroll
-            for (int j = 0; j < 4; ++j) acc[r][j] += av[r] * bv[j];
-        }
-        if (h1) {
-          const float4 b = *reinterpret_cast<const float4*>(&Ls[kk][256 + cg * 4]);
-          const float bv[4] = {b.x, b.y, b.z, b.w};
-#pragma unroll
-          for (int r = 0; r < 8; ++r)
-#pragma unroll
-            for (int j = 0; j < 4; ++j) acc[r][4 + j] += av[r] * bv[j];
-        }
-      }
-    }
-#pragma unroll
-    for (int r = 0; r < 8; ++r) {
-      int64_t pi = p0 + rg * 8 + r;
-      if (pi >= n) continue;
-#pragma unroll
-      for (int h = 0; h < 2; ++h) {
-        int col = base + 256 * h + cg * 4;
-        if (col + 3 < mpad)
-          *reinterpret_cast<float4*>(A + (size_t)pi * mpad + col) =
-              make_float4(acc[r][4 * h], acc[r][4 * h + 1], acc[r][4 * h + 2], acc[r][4 * h + 3]);
-      }
-    }
-  }
-}
-
 template <typename T>
 cudaError_t lowrank_A(const T* Xs, const T* Zs, const T* LinvT, int ldt, T* A, int64_t n, int d, int m,
                       int mpad, int kind, double var, cudaStream_t s) {
   if (m <= 0) return cudaMemsetAsync(A, 0, sizeof(T) * (size_t)n * mpad, s);
   if (d > LR_MAXD) return cudaErrorInvalidValue;
   unsigned grid = (unsigned)((n + LR_BP - 1) / LR_BP);
-  if constexpr (sizeof(T) == 4) {
-    lowrank_A_kernel_f32<<<grid, 256, 0, s>>>(Xs, Zs, LinvT, ldt, A, n, d, m, mpad, kind, (float)var);
-  } else {
-    lowrank_A_kernel<T><<<grid, 256, 0, s>>>(Xs, Zs, LinvT, ldt, A, n, d, m, mpad, kind, (T)var);
-  }
+  lowrank_A_kernel<T><<<grid, 256, 0, s>>>(Xs, Zs, LinvT, ldt, A, n, d, m, mpad, kind, (T)var);
   return cudaGetLastError();
 }
-template cudaError_t lowrank_A<float>(const float*, const float*, const float*, int, float*, int64_t, int, int,
-                                      int, int, double, cudaStream_t);
 template cudaError_t lowrank_A<double>(const double*, const double*, const double*, int, double*, int64_t, int,
                                        int, int, int, double, cudaStream_t);
 

@@ -1,0 +1,323 @@
+// A = K_nm L_m^{-T} (Sec. 2.2, the low-rank factor of the predictive-process part) on the
+// fifth-generation tensor cores, for the float32 (mixed) path.
+//
+// Row p of A is sum_k K(s_p, z_k) Linv[j][k] over k <= j, i.e. a GEMM of the kernel
+// block K_nm (M = points, K = inducing points) with L_m^{-1} read as an N x K K-major
+// operand (row j of L_m^{-1} is contiguous in k).  Float32 accuracy is kept with the
+// three-term split x = hi + lo (hi, lo tf32, round to nearest): each product is
+//   Khi Lhi + Khi Llo + Klo Lhi,
+// which leaves an error of about 2^-21 relative per product.  The tensor core's float32
+// accumulation loses up to about one unit in the last place per step, with a bias, so
+// a TMEM accumulator never runs longer than AT_P chunks of 32 inducing points (12 MMAs
+// each): every such partial is added into float32 registers (round to nearest), and
+// two TMEM accumulators alternate so that the MMAs of one period run while the partial
+// of the previous one is read out.
+//
+// CTA: 128 points (one TMEM lane each) x 256 output columns, 8 warps.  Per chunk every
+// thread evaluates 16 kernel values of one point, splits them and writes them into the
+// swizzled A-operand tiles; thread 0 brings the matching L_m^{-1} tiles (packed once
+// per call, already in the swizzled image) with one bulk copy per tile and issues the
+// 12 MMAs.  Two operand stages let the kernel evaluation of chunk c+1 overlap the MMAs
+// of chunk c; the inducing points of chunk c+1 are prefetched into registers.  Chunks
+// above the tile's last column are skipped (L_m^{-1} is lower triangular).
+#include "vif_internal.cuh"
+#include "vif_tc.cuh"
+
+namespace vif {
+
+namespace {
+
+constexpr int AT_M = 128;                         // points per CTA
+constexpr int AT_N = 256;                         // output columns per CTA
+constexpr int AT_K = 32;                          // inducing points per chunk
+constexpr int AT_MAXD = 16;
+constexpr int AT_THREADS = 256;
+constexpr uint32_t AT_ATILE = AT_M * 128;         // bytes of one A-operand tile (hi or lo)
+constexpr uint32_t AT_BTILE = AT_N * 128;         // bytes of one B-operand tile (hi or lo)
+constexpr uint32_t AT_STAGE = 2 * AT_ATILE + 2 * AT_BTILE;
+constexpr uint32_t AT_SMEM = 2 * AT_STAGE + 1024; // two stages + alignment slack
+constexpr uint32_t AT_TMEM_COLS = 2 * AT_N;       // two accumulators
+constexpr int AT_P = 1;                           // chunks per TMEM accumulation period
+
+struct __align__(8) AtBars {
+  uint64_t full[2];    // B tiles of the stage have landed
+  uint64_t empty[2];   // MMAs of the stage's chunk are done (stage free)
+  uint64_t accf[2];    // accumulator b holds a finished period
+  uint64_t fin;        // every MMA of the CTA is done
+  uint32_t tmem;
+  float zs[2][AT_K * AT_MAXD];
+};
+
+// Packed L_m^{-1}: tile (h, c, part) holds rows j = 256 h + r (r < 256) and columns
+// k = 32 c + kk of L_m^{-1} (hi part = 0, lo part = 1) as a swizzled 256 x 32 tf32 image.
+__global__ void linv_pack_tc_kernel(const double* __restrict__ Linv, int m, int ldl, float* __restrict__ pk,
+                                    int nchunk, int64_t total) {
+  const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= total) return;
+  const int kk = (int)(e % AT_K);
+  const int r = (int)((e / AT_K) % AT_N);
+  const int64_t t = e / ((int64_t)AT_K * AT_N);     // (h * nchunk + c)
+  const int c = (int)(t % nchunk), h = (int)(t / nchunk);
+  const int j = h * AT_N + r, k = c * AT_K + kk;
+  double v = 0.0;
+  if (j < m && k < m && k <= j) v = Linv[(size_t)j * ldl + k];
+  const float hi = tc::to_tf32((float)v);
+  const float lo = tc::to_tf32((float)(v - (double)hi));
+  float* tile = pk + (size_t)t * 2 * (AT_N * AT_K);
+  const uint32_t off = tc::sw128_off32(r, kk) / 4;
+  tile[off] = hi;
+  tile[AT_N * AT_K + off] = lo;
+}
+
+// D > 0: compile-time input dimension; D = 0: any d <= AT_MAXD
+template <int D>
+__global__ __launch_bounds__(AT_THREADS, 1) void lowrank_A_tc_kernel(
+    const float* __restrict__ Xs, const float* __restrict__ Zs, const float* __restrict__ pk, float* __restrict__ A,
+    int64_t n, int d, int m, int mpad, int nchunk_all, int kind, float var, int* status) {
+  extern __shared__ unsigned char smem_raw[];
+  __shared__ AtBars sb;
+  unsigned char* smem = (unsigned char*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int h = blockIdx.y;
+  const int64_t row0 = (int64_t)blockIdx.x * AT_M;
+  const int ncols = min(AT_N, mpad - h * AT_N);                 // multiple of 32
+  const int nchunk = min(nchunk_all, (h * AT_N + ncols - 1) / AT_K + 1);
+  const uint32_t idesc = tc::idesc_tf32(AT_M, ncols);
+  const float* pk_h = pk + (size_t)h * nchunk_all * 2 * (AT_N * AT_K);
+  // kernel evaluation: point krow, values 16 khalf .. 16 khalf + 15 of each chunk
+  const int krow = tid & (AT_M - 1), khalf = tid >> 7;
+  const int64_t p = row0 + krow;
+  // read-out: TMEM lanes dl .. dl + 31, columns dc .. dc + 127 of the accumulator
+  const int dl = 32 * (warp & 3), dc = 128 * (warp >> 2);
+  const int ngrp = max(0, min(4, (ncols - dc) / 32));
+
+  if (warp == 0) tc::tmem_alloc(&sb.tmem, AT_TMEM_COLS);
+  if (tid == 0) {
+    for (int s = 0; s < 2; ++s) {
+      tc::mbar_init(&sb.full[s], 1);
+      tc::mbar_init(&sb.empty[s], 1);
+      tc::mbar_init(&sb.accf[s], 1);
+    }
+    tc::mbar_init(&sb.fin, 1);
+    tc::fence_mbar_init();
+  }
+  constexpr int DX = D > 0 ? D : AT_MAXD;
+  float x[DX];
+#pragma unroll
+  for (int t = 0; t < DX; ++t) x[t] = (t < d && p < n) ? Xs[(size_t)p * d + t] : 0.f;
+  // inducing points of chunk c, element e = tid + 256 j of the chunk's 32 x d block
+  auto zload = [&](int c, float (&zr)[2]) {
+#pragma unroll
+    for (int j = 0; j < 2; ++j) {
+      const int e = tid + AT_THREADS * j;
+      const int k = c * AT_K + e / max(d, 1);
+      zr[j] = (c < nchunk && e < AT_K * d && k < m) ? Zs[(size_t)c * AT_K * d + e] : 0.f;
+    }
+  };
+  float zpre[2];
+  zload(0, zpre);
+  float acc[128];
+#pragma unroll
+  for (int j = 0; j < 128; ++j) acc[j] = 0.f;
+  tc::fence_before_sync();
+  __syncthreads();
+  tc::fence_after_sync();
+  const uint32_t tmem = sb.tmem;
+
+  bool failed = false;
+  // add the partial of period j (accumulator j % 2) into acc
+  auto drain = [&](int j) {
+    if (!tc::mbar_wait(&sb.accf[j & 1], (j >> 1) & 1)) {
+      failed = true;
+      return;
+    }
+    tc::fence_after_sync();
+    const uint32_t base = tmem + ((uint32_t)dl << 16) + (uint32_t)((j & 1) * AT_N + dc);
+#pragma unroll
+    for (int g = 0; g < 4; ++g) {
+      if (g < ngrp) {
+        float v[32];
+        tc::tmem_ld32(base + g * 32, v);
+#pragma unroll
+        for (int i = 0; i < 32; ++i) acc[g * 32 + i] += v[i];
+      }
+    }
+    tc::fence_before_sync();
+  };
+
+  int copies_issued[2] = {0, 0}, copies_seen[2] = {0, 0};
+  int drained = 0;   // periods already read out
+  for (int c = 0; c < nchunk; ++c) {
+    const int s = c & 1;
+    unsigned char* st = smem + s * AT_STAGE;
+    unsigned char* a_hi = st;
+    unsigned char* a_lo = st + AT_ATILE;
+    unsigned char* b_hi = st + 2 * AT_ATILE;
+    unsigned char* b_lo = st + 2 * AT_ATILE + AT_BTILE;
+    // stage s was read by the MMAs of chunk c-2
+    if (c >= 2 && !tc::mbar_wait(&sb.empty[s], ((c - 2) >> 1) & 1)) failed = true;
+    if (tid == 0 && !failed) {
+      const float* src = pk_h + (size_t)c * 2 * (AT_N * AT_K);
+      tc::mbar_arrive_expect_tx(&sb.full[s], 2u * ncols * 128u);
+      tc::bulk_g2s(b_hi, src, ncols * 128u, &sb.full[s]);
+      tc::bulk_g2s(b_lo, src + AT_N * AT_K, ncols * 128u, &sb.full[s]);
+      ++copies_issued[s];
+    }
+#pragma unroll
+    for (int j = 0; j < 2; ++j) {
+      const int e = tid + AT_THREADS * j;
+      if (e < AT_K * AT_MAXD) sb.zs[s][e] = zpre[j];
+    }
+    zload(c + 1, zpre);
+    if (__syncthreads_or(failed)) {
+      failed = true;
+      break;
+    }
+    // 16 kernel values of this thread's point, split into tf32 hi + lo
+    const int kmax = min(AT_K, m - c * AT_K);
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      float hv[4], lv[4];
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        const int kk = khalf * 16 + q * 4 + u;
+        float kv = 0.f;
+        if (kk < kmax && p < n) {
+          float r2 = 0.f;
+          if constexpr (D > 0) {
+            const float* z = &sb.zs[s][kk * D];
+#pragma unroll
+            for (int t = 0; t < D; ++t) {
+              const float df = x[t] - z[t];
+              r2 = fmaf(df, df, r2);
+            }
+          } else {
+            const float* z = &sb.zs[s][kk * d];
+#pragma unroll
+            for (int t = 0; t < AT_MAXD; ++t)
+              if (t < d) {
+                const float df = x[t] - z[t];
+                r2 = fmaf(df, df, r2);
+              }
+          }
+          kv = cov_r2<float>(r2, kind, var);
+        }
+        hv[u] = tc::to_tf32(kv);
+        lv[u] = tc::to_tf32(kv - hv[u]);
+      }
+      const uint32_t off = tc::sw128_off32(krow, khalf * 16 + q * 4);
+      *reinterpret_cast<float4*>(a_hi + off) = make_float4(hv[0], hv[1], hv[2], hv[3]);
+      *reinterpret_cast<float4*>(a_lo + off) = make_float4(lv[0], lv[1], lv[2], lv[3]);
+    }
+    tc::fence_proxy_async();
+    tc::fence_before_sync();
+    __syncthreads();
+    if (tid == 0) {
+      tc::fence_after_sync();
+      if (!tc::mbar_wait(&sb.full[s], copies_seen[s] & 1)) {
+        failed = true;
+      } else {
+        ++copies_seen[s];
+        const uint32_t dt = tmem + (uint32_t)(((c / AT_P) & 1) * AT_N);
+        const uint32_t ah = tc::smem_addr(a_hi), al = tc::smem_addr(a_lo);
+        const uint32_t bh = tc::smem_addr(b_hi), bl = tc::smem_addr(b_lo);
+        // the small cross terms first, the hi x hi products last: every accumulation
+        // step truncates relative to the running sum, so the steps taken once the sum
+        // is large are kept to the four hi x hi ones
+#pragma unroll
+        for (int ks = 0; ks < AT_K / 8; ++ks) {
+          const uint32_t o = ks * 32;
+          tc::mma_tf32(dt, tc::desc_k_sw128(al + o), tc::desc_k_sw128(bh + o), idesc, (c % AT_P != 0 || ks > 0));
+          tc::mma_tf32(dt, tc::desc_k_sw128(ah + o), tc::desc_k_sw128(bl + o), idesc, 1u);
+        }
+#pragma unroll
+        for (int ks = 0; ks < AT_K / 8; ++ks) {
+          const uint32_t o = ks * 32;
+          tc::mma_tf32(dt, tc::desc_k_sw128(ah + o), tc::desc_k_sw128(bh + o), idesc, 1u);
+        }
+      }
+      tc::mma_commit(&sb.empty[s]);
+      if (c % AT_P == AT_P - 1 || c == nchunk - 1) tc::mma_commit(&sb.accf[(c / AT_P) & 1]);
+    }
+    // the previous period ended with chunk c-1: read it out while chunk c multiplies
+    if (c % AT_P == 0 && c >= AT_P && !failed) {
+      drain(c / AT_P - 1);
+      drained = c / AT_P;
+    }
+  }
+  const int nperiod = (nchunk + AT_P - 1) / AT_P;
+  for (int q = drained; q < nperiod && !failed; ++q) drain(q);
+  // every MMA issued by this CTA completes on `fin`
+  if (tid == 0) {
+    tc::mma_commit(&sb.fin);
+    // copies issued but never waited for (only after a failure)
+    for (int s = 0; s < 2; ++s)
+      while (copies_seen[s] < copies_issued[s]) {
+        if (!tc::mbar_wait(&sb.full[s], copies_seen[s] & 1)) break;
+        ++copies_seen[s];
+      }
+  }
+  if (!tc::mbar_wait(&sb.fin, 0)) failed = true;
+  if (__syncthreads_or(failed)) {
+    if (tid == 0 && status) flag_status(status, ST_TIMEOUT, blockIdx.x);
+  } else {
+    const int64_t row = row0 + dl + lane;
+    if (row < n) {
+      float* dst = A + (size_t)row * mpad + h * AT_N + dc;
+#pragma unroll
+      for (int g = 0; g < 4; ++g)
+        if (g < ngrp) {
+#pragma unroll
+          for (int j = 0; j < 32; j += 4)
+            *reinterpret_cast<float4*>(dst + g * 32 + j) =
+                make_float4(acc[g * 32 + j], acc[g * 32 + j + 1], acc[g * 32 + j + 2], acc[g * 32 + j + 3]);
+        }
+    }
+  }
+  tc::fence_before_sync();
+  __syncthreads();
+  if (warp == 0) {
+    tc::fence_after_sync();
+    tc::tmem_dealloc(tmem, AT_TMEM_COLS);
+  }
+}
+
+}  // namespace
+
+cudaError_t lowrank_A_tc_init() {
+  cudaError_t e = cudaFuncSetAttribute(lowrank_A_tc_kernel<0>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)AT_SMEM);
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(lowrank_A_tc_kernel<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)AT_SMEM);
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(lowrank_A_tc_kernel<8>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)AT_SMEM);
+  return e;
+}
+
+size_t lowrank_A_tc_pack_floats(int mpad) {
+  const int nh = (mpad + AT_N - 1) / AT_N, nchunk = mpad / AT_K;
+  return (size_t)nh * nchunk * 2 * AT_N * AT_K;
+}
+
+cudaError_t lowrank_A_tc(const float* Xs, const float* Zs, const double* Linv, int ldl, float* pack, float* A,
+                         int64_t n, int d, int m, int mpad, int kind, double var, int* status, cudaStream_t s) {
+  if (m <= 0) return cudaMemsetAsync(A, 0, sizeof(float) * (size_t)n * mpad, s);
+  if (d > AT_MAXD || mpad % AT_K != 0 || mpad < m || mpad - m >= AT_K || n <= 0) return cudaErrorInvalidValue;
+  // mpad = 32 ceil(m / 32), so the packed chunks and the chunks of m coincide
+  const int nh = (mpad + AT_N - 1) / AT_N, nchunk = mpad / AT_K;
+  const int64_t total = (int64_t)nh * nchunk * AT_N * AT_K;
+  linv_pack_tc_kernel<<<(unsigned)((total + 255) / 256), 256, 0, s>>>(Linv, m, ldl, pack, nchunk, total);
+  dim3 grid((unsigned)((n + AT_M - 1) / AT_M), (unsigned)nh);
+  if (d == 8)
+    lowrank_A_tc_kernel<8><<<grid, AT_THREADS, AT_SMEM, s>>>(Xs, Zs, pack, A, n, d, m, mpad, nchunk, kind,
+                                                             (float)var, status);
+  else if (d == 2)
+    lowrank_A_tc_kernel<2><<<grid, AT_THREADS, AT_SMEM, s>>>(Xs, Zs, pack, A, n, d, m, mpad, nchunk, kind,
+                                                             (float)var, status);
+  else
+    lowrank_A_tc_kernel<0><<<grid, AT_THREADS, AT_SMEM, s>>>(Xs, Zs, pack, A, n, d, m, mpad, nchunk, kind,
+                                                             (float)var, status);
+  return cudaGetLastError();
+}
+
+}  // namespace vif
