@@ -8,8 +8,7 @@
 // below therefore keeps the serial chain short and spreads the rest over many SMs:
 // one launch factors the 32 x 32 diagonal tile (redundantly in every CTA) together
 // with the tile below it in one column sweep (pivots by a Newton-refined reciprocal
-// square root), the next updates the trailing tiles in k-slices (several CTAs per
-// tile, float64 atomics).
+// square root), the next updates the trailing tiles, one CTA per tile.
 #include "vif_internal.cuh"
 
 namespace vif {
@@ -108,32 +107,33 @@ __global__ void chol_panel_kernel(double* A, int m, int lda, int k, int* status,
   }
 }
 
-// Trailing update A_ij -= L_ik L_jk^T of step k, split along k into KS slices: CTA
-// (tile, slice) multiplies 32 x 8 by 8 x 32 and adds with float64 atomics, so that a
-// step's latency is a quarter of a tile product (one CTA per SM holds the float64 pipe).
+// k-slices of the triangular-inverse products (one CTA each, float64 atomics)
 constexpr int KS = 4;
 constexpr int KSW = NB / KS;
 
+// Trailing update A_ij -= L_ik L_jk^T of step k, one CTA per tile (i, j), summed in a
+// fixed order: the capacitance matrix is ill-conditioned enough (condition ~1e7-1e8)
+// that a run-to-run change in the last bits of its factor shows in the likelihood.
 __global__ void chol_update_kernel(double* A, int m, int lda, int k, int T) {
   // tile (i, j), k < j <= i < k+1+T, enumerated over the lower triangle
-  const int b = blockIdx.x / KS, ks = blockIdx.x % KS;
+  int b = blockIdx.x;
   int ii = (int)((sqrt(8.0 * b + 1.0) - 1.0) * 0.5);
   while ((ii + 1) * (ii + 2) / 2 <= b) ++ii;
   while (ii * (ii + 1) / 2 > b) --ii;
   int jj = b - ii * (ii + 1) / 2;
-  const int i0 = (k + 1 + ii) * NB, j0 = (k + 1 + jj) * NB, c0 = k * NB + ks * KSW;
-  __shared__ double Li[NB][KSW + 1];
-  __shared__ double Lj[NB][KSW + 1];
-  for (int idx = threadIdx.x; idx < NB * KSW; idx += blockDim.x) {
-    int r = idx / KSW, c = idx % KSW;
-    Li[r][c] = (i0 + r < m && c0 + c < m) ? A[(size_t)(i0 + r) * lda + c0 + c] : 0.0;
-    Lj[r][c] = (j0 + r < m && c0 + c < m) ? A[(size_t)(j0 + r) * lda + c0 + c] : 0.0;
+  const int i0 = (k + 1 + ii) * NB, j0 = (k + 1 + jj) * NB, k0 = k * NB;
+  __shared__ double Li[NB][NB + 1];
+  __shared__ double Lj[NB][NB + 1];
+  for (int idx = threadIdx.x; idx < NB * NB; idx += blockDim.x) {
+    int r = idx / NB, c = idx % NB;
+    Li[r][c] = (i0 + r < m && k0 + c < m) ? A[(size_t)(i0 + r) * lda + k0 + c] : 0.0;
+    Lj[r][c] = (j0 + r < m && k0 + c < m) ? A[(size_t)(j0 + r) * lda + k0 + c] : 0.0;
   }
   __syncthreads();
   const int tx = threadIdx.x % 16, ty = threadIdx.x / 16;
   double acc[2][2] = {{0, 0}, {0, 0}};
-#pragma unroll
-  for (int c = 0; c < KSW; ++c) {
+#pragma unroll 8
+  for (int c = 0; c < NB; ++c) {
     double a0 = Li[ty][c], a1 = Li[ty + 16][c];
     double b0 = Lj[tx][c], b1 = Lj[tx + 16][c];
     acc[0][0] += a0 * b0; acc[0][1] += a0 * b1;
@@ -142,7 +142,7 @@ __global__ void chol_update_kernel(double* A, int m, int lda, int k, int T) {
   for (int u = 0; u < 2; ++u)
     for (int v = 0; v < 2; ++v) {
       int r = i0 + ty + 16 * u, c = j0 + tx + 16 * v;
-      if (r < m && c < m && c <= r) atomicAdd(&A[(size_t)r * lda + c], -acc[u][v]);
+      if (r < m && c < m && c <= r) A[(size_t)r * lda + c] -= acc[u][v];
     }
 }
 
@@ -152,7 +152,7 @@ cudaError_t dense_cholesky(double* A, int m, int lda, int* status, int code, cud
   for (int k = 0; k < nt; ++k) {
     chol_panel_kernel<<<nt - k, 256, 0, s>>>(A, m, lda, k, status, code);
     int T = nt - k - 1;
-    if (T > 0) chol_update_kernel<<<T * (T + 1) / 2 * KS, 256, 0, s>>>(A, m, lda, k, T);
+    if (T > 0) chol_update_kernel<<<T * (T + 1) / 2, 256, 0, s>>>(A, m, lda, k, T);
   }
   return cudaGetLastError();
 }

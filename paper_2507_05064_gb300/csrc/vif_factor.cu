@@ -117,6 +117,76 @@ __global__ __launch_bounds__(FK_WARPS * 32) void factor_kernel(
     S.xc[t][c] = Xs[(size_t)S.idx[t] * d + c];
   }
   // ---- Gram of the gathered rows of A, double-buffered windows of KC columns
+  // float32 with 15 <= Q <= 21 (the m_v = 20 workloads): seven-row blocks, 3 x 3 grid,
+  // 6 lower block pairs x 4 lanes, lane kg taking the window columns kg + 4t, so each
+  // lane reads 14 values per column for 49 products (2 per shared-memory word instead
+  // of 1.5 with the 3 x 3 blocks below, and 4 per word per block pair); the 4 partial
+  // sums of a block pair are added by shuffles at the end.
+  constexpr bool BIG = (sizeof(T) == 4 && R == 3);
+  if constexpr (BIG) {
+    constexpr int BR = 7;
+    const bool own = lane < 24;
+    const int bp = own ? (lane >> 2) : 0, kg = lane & 3;
+    const int bi = (bp == 0) ? 0 : (bp < 3 ? 1 : 2);
+    const int bj = bp - (bi * (bi + 1) / 2);
+    float acc[BR][BR];
+#pragma unroll
+    for (int r = 0; r < BR; ++r)
+#pragma unroll
+      for (int c = 0; c < BR; ++c) acc[r][c] = 0.f;
+    const int nwin = (m + KC - 1) / KC;
+    constexpr int SEG = KC / V;
+    auto issue = [&](int win, int b) {
+      const int k0 = win * KC;
+      for (int e = lane; e < Q * SEG; e += 32) {
+        int t = e / SEG, sg = e % SEG;
+        int k = k0 + sg * V;
+        if (k < mpad) cp_async16(&S.buf[b][t][sg * V], A + (size_t)S.idx[t] * mpad + k);
+      }
+      cp_async_commit();
+    };
+    if (nwin > 0) issue(0, 0);
+    for (int win = 0; win < nwin; ++win) {
+      const int b = win & 1;
+      if (win + 1 < nwin) {
+        issue(win + 1, b ^ 1);
+        cp_async_wait<1>();
+      } else {
+        cp_async_wait<0>();
+      }
+      __syncwarp();
+#pragma unroll 2
+      for (int t = 0; t < KC / 4; ++t) {
+        const int col = kg + 4 * t;
+        float u[BR], v[BR];
+#pragma unroll
+        for (int r = 0; r < BR; ++r) u[r] = (float)S.buf[b][bi * BR + r][col];
+#pragma unroll
+        for (int c = 0; c < BR; ++c) v[c] = (float)S.buf[b][bj * BR + c][col];
+#pragma unroll
+        for (int r = 0; r < BR; ++r)
+#pragma unroll
+          for (int c = 0; c < BR; ++c) acc[r][c] = fmaf(u[r], v[c], acc[r][c]);
+      }
+      __syncwarp();
+    }
+#pragma unroll
+    for (int r = 0; r < BR; ++r)
+#pragma unroll
+      for (int c = 0; c < BR; ++c) {
+        float a = acc[r][c];
+        a += __shfl_xor_sync(0xffffffffu, a, 1);
+        a += __shfl_xor_sync(0xffffffffu, a, 2);
+        acc[r][c] = a;
+      }
+    if (own && kg == 0) {
+#pragma unroll
+      for (int r = 0; r < BR; ++r)
+#pragma unroll
+        for (int c = 0; c < BR; ++c) S.G[bi * BR + r][bj * BR + c] = (T)acc[r][c];
+    }
+    __syncwarp();
+  } else {
   const bool owner = lane < 28;
   const int bi = owner ? c_blk_i[lane] : 0, bj = owner ? c_blk_j[lane] : 0;
   T acc[R][R];
@@ -170,6 +240,7 @@ __global__ __launch_bounds__(FK_WARPS * 32) void factor_kernel(
       for (int c = 0; c < R; ++c) S.G[bi * R + r][bj * R + c] = acc[r][c];
   }
   __syncwarp();
+  }
   // ---- residual covariance R (lower triangle)
   const int npair = Q * (Q + 1) / 2;
   for (int e = lane; e < npair; e += 32) {

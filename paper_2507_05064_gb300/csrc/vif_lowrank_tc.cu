@@ -7,18 +7,19 @@
 // three-term split x = hi + lo (hi, lo tf32, round to nearest): each product is
 //   Khi Lhi + Khi Llo + Klo Lhi,
 // which leaves an error of about 2^-21 relative per product.  The tensor core's float32
-// accumulation loses up to about one unit in the last place per step, with a bias, so
-// a TMEM accumulator never runs longer than AT_P chunks of 32 inducing points (12 MMAs
-// each): every such partial is added into float32 registers (round to nearest), and
-// two TMEM accumulators alternate so that the MMAs of one period run while the partial
-// of the previous one is read out.
+// accumulation rounds toward zero at every step (a coherent bias), so a TMEM
+// accumulator never runs longer than one chunk of 32 inducing points (12 MMAs): each
+// chunk's partial is added into float32 registers (round to nearest), and two TMEM
+// accumulators alternate so that the MMAs of chunk c run while the partial of chunk
+// c-1 is read out.
 //
 // CTA: 128 points (one TMEM lane each) x 256 output columns, 8 warps.  Per chunk every
 // thread evaluates 16 kernel values of one point, splits them and writes them into the
 // swizzled A-operand tiles; thread 0 brings the matching L_m^{-1} tiles (packed once
 // per call, already in the swizzled image) with one bulk copy per tile and issues the
 // 12 MMAs.  Two operand stages let the kernel evaluation of chunk c+1 overlap the MMAs
-// of chunk c; the inducing points of chunk c+1 are prefetched into registers.  Chunks
+// of chunk c; the inducing points of chunk c+1 are prefetched into registers and the
+// L_m^{-1} tiles of chunk c+1 are requested as soon as their stage is free.  Chunks
 // above the tile's last column are skipped (L_m^{-1} is lower triangular).
 #include "vif_internal.cuh"
 #include "vif_tc.cuh"
@@ -37,12 +38,10 @@ constexpr uint32_t AT_BTILE = AT_N * 128;         // bytes of one B-operand tile
 constexpr uint32_t AT_STAGE = 2 * AT_ATILE + 2 * AT_BTILE;
 constexpr uint32_t AT_SMEM = 2 * AT_STAGE + 1024; // two stages + alignment slack
 constexpr uint32_t AT_TMEM_COLS = 2 * AT_N;       // two accumulators
-constexpr int AT_P = 1;                           // chunks per TMEM accumulation period
 
 struct __align__(8) AtBars {
   uint64_t full[2];    // B tiles of the stage have landed
-  uint64_t empty[2];   // MMAs of the stage's chunk are done (stage free)
-  uint64_t accf[2];    // accumulator b holds a finished period
+  uint64_t done[2];    // MMAs of the stage's chunk are done: stage free, accumulator s ready
   uint64_t fin;        // every MMA of the CTA is done
   uint32_t tmem;
   float zs[2][AT_K * AT_MAXD];
@@ -95,8 +94,7 @@ __global__ __launch_bounds__(AT_THREADS, 1) void lowrank_A_tc_kernel(
   if (tid == 0) {
     for (int s = 0; s < 2; ++s) {
       tc::mbar_init(&sb.full[s], 1);
-      tc::mbar_init(&sb.empty[s], 1);
-      tc::mbar_init(&sb.accf[s], 1);
+      tc::mbar_init(&sb.done[s], 1);
     }
     tc::mbar_init(&sb.fin, 1);
     tc::fence_mbar_init();
@@ -125,9 +123,9 @@ __global__ __launch_bounds__(AT_THREADS, 1) void lowrank_A_tc_kernel(
   const uint32_t tmem = sb.tmem;
 
   bool failed = false;
-  // add the partial of period j (accumulator j % 2) into acc
+  // add the partial of chunk j (accumulator j % 2) into acc
   auto drain = [&](int j) {
-    if (!tc::mbar_wait(&sb.accf[j & 1], (j >> 1) & 1)) {
+    if (!tc::mbar_wait(&sb.done[j & 1], (j >> 1) & 1)) {
       failed = true;
       return;
     }
@@ -144,9 +142,19 @@ __global__ __launch_bounds__(AT_THREADS, 1) void lowrank_A_tc_kernel(
     }
     tc::fence_before_sync();
   };
-
+  // L_m^{-1} tiles of chunk c into stage c % 2 (thread 0)
   int copies_issued[2] = {0, 0}, copies_seen[2] = {0, 0};
-  int drained = 0;   // periods already read out
+  auto fetch_b = [&](int c) {
+    const int s = c & 1;
+    unsigned char* st = smem + s * AT_STAGE;
+    const float* src = pk_h + (size_t)c * 2 * (AT_N * AT_K);
+    tc::mbar_arrive_expect_tx(&sb.full[s], 2u * ncols * 128u);
+    tc::bulk_g2s(st + 2 * AT_ATILE, src, ncols * 128u, &sb.full[s]);
+    tc::bulk_g2s(st + 2 * AT_ATILE + AT_BTILE, src + AT_N * AT_K, ncols * 128u, &sb.full[s]);
+    ++copies_issued[s];
+  };
+  if (tid == 0 && nchunk > 0) fetch_b(0);
+
   for (int c = 0; c < nchunk; ++c) {
     const int s = c & 1;
     unsigned char* st = smem + s * AT_STAGE;
@@ -154,15 +162,7 @@ __global__ __launch_bounds__(AT_THREADS, 1) void lowrank_A_tc_kernel(
     unsigned char* a_lo = st + AT_ATILE;
     unsigned char* b_hi = st + 2 * AT_ATILE;
     unsigned char* b_lo = st + 2 * AT_ATILE + AT_BTILE;
-    // stage s was read by the MMAs of chunk c-2
-    if (c >= 2 && !tc::mbar_wait(&sb.empty[s], ((c - 2) >> 1) & 1)) failed = true;
-    if (tid == 0 && !failed) {
-      const float* src = pk_h + (size_t)c * 2 * (AT_N * AT_K);
-      tc::mbar_arrive_expect_tx(&sb.full[s], 2u * ncols * 128u);
-      tc::bulk_g2s(b_hi, src, ncols * 128u, &sb.full[s]);
-      tc::bulk_g2s(b_lo, src + AT_N * AT_K, ncols * 128u, &sb.full[s]);
-      ++copies_issued[s];
-    }
+    // stage s was last read by the MMAs of chunk c-2, read out at iteration c-1
 #pragma unroll
     for (int j = 0; j < 2; ++j) {
       const int e = tid + AT_THREADS * j;
@@ -218,7 +218,7 @@ __global__ __launch_bounds__(AT_THREADS, 1) void lowrank_A_tc_kernel(
         failed = true;
       } else {
         ++copies_seen[s];
-        const uint32_t dt = tmem + (uint32_t)(((c / AT_P) & 1) * AT_N);
+        const uint32_t dt = tmem + (uint32_t)(s * AT_N);
         const uint32_t ah = tc::smem_addr(a_hi), al = tc::smem_addr(a_lo);
         const uint32_t bh = tc::smem_addr(b_hi), bl = tc::smem_addr(b_lo);
         // the small cross terms first, the hi x hi products last: every accumulation
@@ -227,7 +227,7 @@ __global__ __launch_bounds__(AT_THREADS, 1) void lowrank_A_tc_kernel(
 #pragma unroll
         for (int ks = 0; ks < AT_K / 8; ++ks) {
           const uint32_t o = ks * 32;
-          tc::mma_tf32(dt, tc::desc_k_sw128(al + o), tc::desc_k_sw128(bh + o), idesc, (c % AT_P != 0 || ks > 0));
+          tc::mma_tf32(dt, tc::desc_k_sw128(al + o), tc::desc_k_sw128(bh + o), idesc, ks > 0);
           tc::mma_tf32(dt, tc::desc_k_sw128(ah + o), tc::desc_k_sw128(bl + o), idesc, 1u);
         }
 #pragma unroll
@@ -236,21 +236,18 @@ __global__ __launch_bounds__(AT_THREADS, 1) void lowrank_A_tc_kernel(
           tc::mma_tf32(dt, tc::desc_k_sw128(ah + o), tc::desc_k_sw128(bh + o), idesc, 1u);
         }
       }
-      tc::mma_commit(&sb.empty[s]);
-      if (c % AT_P == AT_P - 1 || c == nchunk - 1) tc::mma_commit(&sb.accf[(c / AT_P) & 1]);
+      tc::mma_commit(&sb.done[s]);
     }
-    // the previous period ended with chunk c-1: read it out while chunk c multiplies
-    if (c % AT_P == 0 && c >= AT_P && !failed) {
-      drain(c / AT_P - 1);
-      drained = c / AT_P;
-    }
+    // read out chunk c-1 while chunk c multiplies; its MMAs were the last readers of
+    // stage (c+1) % 2, which then takes the L_m^{-1} tiles of chunk c+1
+    if (c >= 1 && !failed) drain(c - 1);
+    if (tid == 0 && !failed && c + 1 < nchunk) fetch_b(c + 1);
   }
-  const int nperiod = (nchunk + AT_P - 1) / AT_P;
-  for (int q = drained; q < nperiod && !failed; ++q) drain(q);
+  if (!failed && nchunk > 0) drain(nchunk - 1);
   // every MMA issued by this CTA completes on `fin`
   if (tid == 0) {
     tc::mma_commit(&sb.fin);
-    // copies issued but never waited for (only after a failure)
+    // copies issued but never waited for (after a failure, or prefetched past a break)
     for (int s = 0; s < 2; ++s)
       while (copies_seen[s] < copies_issued[s]) {
         if (!tc::mbar_wait(&sb.full[s], copies_seen[s] & 1)) break;
