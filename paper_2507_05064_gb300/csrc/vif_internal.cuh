@@ -42,6 +42,50 @@ __device__ __forceinline__ T sqdist(const T* __restrict__ a, const T* __restrict
   return s;
 }
 
+// Packed float32 pairs for the f32x2 instructions of the sm_100 family (two IEEE
+// operations per instruction, same rounding as the scalar ones).
+__device__ __forceinline__ unsigned long long pack_f2(float lo, float hi) {
+  unsigned long long r;
+  asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(lo), "f"(hi));
+  return r;
+}
+__device__ __forceinline__ float2 unpack_f2(unsigned long long v) {
+  float2 r;
+  asm("mov.b64 {%0, %1}, %2;" : "=f"(r.x), "=f"(r.y) : "l"(v));
+  return r;
+}
+__device__ __forceinline__ unsigned long long ffma2(unsigned long long a, unsigned long long b,
+                                                    unsigned long long c) {
+  unsigned long long d;
+  asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(d) : "l"(a), "l"(b), "l"(c));
+  return d;
+}
+__device__ __forceinline__ unsigned long long fadd2(unsigned long long a, unsigned long long b) {
+  unsigned long long d;
+  asm("add.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+  return d;
+}
+__device__ __forceinline__ unsigned long long fsub2(unsigned long long a, unsigned long long b) {
+  unsigned long long d;
+  asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+  return d;
+}
+
+// float32 covariance for the tensor-core A kernel: the exponential through exp2 of a
+// rescaled argument (2-ulp exp2 plus the rounding of the product; the absolute error
+// stays far below the tf32 split error of the operand)
+__device__ __forceinline__ float cov_r2_fast(float r2, int kind, float var) {
+  constexpr float L2E = 1.4426950408889634f;
+  if (kind == VIF_SE) return var * exp2f(-0.5f * L2E * r2);
+  if (kind == VIF_MATERN12) return var * exp2f(-L2E * sqrtf(r2));
+  if (kind == VIF_MATERN32) {
+    const float t = sqrtf(3.f * r2);
+    return var * (1.f + t) * exp2f(-L2E * t);
+  }
+  const float t = sqrtf(5.f * r2);
+  return var * (1.f + t + t * t * (1.f / 3.f)) * exp2f(-L2E * t);
+}
+
 // Device status words (int32): [0] error code, [1] failing index, [2..] counters.
 enum StatusCode { ST_OK = 0, ST_NOTPD_SIGMAM = 1, ST_NOTPD_FACTOR = 2, ST_NOTPD_CAP = 3,
                   ST_NOTPD_PRECOND = 4, ST_TIMEOUT = 5, ST_BAD_NEIGHBOR = 6 };

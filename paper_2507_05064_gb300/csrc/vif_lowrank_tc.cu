@@ -39,12 +39,12 @@ constexpr uint32_t AT_STAGE = 2 * AT_ATILE + 2 * AT_BTILE;
 constexpr uint32_t AT_SMEM = 2 * AT_STAGE + 1024; // two stages + alignment slack
 constexpr uint32_t AT_TMEM_COLS = 2 * AT_N;       // two accumulators
 
-struct __align__(8) AtBars {
+struct __align__(16) AtBars {
   uint64_t full[2];    // B tiles of the stage have landed
   uint64_t done[2];    // MMAs of the stage's chunk are done: stage free, accumulator s ready
   uint64_t fin;        // every MMA of the CTA is done
   uint32_t tmem;
-  float zs[2][AT_K * AT_MAXD];
+  alignas(16) float zs[2][AT_K * AT_MAXD];   // 8-byte pairs are read from it
 };
 
 // Packed L_m^{-1}: tile (h, c, part) holds rows j = 256 h + r (r < 256) and columns
@@ -103,6 +103,10 @@ __global__ __launch_bounds__(AT_THREADS, 1) void lowrank_A_tc_kernel(
   float x[DX];
 #pragma unroll
   for (int t = 0; t < DX; ++t) x[t] = (t < d && p < n) ? Xs[(size_t)p * d + t] : 0.f;
+  constexpr int DP = (D > 0 && D % 2 == 0) ? D / 2 : 1;   // coordinate pairs (even D)
+  unsigned long long xp[DP];
+#pragma unroll
+  for (int j = 0; j < DP; ++j) xp[j] = pack_f2(x[(2 * j) % DX], x[(2 * j + 1) % DX]);
   // inducing points of chunk c, element e = tid + 256 j of the chunk's 32 x d block
   auto zload = [&](int c, float (&zr)[2]) {
 #pragma unroll
@@ -114,9 +118,9 @@ __global__ __launch_bounds__(AT_THREADS, 1) void lowrank_A_tc_kernel(
   };
   float zpre[2];
   zload(0, zpre);
-  float acc[128];
+  unsigned long long acc2[64];   // column pairs (2j, 2j+1) of this thread's read-out range
 #pragma unroll
-  for (int j = 0; j < 128; ++j) acc[j] = 0.f;
+  for (int j = 0; j < 64; ++j) acc2[j] = 0ull;
   tc::fence_before_sync();
   __syncthreads();
   tc::fence_after_sync();
@@ -137,7 +141,7 @@ __global__ __launch_bounds__(AT_THREADS, 1) void lowrank_A_tc_kernel(
         float v[32];
         tc::tmem_ld32(base + g * 32, v);
 #pragma unroll
-        for (int i = 0; i < 32; ++i) acc[g * 32 + i] += v[i];
+        for (int i = 0; i < 16; ++i) acc2[g * 16 + i] = fadd2(acc2[g * 16 + i], pack_f2(v[2 * i], v[2 * i + 1]));
       }
     }
     tc::fence_before_sync();
@@ -184,7 +188,18 @@ __global__ __launch_bounds__(AT_THREADS, 1) void lowrank_A_tc_kernel(
         float kv = 0.f;
         if (kk < kmax && p < n) {
           float r2 = 0.f;
-          if constexpr (D > 0) {
+          if constexpr (D > 0 && D % 2 == 0) {
+            const float2* z2 = reinterpret_cast<const float2*>(&sb.zs[s][kk * D]);
+            unsigned long long a2 = 0ull;
+#pragma unroll
+            for (int j = 0; j < DP; ++j) {
+              const float2 zz = z2[j];
+              const unsigned long long df = fsub2(xp[j], pack_f2(zz.x, zz.y));
+              a2 = ffma2(df, df, a2);
+            }
+            const float2 h2 = unpack_f2(a2);
+            r2 = h2.x + h2.y;
+          } else if constexpr (D > 0) {
             const float* z = &sb.zs[s][kk * D];
 #pragma unroll
             for (int t = 0; t < D; ++t) {
@@ -200,7 +215,7 @@ __global__ __launch_bounds__(AT_THREADS, 1) void lowrank_A_tc_kernel(
                 r2 = fmaf(df, df, r2);
               }
           }
-          kv = cov_r2<float>(r2, kind, var);
+          kv = cov_r2_fast(r2, kind, var);
         }
         hv[u] = tc::to_tf32(kv);
         lv[u] = tc::to_tf32(kv - hv[u]);
@@ -265,9 +280,10 @@ __global__ __launch_bounds__(AT_THREADS, 1) void lowrank_A_tc_kernel(
       for (int g = 0; g < 4; ++g)
         if (g < ngrp) {
 #pragma unroll
-          for (int j = 0; j < 32; j += 4)
-            *reinterpret_cast<float4*>(dst + g * 32 + j) =
-                make_float4(acc[g * 32 + j], acc[g * 32 + j + 1], acc[g * 32 + j + 2], acc[g * 32 + j + 3]);
+          for (int j = 0; j < 16; j += 2) {
+            const float2 a = unpack_f2(acc2[g * 16 + j]), b = unpack_f2(acc2[g * 16 + j + 1]);
+            *reinterpret_cast<float4*>(dst + g * 32 + 2 * j) = make_float4(a.x, a.y, b.x, b.y);
+          }
         }
     }
   }
