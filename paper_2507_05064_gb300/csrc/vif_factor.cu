@@ -334,11 +334,18 @@ __global__ __launch_bounds__(FK_WARPS * 32) void factor_kernel(
     inv = T(1) / S.G[q][q];
   }
   const T lii = S.G[q][q];
-  const double Dd = (double)lii * (double)lii;
   for (int t = lane; t < mv; t += 32) Acoef[(size_t)i * mv + t] = (t < q) ? (double)S.coef[t] : 0.0;
   if (lane == 0) {
-    Dv[i] = Dd;
-    logD[i] = log(Dd);
+    if constexpr (sizeof(T) == 4) {
+      // float64 instructions cost 64 cycles each on this part: D and log D of the
+      // float32 factor are formed in float32 (they carry float32 information anyway)
+      Dv[i] = (double)(lii * lii);
+      logD[i] = (double)(2.f * logf(lii));
+    } else {
+      const double Dd = (double)lii * (double)lii;
+      Dv[i] = Dd;
+      logD[i] = log(Dd);
+    }
   }
   // ---- row of [F z]: 16-byte vectors along k
   for (int k = lane * V; k < fpad; k += 32 * V) {
@@ -379,11 +386,14 @@ __global__ __launch_bounds__(FK_WARPS * 32) void factor_kernel(
     *reinterpret_cast<VT*>(F + (size_t)i * fpad + k) = ov;
   }
   __syncwarp();
-  if (lane == 0) {
-    double zz = y[i];
-    for (int t = 0; t < q; ++t) zz -= (double)S.coef[t] * y[S.idx[t]];
-    F[(size_t)i * fpad + m] = (T)(zz * (double)inv);
-  }
+  // z_i = (y_i - sum_t A_i[t] y_{N_t}) / sqrt(D_i) in float64: one product per lane and a
+  // shuffle tree (a few warp-wide float64 instructions instead of q serial ones)
+  double zt = (lane < q) ? -(double)S.coef[lane] * y[S.idx[lane]] : 0.0;
+  if (q > 32)
+    for (int t = lane + 32; t < q; t += 32) zt -= (double)S.coef[t] * y[S.idx[t]];
+#pragma unroll
+  for (int off = 16; off > 0; off >>= 1) zt += __shfl_xor_sync(0xffffffffu, zt, off);
+  if (lane == 0) F[(size_t)i * fpad + m] = (T)((y[i] + zt) * (double)inv);
 }
 
 template <typename T, int R>
