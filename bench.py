@@ -46,6 +46,8 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-laplace", action="store_true")
     ap.add_argument("--laplace-n", type=int, default=200_000)
+    ap.add_argument("--batch", type=int, default=0,
+                    help="also time N independent C5-style problems per CUDA graph replay (0: skip)")
     return ap.parse_args()
 
 
@@ -181,6 +183,39 @@ def cpu_baseline(P, n_s, steps=1):
     return {"value": 1.0 / (t * n / n_s), "unit": UNIT, "cores": os.cpu_count(), "kind": "oracle",
             "sample": f"oracle NLL on the first {n_s} of {n} points (m={P.Z.shape[0]}, m_v={P.mv}, d=8), "
                       f"{t:.2f} s per sample eval, scaled by n/{n_s}"}
+
+
+def batch_block(args, stream):
+    """Many independent problems (C5 recipe: n log-uniform in [2e3, 5e4], d in {2, 5},
+    m in [64, 256], m_v in [10, 40]) likelihoods per CUDA graph replay, mixed path."""
+    import torch
+    from paper_2507_05064_gb300 import synth
+    from paper_2507_05064_gb300 import vif as V
+    t0 = time.time()
+    probs = synth.config5(nprob=args.batch)
+    gen_s = time.time() - t0
+    t0 = time.time()
+    ctxs = [V.Context(P.X, P.Z, P.mv, P.theta, precision=V.MIXED, stream=stream.cuda_stream) for P in probs]
+    ys = [torch.from_numpy(P.y).cuda() for P in probs]
+    torch.cuda.synchronize()
+    build_s = time.time() - t0
+    B = V.Batch(ctxs, [P.theta for P in probs], ys, stream=stream.cuda_stream)
+    for _ in range(3):
+        B.run()
+    reps = 10
+    t0 = time.perf_counter()
+    for _ in range(reps):
+        B.run()
+    ms = (time.perf_counter() - t0) * 1000.0 / reps
+    info = B.info()
+    npts = int(sum(P.X.shape[0] for P in probs))
+    B.close()
+    for c in ctxs:
+        c.close()
+    return {"workload": f"c5-{args.batch}-problems", "problems": args.batch, "points": npts,
+            "ms_per_replay": ms, "problems_per_s": args.batch * 1000.0 / ms, "points_per_s": npts * 1000.0 / ms,
+            "branches": info["branches"], "split_div": info["split_div"], "generate_s": gen_s,
+            "build_s": build_s, "timing": "wall clock around vif_batch_run (graph replay + result read-back)"}
 
 
 def laplace_block(args, stream):
@@ -333,6 +368,7 @@ def run_vif(args, rank, world, dist):
     lap = None
     if not args.no_laplace:
         lap = laplace_block(args, stream)
+    bat = batch_block(args, stream) if args.batch > 0 else None
     cb = None
     if not args.no_cpu_baseline:
         cb = cpu_baseline(P, min(args.cpu_sample, P.X.shape[0]))
@@ -351,6 +387,7 @@ def run_vif(args, rank, world, dist):
         "neighbor_search": {"build_s": build_s, "queries_rescored": rescored, "queries_fallback": fallback},
         "roofline": roof,
         "laplace": lap,
+        "batch": bat,
         "cpu_baseline": cb,
         "e2e": {"value": world * 1000.0 / e2e_ms, "unit": UNIT, "ms_per_step": e2e_ms,
                 "h2d_bytes_per_step": int(P.y.nbytes) + 256, "d2h_bytes_per_step": 16 + 24},
