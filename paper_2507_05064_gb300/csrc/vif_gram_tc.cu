@@ -2,19 +2,21 @@
 // response column appended) on the fifth-generation tensor cores, for the float32 path.
 //
 // Split-K SYRK over 128 x 128 tile pairs (ti >= tj) of the fpad columns: CTA (pair,
-// slice) sums rows r0..r1 of F.  Rows arrive 32 at a time: cp.async brings the two
-// column blocks of chunk c+1 into a raw shared-memory buffer while chunk c is being
-// processed; the 8 warps then split every value of the chunk into tf32 hi + lo (round
-// to nearest) and write them transposed into K-major 128-byte-swizzled tiles (row =
-// column of F, K = row of F); thread 0 issues the 16 MMAs of the chunk
+// slice) sums rows r0..r1 of F, 32 rows per chunk.  Warp specialisation: 8 compute
+// warps bring the rows of chunk c+1 into a raw shared-memory buffer with cp.async, split
+// every value of chunk c into tf32 hi + lo (round to nearest) and write them transposed
+// into K-major 128-byte-swizzled tiles (row = column of F, K = row of F), then read out
+// the previous chunk's accumulator; one more warp issues the chunk's 16 MMAs
 //   Alo Blo + Alo Bhi + Ahi Blo + Ahi Bhi
-// into one of two TMEM accumulators.  The tensor core's float32 accumulation loses up
-// to about one unit in the last place per step, with a bias, and C is ill-conditioned
-// (its largest eigenvalue grows with n), so no TMEM accumulator runs longer than one
-// chunk: while the MMAs of chunk c run, the partial of chunk c-1 is added into
-// per-thread double-float32 sums (TwoSum).  The double-float sums are written as
-// float64 partials in the 64 x 64 pair layout that the float64 Gram kernel uses, so one
-// reduction serves both.
+// into one of two TMEM accumulators as soon as the tiles are staged.  The tensor core's
+// float32 accumulation rounds toward zero at every step and C is ill-conditioned (its
+// largest eigenvalue grows with n), so no TMEM accumulator runs longer than one chunk:
+// the read-out adds it into double-float32 running sums (TwoSum) kept in two more TMEM
+// regions, which frees the registers a per-thread sum would need.  lo x lo is kept: on
+// the diagonal it is a sum of squares, and dropping it would shift every diagonal entry
+// down by about 1e-7 of itself, which the eigenvalues of C near 1 do not tolerate.  The
+// sums are written as float64 partials in the 64 x 64 pair layout that the float64 Gram
+// kernel uses, so one reduction serves both.
 #include "vif_internal.cuh"
 #include "vif_tc.cuh"
 
@@ -24,26 +26,23 @@ namespace {
 
 constexpr int GC_T = 128;                       // tile edge (F columns per block)
 constexpr int GC_K = 32;                        // rows of F per chunk
-constexpr int GC_THREADS = 256;
+constexpr int GC_CW = 8;                        // compute warps
+constexpr int GC_NC = GC_CW * 32;               // compute threads
+constexpr int GC_THREADS = GC_NC + 32;          // + the MMA warp
 constexpr uint32_t GC_TILE = GC_T * 128;        // bytes of one swizzled operand tile
 constexpr uint32_t GC_STAGE = 4 * GC_TILE;      // Ahi, Alo, Bhi, Blo
 constexpr uint32_t GC_RAW = 2 * GC_K * GC_T * 4;  // raw rows of both blocks of one chunk
 constexpr uint32_t GC_SMEM = 2 * GC_STAGE + 2 * GC_RAW + 1024;
+constexpr uint32_t GC_TMEM_COLS = 4 * GC_T;     // accumulators 0, 1; running sums hi, lo
 constexpr int GT64 = 64;                        // sub-tile edge of the partial layout
 
-struct __align__(8) GcBars {
-  uint64_t mma_done[2];   // MMAs of the stage's chunk finished (stage and accumulator free)
-  uint64_t fin;           // every MMA of the CTA finished
+struct __align__(16) GcBars {
+  uint64_t staged[2];   // tiles of the stage written (one arrival per compute thread)
+  uint64_t done[2];     // MMAs of the stage's chunk finished (stage and accumulator free)
+  uint64_t fin;         // every MMA of the CTA finished
   uint32_t tmem;
+  int abort;            // the MMA warp gave up waiting
 };
-
-__device__ __forceinline__ void two_sum_add(float& hi, float& lo, float x) {
-  const float s = hi + x;
-  const float bb = s - hi;
-  const float err = (hi - (s - bb)) + (x - bb);
-  hi = s;
-  lo += err;
-}
 
 // 16-byte global -> shared copy; src_bytes = 0 writes zeros
 __device__ __forceinline__ void cp_async16z(void* dst, const void* src, uint32_t src_bytes) {
@@ -74,152 +73,192 @@ __global__ __launch_bounds__(GC_THREADS, 1) void gram_tc_kernel(const float* __r
   const int nchunk = r1 > r0 ? (int)((r1 - r0 + GC_K - 1) / GC_K) : 0;
   const uint32_t idesc = tc::idesc_tf32(GC_T, GC_T);
 
-  if (warp == 0) tc::tmem_alloc(&sb.tmem, 2 * GC_T);
+  if (warp == 0) tc::tmem_alloc(&sb.tmem, GC_TMEM_COLS);
   if (tid == 0) {
-    for (int s = 0; s < 2; ++s) tc::mbar_init(&sb.mma_done[s], 1);
+    for (int s = 0; s < 2; ++s) {
+      tc::mbar_init(&sb.staged[s], GC_NC);
+      tc::mbar_init(&sb.done[s], 1);
+    }
     tc::mbar_init(&sb.fin, 1);
+    sb.abort = 0;
     tc::fence_mbar_init();
   }
-  // raw rows of chunk c into raw buffer c % 2: 16-byte segments, zeros past r1 / fpad
-  auto fetch = [&](int c) {
-    if (c >= nchunk) return;
-    float* dst = raw + (size_t)(c & 1) * (2 * GC_K * GC_T);
-    const int64_t rb = r0 + (int64_t)c * GC_K;
-    for (int e = tid; e < nblk * GC_K * (GC_T / 4); e += GC_THREADS) {
-      const int blk = e / (GC_K * (GC_T / 4));
-      const int rr = (e / (GC_T / 4)) % GC_K, seg = e % (GC_T / 4);
-      const int col = (blk == 0 ? ti : tj) * GC_T + seg * 4;
-      const int64_t r = rb + rr;
-      const bool ok = r < r1 && col < fpad;
-      cp_async16z(dst + ((size_t)blk * GC_K + rr) * GC_T + seg * 4, ok ? (const void*)(F + (size_t)r * fpad + col)
-                                                                        : (const void*)F,
-                  ok ? 16u : 0u);
-    }
-  };
-  fetch(0);
-  asm volatile("cp.async.commit_group;\n" ::: "memory");
   tc::fence_before_sync();
   __syncthreads();
   tc::fence_after_sync();
   const uint32_t tmem = sb.tmem;
-
-  // staging: thread -> column (tid & 127) of the block, rows (tid >> 7) * 16 .. + 15
-  const int scol = tid & (GC_T - 1), srow0 = (tid >> 7) * 16;
-  // read-out: warp -> TMEM lanes 32 (warp % 4) .., columns 64 (warp / 4) .. + 63
-  const int dlane = 32 * (warp & 3), dcol = 64 * (warp >> 2);
-  float acc_hi[64], acc_lo[64];
-#pragma unroll
-  for (int j = 0; j < 64; ++j) {
-    acc_hi[j] = 0.f;
-    acc_lo[j] = 0.f;
-  }
   bool failed = false;
-  // add the partial of chunk j (accumulator j % 2) into the double-float sums
-  auto drain = [&](int j) {
-    if (!tc::mbar_wait(&sb.mma_done[j & 1], (j >> 1) & 1)) {
-      failed = true;
-      return;
-    }
-    tc::fence_after_sync();
-    const uint32_t base = tmem + ((uint32_t)dlane << 16) + (uint32_t)((j & 1) * GC_T + dcol);
-#pragma unroll
-    for (int g = 0; g < 2; ++g) {
-      float v[32];
-      tc::tmem_ld32(base + g * 32, v);
-#pragma unroll
-      for (int i = 0; i < 32; ++i) two_sum_add(acc_hi[g * 32 + i], acc_lo[g * 32 + i], v[i]);
-    }
-    tc::fence_before_sync();
-  };
 
-  for (int c = 0; c < nchunk; ++c) {
-    const int s = c & 1;
-    unsigned char* st = smem + s * GC_STAGE;
-    unsigned char* a_hi = st;
-    unsigned char* a_lo = st + GC_TILE;
-    unsigned char* b_hi = diag ? a_hi : st + 2 * GC_TILE;
-    unsigned char* b_lo = diag ? a_lo : st + 3 * GC_TILE;
-    // stage s was read by the MMAs of chunk c-2 (already waited for by the read-out)
-    if (c >= 2 && !tc::mbar_wait(&sb.mma_done[s], ((c - 2) >> 1) & 1)) failed = true;
-    asm volatile("cp.async.wait_group 0;\n" ::: "memory");   // raw rows of chunk c
-    if (__syncthreads_or(failed)) {
-      failed = true;
-      break;
-    }
-    // every thread is past chunk c-1's staging: refill the other raw buffer
-    fetch(c + 1);
-    asm volatile("cp.async.commit_group;\n" ::: "memory");
-    const float* rw = raw + (size_t)s * (2 * GC_K * GC_T);
-    for (int blk = 0; blk < nblk; ++blk) {
-      unsigned char* th = blk == 0 ? a_hi : b_hi;
-      unsigned char* tl = blk == 0 ? a_lo : b_lo;
-#pragma unroll
-      for (int q = 0; q < 4; ++q) {
-        float hv[4], lv[4];
-#pragma unroll
-        for (int u = 0; u < 4; ++u) {
-          const float v = rw[((size_t)blk * GC_K + srow0 + q * 4 + u) * GC_T + scol];
-          hv[u] = tc::to_tf32(v);
-          lv[u] = tc::to_tf32(v - hv[u]);
+  if (warp == GC_CW) {
+    // ------------------------------------------------ MMA warp (one lane)
+    if (lane == 0) {
+      for (int c = 0; c < nchunk; ++c) {
+        const int s = c & 1;
+        if (!tc::mbar_wait(&sb.staged[s], (c >> 1) & 1)) {
+          failed = true;
+          sb.abort = 1;
+          break;
         }
-        const uint32_t off = tc::sw128_off32(scol, srow0 + q * 4);
-        *reinterpret_cast<float4*>(th + off) = make_float4(hv[0], hv[1], hv[2], hv[3]);
-        *reinterpret_cast<float4*>(tl + off) = make_float4(lv[0], lv[1], lv[2], lv[3]);
-      }
-    }
-    tc::fence_proxy_async();
-    tc::fence_before_sync();
-    __syncthreads();
-    if (tid == 0) {
-      tc::fence_after_sync();
-      const uint32_t dt = tmem + (uint32_t)(s * GC_T);
-      const uint32_t ah = tc::smem_addr(a_hi), al = tc::smem_addr(a_lo);
-      const uint32_t bh = tc::smem_addr(b_hi), bl = tc::smem_addr(b_lo);
-      // the small terms first, the hi x hi products last (see the A kernel).  lo x lo
-      // is kept: on the diagonal it is a sum of squares, and dropping it would shift
-      // every diagonal entry down by about 1e-7 of itself, which the small eigenvalues
-      // of C (about 1, against a largest one near 1e7) do not tolerate
+        tc::fence_after_sync();
+        unsigned char* st = smem + s * GC_STAGE;
+        const uint32_t dt = tmem + (uint32_t)(s * GC_T);
+        const uint32_t ah = tc::smem_addr(st), al = ah + GC_TILE;
+        const uint32_t bh = diag ? ah : ah + 2 * GC_TILE, bl = diag ? al : ah + 3 * GC_TILE;
+        // the small terms first, the hi x hi products last
 #pragma unroll
-      for (int ks = 0; ks < GC_K / 8; ++ks) {
-        const uint32_t o = ks * 32;
-        tc::mma_tf32(dt, tc::desc_k_sw128(al + o), tc::desc_k_sw128(bl + o), idesc, ks > 0);
-        tc::mma_tf32(dt, tc::desc_k_sw128(al + o), tc::desc_k_sw128(bh + o), idesc, 1u);
-        tc::mma_tf32(dt, tc::desc_k_sw128(ah + o), tc::desc_k_sw128(bl + o), idesc, 1u);
-      }
+        for (int ks = 0; ks < GC_K / 8; ++ks) {
+          const uint32_t o = ks * 32;
+          tc::mma_tf32(dt, tc::desc_k_sw128(al + o), tc::desc_k_sw128(bl + o), idesc, ks > 0);
+          tc::mma_tf32(dt, tc::desc_k_sw128(al + o), tc::desc_k_sw128(bh + o), idesc, 1u);
+          tc::mma_tf32(dt, tc::desc_k_sw128(ah + o), tc::desc_k_sw128(bl + o), idesc, 1u);
+        }
 #pragma unroll
-      for (int ks = 0; ks < GC_K / 8; ++ks) {
-        const uint32_t o = ks * 32;
-        tc::mma_tf32(dt, tc::desc_k_sw128(ah + o), tc::desc_k_sw128(bh + o), idesc, 1u);
+        for (int ks = 0; ks < GC_K / 8; ++ks) {
+          const uint32_t o = ks * 32;
+          tc::mma_tf32(dt, tc::desc_k_sw128(ah + o), tc::desc_k_sw128(bh + o), idesc, 1u);
+        }
+        tc::mma_commit(&sb.done[s]);
       }
-      tc::mma_commit(&sb.mma_done[s]);
+      tc::mma_commit(&sb.fin);
     }
-    if (c >= 1 && !failed) drain(c - 1);
-  }
-  if (!failed && nchunk > 0) drain(nchunk - 1);
-  asm volatile("cp.async.wait_group 0;\n" ::: "memory");
-  // every MMA issued by this CTA completes on `fin` (at once unless a wait failed)
-  if (tid == 0) tc::mma_commit(&sb.fin);
-  if (!tc::mbar_wait(&sb.fin, 0)) failed = true;
-  if (__syncthreads_or(failed)) {
-    if (tid == 0 && status) flag_status(status, ST_TIMEOUT, p);
+    __syncwarp();
   } else {
-    const int np64 = (fpad / GT64) * (fpad / GT64 + 1) / 2;
-    const int row = ti * GC_T + dlane + lane;
+    // ------------------------------------------------ compute warps
+    // raw rows of chunk c into raw buffer c % 2: 16-byte segments, zeros past r1 / fpad
+    auto fetch = [&](int c) {
+      if (c < nchunk) {
+        float* dst = raw + (size_t)(c & 1) * (2 * GC_K * GC_T);
+        const int64_t rb = r0 + (int64_t)c * GC_K;
+        for (int e = tid; e < nblk * GC_K * (GC_T / 4); e += GC_NC) {
+          const int blk = e / (GC_K * (GC_T / 4));
+          const int rr = (e / (GC_T / 4)) % GC_K, seg = e % (GC_T / 4);
+          const int col = (blk == 0 ? ti : tj) * GC_T + seg * 4;
+          const int64_t r = rb + rr;
+          const bool ok = r < r1 && col < fpad;
+          cp_async16z(dst + ((size_t)blk * GC_K + rr) * GC_T + seg * 4,
+                      ok ? (const void*)(F + (size_t)r * fpad + col) : (const void*)F, ok ? 16u : 0u);
+        }
+      }
+      asm volatile("cp.async.commit_group;\n" ::: "memory");
+    };
+    // staging: thread -> column (tid & 127) of the block, rows (tid >> 7) * 16 .. + 15
+    const int scol = tid & (GC_T - 1), srow0 = (tid >> 7) * 16;
+    // read-out: warp -> TMEM lanes 32 (warp % 4) .., columns 64 (warp / 4) .. + 63
+    const int dlane = 32 * (warp & 3), dcol = 64 * (warp >> 2);
+    const uint32_t lane_base = tmem + ((uint32_t)dlane << 16);
+    // add the partial of chunk j (accumulator j % 2) into the TMEM running sums
+    auto drain = [&](int j) {
+      // warp-uniform outcome: the TMEM loads below are warp-collective
+      if (!__all_sync(0xffffffffu, tc::mbar_wait(&sb.done[j & 1], (j >> 1) & 1))) {
+        failed = true;
+        return;
+      }
+      tc::fence_after_sync();
 #pragma unroll
-    for (int j = 0; j < 64; ++j) {
-      const int col = tj * GC_T + dcol + j;
-      if (row >= fpad || col >= fpad || col > row) continue;
-      const int a64 = row / GT64, b64 = col / GT64;
-      const int p64 = a64 * (a64 + 1) / 2 + b64;
-      part[((size_t)sidx * np64 + p64) * GT64 * GT64 + (size_t)(row % GT64) * GT64 + (col % GT64)] =
-          (double)acc_hi[j] + (double)acc_lo[j];
+      for (int g = 0; g < 2; ++g) {
+        const uint32_t col = (uint32_t)(dcol + g * 32);
+        float v[32], hi[32], lo[32];
+        tc::tmem_ld32(lane_base + (uint32_t)((j & 1) * GC_T) + col, v);
+        if (j == 0) {
+#pragma unroll
+          for (int i = 0; i < 32; ++i) {
+            hi[i] = v[i];
+            lo[i] = 0.f;
+          }
+        } else {
+          tc::tmem_ld32(lane_base + 2 * GC_T + col, hi);
+          tc::tmem_ld32(lane_base + 3 * GC_T + col, lo);
+#pragma unroll
+          for (int i = 0; i < 32; ++i) {
+            const float s2 = hi[i] + v[i];
+            const float bb = s2 - hi[i];
+            const float err = (hi[i] - (s2 - bb)) + (v[i] - bb);
+            hi[i] = s2;
+            lo[i] += err;
+          }
+        }
+        tc::tmem_st32(lane_base + 2 * GC_T + col, hi);
+        tc::tmem_st32(lane_base + 3 * GC_T + col, lo);
+      }
+      tc::tmem_st_wait();
+      tc::fence_before_sync();
+    };
+
+    fetch(0);
+    for (int c = 0; c < nchunk; ++c) {
+      const int s = c & 1;
+      unsigned char* st = smem + s * GC_STAGE;
+      unsigned char* a_hi = st;
+      unsigned char* a_lo = st + GC_TILE;
+      unsigned char* b_hi = diag ? a_hi : st + 2 * GC_TILE;
+      unsigned char* b_lo = diag ? a_lo : st + 3 * GC_TILE;
+      asm volatile("cp.async.wait_group 0;\n" ::: "memory");   // raw rows of chunk c
+      // everyone's rows have landed and everyone is past chunk c-1's staging; stage s was
+      // last read by the MMAs of chunk c-2, read out at iteration c-1
+      if (tc::bar_sync_or(1, GC_NC, failed || sb.abort)) {
+        failed = true;
+        break;
+      }
+      fetch(c + 1);
+      const float* rw = raw + (size_t)s * (2 * GC_K * GC_T);
+      for (int blk = 0; blk < nblk; ++blk) {
+        unsigned char* th = blk == 0 ? a_hi : b_hi;
+        unsigned char* tl = blk == 0 ? a_lo : b_lo;
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+          float hv[4], lv[4];
+#pragma unroll
+          for (int u = 0; u < 4; ++u) {
+            const float v = rw[((size_t)blk * GC_K + srow0 + q * 4 + u) * GC_T + scol];
+            hv[u] = tc::to_tf32(v);
+            lv[u] = tc::to_tf32(v - hv[u]);
+          }
+          const uint32_t off = tc::sw128_off32(scol, srow0 + q * 4);
+          *reinterpret_cast<float4*>(th + off) = make_float4(hv[0], hv[1], hv[2], hv[3]);
+          *reinterpret_cast<float4*>(tl + off) = make_float4(lv[0], lv[1], lv[2], lv[3]);
+        }
+      }
+      tc::fence_proxy_async();
+      tc::fence_before_sync();
+      tc::mbar_arrive(&sb.staged[s]);
+      if (c >= 1 && !failed) drain(c - 1);
+    }
+    if (!failed && nchunk > 0) drain(nchunk - 1);
+    asm volatile("cp.async.wait_group 0;\n" ::: "memory");
+    if (!failed) {
+      const int np64 = (fpad / GT64) * (fpad / GT64 + 1) / 2;
+      const int row = ti * GC_T + dlane + lane;
+#pragma unroll
+      for (int g = 0; g < 2; ++g) {
+        float hi[32], lo[32];
+        if (nchunk > 0) {
+          tc::tmem_ld32(lane_base + 2 * GC_T + (uint32_t)(dcol + g * 32), hi);
+          tc::tmem_ld32(lane_base + 3 * GC_T + (uint32_t)(dcol + g * 32), lo);
+        } else {
+#pragma unroll
+          for (int i = 0; i < 32; ++i) hi[i] = lo[i] = 0.f;
+        }
+#pragma unroll
+        for (int i = 0; i < 32; ++i) {
+          const int col = tj * GC_T + dcol + g * 32 + i;
+          if (row >= fpad || col >= fpad || col > row) continue;
+          const int a64 = row / GT64, b64 = col / GT64;
+          const int p64 = a64 * (a64 + 1) / 2 + b64;
+          part[((size_t)sidx * np64 + p64) * GT64 * GT64 + (size_t)(row % GT64) * GT64 + (col % GT64)] =
+              (double)hi[i] + (double)lo[i];
+        }
+      }
     }
   }
+  // every MMA issued by this CTA completes on `fin` (committed by the MMA warp)
+  if (!tc::mbar_wait(&sb.fin, 0)) failed = true;
+  tc::fence_after_sync();
+  if (__syncthreads_or(failed) && tid == 0 && status) flag_status(status, ST_TIMEOUT, p);
   tc::fence_before_sync();
   __syncthreads();
   if (warp == 0) {
     tc::fence_after_sync();
-    tc::tmem_dealloc(tmem, 2 * GC_T);
+    tc::tmem_dealloc(tmem, GC_TMEM_COLS);
   }
 }
 

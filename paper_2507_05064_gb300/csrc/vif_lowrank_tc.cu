@@ -129,7 +129,8 @@ __global__ __launch_bounds__(AT_THREADS, 1) void lowrank_A_tc_kernel(
   bool failed = false;
   // add the partial of chunk j (accumulator j % 2) into acc
   auto drain = [&](int j) {
-    if (!tc::mbar_wait(&sb.done[j & 1], (j >> 1) & 1)) {
+    // warp-uniform outcome: the TMEM loads below are warp-collective
+    if (!__all_sync(0xffffffffu, tc::mbar_wait(&sb.done[j & 1], (j >> 1) & 1))) {
       failed = true;
       return;
     }
