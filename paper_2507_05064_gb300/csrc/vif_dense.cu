@@ -58,7 +58,7 @@ __device__ __forceinline__ double rsqrt_newton(double p) {
 // rank-1 update spread over the CTA.  CTA 0 writes L_kk, CTA b writes X.
 __global__ void chol_panel_kernel(double* A, int m, int lda, int k, int* status, int code) {
   __shared__ double M[2 * NB][NB + 1];
-  __shared__ double rs_c;
+  __shared__ double rs[NB];
   const int k0 = k * NB;
   const bool has_t = blockIdx.x > 0;
   const int rows = has_t ? 2 * NB : NB;
@@ -68,30 +68,35 @@ __global__ void chol_panel_kernel(double* A, int m, int lda, int k, int* status,
     M[r][c] = r < NB ? ((c <= r) ? ld_lower(A, lda, m, k0 + r, k0 + c) : 0.0)
                      : ld_lower(A, lda, m, r0 + r - NB, k0 + c);
   }
+  // pivot c: M[c][c] <- sqrt(p), rs[c] <- 1/sqrt(p)
+  auto pivot = [&](int c) {
+    double p = M[c][c];
+    if (!(p > 0.0)) {
+      if (blockIdx.x == 0 && status) flag_status(status, code, k0 + c);
+      p = nan("");
+    }
+    const double y = rsqrt_newton(p);
+    M[c][c] = p * y;
+    rs[c] = y;
+  };
+  __syncthreads();
+  if (threadIdx.x == 0) pivot(0);
   __syncthreads();
   for (int c = 0; c < NB; ++c) {
-    if (threadIdx.x == 0) {
-      double p = M[c][c];
-      if (!(p > 0.0)) {
-        if (blockIdx.x == 0 && status) flag_status(status, code, k0 + c);
-        p = nan("");
-      }
-      const double y = rsqrt_newton(p);
-      M[c][c] = p * y;
-      rs_c = y;
-    }
-    __syncthreads();
-    const double y = rs_c;
+    const double y = rs[c];
     // column c below the pivot: rows c+1..NB-1 of L_kk and all rows of T_b
     const int ncol = rows - (c + 1);
     for (int t = threadIdx.x; t < ncol; t += blockDim.x) M[c + 1 + t][c] *= y;
     __syncthreads();
-    // rank-1 update of the trailing columns c+1..NB-1 (lower part of L_kk, all of T_b)
+    // rank-1 update of the trailing columns c+1..NB-1 (lower part of L_kk, all of T_b);
+    // element (c+1, c+1) is thread 0's first, so thread 0 then forms the next pivot while
+    // the others finish the update (two barriers per column)
     const int w = NB - c - 1;
     for (int idx = threadIdx.x; idx < ncol * w; idx += blockDim.x) {
       const int r = c + 1 + idx / w, s2 = c + 1 + idx % w;
       if (r >= NB || s2 <= r) M[r][s2] -= M[r][c] * M[s2][c];
     }
+    if (threadIdx.x == 0 && c + 1 < NB) pivot(c + 1);
     __syncthreads();
   }
   if (!has_t) {
