@@ -46,6 +46,7 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-laplace", action="store_true")
     ap.add_argument("--laplace-n", type=int, default=200_000)
+    ap.add_argument("--no-small", action="store_true", help="skip the C1/C2 block")
     ap.add_argument("--batch", type=int, default=0,
                     help="also time N independent C5-style problems per CUDA graph replay (0: skip)")
     return ap.parse_args()
@@ -159,7 +160,13 @@ def launches_per_eval(m):
 
 # DRAM bytes per point of a kernel, from one ncu capture of the kernel as it stands
 # (dram__bytes_read.sum + dram__bytes_write.sum at n = 100,000; traffic grows with n).
-NCU_DRAM_BYTES_PER_POINT = {}
+NCU_DRAM_BYTES_PER_POINT = {
+    # factor_kernel<float, 3> at commit 0b484a5 (unchanged since f9d5560): 379.6 MB read +
+    # 203.2 MB written for 100,000 points
+    "vecchia_factor": ((379.561472 + 203.194368) * 1e6 / 100_000,
+                       "ncu dram__bytes_read.sum + dram__bytes_write.sum, factor_kernel<float, 3>, n = 100,000, "
+                       "profiles/tc_A_factor_gram_n100k.md"),
+}
 
 
 def cpu_baseline(P, n_s, steps=1):
@@ -183,6 +190,55 @@ def cpu_baseline(P, n_s, steps=1):
     return {"value": 1.0 / (t * n / n_s), "unit": UNIT, "cores": os.cpu_count(), "kind": "oracle",
             "sample": f"oracle NLL on the first {n_s} of {n} points (m={P.Z.shape[0]}, m_v={P.mv}, d=8), "
                       f"{t:.2f} s per sample eval, scaled by n/{n_s}"}
+
+
+def small_configs_block(stream):
+    """C2 (n = 100k, d = 2, Matern-5/2, m = 200, m_v = 30): NLL evals/s mixed and FP64 and their
+    agreement; C1 (n = 2000, d = 2, Matern-3/2, m = 50, m_v = 10): latency of one NLL (both
+    paths), one NLL with gradient and one prediction of 500 points.  Device-synchronised wall
+    clock around the C-ABI calls, medians of repeated calls."""
+    import torch
+    from paper_2507_05064_gb300 import synth
+    from paper_2507_05064_gb300 import vif as V
+
+    def med_ms(fn, reps):
+        fn()
+        ts = []
+        for _ in range(reps):
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            fn()
+            torch.cuda.synchronize()
+            ts.append((time.perf_counter() - t0) * 1000.0)
+        return statistics.median(ts)
+
+    out = {}
+    P = synth.config2()
+    c32 = V.Context(P.X, P.Z, P.mv, P.theta, precision=V.MIXED, stream=stream.cuda_stream)
+    c64 = V.Context(P.X, P.Z, P.mv, P.theta, precision=V.FP64, stream=stream.cuda_stream, neighbor_search=False)
+    c64.set_neighbors(c32.neighbors())
+    y = torch.from_numpy(P.y).cuda()
+    t32 = med_ms(lambda: c32.nll(P.theta, y), 20)
+    t64 = med_ms(lambda: c64.nll(P.theta, y), 5)
+    a, b = c32.nll(P.theta, y), c64.nll(P.theta, y)
+    out["c2"] = {"workload": "vif-nll-matern52-n100000-d2-m200-mv30", "mixed_evals_per_s": 1000.0 / t32,
+                 "fp64_evals_per_s": 1000.0 / t64, "nll_mixed": a, "nll_fp64": b,
+                 "rel_err_scale": abs(a - b) / max(abs(b), 0.5 * P.X.shape[0] * math.log(2 * math.pi))}
+    c32.close()
+    c64.close()
+    P = synth.config1()
+    c32 = V.Context(P.X, P.Z, P.mv, P.theta, precision=V.MIXED, stream=stream.cuda_stream)
+    c64 = V.Context(P.X, P.Z, P.mv, P.theta, precision=V.FP64, stream=stream.cuda_stream)
+    y = P.y
+    out["c1"] = {"workload": "matern32-n2000-d2-m50-mv10",
+                 "nll_ms_mixed": med_ms(lambda: c32.nll(P.theta, y), 20),
+                 "nll_ms_fp64": med_ms(lambda: c64.nll(P.theta, y), 20),
+                 "nll_grad_ms_fp64": med_ms(lambda: c64.nll(P.theta, y, grad=True), 5),
+                 "predict_500_ms_fp64": med_ms(lambda: c64.predict(P.theta, y, P.Xp), 10),
+                 "timing": "host y and outputs, synchronised wall clock, median"}
+    c32.close()
+    c64.close()
+    return out
 
 
 def batch_block(args, stream):
@@ -369,6 +425,7 @@ def run_vif(args, rank, world, dist):
     if not args.no_laplace:
         lap = laplace_block(args, stream)
     bat = batch_block(args, stream) if args.batch > 0 else None
+    small = None if args.no_small else small_configs_block(stream)
     cb = None
     if not args.no_cpu_baseline:
         cb = cpu_baseline(P, min(args.cpu_sample, P.X.shape[0]))
@@ -388,6 +445,7 @@ def run_vif(args, rank, world, dist):
         "roofline": roof,
         "laplace": lap,
         "batch": bat,
+        "small_configs": small,
         "cpu_baseline": cb,
         "e2e": {"value": world * 1000.0 / e2e_ms, "unit": UNIT, "ms_per_step": e2e_ms,
                 "h2d_bytes_per_step": int(P.y.nbytes) + 256, "d2h_bytes_per_step": 16 + 24},
