@@ -51,14 +51,16 @@ struct vif_ctx {
   // Laplace buffers (allocated on the first vif_laplace_mode call)
   bool lap_ready = false;
   int32_t *ch_ptr = nullptr, *ch_row = nullptr, *ch_slot = nullptr;
+  int4 *sched_fwd = nullptr, *sched_rev = nullptr;      // level schedules of B^{-1} and B^{-T}
+  int64_t nsteps_fwd = 0, nsteps_rev = 0, ch_nnz = 0;
+  double* ch_coef = nullptr;                            // coefficient of each child term
   double *l_b = nullptr, *l_W = nullptr, *l_v = nullptr, *l_Ginv = nullptr, *l_om = nullptr, *l_rsD = nullptr,
          *l_ll = nullptr, *l_x = nullptr, *l_r = nullptr, *l_z = nullptr, *l_p = nullptr, *l_Ap = nullptr,
          *l_t = nullptr, *l_t2 = nullptr, *l_x1 = nullptr, *l_sdi = nullptr, *l_sm = nullptr, *l_cm = nullptr,
          *l_tm = nullptr, *l_part = nullptr, *l_LinvC = nullptr, *l_G3 = nullptr, *l_LinvC3 = nullptr,
          *l_sc = nullptr, *l_red = nullptr, *l_corr = nullptr;
-  int *l_flags = nullptr, *l_counter = nullptr, *l_abort = nullptr;
+  int *l_counter = nullptr, *l_abort = nullptr;
   float *m_feat = nullptr, *m_gc = nullptr, *m_part = nullptr, *m_grad = nullptr;
-  int lap_epoch = 0;
   int64_t knn_rescored = 0, knn_fallback = 0;
   bool have_factors = false;
   bool timing = false;
@@ -275,7 +277,7 @@ void free_ctx(vif_ctx* c) {
                    c->ch_slot, c->l_b,  c->l_W,    c->l_v,    c->l_Ginv, c->l_om,   c->l_rsD,  c->l_ll,
                    c->l_x,    c->l_r,   c->l_z,    c->l_p,    c->l_Ap,   c->l_t,    c->l_t2,   c->l_x1,
                    c->l_sdi,  c->l_sm,  c->l_cm,   c->l_tm,   c->l_part, c->l_LinvC, c->l_G3,  c->l_LinvC3,
-                   c->l_sc,   c->l_red, c->l_corr, c->l_flags, c->l_counter, c->l_abort, c->m_feat,
+                   c->l_sc,   c->l_red, c->l_corr, c->sched_fwd, c->sched_rev, c->ch_coef, c->l_counter, c->l_abort, c->m_feat,
                    c->m_gc,   c->m_part, c->m_grad};
   for (void* b : pbufs)
     if (b) cudaFree(b);
@@ -452,9 +454,48 @@ vif_status fp64_buffers(vif_ctx* ctx, double** A64, double** F64, double** LT64)
 
 
 // Children lists of the neighbour DAG (the transpose of N, by column), for B^T.
+// Slots {row, first term, end of terms, solo} of a sync-free triangular solve, rows
+// ordered by level: level[r] is 0 for a row that reads no other row, else one more
+// than the deepest row it reads.  Within a level, rows with more than TRSV_SOLO_TERMS
+// terms get a step of their own (four copies of their slot, solo = 1: the whole warp on
+// one row); the others fill steps of LAP_TRSV_RPS rows, the level padded with
+// {-1, 0, 0, 0}, so the rows of one step never read one another.
+constexpr int TRSV_SOLO_TERMS = 24;
+static std::vector<int4> level_schedule(const std::vector<int32_t>& level, const std::vector<int32_t>& first,
+                                        const std::vector<int32_t>& count, bool allow_solo) {
+  int32_t nlev = 0;
+  for (int32_t l : level) nlev = std::max(nlev, l + 1);
+  auto solo = [&](size_t r) { return allow_solo && count[r] > TRSV_SOLO_TERMS; };
+  std::vector<int64_t> cnt((size_t)nlev, 0), nsolo((size_t)nlev, 0);
+  for (size_t r = 0; r < level.size(); ++r) (solo(r) ? nsolo : cnt)[(size_t)level[r]]++;
+  std::vector<int64_t> start((size_t)nlev + 1, 0), split((size_t)nlev, 0);
+  for (int32_t l = 0; l < nlev; ++l) {
+    split[(size_t)l] = start[(size_t)l] + nsolo[(size_t)l] * LAP_TRSV_RPS;
+    const int64_t padded = (cnt[(size_t)l] + LAP_TRSV_RPS - 1) / LAP_TRSV_RPS * LAP_TRSV_RPS;
+    start[(size_t)l + 1] = split[(size_t)l] + padded;
+  }
+  std::vector<int4> sched((size_t)std::max<int64_t>(start[(size_t)nlev], LAP_TRSV_RPS), make_int4(-1, 0, 0, 0));
+  std::vector<int64_t> fs(start.begin(), start.end() - 1), fr(split);
+  for (size_t r = 0; r < level.size(); ++r) {
+    const size_t l = (size_t)level[r];
+    const int4 slot = make_int4((int)r, first[r], first[r] + count[r], solo(r) ? 1 : 0);
+    if (solo(r)) {
+      for (int k = 0; k < LAP_TRSV_RPS; ++k) sched[(size_t)fs[l] + k] = slot;
+      fs[l] += LAP_TRSV_RPS;
+    } else {
+      sched[(size_t)fr[l]++] = slot;
+    }
+  }
+  return sched;
+}
+
+// Children lists of B (CSR over the rows that name j as a neighbour) and the level
+// schedules of the two triangular solves, from the neighbour sets.
 vif_status build_children(vif_ctx* ctx) {
   const int64_t n = ctx->n;
   const int mv = ctx->mv;
+  if (n * std::max(mv, 1) >= ((int64_t)1 << 31))
+    return set_err(ctx, VIF_ERR_ARG, "n * m_v must stay below 2^31 for the Laplace solves");
   std::vector<int32_t> N((size_t)n * std::max(mv, 1), -1);
   if (mv > 0) {
     CK(cudaMemcpyAsync(N.data(), ctx->N, (size_t)n * mv * sizeof(int32_t), cudaMemcpyDeviceToHost, ctx->stream));
@@ -479,24 +520,63 @@ vif_status build_children(vif_ctx* ctx) {
         fill[j]++;
       }
     }
+  // B^{-1}: row i reads its neighbours (all earlier); B^{-T}: row j reads its children (all later)
+  std::vector<int32_t> lev((size_t)n, 0), rlev((size_t)n, 0);
+  for (int64_t i = 0; i < n; ++i) {
+    const int q = (int)std::min<int64_t>(i, mv);
+    int32_t l = 0;
+    for (int t = 0; t < q; ++t) {
+      const int j = N[(size_t)i * mv + t];
+      // the solves read row j while computing row i: it must be an earlier row
+      if (j < 0 || j >= i) return set_err(ctx, VIF_ERR_ARG, "neighbour %d of row %lld is not a predecessor", j,
+                                          (long long)i);
+      l = std::max(l, lev[j] + 1);
+    }
+    lev[i] = l;
+  }
+  for (int64_t j = n - 1; j >= 0; --j) {
+    int32_t l = 0;
+    for (int32_t p = ptr[j]; p < ptr[j + 1]; ++p)
+      if (row[p] > j) l = std::max(l, rlev[row[p]] + 1);
+    rlev[j] = l;
+  }
+  // terms: row i of B^{-1} reads N[i m_v + k], k < min(i, m_v); row j of B^{-T} its children
+  std::vector<int32_t> f_first((size_t)n), f_cnt((size_t)n), r_cnt((size_t)n);
+  for (int64_t i = 0; i < n; ++i) {
+    f_first[(size_t)i] = (int32_t)(i * mv);
+    f_cnt[(size_t)i] = (int32_t)std::min<int64_t>(i, mv);
+    r_cnt[(size_t)i] = ptr[i + 1] - ptr[i];
+  }
+  const std::vector<int4> sf = level_schedule(lev, f_first, f_cnt, false);
+  const std::vector<int4> sr = level_schedule(rlev, std::vector<int32_t>(ptr.begin(), ptr.end() - 1), r_cnt, true);
   if (!ctx->ch_ptr) {
     CKS(dalloc(ctx, &ctx->ch_ptr, (size_t)n + 1));
   }
-  if (ctx->ch_row) cudaFree(ctx->ch_row);
-  if (ctx->ch_slot) cudaFree(ctx->ch_slot);
+  void* owned[] = {ctx->ch_row, ctx->ch_slot, ctx->sched_fwd, ctx->sched_rev, ctx->ch_coef};
+  for (void* b : owned)
+    if (b) cudaFree(b);
   ctx->ch_row = ctx->ch_slot = nullptr;
+  ctx->sched_fwd = ctx->sched_rev = nullptr;
+  ctx->ch_coef = nullptr;
   CKS(dalloc(ctx, &ctx->ch_row, (size_t)std::max<int64_t>(nnz, 1)));
   CKS(dalloc(ctx, &ctx->ch_slot, (size_t)std::max<int64_t>(nnz, 1)));
+  CKS(dalloc(ctx, &ctx->sched_fwd, sf.size()));
+  CKS(dalloc(ctx, &ctx->sched_rev, sr.size()));
+  CKS(dalloc(ctx, &ctx->ch_coef, (size_t)std::max<int64_t>(nnz, 1)));
+  ctx->ch_nnz = nnz;
+  ctx->nsteps_fwd = (int64_t)(sf.size() / LAP_TRSV_RPS);
+  ctx->nsteps_rev = (int64_t)(sr.size() / LAP_TRSV_RPS);
   CK(cudaMemcpy(ctx->ch_ptr, ptr.data(), (n + 1) * sizeof(int32_t), cudaMemcpyHostToDevice));
   CK(cudaMemcpy(ctx->ch_row, row.data(), row.size() * sizeof(int32_t), cudaMemcpyHostToDevice));
   CK(cudaMemcpy(ctx->ch_slot, slot.data(), slot.size() * sizeof(int32_t), cudaMemcpyHostToDevice));
+  CK(cudaMemcpy(ctx->sched_fwd, sf.data(), sf.size() * sizeof(int4), cudaMemcpyHostToDevice));
+  CK(cudaMemcpy(ctx->sched_rev, sr.data(), sr.size() * sizeof(int4), cudaMemcpyHostToDevice));
   return VIF_OK;
 }
 
 vif_status lap_alloc(vif_ctx* ctx) {
   if (ctx->lap_ready) return VIF_OK;
   const int64_t n = ctx->n;
-  const size_t nb = (size_t)((n + 255) / 256);
   double** vecs[] = {&ctx->l_b, &ctx->l_W,  &ctx->l_v,  &ctx->l_Ginv, &ctx->l_om, &ctx->l_rsD, &ctx->l_ll,
                      &ctx->l_x, &ctx->l_r,  &ctx->l_z,  &ctx->l_p,    &ctx->l_Ap, &ctx->l_t,   &ctx->l_t2,
                      &ctx->l_x1, &ctx->l_sdi, &ctx->l_corr};
@@ -504,16 +584,14 @@ vif_status lap_alloc(vif_ctx* ctx) {
   CKS(dalloc(ctx, &ctx->l_sm, (size_t)ctx->fpad));
   CKS(dalloc(ctx, &ctx->l_cm, (size_t)ctx->fpad));
   CKS(dalloc(ctx, &ctx->l_tm, (size_t)ctx->fpad));
-  CKS(dalloc(ctx, &ctx->l_part, nb * ctx->fpad));
+  CKS(dalloc(ctx, &ctx->l_part, (size_t)LAP_FT_BLOCKS * ctx->fpad));
   CKS(dalloc(ctx, &ctx->l_LinvC, (size_t)std::max(ctx->m, 1) * ctx->fpad));
   CKS(dalloc(ctx, &ctx->l_G3, (size_t)(ctx->m + 1) * ctx->fpad));
   CKS(dalloc(ctx, &ctx->l_LinvC3, (size_t)std::max(ctx->m, 1) * ctx->fpad));
   CKS(dalloc(ctx, &ctx->l_sc, 16));
   CKS(dalloc(ctx, &ctx->l_red, 256));
-  CKS(dalloc(ctx, &ctx->l_flags, (size_t)n));
   CKS(dalloc(ctx, &ctx->l_counter, 4));
   CKS(dalloc(ctx, &ctx->l_abort, 1));
-  CK(cudaMemsetAsync(ctx->l_flags, 0, (size_t)n * sizeof(int), ctx->stream));
   CK(cudaMemsetAsync(ctx->l_sm, 0, ctx->fpad * sizeof(double), ctx->stream));
   CK(cudaMemsetAsync(ctx->l_cm, 0, ctx->fpad * sizeof(double), ctx->stream));
   CK(cudaMemsetAsync(ctx->l_G3, 0, (size_t)(ctx->m + 1) * ctx->fpad * sizeof(double), ctx->stream));
@@ -830,10 +908,16 @@ vif_status lap_setup(vif_ctx* ctx, const vif_cov* theta, const double* y, LapOps
   o->cm = ctx->l_cm;
   o->tmpm = ctx->l_tm;
   o->partial = ctx->l_part;
-  o->flags = ctx->l_flags;
+  o->sched_fwd = ctx->sched_fwd;
+  o->sched_rev = ctx->sched_rev;
+  o->nsteps_fwd = ctx->nsteps_fwd;
+  o->nsteps_rev = ctx->nsteps_rev;
+  o->ch_coef = ctx->ch_coef;
+  o->nnz = ctx->ch_nnz;
   o->counter = ctx->l_counter;
   o->abort_flag = ctx->l_abort;
   o->status = ctx->status;
+  CK(lap_child_coef(*o, ctx->ch_coef, s));   // the children's coefficients of the new A
   return VIF_OK;
 }
 
@@ -855,7 +939,7 @@ vif_status lap_pcg(vif_ctx* ctx, const LapOps& o, double tol, int max_it, int* i
   CK(cudaMemsetAsync(ctx->l_x, 0, n * sizeof(double), s));
   CK(cudaMemcpyAsync(ctx->l_r, ctx->l_v, n * sizeof(double), cudaMemcpyDeviceToDevice, s));
   CK(lap_dot(ctx->l_v, ctx->l_v, n, ctx->l_red, sc + 6, s));
-  CK(lap_precond(o, ctx->l_r, ctx->l_z, &ctx->lap_epoch, s));
+  CK(lap_precond(o, ctx->l_r, ctx->l_z, s));
   CK(cudaMemcpyAsync(ctx->l_p, ctx->l_z, n * sizeof(double), cudaMemcpyDeviceToDevice, s));
   CK(lap_dot(ctx->l_r, ctx->l_z, n, ctx->l_red, sc + 0, s));
   CK(cudaMemcpyAsync(ctx->h_pin + 8, sc + 6, sizeof(double), cudaMemcpyDeviceToHost, s));
@@ -878,7 +962,7 @@ vif_status lap_pcg(vif_ctx* ctx, const LapOps& o, double tol, int max_it, int* i
       *rel = std::sqrt(ctx->h_pin[8]) / vnorm;
       if (reinterpret_cast<const int*>(ctx->h_pin + 9)[0] != ST_OK) break;
       if (*rel <= tol) break;
-      CK(lap_precond(o, ctx->l_r, ctx->l_z, &ctx->lap_epoch, s));
+      CK(lap_precond(o, ctx->l_r, ctx->l_z, s));
       CK(lap_dot(ctx->l_r, ctx->l_z, n, ctx->l_red, sc + 4, s));
       CK(lap_beta(sc, s));
       CK(lap_axpy(n, sc + 5, ctx->l_z, nullptr, ctx->l_p, 2, s));
@@ -1107,14 +1191,14 @@ vif_status vif_mlp_train(vif_ctx* ctx, const vif_cov* theta, const double* y, co
         // z -> l_x, A z -> l_r, u = P^-1 A z -> l_z, r = u - z -> l_p, s = P^-1 r -> l_Ap
         CK(mlp_rademacher(to->seed * 0x9E3779B97F4A7C15ull + (++probe_ctr), n, ctx->l_x, s));
         CK(lap_matvec(o, ctx->l_x, ctx->l_W, ctx->l_r, s));
-        CK(lap_precond(o, ctx->l_r, ctx->l_z, &ctx->lap_epoch, s));
+        CK(lap_precond(o, ctx->l_r, ctx->l_z, s));
         {
           // r = u - z: l_p = l_z - 1 * l_x
           double one = 1.0;
           CK(cudaMemcpyAsync(sc + 11, &one, sizeof(double), cudaMemcpyHostToDevice, s));
           CK(lap_axpy(n, sc + 11, ctx->l_z, ctx->l_x, ctx->l_p, 1, s));
         }
-        CK(lap_precond(o, ctx->l_p, ctx->l_Ap, &ctx->lap_epoch, s));
+        CK(lap_precond(o, ctx->l_p, ctx->l_Ap, s));
         CK(mlp_lp_grad(ctx->N, ctx->Acoef, n, ctx->mv, ctx->l_Ap, ctx->l_z, ctx->l_W, ctx->l_corr, coeff, ctx->m_gc,
                        s));
         CK(lap_dot(ctx->l_p, ctx->l_p, n, ctx->l_red, sc + 9, s));

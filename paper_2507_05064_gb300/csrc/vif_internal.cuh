@@ -161,19 +161,30 @@ cudaError_t predict_all(const double* A, const double* Xs, int64_t n, const doub
                         cudaStream_t s);
 
 // vif_laplace.cu
+// rows of the level schedules of the two triangular solves are taken four at a time
+// (slots {row, first term, end of terms, solo}); each level is padded with
+// {-1, 0, 0, 0} to a multiple of this
+constexpr int LAP_TRSV_RPS = 4;
+// row slices of the F^T v product (partial buffer: LAP_FT_BLOCKS x fpad)
+constexpr int LAP_FT_BLOCKS = 608;
 struct LapOps {
   int64_t n;
   int m, mv, fpad, ldl;
   const int32_t *N, *ch_ptr, *ch_row, *ch_slot;
+  const int4 *sched_fwd, *sched_rev;      // level-ordered slots of B^{-1} / B^{-T}
+  int64_t nsteps_fwd, nsteps_rev;         // schedule lengths / LAP_TRSV_RPS
+  const double* ch_coef;                  // A_i[k] of each child term, CSR order (lap_child_coef)
+  int64_t nnz;                            // child terms
   const double *Acoef, *F, *LinvC, *LinvC3;
   double *rsD, *Ginv;          // 1/sqrt(D_i), 1/(W'_i + 1/D_i)
   double *t, *t2, *x1;         // n-vector scratch
   double *sm, *cm, *tmpm;      // m-vector scratch
-  double* partial;             // ceil(n/256) x fpad
-  int *flags, *counter, *abort_flag, *status;
+  double* partial;             // LAP_FT_BLOCKS x fpad
+  int *counter, *abort_flag, *status;   // counter: two 64-bit work-queue counters
 };
 cudaError_t lap_matvec(const LapOps& o, const double* x, const double* diagW, double* out, cudaStream_t s);
-cudaError_t lap_precond(const LapOps& o, const double* w, double* out, int* epoch, cudaStream_t s);
+cudaError_t lap_precond(const LapOps& o, const double* w, double* out, cudaStream_t s);
+cudaError_t lap_child_coef(const LapOps& o, double* ch_coef, cudaStream_t s);
 cudaError_t lap_pointwise(const double* y, const double* b, const double* D, const double* corr, int64_t n, double* W,
                           double* v, double* Ginv, double* omega, double* rsD, double* ll, cudaStream_t s);
 cudaError_t lap_dot(const double* a, const double* b, int64_t n, double* partial, double* out, cudaStream_t s);

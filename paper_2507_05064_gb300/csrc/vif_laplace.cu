@@ -10,152 +10,246 @@
 // L_m^{-1} M_3 L_m^{-T} for the M_3 of App. E.1.  A learned diagonal correction
 // replaces W by W' = W exp(c) inside P only (the system keeps W).
 //
-// The triangular solves with B and B^T are sync-free: warps take rows from an
-// atomic work queue in dependency order and wait for the rows they need through
-// per-row epoch flags (release/acquire).  Every wait is bounded; a wait that runs
-// out sets an abort flag that ends all waits, and the host reports
-// VIF_ERR_TIMEOUT.
+// The triangular solves with B and B^T are sync-free: rows are ordered by level (a
+// row's level is one more than the deepest row it reads), grouped in steps of four
+// rows of one level (eight lanes per row; one row with many terms gets the whole
+// warp), and the steps are dealt round-robin to the warps of a cooperative launch.
+// The output vector is filled with an all-ones bit pattern (a NaN that no arithmetic
+// result takes) before the solve; a row reads its inputs by polling their values
+// until they differ from that pattern, so the value is its own ready flag and no
+// separate flag or fence is needed.  Every wait is bounded; a wait that runs out sets
+// an abort flag that ends all waits, and the host reports VIF_ERR_TIMEOUT.
 #include "vif_internal.cuh"
 
 namespace vif {
 
 constexpr int SPIN_LIMIT = 1 << 22;
+constexpr unsigned long long TR_PENDING = ~0ull;
 
-__device__ __forceinline__ int ld_acquire(const int* p) {
-  int v;
-  asm volatile("ld.acquire.gpu.global.b32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+__device__ __forceinline__ int ld_volatile(const int* p) { return *(volatile const int*)p; }
+__device__ __forceinline__ unsigned long long ld_relaxed_u64(const double* p) {
+  unsigned long long v;
+  asm volatile("ld.relaxed.gpu.global.b64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
   return v;
 }
-__device__ __forceinline__ void st_release(int* p, int v) {
-  asm volatile("st.release.gpu.global.b32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
-}
-__device__ __forceinline__ int ld_volatile(const int* p) { return *(volatile const int*)p; }
-
-// Wait until flags[j] == epoch (or abort).  Returns false on abort/timeout.
-__device__ __forceinline__ bool wait_ready(const int* flags, int64_t j, int epoch, int* abort_flag, int* status,
-                                           int64_t row) {
-  int it = 0;
-  while (ld_acquire(flags + j) != epoch) {
-    if (ld_volatile(abort_flag)) return false;
-    if (++it > SPIN_LIMIT) {
-      atomicExch(abort_flag, 1);
-      flag_status(status, ST_TIMEOUT, row);
-      return false;
-    }
-  }
-  return true;
+__device__ __forceinline__ void st_relaxed_f64(double* p, double v) {
+  unsigned long long b = (unsigned long long)__double_as_longlong(v);
+  if (b == TR_PENDING) b = 0x7FF8000000000000ull;   // never publish the pending pattern
+  asm volatile("st.relaxed.gpu.global.b64 [%0], %1;" ::"l"(p), "l"(b) : "memory");
 }
 
-// out = B^{-1} rhs:  out_i = rhs_i + sum_k A_i[k] out_{N_k}  (rows in increasing order)
-__global__ void sptrsv_B_kernel(const int32_t* __restrict__ N, const double* __restrict__ Acoef, int64_t n, int mv,
-                                const double* __restrict__ rhs, double* out, int* flags, int epoch, int* counter,
-                                int* abort_flag, int* status) {
-  const int lane = threadIdx.x & 31;
-  while (true) {
-    int64_t row = 0;
-    if (lane == 0) row = atomicAdd(reinterpret_cast<unsigned long long*>(counter), 1ull);
-    row = __shfl_sync(0xffffffffu, row, 0);
-    if (row >= n) return;
-    const int q = (int)(row < mv ? row : mv);
-    double s = 0.0;
-    bool ok = true;
-    for (int t = lane; t < q; t += 32) {
-      const int j = N[(size_t)row * mv + t];
-      if (!wait_ready(flags, j, epoch, abort_flag, status, row)) {
-        ok = false;
-        break;
+// Value of *p once it has been written (NaN after an abort or a timeout).  Polls are
+// back to back: a row's inputs land one L2 round trip apart at best, and backing off
+// only lengthens the chain of levels (measured: 1.37 us per level of a pure chain with
+// back-to-back polls, 2.06 us with a 64-512 ns backoff).
+__device__ __noinline__ double wait_value(const double* p, int* abort_flag, int* status, int64_t row) {
+  for (int it = 1;; ++it) {
+    const unsigned long long b = ld_relaxed_u64(p);
+    if (b != TR_PENDING) return __longlong_as_double((long long)b);
+    if ((it & 63) == 0) {
+      if (ld_volatile(abort_flag)) return NAN;
+      if (it > SPIN_LIMIT) {
+        atomicExch(abort_flag, 1);
+        flag_status(status, ST_TIMEOUT, row);
+        return NAN;
       }
-      s += Acoef[(size_t)row * mv + t] * __ldcg(out + j);
-    }
-    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
-    (void)__all_sync(0xffffffffu, ok);
-    if (lane == 0) {
-      out[row] = rhs[row] + s;
-      __threadfence();
-      st_release(flags + row, epoch);   // released even after an abort, so nobody waits on this row
     }
   }
 }
 
-// x = B^{-T} w:  x_j = w_j + sum_{(i,k): N_k(i) = j} A_i[k] x_i  (rows in decreasing order)
-__global__ void sptrsv_Bt_kernel(const int32_t* __restrict__ ch_ptr, const int32_t* __restrict__ ch_row,
-                                 const int32_t* __restrict__ ch_slot, const double* __restrict__ Acoef, int64_t n,
-                                 int mv, const double* __restrict__ w, double* x, int* flags, int epoch, int* counter,
-                                 int* abort_flag, int* status) {
-  const int lane = threadIdx.x & 31;
-  while (true) {
-    int64_t k = 0;
-    if (lane == 0) k = atomicAdd(reinterpret_cast<unsigned long long*>(counter), 1ull);
-    k = __shfl_sync(0xffffffffu, k, 0);
-    if (k >= n) return;
-    const int64_t row = n - 1 - k;
-    const int b = ch_ptr[row], e = ch_ptr[row + 1];
-    double s = 0.0;
-    bool ok = true;
-    for (int t = b + lane; t < e; t += 32) {
-      const int i = ch_row[t];
-      if (!wait_ready(flags, i, epoch, abort_flag, status, row)) {
-        ok = false;
-        break;
-      }
-      s += Acoef[(size_t)i * mv + ch_slot[t]] * __ldcg(x + i);
-    }
-    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
-    (void)__all_sync(0xffffffffu, ok);
-    if (lane == 0) {
-      x[row] = w[row] + s;
-      __threadfence();
-      st_release(flags + row, epoch);
+// A step is four rows of one level, eight lanes per row, or (a "solo" step) one row
+// with many terms and all 32 lanes; a schedule slot is {row, first term, end of
+// terms, solo}, the four slots of a solo step all naming its row, padding slots
+// {-1, 0, 0, 0}.  Lane `sub` of a row owns the terms sub, sub + lanes, ... of the
+// row's sum  sum_t coef[t] * out[idx[t]].
+constexpr int TR_LPR = 8;                  // lanes per row
+constexpr int TR_RPS = 32 / TR_LPR;        // rows per warp step
+static_assert(TR_RPS == LAP_TRSV_RPS, "schedule padding and rows per step differ");
+constexpr int TR_MAXV = 6;                 // terms in flight per lane
+
+struct TrsvTerms {
+  int row, b, e, lanes, sub;
+  bool solo;
+  double rhs;
+  int j[TR_MAXV];
+  double c[TR_MAXV];
+};
+
+// issue the loads of a step's first TR_MAXV terms per lane and of its right-hand side
+__device__ __forceinline__ void trsv_issue(TrsvTerms& T, int4 sl, int lane, const int32_t* __restrict__ idx,
+                                           const double* __restrict__ coef, const double* __restrict__ rhs) {
+  T.row = sl.x;
+  T.b = sl.y;
+  T.e = sl.z;
+  T.solo = sl.w != 0;
+  T.lanes = T.solo ? 32 : TR_LPR;
+  T.sub = T.solo ? lane : lane % TR_LPR;
+  T.rhs = (T.row >= 0 && T.sub == 0) ? rhs[T.row] : 0.0;
+#pragma unroll
+  for (int u = 0; u < TR_MAXV; ++u) {
+    const int t = T.b + T.sub + u * T.lanes;
+    T.j[u] = -1;
+    T.c[u] = 0.0;
+    if (t < T.e) {
+      T.j[u] = idx[t];
+      T.c[u] = coef[t];
     }
   }
 }
 
-// t_i = (x_i - sum_k A_i[k] x_{N_k}) / sqrt(D_i)
+// the row sum of a step whose first terms were issued by trsv_issue (all lanes of the
+// warp take part: the partial sums are added by shuffles)
+__device__ __forceinline__ double trsv_finish(const TrsvTerms& T, const int32_t* __restrict__ idx,
+                                              const double* __restrict__ coef, const double* out, int* abort_flag,
+                                              int* status) {
+  double s = 0.0;
+  unsigned long long v[TR_MAXV];
+#pragma unroll
+  for (int u = 0; u < TR_MAXV; ++u)
+    if (T.j[u] >= 0) v[u] = ld_relaxed_u64(out + T.j[u]);
+#pragma unroll
+  for (int u = 0; u < TR_MAXV; ++u) {
+    if (T.j[u] >= 0) {
+      double x = __longlong_as_double((long long)v[u]);
+      if (v[u] == TR_PENDING) x = wait_value(out + T.j[u], abort_flag, status, T.row);
+      s = fma(T.c[u], x, s);
+    }
+  }
+  // rows with more than lanes * TR_MAXV terms: further passes, one term per lane at a time
+  for (int t = T.b + T.sub + TR_MAXV * T.lanes; t < T.e; t += T.lanes) {
+    const int j = idx[t];
+    const unsigned long long b = ld_relaxed_u64(out + j);
+    const double x = b == TR_PENDING ? wait_value(out + j, abort_flag, status, T.row)
+                                     : __longlong_as_double((long long)b);
+    s = fma(coef[t], x, s);
+  }
+  if (T.solo) {
+    s += __shfl_xor_sync(0xffffffffu, s, 16);
+    s += __shfl_xor_sync(0xffffffffu, s, 8);
+  }
+  s += __shfl_xor_sync(0xffffffffu, s, 4);
+  s += __shfl_xor_sync(0xffffffffu, s, 2);
+  s += __shfl_xor_sync(0xffffffffu, s, 1);
+  return s;
+}
+
+// Both solves: out_r = rhs_r + sum over the terms t of row r of coef[t] * out[idx[t]],
+// rows in level order.
+//   B^{-1}: terms of row i are its neighbours (t = i m_v + k, idx = N, coef = A);
+//   B^{-T}: terms of row j are its children (CSR), idx = child rows, coef = the
+//           children's coefficients of j.
+// Steps are dealt round-robin to the warps of a cooperative launch (all resident), each
+// warp taking its steps in schedule order: a step only reads rows of earlier levels,
+// i.e. of earlier steps, so the earliest unfinished step can always proceed.  While a
+// step waits, the loads of the warp's next step are already in flight and the slots
+// of the one after are being read.
+__global__ __launch_bounds__(128) void sptrsv_kernel(const int4* __restrict__ sched, int64_t nsteps,
+                                                     const int32_t* __restrict__ idx, const double* __restrict__ coef,
+                                                     const double* __restrict__ rhs, double* out, int* abort_flag,
+                                                     int* status) {
+  const int lane = threadIdx.x & 31, g = lane / TR_LPR;
+  const int64_t W = (int64_t)gridDim.x * (blockDim.x >> 5);
+  int64_t step = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+  const int4 pad = make_int4(-1, 0, 0, 0);
+  TrsvTerms cur, nxt;
+  trsv_issue(cur, step < nsteps ? sched[step * TR_RPS + g] : pad, lane, idx, coef, rhs);
+  int4 sl1 = step + W < nsteps ? sched[(step + W) * TR_RPS + g] : pad;
+  for (; step < nsteps; step += W) {
+    trsv_issue(nxt, sl1, lane, idx, coef, rhs);
+    sl1 = step + 2 * W < nsteps ? sched[(step + 2 * W) * TR_RPS + g] : pad;
+    const double s = trsv_finish(cur, idx, coef, out, abort_flag, status);
+    if (cur.sub == 0 && cur.row >= 0) st_relaxed_f64(out + cur.row, cur.rhs + s);
+    cur = nxt;
+  }
+}
+
+// ch_coef[p] = A_{ch_row[p]}[ch_slot[p]]: the coefficient of each child term, in CSR order
+__global__ void child_coef_kernel(const int32_t* __restrict__ ch_row, const int32_t* __restrict__ ch_slot,
+                                  const double* __restrict__ Acoef, int64_t nnz, int mv, double* ch_coef) {
+  const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (p < nnz) ch_coef[p] = Acoef[(size_t)ch_row[p] * mv + ch_slot[p]];
+}
+
+// t_i = (x_i - sum_k A_i[k] x_{N_k}) / sqrt(D_i); thread per row, four gathers in flight
 __global__ void bx_scaled_kernel(const int32_t* __restrict__ N, const double* __restrict__ Acoef,
                                  const double* __restrict__ rsD, int64_t n, int mv, const double* __restrict__ x,
                                  double* t) {
   int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n) return;
   const int q = (int)(i < mv ? i : mv);
-  double s = x[i];
-  for (int k = 0; k < q; ++k) s -= Acoef[(size_t)i * mv + k] * x[N[(size_t)i * mv + k]];
-  t[i] = s * rsD[i];
+  const int32_t* Ni = N + (size_t)i * mv;
+  const double* Ai = Acoef + (size_t)i * mv;
+  double s = x[i], s2 = 0.0;
+  int k = 0;
+  for (; k + 3 < q; k += 4) {
+    const int j0 = Ni[k], j1 = Ni[k + 1], j2 = Ni[k + 2], j3 = Ni[k + 3];
+    const double x0 = x[j0], x1 = x[j1], x2 = x[j2], x3 = x[j3];
+    s = fma(-Ai[k], x0, s);
+    s2 = fma(-Ai[k + 1], x1, s2);
+    s = fma(-Ai[k + 2], x2, s);
+    s2 = fma(-Ai[k + 3], x3, s2);
+  }
+  for (; k < q; ++k) s = fma(-Ai[k], x[Ni[k]], s);
+  t[i] = (s + s2) * rsD[i];
 }
 
-// out_j = diagW_j x_j + rsD_j t_j - sum_{(i,k) in ch(j)} A_i[k] rsD_i t_i
+// out_j = diagW_j x_j + u_j - sum_{(i,k) in ch(j)} A_i[k] u_i   (u = D^{-1/2} t2)
 __global__ void btx_kernel(const int32_t* __restrict__ ch_ptr, const int32_t* __restrict__ ch_row,
-                           const int32_t* __restrict__ ch_slot, const double* __restrict__ Acoef,
-                           const double* __restrict__ rsD, int64_t n, int mv, const double* __restrict__ t,
+                           const double* __restrict__ ch_coef, int64_t n, const double* __restrict__ u,
                            const double* __restrict__ diagW, const double* __restrict__ x, double* out) {
   int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (j >= n) return;
-  double s = rsD[j] * t[j];
-  for (int p = ch_ptr[j]; p < ch_ptr[j + 1]; ++p) {
-    const int i = ch_row[p];
-    s -= Acoef[(size_t)i * mv + ch_slot[p]] * rsD[i] * t[i];
+  double s = u[j], s2 = 0.0;
+  int p = ch_ptr[j];
+  const int e = ch_ptr[j + 1];
+  for (; p + 3 < e; p += 4) {
+    const int i0 = ch_row[p], i1 = ch_row[p + 1], i2 = ch_row[p + 2], i3 = ch_row[p + 3];
+    const double u0 = u[i0], u1 = u[i1], u2 = u[i2], u3 = u[i3];
+    s = fma(-ch_coef[p], u0, s);
+    s2 = fma(-ch_coef[p + 1], u1, s2);
+    s = fma(-ch_coef[p + 2], u2, s);
+    s2 = fma(-ch_coef[p + 3], u3, s2);
   }
+  for (; p < e; ++p) s = fma(-ch_coef[p], u[ch_row[p]], s);
+  s += s2;
   if (diagW) s += diagW[j] * x[j];
   out[j] = s;
 }
 
-// partial[b][c] = sum over the rows of block b of F[i][c] * v[i]   (c < m)
-constexpr int FT_ROWS = 256;
-__global__ void ftv_kernel(const double* __restrict__ F, int fpad, int m, int64_t n, const double* __restrict__ v,
-                           double* partial) {
-  const int64_t r0 = (int64_t)blockIdx.x * FT_ROWS;
-  const int64_t r1 = (n < r0 + FT_ROWS) ? n : r0 + FT_ROWS;
+// partial[b][c] = sum over the rows of block b of F[i][c] * v[i]   (c < m); one block
+// per SM-sized slice of rows, one thread per column
+__global__ void ftv_kernel(const double* __restrict__ F, int fpad, int m, int64_t n, int64_t rows_per_block,
+                           const double* __restrict__ v, double* partial) {
+  const int64_t r0 = (int64_t)blockIdx.x * rows_per_block;
+  const int64_t r1 = (n < r0 + rows_per_block) ? n : r0 + rows_per_block;
   for (int c = threadIdx.x; c < m; c += blockDim.x) {
-    double s = 0.0;
-    for (int64_t r = r0; r < r1; ++r) s += F[(size_t)r * fpad + c] * v[r];
-    partial[(size_t)blockIdx.x * fpad + c] = s;
+    double s0 = 0.0, s1 = 0.0;
+    int64_t r = r0;
+    for (; r + 1 < r1; r += 2) {
+      s0 = fma(F[(size_t)r * fpad + c], v[r], s0);
+      s1 = fma(F[(size_t)(r + 1) * fpad + c], v[r + 1], s1);
+    }
+    if (r < r1) s0 = fma(F[(size_t)r * fpad + c], v[r], s0);
+    partial[(size_t)blockIdx.x * fpad + c] = s0 + s1;
   }
 }
+// out[c] = sum_b partial[b][c]: 32 columns per block, the 8 warps take every 8th partial
+// and their sums are added in a fixed order
 __global__ void col_reduce_kernel(const double* partial, int nb, int fpad, int m, double* out) {
-  int c = blockIdx.x * blockDim.x + threadIdx.x;
-  if (c >= m) return;
+  __shared__ double sh[8][32];
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  const int c = blockIdx.x * 32 + lane;
   double s = 0.0;
-  for (int b = 0; b < nb; ++b) s += partial[(size_t)b * fpad + c];
-  out[c] = s;
+  if (c < m)
+    for (int b = w; b < nb; b += 8) s += partial[(size_t)b * fpad + c];
+  sh[w][lane] = s;
+  __syncthreads();
+  if (w == 0 && c < m) {
+    double t = sh[0][lane];
+#pragma unroll
+    for (int k = 1; k < 8; ++k) t += sh[k][lane];
+    out[c] = t;
+  }
 }
 
 // y = L x (lower) or y = L^T x, L m x m with leading dimension ld; warp per output.
@@ -174,20 +268,40 @@ __global__ void lower_gemv_kernel(const double* __restrict__ L, int ld, int m, c
   if (lane == 0) y[r] = s;
 }
 
-// out_i = scale_i * (base_i + sgn * rsD_i * (F_i . c)) ; warp per row
-__global__ void f_dot_kernel(const double* __restrict__ F, int fpad, int m, int64_t n, const double* __restrict__ c,
-                             const double* __restrict__ base, double sgn, const double* __restrict__ rsD,
-                             const double* __restrict__ scale, double* out) {
-  const int64_t i = (int64_t)blockIdx.x * (blockDim.x / 32) + threadIdx.x / 32;
-  const int lane = threadIdx.x & 31;
+// out_i = scale_i * (base_i + sgn * rsD_i * (F_i . c)), m > 0; thread per row, each
+// thread reading its row in 32-byte pieces (c staged in shared memory)
+constexpr int FD_THREADS = 128;
+__global__ __launch_bounds__(FD_THREADS) void f_dot_kernel(const double* __restrict__ F, int fpad, int m, int64_t n,
+                                                           const double* __restrict__ c,
+                                                           const double* __restrict__ base, double sgn,
+                                                           const double* __restrict__ rsD,
+                                                           const double* __restrict__ scale, double* out) {
+  extern __shared__ double cs[];
+  const int m4 = (m + 3) & ~3;
+  for (int k = threadIdx.x; k < m4; k += blockDim.x) cs[k] = k < m ? c[k] : 0.0;
+  __syncthreads();
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n) return;
-  double s = 0.0;
-  for (int k = lane; k < m; k += 32) s += F[(size_t)i * fpad + k] * c[k];
-  for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
-  if (lane == 0) {
-    double v = base[i] + sgn * (rsD ? rsD[i] : 1.0) * s;
-    out[i] = scale ? scale[i] * v : v;
+  const double* row = F + (size_t)i * fpad;
+  double s0 = 0.0, s1 = 0.0, s2 = 0.0, s3 = 0.0;
+  for (int k = 0; k < m4; k += 4) {
+    const double2 a = *reinterpret_cast<const double2*>(row + k);
+    const double2 b = *reinterpret_cast<const double2*>(row + k + 2);
+    s0 = fma(a.x, cs[k], s0);
+    s1 = fma(a.y, cs[k + 1], s1);
+    s2 = fma(b.x, cs[k + 2], s2);
+    s3 = fma(b.y, cs[k + 3], s3);
   }
+  const double s = (s0 + s1) + (s2 + s3);
+  const double v = base[i] + sgn * (rsD ? rsD[i] : 1.0) * s;
+  out[i] = scale ? scale[i] * v : v;
+}
+
+// out_i = a_i * b_i * x_i (b may be NULL)
+__global__ void scale2_kernel(int64_t n, const double* __restrict__ a, const double* __restrict__ b,
+                              const double* __restrict__ x, double* out) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) out[i] = a[i] * (b ? b[i] : 1.0) * x[i];
 }
 
 // Bernoulli-logit pieces at b (Eq. W_diag): W = p(1-p), v = W b + (y - p), and for the
@@ -271,9 +385,10 @@ cudaError_t lap_dot(const double* a, const double* b, int64_t n, double* partial
 
 cudaError_t lap_ftv(const double* F, int fpad, int m, int64_t n, const double* v, double* partial, double* out,
                     cudaStream_t s) {
-  const int nb = (int)((n + FT_ROWS - 1) / FT_ROWS);
-  ftv_kernel<<<nb, 256, 0, s>>>(F, fpad, m, n, v, partial);
-  col_reduce_kernel<<<blocks(m, 256), 256, 0, s>>>(partial, nb, fpad, m, out);
+  const int64_t rpb = (n + LAP_FT_BLOCKS - 1) / LAP_FT_BLOCKS;
+  const int nb = (int)((n + rpb - 1) / rpb);
+  ftv_kernel<<<nb, 256, 0, s>>>(F, fpad, m, n, rpb, v, partial);
+  col_reduce_kernel<<<blocks(m, 32), 256, 0, s>>>(partial, nb, fpad, m, out);
   return cudaGetLastError();
 }
 
@@ -284,47 +399,81 @@ cudaError_t lap_spd_apply(const double* Linv, int ld, int m, const double* x, do
   return cudaGetLastError();
 }
 
+static void f_dot(const LapOps& o, const double* c, const double* base, double sgn, const double* rsD,
+                  const double* scale, double* out, cudaStream_t s) {
+  const size_t smem = (size_t)((o.m + 3) & ~3) * sizeof(double);
+  f_dot_kernel<<<blocks(o.n, FD_THREADS), FD_THREADS, smem, s>>>(o.F, o.fpad, o.m, o.n, c, base, sgn, rsD, scale,
+                                                                  out);
+}
+
 cudaError_t lap_matvec(const LapOps& o, const double* x, const double* diagW, double* out, cudaStream_t s) {
+  // t = D^{-1/2} B x ; u = D^{-1/2} (t - F C^{-1} F^T t) ; out = W x + B^T u
   bx_scaled_kernel<<<blocks(o.n, 256), 256, 0, s>>>(o.N, o.Acoef, o.rsD, o.n, o.mv, x, o.t);
   if (o.m > 0) {
     lap_ftv(o.F, o.fpad, o.m, o.n, o.t, o.partial, o.sm, s);
     lap_spd_apply(o.LinvC, o.ldl, o.m, o.sm, o.tmpm, o.cm, s);
-    f_dot_kernel<<<blocks(o.n, 8), 256, 0, s>>>(o.F, o.fpad, o.m, o.n, o.cm, o.t, -1.0, nullptr, nullptr, o.t2);
+    f_dot(o, o.cm, o.t, -1.0, nullptr, o.rsD, o.t2, s);
   } else {
-    cudaMemcpyAsync(o.t2, o.t, o.n * sizeof(double), cudaMemcpyDeviceToDevice, s);
+    scale2_kernel<<<blocks(o.n, 256), 256, 0, s>>>(o.n, o.rsD, nullptr, o.t, o.t2);
   }
-  btx_kernel<<<blocks(o.n, 256), 256, 0, s>>>(o.ch_ptr, o.ch_row, o.ch_slot, o.Acoef, o.rsD, o.n, o.mv, o.t2, diagW,
-                                              x, out);
+  btx_kernel<<<blocks(o.n, 256), 256, 0, s>>>(o.ch_ptr, o.ch_row, o.ch_coef, o.n, o.t2, diagW, x, out);
   return cudaGetLastError();
 }
 
-cudaError_t lap_precond(const LapOps& o, const double* w, double* out, int* epoch, cudaStream_t s) {
-  const unsigned grid = 152 * 4;
+cudaError_t lap_child_coef(const LapOps& o, double* ch_coef, cudaStream_t s) {
+  if (o.nnz > 0)
+    child_coef_kernel<<<blocks(o.nnz, 256), 256, 0, s>>>(o.ch_row, o.ch_slot, o.Acoef, o.nnz, o.mv, ch_coef);
+  return cudaGetLastError();
+}
+
+// CTAs per SM of a triangular solve (1, 2 and 4 measured within 5% of one another at
+// n = 2e5).  The launch is cooperative (every CTA resident at once), which the
+// round-robin step assignment needs.
+constexpr int TRSV_CTAS_PER_SM = 2;
+
+static cudaError_t launch_trsv(const int4* sched, int64_t nsteps, const int32_t* idx, const double* coef,
+                               const double* rhs, double* out, int* abort_flag, int* status, cudaStream_t s) {
+  static int grid_of_dev[64] = {0};
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  int& grid = grid_of_dev[dev & 63];
+  if (grid == 0) {
+    int sms = 0, per_sm = 0;
+    e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, sptrsv_kernel, 128, 0);
+    if (e != cudaSuccess) return e;
+    if (per_sm < 1) return cudaErrorLaunchOutOfResources;
+    grid = sms * (per_sm < TRSV_CTAS_PER_SM ? per_sm : TRSV_CTAS_PER_SM);
+  }
+  void* args[] = {(void*)&sched, (void*)&nsteps, (void*)&idx, (void*)&coef, (void*)&rhs, (void*)&out,
+                  (void*)&abort_flag, (void*)&status};
+  return cudaLaunchCooperativeKernel((const void*)sptrsv_kernel, dim3(grid), dim3(128), args, 0, s);
+}
+
+cudaError_t lap_precond(const LapOps& o, const double* w, double* out, cudaStream_t s) {
   // x = B^{-T} w
-  cudaMemsetAsync(o.counter, 0, 2 * sizeof(unsigned long long), s);
-  ++*epoch;
   if (o.mv > 0) {
-    sptrsv_Bt_kernel<<<grid, 256, 0, s>>>(o.ch_ptr, o.ch_row, o.ch_slot, o.Acoef, o.n, o.mv, w, o.x1, o.flags,
-                                          *epoch, o.counter, o.abort_flag, o.status);
+    cudaMemsetAsync(o.x1, 0xFF, (size_t)o.n * sizeof(double), s);
+    cudaError_t e = launch_trsv(o.sched_rev, o.nsteps_rev, o.ch_row, o.ch_coef, w, o.x1, o.abort_flag, o.status, s);
+    if (e != cudaSuccess) return e;
   } else {
     cudaMemcpyAsync(o.x1, w, o.n * sizeof(double), cudaMemcpyDeviceToDevice, s);
   }
   // e = G^{-1} (x + D^{-1/2} F C3^{-1} F^T D^{-1/2} G^{-1} x)
   if (o.m > 0) {
-    f_dot_kernel<<<blocks(o.n, 8), 256, 0, s>>>(o.F, o.fpad, 0, o.n, o.cm, o.x1, 0.0, nullptr, o.Ginv, o.t);
-    // t = x / G ; then t <- rsD * t for the F^T product
-    f_dot_kernel<<<blocks(o.n, 8), 256, 0, s>>>(o.F, o.fpad, 0, o.n, o.cm, o.t, 0.0, nullptr, o.rsD, o.t2);
+    scale2_kernel<<<blocks(o.n, 256), 256, 0, s>>>(o.n, o.rsD, o.Ginv, o.x1, o.t2);
     lap_ftv(o.F, o.fpad, o.m, o.n, o.t2, o.partial, o.sm, s);
     lap_spd_apply(o.LinvC3, o.ldl, o.m, o.sm, o.tmpm, o.cm, s);
-    f_dot_kernel<<<blocks(o.n, 8), 256, 0, s>>>(o.F, o.fpad, o.m, o.n, o.cm, o.x1, 1.0, o.rsD, o.Ginv, o.t);
+    f_dot(o, o.cm, o.x1, 1.0, o.rsD, o.Ginv, o.t, s);
   } else {
-    f_dot_kernel<<<blocks(o.n, 8), 256, 0, s>>>(o.F, o.fpad, 0, o.n, o.cm, o.x1, 0.0, nullptr, o.Ginv, o.t);
+    scale2_kernel<<<blocks(o.n, 256), 256, 0, s>>>(o.n, o.Ginv, nullptr, o.x1, o.t);
   }
   // out = B^{-1} e
-  ++*epoch;
   if (o.mv > 0) {
-    sptrsv_B_kernel<<<grid, 256, 0, s>>>(o.N, o.Acoef, o.n, o.mv, o.t, out, o.flags, *epoch, o.counter + 2,
-                                         o.abort_flag, o.status);
+    cudaMemsetAsync(out, 0xFF, (size_t)o.n * sizeof(double), s);
+    cudaError_t e = launch_trsv(o.sched_fwd, o.nsteps_fwd, o.N, o.Acoef, o.t, out, o.abort_flag, o.status, s);
+    if (e != cudaSuccess) return e;
   } else {
     cudaMemcpyAsync(out, o.t, o.n * sizeof(double), cudaMemcpyDeviceToDevice, s);
   }

@@ -289,6 +289,31 @@ def test_laplace_with_gpu_neighbors_and_no_inducing_points():
     ctx.close()
 
 
+@pytest.mark.parametrize("shape", ["chain", "star_chain"])
+def test_laplace_solves_on_deep_and_wide_dependency_graphs(shape):
+    # chain (m_v = 1): N(i) = {i-1}, as many levels as rows, one row each; star_chain
+    # (m_v = 2): N(i) = {0, i-1}, so row 0 has n-1 children (the whole warp and several
+    # passes of terms in the B^T solve) while the rows still form one long chain
+    n = 700
+    mv = 1 if shape == "chain" else 2
+    P = bern(n, 12, mv, 35)
+    N = np.full((n, mv), -1, dtype=np.int64)
+    for i in range(1, n):
+        if shape == "chain":
+            N[i, 0] = i - 1
+        else:
+            N[i, 0] = 0
+            if i >= 2:
+                N[i, 1] = i - 1
+    vif = O.VIF(P.X, P.Z, P.theta, N)
+    b_dense, _, _ = O.laplace_mode(vif, P.y, dense=True)
+    ctx = V.Context(P.X, P.Z, mv, P.theta, likelihood=V.BERNOULLI_LOGIT, neighbor_search=False)
+    ctx.set_neighbors(N.astype(np.int32))
+    b, st = ctx.laplace_mode(P.theta, P.y, rel_tol=1e-8)
+    assert np.linalg.norm(b - b_dense) <= 1e-6 * np.linalg.norm(b_dense), st
+    ctx.close()
+
+
 def test_laplace_rejects_a_nugget():
     P = bern(300, 10, 4, 34)
     ctx = V.Context(P.X, P.Z, 4, P.theta, likelihood=V.BERNOULLI_LOGIT)
