@@ -54,6 +54,11 @@ __device__ __forceinline__ void cp_async16(void* smem, const void* gmem) {
   unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
   asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(sa), "l"(gmem));
 }
+// 16 bytes, or 16 zero bytes when !valid (nothing is read from gmem then)
+__device__ __forceinline__ void cp_async16_zfill(void* smem, const void* gmem, bool valid) {
+  unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;\n" ::"r"(sa), "l"(gmem), "r"(valid ? 16 : 0));
+}
 __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::); }
 template <int N>
 __device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;\n" ::"n"(N)); }
@@ -73,14 +78,27 @@ __device__ __forceinline__ double rsqrt_refined(double p) {
 
 template <typename T, int R>
 struct FactorSmem {
+  // float32 with R = 3 (m_v = 14..20): seven-row blocks on 5 column groups of a
+  // 40-column window (see the kernel); otherwise R x R blocks on 128-byte windows
+  static constexpr bool BIG = (sizeof(T) == 4 && R == 3);
   static constexpr int QM = FK_NB * R;
   static constexpr int V = Vec16<T>::n;       // elements per 16 bytes
-  static constexpr int KC = 128 / sizeof(T);  // window width: 128 bytes per row
+  static constexpr int GK = 5;                // BIG: column groups
+  static constexpr int KC = BIG ? 8 * GK : 128 / (int)sizeof(T);   // window width
   static constexpr int LD = KC + V;           // row stride (16-byte aligned, bank shift)
-  alignas(16) T buf[2][QM][LD];
+  static constexpr int PL = BIG ? 6 * GK : 1, PE = BIG ? 49 : 1;   // BIG: partial Gram blocks
+  // the windows are dead once the Gram is formed: the partial sums of the column
+  // groups and the coordinates of the rows reuse their space
+  struct Post {
+    T part[PL][PE];
+    T xc[QM][FK_MAXD];
+  };
+  union {
+    alignas(16) T buf[2][QM][LD];
+    Post post;
+  };
   T G[QM][QM + 1];
   T coef[QM];
-  T xc[QM][FK_MAXD];
   int idx[QM];
 };
 
@@ -109,24 +127,22 @@ __global__ __launch_bounds__(FK_WARPS * 32) void factor_kernel(
     }
     S.idx[t] = j;
   }
-  // rows Q..QM-1 of both windows stay zero
-  for (int e = lane; e < 2 * QM * SM::LD; e += 32) (&S.buf[0][0][0])[e] = T(0);
-  __syncwarp();
-  for (int e = lane; e < Q * d; e += 32) {
-    int t = e / d, c = e % d;
-    S.xc[t][c] = Xs[(size_t)S.idx[t] * d + c];
+  // rows Q..QM-1 of both windows stay zero (none once i >= m_v)
+  for (int e = lane; e < 2 * (QM - Q) * SM::LD; e += 32) {
+    const int b = e / ((QM - Q) * SM::LD), r = e % ((QM - Q) * SM::LD);
+    S.buf[b][Q + r / SM::LD][r % SM::LD] = T(0);
   }
+  __syncwarp();
   // ---- Gram of the gathered rows of A, double-buffered windows of KC columns
   // float32 with 15 <= Q <= 21 (the m_v = 20 workloads): seven-row blocks, 3 x 3 grid,
-  // 6 lower block pairs x 4 lanes, lane kg taking the window columns kg + 4t, so each
-  // lane reads 14 values per column for 49 products (2 per shared-memory word instead
-  // of 1.5 with the 3 x 3 blocks below, and 4 per word per block pair); the 4 partial
-  // sums of a block pair are added by shuffles at the end.
-  constexpr bool BIG = (sizeof(T) == 4 && R == 3);
+  // 6 lower block pairs x 5 column groups on 30 lanes, lane kg taking the window
+  // columns kg + 5t, so each lane reads 14 values per column for 49 products; the 5
+  // partial sums of a block pair are added through shared memory at the end.
+  constexpr bool BIG = SM::BIG;
   if constexpr (BIG) {
-    constexpr int BR = 7;
-    const bool own = lane < 24;
-    const int bp = own ? (lane >> 2) : 0, kg = lane & 3;
+    constexpr int BR = 7, GK = SM::GK;
+    const bool own = lane < 6 * GK;
+    const int bp = own ? lane / GK : 0, kg = lane % GK;
     const int bi = (bp == 0) ? 0 : (bp < 3 ? 1 : 2);
     const int bj = bp - (bi * (bi + 1) / 2);
     float acc[BR][BR];
@@ -139,9 +155,11 @@ __global__ __launch_bounds__(FK_WARPS * 32) void factor_kernel(
     auto issue = [&](int win, int b) {
       const int k0 = win * KC;
       for (int e = lane; e < Q * SEG; e += 32) {
-        int t = e / SEG, sg = e % SEG;
-        int k = k0 + sg * V;
-        if (k < mpad) cp_async16(&S.buf[b][t][sg * V], A + (size_t)S.idx[t] * mpad + k);
+        const int t = e / SEG, sg = e % SEG;
+        const int k = k0 + sg * V;
+        // columns past the row (the last window) are filled with zeros
+        const bool in = k < mpad;
+        cp_async16_zfill(&S.buf[b][t][sg * V], A + (size_t)S.idx[t] * mpad + (in ? k : 0), in);
       }
       cp_async_commit();
     };
@@ -156,8 +174,8 @@ __global__ __launch_bounds__(FK_WARPS * 32) void factor_kernel(
       }
       __syncwarp();
 #pragma unroll 2
-      for (int t = 0; t < KC / 4; ++t) {
-        const int col = kg + 4 * t;
+      for (int t = 0; t < KC / GK; ++t) {
+        const int col = kg + GK * t;
         float u[BR], v[BR];
 #pragma unroll
         for (int r = 0; r < BR; ++r) u[r] = (float)S.buf[b][bi * BR + r][col];
@@ -170,20 +188,20 @@ __global__ __launch_bounds__(FK_WARPS * 32) void factor_kernel(
       }
       __syncwarp();
     }
-#pragma unroll
-    for (int r = 0; r < BR; ++r)
-#pragma unroll
-      for (int c = 0; c < BR; ++c) {
-        float a = acc[r][c];
-        a += __shfl_xor_sync(0xffffffffu, a, 1);
-        a += __shfl_xor_sync(0xffffffffu, a, 2);
-        acc[r][c] = a;
-      }
-    if (own && kg == 0) {
+    if (own) {
 #pragma unroll
       for (int r = 0; r < BR; ++r)
 #pragma unroll
-        for (int c = 0; c < BR; ++c) S.G[bi * BR + r][bj * BR + c] = (T)acc[r][c];
+        for (int c = 0; c < BR; ++c) S.post.part[lane][r * BR + c] = acc[r][c];
+    }
+    __syncwarp();
+    for (int e = lane; e < 6 * BR * BR; e += 32) {
+      const int p = e / (BR * BR), rc = e % (BR * BR);
+      const int pi = (p == 0) ? 0 : (p < 3 ? 1 : 2), pj = p - (pi * (pi + 1) / 2);
+      float a = S.post.part[p * GK][rc];
+#pragma unroll
+      for (int k = 1; k < GK; ++k) a += S.post.part[p * GK + k][rc];
+      S.G[pi * BR + rc / BR][pj * BR + rc % BR] = (T)a;
     }
     __syncwarp();
   } else {
@@ -241,6 +259,12 @@ __global__ __launch_bounds__(FK_WARPS * 32) void factor_kernel(
   }
   __syncwarp();
   }
+  // coordinates of the rows (their space was the windows')
+  for (int e = lane; e < Q * d; e += 32) {
+    const int t = e / d, c = e % d;
+    S.post.xc[t][c] = Xs[(size_t)S.idx[t] * d + c];
+  }
+  __syncwarp();
   // ---- residual covariance R (lower triangle)
   const int npair = Q * (Q + 1) / 2;
   for (int e = lane; e < npair; e += 32) {
@@ -248,7 +272,7 @@ __global__ __launch_bounds__(FK_WARPS * 32) void factor_kernel(
     while ((a + 1) * (a + 2) / 2 <= e) ++a;
     while (a * (a + 1) / 2 > e) --a;
     int b2 = e - a * (a + 1) / 2;
-    T kv = cov_r2<T>(sqdist(&S.xc[a][0], &S.xc[b2][0], d), cp.kind, (T)cp.var);
+    T kv = cov_r2<T>(sqdist(&S.post.xc[a][0], &S.post.xc[b2][0], d), cp.kind, (T)cp.var);
     if (a == b2) kv += (T)cp.tdiag;
     S.G[a][b2] = kv - S.G[a][b2];
   }

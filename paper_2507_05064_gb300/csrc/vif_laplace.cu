@@ -193,27 +193,38 @@ __global__ void bx_scaled_kernel(const int32_t* __restrict__ N, const double* __
   t[i] = (s + s2) * rsD[i];
 }
 
-// out_j = diagW_j x_j + u_j - sum_{(i,k) in ch(j)} A_i[k] u_i   (u = D^{-1/2} t2)
-__global__ void btx_kernel(const int32_t* __restrict__ ch_ptr, const int32_t* __restrict__ ch_row,
-                           const double* __restrict__ ch_coef, int64_t n, const double* __restrict__ u,
-                           const double* __restrict__ diagW, const double* __restrict__ x, double* out) {
-  int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (j >= n) return;
-  double s = u[j], s2 = 0.0;
-  int p = ch_ptr[j];
-  const int e = ch_ptr[j + 1];
-  for (; p + 3 < e; p += 4) {
-    const int i0 = ch_row[p], i1 = ch_row[p + 1], i2 = ch_row[p + 2], i3 = ch_row[p + 3];
-    const double u0 = u[i0], u1 = u[i1], u2 = u[i2], u3 = u[i3];
-    s = fma(-ch_coef[p], u0, s);
-    s2 = fma(-ch_coef[p + 1], u1, s2);
-    s = fma(-ch_coef[p + 2], u2, s);
-    s2 = fma(-ch_coef[p + 3], u3, s2);
+// out_j = diagW_j x_j + u_j - sum_{(i,k) in ch(j)} A_i[k] u_i   (u = D^{-1/2} t2), over
+// the steps of the B^T schedule (four rows of eight lanes, or one row with many
+// children on the whole warp), so that rows with hundreds of children do not hold a
+// single thread; nothing here waits, the level order is simply reused.
+__global__ __launch_bounds__(256) void btx_kernel(const int4* __restrict__ sched, int64_t nsteps,
+                                                  const int32_t* __restrict__ ch_row,
+                                                  const double* __restrict__ ch_coef, const double* __restrict__ u,
+                                                  const double* __restrict__ diagW, const double* __restrict__ x,
+                                                  double* out) {
+  const int lane = threadIdx.x & 31;
+  const int64_t step = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+  if (step >= nsteps) return;
+  const int4 sl = sched[step * TR_RPS + lane / TR_LPR];
+  const bool solo = sl.w != 0;
+  const int lanes = solo ? 32 : TR_LPR, sub = solo ? lane : lane % TR_LPR;
+  double s = 0.0, s2 = 0.0;
+  int t = sl.y + sub;
+  for (; t + lanes < sl.z; t += 2 * lanes) {
+    s = fma(ch_coef[t], u[ch_row[t]], s);
+    s2 = fma(ch_coef[t + lanes], u[ch_row[t + lanes]], s2);
   }
-  for (; p < e; ++p) s = fma(-ch_coef[p], u[ch_row[p]], s);
+  if (t < sl.z) s = fma(ch_coef[t], u[ch_row[t]], s);
   s += s2;
-  if (diagW) s += diagW[j] * x[j];
-  out[j] = s;
+  if (solo) {
+    s += __shfl_xor_sync(0xffffffffu, s, 16);
+    s += __shfl_xor_sync(0xffffffffu, s, 8);
+  }
+  s += __shfl_xor_sync(0xffffffffu, s, 4);
+  s += __shfl_xor_sync(0xffffffffu, s, 2);
+  s += __shfl_xor_sync(0xffffffffu, s, 1);
+  const int j = sl.x;
+  if (sub == 0 && j >= 0) out[j] = u[j] - s + (diagW ? diagW[j] * x[j] : 0.0);
 }
 
 // partial[b][c] = sum over the rows of block b of F[i][c] * v[i]   (c < m); one block
@@ -416,7 +427,8 @@ cudaError_t lap_matvec(const LapOps& o, const double* x, const double* diagW, do
   } else {
     scale2_kernel<<<blocks(o.n, 256), 256, 0, s>>>(o.n, o.rsD, nullptr, o.t, o.t2);
   }
-  btx_kernel<<<blocks(o.n, 256), 256, 0, s>>>(o.ch_ptr, o.ch_row, o.ch_coef, o.n, o.t2, diagW, x, out);
+  btx_kernel<<<blocks(o.nsteps_rev, 8), 256, 0, s>>>(o.sched_rev, o.nsteps_rev, o.ch_row, o.ch_coef, o.t2, diagW,
+                                                        x, out);
   return cudaGetLastError();
 }
 
