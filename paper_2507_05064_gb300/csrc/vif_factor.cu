@@ -90,8 +90,8 @@ struct FactorSmem {
   // the windows are dead once the Gram is formed: the partial sums of the column
   // groups and the coordinates of the rows reuse their space
   struct Post {
+    alignas(16) T xc[QM][FK_MAXD];
     T part[PL][PE];
-    T xc[QM][FK_MAXD];
   };
   union {
     alignas(16) T buf[2][QM][LD];
@@ -102,6 +102,27 @@ struct FactorSmem {
   int idx[QM];
 };
 
+// |x_a - x_b|^2 over d coordinates of two shared-memory rows (16-byte aligned)
+template <typename T>
+__device__ __forceinline__ T sqdist_rows(const T* __restrict__ xa, const T* __restrict__ xb, int d) {
+  if constexpr (sizeof(T) == 4) {
+    if ((d & 3) == 0) {
+      float s = 0.f;
+      for (int c = 0; c < d; c += 4) {
+        const float4 a = *reinterpret_cast<const float4*>(xa + c), b = *reinterpret_cast<const float4*>(xb + c);
+        const float d0 = a.x - b.x, d1 = a.y - b.y, d2 = a.z - b.z, d3 = a.w - b.w;
+        s = fmaf(d0, d0, s);
+        s = fmaf(d1, d1, s);
+        s = fmaf(d2, d2, s);
+        s = fmaf(d3, d3, s);
+      }
+      return s;
+    }
+  }
+  return sqdist(xa, xb, d);
+}
+
+// float32 m_v = 20 (R = 3): six CTAs of four warps per SM, as the shared memory allows
 template <typename T, int R>
 __global__ __launch_bounds__(FK_WARPS * 32) void factor_kernel(
     const T* __restrict__ A, const T* __restrict__ Xs, const int32_t* __restrict__ N,
@@ -267,12 +288,18 @@ __global__ __launch_bounds__(FK_WARPS * 32) void factor_kernel(
   __syncwarp();
   // ---- residual covariance R (lower triangle)
   const int npair = Q * (Q + 1) / 2;
-  for (int e = lane; e < npair; e += 32) {
-    int a = (int)((sqrtf(8.0f * e + 1.0f) - 1.0f) * 0.5f);
-    while ((a + 1) * (a + 2) / 2 <= e) ++a;
-    while (a * (a + 1) / 2 > e) --a;
-    int b2 = e - a * (a + 1) / 2;
-    T kv = cov_r2<T>(sqdist(&S.post.xc[a][0], &S.post.xc[b2][0], d), cp.kind, (T)cp.var);
+  // lane walks the entries e = lane, lane + 32, ... of the triangle stored row by row
+  // (e = a (a + 1) / 2 + b2): the first is decoded, the later ones stepped to
+  int a = (int)((sqrtf(8.0f * lane + 1.0f) - 1.0f) * 0.5f);
+  while ((a + 1) * (a + 2) / 2 <= lane) ++a;
+  while (a * (a + 1) / 2 > lane) --a;
+  int b2 = lane - a * (a + 1) / 2;
+  for (int e = lane; e < npair; e += 32, b2 += 32) {
+    while (b2 > a) {
+      b2 -= a + 1;
+      ++a;
+    }
+    T kv = cov_r2<T>(sqdist_rows(&S.post.xc[a][0], &S.post.xc[b2][0], d), cp.kind, (T)cp.var);
     if (a == b2) kv += (T)cp.tdiag;
     S.G[a][b2] = kv - S.G[a][b2];
   }
@@ -301,11 +328,9 @@ __global__ __launch_bounds__(FK_WARPS * 32) void factor_kernel(
       const T lc = (lane == c) ? piv * rs : row[c] * rs;
       if (lane == c) my_rs = rs;
       row[c] = lc;
+      // lanes above s2 update entries above their diagonal, which are never read
 #pragma unroll
-      for (int s2 = c + 1; s2 < QM; ++s2) {
-        const T ls = __shfl_sync(0xffffffffu, lc, s2);
-        if (lane >= s2) row[s2] = fma(-lc, ls, row[s2]);
-      }
+      for (int s2 = c + 1; s2 < QM; ++s2) row[s2] = fma(-lc, __shfl_sync(0xffffffffu, lc, s2), row[s2]);
     }
     if (notpd && lane == 0) flag_status(status, ST_NOTPD_FACTOR, i);
     if (lane < Q) {
