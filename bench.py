@@ -47,6 +47,8 @@ def parse():
     ap.add_argument("--no-laplace", action="store_true")
     ap.add_argument("--laplace-n", type=int, default=200_000)
     ap.add_argument("--no-small", action="store_true", help="skip the C1/C2 block")
+    ap.add_argument("--laplace-only", action="store_true",
+                    help="run only the C4 Laplace block and print its JSON (for profiling the PCG kernels)")
     ap.add_argument("--batch", type=int, default=0,
                     help="also time N independent C5-style problems per CUDA graph replay (0: skip)")
     return ap.parse_args()
@@ -465,6 +467,12 @@ def main():
     dist = None
     if args.impl == "reference":
         run_reference(args, rank, world)
+        return
+    if args.laplace_only:
+        import torch
+        torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", 0)))
+        if rank == 0:
+            print(json.dumps(laplace_block(args, torch.cuda.current_stream())), flush=True)
         return
     if world > 1:
         import torch

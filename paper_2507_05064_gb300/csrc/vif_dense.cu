@@ -4,11 +4,12 @@
 //
 // GB300 executes float64 at 1/64 of its float32 rate: a warp's float64 instruction
 // occupies its SM sub-partition for 64 cycles whether 1 or 32 lanes are active, a
-// square root ~680 cycles and a division ~430.  The blocked right-looking algorithm
+// square root ~680 cycles and a division ~430.  The blocked right-looking Cholesky
 // below therefore keeps the serial chain short and spreads the rest over many SMs:
-// one launch factors the 32 x 32 diagonal tile (redundantly in every CTA) together
-// with the tile below it in one column sweep (pivots by a Newton-refined reciprocal
-// square root), the next updates the trailing tiles, one CTA per tile.
+// one launch factors the 16 x 16 diagonal tile (redundantly in every CTA) together
+// with the tile below it in one column sweep held in registers (pivots by a Newton-
+// refined reciprocal square root, formed one column ahead), the next updates the
+// trailing tiles, one CTA per tile.
 #include "vif_internal.cuh"
 
 namespace vif {
@@ -52,111 +53,114 @@ __device__ __forceinline__ double rsqrt_newton(double p) {
   return y;
 }
 
-// Step k of the blocked Cholesky: CTA b factors the diagonal tile L_kk and, for b > 0,
-// the tile T_b below it (X L_kk^T = T_b) in the same column sweep over the stacked
-// 64 x 32 block [L_kk; T_b]: per column, one pivot (thread 0), one scaling and one
-// rank-1 update spread over the CTA.  CTA 0 writes L_kk, CTA b writes X.
-__global__ void chol_panel_kernel(double* A, int m, int lda, int k, int* status, int code) {
-  __shared__ double M[2 * NB][NB + 1];
-  __shared__ double rs[NB];
-  const int k0 = k * NB;
+// Blocked right-looking Cholesky with 16 x 16 tiles.  Step k: CTA b factors the diagonal
+// tile L_kk and, for b > 0, the tile T_b below it (X L_kk^T = T_b) in one column sweep over
+// the stacked 32 x 16 block [L_kk; T_b], which lives in registers: thread t holds row t / 4,
+// columns t % 4 + 4j.  Per column: the owner of the pivot has already formed it (a
+// look-ahead at the end of the previous column), the column below it is scaled and shared
+// through shared memory, and every later column takes its rank-1 update; a thread whose
+// columns are all done issues no float64 instruction.  CTA 0 writes L_kk, CTA b writes X.
+constexpr int CH = 16;
+
+__global__ __launch_bounds__(128) void chol_panel_kernel(double* A, int m, int lda, int k, int* status, int code) {
+  __shared__ double col[2 * CH];
+  __shared__ double rs[CH];
+  const int t = threadIdx.x, r = t >> 2, g = t & 3;
+  const int k0 = k * CH;
   const bool has_t = blockIdx.x > 0;
-  const int rows = has_t ? 2 * NB : NB;
-  const int r0 = (k + blockIdx.x) * NB;   // first row of T_b
-  for (int idx = threadIdx.x; idx < rows * NB; idx += blockDim.x) {
-    const int r = idx / NB, c = idx % NB;
-    M[r][c] = r < NB ? ((c <= r) ? ld_lower(A, lda, m, k0 + r, k0 + c) : 0.0)
-                     : ld_lower(A, lda, m, r0 + r - NB, k0 + c);
+  const int r0 = (k + blockIdx.x) * CH;   // first row of T_b
+  const bool live = r < CH || has_t;
+  double v[CH / 4];
+#pragma unroll
+  for (int j = 0; j < CH / 4; ++j) {
+    const int sc = g + 4 * j;
+    v[j] = !live ? 0.0
+                 : (r < CH ? (sc <= r ? ld_lower(A, lda, m, k0 + r, k0 + sc) : 0.0)
+                           : ld_lower(A, lda, m, r0 + r - CH, k0 + sc));
   }
-  // pivot c: M[c][c] <- sqrt(p), rs[c] <- 1/sqrt(p)
-  auto pivot = [&](int c) {
-    double p = M[c][c];
+  // pivot c from its owner's current value: M[c][c] <- sqrt(p), rs[c] <- 1/sqrt(p)
+  auto pivot = [&](double& pv, int c) {
+    double p = pv;
     if (!(p > 0.0)) {
       if (blockIdx.x == 0 && status) flag_status(status, code, k0 + c);
       p = nan("");
     }
     const double y = rsqrt_newton(p);
-    M[c][c] = p * y;
+    pv = p * y;
     rs[c] = y;
   };
+  if (t == 0) pivot(v[0], 0);
   __syncthreads();
-  if (threadIdx.x == 0) pivot(0);
-  __syncthreads();
-  for (int c = 0; c < NB; ++c) {
-    const double y = rs[c];
-    // column c below the pivot: rows c+1..NB-1 of L_kk and all rows of T_b
-    const int ncol = rows - (c + 1);
-    for (int t = threadIdx.x; t < ncol; t += blockDim.x) M[c + 1 + t][c] *= y;
-    __syncthreads();
-    // rank-1 update of the trailing columns c+1..NB-1 (lower part of L_kk, all of T_b);
-    // element (c+1, c+1) is thread 0's first, so thread 0 then forms the next pivot while
-    // the others finish the update (two barriers per column)
-    const int w = NB - c - 1;
-    for (int idx = threadIdx.x; idx < ncol * w; idx += blockDim.x) {
-      const int r = c + 1 + idx / w, s2 = c + 1 + idx % w;
-      if (r >= NB || s2 <= r) M[r][s2] -= M[r][c] * M[s2][c];
+#pragma unroll
+  for (int c = 0; c < CH; ++c) {
+    const int jc = c >> 2;
+    // column c below the pivot, scaled and shared
+    if (g == (c & 3) && r > c && live) {
+      v[jc] *= rs[c];
+      col[r] = v[jc];
     }
-    if (threadIdx.x == 0 && c + 1 < NB) pivot(c + 1);
+    __syncthreads();
+    if (r > c && live) {
+      const double lr = col[r];
+#pragma unroll
+      for (int j = 0; j < CH / 4; ++j) {
+        if (j >= jc) {   // uniform: columns 4j .. 4j + 3 may still need column c
+          const int sc = g + 4 * j;
+          if (sc > c && (r >= CH || sc <= r)) v[j] = fma(-lr, col[sc], v[j]);
+        }
+      }
+    }
+    // look-ahead: the owner of pivot c + 1 has just updated it
+    if (c + 1 < CH && t == 4 * (c + 1) + ((c + 1) & 3)) pivot(v[(c + 1) >> 2], c + 1);
     __syncthreads();
   }
-  if (!has_t) {
-    for (int idx = threadIdx.x; idx < NB * NB; idx += blockDim.x) {
-      const int r = idx / NB, c = idx % NB;
-      if (c <= r && k0 + r < m && k0 + c < m) A[(size_t)(k0 + r) * lda + k0 + c] = M[r][c];
-    }
-  } else {
-    for (int idx = threadIdx.x; idx < NB * NB; idx += blockDim.x) {
-      const int r = idx / NB, c = idx % NB;
-      if (r0 + r < m && k0 + c < m) A[(size_t)(r0 + r) * lda + k0 + c] = M[NB + r][c];
+#pragma unroll
+  for (int j = 0; j < CH / 4; ++j) {
+    const int sc = g + 4 * j;
+    if (!has_t) {
+      if (r < CH && sc <= r && k0 + r < m && k0 + sc < m) A[(size_t)(k0 + r) * lda + k0 + sc] = v[j];
+    } else if (r >= CH) {
+      const int rr = r0 + r - CH;
+      if (rr < m && k0 + sc < m) A[(size_t)rr * lda + k0 + sc] = v[j];
     }
   }
+}
+
+// Trailing update A_ij -= L_ik L_jk^T of step k, one CTA per 16 x 16 tile (i, j), one
+// output per thread, summed in a fixed order: the capacitance matrix is ill-conditioned
+// enough (condition ~1e7-1e8) that a run-to-run change in the last bits of its factor shows
+// in the likelihood.
+__global__ __launch_bounds__(256) void chol_update_kernel(double* A, int m, int lda, int k, int T) {
+  // tile (i, j), k < j <= i < k+1+T, enumerated over the lower triangle
+  const int b = blockIdx.x;
+  int ii = (int)((sqrt(8.0 * b + 1.0) - 1.0) * 0.5);
+  while ((ii + 1) * (ii + 2) / 2 <= b) ++ii;
+  while (ii * (ii + 1) / 2 > b) --ii;
+  const int jj = b - ii * (ii + 1) / 2;
+  const int i0 = (k + 1 + ii) * CH, j0 = (k + 1 + jj) * CH, k0 = k * CH;
+  __shared__ double Li[CH][CH + 1];
+  __shared__ double Lj[CH][CH + 1];
+  const int t = threadIdx.x, r = t / CH, c = t % CH;
+  Li[r][c] = (i0 + r < m && k0 + c < m) ? A[(size_t)(i0 + r) * lda + k0 + c] : 0.0;
+  Lj[r][c] = (j0 + r < m && k0 + c < m) ? A[(size_t)(j0 + r) * lda + k0 + c] : 0.0;
+  __syncthreads();
+  if (i0 + r >= m || j0 + c >= m || (ii == jj && c > r)) return;
+  double acc = 0.0;
+#pragma unroll
+  for (int q = 0; q < CH; ++q) acc = fma(Li[r][q], Lj[c][q], acc);
+  A[(size_t)(i0 + r) * lda + j0 + c] -= acc;
 }
 
 // k-slices of the triangular-inverse products (one CTA each, float64 atomics)
 constexpr int KS = 4;
 constexpr int KSW = NB / KS;
 
-// Trailing update A_ij -= L_ik L_jk^T of step k, one CTA per tile (i, j), summed in a
-// fixed order: the capacitance matrix is ill-conditioned enough (condition ~1e7-1e8)
-// that a run-to-run change in the last bits of its factor shows in the likelihood.
-__global__ void chol_update_kernel(double* A, int m, int lda, int k, int T) {
-  // tile (i, j), k < j <= i < k+1+T, enumerated over the lower triangle
-  int b = blockIdx.x;
-  int ii = (int)((sqrt(8.0 * b + 1.0) - 1.0) * 0.5);
-  while ((ii + 1) * (ii + 2) / 2 <= b) ++ii;
-  while (ii * (ii + 1) / 2 > b) --ii;
-  int jj = b - ii * (ii + 1) / 2;
-  const int i0 = (k + 1 + ii) * NB, j0 = (k + 1 + jj) * NB, k0 = k * NB;
-  __shared__ double Li[NB][NB + 1];
-  __shared__ double Lj[NB][NB + 1];
-  for (int idx = threadIdx.x; idx < NB * NB; idx += blockDim.x) {
-    int r = idx / NB, c = idx % NB;
-    Li[r][c] = (i0 + r < m && k0 + c < m) ? A[(size_t)(i0 + r) * lda + k0 + c] : 0.0;
-    Lj[r][c] = (j0 + r < m && k0 + c < m) ? A[(size_t)(j0 + r) * lda + k0 + c] : 0.0;
-  }
-  __syncthreads();
-  const int tx = threadIdx.x % 16, ty = threadIdx.x / 16;
-  double acc[2][2] = {{0, 0}, {0, 0}};
-#pragma unroll 8
-  for (int c = 0; c < NB; ++c) {
-    double a0 = Li[ty][c], a1 = Li[ty + 16][c];
-    double b0 = Lj[tx][c], b1 = Lj[tx + 16][c];
-    acc[0][0] += a0 * b0; acc[0][1] += a0 * b1;
-    acc[1][0] += a1 * b0; acc[1][1] += a1 * b1;
-  }
-  for (int u = 0; u < 2; ++u)
-    for (int v = 0; v < 2; ++v) {
-      int r = i0 + ty + 16 * u, c = j0 + tx + 16 * v;
-      if (r < m && c < m && c <= r) A[(size_t)r * lda + c] -= acc[u][v];
-    }
-}
-
 cudaError_t dense_cholesky(double* A, int m, int lda, int* status, int code, cudaStream_t s) {
   if (m <= 0) return cudaSuccess;
-  const int nt = (m + NB - 1) / NB;
+  const int nt = (m + CH - 1) / CH;
   for (int k = 0; k < nt; ++k) {
-    chol_panel_kernel<<<nt - k, 256, 0, s>>>(A, m, lda, k, status, code);
-    int T = nt - k - 1;
+    chol_panel_kernel<<<nt - k, 128, 0, s>>>(A, m, lda, k, status, code);
+    const int T = nt - k - 1;
     if (T > 0) chol_update_kernel<<<T * (T + 1) / 2, 256, 0, s>>>(A, m, lda, k, T);
   }
   return cudaGetLastError();
