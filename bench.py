@@ -163,9 +163,9 @@ def launches_per_eval(m):
 # DRAM bytes per point of a kernel, from one ncu capture of the kernel as it stands
 # (dram__bytes_read.sum + dram__bytes_write.sum at n = 100,000; traffic grows with n).
 NCU_DRAM_BYTES_PER_POINT = {
-    # factor_kernel<float, 3> at commit 0b484a5 (unchanged since f9d5560): 379.6 MB read +
-    # 203.2 MB written for 100,000 points
-    "vecchia_factor": ((379.561472 + 203.194368) * 1e6 / 100_000,
+    # factor_kernel<float, 3> as of 9ae5d38 (captured at 2ae5bb2): 380.2 MB read + 199.9 MB
+    # written for 100,000 points
+    "vecchia_factor": ((380.208384 + 199.875584) * 1e6 / 100_000,
                        "ncu dram__bytes_read.sum + dram__bytes_write.sum, factor_kernel<float, 3>, n = 100,000, "
                        "profiles/tc_A_factor_gram_n100k.md"),
 }
