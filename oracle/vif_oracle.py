@@ -17,7 +17,9 @@ dense solves, sparse products, sorting) as the only building blocks:
   Sylvester (Sec. 2.2), and the dense definitions used as pins;
 * predictive means and variances (Prop. 2.1, App. C.1);
 * Laplace mode finding for a Bernoulli-logit likelihood (Eq. one_it_newton_mode)
-  with preconditioned CG (Eq. pcls1) and the VIFDU preconditioner (Sec. 4.3, App. E.1).
+  with preconditioned CG (Eq. pcls1) and the VIFDU preconditioner (Sec. 4.3, App. E.1);
+* the VIF-Laplace likelihood (Eq. log_det_VIFLA) with the preconditioned SLQ
+  log-determinant (Eq. slq_v1, App. D), probes drawn by the recipe of Sec. 4.3.
 
 Readings of points the paper leaves open (all shared with the CUDA path):
   R1 kernel forms of Rasmussen & Williams; "range" = length scale lambda.
@@ -648,6 +650,118 @@ def laplace_mode(vif: VIF, y, tol=1e-6, max_pcg=1000, max_newton=50, psi_tol=1e-
             return b, t, tot
         psi_old = psi
     return b, max_newton, tot
+
+
+# ----------------------------------------------------------------------------
+# VIF-Laplace negative log-marginal likelihood (Eq. log_det_VIFLA) with the
+# preconditioned stochastic Lanczos quadrature of Eq. slq_v1 (Sec. 4.1, App. D)
+# ----------------------------------------------------------------------------
+def vifdu_logdet(vif: VIF, W) -> float:
+    """log det P^ = log det(W + D^{-1}) - log det M + log det M_3 (App. E.1, Sylvester)."""
+    ld = float(np.log(W + vif.Dinv).sum())
+    if vif.m:
+        pre = VIFDU(vif, W)
+        ld += 2.0 * float(np.log(np.diag(pre.M3cf[0])).sum()) - 2.0 * float(np.log(np.diag(vif.Mcf[0])).sum())
+    return ld
+
+
+def vifdu_sample(vif: VIF, W, eps1, eps2, eps3):
+    """A draw from N(0, P^) by the recipe of Sec. 4.3:
+    B^T W^{1/2} eps3 + Sigma_dagger^{-1} (B^{-1} D^{1/2} eps2 + Sigma_mn^T Sigma_m^{-T/2} eps1),
+    Sigma_m = L L^T (L lower) and Sigma_m^{-T/2} = L^{-T}, so that the bracket has covariance
+    Sigma_dagger (reading of the paper's Sigma_m^{-1/2}).  eps1 (m), eps2, eps3 (n) are standard
+    normal vectors supplied by the caller."""
+    s = spla.spsolve_triangular(vif.B.tocsr(), np.sqrt(vif.D) * eps2, lower=True)
+    if vif.m:
+        s = s + vif.lowrank.Smn.T @ sla.solve_triangular(vif.lowrank.cf[0], eps1, lower=True, trans="T")
+    return vif.B.T @ (np.sqrt(W) * eps3) + vif.Sigma_dagger_inv(s)
+
+
+def pcg_lanczos(matvec, precond, v, tol: float, max_iter: int):
+    """The PCG of `pcg` (Eq. pcls1, R10 stopping rule), also returning the Lanczos
+    tridiagonal matrix of the preconditioned operator that its coefficients define
+    (App. D, after Saad): with step lengths alpha_j and direction updates
+    beta_j = r_{j+1}^T z_{j+1} / r_j^T z_j,
+        T[0,0] = 1/alpha_0,  T[j,j] = 1/alpha_j + beta_{j-1}/alpha_{j-1},
+        T[j,j-1] = T[j-1,j] = sqrt(beta_{j-1})/alpha_{j-1},
+    and the starting vector's squared length v^T P^{-1} v.
+    Returns (x, iterations, rel_res, T, v^T P^{-1} v)."""
+    x = np.zeros_like(v)
+    r = v.copy()
+    nv = np.linalg.norm(v)
+    z = precond(r)
+    p = z.copy()
+    rz = r @ z
+    rz0 = rz
+    alphas, betas = [], []
+    it, rel = 0, 0.0
+    for it in range(1, max_iter + 1):
+        Ap = matvec(p)
+        alpha = rz / (p @ Ap)
+        alphas.append(alpha)
+        x += alpha * p
+        r -= alpha * Ap
+        rel = np.linalg.norm(r) / nv
+        if rel <= tol:
+            break
+        z = precond(r)
+        rz_new = r @ z
+        betas.append(rz_new / rz)
+        p = z + betas[-1] * p
+        rz = rz_new
+    k = len(alphas)
+    T = np.zeros((k, k))
+    for j in range(k):
+        T[j, j] = 1.0 / alphas[j] + (betas[j - 1] / alphas[j - 1] if j > 0 else 0.0)
+        if j > 0:
+            T[j, j - 1] = T[j - 1, j] = math.sqrt(betas[j - 1]) / alphas[j - 1]
+    return x, it, rel, T, float(rz0)
+
+
+def lanczos_log_quadrature(T) -> float:
+    """e_1^T log(T) e_1: Gauss quadrature of log with the eigenvalues of T as nodes
+    and the squared first eigenvector components as weights (App. D)."""
+    lam, V = np.linalg.eigh(T)
+    return float((V[0, :] ** 2) @ np.log(lam))
+
+
+def vifla_nll_slq(vif: VIF, y, b, eps, tol: float, max_iter: int = 1000):
+    """L^VIFLA of Eq. log_det_VIFLA at the mode b, the log-determinant by Eq. slq_v1:
+        log det(Sigma_dagger W + I) ~ log det Sigma_dagger + (n/l) sum_i e_1^T log(T_i) e_1 + log det P^,
+    T_i from PCG on (W + Sigma_dagger^{-1}) x = z_i with the VIFDU preconditioner P^ and
+    z_i ~ N(0, P^) drawn from eps[i] = (eps1 (m), eps2 (n), eps3 (n)).  Returns a dict with
+    the NLL and its parts, the per-probe quadratures q_i, z_i^T P^{-1} z_i and PCG counts."""
+    n, m = vif.n, vif.m
+    g, W = bern_grad_W(y, b)
+    pre = VIFDU(vif, W)
+    A = lambda w: W * w + vif.Sigma_dagger_inv(w)
+    q, zpz, its = [], [], []
+    for e in np.atleast_2d(eps):
+        z = vifdu_sample(vif, W, e[:m], e[m:m + n], e[m + n:m + 2 * n])
+        _, it, _, T, zz = pcg_lanczos(A, pre.apply, z, tol, max_iter)
+        q.append(lanczos_log_quadrature(T))
+        zpz.append(zz)
+        its.append(it)
+    q, zpz = np.array(q), np.array(zpz)
+    ld_sigma = vif.logdet()
+    ld_P = vifdu_logdet(vif, W)
+    slq = n / len(q) * float(q.sum())
+    logdet = ld_sigma + slq + ld_P
+    nll_lik = -bern_loglik(y, b)
+    quad = float(b @ vif.Sigma_dagger_inv(b))
+    return dict(nll=nll_lik + 0.5 * quad + 0.5 * logdet, neg_log_lik=nll_lik, quad=quad,
+                logdet_sigma=ld_sigma, logdet_P=ld_P, slq_term=slq, logdet=logdet,
+                logdet_exact_norm=ld_sigma + float((zpz * q).mean()) + ld_P,
+                q=q, zPz=zpz, pcg_iters=np.array(its))
+
+
+def vifla_logdet_dense(vif: VIF, b) -> float:
+    """log det(Sigma_dagger W + I) from the dense Sigma_dagger (small n): the exact value
+    the SLQ estimate targets."""
+    _, W = bern_grad_W(np.zeros_like(b), b)
+    S = vif.dense_Sigma_dagger()
+    sgn, ld = np.linalg.slogdet(S * W[None, :] + np.eye(vif.n))
+    return float(ld)
 
 
 # ----------------------------------------------------------------------------

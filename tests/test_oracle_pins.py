@@ -251,6 +251,84 @@ def test_laplace_mode_is_stationary_and_pcg_agrees_with_dense_newton():
     assert steps < 20 and its > 0
 
 
+# --------------------------------------------------------------------------- VIF-Laplace likelihood, SLQ
+def _lap_problem(n=70, m=6, mv=3, seed=21):
+    P = small_problem(n=n, m=m, mv=mv, nugget=0.0, likelihood="bernoulli_logit", ls=0.15, seed=seed)
+    N = O.causal_neighbors(P.X, P.Z, P.theta, mv) if mv else np.zeros((n, 0), dtype=np.int64)
+    vif = O.VIF(P.X, P.Z, P.theta, N)
+    b, _, _ = O.laplace_mode(vif, P.y, dense=True)
+    return P, vif, b
+
+
+def test_vifdu_probe_recipe_has_covariance_P():
+    """Sec. 4.3: the map (eps1, eps2, eps3) -> z is linear; Z Z^T must equal P^ exactly."""
+    P, vif, b = _lap_problem()
+    n, m = vif.n, vif.m
+    _, W = O.bern_grad_W(P.y, b)
+    cols = []
+    for e in np.eye(m + 2 * n):
+        cols.append(O.vifdu_sample(vif, W, e[:m], e[m:m + n], e[m + n:]))
+    Zmap = np.column_stack(cols)
+    Pd = O.VIFDU(vif, W).dense(W)
+    np.testing.assert_allclose(Zmap @ Zmap.T, Pd, rtol=1e-9, atol=1e-9 * np.abs(Pd).max())
+
+
+def test_vifdu_logdet_equals_dense_logdet():
+    """App. E.1 (Sylvester): log det P^ = log det(W + D^-1) - log det M + log det M_3."""
+    P, vif, b = _lap_problem(mv=4, seed=22)
+    _, W = O.bern_grad_W(P.y, b)
+    sgn, ld = np.linalg.slogdet(O.VIFDU(vif, W).dense(W))
+    assert sgn > 0
+    assert abs(O.vifdu_logdet(vif, W) - ld) <= 1e-9 * abs(ld)
+
+
+def test_lanczos_from_pcg_coefficients_is_exact_gauss_quadrature():
+    """App. D: once the Krylov space is exhausted, |P^{-1/2} z|^2 e_1^T log(T) e_1 with T from
+    the PCG coefficients equals z^T P^{-1/2} log(P^{-1/2} A P^{-1/2}) P^{-1/2} z."""
+    P, vif, b = _lap_problem(n=40, m=5, mv=3, seed=23)
+    n = vif.n
+    _, W = O.bern_grad_W(P.y, b)
+    pre = O.VIFDU(vif, W)
+    Amat = np.diag(W) + np.linalg.inv(vif.dense_Sigma_dagger())
+    z = np.random.default_rng(7).standard_normal(n)
+    _, it, rel, T, zpz = O.pcg_lanczos(lambda w: Amat @ w, pre.apply, z, 1e-14, 4 * n)
+    lam, V = np.linalg.eigh(pre.dense(W))
+    Ph = V @ np.diag(lam ** -0.5) @ V.T
+    mu, U = np.linalg.eigh(Ph @ Amat @ Ph)
+    exact = float((Ph @ z) @ (U @ (np.log(mu) * (U.T @ (Ph @ z)))))
+    assert abs(zpz - float(z @ np.linalg.solve(pre.dense(W), z))) <= 1e-7 * zpz
+    assert abs(zpz * O.lanczos_log_quadrature(T) - exact) <= 1e-7 * abs(exact), (it, rel)
+
+
+def test_slq_without_neighbours_is_exact():
+    """m_v = 0: B = I, so P^ = W + Sigma_dagger^{-1} is the system itself, every T_i = [1] and
+    the estimate of Eq. slq_v1 is log det Sigma_dagger + log det P^ = log det(Sigma_dagger W + I)."""
+    P, vif, b = _lap_problem(mv=0, seed=24)
+    eps = np.random.default_rng(8).standard_normal((3, vif.m + 2 * vif.n))
+    r = O.vifla_nll_slq(vif, P.y, b, eps, 1e-10)
+    np.testing.assert_allclose(r["q"], 0.0, atol=1e-12)
+    exact = O.vifla_logdet_dense(vif, b)
+    assert abs(r["logdet"] - exact) <= 1e-10 * abs(exact)
+    assert abs(r["nll"] - (-O.bern_loglik(P.y, b) + 0.5 * r["quad"] + 0.5 * exact)) <= 1e-10 * abs(r["nll"])
+
+
+def test_slq_estimate_is_unbiased_within_its_standard_error():
+    """Hutchinson over probes z ~ N(0, P^): the exactly normalised estimate averages to the dense
+    log det(Sigma_dagger W + I); the paper's n/l normalisation (Eq. slq_v1) to within O(1/n)."""
+    P, vif, b = _lap_problem(n=60, m=5, mv=4, seed=25)
+    n, m = vif.n, vif.m
+    eps = np.random.default_rng(9).standard_normal((300, m + 2 * n))
+    r = O.vifla_nll_slq(vif, P.y, b, eps, 1e-12)
+    exact = O.vifla_logdet_dense(vif, b)
+    base = r["logdet_sigma"] + r["logdet_P"]
+    terms = r["zPz"] * r["q"]
+    se = terms.std(ddof=1) / math.sqrt(len(terms))
+    assert abs(r["logdet_exact_norm"] - exact) <= 4.0 * se + 1e-9, (r["logdet_exact_norm"], exact, se)
+    terms_n = n * r["q"]
+    se_n = terms_n.std(ddof=1) / math.sqrt(len(terms_n))
+    assert abs(base + terms_n.mean() - exact) <= 4.0 * se_n + 0.05 * abs(exact - base) + 1e-9
+
+
 # --------------------------------------------------------------------------- gradient
 def test_fd_gradient_with_full_conditioning_is_the_exact_gp_gradient():
     """m_v = n-1 makes the VIF likelihood the exact one, whose gradient is analytic."""
