@@ -298,6 +298,19 @@ def laplace_block(args, stream):
            "plain": {"precond": "VIFDU", "newton_iters": st["newton_iters"],
                      "pcg_iters_total": st["pcg_iters_total"], "ms_pcg": st["ms_pcg"],
                      "ms_total_device": st["ms_total"], "wall_s": wall, "objective": st["objective"]}}
+    # the VIF-Laplace likelihood with the SLQ log-determinant (Eq. slq_v1): l = 50 probes and
+    # CG tolerance 0.01, the paper's defaults for its simulated experiments
+    nprobe, slq_tol = 50, 1e-2
+    eps = synth.slq_normals(nprobe, P.Z.shape[0], P.X.shape[0])
+    t0 = time.perf_counter()
+    nll, sl = ctx.laplace_nll(P.theta, y, eps, slq_tol=slq_tol, rel_tol=1e-6)
+    wall_slq = time.perf_counter() - t0
+    out["slq"] = {"probes": nprobe, "cg_tol": slq_tol, "nll": nll, "logdet": sl["logdet"],
+                  "logdet_exact_norm": sl["logdet_exact_norm"], "slq_term": sl["slq_term"],
+                  "logdet_precond": sl["logdet_precond"], "pcg_iters_slq": sl["pcg_iters_slq"],
+                  "ms_slq": sl["ms_slq"], "ms_per_probe": sl["ms_slq"] / nprobe, "ms_mode": sl["ms_mode"],
+                  "wall_s": wall_slq,
+                  "q_std_over_mean": float(np.std(sl["q"]) / max(abs(np.mean(sl["q"])), 1e-300))}
     wpath = os.path.join(ROOT, "paper_2507_05064_gb300", "weights", "vifdu_mlp.npy")
     if os.path.exists(wpath):
         net = V.Network(params=np.load(wpath))

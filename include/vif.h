@@ -143,6 +143,51 @@ typedef struct {
 vif_status vif_laplace_mode(vif_ctx *ctx, const vif_cov *theta, const double *y,
                             const vif_laplace_opts *opts, double *mode_out, vif_laplace_stats *stats);
 
+/* vif_laplace_nll -- the VIF-Laplace negative log-marginal likelihood of Eq. log_det_VIFLA,
+ *     L = -log p(y | b~) + b~^T Sigma_dagger^{-1} b~ / 2 + log det(Sigma_dagger W + I) / 2,
+ * at the mode b~ found as by vif_laplace_mode (same options), with the log-determinant by
+ * the preconditioned stochastic Lanczos quadrature of Eq. slq_v1 (Sec. 4.1, App. D):
+ *     log det(Sigma_dagger W + I) ~ log det Sigma_dagger + (n / l) sum_i e_1^T log(T_i) e_1 + log det P,
+ * P the VIFDU preconditioner at the mode (W' = W exp(c) when opts->precond = 1), log det P
+ * in closed form (App. E.1), T_i the Lanczos tridiagonal matrix defined by the coefficients
+ * of preconditioned CG on (W + Sigma_dagger^{-1}) x = z_i (from x = 0, stopping at
+ * ||z_i - (W + Sigma_dagger^{-1}) x||_2 <= slq_tol ||z_i||_2 or after slq_max_iter steps),
+ * and z_i ~ N(0, P) drawn by the recipe of Sec. 4.3,
+ *     z_i = B^T W'^{1/2} eps3 + Sigma_dagger^{-1} (B^{-1} D^{1/2} eps2 + Sigma_mn^T L_m^{-T} eps1)
+ * (Sigma_m = L_m L_m^T), from the standard normal numbers the caller supplies.
+ *   eps: nprobe x (m + 2n) row-major float64 (host or device); row i is (eps1 (m), eps2 (n),
+ *        eps3 (n)) of probe i.
+ *   nll_out: host scalar.  probe_q, probe_zpz: host arrays of nprobe (may be NULL):
+ *        e_1^T log(T_i) e_1 and z_i^T P^{-1} z_i.  stats: host, may be NULL.
+ * Errors as vif_laplace_mode; VIF_ERR_NOT_PD if a Lanczos matrix is not positive definite;
+ * VIF_ERR_NOT_CONVERGED (outputs still written) if Newton or a CG solve hit its cap. */
+typedef struct {
+  double nll;                 /* L of Eq. log_det_VIFLA with the estimate of Eq. slq_v1 */
+  double neg_log_lik;         /* -log p(y | b~) */
+  double quad;                /* b~^T Sigma_dagger^{-1} b~ */
+  double logdet_sigma;        /* log det Sigma_dagger = log det C + sum_i log D_i */
+  double logdet_precond;      /* log det P = sum_i log(W'_i + 1/D_i) - log det C + log det C_3 */
+  double slq_term;            /* (n / l) sum_i e_1^T log(T_i) e_1 */
+  double logdet;              /* estimate of log det(Sigma_dagger W + I) (Eq. slq_v1) */
+  double logdet_exact_norm;   /* the same with z_i^T P^{-1} z_i in place of n */
+  int32_t newton_iters;       /* Newton steps of the mode search */
+  int32_t pcg_iters_mode;     /* CG iterations of the Newton solves */
+  int32_t pcg_iters_slq;      /* CG iterations of the probe solves, summed */
+  int32_t reserved;
+  double ms_mode;             /* device time of the mode search */
+  double ms_slq;              /* wall time of the probes (sampling, CG, quadrature) */
+} vif_laplace_nll_stats;
+
+vif_status vif_laplace_nll(vif_ctx *ctx, const vif_cov *theta, const double *y, const vif_laplace_opts *opts,
+                           int32_t nprobe, const double *eps, double slq_tol, int32_t slq_max_iter,
+                           double *nll_out, double *probe_q, double *probe_zpz, vif_laplace_nll_stats *stats);
+
+/* vif_tridiag_log_quadrature -- e_1^T log(T) e_1 for a symmetric positive-definite
+ * tridiagonal T (diagonal diag[0..k-1], off-diagonal offdiag[0..k-2], host arrays): the
+ * Gauss quadrature of App. D, by implicit symmetric QR with Wilkinson shifts on the host
+ * (no GPU involved).  VIF_ERR_NOT_PD if T is not positive definite. */
+vif_status vif_tridiag_log_quadrature(const double *diag, const double *offdiag, int32_t k, double *out);
+
 /* Learned diagonal correction of the VIFDU preconditioner (the paper has none):
  * c_i = 4 tanh(o_i / 4), o_i from a tanh network 8 -> 64 -> 64 -> 1 on local features
  * of point i, and the preconditioner uses W'_i = W_i exp(c_i).  The network lives in a

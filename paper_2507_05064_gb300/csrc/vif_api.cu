@@ -3,6 +3,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <chrono>
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
@@ -54,6 +55,7 @@ struct vif_ctx {
   int4 *sched_fwd = nullptr, *sched_rev = nullptr;      // level schedules of B^{-1} and B^{-T}
   int64_t nsteps_fwd = 0, nsteps_rev = 0, ch_nnz = 0;
   double* ch_coef = nullptr;                            // coefficient of each child term
+  double* slq_eps = nullptr;                            // normals of one SLQ probe (m + 2n)
   double *l_b = nullptr, *l_W = nullptr, *l_v = nullptr, *l_Ginv = nullptr, *l_om = nullptr, *l_rsD = nullptr,
          *l_ll = nullptr, *l_x = nullptr, *l_r = nullptr, *l_z = nullptr, *l_p = nullptr, *l_Ap = nullptr,
          *l_t = nullptr, *l_t2 = nullptr, *l_x1 = nullptr, *l_sdi = nullptr, *l_sm = nullptr, *l_cm = nullptr,
@@ -277,7 +279,7 @@ void free_ctx(vif_ctx* c) {
                    c->ch_slot, c->l_b,  c->l_W,    c->l_v,    c->l_Ginv, c->l_om,   c->l_rsD,  c->l_ll,
                    c->l_x,    c->l_r,   c->l_z,    c->l_p,    c->l_Ap,   c->l_t,    c->l_t2,   c->l_x1,
                    c->l_sdi,  c->l_sm,  c->l_cm,   c->l_tm,   c->l_part, c->l_LinvC, c->l_G3,  c->l_LinvC3,
-                   c->l_sc,   c->l_red, c->l_corr, c->sched_fwd, c->sched_rev, c->ch_coef, c->l_counter, c->l_abort, c->m_feat,
+                   c->l_sc,   c->l_red, c->l_corr, c->sched_fwd, c->sched_rev, c->ch_coef, c->slq_eps, c->l_counter, c->l_abort, c->m_feat,
                    c->m_gc,   c->m_part, c->m_grad};
   for (void* b : pbufs)
     if (b) cudaFree(b);
@@ -932,19 +934,25 @@ vif_status lap_c3(vif_ctx* ctx, const LapOps& o) {
 }
 
 // Preconditioned CG from x = 0 on (W + Sigma_dagger^{-1}) x = v (v in l_v, x in l_x).
-vif_status lap_pcg(vif_ctx* ctx, const LapOps& o, double tol, int max_it, int* iters, double* rel, bool* capped) {
+// Optionally records the CG step lengths alpha_j, the direction updates beta_j and the
+// starting value r_0^T P^{-1} r_0 (the Lanczos coefficients of App. D).
+vif_status lap_pcg(vif_ctx* ctx, const LapOps& o, double tol, int max_it, int* iters, double* rel, bool* capped,
+                   std::vector<double>* alphas = nullptr, std::vector<double>* betas = nullptr,
+                   double* rz0 = nullptr) {
   cudaStream_t s = ctx->stream;
   const int64_t n = ctx->n;
   double* sc = ctx->l_sc;   // [0]=rz [1]=pAp [2]=alpha [3]=rr [4]=rz_new [5]=beta [6]=vv
+  double* hs = ctx->h_pin + 16;
   CK(cudaMemsetAsync(ctx->l_x, 0, n * sizeof(double), s));
   CK(cudaMemcpyAsync(ctx->l_r, ctx->l_v, n * sizeof(double), cudaMemcpyDeviceToDevice, s));
   CK(lap_dot(ctx->l_v, ctx->l_v, n, ctx->l_red, sc + 6, s));
   CK(lap_precond(o, ctx->l_r, ctx->l_z, s));
   CK(cudaMemcpyAsync(ctx->l_p, ctx->l_z, n * sizeof(double), cudaMemcpyDeviceToDevice, s));
   CK(lap_dot(ctx->l_r, ctx->l_z, n, ctx->l_red, sc + 0, s));
-  CK(cudaMemcpyAsync(ctx->h_pin + 8, sc + 6, sizeof(double), cudaMemcpyDeviceToHost, s));
+  CK(cudaMemcpyAsync(hs, sc, 7 * sizeof(double), cudaMemcpyDeviceToHost, s));
   CK(cudaStreamSynchronize(s));
-  const double vnorm = std::sqrt(ctx->h_pin[8]);
+  const double vnorm = std::sqrt(hs[6]);
+  if (rz0) *rz0 = hs[0];
   int it = 0;
   *rel = 0.0;
   *capped = false;
@@ -956,10 +964,13 @@ vif_status lap_pcg(vif_ctx* ctx, const LapOps& o, double tol, int max_it, int* i
       CK(lap_axpy(n, sc + 2, ctx->l_x, ctx->l_p, ctx->l_x, 0, s));
       CK(lap_axpy(n, sc + 2, ctx->l_r, ctx->l_Ap, ctx->l_r, 1, s));
       CK(lap_dot(ctx->l_r, ctx->l_r, n, ctx->l_red, sc + 3, s));
-      CK(cudaMemcpyAsync(ctx->h_pin + 8, sc + 3, sizeof(double), cudaMemcpyDeviceToHost, s));
+      CK(cudaMemcpyAsync(hs, sc, 6 * sizeof(double), cudaMemcpyDeviceToHost, s));
       CK(cudaMemcpyAsync(ctx->h_pin + 9, ctx->status, 4 * sizeof(int), cudaMemcpyDeviceToHost, s));
       CK(cudaStreamSynchronize(s));
-      *rel = std::sqrt(ctx->h_pin[8]) / vnorm;
+      // hs[2] = alpha of this step; hs[5] = beta of the previous one (set at its end)
+      if (alphas) alphas->push_back(hs[2]);
+      if (betas && it >= 2) betas->push_back(hs[5]);
+      *rel = std::sqrt(hs[3]) / vnorm;
       if (reinterpret_cast<const int*>(ctx->h_pin + 9)[0] != ST_OK) break;
       if (*rel <= tol) break;
       CK(lap_precond(o, ctx->l_r, ctx->l_z, s));
@@ -976,6 +987,64 @@ vif_status lap_pcg(vif_ctx* ctx, const LapOps& o, double tol, int max_it, int* i
   CKS(read_status(ctx, dummy, 0));
   *iters = it;
   return VIF_OK;
+}
+
+// e_1^T log(T) e_1 for the symmetric tridiagonal T with diagonal d[0..k-1] and
+// off-diagonal e[0..k-2]: the Gauss quadrature of log whose nodes are the eigenvalues
+// of T and whose weights are the squared first components of its eigenvectors (App. D).
+// The eigenvalues come from implicit symmetric QR steps with a Wilkinson shift (Golub &
+// Van Loan, Sec. 8.3): each step chases a bulge down the unreduced block with Givens
+// rotations T <- G T G^T; only the first row of the accumulated rotations is kept.
+// Returns false if T is not positive definite or a block fails to converge.
+bool tridiag_log_quadrature(std::vector<double> d, std::vector<double> e, double* out) {
+  const int k = (int)d.size();
+  *out = 0.0;
+  if (k == 0) return true;
+  e.resize(k, 0.0);
+  std::vector<double> z(k, 0.0);   // first row of the accumulated rotations
+  z[0] = 1.0;
+  const double eps = 4.0 * 2.220446049250313e-16;
+  int hi = k - 1, guard = 0;
+  while (hi > 0) {
+    for (int i = 0; i < hi; ++i)
+      if (std::fabs(e[i]) <= eps * (std::fabs(d[i]) + std::fabs(d[i + 1]))) e[i] = 0.0;
+    if (e[hi - 1] == 0.0) {
+      --hi;
+      continue;
+    }
+    int lo = hi - 1;
+    while (lo > 0 && e[lo - 1] != 0.0) --lo;
+    if (++guard > 60 * k) return false;
+    // Wilkinson shift: the eigenvalue of the trailing 2 x 2 block nearer to d[hi]
+    const double dd = 0.5 * (d[hi - 1] - d[hi]), bb = e[hi - 1];
+    const double mu = d[hi] - bb * bb / (dd + std::copysign(std::hypot(dd, bb), dd == 0.0 ? 1.0 : dd));
+    double x = d[lo] - mu, y = e[lo];
+    for (int j = lo; j < hi; ++j) {
+      // rotation G = [[c, s], [-s, c]] on coordinates (j, j+1) with G [x; y] = [r; 0]
+      const double r = std::hypot(x, y);
+      const double c = r == 0.0 ? 1.0 : x / r, sn = r == 0.0 ? 0.0 : y / r;
+      if (j > lo) e[j - 1] = r;   // the bulge below e[j-1] is annihilated
+      const double p = d[j], q = d[j + 1], b = e[j];
+      d[j] = c * c * p + 2.0 * c * sn * b + sn * sn * q;
+      d[j + 1] = sn * sn * p - 2.0 * c * sn * b + c * c * q;
+      e[j] = c * sn * (q - p) + (c * c - sn * sn) * b;
+      if (j + 1 < hi) {   // the rotation of columns (j, j+1) pushes e[j+1] into a bulge at (j+2, j)
+        y = sn * e[j + 1];
+        e[j + 1] = c * e[j + 1];
+        x = e[j];
+      }
+      const double zj = z[j], zj1 = z[j + 1];
+      z[j] = c * zj + sn * zj1;
+      z[j + 1] = -sn * zj + c * zj1;
+    }
+  }
+  double q = 0.0;
+  for (int j = 0; j < k; ++j) {
+    if (!(d[j] > 0.0)) return false;
+    q += z[j] * z[j] * std::log(d[j]);
+  }
+  *out = q;
+  return true;
 }
 
 // mlp scratch: features (n x 8 float), gc (n float), backward partials, gradient
@@ -997,18 +1066,15 @@ vif_status mlp_correction_c(vif_ctx* ctx, const void* net) {
   return VIF_OK;
 }
 
-}  // namespace
-
-extern "C" {
-
-vif_status vif_laplace_mode(vif_ctx* ctx, const vif_cov* theta, const double* y, const vif_laplace_opts* lo,
-                            double* mode_out, vif_laplace_stats* stats) {
-  if (!ctx) return VIF_ERR_ARG;
-  ctx->err[0] = 0;
-  if (!y || !lo || !mode_out) return set_err(ctx, VIF_ERR_ARG, "y, opts and mode_out are required");
+// Newton search of the Laplace mode (Eq. one_it_newton_mode), shared by vif_laplace_mode
+// and vif_laplace_nll.  Leaves the mode in l_b and W, G^{-1}, omega, 1/sqrt(D) and the
+// log-likelihood terms at the mode in the Laplace buffers.
+vif_status laplace_run(vif_ctx* ctx, const vif_cov* theta, const double* y, const vif_laplace_opts* lo, LapOps* op,
+                       vif_laplace_stats* stats, bool* converged_out, bool* capped_out) {
+  if (!y || !lo) return set_err(ctx, VIF_ERR_ARG, "y and opts are required");
   CKS(check_cov(ctx, theta, ctx->d));
   if (ctx->likelihood != VIF_BERNOULLI_LOGIT)
-    return set_err(ctx, VIF_ERR_STATE, "vif_laplace_mode needs a context built for VIF_BERNOULLI_LOGIT");
+    return set_err(ctx, VIF_ERR_STATE, "the Laplace approximation needs a context built for VIF_BERNOULLI_LOGIT");
   if (theta->nugget != 0.0) return set_err(ctx, VIF_ERR_ARG, "a latent GP has no nugget: set nugget = 0");
   if (!(lo->rel_tol > 0.0) || lo->max_pcg < 1 || lo->max_newton < 1 || lo->reserved != 0)
     return set_err(ctx, VIF_ERR_ARG, "invalid Laplace options");
@@ -1028,7 +1094,7 @@ vif_status vif_laplace_mode(vif_ctx* ctx, const vif_cov* theta, const double* y,
     }
   } guard{e0, e1};
   CK(cudaEventRecord(e0, s));
-  LapOps o;
+  LapOps& o = *op;
   CKS(lap_setup(ctx, theta, y, &o));
   const bool learned = lo->precond == 1;
   const double* corr = learned ? ctx->l_corr : nullptr;
@@ -1081,21 +1147,155 @@ vif_status vif_laplace_mode(vif_ctx* ctx, const vif_cov* theta, const double* y,
   }
   if (newton > lo->max_newton) newton = lo->max_newton;
   CK(cudaEventRecord(e1, s));
-  CKS(download(ctx, mode_out, ctx->l_b, (size_t)n * sizeof(double)));
+  CK(cudaEventSynchronize(e1));
   float tot = 0.f;
   CK(cudaEventElapsedTime(&tot, e0, e1));
-  if (stats) {
-    stats->newton_iters = newton;
-    stats->pcg_iters_total = pcg_total;
-    stats->final_rel_res = rel;
-    stats->ms_pcg = ms_pcg;
-    stats->ms_total = tot;
-    stats->objective = psi;
-  }
-  if (!converged || pcg_capped)
-    return set_err(ctx, VIF_ERR_NOT_CONVERGED, "Newton %s, CG %s", converged ? "converged" : "hit its cap",
-                   pcg_capped ? "hit its cap" : "converged");
+  stats->newton_iters = newton;
+  stats->pcg_iters_total = pcg_total;
+  stats->final_rel_res = rel;
+  stats->ms_pcg = ms_pcg;
+  stats->ms_total = tot;
+  stats->objective = psi;
+  *converged_out = converged;
+  *capped_out = pcg_capped;
   return VIF_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+vif_status vif_laplace_mode(vif_ctx* ctx, const vif_cov* theta, const double* y, const vif_laplace_opts* lo,
+                            double* mode_out, vif_laplace_stats* stats) {
+  if (!ctx) return VIF_ERR_ARG;
+  ctx->err[0] = 0;
+  if (!mode_out) return set_err(ctx, VIF_ERR_ARG, "mode_out is required");
+  LapOps o;
+  vif_laplace_stats st{};
+  bool converged = false, capped = false;
+  CKS(laplace_run(ctx, theta, y, lo, &o, &st, &converged, &capped));
+  CKS(download(ctx, mode_out, ctx->l_b, (size_t)ctx->n * sizeof(double)));
+  if (stats) *stats = st;
+  if (!converged || capped)
+    return set_err(ctx, VIF_ERR_NOT_CONVERGED, "Newton %s, CG %s", converged ? "converged" : "hit its cap",
+                   capped ? "hit its cap" : "converged");
+  return VIF_OK;
+}
+
+vif_status vif_laplace_nll(vif_ctx* ctx, const vif_cov* theta, const double* y, const vif_laplace_opts* lo,
+                           int32_t nprobe, const double* eps, double slq_tol, int32_t slq_max_iter, double* nll_out,
+                           double* probe_q, double* probe_zpz, vif_laplace_nll_stats* stats) {
+  if (!ctx) return VIF_ERR_ARG;
+  ctx->err[0] = 0;
+  if (!nll_out || !eps || nprobe < 1 || !(slq_tol > 0.0) || slq_max_iter < 1)
+    return set_err(ctx, VIF_ERR_ARG, "nll_out, eps, nprobe >= 1, slq_tol > 0 and slq_max_iter >= 1 are required");
+  LapOps o;
+  vif_laplace_stats ms{};
+  bool converged = false, capped = false;
+  CKS(laplace_run(ctx, theta, y, lo, &o, &ms, &converged, &capped));
+  const int64_t n = ctx->n;
+  const int m = ctx->m;
+  cudaStream_t s = ctx->stream;
+  const bool learned = lo->precond == 1;
+  // C_3 of the preconditioner at the mode's W (Sec. 4.3, App. E.1)
+  CKS(lap_c3(ctx, o));
+  // log-determinant pieces and the two other terms of Eq. log_det_VIFLA
+  double* sc = ctx->l_sc;
+  CK(reduce_sum(ctx->logD, n, ctx->red, sc + 9, s));                        // sum log D_i
+  CK(lap_log_sum(ctx->l_Ginv, n, 1, -1.0, ctx->l_red, sc + 10, s));         // sum log(W'_i + 1/D_i)
+  if (m > 0) {
+    CK(lap_log_sum(ctx->G, m, (int64_t)ctx->fpad + 1, 2.0, ctx->l_red, sc + 11, s));      // log det C
+    CK(lap_log_sum(ctx->l_G3, m, (int64_t)ctx->fpad + 1, 2.0, ctx->l_red, sc + 12, s));   // log det C_3
+  } else {
+    CK(cudaMemsetAsync(sc + 11, 0, 2 * sizeof(double), s));
+  }
+  CK(lap_dot(ctx->l_ll, nullptr, n, ctx->l_red, sc + 13, s));              // log p(y | b~)
+  CK(lap_matvec(o, ctx->l_b, nullptr, ctx->l_sdi, s));
+  CK(lap_dot(ctx->l_b, ctx->l_sdi, n, ctx->l_red, sc + 14, s));            // b~^T Sigma_dagger^{-1} b~
+  double h[6];
+  CK(cudaMemcpyAsync(ctx->h_pin + 32, sc + 9, 6 * sizeof(double), cudaMemcpyDeviceToHost, s));
+  CK(cudaStreamSynchronize(s));
+  memcpy(h, ctx->h_pin + 32, sizeof(h));
+  // probes
+  double *A64, *F64, *LT64;
+  CKS(fp64_buffers(ctx, &A64, &F64, &LT64));
+  if (!ctx->slq_eps) CKS(dalloc(ctx, &ctx->slq_eps, (size_t)m + 2 * (size_t)n));
+  const size_t per = (size_t)m + 2 * (size_t)n;
+  const auto t0 = std::chrono::steady_clock::now();
+  double qsum = 0.0, wsum = 0.0;
+  int slq_iters = 0;
+  bool slq_capped = false;
+  for (int i = 0; i < nprobe; ++i) {
+    CKS(upload(ctx, ctx->slq_eps, eps + (size_t)i * per, per * sizeof(double)));
+    const double* e1 = ctx->slq_eps;
+    const double* e2 = ctx->slq_eps + m;
+    const double* e3 = ctx->slq_eps + m + n;
+    // z = B^T W'^{1/2} eps3 + Sigma_dagger^{-1} (B^{-1} D^{1/2} eps2 + A^T eps1)   (Sec. 4.3)
+    CK(lap_probe_prep(n, ctx->Dv, ctx->l_W, learned ? ctx->l_corr : nullptr, e2, e3, ctx->l_r, ctx->l_z, s));
+    CK(lap_solve_B(o, ctx->l_r, ctx->l_p, s));
+    if (m > 0) {
+      CK(lap_rows_dot_add(A64, ctx->mpad, m, n, e1, ctx->l_p, ctx->l_Ap, s));
+    } else {
+      CK(cudaMemcpyAsync(ctx->l_Ap, ctx->l_p, n * sizeof(double), cudaMemcpyDeviceToDevice, s));
+    }
+    CK(lap_matvec(o, ctx->l_Ap, nullptr, ctx->l_x, s));
+    CK(lap_apply_Bt(o, ctx->l_z, ctx->l_r, s));
+    CK(lap_vec_add(n, ctx->l_x, ctx->l_r, ctx->l_v, s));
+    // PCG on (W + Sigma_dagger^{-1}) x = z, its coefficients giving T_i (App. D)
+    std::vector<double> al, be;
+    double zpz = 0.0, rel = 0.0;
+    int it = 0;
+    bool cp = false;
+    CKS(lap_pcg(ctx, o, slq_tol, slq_max_iter, &it, &rel, &cp, &al, &be, &zpz));
+    slq_iters += it;
+    slq_capped = slq_capped || cp;
+    std::vector<double> d(al.size()), od(al.size() > 0 ? al.size() - 1 : 0);
+    for (size_t j = 0; j < al.size(); ++j) {
+      d[j] = 1.0 / al[j] + (j > 0 ? be[j - 1] / al[j - 1] : 0.0);
+      if (j > 0) od[j - 1] = std::sqrt(be[j - 1]) / al[j - 1];
+    }
+    double q = 0.0;
+    if (!tridiag_log_quadrature(d, od, &q))
+      return set_err(ctx, VIF_ERR_NOT_PD, "Lanczos matrix of probe %d is not positive definite", i);
+    if (probe_q) probe_q[i] = q;
+    if (probe_zpz) probe_zpz[i] = zpz;
+    qsum += q;
+    wsum += zpz * q;
+  }
+  const double ms_slq =
+      std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+  const double logdet_sigma = h[2] + h[0];
+  const double logdet_P = h[1] - h[2] + h[3];
+  const double slq = (double)n / nprobe * qsum;
+  const double logdet = logdet_sigma + slq + logdet_P;
+  const double nll = -h[4] + 0.5 * h[5] + 0.5 * logdet;
+  *nll_out = nll;
+  if (stats) {
+    stats->nll = nll;
+    stats->neg_log_lik = -h[4];
+    stats->quad = h[5];
+    stats->logdet_sigma = logdet_sigma;
+    stats->logdet_precond = logdet_P;
+    stats->slq_term = slq;
+    stats->logdet = logdet;
+    stats->logdet_exact_norm = logdet_sigma + wsum / nprobe + logdet_P;
+    stats->newton_iters = ms.newton_iters;
+    stats->pcg_iters_mode = ms.pcg_iters_total;
+    stats->pcg_iters_slq = slq_iters;
+    stats->reserved = 0;
+    stats->ms_mode = ms.ms_total;
+    stats->ms_slq = ms_slq;
+  }
+  if (!converged || capped || slq_capped)
+    return set_err(ctx, VIF_ERR_NOT_CONVERGED, "Newton %s, CG %s", converged ? "converged" : "hit its cap",
+                   (capped || slq_capped) ? "hit its cap" : "converged");
+  return VIF_OK;
+}
+
+vif_status vif_tridiag_log_quadrature(const double* diag, const double* offdiag, int32_t k, double* out) {
+  if (!diag || !out || k < 0 || (k > 1 && !offdiag)) return VIF_ERR_ARG;
+  std::vector<double> d(diag, diag + k), e(k > 1 ? offdiag : diag, k > 1 ? offdiag + (k - 1) : diag);
+  return tridiag_log_quadrature(d, e, out) ? VIF_OK : VIF_ERR_NOT_PD;
 }
 
 size_t vif_mlp_bytes(void) { return mlp_bytes(); }

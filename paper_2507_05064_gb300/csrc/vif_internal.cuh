@@ -185,6 +185,16 @@ struct LapOps {
 cudaError_t lap_matvec(const LapOps& o, const double* x, const double* diagW, double* out, cudaStream_t s);
 cudaError_t lap_precond(const LapOps& o, const double* w, double* out, cudaStream_t s);
 cudaError_t lap_child_coef(const LapOps& o, double* ch_coef, cudaStream_t s);
+// VIF-Laplace likelihood with SLQ (Eq. log_det_VIFLA, Eq. slq_v1): probe pieces and log-sums
+cudaError_t lap_log_sum(const double* x, int64_t n, int64_t stride, double sgn, double* partial, double* out,
+                        cudaStream_t s);
+cudaError_t lap_probe_prep(int64_t n, const double* D, const double* W, const double* corr, const double* eps2,
+                           const double* eps3, double* u, double* v, cudaStream_t s);
+cudaError_t lap_vec_add(int64_t n, const double* a, const double* b, double* out, cudaStream_t s);
+cudaError_t lap_solve_B(const LapOps& o, const double* rhs, double* out, cudaStream_t s);
+cudaError_t lap_apply_Bt(const LapOps& o, const double* u, double* out, cudaStream_t s);
+cudaError_t lap_rows_dot_add(const double* rows, int ld, int m, int64_t n, const double* c, const double* base,
+                             double* out, cudaStream_t s);
 cudaError_t lap_pointwise(const double* y, const double* b, const double* D, const double* corr, int64_t n, double* W,
                           double* v, double* Ginv, double* omega, double* rsD, double* ll, cudaStream_t s);
 cudaError_t lap_dot(const double* a, const double* b, int64_t n, double* partial, double* out, cudaStream_t s);

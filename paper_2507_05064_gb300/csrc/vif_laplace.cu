@@ -492,6 +492,85 @@ cudaError_t lap_precond(const LapOps& o, const double* w, double* out, cudaStrea
   return cudaGetLastError();
 }
 
+// ---------------------------------------------------------------------------
+// Pieces of the VIF-Laplace likelihood with the preconditioned SLQ log-determinant
+// (Eq. log_det_VIFLA, Eq. slq_v1): probe draws z ~ N(0, P) by the recipe of Sec. 4.3
+// and the log-determinants of App. E.1.
+// ---------------------------------------------------------------------------
+
+// u_i = sqrt(D_i) eps2_i ;  v_i = sqrt(W'_i) eps3_i with W' = W exp(clip(corr, 4)) (corr may be NULL)
+__global__ void probe_prep_kernel(int64_t n, const double* __restrict__ D, const double* __restrict__ W,
+                                  const double* __restrict__ corr, const double* __restrict__ eps2,
+                                  const double* __restrict__ eps3, double* u, double* v) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  double wp = W[i];
+  if (corr) wp *= exp(fmin(fmax(corr[i], -4.0), 4.0));
+  u[i] = sqrt(D[i]) * eps2[i];
+  v[i] = sqrt(wp) * eps3[i];
+}
+
+__global__ void vec_add_kernel(int64_t n, const double* __restrict__ a, const double* __restrict__ b, double* out) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) out[i] = a[i] + b[i];
+}
+
+// partial[b] = sum over this block's share of sgn * log(x[i * stride])
+__global__ void logsum_stage1(const double* x, int64_t n, int64_t stride, double sgn, double* partial) {
+  __shared__ double sh[256];
+  double v = 0.0;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    v += log(x[i * stride]);
+  sh[threadIdx.x] = sgn * v;
+  __syncthreads();
+  for (int w = 128; w > 0; w >>= 1) {
+    if (threadIdx.x < w) sh[threadIdx.x] += sh[threadIdx.x + w];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) partial[blockIdx.x] = sh[0];
+}
+
+cudaError_t lap_log_sum(const double* x, int64_t n, int64_t stride, double sgn, double* partial, double* out,
+                        cudaStream_t s) {
+  logsum_stage1<<<256, 256, 0, s>>>(x, n, stride, sgn, partial);
+  dot_stage2<<<1, 256, 0, s>>>(partial, 256, out);
+  return cudaGetLastError();
+}
+
+cudaError_t lap_probe_prep(int64_t n, const double* D, const double* W, const double* corr, const double* eps2,
+                           const double* eps3, double* u, double* v, cudaStream_t s) {
+  probe_prep_kernel<<<blocks(n, 256), 256, 0, s>>>(n, D, W, corr, eps2, eps3, u, v);
+  return cudaGetLastError();
+}
+
+cudaError_t lap_vec_add(int64_t n, const double* a, const double* b, double* out, cudaStream_t s) {
+  vec_add_kernel<<<blocks(n, 256), 256, 0, s>>>(n, a, b, out);
+  return cudaGetLastError();
+}
+
+// out = B^{-1} rhs (level-scheduled solve)
+cudaError_t lap_solve_B(const LapOps& o, const double* rhs, double* out, cudaStream_t s) {
+  if (o.mv == 0) return cudaMemcpyAsync(out, rhs, o.n * sizeof(double), cudaMemcpyDeviceToDevice, s);
+  cudaError_t e = cudaMemsetAsync(out, 0xFF, (size_t)o.n * sizeof(double), s);
+  if (e != cudaSuccess) return e;
+  return launch_trsv(o.sched_fwd, o.nsteps_fwd, o.N, o.Acoef, rhs, out, o.abort_flag, o.status, s);
+}
+
+// out = B^T u
+cudaError_t lap_apply_Bt(const LapOps& o, const double* u, double* out, cudaStream_t s) {
+  btx_kernel<<<blocks(o.nsteps_rev, 8), 256, 0, s>>>(o.sched_rev, o.nsteps_rev, o.ch_row, o.ch_coef, u, nullptr,
+                                                      nullptr, out);
+  return cudaGetLastError();
+}
+
+// out_i = base_i + rows_i . c  (rows: n x m, leading dimension ld, 16-byte aligned rows)
+cudaError_t lap_rows_dot_add(const double* rows, int ld, int m, int64_t n, const double* c, const double* base,
+                             double* out, cudaStream_t s) {
+  const size_t smem = (size_t)((m + 3) & ~3) * sizeof(double);
+  f_dot_kernel<<<blocks(n, FD_THREADS), FD_THREADS, smem, s>>>(rows, ld, m, n, c, base, 1.0, nullptr, nullptr, out);
+  return cudaGetLastError();
+}
+
 cudaError_t lap_pointwise(const double* y, const double* b, const double* D, const double* corr, int64_t n, double* W,
                           double* v, double* Gd, double* omega, double* rsD, double* ll, cudaStream_t s) {
   lap_pointwise_kernel<<<blocks(n, 256), 256, 0, s>>>(y, b, D, corr, n, W, v, Gd, omega, rsD, ll);

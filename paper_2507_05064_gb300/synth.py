@@ -187,3 +187,10 @@ def config5(nprob=256, n_lo=2_000, n_hi=50_000, seed=20250712, lloyd=2):
         out.append(make_problem(n, d, m, mv, kind, 1.0, rng_range, nug, seed * 1000 + k, lloyd=lloyd,
                                 rff=256, name=f"c5-{k}"))
     return out
+
+
+def slq_normals(nprobe: int, m: int, n: int, seed: int = 20250714) -> np.ndarray:
+    """Standard normal numbers of nprobe SLQ probes, row i = (eps1 (m), eps2 (n), eps3 (n)):
+    the random draws of the probe recipe, generated here so that every implementation
+    receives the same ones."""
+    return _rng(seed).standard_normal((nprobe, m + 2 * n))

@@ -22,7 +22,8 @@ FP64, MIXED = 0, 1
 GAUSSIAN, BERNOULLI_LOGIT = 0, 1
 
 # every symbol include/vif.h declares
-EXPORTS = ["vif_build", "vif_nll", "vif_predict", "vif_laplace_mode", "vif_batch_create", "vif_batch_run",
+EXPORTS = ["vif_build", "vif_nll", "vif_predict", "vif_laplace_mode", "vif_laplace_nll",
+           "vif_tridiag_log_quadrature", "vif_batch_create", "vif_batch_run",
            "vif_batch_info", "vif_batch_destroy", "vif_mlp_bytes", "vif_mlp_init", "vif_mlp_set_params",
            "vif_mlp_get_params", "vif_mlp_forward", "vif_mlp_backward", "vif_mlp_features", "vif_mlp_train", "vif_set_neighbors", "vif_get_neighbors",
            "vif_get_factors", "vif_get_knn_stats", "vif_get_stage_times", "vif_nll_noalloc",
@@ -43,6 +44,14 @@ class VifOpts(C.Structure):
 class LaplaceOpts(C.Structure):
     _fields_ = [("rel_tol", C.c_double), ("max_pcg", C.c_int32), ("max_newton", C.c_int32),
                 ("precond", C.c_int32), ("reserved", C.c_int32), ("mlp_weights", C.c_void_p)]
+
+
+class LaplaceNllStats(C.Structure):
+    _fields_ = [("nll", C.c_double), ("neg_log_lik", C.c_double), ("quad", C.c_double),
+                ("logdet_sigma", C.c_double), ("logdet_precond", C.c_double), ("slq_term", C.c_double),
+                ("logdet", C.c_double), ("logdet_exact_norm", C.c_double), ("newton_iters", C.c_int32),
+                ("pcg_iters_mode", C.c_int32), ("pcg_iters_slq", C.c_int32), ("reserved", C.c_int32),
+                ("ms_mode", C.c_double), ("ms_slq", C.c_double)]
 
 
 class LaplaceStats(C.Structure):
@@ -89,6 +98,9 @@ def lib() -> C.CDLL:
         L.vif_predict.argtypes = [vp, C.POINTER(VifCov), vp, vp, i64, i32, vp, vp]
         L.vif_laplace_mode.argtypes = [vp, C.POINTER(VifCov), vp, C.POINTER(LaplaceOpts), vp,
                                        C.POINTER(LaplaceStats)]
+        L.vif_laplace_nll.argtypes = [vp, C.POINTER(VifCov), vp, C.POINTER(LaplaceOpts), i32, vp, C.c_double,
+                                      i32, dp, vp, vp, C.POINTER(LaplaceNllStats)]
+        L.vif_tridiag_log_quadrature.argtypes = [vp, vp, i32, dp]
         L.vif_set_neighbors.argtypes = [vp, vp]
         L.vif_get_neighbors.argtypes = [vp, vp]
         L.vif_get_factors.argtypes = [vp, vp, vp]
@@ -239,6 +251,17 @@ class Batch:
             pass
 
 
+def tridiag_log_quadrature(diag, offdiag) -> float:
+    """e_1^T log(T) e_1 of a symmetric tridiagonal T (host computation in the library)."""
+    d = np.ascontiguousarray(diag, dtype=np.float64)
+    e = np.ascontiguousarray(offdiag, dtype=np.float64)
+    out = C.c_double()
+    st = lib().vif_tridiag_log_quadrature(_ptr(d), _ptr(e) if e.size else None, int(d.size), C.byref(out))
+    if st != VIF_OK:
+        raise VifError(st, "vif_tridiag_log_quadrature")
+    return out.value
+
+
 class Context:
     """One built VIF problem: data, inducing points and neighbour sets (vif_build)."""
 
@@ -300,6 +323,29 @@ class Context:
         stats = {k: getattr(st, k) for k, _ in LaplaceStats._fields_}
         stats["status"] = rc
         return mode, stats
+
+    def laplace_nll(self, theta, y, eps, slq_tol=1e-2, slq_max_iter=1000, rel_tol=1e-6, max_pcg=1000,
+                    max_newton=50, precond=0, mlp_weights=None, allow_not_converged=False):
+        """VIF-Laplace NLL (Eq. log_det_VIFLA) with the SLQ log-determinant of Eq. slq_v1;
+        eps: (nprobe, m + 2n) standard normal numbers (host or device).  Returns
+        (nll, stats dict with per-probe 'q' and 'zPz')."""
+        cv, ls = make_cov(theta)
+        wp = None if mlp_weights is None else _ptr(getattr(mlp_weights, "buf", mlp_weights)).value
+        opts = LaplaceOpts(float(rel_tol), int(max_pcg), int(max_newton), int(precond), 0, wp)
+        e = _f64(eps)
+        nprobe = int(e.shape[0])
+        q = np.zeros(nprobe)
+        zpz = np.zeros(nprobe)
+        out = C.c_double()
+        st = LaplaceNllStats()
+        rc = lib().vif_laplace_nll(self.h, C.byref(cv), _ptr(_f64(y)), C.byref(opts), nprobe, _ptr(e),
+                                   float(slq_tol), int(slq_max_iter), C.byref(out), _ptr(q), _ptr(zpz),
+                                   C.byref(st))
+        if not (rc == VIF_OK or (allow_not_converged and rc == VIF_ERR_NOT_CONVERGED)):
+            self._check(rc)
+        stats = {k: getattr(st, k) for k, _ in LaplaceNllStats._fields_}
+        stats["q"], stats["zPz"], stats["status"] = q, zpz, rc
+        return out.value, stats
 
     def mlp_features(self, W) -> np.ndarray:
         F = np.empty((self.n, MLP_NIN), dtype=np.float32)

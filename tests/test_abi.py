@@ -56,3 +56,52 @@ def test_build_rejects_bad_arguments_before_touching_the_gpu(lib):
     bad = V.VifOpts(7, 0, 0, 0, (C.c_int32 * 4)())
     assert lib.vif_build(V._ptr(X), 4, 2, None, 0, 2, C.byref(cv), C.byref(bad), None, C.byref(h)) == V.VIF_ERR_ARG
     assert lib.vif_last_error(None) is not None
+
+
+def test_laplace_nll_stats_layout_matches_header():
+    import ctypes as C
+    assert C.sizeof(V.LaplaceNllStats) == 8 * 8 + 4 * 4 + 2 * 8
+    assert V.LaplaceNllStats.newton_iters.offset == 64 and V.LaplaceNllStats.ms_mode.offset == 80
+
+
+def _tridiag_reference(d, e):
+    import numpy as np
+    T = np.diag(d) + np.diag(e, 1) + np.diag(e, -1)
+    lam, U = np.linalg.eigh(T)
+    return float((U[0] ** 2) @ np.log(lam))
+
+
+@pytest.mark.parametrize("k,kind", [(1, "random"), (2, "random"), (7, "random"), (60, "random"),
+                                    (300, "random"), (40, "clustered"), (120, "lanczos-like")])
+def test_tridiagonal_log_quadrature_matches_eigendecomposition(lib, k, kind):
+    """The host Gauss quadrature e_1^T log(T) e_1 of the SLQ (App. D) against numpy's
+    symmetric eigendecomposition (no GPU involved)."""
+    import numpy as np
+    rng = np.random.default_rng(k)
+    if kind == "random":
+        e = rng.uniform(-1.0, 1.0, k - 1)
+        d = rng.uniform(0.5, 3.0, k) + np.abs(np.concatenate([e, [0]])) + np.abs(np.concatenate([[0], e]))
+    elif kind == "clustered":
+        # eigenvalues in two tight clusters, tridiagonalised by Householder reflections
+        lam = np.concatenate([1.0 + 1e-9 * rng.standard_normal(k // 2), 5.0 + 1e-9 * rng.standard_normal(k - k // 2)])
+        Qm, _ = np.linalg.qr(rng.standard_normal((k, k)))
+        import scipy.linalg as sla
+        H = sla.hessenberg(Qm @ np.diag(lam) @ Qm.T)
+        d, e = np.diag(H).copy(), np.diag(H, -1).copy()
+    else:
+        # the shape CG produces: diagonal 1/alpha_j + beta_{j-1}/alpha_{j-1}, off sqrt(beta)/alpha
+        al = rng.uniform(0.2, 2.0, k)
+        be = rng.uniform(0.05, 0.9, k - 1)
+        d = 1.0 / al + np.concatenate([[0.0], be / al[:-1]])
+        e = np.sqrt(be) / al[:-1]
+    got = V.tridiag_log_quadrature(d, e)
+    ref = _tridiag_reference(d, e)
+    assert abs(got - ref) <= 1e-11 * max(1.0, abs(ref)), (got, ref)
+
+
+def test_tridiagonal_log_quadrature_rejects_an_indefinite_matrix(lib):
+    import numpy as np
+    with pytest.raises(V.VifError) as ei:
+        V.tridiag_log_quadrature(np.array([1.0, -2.0, 1.0]), np.array([0.1, 0.1]))
+    assert ei.value.status == V.VIF_ERR_NOT_PD
+

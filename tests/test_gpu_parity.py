@@ -314,6 +314,62 @@ def test_laplace_solves_on_deep_and_wide_dependency_graphs(shape):
     ctx.close()
 
 
+# --------------------------------------------------------------------------- VIF-Laplace NLL with SLQ
+def _vifla_case(n, m, mv, seed):
+    P = bern(n, m, mv, seed)
+    N = O.causal_neighbors(P.X, P.Z, P.theta, mv) if mv else np.zeros((n, 0), dtype=np.int64)
+    vif = O.VIF(P.X, P.Z, P.theta, N)
+    b_dense, _, _ = O.laplace_mode(vif, P.y, dense=True)
+    ctx = V.Context(P.X, P.Z if m else None, mv, P.theta, likelihood=V.BERNOULLI_LOGIT, neighbor_search=False)
+    if mv:
+        ctx.set_neighbors(N.astype(np.int32))
+    return P, vif, b_dense, ctx
+
+
+def test_vifla_nll_with_slq_matches_oracle_probe_by_probe():
+    """Eq. log_det_VIFLA with the SLQ of Eq. slq_v1: same normals, same probes (Sec. 4.3), same
+    PCG-Lanczos matrices, same quadratures and log-determinants as the oracle."""
+    P, vif, b_dense, ctx = _vifla_case(1500, 25, 10, 41)
+    eps = synth.slq_normals(6, vif.m, vif.n, seed=5)
+    nll, st = ctx.laplace_nll(P.theta, P.y, eps, slq_tol=1e-6, rel_tol=1e-10)
+    ref = O.vifla_nll_slq(vif, P.y, b_dense, eps, 1e-6)
+    for key in ("neg_log_lik", "quad", "logdet_sigma"):
+        assert abs(st[key] - ref[key]) <= 1e-8 * max(1.0, abs(ref[key])), (key, st[key], ref[key])
+    assert abs(st["logdet_precond"] - ref["logdet_P"]) <= 1e-8 * abs(ref["logdet_P"])
+    np.testing.assert_allclose(st["zPz"], ref["zPz"], rtol=1e-7)
+    np.testing.assert_allclose(st["q"], ref["q"], rtol=1e-5, atol=1e-8)
+    assert abs(st["pcg_iters_slq"] - int(ref["pcg_iters"].sum())) <= len(eps)
+    assert abs(nll - ref["nll"]) <= 1e-7 * abs(ref["nll"]), (nll, ref["nll"])
+    assert abs(st["logdet_exact_norm"] - ref["logdet_exact_norm"]) <= 1e-7 * abs(ref["logdet_exact_norm"])
+    ctx.close()
+
+
+def test_vifla_nll_without_neighbours_is_exact():
+    """m_v = 0: P = W + Sigma_dagger^{-1} exactly, every quadrature vanishes and the NLL is the
+    dense VIF-Laplace likelihood."""
+    P, vif, b_dense, ctx = _vifla_case(800, 20, 0, 42)
+    eps = synth.slq_normals(3, vif.m, vif.n, seed=6)
+    nll, st = ctx.laplace_nll(P.theta, P.y, eps, slq_tol=1e-8, rel_tol=1e-10)
+    np.testing.assert_allclose(st["q"], 0.0, atol=1e-10)
+    exact = -O.bern_loglik(P.y, b_dense) + 0.5 * float(b_dense @ vif.Sigma_dagger_inv(b_dense)) \
+        + 0.5 * O.vifla_logdet_dense(vif, b_dense)
+    assert abs(nll - exact) <= 1e-8 * abs(exact), (nll, exact)
+    ctx.close()
+
+
+def test_vifla_nll_untrained_learned_correction_equals_plain_vifdu():
+    """An untrained network outputs c = 0, so W' = W: the learned variant of the SLQ (probes,
+    preconditioner and log det P all use W') must reproduce plain VIFDU."""
+    P, vif, b_dense, ctx = _vifla_case(1200, 20, 8, 43)
+    eps = synth.slq_normals(4, vif.m, vif.n, seed=7)
+    net = V.Network(seed=3)
+    a, sa = ctx.laplace_nll(P.theta, P.y, eps, slq_tol=1e-6, rel_tol=1e-10)
+    b, sb = ctx.laplace_nll(P.theta, P.y, eps, slq_tol=1e-6, rel_tol=1e-10, precond=1, mlp_weights=net)
+    assert abs(a - b) <= 1e-9 * abs(a)
+    np.testing.assert_allclose(sa["q"], sb["q"], rtol=1e-9, atol=1e-12)
+    ctx.close()
+
+
 def test_laplace_rejects_a_nugget():
     P = bern(300, 10, 4, 34)
     ctx = V.Context(P.X, P.Z, 4, P.theta, likelihood=V.BERNOULLI_LOGIT)
