@@ -19,7 +19,9 @@ dense solves, sparse products, sorting) as the only building blocks:
 * Laplace mode finding for a Bernoulli-logit likelihood (Eq. one_it_newton_mode)
   with preconditioned CG (Eq. pcls1) and the VIFDU preconditioner (Sec. 4.3, App. E.1);
 * the VIF-Laplace likelihood (Eq. log_det_VIFLA) with the preconditioned SLQ
-  log-determinant (Eq. slq_v1, App. D), probes drawn by the recipe of Sec. 4.3.
+  log-determinant (Eq. slq_v1, App. D), probes drawn by the recipe of Sec. 4.3;
+* the FITC preconditioner (Sec. 4.3, App. E.2) with the system form of Eq. pcls2 and
+  the SLQ form of Eq. slq_v2.
 
 Readings of points the paper leaves open (all shared with the CUDA path):
   R1 kernel forms of Rasmussen & Williams; "range" = length scale lambda.
@@ -752,6 +754,109 @@ def vifla_nll_slq(vif: VIF, y, b, eps, tol: float, max_iter: int = 1000):
     return dict(nll=nll_lik + 0.5 * quad + 0.5 * logdet, neg_log_lik=nll_lik, quad=quad,
                 logdet_sigma=ld_sigma, logdet_P=ld_P, slq_term=slq, logdet=logdet,
                 logdet_exact_norm=ld_sigma + float((zpz * q).mean()) + ld_P,
+                q=q, zPz=zpz, pcg_iters=np.array(its))
+
+
+class FITCPrecond:
+    """FITC preconditioner P^ = D_V + Sigma_kn^T Sigma_k^{-1} Sigma_kn with
+    D_V = diag(Sigma - Sigma_kn^T Sigma_k^{-1} Sigma_kn) + W^{-1} (Sec. 4.3, App. E.2), its
+    inducing points being those of the VIF approximation (k = m).  Solves by Woodbury with
+    M_V = Sigma_k + Sigma_kn D_V^{-1} Sigma_kn^T; log det by Sylvester; draws by
+    D_V^{1/2} eps2 + Sigma_kn^T Sigma_k^{-T/2} eps1 (Sigma_k = L L^T, L lower)."""
+
+    def __init__(self, vif: VIF, W):
+        self.vif = vif
+        lr = vif.lowrank
+        self.DV = vif.theta.variance - (lr.lr_diag() if vif.m else 0.0) + 1.0 / W
+        if vif.m:
+            self.MV = lr.Sm + lr.Smn @ (lr.Smn.T / self.DV[:, None])
+            self.MVcf = sla.cho_factor(self.MV, lower=True)
+
+    def apply(self, w):
+        g = w / self.DV
+        if self.vif.m:
+            lr = self.vif.lowrank
+            g = g - (lr.Smn.T @ sla.cho_solve(self.MVcf, lr.Smn @ g)) / self.DV
+        return g
+
+    def logdet(self) -> float:
+        ld = float(np.log(self.DV).sum())
+        if self.vif.m:
+            ld += 2.0 * float(np.log(np.diag(self.MVcf[0])).sum()) - self.vif.lowrank.logdet_Sm()
+        return ld
+
+    def sample(self, eps1, eps2):
+        z = np.sqrt(self.DV) * eps2
+        if self.vif.m:
+            lr = self.vif.lowrank
+            z = z + lr.Smn.T @ sla.solve_triangular(lr.cf[0], eps1, lower=True, trans="T")
+        return z
+
+    def dense(self) -> np.ndarray:
+        S = np.diag(self.DV)
+        if self.vif.m:
+            S = S + self.vif.lowrank.Smn.T @ self.vif.lowrank.SinvSmn
+        return S
+
+
+def Sigma_dagger_matvec(vif: VIF, x):
+    """Sigma_dagger x = B^{-1} D B^{-T} x + Sigma_mn^T Sigma_m^{-1} Sigma_mn x (Sec. 2.1)."""
+    t = spla.spsolve_triangular(vif.B.T.tocsr(), x, lower=False)
+    out = spla.spsolve_triangular(vif.B.tocsr(), vif.D * t, lower=True)
+    if vif.m:
+        out = out + vif.lowrank.Smn.T @ (vif.lowrank.SinvSmn @ x)
+    return out
+
+
+def laplace_mode_fitc(vif: VIF, y, tol=1e-6, max_pcg=1000, max_newton=50, psi_tol=1e-10):
+    """Newton iterations of Eq. one_it_newton_mode from b = 0 (R10), each system solved in the
+    form of Eq. pcls2, (W^{-1} + Sigma_dagger)(W u) = Sigma_dagger v, by PCG with the FITC
+    preconditioner.  Returns (mode, newton_steps, total_pcg_iterations)."""
+    n = vif.n
+    b = np.zeros(n)
+    psi_old = None
+    tot = 0
+    for t in range(1, max_newton + 1):
+        g, W = bern_grad_W(y, b)
+        v = W * b + g
+        pre = FITCPrecond(vif, W)
+        rhs = Sigma_dagger_matvec(vif, v)
+        yw, it, _ = pcg(lambda w: w / W + Sigma_dagger_matvec(vif, w), pre.apply, rhs, tol, max_pcg)
+        b = yw / W
+        tot += it
+        psi = bern_loglik(y, b) - 0.5 * float(b @ vif.Sigma_dagger_inv(b))
+        if psi_old is not None and abs(psi - psi_old) <= psi_tol * abs(psi):
+            return b, t, tot
+        psi_old = psi
+    return b, max_newton, tot
+
+
+def vifla_nll_slq_fitc(vif: VIF, y, b, eps, tol: float, max_iter: int = 1000):
+    """L^VIFLA of Eq. log_det_VIFLA at the mode b, the log-determinant by Eq. slq_v2:
+        log det(Sigma_dagger W + I) ~ log det W + (n/l) sum_i e_1^T log(T_i) e_1 + log det P^,
+    T_i from PCG on (W^{-1} + Sigma_dagger) x = z_i with the FITC preconditioner P^ and
+    z_i ~ N(0, P^) drawn from eps[i] = (eps1 (m), eps2 (n))."""
+    n, m = vif.n, vif.m
+    g, W = bern_grad_W(y, b)
+    pre = FITCPrecond(vif, W)
+    A = lambda w: w / W + Sigma_dagger_matvec(vif, w)
+    q, zpz, its = [], [], []
+    for e in np.atleast_2d(eps):
+        z = pre.sample(e[:m], e[m:m + n])
+        _, it, _, T, zz = pcg_lanczos(A, pre.apply, z, tol, max_iter)
+        q.append(lanczos_log_quadrature(T))
+        zpz.append(zz)
+        its.append(it)
+    q, zpz = np.array(q), np.array(zpz)
+    ld_W = float(np.log(W).sum())
+    ld_P = pre.logdet()
+    slq = n / len(q) * float(q.sum())
+    logdet = ld_W + slq + ld_P
+    nll_lik = -bern_loglik(y, b)
+    quad = float(b @ vif.Sigma_dagger_inv(b))
+    return dict(nll=nll_lik + 0.5 * quad + 0.5 * logdet, neg_log_lik=nll_lik, quad=quad,
+                logdet_W=ld_W, logdet_P=ld_P, slq_term=slq, logdet=logdet,
+                logdet_exact_norm=ld_W + float((zpz * q).mean()) + ld_P,
                 q=q, zPz=zpz, pcg_iters=np.array(its))
 
 

@@ -329,6 +329,61 @@ def test_slq_estimate_is_unbiased_within_its_standard_error():
     assert abs(base + terms_n.mean() - exact) <= 4.0 * se_n + 0.05 * abs(exact - base) + 1e-9
 
 
+def test_fitc_preconditioner_solve_logdet_and_draws_match_its_dense_definition():
+    """App. E.2: Woodbury solve = dense inverse, Sylvester log det = dense log det, and the draw
+    map D_V^{1/2} eps2 + Sigma_kn^T Sigma_k^{-T/2} eps1 has covariance P^ exactly."""
+    P, vif, b = _lap_problem(mv=4, seed=26)
+    n, m = vif.n, vif.m
+    _, W = O.bern_grad_W(P.y, b)
+    pre = O.FITCPrecond(vif, W)
+    Pd = pre.dense()
+    w = np.random.default_rng(10).standard_normal(n)
+    np.testing.assert_allclose(pre.apply(w), np.linalg.solve(Pd, w), rtol=1e-8, atol=1e-10)
+    sgn, ld = np.linalg.slogdet(Pd)
+    assert sgn > 0 and abs(pre.logdet() - ld) <= 1e-9 * abs(ld)
+    Zmap = np.column_stack([pre.sample(e[:m], e[m:]) for e in np.eye(m + n)])
+    np.testing.assert_allclose(Zmap @ Zmap.T, Pd, rtol=1e-9, atol=1e-9 * np.abs(Pd).max())
+    # P^ = W^{-1} + the FITC covariance (Sigma_mn^T Sigma_m^{-1} Sigma_mn + diagonal residual)
+    np.testing.assert_allclose(Pd, O.fitc_cov(P.X, P.Z, P.theta) + np.diag(1.0 / W), rtol=1e-8, atol=1e-10)
+
+
+def test_pcls2_newton_with_fitc_reaches_the_dense_mode():
+    """Eq. pcls2: solving (W^{-1} + Sigma_dagger)(W u) = Sigma_dagger v gives the Newton step of
+    Eq. one_it_newton_mode; the mode equals the dense-Newton mode."""
+    P, vif, b = _lap_problem(n=150, m=10, mv=5, seed=27)
+    b_f, steps, its = O.laplace_mode_fitc(vif, P.y, tol=1e-11)
+    np.testing.assert_allclose(b_f, b, rtol=1e-7, atol=1e-9)
+    assert its > 0 and steps < 20
+
+
+def test_slq_fitc_is_nearly_exact_when_the_vif_is_fitc_itself():
+    """m_v = 0: Sigma_dagger = Sigma_mn^T Sigma_m^{-1} Sigma_mn + diag(residual + R7 jitter), so
+    the FITC preconditioner equals W^{-1} + Sigma_dagger up to the 1e-10 sigma_1^2 jitter: every
+    quadrature is ~0 and the estimate of Eq. slq_v2 is the dense log det."""
+    P, vif, b = _lap_problem(mv=0, seed=28)
+    eps = np.random.default_rng(11).standard_normal((3, vif.m + vif.n))
+    r = O.vifla_nll_slq_fitc(vif, P.y, b, eps, 1e-10)
+    assert np.abs(r["q"]).max() <= 1e-8
+    exact = O.vifla_logdet_dense(vif, b)
+    assert abs(r["logdet"] - exact) <= 1e-8 * abs(exact) + 1e-6
+
+
+def test_slq_fitc_estimate_is_unbiased_within_its_standard_error():
+    P, vif, b = _lap_problem(n=60, m=5, mv=4, seed=29)
+    n, m = vif.n, vif.m
+    eps = np.random.default_rng(12).standard_normal((300, m + n))
+    r = O.vifla_nll_slq_fitc(vif, P.y, b, eps, 1e-12)
+    exact = O.vifla_logdet_dense(vif, b)
+    terms = r["zPz"] * r["q"]
+    se = terms.std(ddof=1) / math.sqrt(len(terms))
+    assert abs(r["logdet_exact_norm"] - exact) <= 4.0 * se + 1e-9, (r["logdet_exact_norm"], exact, se)
+    # the two SLQ forms agree on the same log-determinant
+    r1 = O.vifla_nll_slq(vif, P.y, b, np.random.default_rng(13).standard_normal((300, m + 2 * n)), 1e-12)
+    t1 = r1["zPz"] * r1["q"]
+    se1 = t1.std(ddof=1) / math.sqrt(len(t1))
+    assert abs(r["logdet_exact_norm"] - r1["logdet_exact_norm"]) <= 4.0 * math.hypot(se, se1) + 1e-9
+
+
 # --------------------------------------------------------------------------- gradient
 def test_fd_gradient_with_full_conditioning_is_the_exact_gp_gradient():
     """m_v = n-1 makes the VIF likelihood the exact one, whose gradient is analytic."""
