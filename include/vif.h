@@ -121,12 +121,17 @@ vif_status vif_predict(vif_ctx *ctx, const vif_cov *theta, const double *y, cons
  * log p(y|b) - b^T Sigma_dagger^{-1} b / 2 changes by at most 1e-10 relative.
  *   y: n responses in {0,1}.  mode_out: n values (host or device).  stats: host, may be NULL.
  *   precond: 0 = VIFDU; 1 = VIFDU with a learned diagonal correction c (W' = W exp(c),
- *   c from the two-layer network whose weights mlp_weights points to, see vif_mlp_*). */
+ *   c from the two-layer network whose weights mlp_weights points to, see vif_mlp_*);
+ *   2 = FITC, P = D_V + Sigma_mn^T Sigma_m^{-1} Sigma_mn with D_V = diag(Sigma - Sigma_mn^T
+ *   Sigma_m^{-1} Sigma_mn) + W^{-1} (Sec. 4.3, App. E.2; its inducing points are the VIF's), each
+ *   Newton system then solved in the form of Eq. pcls2, (W^{-1} + Sigma_dagger)(W b) = Sigma_dagger v,
+ *   with the same stopping rule on that system. */
 typedef struct {
   double rel_tol;             /* CG tolerance (e.g. 1e-6) */
   int32_t max_pcg;            /* CG iteration cap per Newton step (e.g. 1000) */
   int32_t max_newton;         /* Newton step cap (e.g. 50) */
-  int32_t precond;            /* 0 VIFDU, 1 VIFDU with learned diagonal correction */
+  int32_t precond;            /* 0 VIFDU (Eq. pcls1), 1 VIFDU with learned diagonal correction,
+                                 2 FITC with the VIF's inducing points (App. E.2, Eq. pcls2) */
   int32_t reserved;           /* must be zero */
   const void *mlp_weights;    /* device pointer to the packed network weights when precond = 1 */
 } vif_laplace_opts;
@@ -157,6 +162,10 @@ vif_status vif_laplace_mode(vif_ctx *ctx, const vif_cov *theta, const double *y,
  * (Sigma_m = L_m L_m^T), from the standard normal numbers the caller supplies.
  *   eps: nprobe x (m + 2n) row-major float64 (host or device); row i is (eps1 (m), eps2 (n),
  *        eps3 (n)) of probe i.
+ * With opts->precond = 2 (FITC) the estimate is that of Eq. slq_v2,
+ *     log det(Sigma_dagger W + I) ~ log det W + (n / l) sum_i e_1^T log(T_i) e_1 + log det P,
+ * T_i from CG on (W^{-1} + Sigma_dagger) x = z_i, z_i = D_V^{1/2} eps2 + Sigma_mn^T L_m^{-T} eps1
+ * (eps3 unused), log det P = log det D_V + log det(I + L_m^{-1} Sigma_mn D_V^{-1} Sigma_mn^T L_m^{-T}).
  *   nll_out: host scalar.  probe_q, probe_zpz: host arrays of nprobe (may be NULL):
  *        e_1^T log(T_i) e_1 and z_i^T P^{-1} z_i.  stats: host, may be NULL.
  * Errors as vif_laplace_mode; VIF_ERR_NOT_PD if a Lanczos matrix is not positive definite;
@@ -166,7 +175,8 @@ typedef struct {
   double neg_log_lik;         /* -log p(y | b~) */
   double quad;                /* b~^T Sigma_dagger^{-1} b~ */
   double logdet_sigma;        /* log det Sigma_dagger = log det C + sum_i log D_i */
-  double logdet_precond;      /* log det P = sum_i log(W'_i + 1/D_i) - log det C + log det C_3 */
+  double logdet_precond;      /* log det P: sum_i log(W'_i + 1/D_i) - log det C + log det C_3 (VIFDU), or
+                                 log det D_V + log det M_V (FITC) */
   double slq_term;            /* (n / l) sum_i e_1^T log(T_i) e_1 */
   double logdet;              /* estimate of log det(Sigma_dagger W + I) (Eq. slq_v1) */
   double logdet_exact_norm;   /* the same with z_i^T P^{-1} z_i in place of n */

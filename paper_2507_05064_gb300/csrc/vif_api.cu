@@ -56,6 +56,7 @@ struct vif_ctx {
   int64_t nsteps_fwd = 0, nsteps_rev = 0, ch_nnz = 0;
   double* ch_coef = nullptr;                            // coefficient of each child term
   double* slq_eps = nullptr;                            // normals of one SLQ probe (m + 2n)
+  double *l_Apad = nullptr, *l_anorm2 = nullptr, *l_dvinv = nullptr;   // FITC preconditioner
   double *l_b = nullptr, *l_W = nullptr, *l_v = nullptr, *l_Ginv = nullptr, *l_om = nullptr, *l_rsD = nullptr,
          *l_ll = nullptr, *l_x = nullptr, *l_r = nullptr, *l_z = nullptr, *l_p = nullptr, *l_Ap = nullptr,
          *l_t = nullptr, *l_t2 = nullptr, *l_x1 = nullptr, *l_sdi = nullptr, *l_sm = nullptr, *l_cm = nullptr,
@@ -279,7 +280,7 @@ void free_ctx(vif_ctx* c) {
                    c->ch_slot, c->l_b,  c->l_W,    c->l_v,    c->l_Ginv, c->l_om,   c->l_rsD,  c->l_ll,
                    c->l_x,    c->l_r,   c->l_z,    c->l_p,    c->l_Ap,   c->l_t,    c->l_t2,   c->l_x1,
                    c->l_sdi,  c->l_sm,  c->l_cm,   c->l_tm,   c->l_part, c->l_LinvC, c->l_G3,  c->l_LinvC3,
-                   c->l_sc,   c->l_red, c->l_corr, c->sched_fwd, c->sched_rev, c->ch_coef, c->slq_eps, c->l_counter, c->l_abort, c->m_feat,
+                   c->l_sc,   c->l_red, c->l_corr, c->sched_fwd, c->sched_rev, c->ch_coef, c->slq_eps, c->l_Apad, c->l_anorm2, c->l_dvinv, c->l_counter, c->l_abort, c->m_feat,
                    c->m_gc,   c->m_part, c->m_grad};
   for (void* b : pbufs)
     if (b) cudaFree(b);
@@ -919,6 +920,15 @@ vif_status lap_setup(vif_ctx* ctx, const vif_cov* theta, const double* y, LapOps
   o->counter = ctx->l_counter;
   o->abort_flag = ctx->l_abort;
   o->status = ctx->status;
+  o->kind = LAP_VIFDU;
+  o->A = A64;
+  o->Apad = ctx->l_Apad;
+  o->D = ctx->Dv;
+  o->W = ctx->l_W;
+  o->mpad = ctx->mpad;
+  o->dvinv = ctx->l_dvinv;
+  o->anorm2 = ctx->l_anorm2;
+  o->LinvMV = ctx->l_LinvC3;
   CK(lap_child_coef(*o, ctx->ch_coef, s));   // the children's coefficients of the new A
   return VIF_OK;
 }
@@ -928,6 +938,37 @@ vif_status lap_c3(vif_ctx* ctx, const LapOps& o) {
   if (ctx->m == 0) return VIF_OK;
   cudaStream_t s = ctx->stream;
   CK(gram_FtF<double>(o.F, ctx->n, ctx->fpad, ctx->m, ctx->part, ctx->nsplit, ctx->l_G3, ctx->fpad, s, ctx->l_om));
+  CK(dense_cholesky(ctx->l_G3, ctx->m, ctx->fpad, ctx->status, ST_NOTPD_PRECOND, s));
+  CK(dense_trtri_lower(ctx->l_G3, ctx->l_LinvC3, ctx->m, ctx->fpad, ctx->trw, s));
+  return VIF_OK;
+}
+
+// FITC preconditioner at the current W (App. E.2): D_V^{-1}, M_V = I + A D_V^{-1} A^T (whitened, in
+// l_G3), its Cholesky factor and inverse factor (in l_LinvC3).  A's padded copy and row norms
+// are formed on the first call after lap_setup (fresh = true).
+vif_status lap_fitc_setup(vif_ctx* ctx, LapOps& o, bool fresh, double var) {
+  cudaStream_t s = ctx->stream;
+  const int64_t n = ctx->n;
+  if (!ctx->l_dvinv) {
+    CKS(dalloc(ctx, &ctx->l_dvinv, (size_t)n));
+    CKS(dalloc(ctx, &ctx->l_anorm2, (size_t)n));
+    if (ctx->m > 0) CKS(dalloc(ctx, &ctx->l_Apad, (size_t)n * ctx->fpad));
+    fresh = true;
+  }
+  o.dvinv = ctx->l_dvinv;
+  o.anorm2 = ctx->l_anorm2;
+  o.Apad = ctx->l_Apad;
+  if (fresh) {
+    if (ctx->m > 0) {
+      CK(lap_fitc_prepare_A(o.A, ctx->mpad, ctx->m, n, ctx->fpad, ctx->l_Apad, ctx->l_anorm2, s));
+    } else {
+      CK(cudaMemsetAsync(ctx->l_anorm2, 0, (size_t)n * sizeof(double), s));
+    }
+  }
+  CK(lap_fitc_dv(n, var, ctx->l_anorm2, ctx->l_W, ctx->l_dvinv, s));
+  if (ctx->m == 0) return VIF_OK;
+  CK(gram_FtF<double>(ctx->l_Apad, n, ctx->fpad, ctx->m, ctx->part, ctx->nsplit, ctx->l_G3, ctx->fpad, s,
+                      ctx->l_dvinv));
   CK(dense_cholesky(ctx->l_G3, ctx->m, ctx->fpad, ctx->status, ST_NOTPD_PRECOND, s));
   CK(dense_trtri_lower(ctx->l_G3, ctx->l_LinvC3, ctx->m, ctx->fpad, ctx->trw, s));
   return VIF_OK;
@@ -946,7 +987,7 @@ vif_status lap_pcg(vif_ctx* ctx, const LapOps& o, double tol, int max_it, int* i
   CK(cudaMemsetAsync(ctx->l_x, 0, n * sizeof(double), s));
   CK(cudaMemcpyAsync(ctx->l_r, ctx->l_v, n * sizeof(double), cudaMemcpyDeviceToDevice, s));
   CK(lap_dot(ctx->l_v, ctx->l_v, n, ctx->l_red, sc + 6, s));
-  CK(lap_precond(o, ctx->l_r, ctx->l_z, s));
+  CK(lap_system_precond(o, ctx->l_r, ctx->l_z, s));
   CK(cudaMemcpyAsync(ctx->l_p, ctx->l_z, n * sizeof(double), cudaMemcpyDeviceToDevice, s));
   CK(lap_dot(ctx->l_r, ctx->l_z, n, ctx->l_red, sc + 0, s));
   CK(cudaMemcpyAsync(hs, sc, 7 * sizeof(double), cudaMemcpyDeviceToHost, s));
@@ -958,7 +999,7 @@ vif_status lap_pcg(vif_ctx* ctx, const LapOps& o, double tol, int max_it, int* i
   *capped = false;
   if (vnorm > 0.0) {
     for (it = 1; it <= max_it; ++it) {
-      CK(lap_matvec(o, ctx->l_p, ctx->l_W, ctx->l_Ap, s));
+      CK(lap_system_matvec(o, ctx->l_p, ctx->l_Ap, s));
       CK(lap_dot(ctx->l_p, ctx->l_Ap, n, ctx->l_red, sc + 1, s));
       CK(lap_alpha(sc, s));
       CK(lap_axpy(n, sc + 2, ctx->l_x, ctx->l_p, ctx->l_x, 0, s));
@@ -973,7 +1014,7 @@ vif_status lap_pcg(vif_ctx* ctx, const LapOps& o, double tol, int max_it, int* i
       *rel = std::sqrt(hs[3]) / vnorm;
       if (reinterpret_cast<const int*>(ctx->h_pin + 9)[0] != ST_OK) break;
       if (*rel <= tol) break;
-      CK(lap_precond(o, ctx->l_r, ctx->l_z, s));
+      CK(lap_system_precond(o, ctx->l_r, ctx->l_z, s));
       CK(lap_dot(ctx->l_r, ctx->l_z, n, ctx->l_red, sc + 4, s));
       CK(lap_beta(sc, s));
       CK(lap_axpy(n, sc + 5, ctx->l_z, nullptr, ctx->l_p, 2, s));
@@ -1078,7 +1119,8 @@ vif_status laplace_run(vif_ctx* ctx, const vif_cov* theta, const double* y, cons
   if (theta->nugget != 0.0) return set_err(ctx, VIF_ERR_ARG, "a latent GP has no nugget: set nugget = 0");
   if (!(lo->rel_tol > 0.0) || lo->max_pcg < 1 || lo->max_newton < 1 || lo->reserved != 0)
     return set_err(ctx, VIF_ERR_ARG, "invalid Laplace options");
-  if (lo->precond != 0 && lo->precond != 1) return set_err(ctx, VIF_ERR_ARG, "unknown preconditioner");
+  if (lo->precond != 0 && lo->precond != 1 && lo->precond != LAP_FITC)
+    return set_err(ctx, VIF_ERR_ARG, "unknown preconditioner");
   if (lo->precond == 1 && !lo->mlp_weights)
     return set_err(ctx, VIF_ERR_ARG, "the learned correction needs mlp_weights");
   const int64_t n = ctx->n;
@@ -1096,6 +1138,9 @@ vif_status laplace_run(vif_ctx* ctx, const vif_cov* theta, const double* y, cons
   CK(cudaEventRecord(e0, s));
   LapOps& o = *op;
   CKS(lap_setup(ctx, theta, y, &o));
+  const bool fitc = lo->precond == LAP_FITC;
+  if (fitc) o.kind = LAP_FITC;
+  bool fresh = true;   // FITC: A's padded copy is due after lap_setup
   const bool learned = lo->precond == 1;
   const double* corr = learned ? ctx->l_corr : nullptr;
   CK(cudaMemsetAsync(ctx->l_b, 0, n * sizeof(double), s));
@@ -1116,7 +1161,15 @@ vif_status laplace_run(vif_ctx* ctx, const vif_cov* theta, const double* y, cons
       CK(lap_pointwise(ctx->y, ctx->l_b, ctx->Dv, corr, n, ctx->l_W, ctx->l_v, ctx->l_Ginv, ctx->l_om,
                        ctx->l_rsD, ctx->l_ll, s));
     }
-    CKS(lap_c3(ctx, o));
+    if (fitc) {
+      // Eq. pcls2: (W^{-1} + Sigma_dagger)(W b) = Sigma_dagger v
+      CKS(lap_fitc_setup(ctx, o, fresh, theta->variance));
+      fresh = false;
+      CK(lap_sigma_matvec(o, ctx->l_v, nullptr, ctx->l_sdi, s));
+      CK(cudaMemcpyAsync(ctx->l_v, ctx->l_sdi, n * sizeof(double), cudaMemcpyDeviceToDevice, s));
+    } else {
+      CKS(lap_c3(ctx, o));
+    }
     CK(cudaEventRecord(p0, s));
     int it = 0;
     bool capped = false;
@@ -1128,7 +1181,11 @@ vif_status laplace_run(vif_ctx* ctx, const vif_cov* theta, const double* y, cons
     ms_pcg += tms;
     pcg_total += it;
     pcg_capped = pcg_capped || capped;
-    CK(cudaMemcpyAsync(ctx->l_b, ctx->l_x, n * sizeof(double), cudaMemcpyDeviceToDevice, s));
+    if (fitc) {
+      CK(lap_div(n, ctx->l_x, ctx->l_W, ctx->l_b, s));   // b = (W b) / W
+    } else {
+      CK(cudaMemcpyAsync(ctx->l_b, ctx->l_x, n * sizeof(double), cudaMemcpyDeviceToDevice, s));
+    }
     // objective at the new b: sum log p(y|b) - b^T Sigma_dagger^{-1} b / 2
     CK(lap_pointwise(ctx->y, ctx->l_b, ctx->Dv, corr, n, ctx->l_W, ctx->l_v, ctx->l_Ginv, ctx->l_om, ctx->l_rsD,
                      ctx->l_ll, s));
@@ -1197,23 +1254,33 @@ vif_status vif_laplace_nll(vif_ctx* ctx, const vif_cov* theta, const double* y, 
   const int m = ctx->m;
   cudaStream_t s = ctx->stream;
   const bool learned = lo->precond == 1;
-  // C_3 of the preconditioner at the mode's W (Sec. 4.3, App. E.1)
-  CKS(lap_c3(ctx, o));
+  const bool fitc = lo->precond == LAP_FITC;
+  // the preconditioner at the mode's W: C_3 of VIFDU (App. E.1) or M_V of FITC (App. E.2)
+  if (fitc) {
+    CKS(lap_fitc_setup(ctx, o, false, theta->variance));
+  } else {
+    CKS(lap_c3(ctx, o));
+  }
   // log-determinant pieces and the two other terms of Eq. log_det_VIFLA
   double* sc = ctx->l_sc;
   CK(reduce_sum(ctx->logD, n, ctx->red, sc + 9, s));                        // sum log D_i
-  CK(lap_log_sum(ctx->l_Ginv, n, 1, -1.0, ctx->l_red, sc + 10, s));         // sum log(W'_i + 1/D_i)
+  if (fitc) {
+    CK(lap_log_sum(ctx->l_dvinv, n, 1, -1.0, ctx->l_red, sc + 10, s));      // log det D_V
+  } else {
+    CK(lap_log_sum(ctx->l_Ginv, n, 1, -1.0, ctx->l_red, sc + 10, s));       // sum log(W'_i + 1/D_i)
+  }
   if (m > 0) {
     CK(lap_log_sum(ctx->G, m, (int64_t)ctx->fpad + 1, 2.0, ctx->l_red, sc + 11, s));      // log det C
-    CK(lap_log_sum(ctx->l_G3, m, (int64_t)ctx->fpad + 1, 2.0, ctx->l_red, sc + 12, s));   // log det C_3
+    CK(lap_log_sum(ctx->l_G3, m, (int64_t)ctx->fpad + 1, 2.0, ctx->l_red, sc + 12, s));   // log det C_3 / M_V
   } else {
     CK(cudaMemsetAsync(sc + 11, 0, 2 * sizeof(double), s));
   }
+  CK(lap_log_sum(ctx->l_W, n, 1, 1.0, ctx->l_red, sc + 15, s));             // log det W
   CK(lap_dot(ctx->l_ll, nullptr, n, ctx->l_red, sc + 13, s));              // log p(y | b~)
   CK(lap_matvec(o, ctx->l_b, nullptr, ctx->l_sdi, s));
   CK(lap_dot(ctx->l_b, ctx->l_sdi, n, ctx->l_red, sc + 14, s));            // b~^T Sigma_dagger^{-1} b~
-  double h[6];
-  CK(cudaMemcpyAsync(ctx->h_pin + 32, sc + 9, 6 * sizeof(double), cudaMemcpyDeviceToHost, s));
+  double h[7];
+  CK(cudaMemcpyAsync(ctx->h_pin + 32, sc + 9, 7 * sizeof(double), cudaMemcpyDeviceToHost, s));
   CK(cudaStreamSynchronize(s));
   memcpy(h, ctx->h_pin + 32, sizeof(h));
   // probes
@@ -1230,18 +1297,24 @@ vif_status vif_laplace_nll(vif_ctx* ctx, const vif_cov* theta, const double* y, 
     const double* e1 = ctx->slq_eps;
     const double* e2 = ctx->slq_eps + m;
     const double* e3 = ctx->slq_eps + m + n;
-    // z = B^T W'^{1/2} eps3 + Sigma_dagger^{-1} (B^{-1} D^{1/2} eps2 + A^T eps1)   (Sec. 4.3)
-    CK(lap_probe_prep(n, ctx->Dv, ctx->l_W, learned ? ctx->l_corr : nullptr, e2, e3, ctx->l_r, ctx->l_z, s));
-    CK(lap_solve_B(o, ctx->l_r, ctx->l_p, s));
-    if (m > 0) {
-      CK(lap_rows_dot_add(A64, ctx->mpad, m, n, e1, ctx->l_p, ctx->l_Ap, s));
+    if (fitc) {
+      // z = D_V^{1/2} eps2 + Sigma_mn^T L_m^{-T} eps1   (App. E.2)
+      CK(lap_fitc_probe(o, e1, e2, ctx->l_v, s));
     } else {
-      CK(cudaMemcpyAsync(ctx->l_Ap, ctx->l_p, n * sizeof(double), cudaMemcpyDeviceToDevice, s));
+      // z = B^T W'^{1/2} eps3 + Sigma_dagger^{-1} (B^{-1} D^{1/2} eps2 + A^T eps1)   (Sec. 4.3)
+      CK(lap_probe_prep(n, ctx->Dv, ctx->l_W, learned ? ctx->l_corr : nullptr, e2, e3, ctx->l_r, ctx->l_z, s));
+      CK(lap_solve_B(o, ctx->l_r, ctx->l_p, s));
+      if (m > 0) {
+        CK(lap_rows_dot_add(A64, ctx->mpad, m, n, e1, ctx->l_p, ctx->l_Ap, s));
+      } else {
+        CK(cudaMemcpyAsync(ctx->l_Ap, ctx->l_p, n * sizeof(double), cudaMemcpyDeviceToDevice, s));
+      }
+      CK(lap_matvec(o, ctx->l_Ap, nullptr, ctx->l_x, s));
+      CK(lap_apply_Bt(o, ctx->l_z, ctx->l_r, s));
+      CK(lap_vec_add(n, ctx->l_x, ctx->l_r, ctx->l_v, s));
     }
-    CK(lap_matvec(o, ctx->l_Ap, nullptr, ctx->l_x, s));
-    CK(lap_apply_Bt(o, ctx->l_z, ctx->l_r, s));
-    CK(lap_vec_add(n, ctx->l_x, ctx->l_r, ctx->l_v, s));
-    // PCG on (W + Sigma_dagger^{-1}) x = z, its coefficients giving T_i (App. D)
+    // PCG on the system of Eq. pcls1 (VIFDU) or Eq. pcls2 (FITC) with right-hand side z,
+    // its coefficients giving T_i (App. D)
     std::vector<double> al, be;
     double zpz = 0.0, rel = 0.0;
     int it = 0;
@@ -1265,9 +1338,12 @@ vif_status vif_laplace_nll(vif_ctx* ctx, const vif_cov* theta, const double* y, 
   const double ms_slq =
       std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
   const double logdet_sigma = h[2] + h[0];
-  const double logdet_P = h[1] - h[2] + h[3];
+  // VIFDU: log det P = sum log(W' + 1/D) - log det C + log det C_3 (App. E.1), Eq. slq_v1;
+  // FITC: log det P = log det D_V + log det M_V (whitened, App. E.2), Eq. slq_v2 with log det W
+  const double logdet_P = fitc ? h[1] + h[3] : h[1] - h[2] + h[3];
+  const double base = fitc ? h[6] : logdet_sigma;
   const double slq = (double)n / nprobe * qsum;
-  const double logdet = logdet_sigma + slq + logdet_P;
+  const double logdet = base + slq + logdet_P;
   const double nll = -h[4] + 0.5 * h[5] + 0.5 * logdet;
   *nll_out = nll;
   if (stats) {
@@ -1278,7 +1354,7 @@ vif_status vif_laplace_nll(vif_ctx* ctx, const vif_cov* theta, const double* y, 
     stats->logdet_precond = logdet_P;
     stats->slq_term = slq;
     stats->logdet = logdet;
-    stats->logdet_exact_norm = logdet_sigma + wsum / nprobe + logdet_P;
+    stats->logdet_exact_norm = base + wsum / nprobe + logdet_P;
     stats->newton_iters = ms.newton_iters;
     stats->pcg_iters_mode = ms.pcg_iters_total;
     stats->pcg_iters_slq = slq_iters;

@@ -165,6 +165,9 @@ cudaError_t predict_all(const double* A, const double* Xs, int64_t n, const doub
 // (slots {row, first term, end of terms, solo}); each level is padded with
 // {-1, 0, 0, 0} to a multiple of this
 constexpr int LAP_TRSV_RPS = 4;
+// preconditioner / system form of the Laplace CG
+constexpr int LAP_VIFDU = 0;   // VIFDU, Eq. pcls1: (W + Sigma_dagger^{-1}) x = v
+constexpr int LAP_FITC = 2;    // FITC, Eq. pcls2: (W^{-1} + Sigma_dagger) x = v
 // row slices of the F^T v product (partial buffer: LAP_FT_BLOCKS x fpad)
 constexpr int LAP_FT_BLOCKS = 608;
 struct LapOps {
@@ -175,6 +178,12 @@ struct LapOps {
   int64_t nsteps_fwd, nsteps_rev;         // schedule lengths / LAP_TRSV_RPS
   const double* ch_coef;                  // A_i[k] of each child term, CSR order (lap_child_coef)
   int64_t nnz;                            // child terms
+  // FITC preconditioner with the system form of Eq. pcls2 (kind = LAP_FITC)
+  int kind;                               // LAP_VIFDU or LAP_FITC
+  const double *A, *Apad, *D, *W;         // rows of A (ld mpad), A zero-padded to ld fpad, D_i, W_i
+  int mpad;
+  double *dvinv, *anorm2;                 // 1/D_V; |a_i|^2
+  const double* LinvMV;                   // inverse Cholesky factor of I + A D_V^{-1} A^T (ld fpad)
   const double *Acoef, *F, *LinvC, *LinvC3;
   double *rsD, *Ginv;          // 1/sqrt(D_i), 1/(W'_i + 1/D_i)
   double *t, *t2, *x1;         // n-vector scratch
@@ -195,6 +204,16 @@ cudaError_t lap_solve_B(const LapOps& o, const double* rhs, double* out, cudaStr
 cudaError_t lap_apply_Bt(const LapOps& o, const double* u, double* out, cudaStream_t s);
 cudaError_t lap_rows_dot_add(const double* rows, int ld, int m, int64_t n, const double* c, const double* base,
                              double* out, cudaStream_t s);
+// FITC / Eq. pcls2 pieces
+cudaError_t lap_fitc_prepare_A(const double* A, int mpad, int m, int64_t n, int fpad, double* Apad, double* anorm2,
+                               cudaStream_t s);
+cudaError_t lap_fitc_dv(int64_t n, double var, const double* anorm2, const double* W, double* dvinv, cudaStream_t s);
+cudaError_t lap_sigma_matvec(const LapOps& o, const double* x, const double* Winv_of, double* out, cudaStream_t s);
+cudaError_t lap_precond_fitc(const LapOps& o, const double* w, double* out, cudaStream_t s);
+cudaError_t lap_system_matvec(const LapOps& o, const double* x, double* out, cudaStream_t s);
+cudaError_t lap_system_precond(const LapOps& o, const double* w, double* out, cudaStream_t s);
+cudaError_t lap_fitc_probe(const LapOps& o, const double* eps1, const double* eps2, double* z, cudaStream_t s);
+cudaError_t lap_div(int64_t n, const double* x, const double* d, double* out, cudaStream_t s);
 cudaError_t lap_pointwise(const double* y, const double* b, const double* D, const double* corr, int64_t n, double* W,
                           double* v, double* Ginv, double* omega, double* rsD, double* ll, cudaStream_t s);
 cudaError_t lap_dot(const double* a, const double* b, int64_t n, double* partial, double* out, cudaStream_t s);

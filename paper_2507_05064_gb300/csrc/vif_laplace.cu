@@ -571,6 +571,120 @@ cudaError_t lap_rows_dot_add(const double* rows, int ld, int m, int64_t n, const
   return cudaGetLastError();
 }
 
+// ---------------------------------------------------------------------------
+// FITC preconditioner (Sec. 4.3, App. E.2) with the system form of Eq. pcls2,
+//   (W^{-1} + Sigma_dagger) x = v,   Sigma_dagger x = B^{-1} D B^{-T} x + A^T A x,
+//   P = D_V + A^T A,   D_V = diag(sigma_1^2 - |a_i|^2) + W^{-1},
+// its inducing points being those of the VIF (A^T A = Sigma_mn^T Sigma_m^{-1} Sigma_mn).
+// Solves by Woodbury with the whitened M_V = I + A D_V^{-1} A^T (m x m), draws by
+// D_V^{1/2} eps2 + A^T eps1.
+// ---------------------------------------------------------------------------
+
+// Apad = A with rows zero-padded from mpad to fpad columns (columns >= m zero); anorm2_i = |a_i|^2
+__global__ void fitc_prepare_kernel(const double* __restrict__ A, int mpad, int m, int64_t n, int fpad, double* Apad,
+                                    double* anorm2) {
+  const int64_t i = (int64_t)blockIdx.x * (blockDim.x / 32) + threadIdx.x / 32;
+  const int lane = threadIdx.x & 31;
+  if (i >= n) return;
+  double s = 0.0;
+  for (int k = lane; k < fpad; k += 32) {
+    const double v = k < m ? A[(size_t)i * mpad + k] : 0.0;
+    Apad[(size_t)i * fpad + k] = v;
+    s = fma(v, v, s);
+  }
+  for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+  if (lane == 0) anorm2[i] = s;
+}
+
+__global__ void fitc_dv_kernel(int64_t n, double var, const double* __restrict__ anorm2, const double* __restrict__ W,
+                               double* dvinv) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) dvinv[i] = 1.0 / (var - anorm2[i] + 1.0 / W[i]);
+}
+
+// out_i = a_i + x_i / d_i   (d may be NULL: out = a + 0)
+__global__ void add_div_kernel(int64_t n, const double* __restrict__ a, const double* __restrict__ x,
+                               const double* __restrict__ d, double* out) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) out[i] = a[i] + (d ? x[i] / d[i] : 0.0);
+}
+
+__global__ void div_kernel(int64_t n, const double* __restrict__ x, const double* __restrict__ d, double* out) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) out[i] = x[i] / d[i];
+}
+
+// z_i = sqrt(D_V,i) eps2_i
+__global__ void fitc_probe_kernel(int64_t n, const double* __restrict__ dvinv, const double* __restrict__ eps2,
+                                  double* z) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) z[i] = eps2[i] / sqrt(dvinv[i]);
+}
+
+cudaError_t lap_fitc_prepare_A(const double* A, int mpad, int m, int64_t n, int fpad, double* Apad, double* anorm2,
+                               cudaStream_t s) {
+  fitc_prepare_kernel<<<blocks(n, 8), 256, 0, s>>>(A, mpad, m, n, fpad, Apad, anorm2);
+  return cudaGetLastError();
+}
+
+cudaError_t lap_fitc_dv(int64_t n, double var, const double* anorm2, const double* W, double* dvinv, cudaStream_t s) {
+  fitc_dv_kernel<<<blocks(n, 256), 256, 0, s>>>(n, var, anorm2, W, dvinv);
+  return cudaGetLastError();
+}
+
+cudaError_t lap_div(int64_t n, const double* x, const double* d, double* out, cudaStream_t s) {
+  div_kernel<<<blocks(n, 256), 256, 0, s>>>(n, x, d, out);
+  return cudaGetLastError();
+}
+
+// out = Sigma_dagger x (+ x / Wd when Wd is given) = B^{-1}(D o B^{-T} x) + A^T A x (+ W^{-1} x)
+cudaError_t lap_sigma_matvec(const LapOps& o, const double* x, const double* Wd, double* out, cudaStream_t s) {
+  cudaError_t e = cudaSuccess;
+  if (o.mv > 0) {
+    if ((e = cudaMemsetAsync(o.t, 0xFF, (size_t)o.n * sizeof(double), s)) != cudaSuccess) return e;
+    if ((e = launch_trsv(o.sched_rev, o.nsteps_rev, o.ch_row, o.ch_coef, x, o.t, o.abort_flag, o.status, s)) !=
+        cudaSuccess)
+      return e;
+    scale2_kernel<<<blocks(o.n, 256), 256, 0, s>>>(o.n, o.D, nullptr, o.t, o.t2);
+    if ((e = lap_solve_B(o, o.t2, o.x1, s)) != cudaSuccess) return e;
+  } else {
+    scale2_kernel<<<blocks(o.n, 256), 256, 0, s>>>(o.n, o.D, nullptr, x, o.x1);
+  }
+  add_div_kernel<<<blocks(o.n, 256), 256, 0, s>>>(o.n, o.x1, x, Wd, o.t);
+  if (o.m > 0) {
+    lap_ftv(o.A, o.mpad, o.m, o.n, x, o.partial, o.cm, s);
+    return lap_rows_dot_add(o.A, o.mpad, o.m, o.n, o.cm, o.t, out, s);
+  }
+  return cudaMemcpyAsync(out, o.t, o.n * sizeof(double), cudaMemcpyDeviceToDevice, s);
+}
+
+// out = P^{-1} w = D_V^{-1} (w - A^T M_V^{-1} A D_V^{-1} w)
+cudaError_t lap_precond_fitc(const LapOps& o, const double* w, double* out, cudaStream_t s) {
+  scale2_kernel<<<blocks(o.n, 256), 256, 0, s>>>(o.n, o.dvinv, nullptr, w, o.t2);
+  if (o.m == 0) return cudaMemcpyAsync(out, o.t2, o.n * sizeof(double), cudaMemcpyDeviceToDevice, s);
+  lap_ftv(o.A, o.mpad, o.m, o.n, o.t2, o.partial, o.sm, s);
+  lap_spd_apply(o.LinvMV, o.ldl, o.m, o.sm, o.tmpm, o.cm, s);
+  const size_t smem = (size_t)((o.m + 3) & ~3) * sizeof(double);
+  f_dot_kernel<<<blocks(o.n, FD_THREADS), FD_THREADS, smem, s>>>(o.A, o.mpad, o.m, o.n, o.cm, w, -1.0, nullptr,
+                                                                  o.dvinv, out);
+  return cudaGetLastError();
+}
+
+cudaError_t lap_system_matvec(const LapOps& o, const double* x, double* out, cudaStream_t s) {
+  return o.kind == LAP_FITC ? lap_sigma_matvec(o, x, o.W, out, s) : lap_matvec(o, x, o.W, out, s);
+}
+
+cudaError_t lap_system_precond(const LapOps& o, const double* w, double* out, cudaStream_t s) {
+  return o.kind == LAP_FITC ? lap_precond_fitc(o, w, out, s) : lap_precond(o, w, out, s);
+}
+
+// z = D_V^{1/2} eps2 + A^T eps1  ~ N(0, P) for the FITC preconditioner
+cudaError_t lap_fitc_probe(const LapOps& o, const double* eps1, const double* eps2, double* z, cudaStream_t s) {
+  fitc_probe_kernel<<<blocks(o.n, 256), 256, 0, s>>>(o.n, o.dvinv, eps2, o.t);
+  if (o.m == 0) return cudaMemcpyAsync(z, o.t, o.n * sizeof(double), cudaMemcpyDeviceToDevice, s);
+  return lap_rows_dot_add(o.A, o.mpad, o.m, o.n, eps1, o.t, z, s);
+}
+
 cudaError_t lap_pointwise(const double* y, const double* b, const double* D, const double* corr, int64_t n, double* W,
                           double* v, double* Gd, double* omega, double* rsD, double* ll, cudaStream_t s) {
   lap_pointwise_kernel<<<blocks(n, 256), 256, 0, s>>>(y, b, D, corr, n, W, v, Gd, omega, rsD, ll);

@@ -19,6 +19,7 @@ VIF_OK, VIF_ERR_ARG, VIF_ERR_CUDA, VIF_ERR_NOMEM, VIF_ERR_NOT_PD, VIF_ERR_TIMEOU
 STATUS_NAMES = ["OK", "ERR_ARG", "ERR_CUDA", "ERR_NOMEM", "ERR_NOT_PD", "ERR_TIMEOUT",
                 "ERR_NOT_CONVERGED", "ERR_STATE"]
 FP64, MIXED = 0, 1
+PRECOND_VIFDU, PRECOND_VIFDU_LEARNED, PRECOND_FITC = 0, 1, 2
 GAUSSIAN, BERNOULLI_LOGIT = 0, 1
 
 # every symbol include/vif.h declares

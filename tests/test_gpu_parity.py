@@ -370,6 +370,35 @@ def test_vifla_nll_untrained_learned_correction_equals_plain_vifdu():
     ctx.close()
 
 
+def test_laplace_mode_with_fitc_preconditioner_matches_oracle():
+    """FITC preconditioner (App. E.2) with the system form of Eq. pcls2: the mode equals the dense
+    Newton mode and the CG counts follow the oracle's pcls2 PCG."""
+    P, vif, b_dense, ctx = _vifla_case(1500, 25, 10, 44)
+    b, st = ctx.laplace_mode(P.theta, P.y, rel_tol=1e-6, precond=V.PRECOND_FITC)
+    b_or, steps_o, its_o = O.laplace_mode_fitc(vif, P.y, tol=1e-6)
+    assert np.linalg.norm(b - b_dense) <= 1e-5 * np.linalg.norm(b_dense)
+    assert np.linalg.norm(b - b_or) <= 1e-5 * np.linalg.norm(b_or)
+    assert abs(st["newton_iters"] - steps_o) <= 1
+    assert abs(st["pcg_iters_total"] - its_o) <= 2 * steps_o, (st, its_o)
+    ctx.close()
+
+
+def test_vifla_nll_with_fitc_slq_matches_oracle_probe_by_probe():
+    """Eq. slq_v2 with the FITC preconditioner: same normals, same probes, same quadratures."""
+    P, vif, b_dense, ctx = _vifla_case(1500, 25, 10, 45)
+    eps = synth.slq_normals(6, vif.m, vif.n, seed=8)
+    nll, st = ctx.laplace_nll(P.theta, P.y, eps, slq_tol=1e-6, rel_tol=1e-10, precond=V.PRECOND_FITC)
+    ref = O.vifla_nll_slq_fitc(vif, P.y, b_dense, eps[:, :vif.m + vif.n], 1e-6)
+    assert abs(st["logdet_precond"] - ref["logdet_P"]) <= 1e-8 * abs(ref["logdet_P"])
+    np.testing.assert_allclose(st["zPz"], ref["zPz"], rtol=1e-7)
+    np.testing.assert_allclose(st["q"], ref["q"], rtol=1e-5, atol=1e-8)
+    assert abs(nll - ref["nll"]) <= 1e-7 * abs(ref["nll"]), (nll, ref["nll"])
+    # both SLQ forms estimate the same log-determinant
+    nll1, st1 = ctx.laplace_nll(P.theta, P.y, eps, slq_tol=1e-6, rel_tol=1e-10)
+    assert abs(st["quad"] - st1["quad"]) <= 1e-8 * abs(st1["quad"])
+    ctx.close()
+
+
 def test_laplace_rejects_a_nugget():
     P = bern(300, 10, 4, 34)
     ctx = V.Context(P.X, P.Z, 4, P.theta, likelihood=V.BERNOULLI_LOGIT)
