@@ -21,7 +21,8 @@ dense solves, sparse products, sorting) as the only building blocks:
 * the VIF-Laplace likelihood (Eq. log_det_VIFLA) with the preconditioned SLQ
   log-determinant (Eq. slq_v1, App. D), probes drawn by the recipe of Sec. 4.3;
 * the FITC preconditioner (Sec. 4.3, App. E.2) with the system form of Eq. pcls2 and
-  the SLQ form of Eq. slq_v2.
+  the SLQ form of Eq. slq_v2;
+* VIF-Laplace predictive distributions (Prop. 3.1) and their variances by Alg. 1 (SBPV).
 
 Readings of points the paper leaves open (all shared with the CUDA path):
   R1 kernel forms of Rasmussen & Williams; "range" = length scale lambda.
@@ -858,6 +859,60 @@ def vifla_nll_slq_fitc(vif: VIF, y, b, eps, tol: float, max_iter: int = 1000):
                 logdet_W=ld_W, logdet_P=ld_P, slq_term=slq, logdet=logdet,
                 logdet_exact_norm=ld_W + float((zpz * q).mean()) + ld_P,
                 q=q, zPz=zpz, pcg_iters=np.array(its))
+
+
+def laplace_predict_dense(vif: VIF, y, b, Xp, Np):
+    """Prop. 3.1 with dense matrices (small n): the latent predictive mean omega_p and covariance
+    Omega_p at the mode b.  The first part of Omega_p and omega_p have the algebra of Prop. 2.1
+    with y replaced by b (predict_prop21_dense); the Laplace part adds
+    K_p Sigma_dagger^{-1} (W + Sigma_dagger^{-1})^{-1} Sigma_dagger^{-1} K_p^T with
+    K_p = Sigma_mnp^T Sigma_m^{-1} Sigma_mn - B_p^{-1} B_po (B^T D^{-1} B)^{-1}."""
+    mu, Sig = predict_prop21_dense(vif, b, Xp, Np)
+    X, Z, theta = vif.X, vif.Z, vif.theta
+    n = vif.n
+    Ap, Dp, lrp = pred_factors(X, Z, theta, Xp, Np, vif.lowrank)
+    npred = Xp.shape[0]
+    Bpo = np.zeros((npred, n))
+    for p in range(npred):
+        Bpo[p, Np[p]] = -Ap[p]
+    Bd = vif.B.toarray()
+    PrecInv = np.linalg.inv(Bd.T @ np.diag(vif.Dinv) @ Bd)
+    LRpn = lrp.Smn.T @ np.linalg.inv(vif.lowrank.Sm) @ vif.lowrank.Smn if vif.m else np.zeros((npred, n))
+    Kp = LRpn - Bpo @ PrecInv
+    Sdi = np.linalg.inv(vif.dense_Sigma_dagger())
+    _, W = bern_grad_W(y, b)
+    H = Sdi @ np.linalg.solve(np.diag(W) + Sdi, Sdi)
+    return mu, Sig + Kp @ H @ Kp.T
+
+
+def laplace_predict_sbpv(vif: VIF, y, b, Xp, Np, eps, tol: float, max_iter: int = 1000):
+    """Latent predictive means (Prop. 3.1) and variances by Alg. 1 (SBPV) at the mode b, the
+    variance diagonal version: the deterministic part is the latent variance of Prop. 2.1 /
+    App. C.1 with b for y, the stochastic part (1/l) sum_i z8_i o z8_i with, for each row
+    eps[i] = (z3 (m), z1 (n), z2 (n)):
+        z4 = Sigma_mn^T L_m^{-T} z3 + B^{-1} D^{1/2} z1        ~ N(0, Sigma_dagger)
+        z5 = Sigma_dagger^{-1} z4                               ~ N(0, Sigma_dagger^{-1})
+        z6 = z5 + W^{1/2} z2                                    ~ N(0, Sigma_dagger^{-1} + W)
+        z7 = (Sigma_dagger^{-1} + W)^{-1} z6  (PCG with VIFDU)  ~ N(0, (Sigma_dagger^{-1} + W)^{-1})
+        z8 = K_p Sigma_dagger^{-1} z7  (the predictive-mean operator applied to z7).
+    Returns (mean, var, per-sample PCG iterations)."""
+    n, m = vif.n, vif.m
+    mu, var_det = predict_appC(vif, b, Xp, Np)
+    _, W = bern_grad_W(y, b)
+    pre = VIFDU(vif, W)
+    acc = np.zeros(Xp.shape[0])
+    its = []
+    for e in np.atleast_2d(eps):
+        z3, z1, z2 = e[:m], e[m:m + n], e[m + n:m + 2 * n]
+        z4 = spla.spsolve_triangular(vif.B.tocsr(), np.sqrt(vif.D) * z1, lower=True)
+        if m:
+            z4 = z4 + vif.lowrank.Smn.T @ sla.solve_triangular(vif.lowrank.cf[0], z3, lower=True, trans="T")
+        z6 = vif.Sigma_dagger_inv(z4) + np.sqrt(W) * z2
+        z7, it, _ = pcg(lambda w: W * w + vif.Sigma_dagger_inv(w), pre.apply, z6, tol, max_iter)
+        z8, _ = predict_appC(vif, z7, Xp, Np)
+        acc += z8 * z8
+        its.append(it)
+    return mu, var_det + acc / len(its), np.array(its)
 
 
 def vifla_logdet_dense(vif: VIF, b) -> float:

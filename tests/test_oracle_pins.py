@@ -384,6 +384,54 @@ def test_slq_fitc_estimate_is_unbiased_within_its_standard_error():
     assert abs(r["logdet_exact_norm"] - r1["logdet_exact_norm"]) <= 4.0 * math.hypot(se, se1) + 1e-9
 
 
+# --------------------------------------------------------------------------- VIF-Laplace prediction
+def _gp_laplace_textbook(K, Kp, kpp, y, f):
+    """Latent predictive mean and variance of the Laplace-approximated GP classifier at the mode f
+    (Rasmussen & Williams, Sec. 3.4, Alg. 3.2): mean = Kp (y - sigmoid(f)), var = kpp - |v|^2 with
+    v = L^{-1} W^{1/2} Kp^T, L = chol(I + W^{1/2} K W^{1/2})."""
+    p = 1.0 / (1.0 + np.exp(-f))
+    W = p * (1.0 - p)
+    sw = np.sqrt(W)
+    L = np.linalg.cholesky(np.eye(len(f)) + sw[:, None] * K * sw[None, :])
+    v = sla.solve_triangular(L, sw[:, None] * Kp.T, lower=True)
+    return Kp @ (y - p), kpp - (v * v).sum(0)
+
+
+def test_laplace_prediction_with_full_conditioning_is_the_textbook_gp_laplace():
+    """m_v = n-1 and every training point a prediction neighbour: the VIF prior is the exact GP
+    (up to the 1e-10 jitter), so Prop. 3.1 must give the textbook Laplace predictive distribution."""
+    P = small_problem(n=70, m=6, mv=69, nugget=0.0, likelihood="bernoulli_logit", ls=0.2, seed=30, n_pred=15)
+    N = O.causal_neighbors(P.X, P.Z, P.theta, 69)
+    vif = O.VIF(P.X, P.Z, P.theta, N)
+    b, _, _ = O.laplace_mode(vif, P.y, dense=True)
+    Np = np.tile(np.arange(70), (15, 1))
+    mu, Om = O.laplace_predict_dense(vif, P.y, b, P.Xp, Np)
+    K = O.cov(P.X, P.X, P.theta)
+    mu_t, var_t = _gp_laplace_textbook(K, O.cov(P.Xp, P.X, P.theta), np.full(15, P.theta.variance), P.y, b)
+    np.testing.assert_allclose(mu, mu_t, rtol=1e-6, atol=1e-7)
+    np.testing.assert_allclose(np.diag(Om), var_t, rtol=1e-5, atol=1e-7)
+
+
+def test_sbpv_is_unbiased_for_the_laplace_predictive_variances():
+    """Alg. 1: the deterministic part equals the first part of Omega_p (App. C.1 = Prop. 2.1 with b for
+    y) and the sample average of z8 o z8 converges to the Laplace part (Prop. 4 of the paper)."""
+    P = small_problem(n=90, m=6, mv=5, nugget=0.0, likelihood="bernoulli_logit", ls=0.15, seed=31, n_pred=12)
+    N = O.causal_neighbors(P.X, P.Z, P.theta, 5)
+    vif = O.VIF(P.X, P.Z, P.theta, N)
+    b, _, _ = O.laplace_mode(vif, P.y, dense=True)
+    Np = O.pred_neighbors(P.X, P.Z, P.theta, P.Xp, 5)
+    mu_d, Om = O.laplace_predict_dense(vif, P.y, b, P.Xp, Np)
+    eps = np.random.default_rng(14).standard_normal((1000, vif.m + 2 * vif.n))
+    mu, var, its = O.laplace_predict_sbpv(vif, P.y, b, P.Xp, Np, eps, 1e-12)
+    np.testing.assert_allclose(mu, mu_d, rtol=1e-8, atol=1e-10)
+    _, var_det = O.predict_appC(vif, b, P.Xp, Np)
+    part = np.diag(Om) - var_det
+    assert (part > 0).all()
+    # each z8_p^2 has mean part_p and variance 2 part_p^2 (z8_p is Gaussian), so the average of
+    # 1000 has standard error part_p sqrt(2/1000)
+    assert np.all(np.abs(var - np.diag(Om)) <= 4.0 * part * math.sqrt(2.0 / len(eps)))
+
+
 # --------------------------------------------------------------------------- gradient
 def test_fd_gradient_with_full_conditioning_is_the_exact_gp_gradient():
     """m_v = n-1 makes the VIF likelihood the exact one, whose gradient is analytic."""
