@@ -327,6 +327,17 @@ def laplace_block(args, stream):
                            "logdet_exact_norm": slf["logdet_exact_norm"],
                            "pcg_iters_slq": slf["pcg_iters_slq"], "ms_slq": slf["ms_slq"],
                            "ms_per_probe": slf["ms_slq"] / nprobe}}
+    # predictive means (Prop. 3.1) and SBPV variances (Alg. 1) at 1000 new points: 100 draws (the
+    # paper's default), FITC solves at CG tolerance 0.01
+    Xp = synth._rng(20250715).uniform(size=(1000, P.X.shape[1]))
+    eps_p = synth.slq_normals(100, P.Z.shape[0], P.X.shape[0], seed=20250716)
+    t0 = time.perf_counter()
+    mu_p, var_p, sp = ctx.laplace_predict(P.theta, y, Xp, eps_p, cg_tol=1e-2, rel_tol=1e-6,
+                                          precond=V.PRECOND_FITC)
+    out["predict"] = {"n_pred": 1000, "samples": 100, "precond": "FITC", "cg_tol": 1e-2,
+                      "wall_s": time.perf_counter() - t0, "ms_mode": sp["ms_total"],
+                      "cg_iters_total": sp["pcg_iters_total"], "mean_abs_mean": float(np.abs(mu_p).mean()),
+                      "mean_var": float(var_p.mean())}
     wpath = os.path.join(ROOT, "paper_2507_05064_gb300", "weights", "vifdu_mlp.npy")
     if os.path.exists(wpath):
         net = V.Network(params=np.load(wpath))

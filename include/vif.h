@@ -192,6 +192,24 @@ vif_status vif_laplace_nll(vif_ctx *ctx, const vif_cov *theta, const double *y, 
                            int32_t nprobe, const double *eps, double slq_tol, int32_t slq_max_iter,
                            double *nll_out, double *probe_q, double *probe_zpz, vif_laplace_nll_stats *stats);
 
+/* vif_laplace_predict -- VIF-Laplace posterior predictive distribution of the latent GP at np
+ * new inputs (Prop. 3.1, prediction points conditioning on training points only as in
+ * vif_predict), at the mode b~ found as by vif_laplace_mode (opts->precond 0 = VIFDU or 2 = FITC).
+ *   mean: omega_p = K_p Sigma_dagger^{-1} b~,  K_p = Sigma_mnp^T Sigma_m^{-1} Sigma_mn - B_po (B^T D^{-1} B)^{-1}.
+ *   var (may be NULL): diag(Omega_p) by Alg. 1 (SBPV, variance version): the latent variance of
+ *        Prop. 2.1 with b~ for y, plus (1/l) sum_i z8_i o z8_i over nsample draws, where
+ *        z4 = Sigma_mn^T L_m^{-T} z3 + B^{-1} D^{1/2} z1, z6 = Sigma_dagger^{-1} z4 + W^{1/2} z2,
+ *        z7 = (W + Sigma_dagger^{-1})^{-1} z6 by preconditioned CG (stopping as vif_laplace_mode, with
+ *        cg_tol and cg_max_iter; Eq. pcls2 for FITC) and z8 = K_p Sigma_dagger^{-1} z7.
+ *   eps: nsample x (m + 2n) row-major float64 standard normal numbers (host or device), row i =
+ *        (z3 (m), z1 (n), z2 (n)); unused when var is NULL.
+ *   Xp: np x d (host or device); mean, var: np values (host or device).  stats: host, may be NULL
+ *        (pcg_iters_total counts the Newton and the SBPV solves).
+ * Errors as vif_laplace_mode; VIF_ERR_ARG for precond = 1 or m_v > 48. */
+vif_status vif_laplace_predict(vif_ctx *ctx, const vif_cov *theta, const double *y, const vif_laplace_opts *opts,
+                               const double *Xp, int64_t np, int32_t nsample, const double *eps, double cg_tol,
+                               int32_t cg_max_iter, double *mean, double *var, vif_laplace_stats *stats);
+
 /* vif_tridiag_log_quadrature -- e_1^T log(T) e_1 for a symmetric positive-definite
  * tridiagonal T (diagonal diag[0..k-1], off-diagonal offdiag[0..k-2], host arrays): the
  * Gauss quadrature of App. D, by implicit symmetric QR with Wilkinson shifts on the host

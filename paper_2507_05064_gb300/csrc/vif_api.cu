@@ -57,6 +57,8 @@ struct vif_ctx {
   double* ch_coef = nullptr;                            // coefficient of each child term
   double* slq_eps = nullptr;                            // normals of one SLQ probe (m + 2n)
   double *l_Apad = nullptr, *l_anorm2 = nullptr, *l_dvinv = nullptr;   // FITC preconditioner
+  double* l_pacc = nullptr;                             // SBPV sums of squares (np)
+  int64_t l_pacc_cap = 0;
   double *l_b = nullptr, *l_W = nullptr, *l_v = nullptr, *l_Ginv = nullptr, *l_om = nullptr, *l_rsD = nullptr,
          *l_ll = nullptr, *l_x = nullptr, *l_r = nullptr, *l_z = nullptr, *l_p = nullptr, *l_Ap = nullptr,
          *l_t = nullptr, *l_t2 = nullptr, *l_x1 = nullptr, *l_sdi = nullptr, *l_sm = nullptr, *l_cm = nullptr,
@@ -280,7 +282,7 @@ void free_ctx(vif_ctx* c) {
                    c->ch_slot, c->l_b,  c->l_W,    c->l_v,    c->l_Ginv, c->l_om,   c->l_rsD,  c->l_ll,
                    c->l_x,    c->l_r,   c->l_z,    c->l_p,    c->l_Ap,   c->l_t,    c->l_t2,   c->l_x1,
                    c->l_sdi,  c->l_sm,  c->l_cm,   c->l_tm,   c->l_part, c->l_LinvC, c->l_G3,  c->l_LinvC3,
-                   c->l_sc,   c->l_red, c->l_corr, c->sched_fwd, c->sched_rev, c->ch_coef, c->slq_eps, c->l_Apad, c->l_anorm2, c->l_dvinv, c->l_counter, c->l_abort, c->m_feat,
+                   c->l_sc,   c->l_red, c->l_corr, c->sched_fwd, c->sched_rev, c->ch_coef, c->slq_eps, c->l_Apad, c->l_anorm2, c->l_dvinv, c->l_pacc, c->l_counter, c->l_abort, c->m_feat,
                    c->m_gc,   c->m_part, c->m_grad};
   for (void* b : pbufs)
     if (b) cudaFree(b);
@@ -603,6 +605,37 @@ vif_status lap_alloc(vif_ctx* ctx) {
   return VIF_OK;
 }
 
+// Prediction buffers for np points (grown on demand) and the n-sized ones.
+vif_status predict_buffers(vif_ctx* ctx, int64_t np) {
+  const int d = ctx->d, m = ctx->m, mpad = ctx->mpad, fpad = ctx->fpad, mv = ctx->mv;
+  const int64_t n = ctx->n;
+  if (np > ctx->p_cap) {
+    double* pb[] = {ctx->pXp, ctx->pXps, ctx->pAp, ctx->pcpp, ctx->pmean, ctx->pvar};
+    for (double* b : pb)
+      if (b) cudaFree(b);
+    if (ctx->pNp) cudaFree(ctx->pNp);
+    ctx->pXp = ctx->pXps = ctx->pAp = ctx->pcpp = ctx->pmean = ctx->pvar = nullptr;
+    ctx->pNp = nullptr;
+    ctx->p_cap = 0;
+    CKS(dalloc(ctx, &ctx->pXp, (size_t)np * d));
+    CKS(dalloc(ctx, &ctx->pXps, (size_t)np * d));
+    CKS(dalloc(ctx, &ctx->pAp, (size_t)np * mpad));
+    CKS(dalloc(ctx, &ctx->pcpp, (size_t)np));
+    CKS(dalloc(ctx, &ctx->pmean, (size_t)np));
+    CKS(dalloc(ctx, &ctx->pvar, (size_t)np));
+    CKS(dalloc(ctx, &ctx->pNp, (size_t)np * std::max(mv, 1)));
+    ctx->p_cap = np;
+  }
+  if (!ctx->pcjj) {
+    CKS(dalloc(ctx, &ctx->pcjj, (size_t)n));
+    CKS(dalloc(ctx, &ctx->pw, (size_t)mpad));
+    CKS(dalloc(ctx, &ctx->pr, (size_t)n));
+    CKS(dalloc(ctx, &ctx->pLinvC, (size_t)std::max(m, 1) * fpad));
+    CK(cudaMemsetAsync(ctx->pw, 0, (size_t)mpad * sizeof(double), ctx->stream));
+  }
+  return VIF_OK;
+}
+
 }  // namespace
 
 void vif_internal_set_global_error(const char* msg) { snprintf(g_build_err, sizeof(g_build_err), "%s", msg); }
@@ -826,30 +859,7 @@ vif_status vif_predict(vif_ctx* ctx, const vif_cov* theta, const double* y, cons
   const int d = ctx->d, m = ctx->m, mpad = ctx->mpad, fpad = ctx->fpad, mv = ctx->mv;
   double *A64, *F64, *LT64;
   CKS(fp64_buffers(ctx, &A64, &F64, &LT64));
-  if (np > ctx->p_cap) {
-    double* pb[] = {ctx->pXp, ctx->pXps, ctx->pAp, ctx->pcpp, ctx->pmean, ctx->pvar};
-    for (double* b : pb)
-      if (b) cudaFree(b);
-    if (ctx->pNp) cudaFree(ctx->pNp);
-    ctx->pXp = ctx->pXps = ctx->pAp = ctx->pcpp = ctx->pmean = ctx->pvar = nullptr;
-    ctx->pNp = nullptr;
-    ctx->p_cap = 0;
-    CKS(dalloc(ctx, &ctx->pXp, (size_t)np * d));
-    CKS(dalloc(ctx, &ctx->pXps, (size_t)np * d));
-    CKS(dalloc(ctx, &ctx->pAp, (size_t)np * mpad));
-    CKS(dalloc(ctx, &ctx->pcpp, (size_t)np));
-    CKS(dalloc(ctx, &ctx->pmean, (size_t)np));
-    CKS(dalloc(ctx, &ctx->pvar, (size_t)np));
-    CKS(dalloc(ctx, &ctx->pNp, (size_t)np * std::max(mv, 1)));
-    ctx->p_cap = np;
-  }
-  if (!ctx->pcjj) {
-    CKS(dalloc(ctx, &ctx->pcjj, (size_t)n));
-    CKS(dalloc(ctx, &ctx->pw, (size_t)mpad));
-    CKS(dalloc(ctx, &ctx->pr, (size_t)n));
-    CKS(dalloc(ctx, &ctx->pLinvC, (size_t)std::max(m, 1) * fpad));
-    CK(cudaMemsetAsync(ctx->pw, 0, (size_t)mpad * sizeof(double), ctx->stream));
-  }
+  CKS(predict_buffers(ctx, np));
   CovParams cp = cov_params(theta);
   CK(cudaMemsetAsync(ctx->status, 0, 4 * sizeof(int), ctx->stream));
   CKS(upload(ctx, ctx->y, y, (size_t)n * sizeof(double)));
@@ -1365,6 +1375,109 @@ vif_status vif_laplace_nll(vif_ctx* ctx, const vif_cov* theta, const double* y, 
   if (!converged || capped || slq_capped)
     return set_err(ctx, VIF_ERR_NOT_CONVERGED, "Newton %s, CG %s", converged ? "converged" : "hit its cap",
                    (capped || slq_capped) ? "hit its cap" : "converged");
+  return VIF_OK;
+}
+
+vif_status vif_laplace_predict(vif_ctx* ctx, const vif_cov* theta, const double* y, const vif_laplace_opts* lo,
+                               const double* Xp, int64_t np, int32_t nsample, const double* eps, double cg_tol,
+                               int32_t cg_max_iter, double* mean, double* var, vif_laplace_stats* stats) {
+  if (!ctx) return VIF_ERR_ARG;
+  ctx->err[0] = 0;
+  if (!Xp || !mean || np < 1) return set_err(ctx, VIF_ERR_ARG, "Xp, mean and np >= 1 are required");
+  if (var && (nsample < 1 || !eps || !(cg_tol > 0.0) || cg_max_iter < 1))
+    return set_err(ctx, VIF_ERR_ARG, "variances need nsample >= 1 normals, cg_tol > 0 and cg_max_iter >= 1");
+  if (ctx->mv > 48) return set_err(ctx, VIF_ERR_ARG, "m_v too large for prediction");
+  if (lo && lo->precond == 1) return set_err(ctx, VIF_ERR_ARG, "prediction uses VIFDU (0) or FITC (2)");
+  LapOps o;
+  vif_laplace_stats ms{};
+  bool converged = false, capped = false;
+  CKS(laplace_run(ctx, theta, y, lo, &o, &ms, &converged, &capped));
+  const int64_t n = ctx->n;
+  const int d = ctx->d, m = ctx->m, mpad = ctx->mpad, fpad = ctx->fpad, mv = ctx->mv;
+  cudaStream_t s = ctx->stream;
+  const bool fitc = lo->precond == LAP_FITC;
+  double *A64, *F64, *LT64;
+  CKS(fp64_buffers(ctx, &A64, &F64, &LT64));
+  CKS(predict_buffers(ctx, np));
+  if (!ctx->l_pacc) CKS(dalloc(ctx, &ctx->l_pacc, (size_t)np));
+  else if (np > ctx->l_pacc_cap) {
+    cudaFree(ctx->l_pacc);
+    ctx->l_pacc = nullptr;
+    CKS(dalloc(ctx, &ctx->l_pacc, (size_t)np));
+  }
+  ctx->l_pacc_cap = std::max<int64_t>(ctx->l_pacc_cap, np);
+  CovParams cp = cov_params(theta);
+  // prediction points: scaled coordinates, a_p, neighbour sets (Prop. 3.1 with B_p = I, reading R7)
+  CKS(upload(ctx, ctx->pXp, Xp, (size_t)np * d * sizeof(double)));
+  CK(scale_coords(ctx->pXp, np, d, ctx->hyp, ctx->hyp + 16, ctx->pXps, nullptr, s));
+  CK(lowrank_A<double>(ctx->pXps, ctx->Zs, LT64, mpad, ctx->pAp, np, d, m, mpad, cp.kind, cp.var, s));
+  CK(predict_setup(A64, ctx->Xs, n, ctx->pAp, ctx->pXps, np, d, m, mpad, mv, cp, ctx->pcjj, ctx->pcpp, ctx->pNp, s));
+  // the predictive-mean operator K_p Sigma_dagger^{-1} v: w = C^{-1} F^T D^{-1/2} B v, r = v - A^T w,
+  // then a_p . w + sum_k A_p[k] r_{N_k} per prediction point (Prop. 2.1 algebra)
+  auto mean_operator = [&](const double* v, double* out, double* vout) -> vif_status {
+    if (m > 0) {
+      CK(lap_bx_scaled(o, v, ctx->l_t, s));
+      CK(lap_ftv(F64, fpad, m, n, ctx->l_t, ctx->l_part, ctx->l_sm, s));
+      CK(lap_spd_apply(ctx->l_LinvC, fpad, m, ctx->l_sm, ctx->l_tm, ctx->pw, s));
+    }
+    CK(predict_resid(A64, ctx->pw, v, n, m, mpad, ctx->pr, s));
+    CK(predict_eval(A64, ctx->Xs, ctx->pAp, ctx->pXps, ctx->pNp, ctx->pr, ctx->pw, ctx->l_LinvC, fpad, np, d, m,
+                    mpad, mv, cp, 1, 0.0, out, vout, ctx->status, s));
+    return VIF_OK;
+  };
+  // omega_p and the first part of Omega_p (the latent variance of Prop. 2.1 with b~ for y)
+  CKS(mean_operator(ctx->l_b, ctx->pmean, ctx->pvar));
+  int cg_total = 0;
+  bool cg_capped = false;
+  double rel = 0.0;
+  if (var) {
+    // Alg. 1 (SBPV): z4 ~ N(0, Sigma_dagger), z6 = Sigma_dagger^{-1} z4 + W^{1/2} z2, z7 solves the
+    // Newton system, z8 = K_p Sigma_dagger^{-1} z7; the variances gain mean(z8 o z8)
+    if (!ctx->slq_eps) CKS(dalloc(ctx, &ctx->slq_eps, (size_t)m + 2 * (size_t)n));
+    CK(cudaMemsetAsync(ctx->l_pacc, 0, (size_t)np * sizeof(double), s));
+    const size_t per = (size_t)m + 2 * (size_t)n;
+    if (fitc) CKS(lap_fitc_setup(ctx, o, false, theta->variance));
+    else CKS(lap_c3(ctx, o));
+    for (int i = 0; i < nsample; ++i) {
+      CKS(upload(ctx, ctx->slq_eps, eps + (size_t)i * per, per * sizeof(double)));
+      const double* z3 = ctx->slq_eps;
+      const double* z1 = ctx->slq_eps + m;
+      const double* z2 = ctx->slq_eps + m + n;
+      CK(lap_probe_prep(n, ctx->Dv, ctx->l_W, nullptr, z1, z2, ctx->l_r, ctx->l_z, s));
+      CK(lap_solve_B(o, ctx->l_r, ctx->l_p, s));
+      if (m > 0) {
+        CK(lap_rows_dot_add(A64, mpad, m, n, z3, ctx->l_p, ctx->l_Ap, s));
+      } else {
+        CK(cudaMemcpyAsync(ctx->l_Ap, ctx->l_p, n * sizeof(double), cudaMemcpyDeviceToDevice, s));
+      }
+      CK(lap_matvec(o, ctx->l_Ap, nullptr, ctx->l_x, s));
+      CK(lap_vec_add(n, ctx->l_x, ctx->l_z, ctx->l_v, s));
+      if (fitc) {   // Eq. pcls2: z7 = W^{-1} (W^{-1} + Sigma_dagger)^{-1} Sigma_dagger z6
+        CK(lap_sigma_matvec(o, ctx->l_v, nullptr, ctx->l_sdi, s));
+        CK(cudaMemcpyAsync(ctx->l_v, ctx->l_sdi, n * sizeof(double), cudaMemcpyDeviceToDevice, s));
+      }
+      int it = 0;
+      bool cp_ = false;
+      CKS(lap_pcg(ctx, o, cg_tol, cg_max_iter, &it, &rel, &cp_));
+      cg_total += it;
+      cg_capped = cg_capped || cp_;
+      if (fitc) CK(lap_div(n, ctx->l_x, ctx->l_W, ctx->l_x, s));
+      CKS(mean_operator(ctx->l_x, ctx->pcpp, nullptr));
+      CK(lap_sq_accumulate(np, ctx->pcpp, ctx->l_pacc, s));
+    }
+    CK(lap_axpy_host(np, 1.0 / nsample, ctx->pvar, ctx->l_pacc, ctx->pvar, s));
+  }
+  double sc[1];
+  CKS(read_status(ctx, sc, 0));
+  CKS(download(ctx, mean, ctx->pmean, (size_t)np * sizeof(double)));
+  if (var) CKS(download(ctx, var, ctx->pvar, (size_t)np * sizeof(double)));
+  if (stats) {
+    *stats = ms;
+    stats->pcg_iters_total = ms.pcg_iters_total + cg_total;
+  }
+  if (!converged || capped || cg_capped)
+    return set_err(ctx, VIF_ERR_NOT_CONVERGED, "Newton %s, CG %s", converged ? "converged" : "hit its cap",
+                   (capped || cg_capped) ? "hit its cap" : "converged");
   return VIF_OK;
 }
 

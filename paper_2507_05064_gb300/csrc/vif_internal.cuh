@@ -154,6 +154,15 @@ cudaError_t nll_finish(const double* Lg, int ldg, int m, const double* logD_sum,
                        double* out, cudaStream_t s);
 
 // vif_predict.cu
+cudaError_t predict_setup(const double* A, const double* Xs, int64_t n, const double* Ap, const double* Xps,
+                          int64_t np, int d, int m, int mpad, int mv, CovParams cp, double* cjj, double* cpp,
+                          int32_t* Np, cudaStream_t s);
+cudaError_t predict_resid(const double* A, const double* w, const double* y, int64_t n, int m, int mpad, double* r,
+                          cudaStream_t s);
+cudaError_t predict_eval(const double* A, const double* Xs, const double* Ap, const double* Xps, const int32_t* Np,
+                         const double* r, const double* w, const double* LinvC, int ldg, int64_t np, int d, int m,
+                         int mpad, int mv, CovParams cp, int latent, double nugget, double* mean, double* var,
+                         int* status, cudaStream_t s);
 cudaError_t predict_all(const double* A, const double* Xs, int64_t n, const double* Ap, const double* Xps,
                         int64_t np, int d, int m, int mpad, int mv, CovParams cp, const double* y, const double* Lg,
                         int ldg, double* LinvC, double* w, double* r, double* cjj, double* cpp, int32_t* Np,
@@ -214,6 +223,12 @@ cudaError_t lap_system_matvec(const LapOps& o, const double* x, double* out, cud
 cudaError_t lap_system_precond(const LapOps& o, const double* w, double* out, cudaStream_t s);
 cudaError_t lap_fitc_probe(const LapOps& o, const double* eps1, const double* eps2, double* z, cudaStream_t s);
 cudaError_t lap_div(int64_t n, const double* x, const double* d, double* out, cudaStream_t s);
+cudaError_t lap_bx_scaled(const LapOps& o, const double* x, double* t, cudaStream_t s);
+cudaError_t lap_ftv(const double* F, int fpad, int m, int64_t n, const double* v, double* partial, double* out,
+                    cudaStream_t s);
+cudaError_t lap_spd_apply(const double* Linv, int ld, int m, const double* x, double* tmp, double* y, cudaStream_t s);
+cudaError_t lap_sq_accumulate(int64_t n, const double* x, double* acc, cudaStream_t s);
+cudaError_t lap_axpy_host(int64_t n, double a, const double* x, const double* y, double* out, cudaStream_t s);
 cudaError_t lap_pointwise(const double* y, const double* b, const double* D, const double* corr, int64_t n, double* W,
                           double* v, double* Ginv, double* omega, double* rsD, double* ll, cudaStream_t s);
 cudaError_t lap_dot(const double* a, const double* b, int64_t n, double* partial, double* out, cudaStream_t s);

@@ -685,6 +685,33 @@ cudaError_t lap_fitc_probe(const LapOps& o, const double* eps1, const double* ep
   return lap_rows_dot_add(o.A, o.mpad, o.m, o.n, eps1, o.t, z, s);
 }
 
+// acc_i += x_i^2 ;  out_i = x_i + a y_i
+__global__ void sq_acc_kernel(int64_t n, const double* __restrict__ x, double* acc) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) acc[i] = fma(x[i], x[i], acc[i]);
+}
+__global__ void axpy_host_kernel(int64_t n, double a, const double* __restrict__ x, const double* __restrict__ y,
+                                 double* out) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) out[i] = fma(a, y[i], x[i]);
+}
+
+cudaError_t lap_sq_accumulate(int64_t n, const double* x, double* acc, cudaStream_t s) {
+  sq_acc_kernel<<<blocks(n, 256), 256, 0, s>>>(n, x, acc);
+  return cudaGetLastError();
+}
+
+cudaError_t lap_axpy_host(int64_t n, double a, const double* x, const double* y, double* out, cudaStream_t s) {
+  axpy_host_kernel<<<blocks(n, 256), 256, 0, s>>>(n, a, x, y, out);
+  return cudaGetLastError();
+}
+
+// t = D^{-1/2} B x
+cudaError_t lap_bx_scaled(const LapOps& o, const double* x, double* t, cudaStream_t s) {
+  bx_scaled_kernel<<<blocks(o.n, 256), 256, 0, s>>>(o.N, o.Acoef, o.rsD, o.n, o.mv, x, t);
+  return cudaGetLastError();
+}
+
 cudaError_t lap_pointwise(const double* y, const double* b, const double* D, const double* corr, int64_t n, double* W,
                           double* v, double* Gd, double* omega, double* rsD, double* ll, cudaStream_t s) {
   lap_pointwise_kernel<<<blocks(n, 256), 256, 0, s>>>(y, b, D, corr, n, W, v, Gd, omega, rsD, ll);

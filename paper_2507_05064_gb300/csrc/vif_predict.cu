@@ -275,11 +275,10 @@ __global__ __launch_bounds__(PK_WARPS * 32) void predict_kernel(
   }
 }
 
-cudaError_t predict_all(const double* A, const double* Xs, int64_t n, const double* Ap, const double* Xps,
-                        int64_t np, int d, int m, int mpad, int mv, CovParams cp, const double* y, const double* Lg,
-                        int ldg, double* LinvC, double* w, double* r, double* cjj, double* cpp, int32_t* Np,
-                        int latent, double nugget, double* mean, double* var, int* status, double* trwork,
-                        cudaStream_t s) {
+// Neighbour sets N_p and residual variances of the prediction points.
+cudaError_t predict_setup(const double* A, const double* Xs, int64_t n, const double* Ap, const double* Xps,
+                          int64_t np, int d, int m, int mpad, int mv, CovParams cp, double* cjj, double* cpp,
+                          int32_t* Np, cudaStream_t s) {
   if (mv > PK_QM - 1 || d > 16) return cudaErrorInvalidValue;
   const double tau = 1e-6 * cp.var;
   resid_var64_kernel<<<(unsigned)((n + 7) / 8), 256, 0, s>>>(A, n, m, mpad, cp.var, cjj);
@@ -287,12 +286,21 @@ cudaError_t predict_all(const double* A, const double* Xs, int64_t n, const doub
   if (mv > 0)
     pred_knn_kernel<<<(unsigned)np, 256, 0, s>>>(A, Xs, cjj, Ap, Xps, cpp, n, d, m, mpad, mv, cp.kind, cp.var, tau,
                                                  Np);
-  if (m > 0) {
-    solve_w_kernel<<<1, 256, (size_t)m * sizeof(double), s>>>(Lg, ldg, m, w);
-    cudaError_t e = dense_trtri_lower(Lg, LinvC, m, ldg, trwork, s);
-    if (e != cudaSuccess) return e;
-  }
+  return cudaGetLastError();
+}
+
+// r = y - A^T w (one value per training point)
+cudaError_t predict_resid(const double* A, const double* w, const double* y, int64_t n, int m, int mpad, double* r,
+                          cudaStream_t s) {
   resid_r_kernel<<<(unsigned)((n + 7) / 8), 256, 0, s>>>(A, w, y, n, m, mpad, r);
+  return cudaGetLastError();
+}
+
+// Means (and, if var != NULL, variances) of the prediction points from w and r.
+cudaError_t predict_eval(const double* A, const double* Xs, const double* Ap, const double* Xps, const int32_t* Np,
+                         const double* r, const double* w, const double* LinvC, int ldg, int64_t np, int d, int m,
+                         int mpad, int mv, CovParams cp, int latent, double nugget, double* mean, double* var,
+                         int* status, cudaStream_t s) {
   const size_t per_warp = (size_t)(PK_QM * (PK_QM + 1) + PK_QM + mpad + 16 * PK_QM) * sizeof(double);
   const size_t smem = per_warp * PK_WARPS;
   cudaError_t e = cudaFuncSetAttribute(predict_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
@@ -300,6 +308,24 @@ cudaError_t predict_all(const double* A, const double* Xs, int64_t n, const doub
   predict_kernel<<<(unsigned)((np + PK_WARPS - 1) / PK_WARPS), PK_WARPS * 32, smem, s>>>(
       A, Xs, Ap, Xps, Np, r, w, LinvC, ldg, np, d, m, mpad, mv, cp, latent, nugget, mean, var, status);
   return cudaGetLastError();
+}
+
+cudaError_t predict_all(const double* A, const double* Xs, int64_t n, const double* Ap, const double* Xps,
+                        int64_t np, int d, int m, int mpad, int mv, CovParams cp, const double* y, const double* Lg,
+                        int ldg, double* LinvC, double* w, double* r, double* cjj, double* cpp, int32_t* Np,
+                        int latent, double nugget, double* mean, double* var, int* status, double* trwork,
+                        cudaStream_t s) {
+  cudaError_t e = predict_setup(A, Xs, n, Ap, Xps, np, d, m, mpad, mv, cp, cjj, cpp, Np, s);
+  if (e != cudaSuccess) return e;
+  if (m > 0) {
+    solve_w_kernel<<<1, 256, (size_t)m * sizeof(double), s>>>(Lg, ldg, m, w);
+    e = dense_trtri_lower(Lg, LinvC, m, ldg, trwork, s);
+    if (e != cudaSuccess) return e;
+  }
+  e = predict_resid(A, w, y, n, m, mpad, r, s);
+  if (e != cudaSuccess) return e;
+  return predict_eval(A, Xs, Ap, Xps, Np, r, w, LinvC, ldg, np, d, m, mpad, mv, cp, latent, nugget, mean, var,
+                      status, s);
 }
 
 }  // namespace vif

@@ -23,7 +23,7 @@ PRECOND_VIFDU, PRECOND_VIFDU_LEARNED, PRECOND_FITC = 0, 1, 2
 GAUSSIAN, BERNOULLI_LOGIT = 0, 1
 
 # every symbol include/vif.h declares
-EXPORTS = ["vif_build", "vif_nll", "vif_predict", "vif_laplace_mode", "vif_laplace_nll",
+EXPORTS = ["vif_build", "vif_nll", "vif_predict", "vif_laplace_mode", "vif_laplace_nll", "vif_laplace_predict",
            "vif_tridiag_log_quadrature", "vif_batch_create", "vif_batch_run",
            "vif_batch_info", "vif_batch_destroy", "vif_mlp_bytes", "vif_mlp_init", "vif_mlp_set_params",
            "vif_mlp_get_params", "vif_mlp_forward", "vif_mlp_backward", "vif_mlp_features", "vif_mlp_train", "vif_set_neighbors", "vif_get_neighbors",
@@ -102,6 +102,8 @@ def lib() -> C.CDLL:
         L.vif_laplace_nll.argtypes = [vp, C.POINTER(VifCov), vp, C.POINTER(LaplaceOpts), i32, vp, C.c_double,
                                       i32, dp, vp, vp, C.POINTER(LaplaceNllStats)]
         L.vif_tridiag_log_quadrature.argtypes = [vp, vp, i32, dp]
+        L.vif_laplace_predict.argtypes = [vp, C.POINTER(VifCov), vp, C.POINTER(LaplaceOpts), vp, i64, i32, vp,
+                                          C.c_double, i32, vp, vp, C.POINTER(LaplaceStats)]
         L.vif_set_neighbors.argtypes = [vp, vp]
         L.vif_get_neighbors.argtypes = [vp, vp]
         L.vif_get_factors.argtypes = [vp, vp, vp]
@@ -347,6 +349,27 @@ class Context:
         stats = {k: getattr(st, k) for k, _ in LaplaceNllStats._fields_}
         stats["q"], stats["zPz"], stats["status"] = q, zpz, rc
         return out.value, stats
+
+    def laplace_predict(self, theta, y, Xp, eps=None, cg_tol=1e-6, cg_max_iter=1000, rel_tol=1e-6,
+                        max_pcg=1000, max_newton=50, precond=0, allow_not_converged=False):
+        """Latent predictive means (Prop. 3.1) and, with eps (nsample x (m + 2n) normals),
+        variances by Alg. 1 (SBPV).  Returns (mean, var or None, stats)."""
+        cv, ls = make_cov(theta)
+        opts = LaplaceOpts(float(rel_tol), int(max_pcg), int(max_newton), int(precond), 0, None)
+        Xp = _f64(Xp)
+        npred = int(Xp.shape[0])
+        mean = np.empty(npred)
+        var = np.empty(npred) if eps is not None else None
+        e = _f64(eps) if eps is not None else None
+        st = LaplaceStats()
+        rc = lib().vif_laplace_predict(self.h, C.byref(cv), _ptr(_f64(y)), C.byref(opts), _ptr(Xp), npred,
+                                       int(e.shape[0]) if e is not None else 0, _ptr(e), float(cg_tol),
+                                       int(cg_max_iter), _ptr(mean), _ptr(var), C.byref(st))
+        if not (rc == VIF_OK or (allow_not_converged and rc == VIF_ERR_NOT_CONVERGED)):
+            self._check(rc)
+        stats = {k: getattr(st, k) for k, _ in LaplaceStats._fields_}
+        stats["status"] = rc
+        return mean, var, stats
 
     def mlp_features(self, W) -> np.ndarray:
         F = np.empty((self.n, MLP_NIN), dtype=np.float32)

@@ -399,6 +399,32 @@ def test_vifla_nll_with_fitc_slq_matches_oracle_probe_by_probe():
     ctx.close()
 
 
+def test_laplace_prediction_with_sbpv_matches_oracle():
+    """Prop. 3.1 means and Alg. 1 (SBPV) variances with the same normals as the oracle; the FITC
+    solves (Eq. pcls2) give the same draws z7 and so the same variances."""
+    P = synth.make_problem(1500, 2, 25, 10, "matern32", 1.0, 0.1, 0.0, 46, likelihood="bernoulli_logit",
+                           lloyd=3, n_pred=150)
+    N = O.causal_neighbors(P.X, P.Z, P.theta, 10)
+    vif = O.VIF(P.X, P.Z, P.theta, N)
+    b_dense, _, _ = O.laplace_mode(vif, P.y, dense=True)
+    Np = O.pred_neighbors(P.X, P.Z, P.theta, P.Xp, 10)
+    eps = synth.slq_normals(8, vif.m, vif.n, seed=9)
+    mu_o, var_o, _ = O.laplace_predict_sbpv(vif, P.y, b_dense, P.Xp, Np, eps, 1e-10)
+    ctx = V.Context(P.X, P.Z, 10, P.theta, likelihood=V.BERNOULLI_LOGIT, neighbor_search=False)
+    ctx.set_neighbors(N.astype(np.int32))
+    mu, var, st = ctx.laplace_predict(P.theta, P.y, P.Xp, eps, cg_tol=1e-10, rel_tol=1e-10)
+    np.testing.assert_allclose(mu, mu_o, rtol=1e-6, atol=1e-8)
+    np.testing.assert_allclose(var, var_o, rtol=1e-6, atol=1e-9)
+    mu_f, var_f, _ = ctx.laplace_predict(P.theta, P.y, P.Xp, eps, cg_tol=1e-10, rel_tol=1e-10,
+                                         precond=V.PRECOND_FITC)
+    np.testing.assert_allclose(mu_f, mu_o, rtol=1e-6, atol=1e-8)
+    np.testing.assert_allclose(var_f, var_o, rtol=1e-6, atol=1e-9)
+    mu_n, var_n, _ = ctx.laplace_predict(P.theta, P.y, P.Xp)
+    assert var_n is None
+    np.testing.assert_allclose(mu_n, mu_o, rtol=1e-5, atol=1e-7)
+    ctx.close()
+
+
 def test_laplace_rejects_a_nugget():
     P = bern(300, 10, 4, 34)
     ctx = V.Context(P.X, P.Z, 4, P.theta, likelihood=V.BERNOULLI_LOGIT)
