@@ -13,8 +13,8 @@
 // accumulators alternate so that the MMAs of chunk c run while the partial of chunk
 // c-1 is read out.
 //
-// CTA: 128 points (one TMEM lane each) x 256 output columns, 8 warps.  Per chunk every
-// thread evaluates 16 kernel values of one point, splits them and writes them into the
+// CTA: 128 points (one TMEM lane each) x 256 output columns, 16 warps.  Per chunk every
+// thread evaluates 8 kernel values of one point, splits them and writes them into the
 // swizzled A-operand tiles; thread 0 brings the matching L_m^{-1} tiles (packed once
 // per call, already in the swizzled image) with one bulk copy per tile and issues the
 // 12 MMAs.  Two operand stages let the kernel evaluation of chunk c+1 overlap the MMAs
@@ -32,7 +32,7 @@ constexpr int AT_M = 128;                         // points per CTA
 constexpr int AT_N = 256;                         // output columns per CTA
 constexpr int AT_K = 32;                          // inducing points per chunk
 constexpr int AT_MAXD = 16;
-constexpr int AT_THREADS = 256;
+constexpr int AT_THREADS = 512;
 constexpr uint32_t AT_ATILE = AT_M * 128;         // bytes of one A-operand tile (hi or lo)
 constexpr uint32_t AT_BTILE = AT_N * 128;         // bytes of one B-operand tile (hi or lo)
 constexpr uint32_t AT_STAGE = 2 * AT_ATILE + 2 * AT_BTILE;
@@ -83,12 +83,12 @@ __global__ __launch_bounds__(AT_THREADS, 1) void lowrank_A_tc_kernel(
   const int nchunk = min(nchunk_all, (h * AT_N + ncols - 1) / AT_K + 1);
   const uint32_t idesc = tc::idesc_tf32(AT_M, ncols);
   const float* pk_h = pk + (size_t)h * nchunk_all * 2 * (AT_N * AT_K);
-  // kernel evaluation: point krow, values 16 khalf .. 16 khalf + 15 of each chunk
-  const int krow = tid & (AT_M - 1), khalf = tid >> 7;
+  // kernel evaluation: point krow, values 8 kq .. 8 kq + 7 of each chunk
+  const int krow = tid & (AT_M - 1), kq = tid >> 7;
   const int64_t p = row0 + krow;
-  // read-out: TMEM lanes dl .. dl + 31, columns dc .. dc + 127 of the accumulator
-  const int dl = 32 * (warp & 3), dc = 128 * (warp >> 2);
-  const int ngrp = max(0, min(4, (ncols - dc) / 32));
+  // read-out: TMEM lanes dl .. dl + 31, columns dc .. dc + 63 of the accumulator
+  const int dl = 32 * (warp & 3), dc = 64 * (warp >> 2);
+  const int ngrp = max(0, min(2, (ncols - dc) / 32));
 
   if (warp == 0) tc::tmem_alloc(&sb.tmem, AT_TMEM_COLS);
   if (tid == 0) {
@@ -107,20 +107,20 @@ __global__ __launch_bounds__(AT_THREADS, 1) void lowrank_A_tc_kernel(
   unsigned long long xp[DP];
 #pragma unroll
   for (int j = 0; j < DP; ++j) xp[j] = pack_f2(x[(2 * j) % DX], x[(2 * j + 1) % DX]);
-  // inducing points of chunk c, element e = tid + 256 j of the chunk's 32 x d block
-  auto zload = [&](int c, float (&zr)[2]) {
+  // inducing points of chunk c, element e = tid + 512 j of the chunk's 32 x d block
+  auto zload = [&](int c, float (&zr)[1]) {
 #pragma unroll
-    for (int j = 0; j < 2; ++j) {
+    for (int j = 0; j < 1; ++j) {
       const int e = tid + AT_THREADS * j;
       const int k = c * AT_K + e / max(d, 1);
       zr[j] = (c < nchunk && e < AT_K * d && k < m) ? Zs[(size_t)c * AT_K * d + e] : 0.f;
     }
   };
-  float zpre[2];
+  float zpre[1];
   zload(0, zpre);
-  unsigned long long acc2[64];   // column pairs (2j, 2j+1) of this thread's read-out range
+  unsigned long long acc2[32];   // column pairs (2j, 2j+1) of this thread's read-out range
 #pragma unroll
-  for (int j = 0; j < 64; ++j) acc2[j] = 0ull;
+  for (int j = 0; j < 32; ++j) acc2[j] = 0ull;
   tc::fence_before_sync();
   __syncthreads();
   tc::fence_after_sync();
@@ -137,7 +137,7 @@ __global__ __launch_bounds__(AT_THREADS, 1) void lowrank_A_tc_kernel(
     tc::fence_after_sync();
     const uint32_t base = tmem + ((uint32_t)dl << 16) + (uint32_t)((j & 1) * AT_N + dc);
 #pragma unroll
-    for (int g = 0; g < 4; ++g) {
+    for (int g = 0; g < 2; ++g) {
       if (g < ngrp) {
         float v[32];
         tc::tmem_ld32(base + g * 32, v);
@@ -169,7 +169,7 @@ __global__ __launch_bounds__(AT_THREADS, 1) void lowrank_A_tc_kernel(
     unsigned char* b_lo = st + 2 * AT_ATILE + AT_BTILE;
     // stage s was last read by the MMAs of chunk c-2, read out at iteration c-1
 #pragma unroll
-    for (int j = 0; j < 2; ++j) {
+    for (int j = 0; j < 1; ++j) {
       const int e = tid + AT_THREADS * j;
       if (e < AT_K * AT_MAXD) sb.zs[s][e] = zpre[j];
     }
@@ -178,14 +178,14 @@ __global__ __launch_bounds__(AT_THREADS, 1) void lowrank_A_tc_kernel(
       failed = true;
       break;
     }
-    // 16 kernel values of this thread's point, split into tf32 hi + lo
+    // 8 kernel values of this thread's point, split into tf32 hi + lo
     const int kmax = min(AT_K, m - c * AT_K);
 #pragma unroll
-    for (int q = 0; q < 4; ++q) {
+    for (int q = 0; q < 2; ++q) {
       float hv[4], lv[4];
 #pragma unroll
       for (int u = 0; u < 4; ++u) {
-        const int kk = khalf * 16 + q * 4 + u;
+        const int kk = kq * 8 + q * 4 + u;
         float kv = 0.f;
         if (kk < kmax && p < n) {
           float r2 = 0.f;
@@ -221,7 +221,7 @@ __global__ __launch_bounds__(AT_THREADS, 1) void lowrank_A_tc_kernel(
         hv[u] = tc::to_tf32(kv);
         lv[u] = tc::to_tf32(kv - hv[u]);
       }
-      const uint32_t off = tc::sw128_off32(krow, khalf * 16 + q * 4);
+      const uint32_t off = tc::sw128_off32(krow, kq * 8 + q * 4);
       *reinterpret_cast<float4*>(a_hi + off) = make_float4(hv[0], hv[1], hv[2], hv[3]);
       *reinterpret_cast<float4*>(a_lo + off) = make_float4(lv[0], lv[1], lv[2], lv[3]);
     }
@@ -278,7 +278,7 @@ __global__ __launch_bounds__(AT_THREADS, 1) void lowrank_A_tc_kernel(
     if (row < n) {
       float* dst = A + (size_t)row * mpad + h * AT_N + dc;
 #pragma unroll
-      for (int g = 0; g < 4; ++g)
+      for (int g = 0; g < 2; ++g)
         if (g < ngrp) {
 #pragma unroll
           for (int j = 0; j < 16; j += 2) {
