@@ -150,13 +150,14 @@ def stage_algorithmic(P, stage):
 
 
 def launches_per_eval(m):
-    """Kernel launches of one vif_nll call (counted from the launch sites; 104 for
+    """Kernel launches of one vif_nll call (counted from the launch sites; 168 for
     m = 500, as in the committed launch list)."""
-    nt = (m + 31) // 32
-    nt1 = (m + 1 + 31) // 32
+    ch = lambda k: (k + 15) // 16      # 16 x 16 Cholesky tiles
+    tr = (m + 31) // 32                # 32 x 32 triangular-inverse tiles
+    nt, nt1 = ch(m), ch(m + 1)
     chol = lambda t: t + (t - 1)       # panel launches + trailing-update launches
     trtri = lambda t: 1 + 2 * (t - 1)  # diagonal tiles, then product + finish per block diagonal
-    return (2 + 1 + chol(nt) + trtri(nt) + 1 + 1   # scaling x2, Sigma_m, Cholesky, inverse, L^-1 operand, A
+    return (2 + 1 + chol(nt) + trtri(tr) + 1 + 1   # scaling x2, Sigma_m, Cholesky, inverse, L^-1 operand, A
             + 1 + 2 + 2 + chol(nt1) + 1)          # factor, Gram + reduce, logD sum, capacitance Cholesky, finish
 
 
@@ -358,10 +359,10 @@ def run_reference(args, rank, world):
     if rank != 0:
         return
     P, _ = workload(args.n)
-    cb = cpu_baseline(P, args.cpu_sample, steps=1)       # warm-up / calibration
+    cb = cpu_baseline(P, args.cpu_sample, steps=1)       # first warm-up step (also the calibration)
     vals = []
-    for _ in range(max(args.warmup, 0)):
-        pass
+    for _ in range(max(args.warmup - 1, 0)):
+        cpu_baseline(P, args.cpu_sample, steps=1)
     t0 = time.time()
     for _ in range(args.steps):
         vals.append(cpu_baseline(P, args.cpu_sample, steps=1)["value"])
