@@ -22,7 +22,9 @@ dense solves, sparse products, sorting) as the only building blocks:
   log-determinant (Eq. slq_v1, App. D), probes drawn by the recipe of Sec. 4.3;
 * the FITC preconditioner (Sec. 4.3, App. E.2) with the system form of Eq. pcls2 and
   the SLQ form of Eq. slq_v2;
-* VIF-Laplace predictive distributions (Prop. 3.1) and their variances by Alg. 1 (SBPV).
+* VIF-Laplace predictive distributions (Prop. 3.1) and their variances by Alg. 1 (SBPV);
+* the VIF-Laplace gradient by stochastic trace estimation with the preconditioner control
+  variate (Sec. 4.1, App. B, App. D).
 
 Readings of points the paper leaves open (all shared with the CUDA path):
   R1 kernel forms of Rasmussen & Williams; "range" = length scale lambda.
@@ -35,6 +37,9 @@ Readings of points the paper leaves open (all shared with the CUDA path):
   R9 prediction points condition on training points only (B_p = I); their
      neighbours are the m_v nearest training points by d_c (non-causal).
   R10 Newton from b=0; PCG from x=0 stops at ||v - A x||_2/||v||_2 <= tol.
+  R16 derivatives in theta of Sigma_dagger^{-1}, log det Sigma_dagger, log det P^ and B^T W B are
+      central differences (relative step 1e-4) with N, Z, W and the mode fixed; the control
+      variate is applied to the theta traces, the traces for dL/db use the plain estimate.
 """
 from __future__ import annotations
 
@@ -922,6 +927,145 @@ def vifla_logdet_dense(vif: VIF, b) -> float:
     S = vif.dense_Sigma_dagger()
     sgn, ld = np.linalg.slogdet(S * W[None, :] + np.eye(vif.n))
     return float(ld)
+
+
+# ----------------------------------------------------------------------------
+# Gradient of the VIF-Laplace likelihood by stochastic trace estimation
+# (Sec. 4.1 after Eq. slq_v2, App. B "Gradients", App. D control variate)
+# ----------------------------------------------------------------------------
+def laplace_param_vector(theta) -> np.ndarray:
+    """Parameter order of the VIF-Laplace gradient: (sigma1^2, lambda_1..lambda_k); a latent
+    GP has no nugget."""
+    return np.concatenate([[theta.variance], np.atleast_1d(theta.lengthscale)])
+
+
+def laplace_theta_from_vector(theta, v):
+    t = theta.copy()
+    t.variance = float(v[0])
+    t.lengthscale = np.array(v[1:], dtype=np.float64)
+    return t
+
+
+def bern_dW(b):
+    """dW_ii/db_i for the Bernoulli-logit W_ii = p(1-p), p = sigmoid(b_i):  p(1-p)(1-2p)."""
+    p = 1.0 / (1.0 + np.exp(-b))
+    return p * (1.0 - p) * (1.0 - 2.0 * p)
+
+
+def _perturbed(X, Z, theta, N, rel_step):
+    """For each parameter k: (h_k, VIF at theta + h_k e_k, VIF at theta - h_k e_k), N and Z
+    fixed (R16)."""
+    v0 = laplace_param_vector(theta)
+    out = []
+    for k in range(v0.size):
+        h = rel_step * abs(v0[k])
+        vp, vm = v0.copy(), v0.copy()
+        vp[k] += h
+        vm[k] -= h
+        out.append((h, VIF(X, Z, laplace_theta_from_vector(theta, vp), N),
+                    VIF(X, Z, laplace_theta_from_vector(theta, vm), N)))
+    return out
+
+
+def vifla_grad_ste(X, Z, theta, N, y, b, eps, tol: float, solve_tol: float, max_iter: int = 1000,
+                   rel_step: float = 1e-4):
+    """Gradient of L^VIFLA (Eq. log_det_VIFLA) with respect to (sigma1^2, lambda) at the mode b,
+    VIFDU form (Eq. pcls1 / slq_v1), assembled as in App. B:
+
+        dL/dth_k = 1/2 b^T Delta_k b + 1/2 dlogdet(Sigma_dagger W + I)/dth_k + (dL/db)^T db/dth_k,
+        dlogdet(Sigma_dagger W + I)/dth_k = dlogdet(Sigma_dagger)/dth_k + Tr(H^{-1} Delta_k),
+        db/dth_k = -H^{-1} Delta_k b,   dL/db_i = 1/2 Tr(H^{-1} dW/db_i),
+
+    with H = W + Sigma_dagger^{-1} and Delta_k = dSigma_dagger^{-1}/dth_k.  Both traces are
+    stochastic trace estimates (Sec. 4.1) from the SLQ probes z_i ~ N(0, P^) (recipe of
+    Sec. 4.3): with u_i = H^{-1} z_i (the PCG solves of the SLQ, tolerance `tol`) and
+    y_i = P^{-1} z_i,
+        Tr(H^{-1} dW/db_j) ~ (1/l) sum_i u_ij dW_jj/db_j y_ij,
+        Tr(H^{-1} Delta_k) ~ (1/l) sum_i s_ik,  s_ik = u_i^T Delta_k y_i,
+    the latter with the control variate of App. D built from P^ = B^T W B + Sigma_dagger^{-1}:
+        c_ik = y_i^T (dP^/dth_k) y_i,  tau_k = Tr(P^{-1} dP^/dth_k) = dlogdet(P^)/dth_k,
+        c_opt = sum_i (s_ik - mean s_k)(c_ik - tau_k) / sum_i (c_ik - tau_k)^2,
+        T_k = (1/l) sum_i (s_ik - c_opt c_ik) + c_opt tau_k.
+    The implicit term is -v^T Delta_k b with v = H^{-1} (dL/db) (PCG, tolerance `solve_tol`).
+    Every derivative of a theta-dependent quantity (the bilinear forms x^T Sigma_dagger^{-1} y,
+    (B y)^T W (B y), log det Sigma_dagger, log det P^) is a central difference in th_k with step
+    rel_step * th_k, holding N, Z, W and b fixed (R16).
+    eps: l x (m + 2n) standard normals as in vifla_nll_slq.  Returns a dict with grad, s, c
+    (l x q), trace_plain, c_opt, tau, trace (q) and the vectors g = dL/db, v."""
+    vif = VIF(X, Z, theta, N)
+    n, m = vif.n, vif.m
+    _, W = bern_grad_W(y, b)
+    pre = VIFDU(vif, W)
+    H = lambda w: W * w + vif.Sigma_dagger_inv(w)
+    U, Yp = [], []
+    for e in np.atleast_2d(eps):
+        z = vifdu_sample(vif, W, e[:m], e[m:m + n], e[m + n:m + 2 * n])
+        u, _, _, _, _ = pcg_lanczos(H, pre.apply, z, tol, max_iter)
+        U.append(u)
+        Yp.append(pre.apply(z))
+    U, Yp = np.array(U), np.array(Yp)
+    ell = U.shape[0]
+    g = 0.5 * bern_dW(b) * (U * Yp).mean(axis=0)
+    v, _, _ = pcg(H, pre.apply, g, solve_tol, max_iter)
+
+    def forms(vf):
+        sdb = vf.Sigma_dagger_inv(b)
+        sdy = np.array([vf.Sigma_dagger_inv(yi) for yi in Yp])
+        By = np.array([vf.B @ yi for yi in Yp])
+        return dict(ldS=vf.logdet(), ldP=vifdu_logdet(vf, W), bb=float(b @ sdb), vb=float(v @ sdb),
+                    uy=(U * sdy).sum(axis=1), yy=(Yp * sdy).sum(axis=1), bwb=(By * (W * By)).sum(axis=1))
+
+    q = laplace_param_vector(theta).size
+    grad = np.empty(q)
+    S = np.empty((ell, q))
+    C = np.empty((ell, q))
+    tr_plain, c_opt, tau, trace = (np.empty(q) for _ in range(4))
+    for k, (h, vp, vm) in enumerate(_perturbed(X, Z, theta, N, rel_step)):
+        fp, fm = forms(vp), forms(vm)
+        d = {key: (fp[key] - fm[key]) / (2.0 * h) for key in fp}
+        S[:, k] = d["uy"]
+        C[:, k] = d["bwb"] + d["yy"]
+        tau[k] = d["ldP"]
+        tr_plain[k] = S[:, k].mean()
+        dc = C[:, k] - tau[k]
+        den = float(dc @ dc)
+        c_opt[k] = float((S[:, k] - tr_plain[k]) @ dc) / den if den > 0 else 0.0
+        trace[k] = float((S[:, k] - c_opt[k] * C[:, k]).mean()) + c_opt[k] * tau[k]
+        grad[k] = 0.5 * d["bb"] + 0.5 * (d["ldS"] + trace[k]) - d["vb"]
+    return dict(grad=grad, s=S, c=C, trace_plain=tr_plain, c_opt=c_opt, tau=tau, trace=trace, g=g, v=v)
+
+
+def dense_Sigma_dagger_inv(vif: VIF) -> np.ndarray:
+    """Sigma_dagger^{-1} column by column through the Woodbury form (Sec. 2.2); inverting the dense
+    Sigma_dagger of a latent GP (no nugget) loses digits to its conditioning."""
+    return np.column_stack([vif.Sigma_dagger_inv(e) for e in np.eye(vif.n)])
+
+
+def vifla_grad_exact(X, Z, theta, N, y, b, rel_step: float = 1e-4):
+    """The gradient of vifla_grad_ste with every trace taken exactly from dense matrices (small n):
+    Tr(H^{-1} Delta_k) with Delta_k the central difference of the dense Sigma_dagger^{-1}, and
+    dL/db_j = 1/2 (H^{-1})_jj dW_jj/db_j.  The value the stochastic estimate targets."""
+    vif = VIF(X, Z, theta, N)
+    _, W = bern_grad_W(y, b)
+    Hinv = np.linalg.inv(np.diag(W) + dense_Sigma_dagger_inv(vif))
+    g = 0.5 * bern_dW(b) * np.diag(Hinv)
+    v = Hinv @ g
+    q = laplace_param_vector(theta).size
+    grad, trace = np.empty(q), np.empty(q)
+    for k, (h, vp, vm) in enumerate(_perturbed(X, Z, theta, N, rel_step)):
+        Dk = (dense_Sigma_dagger_inv(vp) - dense_Sigma_dagger_inv(vm)) / (2.0 * h)
+        dldS = (vp.logdet() - vm.logdet()) / (2.0 * h)
+        trace[k] = float(np.sum(Hinv * Dk))
+        grad[k] = 0.5 * b @ Dk @ b + 0.5 * (dldS + trace[k]) - v @ Dk @ b
+    return dict(grad=grad, trace=trace, g=g, v=v)
+
+
+def vifla_nll_exact(X, Z, theta, N, y) -> float:
+    """L^VIFLA (Eq. log_det_VIFLA) with the exact (dense Newton) mode and the dense
+    log det(Sigma_dagger W + I) (small n)."""
+    vif = VIF(X, Z, theta, N)
+    b, _, _ = laplace_mode(vif, y, dense=True, psi_tol=1e-14)
+    return -bern_loglik(y, b) + 0.5 * float(b @ vif.Sigma_dagger_inv(b)) + 0.5 * vifla_logdet_dense(vif, b)
 
 
 # ----------------------------------------------------------------------------

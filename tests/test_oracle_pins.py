@@ -433,6 +433,69 @@ def test_sbpv_is_unbiased_for_the_laplace_predictive_variances():
 
 
 # --------------------------------------------------------------------------- gradient
+def _lap_grad_problem(n=70, m=6, mv=3, seed=21):
+    P = small_problem(n=n, m=m, mv=mv, nugget=0.0, likelihood="bernoulli_logit", ls=0.15, seed=seed)
+    N = O.causal_neighbors(P.X, P.Z, P.theta, mv)
+    vif = O.VIF(P.X, P.Z, P.theta, N)
+    b, _, _ = O.laplace_mode(vif, P.y, dense=True, psi_tol=1e-14)
+    return P, N, vif, b
+
+
+def test_vifla_gradient_with_exact_traces_is_the_derivative_of_the_exact_likelihood():
+    """App. B: explicit terms, log det derivative and the implicit term -v^T Delta_k b through the
+    mode; with every trace exact the assembled gradient must equal central differences of L^VIFLA
+    itself (dense Newton mode re-found at each perturbed theta, dense log-determinant)."""
+    P, N, vif, b = _lap_grad_problem()
+    ex = O.vifla_grad_exact(P.X, P.Z, P.theta, N, P.y, b)
+    v0 = O.laplace_param_vector(P.theta)
+    fd = np.empty(v0.size)
+    for k in range(v0.size):
+        h = 1e-4 * abs(v0[k])
+        vp, vm = v0.copy(), v0.copy()
+        vp[k] += h
+        vm[k] -= h
+        fd[k] = (O.vifla_nll_exact(P.X, P.Z, O.laplace_theta_from_vector(P.theta, vp), N, P.y)
+                 - O.vifla_nll_exact(P.X, P.Z, O.laplace_theta_from_vector(P.theta, vm), N, P.y)) / (2 * h)
+    np.testing.assert_allclose(ex["grad"], fd, rtol=2e-5, atol=1e-6)
+
+
+def test_ste_sums_are_exact_when_the_probes_span_the_preconditioner():
+    """With eps running over the identity of R^(m+2n) the probes satisfy sum_i z_i z_i^T = P^
+    exactly (Sec. 4.3 recipe), so l times each STE average of Sec. 4.1 / App. D is the exact
+    trace: Tr(H^{-1} Delta_k), Tr(P^{-1} dP^/dth_k) and the diagonal (H^{-1})_jj behind dL/db.
+    The recipe reproduces P^ to about 1e-7 relative (Sigma_dagger^{-1} Sigma_dagger Sigma_dagger^{-1}
+    of a latent GP amplifies rounding by the conditioning of Sigma_dagger), and cond(P^) ~ 300 here,
+    hence rtol 3e-4; a wrong normalisation or a dropped term is off by 7e-3 or more."""
+    P, N, vif, b = _lap_grad_problem(n=40, m=5, mv=3, seed=23)
+    n, m = vif.n, vif.m
+    eps = np.eye(m + 2 * n)
+    ell = eps.shape[0]
+    r = O.vifla_grad_ste(P.X, P.Z, P.theta, N, P.y, b, eps, 1e-13, 1e-13)
+    ex = O.vifla_grad_exact(P.X, P.Z, P.theta, N, P.y, b)
+    np.testing.assert_allclose(ell * r["trace_plain"], ex["trace"], rtol=3e-4)
+    np.testing.assert_allclose(ell * r["c"].mean(axis=0), r["tau"], rtol=3e-4)
+    np.testing.assert_allclose(ell * r["g"], ex["g"], rtol=3e-4, atol=1e-9)
+
+
+def test_ste_gradient_is_unbiased_and_the_control_variate_reduces_its_variance():
+    """Random probes z ~ N(0, P^): the plain STE of Tr(H^{-1} Delta_k) averages to the exact trace
+    and the control-variate samples c_ik to Tr(P^{-1} dP^/dth_k), within four standard errors;
+    the control-variate estimate of App. D stays unbiased with a smaller spread."""
+    P, N, vif, b = _lap_grad_problem()
+    n, m = vif.n, vif.m
+    ell = 200
+    eps = np.random.default_rng(9).standard_normal((ell, m + 2 * n))
+    r = O.vifla_grad_ste(P.X, P.Z, P.theta, N, P.y, b, eps, 1e-12, 1e-12)
+    ex = O.vifla_grad_exact(P.X, P.Z, P.theta, N, P.y, b)
+    se = r["s"].std(axis=0, ddof=1) / math.sqrt(ell)
+    se_c = r["c"].std(axis=0, ddof=1) / math.sqrt(ell)
+    se_cv = (r["s"] - r["c_opt"] * r["c"]).std(axis=0, ddof=1) / math.sqrt(ell)
+    assert np.all(np.abs(r["trace_plain"] - ex["trace"]) <= 4 * se), (r["trace_plain"], ex["trace"], se)
+    assert np.all(np.abs(r["c"].mean(axis=0) - r["tau"]) <= 4 * se_c), (r["c"].mean(axis=0), r["tau"], se_c)
+    assert np.all(np.abs(r["trace"] - ex["trace"]) <= 4 * se_cv), (r["trace"], ex["trace"], se_cv)
+    assert np.all(se_cv < 0.5 * se), (se_cv, se)
+
+
 def test_fd_gradient_with_full_conditioning_is_the_exact_gp_gradient():
     """m_v = n-1 makes the VIF likelihood the exact one, whose gradient is analytic."""
     P = small_problem(n=60, m=8, mv=59, nugget=0.1, kind="matern32", ls=0.2)
