@@ -192,6 +192,39 @@ vif_status vif_laplace_nll(vif_ctx *ctx, const vif_cov *theta, const double *y, 
                            int32_t nprobe, const double *eps, double slq_tol, int32_t slq_max_iter,
                            double *nll_out, double *probe_q, double *probe_zpz, vif_laplace_nll_stats *stats);
 
+/* vif_laplace_nll_grad -- vif_laplace_nll (same arguments, same nll_out and stats->nll) and the
+ * gradient of L with respect to (sigma1^2, lambda_1..lambda_{n_ls}) by stochastic trace estimation
+ * (Sec. 4.1 after Eq. slq_v2; App. B "Gradients"; App. D), VIFDU form (opts->precond = 0 only):
+ *     dL/dth_k = b~^T Delta_k b~ / 2 + (dlog det Sigma_dagger/dth_k + T_k) / 2 - v^T Delta_k b~,
+ * H = W + Sigma_dagger^{-1}, Delta_k = dSigma_dagger^{-1}/dth_k, the last term being dL/db~ . db~/dth_k
+ * with db~/dth_k = -H^{-1} Delta_k b~ and v = H^{-1} dL/db~ (CG on Eq. pcls1 with the mode's rel_tol and
+ * max_pcg).  The probes of the likelihood's SLQ are reused: with u_i = H^{-1} z_i (their CG solutions)
+ * and y_i = P^{-1} z_i,
+ *     dL/db~_j ~ dW_jj/db_j (1/l) sum_i u_ij y_ij / 2,   s_ik = u_i^T Delta_k y_i,
+ *     T_k = (1/l) sum_i (s_ik - c_k c_ik) + c_k tau_k   (control variate of App. D),
+ *     c_ik = y_i^T (dP/dth_k) y_i,  tau_k = Tr(P^{-1} dP/dth_k) = dlog det P/dth_k,
+ *     c_k = sum_i (s_ik - mean_i s_ik)(c_ik - tau_k) / sum_i (c_ik - tau_k)^2  (0 if the sum is 0),
+ * P = B^T W B + Sigma_dagger^{-1} (App. E.1).  Derivatives in theta (of the bilinear forms
+ * x^T Sigma_dagger^{-1} y and (B y)^T W (B y), of log det Sigma_dagger and of log det P) are central
+ * differences with step 1e-4 |th_k|, holding N, Z, the mode b~ and W fixed: the factors are rebuilt
+ * twice per parameter, and those of theta are restored before the call returns.
+ *   grad_out: host, 1 + n_ls values (required).
+ *   probe_terms: host, nprobe x (1 + n_ls) x 2 (s_ik, c_ik), or NULL.
+ *   trace_out: host, (1 + n_ls) x 4 (mean_i s_ik, c_k, tau_k, T_k), or NULL.
+ *   stats: host, may be NULL.
+ * Errors as vif_laplace_nll; VIF_ERR_ARG for precond != 0. */
+typedef struct {
+  vif_laplace_nll_stats nll;  /* as vif_laplace_nll */
+  int32_t pcg_iters_v;        /* CG iterations of the solve v = H^{-1} dL/db~ */
+  int32_t reserved;
+  double ms_grad;             /* wall time after the likelihood: the solve for v and the differences */
+} vif_laplace_grad_stats;
+
+vif_status vif_laplace_nll_grad(vif_ctx *ctx, const vif_cov *theta, const double *y, const vif_laplace_opts *opts,
+                                int32_t nprobe, const double *eps, double slq_tol, int32_t slq_max_iter,
+                                double *nll_out, double *grad_out, double *probe_terms, double *trace_out,
+                                vif_laplace_grad_stats *stats);
+
 /* vif_laplace_predict -- VIF-Laplace posterior predictive distribution of the latent GP at np
  * new inputs (Prop. 3.1, prediction points conditioning on training points only as in
  * vif_predict), at the mode b~ found as by vif_laplace_mode (opts->precond 0 = VIFDU or 2 = FITC).

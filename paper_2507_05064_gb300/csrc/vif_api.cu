@@ -59,6 +59,10 @@ struct vif_ctx {
   double *l_Apad = nullptr, *l_anorm2 = nullptr, *l_dvinv = nullptr;   // FITC preconditioner
   double* l_pacc = nullptr;                             // SBPV sums of squares (np)
   int64_t l_pacc_cap = 0;
+  // gradient by stochastic trace estimation: probe solves U, P^{-1} z_i (g_cap x n each), dL/db~, v,
+  // the bilinear forms of one perturbed theta (6 + 3 g_cap) and a three-way reduction scratch
+  double *g_U = nullptr, *g_Y = nullptr, *g_g = nullptr, *g_v = nullptr, *g_sc = nullptr, *g_red = nullptr;
+  int64_t g_cap = 0;
   double *l_b = nullptr, *l_W = nullptr, *l_v = nullptr, *l_Ginv = nullptr, *l_om = nullptr, *l_rsD = nullptr,
          *l_ll = nullptr, *l_x = nullptr, *l_r = nullptr, *l_z = nullptr, *l_p = nullptr, *l_Ap = nullptr,
          *l_t = nullptr, *l_t2 = nullptr, *l_x1 = nullptr, *l_sdi = nullptr, *l_sm = nullptr, *l_cm = nullptr,
@@ -283,6 +287,7 @@ void free_ctx(vif_ctx* c) {
                    c->l_x,    c->l_r,   c->l_z,    c->l_p,    c->l_Ap,   c->l_t,    c->l_t2,   c->l_x1,
                    c->l_sdi,  c->l_sm,  c->l_cm,   c->l_tm,   c->l_part, c->l_LinvC, c->l_G3,  c->l_LinvC3,
                    c->l_sc,   c->l_red, c->l_corr, c->sched_fwd, c->sched_rev, c->ch_coef, c->slq_eps, c->l_Apad, c->l_anorm2, c->l_dvinv, c->l_pacc, c->l_counter, c->l_abort, c->m_feat,
+                   c->g_U,    c->g_Y,   c->g_g,    c->g_v,    c->g_sc,   c->g_red,
                    c->m_gc,   c->m_part, c->m_grad};
   for (void* b : pbufs)
     if (b) cudaFree(b);
@@ -884,7 +889,8 @@ vif_status vif_predict(vif_ctx* ctx, const vif_cov* theta, const double* y, cons
 namespace {
 
 // Factors of the latent-GP VIF prior for theta (A, B, D, F, C = I + F^T F and the
-// inverse of its Cholesky factor) and the operator bundle of the Laplace kernels.
+// inverse of its Cholesky factor) and the operator bundle of the Laplace kernels
+// (y: host or device responses, or NULL to keep those already on the device).
 vif_status lap_setup(vif_ctx* ctx, const vif_cov* theta, const double* y, LapOps* o) {
   cudaStream_t s = ctx->stream;
   double *A64, *F64, *LT64;
@@ -893,7 +899,7 @@ vif_status lap_setup(vif_ctx* ctx, const vif_cov* theta, const double* y, LapOps
   CovParams cp = cov_params(theta);
   CK(cudaMemsetAsync(ctx->status, 0, 4 * sizeof(int), s));
   CK(cudaMemsetAsync(ctx->l_abort, 0, sizeof(int), s));
-  CKS(upload(ctx, ctx->y, y, (size_t)ctx->n * sizeof(double)));
+  if (y) CKS(upload(ctx, ctx->y, y, (size_t)ctx->n * sizeof(double)));   // NULL: y already resident
   CKS(apply_scaling(ctx, theta, false));
   CKS(run_pipeline<double>(ctx, cp, A64, LT64, F64, ctx->Xs, ctx->Zs));
   if (ctx->m > 0) CK(dense_trtri_lower(ctx->G, ctx->l_LinvC, ctx->m, ctx->fpad, ctx->trw, s));
@@ -986,10 +992,11 @@ vif_status lap_fitc_setup(vif_ctx* ctx, LapOps& o, bool fresh, double var) {
 
 // Preconditioned CG from x = 0 on (W + Sigma_dagger^{-1}) x = v (v in l_v, x in l_x).
 // Optionally records the CG step lengths alpha_j, the direction updates beta_j and the
-// starting value r_0^T P^{-1} r_0 (the Lanczos coefficients of App. D).
+// starting value r_0^T P^{-1} r_0 (the Lanczos coefficients of App. D), and copies
+// P^{-1} v to z0_out (device, n).
 vif_status lap_pcg(vif_ctx* ctx, const LapOps& o, double tol, int max_it, int* iters, double* rel, bool* capped,
                    std::vector<double>* alphas = nullptr, std::vector<double>* betas = nullptr,
-                   double* rz0 = nullptr) {
+                   double* rz0 = nullptr, double* z0_out = nullptr) {
   cudaStream_t s = ctx->stream;
   const int64_t n = ctx->n;
   double* sc = ctx->l_sc;   // [0]=rz [1]=pAp [2]=alpha [3]=rr [4]=rz_new [5]=beta [6]=vv
@@ -999,6 +1006,7 @@ vif_status lap_pcg(vif_ctx* ctx, const LapOps& o, double tol, int max_it, int* i
   CK(lap_dot(ctx->l_v, ctx->l_v, n, ctx->l_red, sc + 6, s));
   CK(lap_system_precond(o, ctx->l_r, ctx->l_z, s));
   CK(cudaMemcpyAsync(ctx->l_p, ctx->l_z, n * sizeof(double), cudaMemcpyDeviceToDevice, s));
+  if (z0_out) CK(cudaMemcpyAsync(z0_out, ctx->l_z, n * sizeof(double), cudaMemcpyDeviceToDevice, s));
   CK(lap_dot(ctx->l_r, ctx->l_z, n, ctx->l_red, sc + 0, s));
   CK(cudaMemcpyAsync(hs, sc, 7 * sizeof(double), cudaMemcpyDeviceToHost, s));
   CK(cudaStreamSynchronize(s));
@@ -1249,14 +1257,21 @@ vif_status vif_laplace_mode(vif_ctx* ctx, const vif_cov* theta, const double* y,
   return VIF_OK;
 }
 
-vif_status vif_laplace_nll(vif_ctx* ctx, const vif_cov* theta, const double* y, const vif_laplace_opts* lo,
-                           int32_t nprobe, const double* eps, double slq_tol, int32_t slq_max_iter, double* nll_out,
-                           double* probe_q, double* probe_zpz, vif_laplace_nll_stats* stats) {
-  if (!ctx) return VIF_ERR_ARG;
-  ctx->err[0] = 0;
+}  // extern "C"
+
+namespace {
+
+// The body of vif_laplace_nll.  With keepU / keepY (device, nprobe x n, probe-major) it also
+// keeps each probe's CG solution u_i = (W + Sigma_dagger^{-1})^{-1} z_i and y_i = P^{-1} z_i, the
+// vectors the stochastic trace estimates of the gradient reuse (Sec. 4.1).  *newton_ok and
+// *cg_ok report whether Newton converged and no CG solve hit its cap (outputs written either way).
+vif_status laplace_nll_core(vif_ctx* ctx, const vif_cov* theta, const double* y, const vif_laplace_opts* lo,
+                            int32_t nprobe, const double* eps, double slq_tol, int32_t slq_max_iter,
+                            double* nll_out, double* probe_q, double* probe_zpz, vif_laplace_nll_stats* stats,
+                            LapOps* op, double* keepU, double* keepY, bool* newton_ok, bool* cg_ok) {
   if (!nll_out || !eps || nprobe < 1 || !(slq_tol > 0.0) || slq_max_iter < 1)
     return set_err(ctx, VIF_ERR_ARG, "nll_out, eps, nprobe >= 1, slq_tol > 0 and slq_max_iter >= 1 are required");
-  LapOps o;
+  LapOps& o = *op;
   vif_laplace_stats ms{};
   bool converged = false, capped = false;
   CKS(laplace_run(ctx, theta, y, lo, &o, &ms, &converged, &capped));
@@ -1329,7 +1344,9 @@ vif_status vif_laplace_nll(vif_ctx* ctx, const vif_cov* theta, const double* y, 
     double zpz = 0.0, rel = 0.0;
     int it = 0;
     bool cp = false;
-    CKS(lap_pcg(ctx, o, slq_tol, slq_max_iter, &it, &rel, &cp, &al, &be, &zpz));
+    CKS(lap_pcg(ctx, o, slq_tol, slq_max_iter, &it, &rel, &cp, &al, &be, &zpz,
+                keepY ? keepY + (size_t)i * n : nullptr));
+    if (keepU) CK(cudaMemcpyAsync(keepU + (size_t)i * n, ctx->l_x, n * sizeof(double), cudaMemcpyDeviceToDevice, s));
     slq_iters += it;
     slq_capped = slq_capped || cp;
     std::vector<double> d(al.size()), od(al.size() > 0 ? al.size() - 1 : 0);
@@ -1372,10 +1389,187 @@ vif_status vif_laplace_nll(vif_ctx* ctx, const vif_cov* theta, const double* y, 
     stats->ms_mode = ms.ms_total;
     stats->ms_slq = ms_slq;
   }
-  if (!converged || capped || slq_capped)
-    return set_err(ctx, VIF_ERR_NOT_CONVERGED, "Newton %s, CG %s", converged ? "converged" : "hit its cap",
-                   (capped || slq_capped) ? "hit its cap" : "converged");
+  *newton_ok = converged;
+  *cg_ok = !capped && !slq_capped;
   return VIF_OK;
+}
+
+vif_status not_converged(vif_ctx* ctx, bool newton_ok, bool cg_ok) {
+  if (newton_ok && cg_ok) return VIF_OK;
+  return set_err(ctx, VIF_ERR_NOT_CONVERGED, "Newton %s, CG %s", newton_ok ? "converged" : "hit its cap",
+                 cg_ok ? "converged" : "hit its cap");
+}
+
+// Gradient buffers for nprobe probes (grown on demand).
+vif_status grad_buffers(vif_ctx* ctx, int nprobe) {
+  const int64_t n = ctx->n;
+  if (nprobe > ctx->g_cap) {
+    for (double** b : {&ctx->g_U, &ctx->g_Y, &ctx->g_sc}) {
+      if (*b) cudaFree(*b);
+      *b = nullptr;
+    }
+    CKS(dalloc(ctx, &ctx->g_U, (size_t)nprobe * n));
+    CKS(dalloc(ctx, &ctx->g_Y, (size_t)nprobe * n));
+    CKS(dalloc(ctx, &ctx->g_sc, 6 + 3 * (size_t)nprobe));
+    ctx->g_cap = nprobe;
+  }
+  if (!ctx->g_g) {
+    CKS(dalloc(ctx, &ctx->g_g, (size_t)n));
+    CKS(dalloc(ctx, &ctx->g_v, (size_t)n));
+    CKS(dalloc(ctx, &ctx->g_red, 3 * 256));
+  }
+  return VIF_OK;
+}
+
+// The theta-dependent quantities whose central differences give the gradient, at the perturbed
+// hyperparameters tk with N, Z, the mode b~ and W held fixed (out: 6 + 3 nprobe host values):
+//   [0] sum log D_i  [1] log det C  [2] sum log(W_i + 1/D_i)  [3] log det C_3
+//   [4] b~^T Sigma_dagger^{-1} b~  [5] v^T Sigma_dagger^{-1} b~
+//   [6 + i] u_i^T Sigma_dagger^{-1} y_i  [6 + l + i] y_i^T Sigma_dagger^{-1} y_i  [6 + 2l + i] (B y_i)^T W (B y_i)
+vif_status grad_forms(vif_ctx* ctx, const vif_cov* tk, LapOps& o, int nprobe, double* out) {
+  cudaStream_t s = ctx->stream;
+  const int64_t n = ctx->n;
+  const int m = ctx->m;
+  CKS(lap_setup(ctx, tk, nullptr, &o));
+  CK(lap_pointwise(ctx->y, ctx->l_b, ctx->Dv, nullptr, n, ctx->l_W, ctx->l_v, ctx->l_Ginv, ctx->l_om, ctx->l_rsD,
+                   ctx->l_ll, s));
+  CKS(lap_c3(ctx, o));
+  double* gs = ctx->g_sc;
+  CK(reduce_sum(ctx->logD, n, ctx->red, gs + 0, s));
+  if (m > 0) {
+    CK(lap_log_sum(ctx->G, m, (int64_t)ctx->fpad + 1, 2.0, ctx->l_red, gs + 1, s));
+    CK(lap_log_sum(ctx->l_G3, m, (int64_t)ctx->fpad + 1, 2.0, ctx->l_red, gs + 3, s));
+  } else {
+    CK(cudaMemsetAsync(gs + 1, 0, sizeof(double), s));
+    CK(cudaMemsetAsync(gs + 3, 0, sizeof(double), s));
+  }
+  CK(lap_log_sum(ctx->l_Ginv, n, 1, -1.0, ctx->l_red, gs + 2, s));
+  CK(lap_matvec(o, ctx->l_b, nullptr, ctx->l_sdi, s));
+  CK(lap_grad_forms(n, ctx->l_b, ctx->g_v, ctx->l_sdi, nullptr, nullptr, nullptr, ctx->g_red, gs + 4, gs + 5,
+                    nullptr, s));
+  for (int i = 0; i < nprobe; ++i) {
+    const double* Ui = ctx->g_U + (size_t)i * n;
+    const double* Yi = ctx->g_Y + (size_t)i * n;
+    // lap_matvec leaves D^{-1/2} B y_i in o.t, so that (B y_i)^T W (B y_i) = sum t^2 W D
+    CK(lap_matvec(o, Yi, nullptr, ctx->l_sdi, s));
+    CK(lap_grad_forms(n, Ui, Yi, ctx->l_sdi, o.t, ctx->l_W, ctx->Dv, ctx->g_red, gs + 6 + i, gs + 6 + nprobe + i,
+                      gs + 6 + 2 * nprobe + i, s));
+  }
+  CK(cudaMemcpyAsync(out, gs, (6 + 3 * (size_t)nprobe) * sizeof(double), cudaMemcpyDeviceToHost, s));
+  CK(cudaStreamSynchronize(s));
+  double dummy[1];
+  CKS(read_status(ctx, dummy, 0));
+  return VIF_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+vif_status vif_laplace_nll(vif_ctx* ctx, const vif_cov* theta, const double* y, const vif_laplace_opts* lo,
+                           int32_t nprobe, const double* eps, double slq_tol, int32_t slq_max_iter, double* nll_out,
+                           double* probe_q, double* probe_zpz, vif_laplace_nll_stats* stats) {
+  if (!ctx) return VIF_ERR_ARG;
+  ctx->err[0] = 0;
+  LapOps o;
+  bool newton_ok = true, cg_ok = true;
+  CKS(laplace_nll_core(ctx, theta, y, lo, nprobe, eps, slq_tol, slq_max_iter, nll_out, probe_q, probe_zpz, stats,
+                       &o, nullptr, nullptr, &newton_ok, &cg_ok));
+  return not_converged(ctx, newton_ok, cg_ok);
+}
+
+vif_status vif_laplace_nll_grad(vif_ctx* ctx, const vif_cov* theta, const double* y, const vif_laplace_opts* lo,
+                                int32_t nprobe, const double* eps, double slq_tol, int32_t slq_max_iter,
+                                double* nll_out, double* grad_out, double* probe_terms, double* trace_out,
+                                vif_laplace_grad_stats* stats) {
+  if (!ctx) return VIF_ERR_ARG;
+  ctx->err[0] = 0;
+  if (!theta || !lo || !grad_out) return set_err(ctx, VIF_ERR_ARG, "theta, opts and grad_out are required");
+  if (lo->precond != 0)
+    return set_err(ctx, VIF_ERR_ARG, "the gradient is implemented for the VIFDU preconditioner (precond 0)");
+  if (nprobe < 1) return set_err(ctx, VIF_ERR_ARG, "nprobe >= 1 is required");
+  CKS(check_cov(ctx, theta, ctx->d));
+  const int64_t n = ctx->n;
+  cudaStream_t s = ctx->stream;
+  CKS(lap_alloc(ctx));
+  CKS(grad_buffers(ctx, nprobe));
+  LapOps o;
+  bool newton_ok = true, cg_ok = true;
+  vif_laplace_grad_stats st{};
+  CKS(laplace_nll_core(ctx, theta, y, lo, nprobe, eps, slq_tol, slq_max_iter, nll_out, nullptr, nullptr, &st.nll,
+                       &o, ctx->g_U, ctx->g_Y, &newton_ok, &cg_ok));
+  const auto t0 = std::chrono::steady_clock::now();
+  // dL/db~_j = 1/2 Tr(H^{-1} dW/db_j) by the probe estimate, H = W + Sigma_dagger^{-1} (App. B), and
+  // v = H^{-1} dL/db~ by CG on Eq. pcls1 with the mode's options
+  CK(lap_ste_diag(n, nprobe, ctx->g_U, ctx->g_Y, ctx->l_b, ctx->l_v, s));
+  CK(cudaMemcpyAsync(ctx->g_g, ctx->l_v, n * sizeof(double), cudaMemcpyDeviceToDevice, s));
+  int vit = 0;
+  double vrel = 0.0;
+  bool vcap = false;
+  CKS(lap_pcg(ctx, o, lo->rel_tol, lo->max_pcg, &vit, &vrel, &vcap));
+  cg_ok = cg_ok && !vcap;
+  CK(cudaMemcpyAsync(ctx->g_v, ctx->l_x, n * sizeof(double), cudaMemcpyDeviceToDevice, s));
+  // central differences in each parameter (sigma1^2, lambda_1..), relative step 1e-4
+  const int q = 1 + theta->n_ls;
+  const int nf = 6 + 3 * nprobe;
+  std::vector<double> fp((size_t)q * nf), fm((size_t)q * nf), hk(q);
+  const std::vector<double> ls(theta->lengthscale, theta->lengthscale + theta->n_ls);
+  for (int k = 0; k < q; ++k) {
+    for (int sgn = 0; sgn < 2; ++sgn) {
+      vif_cov tk = *theta;
+      std::vector<double> lk = ls;
+      tk.lengthscale = lk.data();
+      double* par = k == 0 ? &tk.variance : &lk[k - 1];
+      const double h = 1e-4 * std::fabs(*par);
+      hk[k] = h;
+      *par += sgn ? -h : h;
+      CKS(grad_forms(ctx, &tk, o, nprobe, (sgn ? fm : fp).data() + (size_t)k * nf));
+    }
+  }
+  // leave the factors of theta (and the preconditioner pieces at the mode) in the context
+  CKS(lap_setup(ctx, theta, nullptr, &o));
+  CK(lap_pointwise(ctx->y, ctx->l_b, ctx->Dv, nullptr, n, ctx->l_W, ctx->l_v, ctx->l_Ginv, ctx->l_om, ctx->l_rsD,
+                   ctx->l_ll, s));
+  CK(cudaStreamSynchronize(s));
+  // assembly (App. B): dL/dth_k = 1/2 b~^T Delta_k b~ + 1/2 (dlogdet Sigma_dagger + T_k) - v^T Delta_k b~,
+  // T_k the control-variate estimate of Tr(H^{-1} Delta_k) (App. D)
+  for (int k = 0; k < q; ++k) {
+    const double* P = fp.data() + (size_t)k * nf;
+    const double* M = fm.data() + (size_t)k * nf;
+    const double h2 = 2.0 * hk[k];
+    auto d = [&](int j) { return (P[j] - M[j]) / h2; };
+    const double dlogdet_sigma = d(0) + d(1);
+    const double tau = d(2) - d(1) + d(3);   // dlogdet P = Tr(P^{-1} dP/dth_k)
+    double smean = 0.0;
+    for (int i = 0; i < nprobe; ++i) smean += d(6 + i);
+    smean /= nprobe;
+    double num = 0.0, den = 0.0, cvmean = 0.0;
+    for (int i = 0; i < nprobe; ++i) {
+      const double si = d(6 + i);
+      const double ci = d(6 + 2 * nprobe + i) + d(6 + nprobe + i);
+      num += (si - smean) * (ci - tau);
+      den += (ci - tau) * (ci - tau);
+      if (probe_terms) {
+        probe_terms[((size_t)i * q + k) * 2 + 0] = si;
+        probe_terms[((size_t)i * q + k) * 2 + 1] = ci;
+      }
+    }
+    const double copt = den > 0.0 ? num / den : 0.0;
+    for (int i = 0; i < nprobe; ++i) cvmean += d(6 + i) - copt * (d(6 + 2 * nprobe + i) + d(6 + nprobe + i));
+    const double T = cvmean / nprobe + copt * tau;
+    grad_out[k] = 0.5 * d(4) + 0.5 * (dlogdet_sigma + T) - d(5);
+    if (trace_out) {
+      trace_out[(size_t)k * 4 + 0] = smean;
+      trace_out[(size_t)k * 4 + 1] = copt;
+      trace_out[(size_t)k * 4 + 2] = tau;
+      trace_out[(size_t)k * 4 + 3] = T;
+    }
+  }
+  st.pcg_iters_v = vit;
+  st.reserved = 0;
+  st.ms_grad = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+  if (stats) *stats = st;
+  return not_converged(ctx, newton_ok, cg_ok);
 }
 
 vif_status vif_laplace_predict(vif_ctx* ctx, const vif_cov* theta, const double* y, const vif_laplace_opts* lo,

@@ -236,6 +236,12 @@ cudaError_t lap_axpy(int64_t n, const double* scal, const double* x, const doubl
                      cudaStream_t s);
 cudaError_t lap_alpha(double* sc, cudaStream_t s);
 cudaError_t lap_beta(double* sc, cudaStream_t s);
+// gradient of the VIF-Laplace likelihood (Sec. 4.1, App. B, App. D)
+cudaError_t lap_ste_diag(int64_t n, int l, const double* U, const double* Y, const double* b, double* g,
+                         cudaStream_t s);
+cudaError_t lap_grad_forms(int64_t n, const double* a, const double* c, const double* x, const double* t,
+                           const double* w, const double* d, double* partial, double* out0, double* out1,
+                           double* out2, cudaStream_t s);
 
 // vif_mlp.cu
 size_t mlp_bytes();

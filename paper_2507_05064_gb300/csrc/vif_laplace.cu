@@ -742,4 +742,90 @@ cudaError_t lap_beta(double* sc, cudaStream_t s) {
   return cudaGetLastError();
 }
 
+// ---------------------------------------------------------------------------
+// Gradient of the VIF-Laplace likelihood by stochastic trace estimation (Sec. 4.1,
+// App. B, App. D): the probe estimate of dL/db~ and the bilinear forms whose central
+// differences in theta give the traces.
+// ---------------------------------------------------------------------------
+
+// g_i = 1/2 dW_ii/db_i (1/l) sum_j U[j][i] Y[j][i]   (U, Y: l x n, probe-major), the Bernoulli-logit
+// dW/db = p (1 - p)(1 - 2p), p = sigmoid(b_i)
+__global__ void ste_diag_kernel(int64_t n, int l, const double* __restrict__ U, const double* __restrict__ Y,
+                                const double* __restrict__ b, double* g) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  double s0 = 0.0, s1 = 0.0;
+  int j = 0;
+  for (; j + 1 < l; j += 2) {
+    s0 = fma(U[(size_t)j * n + i], Y[(size_t)j * n + i], s0);
+    s1 = fma(U[(size_t)(j + 1) * n + i], Y[(size_t)(j + 1) * n + i], s1);
+  }
+  if (j < l) s0 = fma(U[(size_t)j * n + i], Y[(size_t)j * n + i], s0);
+  const double p = 1.0 / (1.0 + exp(-b[i]));
+  g[i] = 0.5 * p * (1.0 - p) * (1.0 - 2.0 * p) * (s0 + s1) / l;
+}
+
+// per block: sum a_i x_i, sum c_i x_i and (t != NULL) sum t_i^2 w_i d_i, into partial[k * 256 + block]
+__global__ __launch_bounds__(256) void forms_stage1(const double* __restrict__ a, const double* __restrict__ c,
+                                                    const double* __restrict__ x, const double* __restrict__ t,
+                                                    const double* __restrict__ w, const double* __restrict__ d,
+                                                    int64_t n, double* partial) {
+  __shared__ double sh[3][256];
+  double v0 = 0.0, v1 = 0.0, v2 = 0.0;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    const double xi = x[i];
+    v0 = fma(a[i], xi, v0);
+    v1 = fma(c[i], xi, v1);
+    if (t) {
+      const double ti = t[i];
+      v2 = fma(ti * ti, w[i] * d[i], v2);
+    }
+  }
+  sh[0][threadIdx.x] = v0;
+  sh[1][threadIdx.x] = v1;
+  sh[2][threadIdx.x] = v2;
+  __syncthreads();
+  for (int h = 128; h > 0; h >>= 1) {
+    if (threadIdx.x < h) {
+      sh[0][threadIdx.x] += sh[0][threadIdx.x + h];
+      sh[1][threadIdx.x] += sh[1][threadIdx.x + h];
+      sh[2][threadIdx.x] += sh[2][threadIdx.x + h];
+    }
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) {
+    partial[blockIdx.x] = sh[0][0];
+    partial[256 + blockIdx.x] = sh[1][0];
+    partial[512 + blockIdx.x] = sh[2][0];
+  }
+}
+
+// block k sums partial[k * 256 .. k * 256 + 255] into *out_k (out_k may be NULL)
+__global__ void forms_stage2(const double* partial, double* out0, double* out1, double* out2) {
+  double* out = blockIdx.x == 0 ? out0 : (blockIdx.x == 1 ? out1 : out2);
+  if (!out) return;
+  __shared__ double sh[256];
+  sh[threadIdx.x] = partial[blockIdx.x * 256 + threadIdx.x];
+  __syncthreads();
+  for (int h = 128; h > 0; h >>= 1) {
+    if (threadIdx.x < h) sh[threadIdx.x] += sh[threadIdx.x + h];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) *out = sh[0];
+}
+
+cudaError_t lap_ste_diag(int64_t n, int l, const double* U, const double* Y, const double* b, double* g,
+                         cudaStream_t s) {
+  ste_diag_kernel<<<blocks(n, 256), 256, 0, s>>>(n, l, U, Y, b, g);
+  return cudaGetLastError();
+}
+
+cudaError_t lap_grad_forms(int64_t n, const double* a, const double* c, const double* x, const double* t,
+                           const double* w, const double* d, double* partial, double* out0, double* out1,
+                           double* out2, cudaStream_t s) {
+  forms_stage1<<<256, 256, 0, s>>>(a, c, x, t, w, d, n, partial);
+  forms_stage2<<<3, 256, 0, s>>>(partial, out0, out1, out2);
+  return cudaGetLastError();
+}
+
 }  // namespace vif

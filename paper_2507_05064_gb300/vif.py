@@ -23,7 +23,8 @@ PRECOND_VIFDU, PRECOND_VIFDU_LEARNED, PRECOND_FITC = 0, 1, 2
 GAUSSIAN, BERNOULLI_LOGIT = 0, 1
 
 # every symbol include/vif.h declares
-EXPORTS = ["vif_build", "vif_nll", "vif_predict", "vif_laplace_mode", "vif_laplace_nll", "vif_laplace_predict",
+EXPORTS = ["vif_build", "vif_nll", "vif_predict", "vif_laplace_mode", "vif_laplace_nll", "vif_laplace_nll_grad",
+           "vif_laplace_predict",
            "vif_tridiag_log_quadrature", "vif_batch_create", "vif_batch_run",
            "vif_batch_info", "vif_batch_destroy", "vif_mlp_bytes", "vif_mlp_init", "vif_mlp_set_params",
            "vif_mlp_get_params", "vif_mlp_forward", "vif_mlp_backward", "vif_mlp_features", "vif_mlp_train", "vif_set_neighbors", "vif_get_neighbors",
@@ -53,6 +54,11 @@ class LaplaceNllStats(C.Structure):
                 ("logdet", C.c_double), ("logdet_exact_norm", C.c_double), ("newton_iters", C.c_int32),
                 ("pcg_iters_mode", C.c_int32), ("pcg_iters_slq", C.c_int32), ("reserved", C.c_int32),
                 ("ms_mode", C.c_double), ("ms_slq", C.c_double)]
+
+
+class LaplaceGradStats(C.Structure):
+    _fields_ = [("nll", LaplaceNllStats), ("pcg_iters_v", C.c_int32), ("reserved", C.c_int32),
+                ("ms_grad", C.c_double)]
 
 
 class LaplaceStats(C.Structure):
@@ -101,6 +107,8 @@ def lib() -> C.CDLL:
                                        C.POINTER(LaplaceStats)]
         L.vif_laplace_nll.argtypes = [vp, C.POINTER(VifCov), vp, C.POINTER(LaplaceOpts), i32, vp, C.c_double,
                                       i32, dp, vp, vp, C.POINTER(LaplaceNllStats)]
+        L.vif_laplace_nll_grad.argtypes = [vp, C.POINTER(VifCov), vp, C.POINTER(LaplaceOpts), i32, vp, C.c_double,
+                                           i32, dp, vp, vp, vp, C.POINTER(LaplaceGradStats)]
         L.vif_tridiag_log_quadrature.argtypes = [vp, vp, i32, dp]
         L.vif_laplace_predict.argtypes = [vp, C.POINTER(VifCov), vp, C.POINTER(LaplaceOpts), vp, i64, i32, vp,
                                           C.c_double, i32, vp, vp, C.POINTER(LaplaceStats)]
@@ -349,6 +357,31 @@ class Context:
         stats = {k: getattr(st, k) for k, _ in LaplaceNllStats._fields_}
         stats["q"], stats["zPz"], stats["status"] = q, zpz, rc
         return out.value, stats
+
+    def laplace_nll_grad(self, theta, y, eps, slq_tol=1e-2, slq_max_iter=1000, rel_tol=1e-6, max_pcg=1000,
+                         max_newton=50, allow_not_converged=False):
+        """VIF-Laplace NLL (as laplace_nll, VIFDU) and its gradient in (sigma1^2, lambda...) by
+        stochastic trace estimation with the preconditioner control variate (Sec. 4.1, App. B, App. D).
+        Returns (nll, grad, stats dict with 'probe_terms' (nprobe, q, 2) = (s_ik, c_ik) and 'trace'
+        (q, 4) = (plain mean, c_k, tau_k, T_k))."""
+        cv, ls = make_cov(theta)
+        opts = LaplaceOpts(float(rel_tol), int(max_pcg), int(max_newton), 0, 0, None)
+        e = _f64(eps)
+        nprobe = int(e.shape[0])
+        q = 1 + int(cv.n_ls)
+        grad = np.zeros(q)
+        terms = np.zeros((nprobe, q, 2))
+        trace = np.zeros((q, 4))
+        out = C.c_double()
+        st = LaplaceGradStats()
+        rc = lib().vif_laplace_nll_grad(self.h, C.byref(cv), _ptr(_f64(y)), C.byref(opts), nprobe, _ptr(e),
+                                        float(slq_tol), int(slq_max_iter), C.byref(out), _ptr(grad), _ptr(terms),
+                                        _ptr(trace), C.byref(st))
+        if not (rc == VIF_OK or (allow_not_converged and rc == VIF_ERR_NOT_CONVERGED)):
+            self._check(rc)
+        stats = {k: getattr(st.nll, k) for k, _ in LaplaceNllStats._fields_}
+        stats.update(pcg_iters_v=st.pcg_iters_v, ms_grad=st.ms_grad, probe_terms=terms, trace=trace, status=rc)
+        return out.value, grad, stats
 
     def laplace_predict(self, theta, y, Xp, eps=None, cg_tol=1e-6, cg_max_iter=1000, rel_tol=1e-6,
                         max_pcg=1000, max_newton=50, precond=0, allow_not_converged=False):

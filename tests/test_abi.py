@@ -62,6 +62,21 @@ def test_laplace_nll_stats_layout_matches_header():
     import ctypes as C
     assert C.sizeof(V.LaplaceNllStats) == 8 * 8 + 4 * 4 + 2 * 8
     assert V.LaplaceNllStats.newton_iters.offset == 64 and V.LaplaceNllStats.ms_mode.offset == 80
+    assert C.sizeof(V.LaplaceGradStats) == C.sizeof(V.LaplaceNllStats) + 2 * 4 + 8
+    assert V.LaplaceGradStats.pcg_iters_v.offset == C.sizeof(V.LaplaceNllStats)
+
+
+def test_laplace_grad_rejects_non_vifdu_and_missing_outputs_without_a_gpu():
+    """Argument checks of vif_laplace_nll_grad run before any device work."""
+    import ctypes as C
+    import numpy as np
+    lib = V.lib()
+    ls = np.array([0.2])
+    cv = V.VifCov(1, 1.0, ls.ctypes.data_as(C.POINTER(C.c_double)), 1, 0.0)
+    out = C.c_double()
+    g = np.zeros(2)
+    assert lib.vif_laplace_nll_grad(None, C.byref(cv), None, None, 1, None, 1e-2, 10, C.byref(out), V._ptr(g),
+                                    None, None, None) == V.VIF_ERR_ARG
 
 
 def _tridiag_reference(d, e):

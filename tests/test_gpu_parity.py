@@ -344,6 +344,56 @@ def test_vifla_nll_with_slq_matches_oracle_probe_by_probe():
     ctx.close()
 
 
+@pytest.mark.parametrize("ard", [False, True])
+def test_vifla_gradient_by_ste_matches_oracle_probe_by_probe(ard):
+    """Sec. 4.1, App. B, App. D: the SLQ probes' CG solutions reused, the same central differences
+    of the bilinear forms and log-determinants, the same control variate: s_ik, c_ik, the traces,
+    c_k, tau_k and the assembled gradient agree with the oracle (isotropic and ARD ranges)."""
+    P = bern(1200, 20, 8, 43)
+    if ard:
+        P.theta.lengthscale = np.array([0.08, 0.13])
+    N = O.causal_neighbors(P.X, P.Z, P.theta, 8)
+    vif = O.VIF(P.X, P.Z, P.theta, N)
+    b_dense, _, _ = O.laplace_mode(vif, P.y, dense=True, psi_tol=1e-14)
+    ctx = V.Context(P.X, P.Z, 8, P.theta, likelihood=V.BERNOULLI_LOGIT, neighbor_search=False)
+    ctx.set_neighbors(N.astype(np.int32))
+    eps = synth.slq_normals(5, vif.m, vif.n, seed=7)
+    nll, grad, st = ctx.laplace_nll_grad(P.theta, P.y, eps, slq_tol=1e-10, rel_tol=1e-10)
+    ref = O.vifla_grad_ste(P.X, P.Z, P.theta, N, P.y, b_dense, eps, 1e-10, 1e-10)
+    q = 1 + np.atleast_1d(P.theta.lengthscale).size
+    assert grad.shape == (q,)
+    terms = st["probe_terms"]
+    for k in range(q):
+        sc = np.abs(ref["s"][:, k]).max()
+        cc = np.abs(ref["c"][:, k]).max()
+        np.testing.assert_allclose(terms[:, k, 0], ref["s"][:, k], rtol=1e-6, atol=1e-7 * sc)
+        np.testing.assert_allclose(terms[:, k, 1], ref["c"][:, k], rtol=1e-6, atol=1e-7 * cc)
+    np.testing.assert_allclose(st["trace"][:, 2], ref["tau"], rtol=1e-6)
+    np.testing.assert_allclose(st["trace"][:, 0], ref["trace_plain"], rtol=1e-6, atol=1e-7 * np.abs(ref["s"]).max())
+    np.testing.assert_allclose(st["trace"][:, 1], ref["c_opt"], rtol=1e-5, atol=1e-6)
+    np.testing.assert_allclose(st["trace"][:, 3], ref["trace"], rtol=1e-6, atol=1e-7 * np.abs(ref["s"]).max())
+    np.testing.assert_allclose(grad, ref["grad"], rtol=1e-5, atol=1e-6 * np.abs(ref["grad"]).max())
+    # the factors of theta are back in the context: the likelihood alone is unchanged
+    nll2, _ = ctx.laplace_nll(P.theta, P.y, eps, slq_tol=1e-10, rel_tol=1e-10)
+    assert abs(nll2 - nll) <= 1e-9 * abs(nll)
+    ctx.close()
+
+
+def test_vifla_gradient_rejects_fitc_and_learned_preconditioners():
+    P, vif, b_dense, ctx = _vifla_case(300, 10, 5, 44)
+    eps = synth.slq_normals(2, vif.m, vif.n, seed=8)
+    cv, ls = V.make_cov(P.theta)
+    import ctypes as C
+    for pre in (1, 2):
+        opts = V.LaplaceOpts(1e-6, 100, 20, pre, 0, None)
+        g = np.zeros(2)
+        out = C.c_double()
+        rc = V.lib().vif_laplace_nll_grad(ctx.h, C.byref(cv), V._ptr(P.y), C.byref(opts), 2, V._ptr(eps), 1e-3,
+                                          100, C.byref(out), V._ptr(g), None, None, None)
+        assert rc == V.VIF_ERR_ARG
+    ctx.close()
+
+
 def test_vifla_nll_without_neighbours_is_exact():
     """m_v = 0: P = W + Sigma_dagger^{-1} exactly, every quadrature vanishes and the NLL is the
     dense VIF-Laplace likelihood."""
