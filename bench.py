@@ -314,6 +314,20 @@ def laplace_block(args, stream):
                   "ms_slq": sl["ms_slq"], "ms_per_probe": sl["ms_slq"] / nprobe, "ms_mode": sl["ms_mode"],
                   "wall_s": wall_slq,
                   "q_std_over_mean": float(np.std(sl["q"]) / max(abs(np.mean(sl["q"])), 1e-300))}
+    # its gradient in (sigma1^2, lambda) by stochastic trace estimation with the same 50 probes and the
+    # preconditioner control variate (Sec. 4.1, App. B, App. D); standard errors of the plain and the
+    # control-variate trace estimates from the per-probe terms
+    t0 = time.perf_counter()
+    nll_g, grad, sg = ctx.laplace_nll_grad(P.theta, y, eps, slq_tol=slq_tol, rel_tol=1e-6)
+    wall_g = time.perf_counter() - t0
+    pt, tr = sg["probe_terms"], sg["trace"]
+    se_plain = pt[:, :, 0].std(axis=0, ddof=1) / np.sqrt(nprobe)
+    se_cv = (pt[:, :, 0] - tr[None, :, 1] * pt[:, :, 1]).std(axis=0, ddof=1) / np.sqrt(nprobe)
+    out["grad"] = {"params": ["sigma1^2", "lambda"], "grad": grad.tolist(), "nll": nll_g, "wall_s": wall_g,
+                   "ms_after_nll": sg["ms_grad"], "pcg_iters_v": sg["pcg_iters_v"],
+                   "trace_plain": tr[:, 0].tolist(), "c_opt": tr[:, 1].tolist(), "tau": tr[:, 2].tolist(),
+                   "trace_cv": tr[:, 3].tolist(), "se_plain": se_plain.tolist(), "se_cv": se_cv.tolist(),
+                   "wall_ratio_nll_grad_over_nll": wall_g / wall_slq}
     # the same with the FITC preconditioner (App. E.2, systems in the form of Eq. pcls2, Eq. slq_v2)
     ctx.laplace_mode(P.theta, y, rel_tol=1e-6, precond=V.PRECOND_FITC)          # warm-up
     t0 = time.perf_counter()
