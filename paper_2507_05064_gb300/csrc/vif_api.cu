@@ -63,6 +63,12 @@ struct vif_ctx {
   // the bilinear forms of one perturbed theta (6 + 3 g_cap) and a three-way reduction scratch
   double *g_U = nullptr, *g_Y = nullptr, *g_g = nullptr, *g_v = nullptr, *g_sc = nullptr, *g_red = nullptr;
   int64_t g_cap = 0;
+  // block CG over up to mr_cap probes: n x L vectors, m x L and reduction scratch, per-column scalars
+  double *mr_v = nullptr, *mr_x = nullptr, *mr_r = nullptr, *mr_z = nullptr, *mr_p = nullptr, *mr_Ap = nullptr,
+         *mr_t = nullptr, *mr_t2 = nullptr, *mr_x1 = nullptr, *mr_sm = nullptr, *mr_cm = nullptr, *mr_tm = nullptr,
+         *mr_part = nullptr, *mr_dpart = nullptr, *mr_sc = nullptr;
+  int* mr_active = nullptr;
+  int mr_cap = 0;
   double *l_b = nullptr, *l_W = nullptr, *l_v = nullptr, *l_Ginv = nullptr, *l_om = nullptr, *l_rsD = nullptr,
          *l_ll = nullptr, *l_x = nullptr, *l_r = nullptr, *l_z = nullptr, *l_p = nullptr, *l_Ap = nullptr,
          *l_t = nullptr, *l_t2 = nullptr, *l_x1 = nullptr, *l_sdi = nullptr, *l_sm = nullptr, *l_cm = nullptr,
@@ -288,6 +294,8 @@ void free_ctx(vif_ctx* c) {
                    c->l_sdi,  c->l_sm,  c->l_cm,   c->l_tm,   c->l_part, c->l_LinvC, c->l_G3,  c->l_LinvC3,
                    c->l_sc,   c->l_red, c->l_corr, c->sched_fwd, c->sched_rev, c->ch_coef, c->slq_eps, c->l_Apad, c->l_anorm2, c->l_dvinv, c->l_pacc, c->l_counter, c->l_abort, c->m_feat,
                    c->g_U,    c->g_Y,   c->g_g,    c->g_v,    c->g_sc,   c->g_red,
+                   c->mr_v,   c->mr_x,  c->mr_r,   c->mr_z,   c->mr_p,   c->mr_Ap,  c->mr_t,   c->mr_t2,
+                   c->mr_x1,  c->mr_sm, c->mr_cm,  c->mr_tm,  c->mr_part, c->mr_dpart, c->mr_sc, c->mr_active,
                    c->m_gc,   c->m_part, c->m_grad};
   for (void* b : pbufs)
     if (b) cudaFree(b);
@@ -1048,6 +1056,126 @@ vif_status lap_pcg(vif_ctx* ctx, const LapOps& o, double tol, int max_it, int* i
   return VIF_OK;
 }
 
+// Block-CG buffers for L <= LAP_MR_MAXL columns (grown on demand) and their bundle.
+vif_status mr_buffers(vif_ctx* ctx, int L, LapMulti* w) {
+  const int64_t n = ctx->n;
+  const size_t fp = (size_t)std::max(ctx->fpad, 1);
+  if (L > ctx->mr_cap) {
+    double** vecs[] = {&ctx->mr_v, &ctx->mr_x, &ctx->mr_r, &ctx->mr_z, &ctx->mr_p, &ctx->mr_Ap, &ctx->mr_t,
+                       &ctx->mr_t2, &ctx->mr_x1};
+    double** small[] = {&ctx->mr_sm, &ctx->mr_cm, &ctx->mr_tm, &ctx->mr_part, &ctx->mr_dpart};
+    for (double** b : vecs) {
+      if (*b) cudaFree(*b);
+      *b = nullptr;
+    }
+    for (double** b : small) {
+      if (*b) cudaFree(*b);
+      *b = nullptr;
+    }
+    ctx->mr_cap = 0;
+    for (double** b : vecs) CKS(dalloc(ctx, b, (size_t)n * L));
+    CKS(dalloc(ctx, &ctx->mr_sm, fp * L));
+    CKS(dalloc(ctx, &ctx->mr_cm, fp * L));
+    CKS(dalloc(ctx, &ctx->mr_tm, fp * L));
+    CKS(dalloc(ctx, &ctx->mr_part, (size_t)LAP_MR_FT_BLOCKS * fp * L));
+    CKS(dalloc(ctx, &ctx->mr_dpart, (size_t)LAP_MR_DOT_BLOCKS * L));
+    if (!ctx->mr_sc) {
+      CKS(dalloc(ctx, &ctx->mr_sc, 7 * (size_t)LAP_MR_MAXL));
+      CKS(dalloc(ctx, &ctx->mr_active, (size_t)LAP_MR_MAXL));
+    }
+    ctx->mr_cap = L;
+  }
+  w->L = L;
+  w->t = ctx->mr_t;
+  w->t2 = ctx->mr_t2;
+  w->x1 = ctx->mr_x1;
+  w->sm = ctx->mr_sm;
+  w->cm = ctx->mr_cm;
+  w->tmpm = ctx->mr_tm;
+  w->partial = ctx->mr_part;
+  w->dpart = ctx->mr_dpart;
+  return VIF_OK;
+}
+
+// Preconditioned CG from X = 0 on (W + Sigma_dagger^{-1}) X = V (Eq. pcls1, VIFDU) for the L columns
+// of mr_v at once: each column takes the steps of lap_pcg with its own step lengths and stopping
+// test, and a finished column is frozen (alpha = beta = 0) while the others go on.  Per column:
+// iterations, final relative residual, whether the cap was hit, the Lanczos coefficients alpha_j,
+// beta_j and v^T P^{-1} v (App. D); with z0_cols (device, L x n probe-major) also P^{-1} v.
+vif_status lap_pcg_multi(vif_ctx* ctx, const LapOps& o, const LapMulti& w, double tol, int max_it,
+                         std::vector<int>& iters, std::vector<double>& rel, std::vector<char>& capped,
+                         std::vector<std::vector<double>>& alphas, std::vector<std::vector<double>>& betas,
+                         std::vector<double>& rz0, double* z0_cols) {
+  cudaStream_t s = ctx->stream;
+  const int64_t n = ctx->n;
+  const int L = w.L;
+  const size_t bytes = (size_t)n * L * sizeof(double);
+  double* sc = ctx->mr_sc;   // per column: rz, pAp, alpha, rr, rz_new, beta, v^T v
+  double *rz = sc, *pAp = sc + L, *alpha = sc + 2 * L, *rr = sc + 3 * L, *rznew = sc + 4 * L, *beta = sc + 5 * L,
+         *vv = sc + 6 * L;
+  double* hs = ctx->h_pin + 64;   // 7 L <= 448 doubles of pinned staging
+  CK(cudaMemsetAsync(ctx->mr_x, 0, bytes, s));
+  CK(cudaMemsetAsync(sc, 0, 7 * (size_t)L * sizeof(double), s));
+  CK(cudaMemcpyAsync(ctx->mr_r, ctx->mr_v, bytes, cudaMemcpyDeviceToDevice, s));
+  CK(lap_mr_dot(w, n, ctx->mr_v, ctx->mr_v, vv, s));
+  CK(lap_mr_precond(o, w, ctx->mr_r, ctx->mr_z, s));
+  CK(cudaMemcpyAsync(ctx->mr_p, ctx->mr_z, bytes, cudaMemcpyDeviceToDevice, s));
+  if (z0_cols)
+    for (int j = 0; j < L; ++j) CK(lap_mr_column(n, L, j, ctx->mr_z, z0_cols + (size_t)j * n, true, s));
+  CK(lap_mr_dot(w, n, ctx->mr_r, ctx->mr_z, rz, s));
+  CK(cudaMemcpyAsync(hs, sc, 7 * (size_t)L * sizeof(double), cudaMemcpyDeviceToHost, s));
+  CK(cudaStreamSynchronize(s));
+  std::vector<double> vnorm(L);
+  std::vector<int> act(L);
+  int nact = 0;
+  for (int j = 0; j < L; ++j) {
+    vnorm[j] = std::sqrt(hs[6 * L + j]);
+    rz0[j] = hs[j];
+    act[j] = vnorm[j] > 0.0 ? 1 : 0;
+    nact += act[j];
+    iters[j] = 0;
+    rel[j] = 0.0;
+    capped[j] = 0;
+    alphas[j].clear();
+    betas[j].clear();
+  }
+  CK(cudaMemcpyAsync(ctx->mr_active, act.data(), L * sizeof(int), cudaMemcpyHostToDevice, s));
+  for (int it = 1; nact > 0 && it <= max_it; ++it) {
+    CK(lap_mr_matvec(o, w, ctx->mr_p, ctx->mr_Ap, s));
+    CK(lap_mr_dot(w, n, ctx->mr_p, ctx->mr_Ap, pAp, s));
+    CK(lap_mr_alpha(w, ctx->mr_active, rz, pAp, alpha, s));
+    CK(lap_mr_update_xr(w, n, alpha, ctx->mr_p, ctx->mr_Ap, ctx->mr_x, ctx->mr_r, s));
+    CK(lap_mr_dot(w, n, ctx->mr_r, ctx->mr_r, rr, s));
+    CK(cudaMemcpyAsync(hs, sc, 7 * (size_t)L * sizeof(double), cudaMemcpyDeviceToHost, s));
+    CK(cudaMemcpyAsync(ctx->h_pin + 9, ctx->status, 4 * sizeof(int), cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    // alpha of this step; beta of the previous one (set at its end)
+    for (int j = 0; j < L; ++j) {
+      if (!act[j]) continue;
+      alphas[j].push_back(hs[2 * L + j]);
+      if (it >= 2) betas[j].push_back(hs[5 * L + j]);
+      rel[j] = std::sqrt(hs[3 * L + j]) / vnorm[j];
+      iters[j] = it;
+      if (rel[j] <= tol) {
+        act[j] = 0;
+        --nact;
+      } else if (it == max_it) {
+        capped[j] = 1;
+      }
+    }
+    if (reinterpret_cast<const int*>(ctx->h_pin + 9)[0] != ST_OK) break;
+    if (nact == 0 || it == max_it) break;
+    CK(cudaMemcpyAsync(ctx->mr_active, act.data(), L * sizeof(int), cudaMemcpyHostToDevice, s));
+    CK(lap_mr_precond(o, w, ctx->mr_r, ctx->mr_z, s));
+    CK(lap_mr_dot(w, n, ctx->mr_r, ctx->mr_z, rznew, s));
+    CK(lap_mr_beta(w, ctx->mr_active, rz, rznew, beta, s));
+    CK(lap_mr_update_p(w, n, beta, ctx->mr_z, ctx->mr_p, s));
+  }
+  double dummy[1];
+  CKS(read_status(ctx, dummy, 0));
+  return VIF_OK;
+}
+
 // e_1^T log(T) e_1 for the symmetric tridiagonal T with diagonal d[0..k-1] and
 // off-diagonal e[0..k-2]: the Gauss quadrature of log whose nodes are the eigenvalues
 // of T and whose weights are the squared first components of its eigenvectors (App. D).
@@ -1317,38 +1445,32 @@ vif_status laplace_nll_core(vif_ctx* ctx, const vif_cov* theta, const double* y,
   double qsum = 0.0, wsum = 0.0;
   int slq_iters = 0;
   bool slq_capped = false;
-  for (int i = 0; i < nprobe; ++i) {
+  // probe i into l_v:
+  //   VIFDU: z = B^T W'^{1/2} eps3 + Sigma_dagger^{-1} (B^{-1} D^{1/2} eps2 + A^T eps1)   (Sec. 4.3)
+  //   FITC:  z = D_V^{1/2} eps2 + Sigma_mn^T L_m^{-T} eps1   (App. E.2)
+  auto draw = [&](int i) -> vif_status {
     CKS(upload(ctx, ctx->slq_eps, eps + (size_t)i * per, per * sizeof(double)));
     const double* e1 = ctx->slq_eps;
     const double* e2 = ctx->slq_eps + m;
     const double* e3 = ctx->slq_eps + m + n;
     if (fitc) {
-      // z = D_V^{1/2} eps2 + Sigma_mn^T L_m^{-T} eps1   (App. E.2)
       CK(lap_fitc_probe(o, e1, e2, ctx->l_v, s));
-    } else {
-      // z = B^T W'^{1/2} eps3 + Sigma_dagger^{-1} (B^{-1} D^{1/2} eps2 + A^T eps1)   (Sec. 4.3)
-      CK(lap_probe_prep(n, ctx->Dv, ctx->l_W, learned ? ctx->l_corr : nullptr, e2, e3, ctx->l_r, ctx->l_z, s));
-      CK(lap_solve_B(o, ctx->l_r, ctx->l_p, s));
-      if (m > 0) {
-        CK(lap_rows_dot_add(A64, ctx->mpad, m, n, e1, ctx->l_p, ctx->l_Ap, s));
-      } else {
-        CK(cudaMemcpyAsync(ctx->l_Ap, ctx->l_p, n * sizeof(double), cudaMemcpyDeviceToDevice, s));
-      }
-      CK(lap_matvec(o, ctx->l_Ap, nullptr, ctx->l_x, s));
-      CK(lap_apply_Bt(o, ctx->l_z, ctx->l_r, s));
-      CK(lap_vec_add(n, ctx->l_x, ctx->l_r, ctx->l_v, s));
+      return VIF_OK;
     }
-    // PCG on the system of Eq. pcls1 (VIFDU) or Eq. pcls2 (FITC) with right-hand side z,
-    // its coefficients giving T_i (App. D)
-    std::vector<double> al, be;
-    double zpz = 0.0, rel = 0.0;
-    int it = 0;
-    bool cp = false;
-    CKS(lap_pcg(ctx, o, slq_tol, slq_max_iter, &it, &rel, &cp, &al, &be, &zpz,
-                keepY ? keepY + (size_t)i * n : nullptr));
-    if (keepU) CK(cudaMemcpyAsync(keepU + (size_t)i * n, ctx->l_x, n * sizeof(double), cudaMemcpyDeviceToDevice, s));
-    slq_iters += it;
-    slq_capped = slq_capped || cp;
+    CK(lap_probe_prep(n, ctx->Dv, ctx->l_W, learned ? ctx->l_corr : nullptr, e2, e3, ctx->l_r, ctx->l_z, s));
+    CK(lap_solve_B(o, ctx->l_r, ctx->l_p, s));
+    if (m > 0) {
+      CK(lap_rows_dot_add(A64, ctx->mpad, m, n, e1, ctx->l_p, ctx->l_Ap, s));
+    } else {
+      CK(cudaMemcpyAsync(ctx->l_Ap, ctx->l_p, n * sizeof(double), cudaMemcpyDeviceToDevice, s));
+    }
+    CK(lap_matvec(o, ctx->l_Ap, nullptr, ctx->l_x, s));
+    CK(lap_apply_Bt(o, ctx->l_z, ctx->l_r, s));
+    CK(lap_vec_add(n, ctx->l_x, ctx->l_r, ctx->l_v, s));
+    return VIF_OK;
+  };
+  // T_i from the CG coefficients of probe i (App. D) and its Gauss quadrature
+  auto quadrature = [&](int i, const std::vector<double>& al, const std::vector<double>& be, double zpz) -> vif_status {
     std::vector<double> d(al.size()), od(al.size() > 0 ? al.size() - 1 : 0);
     for (size_t j = 0; j < al.size(); ++j) {
       d[j] = 1.0 / al[j] + (j > 0 ? be[j - 1] / al[j - 1] : 0.0);
@@ -1361,6 +1483,49 @@ vif_status laplace_nll_core(vif_ctx* ctx, const vif_cov* theta, const double* y,
     if (probe_zpz) probe_zpz[i] = zpz;
     qsum += q;
     wsum += zpz * q;
+    return VIF_OK;
+  };
+  if (!fitc) {
+    // VIFDU (Eq. pcls1): the probes' CGs run side by side in blocks of up to LAP_MR_MAXL columns,
+    // sharing every operator application
+    for (int b0 = 0; b0 < nprobe; b0 += LAP_MR_MAXL) {
+      const int L = std::min(LAP_MR_MAXL, nprobe - b0);
+      LapMulti w;
+      CKS(mr_buffers(ctx, L, &w));
+      for (int j = 0; j < L; ++j) {
+        CKS(draw(b0 + j));
+        CK(lap_mr_column(n, L, j, ctx->mr_v, ctx->l_v, false, s));
+      }
+      std::vector<int> its(L);
+      std::vector<double> rels(L), rz0(L);
+      std::vector<char> caps(L);
+      std::vector<std::vector<double>> al(L), be(L);
+      CKS(lap_pcg_multi(ctx, o, w, slq_tol, slq_max_iter, its, rels, caps, al, be, rz0,
+                        keepY ? keepY + (size_t)b0 * n : nullptr));
+      if (keepU)
+        for (int j = 0; j < L; ++j) CK(lap_mr_column(n, L, j, ctx->mr_x, keepU + (size_t)(b0 + j) * n, true, s));
+      for (int j = 0; j < L; ++j) {
+        slq_iters += its[j];
+        slq_capped = slq_capped || caps[j];
+        CKS(quadrature(b0 + j, al[j], be[j], rz0[j]));
+      }
+    }
+  } else {
+    // FITC (Eq. pcls2): one probe at a time
+    for (int i = 0; i < nprobe; ++i) {
+      CKS(draw(i));
+      std::vector<double> al, be;
+      double zpz = 0.0, rel = 0.0;
+      int it = 0;
+      bool cp = false;
+      CKS(lap_pcg(ctx, o, slq_tol, slq_max_iter, &it, &rel, &cp, &al, &be, &zpz,
+                  keepY ? keepY + (size_t)i * n : nullptr));
+      if (keepU)
+        CK(cudaMemcpyAsync(keepU + (size_t)i * n, ctx->l_x, n * sizeof(double), cudaMemcpyDeviceToDevice, s));
+      slq_iters += it;
+      slq_capped = slq_capped || cp;
+      CKS(quadrature(i, al, be, zpz));
+    }
   }
   const double ms_slq =
       std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();

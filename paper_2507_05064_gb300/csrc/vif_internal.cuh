@@ -236,6 +236,29 @@ cudaError_t lap_axpy(int64_t n, const double* scal, const double* x, const doubl
                      cudaStream_t s);
 cudaError_t lap_alpha(double* sc, cudaStream_t s);
 cudaError_t lap_beta(double* sc, cudaStream_t s);
+// many right-hand sides (the SLQ probes, Sec. 4.1): n x L row-major block vectors, L <= LAP_MR_MAXL
+constexpr int LAP_MR_MAXL = 64;
+constexpr int LAP_MR_FT_BLOCKS = 304;   // row slices of the block F^T T product
+constexpr int LAP_MR_DOT_BLOCKS = 256;
+struct LapMulti {
+  int L;
+  double *t, *t2, *x1;        // n x L scratch
+  double *sm, *cm, *tmpm;     // m x L scratch
+  double* partial;            // LAP_MR_FT_BLOCKS x fpad x L
+  double* dpart;              // LAP_MR_DOT_BLOCKS x L
+};
+cudaError_t lap_mr_matvec(const LapOps& o, const LapMulti& w, const double* X, double* out, cudaStream_t s);
+cudaError_t lap_mr_precond(const LapOps& o, const LapMulti& w, const double* R, double* out, cudaStream_t s);
+cudaError_t lap_mr_dot(const LapMulti& w, int64_t n, const double* a, const double* b, double* out, cudaStream_t s);
+cudaError_t lap_mr_alpha(const LapMulti& w, const int* active, const double* rz, const double* pAp, double* alpha,
+                         cudaStream_t s);
+cudaError_t lap_mr_beta(const LapMulti& w, const int* active, double* rz, const double* rznew, double* beta,
+                        cudaStream_t s);
+cudaError_t lap_mr_update_xr(const LapMulti& w, int64_t n, const double* alpha, const double* p, const double* Ap,
+                             double* x, double* r, cudaStream_t s);
+cudaError_t lap_mr_update_p(const LapMulti& w, int64_t n, const double* beta, const double* z, double* p,
+                            cudaStream_t s);
+cudaError_t lap_mr_column(int64_t n, int L, int j, double* X, double* v, bool get, cudaStream_t s);
 // gradient of the VIF-Laplace likelihood (Sec. 4.1, App. B, App. D)
 cudaError_t lap_ste_diag(int64_t n, int l, const double* U, const double* Y, const double* b, double* g,
                          cudaStream_t s);

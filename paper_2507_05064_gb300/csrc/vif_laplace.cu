@@ -828,4 +828,484 @@ cudaError_t lap_grad_forms(int64_t n, const double* a, const double* c, const do
   return cudaGetLastError();
 }
 
+// ---------------------------------------------------------------------------
+// Many right-hand sides at once: the L probes of the SLQ (Sec. 4.1) share every operator
+// application of their CG.  Block vectors are n x L, row-major (value j of row i at
+// i L + j, L <= LAP_MR_MAXL); each kernel acts on every column as the single-vector kernel
+// above acts on its vector, and nothing mixes columns.  The triangular solves reuse the
+// level schedules and the value-as-flag protocol; a step's rows run over the columns in
+// passes of MR_CW, and a pass only reads the same pass of earlier rows, so passes of
+// consecutive levels overlap.
+// ---------------------------------------------------------------------------
+constexpr int MR_CW = 16;   // columns per pass of a triangular-solve step
+constexpr int MR_TG = 3;    // terms per lane with loads in flight
+
+__global__ __launch_bounds__(128) void mr_sptrsv_kernel(const int4* __restrict__ sched, int64_t nsteps,
+                                                        const int32_t* __restrict__ idx,
+                                                        const double* __restrict__ coef,
+                                                        const double* __restrict__ rhs, double* out, int L,
+                                                        int* abort_flag, int* status) {
+  const int lane = threadIdx.x & 31, g = lane / TR_LPR;
+  const int64_t W = (int64_t)gridDim.x * (blockDim.x >> 5);
+  for (int64_t step = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); step < nsteps; step += W) {
+    const int4 sl = sched[step * TR_RPS + g];
+    const int row = sl.x;
+    const bool solo = sl.w != 0;
+    const int lanes = solo ? 32 : TR_LPR, sub = solo ? lane : lane % TR_LPR;
+    for (int c0 = 0; c0 < L; c0 += MR_CW) {
+      const int cw = min(MR_CW, L - c0);
+      double acc[MR_CW];
+#pragma unroll
+      for (int u = 0; u < MR_CW; ++u) acc[u] = 0.0;
+      for (int t0 = sl.y + sub; t0 < sl.z; t0 += MR_TG * lanes) {
+        int jj[MR_TG];
+        double cf[MR_TG];
+        unsigned long long v[MR_TG][MR_CW];
+#pragma unroll
+        for (int q = 0; q < MR_TG; ++q) {
+          const int t = t0 + q * lanes;
+          jj[q] = t < sl.z ? idx[t] : -1;
+          cf[q] = t < sl.z ? coef[t] : 0.0;
+        }
+#pragma unroll
+        for (int q = 0; q < MR_TG; ++q)
+#pragma unroll
+          for (int u = 0; u < MR_CW; ++u)
+            if (jj[q] >= 0 && u < cw) v[q][u] = ld_relaxed_u64(out + (size_t)jj[q] * L + c0 + u);
+#pragma unroll
+        for (int q = 0; q < MR_TG; ++q)
+#pragma unroll
+          for (int u = 0; u < MR_CW; ++u)
+            if (jj[q] >= 0 && u < cw) {
+              const double* src = out + (size_t)jj[q] * L + c0 + u;
+              const double x = v[q][u] == TR_PENDING ? wait_value(src, abort_flag, status, row)
+                                                     : __longlong_as_double((long long)v[q][u]);
+              acc[u] = fma(cf[q], x, acc[u]);
+            }
+      }
+#pragma unroll
+      for (int u = 0; u < MR_CW; ++u) {
+        double sum = acc[u];
+        if (solo) {
+          sum += __shfl_xor_sync(0xffffffffu, sum, 16);
+          sum += __shfl_xor_sync(0xffffffffu, sum, 8);
+        }
+        sum += __shfl_xor_sync(0xffffffffu, sum, 4);
+        sum += __shfl_xor_sync(0xffffffffu, sum, 2);
+        sum += __shfl_xor_sync(0xffffffffu, sum, 1);
+        acc[u] = sum;
+      }
+      if (sub == 0 && row >= 0)
+#pragma unroll
+        for (int u = 0; u < MR_CW; ++u)
+          if (u < cw) {
+            const size_t e = (size_t)row * L + c0 + u;
+            st_relaxed_f64(out + e, rhs[e] + acc[u]);
+          }
+    }
+  }
+}
+
+// t[i][j] = (x[i][j] - sum_k A_i[k] x[N_k][j]) / sqrt(D_i)
+__global__ void mr_bx_scaled_kernel(const int32_t* __restrict__ N, const double* __restrict__ Acoef,
+                                    const double* __restrict__ rsD, int64_t n, int mv, int L,
+                                    const double* __restrict__ x, double* t) {
+  const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= n * L) return;
+  const int64_t i = e / L;
+  const int j = (int)(e - i * L);
+  const int q = (int)(i < mv ? i : mv);
+  const int32_t* Ni = N + (size_t)i * mv;
+  const double* Ai = Acoef + (size_t)i * mv;
+  double s = x[e], s2 = 0.0;
+  int k = 0;
+  for (; k + 1 < q; k += 2) {
+    s = fma(-Ai[k], x[(size_t)Ni[k] * L + j], s);
+    s2 = fma(-Ai[k + 1], x[(size_t)Ni[k + 1] * L + j], s2);
+  }
+  if (k < q) s = fma(-Ai[k], x[(size_t)Ni[k] * L + j], s);
+  t[e] = (s + s2) * rsD[i];
+}
+
+// out[r][j] = diagW_r x[r][j] + u[r][j] - sum over the children c of r of A_c[slot] u[c][j]  (CSR)
+__global__ void mr_btx_kernel(const int32_t* __restrict__ ch_ptr, const int32_t* __restrict__ ch_row,
+                              const double* __restrict__ ch_coef, int64_t n, int L, const double* __restrict__ u,
+                              const double* __restrict__ diagW, const double* __restrict__ x, double* out) {
+  const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= n * L) return;
+  const int64_t r = e / L;
+  const int j = (int)(e - r * L);
+  double s = 0.0, s2 = 0.0;
+  int p = ch_ptr[r];
+  const int pe = ch_ptr[r + 1];
+  for (; p + 1 < pe; p += 2) {
+    s = fma(ch_coef[p], u[(size_t)ch_row[p] * L + j], s);
+    s2 = fma(ch_coef[p + 1], u[(size_t)ch_row[p + 1] * L + j], s2);
+  }
+  if (p < pe) s = fma(ch_coef[p], u[(size_t)ch_row[p] * L + j], s);
+  out[e] = u[e] - (s + s2) + (diagW ? diagW[r] * x[e] : 0.0);
+}
+
+// partial[b][c][j] = sum over the rows r of slice b of F[r][c] T[r][j]: shared-memory chunks of
+// 16 rows, 128 columns c per pass, each thread 8 c x 4 j products (j fastest across threads)
+constexpr int MR_FT_ROWS = 16;
+constexpr int MR_FT_CB = 128;
+__global__ __launch_bounds__(256) void mr_ftv_kernel(const double* __restrict__ F, int fpad, int m, int64_t n,
+                                                     int64_t rows_per_block, const double* __restrict__ T, int L,
+                                                     double* partial) {
+  __shared__ double Fs[MR_FT_ROWS][MR_FT_CB];
+  __shared__ double Ts[MR_FT_ROWS][LAP_MR_MAXL];
+  const int tj = threadIdx.x & 15, tc = threadIdx.x >> 4;
+  const int64_t r0 = (int64_t)blockIdx.x * rows_per_block;
+  const int64_t r1 = (n < r0 + rows_per_block) ? n : r0 + rows_per_block;
+  for (int cb = 0; cb < m; cb += MR_FT_CB) {
+    double acc[8][4];
+#pragma unroll
+    for (int a = 0; a < 8; ++a)
+#pragma unroll
+      for (int b = 0; b < 4; ++b) acc[a][b] = 0.0;
+    for (int64_t rr = r0; rr < r1; rr += MR_FT_ROWS) {
+      for (int e = threadIdx.x; e < MR_FT_ROWS * MR_FT_CB; e += blockDim.x) {
+        const int rl = e / MR_FT_CB, cl = e % MR_FT_CB;
+        const int64_t r = rr + rl;
+        const int c = cb + cl;
+        Fs[rl][cl] = (r < r1 && c < m) ? F[(size_t)r * fpad + c] : 0.0;
+      }
+      for (int e = threadIdx.x; e < MR_FT_ROWS * LAP_MR_MAXL; e += blockDim.x) {
+        const int rl = e / LAP_MR_MAXL, jl = e % LAP_MR_MAXL;
+        const int64_t r = rr + rl;
+        Ts[rl][jl] = (r < r1 && jl < L) ? T[(size_t)r * L + jl] : 0.0;
+      }
+      __syncthreads();
+#pragma unroll 4
+      for (int rl = 0; rl < MR_FT_ROWS; ++rl) {
+        double f[8], tv[4];
+#pragma unroll
+        for (int a = 0; a < 8; ++a) f[a] = Fs[rl][tc + 16 * a];
+#pragma unroll
+        for (int b = 0; b < 4; ++b) tv[b] = Ts[rl][tj + 16 * b];
+#pragma unroll
+        for (int a = 0; a < 8; ++a)
+#pragma unroll
+          for (int b = 0; b < 4; ++b) acc[a][b] = fma(f[a], tv[b], acc[a][b]);
+      }
+      __syncthreads();
+    }
+#pragma unroll
+    for (int a = 0; a < 8; ++a)
+#pragma unroll
+      for (int b = 0; b < 4; ++b) {
+        const int c = cb + tc + 16 * a, j = tj + 16 * b;
+        if (c < m && j < L) partial[((size_t)blockIdx.x * fpad + c) * L + j] = acc[a][b];
+      }
+  }
+}
+
+// out[c][j] = sum_b partial[b][c][j], the slices added in a fixed order
+__global__ void mr_col_reduce_kernel(const double* __restrict__ partial, int nb, int fpad, int m, int L,
+                                     double* out) {
+  const int e = blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= m * L) return;
+  const int c = e / L, j = e % L;
+  double s0 = 0.0, s1 = 0.0;
+  int b = 0;
+  for (; b + 1 < nb; b += 2) {
+    s0 += partial[((size_t)b * fpad + c) * L + j];
+    s1 += partial[((size_t)(b + 1) * fpad + c) * L + j];
+  }
+  if (b < nb) s0 += partial[((size_t)b * fpad + c) * L + j];
+  out[e] = s0 + s1;
+}
+
+// Y = Lm X (lower, m x m, leading dimension ld) or Y = Lm^T X; X, Y: m x L
+__global__ void mr_lower_gemm_kernel(const double* __restrict__ Lm, int ld, int m, int L, const double* __restrict__ X,
+                                     double* Y, int transpose) {
+  const int e = blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= m * L) return;
+  const int r = e / L, j = e % L;
+  double s0 = 0.0, s1 = 0.0;
+  if (!transpose) {
+    int c = 0;
+    for (; c + 1 <= r; c += 2) {
+      s0 = fma(Lm[(size_t)r * ld + c], X[(size_t)c * L + j], s0);
+      s1 = fma(Lm[(size_t)r * ld + c + 1], X[(size_t)(c + 1) * L + j], s1);
+    }
+    if (c <= r) s0 = fma(Lm[(size_t)r * ld + c], X[(size_t)c * L + j], s0);
+  } else {
+    int c = r;
+    for (; c + 1 < m; c += 2) {
+      s0 = fma(Lm[(size_t)c * ld + r], X[(size_t)c * L + j], s0);
+      s1 = fma(Lm[(size_t)(c + 1) * ld + r], X[(size_t)(c + 1) * L + j], s1);
+    }
+    if (c < m) s0 = fma(Lm[(size_t)c * ld + r], X[(size_t)c * L + j], s0);
+  }
+  Y[e] = s0 + s1;
+}
+
+// out[i][j] = scale_i (base[i][j] + sgn rsD_i sum_c F[i][c] Y[c][j]); 64 rows x 64 columns per
+// block in chunks of 32 c, each thread 4 rows x 4 columns (j fastest across threads)
+__global__ __launch_bounds__(256) void mr_f_dot_kernel(const double* __restrict__ F, int fpad, int m, int64_t n, int L,
+                                                       const double* __restrict__ Y, const double* __restrict__ base,
+                                                       double sgn, const double* __restrict__ rsD,
+                                                       const double* __restrict__ scale, double* out) {
+  __shared__ double Fs[32][65];
+  __shared__ double Ys[32][LAP_MR_MAXL];
+  const int tj = threadIdx.x & 15, tr = threadIdx.x >> 4;
+  const int64_t i0 = (int64_t)blockIdx.x * 64;
+  double acc[4][4];
+#pragma unroll
+  for (int a = 0; a < 4; ++a)
+#pragma unroll
+    for (int b = 0; b < 4; ++b) acc[a][b] = 0.0;
+  for (int k0 = 0; k0 < m; k0 += 32) {
+    for (int e = threadIdx.x; e < 64 * 32; e += blockDim.x) {
+      const int rl = e / 32, kk = e % 32;
+      const int64_t i = i0 + rl;
+      const int k = k0 + kk;
+      Fs[kk][rl] = (i < n && k < m) ? F[(size_t)i * fpad + k] : 0.0;
+    }
+    for (int e = threadIdx.x; e < 32 * LAP_MR_MAXL; e += blockDim.x) {
+      const int kk = e / LAP_MR_MAXL, jl = e % LAP_MR_MAXL;
+      const int k = k0 + kk;
+      Ys[kk][jl] = (k < m && jl < L) ? Y[(size_t)k * L + jl] : 0.0;
+    }
+    __syncthreads();
+#pragma unroll 4
+    for (int kk = 0; kk < 32; ++kk) {
+      double f[4], y[4];
+#pragma unroll
+      for (int a = 0; a < 4; ++a) f[a] = Fs[kk][tr + 16 * a];
+#pragma unroll
+      for (int b = 0; b < 4; ++b) y[b] = Ys[kk][tj + 16 * b];
+#pragma unroll
+      for (int a = 0; a < 4; ++a)
+#pragma unroll
+        for (int b = 0; b < 4; ++b) acc[a][b] = fma(f[a], y[b], acc[a][b]);
+    }
+    __syncthreads();
+  }
+#pragma unroll
+  for (int a = 0; a < 4; ++a) {
+    const int64_t i = i0 + tr + 16 * a;
+    if (i >= n) continue;
+    const double rs = rsD ? rsD[i] : 1.0;
+    const double sc = scale ? scale[i] : 1.0;
+#pragma unroll
+    for (int b = 0; b < 4; ++b) {
+      const int j = tj + 16 * b;
+      if (j < L) {
+        const size_t e = (size_t)i * L + j;
+        out[e] = sc * (base[e] + sgn * rs * acc[a][b]);
+      }
+    }
+  }
+}
+
+// out[i][j] = a_i (b_i) x[i][j]  (b may be NULL)
+__global__ void mr_scale2_kernel(int64_t n, int L, const double* __restrict__ a, const double* __restrict__ b,
+                                 const double* __restrict__ x, double* out) {
+  const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= n * L) return;
+  const int64_t i = e / L;
+  out[e] = a[i] * (b ? b[i] : 1.0) * x[e];
+}
+
+// partial[blk][j] = sum over this block's rows of a[i][j] b[i][j] (b may be NULL: a alone)
+__global__ __launch_bounds__(256) void mr_dot_stage1(const double* __restrict__ a, const double* __restrict__ b,
+                                                     int64_t n, int L, double* partial) {
+  __shared__ double sh[256];
+  const int rpb = 256 / L;
+  const int j = threadIdx.x % L, r0 = threadIdx.x / L;
+  double v = 0.0;
+  if (r0 < rpb)
+    for (int64_t i = (int64_t)blockIdx.x * rpb + r0; i < n; i += (int64_t)gridDim.x * rpb) {
+      const size_t e = (size_t)i * L + j;
+      v = b ? fma(a[e], b[e], v) : v + a[e];
+    }
+  sh[threadIdx.x] = v;
+  __syncthreads();
+  if (threadIdx.x < L) {
+    double s = 0.0;
+    for (int r = 0; r < rpb; ++r) s += sh[r * L + threadIdx.x];
+    partial[(size_t)blockIdx.x * L + threadIdx.x] = s;
+  }
+}
+__global__ void mr_dot_stage2(const double* __restrict__ partial, int nb, int L, double* out) {
+  const int j = threadIdx.x;
+  if (j >= L) return;
+  double s0 = 0.0, s1 = 0.0;
+  int b = 0;
+  for (; b + 1 < nb; b += 2) {
+    s0 += partial[(size_t)b * L + j];
+    s1 += partial[(size_t)(b + 1) * L + j];
+  }
+  if (b < nb) s0 += partial[(size_t)b * L + j];
+  out[j] = s0 + s1;
+}
+
+// per column: alpha_j = rz_j / pAp_j (0 for a finished column)
+__global__ void mr_alpha_kernel(int L, const int* __restrict__ active, const double* __restrict__ rz,
+                                const double* __restrict__ pAp, double* alpha) {
+  const int j = threadIdx.x;
+  if (j < L) alpha[j] = active[j] ? rz[j] / pAp[j] : 0.0;
+}
+// per column: beta_j = rz_new_j / rz_j and rz_j = rz_new_j (0 and unchanged for a finished column)
+__global__ void mr_beta_kernel(int L, const int* __restrict__ active, double* rz, const double* __restrict__ rznew,
+                               double* beta) {
+  const int j = threadIdx.x;
+  if (j >= L) return;
+  if (active[j]) {
+    beta[j] = rznew[j] / rz[j];
+    rz[j] = rznew[j];
+  } else {
+    beta[j] = 0.0;
+  }
+}
+// x += alpha_j p ;  r -= alpha_j Ap
+__global__ void mr_update_xr_kernel(int64_t n, int L, const double* __restrict__ alpha, const double* __restrict__ p,
+                                    const double* __restrict__ Ap, double* x, double* r) {
+  const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= n * L) return;
+  const double a = alpha[e % L];
+  x[e] = fma(a, p[e], x[e]);
+  r[e] = fma(-a, Ap[e], r[e]);
+}
+// p = z + beta_j p
+__global__ void mr_update_p_kernel(int64_t n, int L, const double* __restrict__ beta, const double* __restrict__ z,
+                                   double* p) {
+  const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= n * L) return;
+  p[e] = fma(beta[e % L], p[e], z[e]);
+}
+// X[i][j] = v[i] (put) or v[i] = X[i][j] (get)
+__global__ void mr_column_kernel(int64_t n, int L, int j, double* X, double* v, int get) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  if (get) v[i] = X[(size_t)i * L + j];
+  else X[(size_t)i * L + j] = v[i];
+}
+
+static cudaError_t launch_mr_trsv(const int4* sched, int64_t nsteps, const int32_t* idx, const double* coef,
+                                  const double* rhs, double* out, int L, int* abort_flag, int* status,
+                                  cudaStream_t s) {
+  static int grid_of_dev[64] = {0};
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  int& grid = grid_of_dev[dev & 63];
+  if (grid == 0) {
+    int sms = 0, per_sm = 0;
+    e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, mr_sptrsv_kernel, 128, 0);
+    if (e != cudaSuccess) return e;
+    if (per_sm < 1) return cudaErrorLaunchOutOfResources;
+    grid = sms * (per_sm < TRSV_CTAS_PER_SM ? per_sm : TRSV_CTAS_PER_SM);
+  }
+  void* args[] = {(void*)&sched, (void*)&nsteps, (void*)&idx, (void*)&coef, (void*)&rhs, (void*)&out, (void*)&L,
+                  (void*)&abort_flag, (void*)&status};
+  return cudaLaunchCooperativeKernel((const void*)mr_sptrsv_kernel, dim3(grid), dim3(128), args, 0, s);
+}
+
+static unsigned mr_blocks(int64_t n, int L) { return blocks(n * L, 256); }
+
+static void mr_ftv(const LapOps& o, const LapMulti& w, const double* T, double* out, cudaStream_t s) {
+  const int64_t rpb = (o.n + LAP_MR_FT_BLOCKS - 1) / LAP_MR_FT_BLOCKS;
+  const int nb = (int)((o.n + rpb - 1) / rpb);
+  mr_ftv_kernel<<<nb, 256, 0, s>>>(o.F, o.fpad, o.m, o.n, rpb, T, w.L, w.partial);
+  mr_col_reduce_kernel<<<blocks((int64_t)o.m * w.L, 256), 256, 0, s>>>(w.partial, nb, o.fpad, o.m, w.L, out);
+}
+
+static void mr_spd_apply(const LapMulti& w, const double* Linv, int ld, int m, const double* X, double* Y,
+                         cudaStream_t s) {
+  mr_lower_gemm_kernel<<<blocks((int64_t)m * w.L, 256), 256, 0, s>>>(Linv, ld, m, w.L, X, w.tmpm, 0);
+  mr_lower_gemm_kernel<<<blocks((int64_t)m * w.L, 256), 256, 0, s>>>(Linv, ld, m, w.L, w.tmpm, Y, 1);
+}
+
+static void mr_f_dot(const LapOps& o, const LapMulti& w, const double* Y, const double* base, double sgn,
+                     const double* rsD, const double* scale, double* out, cudaStream_t s) {
+  mr_f_dot_kernel<<<blocks(o.n, 64), 256, 0, s>>>(o.F, o.fpad, o.m, o.n, w.L, Y, base, sgn, rsD, scale, out);
+}
+
+cudaError_t lap_mr_matvec(const LapOps& o, const LapMulti& w, const double* X, double* out, cudaStream_t s) {
+  // t = D^{-1/2} B X ; t2 = D^{-1/2} (t - F C^{-1} F^T t) ; out = W X + B^T t2
+  mr_bx_scaled_kernel<<<mr_blocks(o.n, w.L), 256, 0, s>>>(o.N, o.Acoef, o.rsD, o.n, o.mv, w.L, X, w.t);
+  if (o.m > 0) {
+    mr_ftv(o, w, w.t, w.sm, s);
+    mr_spd_apply(w, o.LinvC, o.ldl, o.m, w.sm, w.cm, s);
+    mr_f_dot(o, w, w.cm, w.t, -1.0, nullptr, o.rsD, w.t2, s);
+  } else {
+    mr_scale2_kernel<<<mr_blocks(o.n, w.L), 256, 0, s>>>(o.n, w.L, o.rsD, nullptr, w.t, w.t2);
+  }
+  mr_btx_kernel<<<mr_blocks(o.n, w.L), 256, 0, s>>>(o.ch_ptr, o.ch_row, o.ch_coef, o.n, w.L, w.t2, o.W, X, out);
+  return cudaGetLastError();
+}
+
+cudaError_t lap_mr_precond(const LapOps& o, const LapMulti& w, const double* R, double* out, cudaStream_t s) {
+  const size_t bytes = (size_t)o.n * w.L * sizeof(double);
+  cudaError_t e = cudaSuccess;
+  // x1 = B^{-T} R
+  if (o.mv > 0) {
+    if ((e = cudaMemsetAsync(w.x1, 0xFF, bytes, s)) != cudaSuccess) return e;
+    if ((e = launch_mr_trsv(o.sched_rev, o.nsteps_rev, o.ch_row, o.ch_coef, R, w.x1, w.L, o.abort_flag, o.status,
+                            s)) != cudaSuccess)
+      return e;
+  } else if ((e = cudaMemcpyAsync(w.x1, R, bytes, cudaMemcpyDeviceToDevice, s)) != cudaSuccess) {
+    return e;
+  }
+  // t = G^{-1} (x1 + D^{-1/2} F C3^{-1} F^T D^{-1/2} G^{-1} x1)
+  if (o.m > 0) {
+    mr_scale2_kernel<<<mr_blocks(o.n, w.L), 256, 0, s>>>(o.n, w.L, o.rsD, o.Ginv, w.x1, w.t2);
+    mr_ftv(o, w, w.t2, w.sm, s);
+    mr_spd_apply(w, o.LinvC3, o.ldl, o.m, w.sm, w.cm, s);
+    mr_f_dot(o, w, w.cm, w.x1, 1.0, o.rsD, o.Ginv, w.t, s);
+  } else {
+    mr_scale2_kernel<<<mr_blocks(o.n, w.L), 256, 0, s>>>(o.n, w.L, o.Ginv, nullptr, w.x1, w.t);
+  }
+  // out = B^{-1} t
+  if (o.mv > 0) {
+    if ((e = cudaMemsetAsync(out, 0xFF, bytes, s)) != cudaSuccess) return e;
+    if ((e = launch_mr_trsv(o.sched_fwd, o.nsteps_fwd, o.N, o.Acoef, w.t, out, w.L, o.abort_flag, o.status, s)) !=
+        cudaSuccess)
+      return e;
+  } else if ((e = cudaMemcpyAsync(out, w.t, bytes, cudaMemcpyDeviceToDevice, s)) != cudaSuccess) {
+    return e;
+  }
+  return cudaGetLastError();
+}
+
+cudaError_t lap_mr_dot(const LapMulti& w, int64_t n, const double* a, const double* b, double* out, cudaStream_t s) {
+  mr_dot_stage1<<<LAP_MR_DOT_BLOCKS, 256, 0, s>>>(a, b, n, w.L, w.dpart);
+  mr_dot_stage2<<<1, LAP_MR_MAXL, 0, s>>>(w.dpart, LAP_MR_DOT_BLOCKS, w.L, out);
+  return cudaGetLastError();
+}
+
+cudaError_t lap_mr_alpha(const LapMulti& w, const int* active, const double* rz, const double* pAp, double* alpha,
+                         cudaStream_t s) {
+  mr_alpha_kernel<<<1, LAP_MR_MAXL, 0, s>>>(w.L, active, rz, pAp, alpha);
+  return cudaGetLastError();
+}
+
+cudaError_t lap_mr_beta(const LapMulti& w, const int* active, double* rz, const double* rznew, double* beta,
+                        cudaStream_t s) {
+  mr_beta_kernel<<<1, LAP_MR_MAXL, 0, s>>>(w.L, active, rz, rznew, beta);
+  return cudaGetLastError();
+}
+
+cudaError_t lap_mr_update_xr(const LapMulti& w, int64_t n, const double* alpha, const double* p, const double* Ap,
+                             double* x, double* r, cudaStream_t s) {
+  mr_update_xr_kernel<<<mr_blocks(n, w.L), 256, 0, s>>>(n, w.L, alpha, p, Ap, x, r);
+  return cudaGetLastError();
+}
+
+cudaError_t lap_mr_update_p(const LapMulti& w, int64_t n, const double* beta, const double* z, double* p,
+                            cudaStream_t s) {
+  mr_update_p_kernel<<<mr_blocks(n, w.L), 256, 0, s>>>(n, w.L, beta, z, p);
+  return cudaGetLastError();
+}
+
+cudaError_t lap_mr_column(int64_t n, int L, int j, double* X, double* v, bool get, cudaStream_t s) {
+  mr_column_kernel<<<blocks(n, 256), 256, 0, s>>>(n, L, j, X, v, get ? 1 : 0);
+  return cudaGetLastError();
+}
+
 }  // namespace vif

@@ -379,6 +379,25 @@ def test_vifla_gradient_by_ste_matches_oracle_probe_by_probe(ard):
     ctx.close()
 
 
+@pytest.mark.parametrize("m,mv", [(12, 0), (0, 6)])
+def test_vifla_gradient_degenerate_structures_match_oracle(m, mv):
+    """m_v = 0 (B = I: the VIF is FITC) and m = 0 (classical Vecchia): the same STE gradient as the
+    oracle; with m_v = 0 the VIFDU preconditioner is W + Sigma_dagger^{-1} itself, so u_i = P^{-1} z_i
+    and every STE sample s_ik equals its control-variate sample c_ik."""
+    P, vif, b_dense, ctx = _vifla_case(700, m, mv, 45)
+    N = vif.N
+    eps = synth.slq_normals(4, vif.m, vif.n, seed=9)
+    nll, grad, st = ctx.laplace_nll_grad(P.theta, P.y, eps, slq_tol=1e-10, rel_tol=1e-10)
+    ref = O.vifla_grad_ste(P.X, P.Z, P.theta, N, P.y, b_dense, eps, 1e-10, 1e-10)
+    np.testing.assert_allclose(st["probe_terms"][:, :, 0], ref["s"], rtol=1e-6, atol=1e-7 * np.abs(ref["s"]).max())
+    np.testing.assert_allclose(st["trace"][:, 3], ref["trace"], rtol=1e-6, atol=1e-7 * np.abs(ref["s"]).max())
+    np.testing.assert_allclose(grad, ref["grad"], rtol=1e-5, atol=1e-6 * np.abs(ref["grad"]).max())
+    if mv == 0:
+        pt = st["probe_terms"]
+        np.testing.assert_allclose(pt[:, :, 0], pt[:, :, 1], rtol=1e-8, atol=1e-9 * np.abs(pt).max())
+    ctx.close()
+
+
 def test_vifla_gradient_rejects_fitc_and_learned_preconditioners():
     P, vif, b_dense, ctx = _vifla_case(300, 10, 5, 44)
     eps = synth.slq_normals(2, vif.m, vif.n, seed=8)
@@ -391,6 +410,21 @@ def test_vifla_gradient_rejects_fitc_and_learned_preconditioners():
         rc = V.lib().vif_laplace_nll_grad(ctx.h, C.byref(cv), V._ptr(P.y), C.byref(opts), 2, V._ptr(eps), 1e-3,
                                           100, C.byref(out), V._ptr(g), None, None, None)
         assert rc == V.VIF_ERR_ARG
+    ctx.close()
+
+
+def test_vifla_slq_with_more_probes_than_one_block_matches_oracle():
+    """70 probes: the VIFDU probe CGs run side by side in blocks of at most 64 columns (64 + 6),
+    each column with its own step lengths and stopping test; every probe's quadrature and
+    z^T P^{-1} z match the oracle's one-at-a-time CG."""
+    P, vif, b_dense, ctx = _vifla_case(500, 12, 6, 46)
+    eps = synth.slq_normals(70, vif.m, vif.n, seed=11)
+    nll, st = ctx.laplace_nll(P.theta, P.y, eps, slq_tol=1e-8, rel_tol=1e-10)
+    ref = O.vifla_nll_slq(vif, P.y, b_dense, eps, 1e-8)
+    np.testing.assert_allclose(st["zPz"], ref["zPz"], rtol=1e-7)
+    np.testing.assert_allclose(st["q"], ref["q"], rtol=1e-5, atol=1e-8)
+    assert abs(st["pcg_iters_slq"] - int(ref["pcg_iters"].sum())) <= len(eps)
+    assert abs(nll - ref["nll"]) <= 1e-7 * abs(ref["nll"])
     ctx.close()
 
 
