@@ -53,6 +53,7 @@ struct vif_ctx {
   bool lap_ready = false;
   int32_t *ch_ptr = nullptr, *ch_row = nullptr, *ch_slot = nullptr;
   int4 *sched_fwd = nullptr, *sched_rev = nullptr;      // level schedules of B^{-1} and B^{-T}
+  int4 *ord_fwd = nullptr, *ord_rev = nullptr;          // the rows in level order (block solves)
   int64_t nsteps_fwd = 0, nsteps_rev = 0, ch_nnz = 0;
   double* ch_coef = nullptr;                            // coefficient of each child term
   double* slq_eps = nullptr;                            // normals of one SLQ probe (m + 2n)
@@ -292,7 +293,7 @@ void free_ctx(vif_ctx* c) {
                    c->ch_slot, c->l_b,  c->l_W,    c->l_v,    c->l_Ginv, c->l_om,   c->l_rsD,  c->l_ll,
                    c->l_x,    c->l_r,   c->l_z,    c->l_p,    c->l_Ap,   c->l_t,    c->l_t2,   c->l_x1,
                    c->l_sdi,  c->l_sm,  c->l_cm,   c->l_tm,   c->l_part, c->l_LinvC, c->l_G3,  c->l_LinvC3,
-                   c->l_sc,   c->l_red, c->l_corr, c->sched_fwd, c->sched_rev, c->ch_coef, c->slq_eps, c->l_Apad, c->l_anorm2, c->l_dvinv, c->l_pacc, c->l_counter, c->l_abort, c->m_feat,
+                   c->l_sc,   c->l_red, c->l_corr, c->sched_fwd, c->sched_rev, c->ord_fwd, c->ord_rev, c->ch_coef, c->slq_eps, c->l_Apad, c->l_anorm2, c->l_dvinv, c->l_pacc, c->l_counter, c->l_abort, c->m_feat,
                    c->g_U,    c->g_Y,   c->g_g,    c->g_v,    c->g_sc,   c->g_red,
                    c->mr_v,   c->mr_x,  c->mr_r,   c->mr_z,   c->mr_p,   c->mr_Ap,  c->mr_t,   c->mr_t2,
                    c->mr_x1,  c->mr_sm, c->mr_cm,  c->mr_tm,  c->mr_part, c->mr_dpart, c->mr_sc, c->mr_active,
@@ -567,20 +568,40 @@ vif_status build_children(vif_ctx* ctx) {
   }
   const std::vector<int4> sf = level_schedule(lev, f_first, f_cnt, false);
   const std::vector<int4> sr = level_schedule(rlev, std::vector<int32_t>(ptr.begin(), ptr.end() - 1), r_cnt, true);
+  // every row once in level order (counting sort by level), for the block solves
+  auto row_order = [&](const std::vector<int32_t>& level, const std::vector<int32_t>& first,
+                       const std::vector<int32_t>& count) {
+    int32_t nlev = 0;
+    for (int32_t l : level) nlev = std::max(nlev, l + 1);
+    std::vector<int64_t> at((size_t)nlev + 1, 0);
+    for (int32_t l : level) at[(size_t)l + 1]++;
+    for (int32_t l = 0; l < nlev; ++l) at[(size_t)l + 1] += at[(size_t)l];
+    std::vector<int4> ord((size_t)n);
+    for (int64_t r = 0; r < n; ++r)
+      ord[(size_t)at[(size_t)level[(size_t)r]]++] =
+          make_int4((int)r, first[(size_t)r], first[(size_t)r] + count[(size_t)r], 0);
+    return ord;
+  };
+  const std::vector<int4> of = row_order(lev, f_first, f_cnt);
+  const std::vector<int4> orv = row_order(rlev, std::vector<int32_t>(ptr.begin(), ptr.end() - 1), r_cnt);
   if (!ctx->ch_ptr) {
     CKS(dalloc(ctx, &ctx->ch_ptr, (size_t)n + 1));
   }
-  void* owned[] = {ctx->ch_row, ctx->ch_slot, ctx->sched_fwd, ctx->sched_rev, ctx->ch_coef};
+  void* owned[] = {ctx->ch_row, ctx->ch_slot, ctx->sched_fwd, ctx->sched_rev, ctx->ch_coef, ctx->ord_fwd,
+                   ctx->ord_rev};
   for (void* b : owned)
     if (b) cudaFree(b);
   ctx->ch_row = ctx->ch_slot = nullptr;
   ctx->sched_fwd = ctx->sched_rev = nullptr;
+  ctx->ord_fwd = ctx->ord_rev = nullptr;
   ctx->ch_coef = nullptr;
   CKS(dalloc(ctx, &ctx->ch_row, (size_t)std::max<int64_t>(nnz, 1)));
   CKS(dalloc(ctx, &ctx->ch_slot, (size_t)std::max<int64_t>(nnz, 1)));
   CKS(dalloc(ctx, &ctx->sched_fwd, sf.size()));
   CKS(dalloc(ctx, &ctx->sched_rev, sr.size()));
   CKS(dalloc(ctx, &ctx->ch_coef, (size_t)std::max<int64_t>(nnz, 1)));
+  CKS(dalloc(ctx, &ctx->ord_fwd, (size_t)n));
+  CKS(dalloc(ctx, &ctx->ord_rev, (size_t)n));
   ctx->ch_nnz = nnz;
   ctx->nsteps_fwd = (int64_t)(sf.size() / LAP_TRSV_RPS);
   ctx->nsteps_rev = (int64_t)(sr.size() / LAP_TRSV_RPS);
@@ -589,6 +610,8 @@ vif_status build_children(vif_ctx* ctx) {
   CK(cudaMemcpy(ctx->ch_slot, slot.data(), slot.size() * sizeof(int32_t), cudaMemcpyHostToDevice));
   CK(cudaMemcpy(ctx->sched_fwd, sf.data(), sf.size() * sizeof(int4), cudaMemcpyHostToDevice));
   CK(cudaMemcpy(ctx->sched_rev, sr.data(), sr.size() * sizeof(int4), cudaMemcpyHostToDevice));
+  CK(cudaMemcpy(ctx->ord_fwd, of.data(), of.size() * sizeof(int4), cudaMemcpyHostToDevice));
+  CK(cudaMemcpy(ctx->ord_rev, orv.data(), orv.size() * sizeof(int4), cudaMemcpyHostToDevice));
   return VIF_OK;
 }
 
@@ -939,6 +962,8 @@ vif_status lap_setup(vif_ctx* ctx, const vif_cov* theta, const double* y, LapOps
   o->sched_rev = ctx->sched_rev;
   o->nsteps_fwd = ctx->nsteps_fwd;
   o->nsteps_rev = ctx->nsteps_rev;
+  o->ord_fwd = ctx->ord_fwd;
+  o->ord_rev = ctx->ord_rev;
   o->ch_coef = ctx->ch_coef;
   o->nnz = ctx->ch_nnz;
   o->counter = ctx->l_counter;

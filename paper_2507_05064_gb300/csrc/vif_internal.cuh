@@ -184,6 +184,7 @@ struct LapOps {
   int m, mv, fpad, ldl;
   const int32_t *N, *ch_ptr, *ch_row, *ch_slot;
   const int4 *sched_fwd, *sched_rev;      // level-ordered slots of B^{-1} / B^{-T}
+  const int4 *ord_fwd, *ord_rev;          // every row once in level order: {row, first term, end, 0}
   int64_t nsteps_fwd, nsteps_rev;         // schedule lengths / LAP_TRSV_RPS
   const double* ch_coef;                  // A_i[k] of each child term, CSR order (lap_child_coef)
   int64_t nnz;                            // child terms

@@ -832,76 +832,62 @@ cudaError_t lap_grad_forms(int64_t n, const double* a, const double* c, const do
 // Many right-hand sides at once: the L probes of the SLQ (Sec. 4.1) share every operator
 // application of their CG.  Block vectors are n x L, row-major (value j of row i at
 // i L + j, L <= LAP_MR_MAXL); each kernel acts on every column as the single-vector kernel
-// above acts on its vector, and nothing mixes columns.  The triangular solves reuse the
-// level schedules and the value-as-flag protocol; a step's rows run over the columns in
-// passes of MR_CW, and a pass only reads the same pass of earlier rows, so passes of
-// consecutive levels overlap.
+// above acts on its vector, and nothing mixes columns.  The triangular solves keep the
+// value-as-flag protocol over the rows in level order; their work is split so that few
+// float64 instructions (64 cycles each per warp on this part) lie on the chain of levels.
 // ---------------------------------------------------------------------------
-constexpr int MR_CW = 16;   // columns per pass of a triangular-solve step
-constexpr int MR_TG = 3;    // terms per lane with loads in flight
+constexpr int MR_CW = 8;              // columns of one solve task
+constexpr int MR_TS = 32 / MR_CW;     // lanes sharing one column's terms
+constexpr int MR_TG = 8;              // terms per lane with loads in flight
 
-__global__ __launch_bounds__(128) void mr_sptrsv_kernel(const int4* __restrict__ sched, int64_t nsteps,
+// A task is one row and one chunk of MR_CW columns: lane (u, h) = (lane % MR_CW, lane / MR_CW)
+// sums the terms h, h + MR_TS, ... of column c MR_CW + u, and the MR_TS partial sums are added
+// by two shuffles.  Tasks are numbered (position of the row in level order) * nch + chunk and
+// dealt round-robin to the warps of a cooperative launch; a task reads only its own chunk of
+// rows of earlier levels, i.e. of earlier tasks, so the earliest unfinished task can always
+// proceed.  Each chunk is a solve of its own, and chunks of consecutive levels overlap.
+__global__ __launch_bounds__(128) void mr_sptrsv_kernel(const int4* __restrict__ ord, int64_t nrows,
                                                         const int32_t* __restrict__ idx,
                                                         const double* __restrict__ coef,
-                                                        const double* __restrict__ rhs, double* out, int L,
+                                                        const double* __restrict__ rhs, double* out, int L, int nch,
                                                         int* abort_flag, int* status) {
-  const int lane = threadIdx.x & 31, g = lane / TR_LPR;
+  const int lane = threadIdx.x & 31, u = lane % MR_CW, h = lane / MR_CW;
   const int64_t W = (int64_t)gridDim.x * (blockDim.x >> 5);
-  for (int64_t step = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); step < nsteps; step += W) {
-    const int4 sl = sched[step * TR_RPS + g];
-    const int row = sl.x;
-    const bool solo = sl.w != 0;
-    const int lanes = solo ? 32 : TR_LPR, sub = solo ? lane : lane % TR_LPR;
-    for (int c0 = 0; c0 < L; c0 += MR_CW) {
-      const int cw = min(MR_CW, L - c0);
-      double acc[MR_CW];
+  const int64_t ntask = nrows * nch;
+  for (int64_t task = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); task < ntask; task += W) {
+    const int64_t k = task / nch;
+    const int c = (int)(task - k * nch);
+    const int4 sl = ord[k];
+    const int col = c * MR_CW + u;
+    const bool on = col < L;
+    double acc = 0.0;
+    for (int t0 = sl.y + h; t0 < sl.z; t0 += MR_TG * MR_TS) {
+      int jj[MR_TG];
+      double cf[MR_TG];
+      unsigned long long v[MR_TG];
 #pragma unroll
-      for (int u = 0; u < MR_CW; ++u) acc[u] = 0.0;
-      for (int t0 = sl.y + sub; t0 < sl.z; t0 += MR_TG * lanes) {
-        int jj[MR_TG];
-        double cf[MR_TG];
-        unsigned long long v[MR_TG][MR_CW];
-#pragma unroll
-        for (int q = 0; q < MR_TG; ++q) {
-          const int t = t0 + q * lanes;
-          jj[q] = t < sl.z ? idx[t] : -1;
-          cf[q] = t < sl.z ? coef[t] : 0.0;
-        }
-#pragma unroll
-        for (int q = 0; q < MR_TG; ++q)
-#pragma unroll
-          for (int u = 0; u < MR_CW; ++u)
-            if (jj[q] >= 0 && u < cw) v[q][u] = ld_relaxed_u64(out + (size_t)jj[q] * L + c0 + u);
-#pragma unroll
-        for (int q = 0; q < MR_TG; ++q)
-#pragma unroll
-          for (int u = 0; u < MR_CW; ++u)
-            if (jj[q] >= 0 && u < cw) {
-              const double* src = out + (size_t)jj[q] * L + c0 + u;
-              const double x = v[q][u] == TR_PENDING ? wait_value(src, abort_flag, status, row)
-                                                     : __longlong_as_double((long long)v[q][u]);
-              acc[u] = fma(cf[q], x, acc[u]);
-            }
+      for (int q = 0; q < MR_TG; ++q) {
+        const int t = t0 + q * MR_TS;
+        jj[q] = t < sl.z ? idx[t] : -1;
+        cf[q] = t < sl.z ? coef[t] : 0.0;
       }
 #pragma unroll
-      for (int u = 0; u < MR_CW; ++u) {
-        double sum = acc[u];
-        if (solo) {
-          sum += __shfl_xor_sync(0xffffffffu, sum, 16);
-          sum += __shfl_xor_sync(0xffffffffu, sum, 8);
-        }
-        sum += __shfl_xor_sync(0xffffffffu, sum, 4);
-        sum += __shfl_xor_sync(0xffffffffu, sum, 2);
-        sum += __shfl_xor_sync(0xffffffffu, sum, 1);
-        acc[u] = sum;
-      }
-      if (sub == 0 && row >= 0)
+      for (int q = 0; q < MR_TG; ++q)
+        if (on && jj[q] >= 0) v[q] = ld_relaxed_u64(out + (size_t)jj[q] * L + col);
 #pragma unroll
-        for (int u = 0; u < MR_CW; ++u)
-          if (u < cw) {
-            const size_t e = (size_t)row * L + c0 + u;
-            st_relaxed_f64(out + e, rhs[e] + acc[u]);
-          }
+      for (int q = 0; q < MR_TG; ++q)
+        if (on && jj[q] >= 0) {
+          const double* src = out + (size_t)jj[q] * L + col;
+          const double x = v[q] == TR_PENDING ? wait_value(src, abort_flag, status, sl.x)
+                                               : __longlong_as_double((long long)v[q]);
+          acc = fma(cf[q], x, acc);
+        }
+    }
+    acc += __shfl_xor_sync(0xffffffffu, acc, MR_CW);
+    acc += __shfl_xor_sync(0xffffffffu, acc, 2 * MR_CW);
+    if (h == 0 && on) {
+      const size_t e = (size_t)sl.x * L + col;
+      st_relaxed_f64(out + e, rhs[e] + acc);
     }
   }
 }
@@ -1185,7 +1171,7 @@ __global__ void mr_column_kernel(int64_t n, int L, int j, double* X, double* v, 
   else X[(size_t)i * L + j] = v[i];
 }
 
-static cudaError_t launch_mr_trsv(const int4* sched, int64_t nsteps, const int32_t* idx, const double* coef,
+static cudaError_t launch_mr_trsv(const int4* ord, int64_t nrows, const int32_t* idx, const double* coef,
                                   const double* rhs, double* out, int L, int* abort_flag, int* status,
                                   cudaStream_t s) {
   static int grid_of_dev[64] = {0};
@@ -1201,8 +1187,9 @@ static cudaError_t launch_mr_trsv(const int4* sched, int64_t nsteps, const int32
     if (per_sm < 1) return cudaErrorLaunchOutOfResources;
     grid = sms * (per_sm < TRSV_CTAS_PER_SM ? per_sm : TRSV_CTAS_PER_SM);
   }
-  void* args[] = {(void*)&sched, (void*)&nsteps, (void*)&idx, (void*)&coef, (void*)&rhs, (void*)&out, (void*)&L,
-                  (void*)&abort_flag, (void*)&status};
+  int nch = (L + MR_CW - 1) / MR_CW;
+  void* args[] = {(void*)&ord, (void*)&nrows, (void*)&idx, (void*)&coef, (void*)&rhs, (void*)&out, (void*)&L,
+                  (void*)&nch, (void*)&abort_flag, (void*)&status};
   return cudaLaunchCooperativeKernel((const void*)mr_sptrsv_kernel, dim3(grid), dim3(128), args, 0, s);
 }
 
@@ -1246,8 +1233,8 @@ cudaError_t lap_mr_precond(const LapOps& o, const LapMulti& w, const double* R, 
   // x1 = B^{-T} R
   if (o.mv > 0) {
     if ((e = cudaMemsetAsync(w.x1, 0xFF, bytes, s)) != cudaSuccess) return e;
-    if ((e = launch_mr_trsv(o.sched_rev, o.nsteps_rev, o.ch_row, o.ch_coef, R, w.x1, w.L, o.abort_flag, o.status,
-                            s)) != cudaSuccess)
+    if ((e = launch_mr_trsv(o.ord_rev, o.n, o.ch_row, o.ch_coef, R, w.x1, w.L, o.abort_flag, o.status, s)) !=
+        cudaSuccess)
       return e;
   } else if ((e = cudaMemcpyAsync(w.x1, R, bytes, cudaMemcpyDeviceToDevice, s)) != cudaSuccess) {
     return e;
@@ -1264,7 +1251,7 @@ cudaError_t lap_mr_precond(const LapOps& o, const LapMulti& w, const double* R, 
   // out = B^{-1} t
   if (o.mv > 0) {
     if ((e = cudaMemsetAsync(out, 0xFF, bytes, s)) != cudaSuccess) return e;
-    if ((e = launch_mr_trsv(o.sched_fwd, o.nsteps_fwd, o.N, o.Acoef, w.t, out, w.L, o.abort_flag, o.status, s)) !=
+    if ((e = launch_mr_trsv(o.ord_fwd, o.n, o.N, o.Acoef, w.t, out, w.L, o.abort_flag, o.status, s)) !=
         cudaSuccess)
       return e;
   } else if ((e = cudaMemcpyAsync(out, w.t, bytes, cudaMemcpyDeviceToDevice, s)) != cudaSuccess) {
