@@ -1122,8 +1122,8 @@ vif_status mr_buffers(vif_ctx* ctx, int L, LapMulti* w) {
   return VIF_OK;
 }
 
-// Preconditioned CG from X = 0 on (W + Sigma_dagger^{-1}) X = V (Eq. pcls1, VIFDU) for the L columns
-// of mr_v at once: each column takes the steps of lap_pcg with its own step lengths and stopping
+// Preconditioned CG from X = 0 on the system of o.kind (Eq. pcls1 with VIFDU, Eq. pcls2 with FITC)
+// with right-hand sides V, for the L columns of mr_v at once: each column takes the steps of lap_pcg with its own step lengths and stopping
 // test, and a finished column is frozen (alpha = beta = 0) while the others go on.  Per column:
 // iterations, final relative residual, whether the cap was hit, the Lanczos coefficients alpha_j,
 // beta_j and v^T P^{-1} v (App. D); with z0_cols (device, L x n probe-major) also P^{-1} v.
@@ -1143,7 +1143,7 @@ vif_status lap_pcg_multi(vif_ctx* ctx, const LapOps& o, const LapMulti& w, doubl
   CK(cudaMemsetAsync(sc, 0, 7 * (size_t)L * sizeof(double), s));
   CK(cudaMemcpyAsync(ctx->mr_r, ctx->mr_v, bytes, cudaMemcpyDeviceToDevice, s));
   CK(lap_mr_dot(w, n, ctx->mr_v, ctx->mr_v, vv, s));
-  CK(lap_mr_precond(o, w, ctx->mr_r, ctx->mr_z, s));
+  CK(lap_mr_system_precond(o, w, ctx->mr_r, ctx->mr_z, s));
   CK(cudaMemcpyAsync(ctx->mr_p, ctx->mr_z, bytes, cudaMemcpyDeviceToDevice, s));
   if (z0_cols)
     for (int j = 0; j < L; ++j) CK(lap_mr_column(n, L, j, ctx->mr_z, z0_cols + (size_t)j * n, true, s));
@@ -1166,7 +1166,7 @@ vif_status lap_pcg_multi(vif_ctx* ctx, const LapOps& o, const LapMulti& w, doubl
   }
   CK(cudaMemcpyAsync(ctx->mr_active, act.data(), L * sizeof(int), cudaMemcpyHostToDevice, s));
   for (int it = 1; nact > 0 && it <= max_it; ++it) {
-    CK(lap_mr_matvec(o, w, ctx->mr_p, ctx->mr_Ap, s));
+    CK(lap_mr_system_matvec(o, w, ctx->mr_p, ctx->mr_Ap, s));
     CK(lap_mr_dot(w, n, ctx->mr_p, ctx->mr_Ap, pAp, s));
     CK(lap_mr_alpha(w, ctx->mr_active, rz, pAp, alpha, s));
     CK(lap_mr_update_xr(w, n, alpha, ctx->mr_p, ctx->mr_Ap, ctx->mr_x, ctx->mr_r, s));
@@ -1191,7 +1191,7 @@ vif_status lap_pcg_multi(vif_ctx* ctx, const LapOps& o, const LapMulti& w, doubl
     if (reinterpret_cast<const int*>(ctx->h_pin + 9)[0] != ST_OK) break;
     if (nact == 0 || it == max_it) break;
     CK(cudaMemcpyAsync(ctx->mr_active, act.data(), L * sizeof(int), cudaMemcpyHostToDevice, s));
-    CK(lap_mr_precond(o, w, ctx->mr_r, ctx->mr_z, s));
+    CK(lap_mr_system_precond(o, w, ctx->mr_r, ctx->mr_z, s));
     CK(lap_mr_dot(w, n, ctx->mr_r, ctx->mr_z, rznew, s));
     CK(lap_mr_beta(w, ctx->mr_active, rz, rznew, beta, s));
     CK(lap_mr_update_p(w, n, beta, ctx->mr_z, ctx->mr_p, s));
@@ -1510,46 +1510,28 @@ vif_status laplace_nll_core(vif_ctx* ctx, const vif_cov* theta, const double* y,
     wsum += zpz * q;
     return VIF_OK;
   };
-  if (!fitc) {
-    // VIFDU (Eq. pcls1): the probes' CGs run side by side in blocks of up to LAP_MR_MAXL columns,
-    // sharing every operator application
-    for (int b0 = 0; b0 < nprobe; b0 += LAP_MR_MAXL) {
-      const int L = std::min(LAP_MR_MAXL, nprobe - b0);
-      LapMulti w;
-      CKS(mr_buffers(ctx, L, &w));
-      for (int j = 0; j < L; ++j) {
-        CKS(draw(b0 + j));
-        CK(lap_mr_column(n, L, j, ctx->mr_v, ctx->l_v, false, s));
-      }
-      std::vector<int> its(L);
-      std::vector<double> rels(L), rz0(L);
-      std::vector<char> caps(L);
-      std::vector<std::vector<double>> al(L), be(L);
-      CKS(lap_pcg_multi(ctx, o, w, slq_tol, slq_max_iter, its, rels, caps, al, be, rz0,
-                        keepY ? keepY + (size_t)b0 * n : nullptr));
-      if (keepU)
-        for (int j = 0; j < L; ++j) CK(lap_mr_column(n, L, j, ctx->mr_x, keepU + (size_t)(b0 + j) * n, true, s));
-      for (int j = 0; j < L; ++j) {
-        slq_iters += its[j];
-        slq_capped = slq_capped || caps[j];
-        CKS(quadrature(b0 + j, al[j], be[j], rz0[j]));
-      }
+  // the probes' CGs (Eq. pcls1 with VIFDU, Eq. pcls2 with FITC) run side by side in blocks of up to
+  // LAP_MR_MAXL columns, sharing every operator application
+  for (int b0 = 0; b0 < nprobe; b0 += LAP_MR_MAXL) {
+    const int L = std::min(LAP_MR_MAXL, nprobe - b0);
+    LapMulti w;
+    CKS(mr_buffers(ctx, L, &w));
+    for (int j = 0; j < L; ++j) {
+      CKS(draw(b0 + j));
+      CK(lap_mr_column(n, L, j, ctx->mr_v, ctx->l_v, false, s));
     }
-  } else {
-    // FITC (Eq. pcls2): one probe at a time
-    for (int i = 0; i < nprobe; ++i) {
-      CKS(draw(i));
-      std::vector<double> al, be;
-      double zpz = 0.0, rel = 0.0;
-      int it = 0;
-      bool cp = false;
-      CKS(lap_pcg(ctx, o, slq_tol, slq_max_iter, &it, &rel, &cp, &al, &be, &zpz,
-                  keepY ? keepY + (size_t)i * n : nullptr));
-      if (keepU)
-        CK(cudaMemcpyAsync(keepU + (size_t)i * n, ctx->l_x, n * sizeof(double), cudaMemcpyDeviceToDevice, s));
-      slq_iters += it;
-      slq_capped = slq_capped || cp;
-      CKS(quadrature(i, al, be, zpz));
+    std::vector<int> its(L);
+    std::vector<double> rels(L), rz0(L);
+    std::vector<char> caps(L);
+    std::vector<std::vector<double>> al(L), be(L);
+    CKS(lap_pcg_multi(ctx, o, w, slq_tol, slq_max_iter, its, rels, caps, al, be, rz0,
+                      keepY ? keepY + (size_t)b0 * n : nullptr));
+    if (keepU)
+      for (int j = 0; j < L; ++j) CK(lap_mr_column(n, L, j, ctx->mr_x, keepU + (size_t)(b0 + j) * n, true, s));
+    for (int j = 0; j < L; ++j) {
+      slq_iters += its[j];
+      slq_capped = slq_capped || caps[j];
+      CKS(quadrature(b0 + j, al[j], be[j], rz0[j]));
     }
   }
   const double ms_slq =
@@ -1822,32 +1804,45 @@ vif_status vif_laplace_predict(vif_ctx* ctx, const vif_cov* theta, const double*
     const size_t per = (size_t)m + 2 * (size_t)n;
     if (fitc) CKS(lap_fitc_setup(ctx, o, false, theta->variance));
     else CKS(lap_c3(ctx, o));
-    for (int i = 0; i < nsample; ++i) {
-      CKS(upload(ctx, ctx->slq_eps, eps + (size_t)i * per, per * sizeof(double)));
-      const double* z3 = ctx->slq_eps;
-      const double* z1 = ctx->slq_eps + m;
-      const double* z2 = ctx->slq_eps + m + n;
-      CK(lap_probe_prep(n, ctx->Dv, ctx->l_W, nullptr, z1, z2, ctx->l_r, ctx->l_z, s));
-      CK(lap_solve_B(o, ctx->l_r, ctx->l_p, s));
-      if (m > 0) {
-        CK(lap_rows_dot_add(A64, mpad, m, n, z3, ctx->l_p, ctx->l_Ap, s));
-      } else {
-        CK(cudaMemcpyAsync(ctx->l_Ap, ctx->l_p, n * sizeof(double), cudaMemcpyDeviceToDevice, s));
+    // the draws' CGs run side by side in blocks of up to LAP_MR_MAXL columns
+    for (int b0 = 0; b0 < nsample; b0 += LAP_MR_MAXL) {
+      const int L = std::min(LAP_MR_MAXL, nsample - b0);
+      LapMulti w;
+      CKS(mr_buffers(ctx, L, &w));
+      for (int j = 0; j < L; ++j) {
+        CKS(upload(ctx, ctx->slq_eps, eps + (size_t)(b0 + j) * per, per * sizeof(double)));
+        const double* z3 = ctx->slq_eps;
+        const double* z1 = ctx->slq_eps + m;
+        const double* z2 = ctx->slq_eps + m + n;
+        CK(lap_probe_prep(n, ctx->Dv, ctx->l_W, nullptr, z1, z2, ctx->l_r, ctx->l_z, s));
+        CK(lap_solve_B(o, ctx->l_r, ctx->l_p, s));
+        if (m > 0) {
+          CK(lap_rows_dot_add(A64, mpad, m, n, z3, ctx->l_p, ctx->l_Ap, s));
+        } else {
+          CK(cudaMemcpyAsync(ctx->l_Ap, ctx->l_p, n * sizeof(double), cudaMemcpyDeviceToDevice, s));
+        }
+        CK(lap_matvec(o, ctx->l_Ap, nullptr, ctx->l_x, s));
+        CK(lap_vec_add(n, ctx->l_x, ctx->l_z, ctx->l_v, s));
+        if (fitc) {   // Eq. pcls2: z7 = W^{-1} (W^{-1} + Sigma_dagger)^{-1} Sigma_dagger z6
+          CK(lap_sigma_matvec(o, ctx->l_v, nullptr, ctx->l_sdi, s));
+          CK(cudaMemcpyAsync(ctx->l_v, ctx->l_sdi, n * sizeof(double), cudaMemcpyDeviceToDevice, s));
+        }
+        CK(lap_mr_column(n, L, j, ctx->mr_v, ctx->l_v, false, s));
       }
-      CK(lap_matvec(o, ctx->l_Ap, nullptr, ctx->l_x, s));
-      CK(lap_vec_add(n, ctx->l_x, ctx->l_z, ctx->l_v, s));
-      if (fitc) {   // Eq. pcls2: z7 = W^{-1} (W^{-1} + Sigma_dagger)^{-1} Sigma_dagger z6
-        CK(lap_sigma_matvec(o, ctx->l_v, nullptr, ctx->l_sdi, s));
-        CK(cudaMemcpyAsync(ctx->l_v, ctx->l_sdi, n * sizeof(double), cudaMemcpyDeviceToDevice, s));
+      std::vector<int> its(L);
+      std::vector<double> rels(L), rz0(L);
+      std::vector<char> caps(L);
+      std::vector<std::vector<double>> al(L), be(L);
+      CKS(lap_pcg_multi(ctx, o, w, cg_tol, cg_max_iter, its, rels, caps, al, be, rz0, nullptr));
+      for (int j = 0; j < L; ++j) {
+        cg_total += its[j];
+        cg_capped = cg_capped || caps[j];
+        rel = std::max(rel, rels[j]);
+        CK(lap_mr_column(n, L, j, ctx->mr_x, ctx->l_x, true, s));
+        if (fitc) CK(lap_div(n, ctx->l_x, ctx->l_W, ctx->l_x, s));
+        CKS(mean_operator(ctx->l_x, ctx->pcpp, nullptr));
+        CK(lap_sq_accumulate(np, ctx->pcpp, ctx->l_pacc, s));
       }
-      int it = 0;
-      bool cp_ = false;
-      CKS(lap_pcg(ctx, o, cg_tol, cg_max_iter, &it, &rel, &cp_));
-      cg_total += it;
-      cg_capped = cg_capped || cp_;
-      if (fitc) CK(lap_div(n, ctx->l_x, ctx->l_W, ctx->l_x, s));
-      CKS(mean_operator(ctx->l_x, ctx->pcpp, nullptr));
-      CK(lap_sq_accumulate(np, ctx->pcpp, ctx->l_pacc, s));
     }
     CK(lap_axpy_host(np, 1.0 / nsample, ctx->pvar, ctx->l_pacc, ctx->pvar, s));
   }

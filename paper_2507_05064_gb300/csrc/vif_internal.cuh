@@ -250,6 +250,10 @@ struct LapMulti {
 };
 cudaError_t lap_mr_matvec(const LapOps& o, const LapMulti& w, const double* X, double* out, cudaStream_t s);
 cudaError_t lap_mr_precond(const LapOps& o, const LapMulti& w, const double* R, double* out, cudaStream_t s);
+cudaError_t lap_mr_sigma_matvec(const LapOps& o, const LapMulti& w, const double* X, double* out, cudaStream_t s);
+cudaError_t lap_mr_precond_fitc(const LapOps& o, const LapMulti& w, const double* R, double* out, cudaStream_t s);
+cudaError_t lap_mr_system_matvec(const LapOps& o, const LapMulti& w, const double* X, double* out, cudaStream_t s);
+cudaError_t lap_mr_system_precond(const LapOps& o, const LapMulti& w, const double* R, double* out, cudaStream_t s);
 cudaError_t lap_mr_dot(const LapMulti& w, int64_t n, const double* a, const double* b, double* out, cudaStream_t s);
 cudaError_t lap_mr_alpha(const LapMulti& w, const int* active, const double* rz, const double* pAp, double* alpha,
                          cudaStream_t s);

@@ -1195,10 +1195,12 @@ static cudaError_t launch_mr_trsv(const int4* ord, int64_t nrows, const int32_t*
 
 static unsigned mr_blocks(int64_t n, int L) { return blocks(n * L, 256); }
 
-static void mr_ftv(const LapOps& o, const LapMulti& w, const double* T, double* out, cudaStream_t s) {
+// out (m x L) = F^T T for the n x m rows F (leading dimension o.fpad: F itself or A zero-padded)
+static void mr_ftv(const LapOps& o, const LapMulti& w, const double* F, const double* T, double* out,
+                   cudaStream_t s) {
   const int64_t rpb = (o.n + LAP_MR_FT_BLOCKS - 1) / LAP_MR_FT_BLOCKS;
   const int nb = (int)((o.n + rpb - 1) / rpb);
-  mr_ftv_kernel<<<nb, 256, 0, s>>>(o.F, o.fpad, o.m, o.n, rpb, T, w.L, w.partial);
+  mr_ftv_kernel<<<nb, 256, 0, s>>>(F, o.fpad, o.m, o.n, rpb, T, w.L, w.partial);
   mr_col_reduce_kernel<<<blocks((int64_t)o.m * w.L, 256), 256, 0, s>>>(w.partial, nb, o.fpad, o.m, w.L, out);
 }
 
@@ -1208,18 +1210,18 @@ static void mr_spd_apply(const LapMulti& w, const double* Linv, int ld, int m, c
   mr_lower_gemm_kernel<<<blocks((int64_t)m * w.L, 256), 256, 0, s>>>(Linv, ld, m, w.L, w.tmpm, Y, 1);
 }
 
-static void mr_f_dot(const LapOps& o, const LapMulti& w, const double* Y, const double* base, double sgn,
-                     const double* rsD, const double* scale, double* out, cudaStream_t s) {
-  mr_f_dot_kernel<<<blocks(o.n, 64), 256, 0, s>>>(o.F, o.fpad, o.m, o.n, w.L, Y, base, sgn, rsD, scale, out);
+static void mr_f_dot(const LapOps& o, const LapMulti& w, const double* F, const double* Y, const double* base,
+                     double sgn, const double* rsD, const double* scale, double* out, cudaStream_t s) {
+  mr_f_dot_kernel<<<blocks(o.n, 64), 256, 0, s>>>(F, o.fpad, o.m, o.n, w.L, Y, base, sgn, rsD, scale, out);
 }
 
 cudaError_t lap_mr_matvec(const LapOps& o, const LapMulti& w, const double* X, double* out, cudaStream_t s) {
   // t = D^{-1/2} B X ; t2 = D^{-1/2} (t - F C^{-1} F^T t) ; out = W X + B^T t2
   mr_bx_scaled_kernel<<<mr_blocks(o.n, w.L), 256, 0, s>>>(o.N, o.Acoef, o.rsD, o.n, o.mv, w.L, X, w.t);
   if (o.m > 0) {
-    mr_ftv(o, w, w.t, w.sm, s);
+    mr_ftv(o, w, o.F, w.t, w.sm, s);
     mr_spd_apply(w, o.LinvC, o.ldl, o.m, w.sm, w.cm, s);
-    mr_f_dot(o, w, w.cm, w.t, -1.0, nullptr, o.rsD, w.t2, s);
+    mr_f_dot(o, w, o.F, w.cm, w.t, -1.0, nullptr, o.rsD, w.t2, s);
   } else {
     mr_scale2_kernel<<<mr_blocks(o.n, w.L), 256, 0, s>>>(o.n, w.L, o.rsD, nullptr, w.t, w.t2);
   }
@@ -1242,9 +1244,9 @@ cudaError_t lap_mr_precond(const LapOps& o, const LapMulti& w, const double* R, 
   // t = G^{-1} (x1 + D^{-1/2} F C3^{-1} F^T D^{-1/2} G^{-1} x1)
   if (o.m > 0) {
     mr_scale2_kernel<<<mr_blocks(o.n, w.L), 256, 0, s>>>(o.n, w.L, o.rsD, o.Ginv, w.x1, w.t2);
-    mr_ftv(o, w, w.t2, w.sm, s);
+    mr_ftv(o, w, o.F, w.t2, w.sm, s);
     mr_spd_apply(w, o.LinvC3, o.ldl, o.m, w.sm, w.cm, s);
-    mr_f_dot(o, w, w.cm, w.x1, 1.0, o.rsD, o.Ginv, w.t, s);
+    mr_f_dot(o, w, o.F, w.cm, w.x1, 1.0, o.rsD, o.Ginv, w.t, s);
   } else {
     mr_scale2_kernel<<<mr_blocks(o.n, w.L), 256, 0, s>>>(o.n, w.L, o.Ginv, nullptr, w.x1, w.t);
   }
@@ -1258,6 +1260,62 @@ cudaError_t lap_mr_precond(const LapOps& o, const LapMulti& w, const double* R, 
     return e;
   }
   return cudaGetLastError();
+}
+
+// out[i][j] = t[i][j] + x[i][j] / d_i
+__global__ void mr_add_div_kernel(int64_t n, int L, const double* __restrict__ t, const double* __restrict__ x,
+                                  const double* __restrict__ d, double* out) {
+  const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= n * L) return;
+  out[e] = t[e] + x[e] / d[e / L];
+}
+
+// FITC form (Eq. pcls2): out = (W^{-1} + Sigma_dagger) X = B^{-1} (D o B^{-T} X) + A^T (A X) + X / W
+cudaError_t lap_mr_sigma_matvec(const LapOps& o, const LapMulti& w, const double* X, double* out, cudaStream_t s) {
+  const size_t bytes = (size_t)o.n * w.L * sizeof(double);
+  cudaError_t e = cudaSuccess;
+  if (o.mv > 0) {
+    if ((e = cudaMemsetAsync(w.x1, 0xFF, bytes, s)) != cudaSuccess) return e;
+    if ((e = launch_mr_trsv(o.ord_rev, o.n, o.ch_row, o.ch_coef, X, w.x1, w.L, o.abort_flag, o.status, s)) !=
+        cudaSuccess)
+      return e;
+    mr_scale2_kernel<<<mr_blocks(o.n, w.L), 256, 0, s>>>(o.n, w.L, o.D, nullptr, w.x1, w.t2);
+    if ((e = cudaMemsetAsync(w.t, 0xFF, bytes, s)) != cudaSuccess) return e;
+    if ((e = launch_mr_trsv(o.ord_fwd, o.n, o.N, o.Acoef, w.t2, w.t, w.L, o.abort_flag, o.status, s)) !=
+        cudaSuccess)
+      return e;
+  } else {
+    mr_scale2_kernel<<<mr_blocks(o.n, w.L), 256, 0, s>>>(o.n, w.L, o.D, nullptr, X, w.t);
+  }
+  mr_add_div_kernel<<<mr_blocks(o.n, w.L), 256, 0, s>>>(o.n, w.L, w.t, X, o.W, w.t2);
+  if (o.m > 0) {
+    mr_ftv(o, w, o.Apad, X, w.sm, s);
+    mr_f_dot(o, w, o.Apad, w.sm, w.t2, 1.0, nullptr, nullptr, out, s);
+  } else if ((e = cudaMemcpyAsync(out, w.t2, bytes, cudaMemcpyDeviceToDevice, s)) != cudaSuccess) {
+    return e;
+  }
+  return cudaGetLastError();
+}
+
+// FITC preconditioner (App. E.2): out = D_V^{-1} (R - A^T M_V^{-1} A D_V^{-1} R)
+cudaError_t lap_mr_precond_fitc(const LapOps& o, const LapMulti& w, const double* R, double* out, cudaStream_t s) {
+  if (o.m == 0) {
+    mr_scale2_kernel<<<mr_blocks(o.n, w.L), 256, 0, s>>>(o.n, w.L, o.dvinv, nullptr, R, out);
+    return cudaGetLastError();
+  }
+  mr_scale2_kernel<<<mr_blocks(o.n, w.L), 256, 0, s>>>(o.n, w.L, o.dvinv, nullptr, R, w.t2);
+  mr_ftv(o, w, o.Apad, w.t2, w.sm, s);
+  mr_spd_apply(w, o.LinvMV, o.ldl, o.m, w.sm, w.cm, s);
+  mr_f_dot(o, w, o.Apad, w.cm, R, -1.0, nullptr, o.dvinv, out, s);
+  return cudaGetLastError();
+}
+
+cudaError_t lap_mr_system_matvec(const LapOps& o, const LapMulti& w, const double* X, double* out, cudaStream_t s) {
+  return o.kind == LAP_FITC ? lap_mr_sigma_matvec(o, w, X, out, s) : lap_mr_matvec(o, w, X, out, s);
+}
+
+cudaError_t lap_mr_system_precond(const LapOps& o, const LapMulti& w, const double* R, double* out, cudaStream_t s) {
+  return o.kind == LAP_FITC ? lap_mr_precond_fitc(o, w, R, out, s) : lap_mr_precond(o, w, R, out, s);
 }
 
 cudaError_t lap_mr_dot(const LapMulti& w, int64_t n, const double* a, const double* b, double* out, cudaStream_t s) {

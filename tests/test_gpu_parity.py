@@ -413,14 +413,19 @@ def test_vifla_gradient_rejects_fitc_and_learned_preconditioners():
     ctx.close()
 
 
-def test_vifla_slq_with_more_probes_than_one_block_matches_oracle():
-    """70 probes: the VIFDU probe CGs run side by side in blocks of at most 64 columns (64 + 6),
-    each column with its own step lengths and stopping test; every probe's quadrature and
-    z^T P^{-1} z match the oracle's one-at-a-time CG."""
+@pytest.mark.parametrize("fitc", [False, True])
+def test_vifla_slq_with_more_probes_than_one_block_matches_oracle(fitc):
+    """70 probes: the probe CGs (VIFDU, Eq. pcls1; FITC, Eq. pcls2) run side by side in blocks of
+    at most 64 columns (64 + 6), each column with its own step lengths and stopping test; every
+    probe's quadrature and z^T P^{-1} z match the oracle's one-at-a-time CG."""
     P, vif, b_dense, ctx = _vifla_case(500, 12, 6, 46)
     eps = synth.slq_normals(70, vif.m, vif.n, seed=11)
-    nll, st = ctx.laplace_nll(P.theta, P.y, eps, slq_tol=1e-8, rel_tol=1e-10)
-    ref = O.vifla_nll_slq(vif, P.y, b_dense, eps, 1e-8)
+    if fitc:
+        nll, st = ctx.laplace_nll(P.theta, P.y, eps, slq_tol=1e-8, rel_tol=1e-10, precond=V.PRECOND_FITC)
+        ref = O.vifla_nll_slq_fitc(vif, P.y, b_dense, eps[:, :vif.m + vif.n], 1e-8)
+    else:
+        nll, st = ctx.laplace_nll(P.theta, P.y, eps, slq_tol=1e-8, rel_tol=1e-10)
+        ref = O.vifla_nll_slq(vif, P.y, b_dense, eps, 1e-8)
     np.testing.assert_allclose(st["zPz"], ref["zPz"], rtol=1e-7)
     np.testing.assert_allclose(st["q"], ref["q"], rtol=1e-5, atol=1e-8)
     assert abs(st["pcg_iters_slq"] - int(ref["pcg_iters"].sum())) <= len(eps)
