@@ -68,7 +68,7 @@ struct vif_ctx {
   double *mr_v = nullptr, *mr_x = nullptr, *mr_r = nullptr, *mr_z = nullptr, *mr_p = nullptr, *mr_Ap = nullptr,
          *mr_t = nullptr, *mr_t2 = nullptr, *mr_x1 = nullptr, *mr_sm = nullptr, *mr_cm = nullptr, *mr_tm = nullptr,
          *mr_part = nullptr, *mr_dpart = nullptr, *mr_sc = nullptr;
-  int* mr_active = nullptr;
+  int *mr_active = nullptr, *mr_map = nullptr;
   int mr_cap = 0;
   double *l_b = nullptr, *l_W = nullptr, *l_v = nullptr, *l_Ginv = nullptr, *l_om = nullptr, *l_rsD = nullptr,
          *l_ll = nullptr, *l_x = nullptr, *l_r = nullptr, *l_z = nullptr, *l_p = nullptr, *l_Ap = nullptr,
@@ -296,7 +296,7 @@ void free_ctx(vif_ctx* c) {
                    c->l_sc,   c->l_red, c->l_corr, c->sched_fwd, c->sched_rev, c->ord_fwd, c->ord_rev, c->ch_coef, c->slq_eps, c->l_Apad, c->l_anorm2, c->l_dvinv, c->l_pacc, c->l_counter, c->l_abort, c->m_feat,
                    c->g_U,    c->g_Y,   c->g_g,    c->g_v,    c->g_sc,   c->g_red,
                    c->mr_v,   c->mr_x,  c->mr_r,   c->mr_z,   c->mr_p,   c->mr_Ap,  c->mr_t,   c->mr_t2,
-                   c->mr_x1,  c->mr_sm, c->mr_cm,  c->mr_tm,  c->mr_part, c->mr_dpart, c->mr_sc, c->mr_active,
+                   c->mr_x1,  c->mr_sm, c->mr_cm,  c->mr_tm,  c->mr_part, c->mr_dpart, c->mr_sc, c->mr_active, c->mr_map,
                    c->m_gc,   c->m_part, c->m_grad};
   for (void* b : pbufs)
     if (b) cudaFree(b);
@@ -1107,6 +1107,7 @@ vif_status mr_buffers(vif_ctx* ctx, int L, LapMulti* w) {
     if (!ctx->mr_sc) {
       CKS(dalloc(ctx, &ctx->mr_sc, 7 * (size_t)LAP_MR_MAXL));
       CKS(dalloc(ctx, &ctx->mr_active, (size_t)LAP_MR_MAXL));
+      CKS(dalloc(ctx, &ctx->mr_map, (size_t)LAP_MR_MAXL));
     }
     ctx->mr_cap = L;
   }
@@ -1123,10 +1124,13 @@ vif_status mr_buffers(vif_ctx* ctx, int L, LapMulti* w) {
 }
 
 // Preconditioned CG from X = 0 on the system of o.kind (Eq. pcls1 with VIFDU, Eq. pcls2 with FITC)
-// with right-hand sides V, for the L columns of mr_v at once: each column takes the steps of lap_pcg with its own step lengths and stopping
-// test, and a finished column is frozen (alpha = beta = 0) while the others go on.  Per column:
-// iterations, final relative residual, whether the cap was hit, the Lanczos coefficients alpha_j,
-// beta_j and v^T P^{-1} v (App. D); with z0_cols (device, L x n probe-major) also P^{-1} v.
+// with right-hand sides V, for the L columns of mr_v at once: each column takes the steps of
+// lap_pcg with its own step lengths and stopping test.  A column that meets its test leaves the
+// block: its solution is parked in mr_v (whose right-hand sides are no longer needed) and the
+// others are packed into the first columns, so later products only cover unfinished columns.
+// On return mr_x holds every column's solution (n x L).  Per column: iterations, final relative
+// residual, whether the cap was hit, the Lanczos coefficients alpha_j, beta_j and v^T P^{-1} v
+// (App. D); with z0_cols (device, L x n probe-major) also P^{-1} v.
 vif_status lap_pcg_multi(vif_ctx* ctx, const LapOps& o, const LapMulti& w, double tol, int max_it,
                          std::vector<int>& iters, std::vector<double>& rel, std::vector<char>& capped,
                          std::vector<std::vector<double>>& alphas, std::vector<std::vector<double>>& betas,
@@ -1135,67 +1139,111 @@ vif_status lap_pcg_multi(vif_ctx* ctx, const LapOps& o, const LapMulti& w, doubl
   const int64_t n = ctx->n;
   const int L = w.L;
   const size_t bytes = (size_t)n * L * sizeof(double);
-  double* sc = ctx->mr_sc;   // per column: rz, pAp, alpha, rr, rz_new, beta, v^T v
-  double *rz = sc, *pAp = sc + L, *alpha = sc + 2 * L, *rr = sc + 3 * L, *rznew = sc + 4 * L, *beta = sc + 5 * L,
-         *vv = sc + 6 * L;
+  double* sc = ctx->mr_sc;   // per current column, stride Lc: rz, pAp, alpha, rr, rz_new, beta (, v^T v)
   double* hs = ctx->h_pin + 64;   // 7 L <= 448 doubles of pinned staging
   CK(cudaMemsetAsync(ctx->mr_x, 0, bytes, s));
   CK(cudaMemsetAsync(sc, 0, 7 * (size_t)L * sizeof(double), s));
   CK(cudaMemcpyAsync(ctx->mr_r, ctx->mr_v, bytes, cudaMemcpyDeviceToDevice, s));
-  CK(lap_mr_dot(w, n, ctx->mr_v, ctx->mr_v, vv, s));
+  CK(lap_mr_dot(w, n, ctx->mr_v, ctx->mr_v, sc + 6 * L, s));
   CK(lap_mr_system_precond(o, w, ctx->mr_r, ctx->mr_z, s));
   CK(cudaMemcpyAsync(ctx->mr_p, ctx->mr_z, bytes, cudaMemcpyDeviceToDevice, s));
   if (z0_cols)
     for (int j = 0; j < L; ++j) CK(lap_mr_column(n, L, j, ctx->mr_z, z0_cols + (size_t)j * n, true, s));
-  CK(lap_mr_dot(w, n, ctx->mr_r, ctx->mr_z, rz, s));
+  CK(lap_mr_dot(w, n, ctx->mr_r, ctx->mr_z, sc, s));
   CK(cudaMemcpyAsync(hs, sc, 7 * (size_t)L * sizeof(double), cudaMemcpyDeviceToHost, s));
   CK(cudaStreamSynchronize(s));
   std::vector<double> vnorm(L);
-  std::vector<int> act(L);
-  int nact = 0;
+  std::vector<int> col(L);            // current slot -> column
+  std::vector<char> keep(L);
   for (int j = 0; j < L; ++j) {
     vnorm[j] = std::sqrt(hs[6 * L + j]);
     rz0[j] = hs[j];
-    act[j] = vnorm[j] > 0.0 ? 1 : 0;
-    nact += act[j];
+    keep[j] = vnorm[j] > 0.0 ? 1 : 0;
+    col[j] = j;
     iters[j] = 0;
     rel[j] = 0.0;
     capped[j] = 0;
     alphas[j].clear();
     betas[j].clear();
   }
-  CK(cudaMemcpyAsync(ctx->mr_active, act.data(), L * sizeof(int), cudaMemcpyHostToDevice, s));
-  for (int it = 1; nact > 0 && it <= max_it; ++it) {
-    CK(lap_mr_system_matvec(o, w, ctx->mr_p, ctx->mr_Ap, s));
-    CK(lap_mr_dot(w, n, ctx->mr_p, ctx->mr_Ap, pAp, s));
-    CK(lap_mr_alpha(w, ctx->mr_active, rz, pAp, alpha, s));
-    CK(lap_mr_update_xr(w, n, alpha, ctx->mr_p, ctx->mr_Ap, ctx->mr_x, ctx->mr_r, s));
-    CK(lap_mr_dot(w, n, ctx->mr_r, ctx->mr_r, rr, s));
-    CK(cudaMemcpyAsync(hs, sc, 7 * (size_t)L * sizeof(double), cudaMemcpyDeviceToHost, s));
+  int Lc = L;
+  // park the solutions of the slots with keep = 0 in mr_v, pack the others (x, r, p and rz of sc)
+  auto repack = [&]() -> vif_status {
+    std::vector<int> map, ncol;
+    std::vector<double> nrz;
+    for (int jj = 0; jj < Lc; ++jj) {
+      if (keep[jj]) {
+        map.push_back(jj);
+        ncol.push_back(col[jj]);
+        nrz.push_back(hs[jj]);
+      } else {
+        CK(lap_mr_copy_col(n, ctx->mr_x, Lc, jj, ctx->mr_v, L, col[jj], s));
+      }
+    }
+    const int Lk = (int)map.size();
+    if (Lk > 0 && Lk < Lc) {
+      const size_t kb = (size_t)n * Lk * sizeof(double);
+      CK(cudaMemcpyAsync(ctx->mr_map, map.data(), Lk * sizeof(int), cudaMemcpyHostToDevice, s));
+      CK(lap_mr_gather(n, Lc, Lk, ctx->mr_map, ctx->mr_x, ctx->mr_t, s));
+      CK(lap_mr_gather(n, Lc, Lk, ctx->mr_map, ctx->mr_r, ctx->mr_t2, s));
+      CK(lap_mr_gather(n, Lc, Lk, ctx->mr_map, ctx->mr_p, ctx->mr_x1, s));
+      CK(cudaMemcpyAsync(ctx->mr_x, ctx->mr_t, kb, cudaMemcpyDeviceToDevice, s));
+      CK(cudaMemcpyAsync(ctx->mr_r, ctx->mr_t2, kb, cudaMemcpyDeviceToDevice, s));
+      CK(cudaMemcpyAsync(ctx->mr_p, ctx->mr_x1, kb, cudaMemcpyDeviceToDevice, s));
+      CK(cudaMemcpyAsync(sc, nrz.data(), Lk * sizeof(double), cudaMemcpyHostToDevice, s));
+      CK(cudaStreamSynchronize(s));   // the host vectors above go out of scope
+    }
+    col = ncol;
+    Lc = Lk;
+    keep.assign(Lc, 1);
+    return VIF_OK;
+  };
+  CKS(repack());
+  {
+    const std::vector<int> ones(LAP_MR_MAXL, 1);
+    CK(cudaMemcpyAsync(ctx->mr_active, ones.data(), LAP_MR_MAXL * sizeof(int), cudaMemcpyHostToDevice, s));
+    CK(cudaStreamSynchronize(s));
+  }
+  for (int it = 1; Lc > 0 && it <= max_it; ++it) {
+    LapMulti wc = w;
+    wc.L = Lc;
+    double *rz = sc, *pAp = sc + Lc, *alpha = sc + 2 * Lc, *rr = sc + 3 * Lc;
+    CK(lap_mr_system_matvec(o, wc, ctx->mr_p, ctx->mr_Ap, s));
+    CK(lap_mr_dot(wc, n, ctx->mr_p, ctx->mr_Ap, pAp, s));
+    CK(lap_mr_alpha(wc, ctx->mr_active, rz, pAp, alpha, s));
+    CK(lap_mr_update_xr(wc, n, alpha, ctx->mr_p, ctx->mr_Ap, ctx->mr_x, ctx->mr_r, s));
+    CK(lap_mr_dot(wc, n, ctx->mr_r, ctx->mr_r, rr, s));
+    CK(cudaMemcpyAsync(hs, sc, 6 * (size_t)Lc * sizeof(double), cudaMemcpyDeviceToHost, s));
     CK(cudaMemcpyAsync(ctx->h_pin + 9, ctx->status, 4 * sizeof(int), cudaMemcpyDeviceToHost, s));
     CK(cudaStreamSynchronize(s));
     // alpha of this step; beta of the previous one (set at its end)
-    for (int j = 0; j < L; ++j) {
-      if (!act[j]) continue;
-      alphas[j].push_back(hs[2 * L + j]);
-      if (it >= 2) betas[j].push_back(hs[5 * L + j]);
-      rel[j] = std::sqrt(hs[3 * L + j]) / vnorm[j];
+    bool any_done = false;
+    for (int jj = 0; jj < Lc; ++jj) {
+      const int j = col[jj];
+      alphas[j].push_back(hs[2 * Lc + jj]);
+      if (it >= 2) betas[j].push_back(hs[5 * Lc + jj]);
+      rel[j] = std::sqrt(hs[3 * Lc + jj]) / vnorm[j];
       iters[j] = it;
       if (rel[j] <= tol) {
-        act[j] = 0;
-        --nact;
+        keep[jj] = 0;
+        any_done = true;
       } else if (it == max_it) {
         capped[j] = 1;
       }
     }
     if (reinterpret_cast<const int*>(ctx->h_pin + 9)[0] != ST_OK) break;
-    if (nact == 0 || it == max_it) break;
-    CK(cudaMemcpyAsync(ctx->mr_active, act.data(), L * sizeof(int), cudaMemcpyHostToDevice, s));
-    CK(lap_mr_system_precond(o, w, ctx->mr_r, ctx->mr_z, s));
-    CK(lap_mr_dot(w, n, ctx->mr_r, ctx->mr_z, rznew, s));
-    CK(lap_mr_beta(w, ctx->mr_active, rz, rznew, beta, s));
-    CK(lap_mr_update_p(w, n, beta, ctx->mr_z, ctx->mr_p, s));
+    if (any_done) CKS(repack());
+    if (Lc == 0 || it == max_it) break;
+    wc.L = Lc;
+    double *rzn = sc + 4 * Lc, *beta = sc + 5 * Lc;
+    CK(lap_mr_system_precond(o, wc, ctx->mr_r, ctx->mr_z, s));
+    CK(lap_mr_dot(wc, n, ctx->mr_r, ctx->mr_z, rzn, s));
+    CK(lap_mr_beta(wc, ctx->mr_active, sc, rzn, beta, s));
+    CK(lap_mr_update_p(wc, n, beta, ctx->mr_z, ctx->mr_p, s));
   }
+  // every column's solution into mr_x (n x L)
+  for (int jj = 0; jj < Lc; ++jj) CK(lap_mr_copy_col(n, ctx->mr_x, Lc, jj, ctx->mr_v, L, col[jj], s));
+  CK(cudaMemcpyAsync(ctx->mr_x, ctx->mr_v, bytes, cudaMemcpyDeviceToDevice, s));
   double dummy[1];
   CKS(read_status(ctx, dummy, 0));
   return VIF_OK;

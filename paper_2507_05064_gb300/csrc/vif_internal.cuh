@@ -264,6 +264,10 @@ cudaError_t lap_mr_update_xr(const LapMulti& w, int64_t n, const double* alpha, 
 cudaError_t lap_mr_update_p(const LapMulti& w, int64_t n, const double* beta, const double* z, double* p,
                             cudaStream_t s);
 cudaError_t lap_mr_column(int64_t n, int L, int j, double* X, double* v, bool get, cudaStream_t s);
+cudaError_t lap_mr_gather(int64_t n, int Ls, int Ld, const int* map, const double* src, double* dst,
+                          cudaStream_t s);
+cudaError_t lap_mr_copy_col(int64_t n, const double* src, int Ls, int js, double* dst, int Ld, int jd,
+                            cudaStream_t s);
 // gradient of the VIF-Laplace likelihood (Sec. 4.1, App. B, App. D)
 cudaError_t lap_ste_diag(int64_t n, int l, const double* U, const double* Y, const double* b, double* g,
                          cudaStream_t s);

@@ -1171,6 +1171,10 @@ __global__ void mr_column_kernel(int64_t n, int L, int j, double* X, double* v, 
   else X[(size_t)i * L + j] = v[i];
 }
 
+// CTAs per SM of a block solve: its tasks are many and short, so more resident warps keep more
+// loads in flight (all resident at once: the launch is cooperative)
+constexpr int MR_TRSV_CTAS_PER_SM = 6;
+
 static cudaError_t launch_mr_trsv(const int4* ord, int64_t nrows, const int32_t* idx, const double* coef,
                                   const double* rhs, double* out, int L, int* abort_flag, int* status,
                                   cudaStream_t s) {
@@ -1185,7 +1189,7 @@ static cudaError_t launch_mr_trsv(const int4* ord, int64_t nrows, const int32_t*
     if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, mr_sptrsv_kernel, 128, 0);
     if (e != cudaSuccess) return e;
     if (per_sm < 1) return cudaErrorLaunchOutOfResources;
-    grid = sms * (per_sm < TRSV_CTAS_PER_SM ? per_sm : TRSV_CTAS_PER_SM);
+    grid = sms * (per_sm < MR_TRSV_CTAS_PER_SM ? per_sm : MR_TRSV_CTAS_PER_SM);
   }
   int nch = (L + MR_CW - 1) / MR_CW;
   void* args[] = {(void*)&ord, (void*)&nrows, (void*)&idx, (void*)&coef, (void*)&rhs, (void*)&out, (void*)&L,
@@ -1345,6 +1349,34 @@ cudaError_t lap_mr_update_xr(const LapMulti& w, int64_t n, const double* alpha, 
 cudaError_t lap_mr_update_p(const LapMulti& w, int64_t n, const double* beta, const double* z, double* p,
                             cudaStream_t s) {
   mr_update_p_kernel<<<mr_blocks(n, w.L), 256, 0, s>>>(n, w.L, beta, z, p);
+  return cudaGetLastError();
+}
+
+// dst[i][j] = src[i][map[j]]  (src n x Ls, dst n x Ld)
+__global__ void mr_gather_kernel(int64_t n, int Ls, int Ld, const int* __restrict__ map,
+                                 const double* __restrict__ src, double* dst) {
+  const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= n * Ld) return;
+  const int64_t i = e / Ld;
+  const int j = (int)(e - i * Ld);
+  dst[e] = src[(size_t)i * Ls + map[j]];
+}
+// dst[i][jd] = src[i][js]
+__global__ void mr_copy_col_kernel(int64_t n, const double* __restrict__ src, int Ls, int js, double* dst, int Ld,
+                                   int jd) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) dst[(size_t)i * Ld + jd] = src[(size_t)i * Ls + js];
+}
+
+cudaError_t lap_mr_gather(int64_t n, int Ls, int Ld, const int* map, const double* src, double* dst,
+                          cudaStream_t s) {
+  mr_gather_kernel<<<mr_blocks(n, Ld), 256, 0, s>>>(n, Ls, Ld, map, src, dst);
+  return cudaGetLastError();
+}
+
+cudaError_t lap_mr_copy_col(int64_t n, const double* src, int Ls, int js, double* dst, int Ld, int jd,
+                            cudaStream_t s) {
+  mr_copy_col_kernel<<<blocks(n, 256), 256, 0, s>>>(n, src, Ls, js, dst, Ld, jd);
   return cudaGetLastError();
 }
 
