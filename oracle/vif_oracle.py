@@ -24,7 +24,7 @@ dense solves, sparse products, sorting) as the only building blocks:
   the SLQ form of Eq. slq_v2;
 * VIF-Laplace predictive distributions (Prop. 3.1) and their variances by Alg. 1 (SBPV);
 * the VIF-Laplace gradient by stochastic trace estimation with the preconditioner control
-  variate (Sec. 4.1, App. B, App. D).
+  variate (Sec. 4.1, App. B, App. D), in the VIFDU (Eq. pcls1) and the FITC (Eq. pcls2) form.
 
 Readings of points the paper leaves open (all shared with the CUDA path):
   R1 kernel forms of Rasmussen & Williams; "range" = length scale lambda.
@@ -1033,6 +1033,100 @@ def vifla_grad_ste(X, Z, theta, N, y, b, eps, tol: float, solve_tol: float, max_
         trace[k] = float((S[:, k] - c_opt[k] * C[:, k]).mean()) + c_opt[k] * tau[k]
         grad[k] = 0.5 * d["bb"] + 0.5 * (d["ldS"] + trace[k]) - d["vb"]
     return dict(grad=grad, s=S, c=C, trace_plain=tr_plain, c_opt=c_opt, tau=tau, trace=trace, g=g, v=v)
+
+
+def vifla_grad_ste_fitc(X, Z, theta, N, y, b, eps, tol: float, solve_tol: float, max_iter: int = 1000,
+                        rel_step: float = 1e-4):
+    """The gradient of vifla_grad_ste in the FITC form (Eq. pcls2 / slq_v2, App. D second form):
+    with H_F = W^{-1} + Sigma_dagger, log det(Sigma_dagger W + I) = log det W + log det H_F, so
+
+        dL/dth_k = -1/2 a^T dSigma_k a + av^T dSigma_k a + 1/2 Tr(H_F^{-1} dSigma_k),
+        dL/db_j  = 1/2 (dW_jj/db_j / W_jj - dW_jj/db_j / W_jj^2 (H_F^{-1})_jj),
+
+    dSigma_k = dSigma_dagger/dth_k, a = Sigma_dagger^{-1} b (so that b^T Delta_k b = -a^T dSigma_k a) and
+    av = Sigma_dagger^{-1} v, v = (W + Sigma_dagger^{-1})^{-1} dL/db = W^{-1} H_F^{-1} Sigma_dagger dL/db (CG on
+    Eq. pcls2, tolerance `solve_tol`).  The traces are the STE of Sec. 4.1 with the FITC probes
+    z_i ~ N(0, P) (App. E.2), u_i = H_F^{-1} z_i (the SLQ's CG solves, tolerance `tol`), y_i = P^{-1} z_i:
+        (H_F^{-1})_jj ~ (1/l) sum_i u_ij y_ij,   s_ik = u_i^T dSigma_k y_i,
+    with the control variate of App. D: c_ik = y_i^T (dP/dth_k) y_i, tau_k = dlog det P/dth_k
+    (P = D_V + Sigma_mn^T Sigma_m^{-1} Sigma_mn, W fixed).  Derivatives in theta are central differences
+    (R16).  eps: l x (m + n) (or wider; the first m + n entries are used).  Returns the dict of
+    vifla_grad_ste plus dhat (the diagonal estimate)."""
+    vif = VIF(X, Z, theta, N)
+    n, m = vif.n, vif.m
+    _, W = bern_grad_W(y, b)
+    pre = FITCPrecond(vif, W)
+    HF = lambda w: w / W + Sigma_dagger_matvec(vif, w)
+    U, Yp = [], []
+    for e in np.atleast_2d(eps):
+        z = pre.sample(e[:m], e[m:m + n])
+        u, _, _, _, _ = pcg_lanczos(HF, pre.apply, z, tol, max_iter)
+        U.append(u)
+        Yp.append(pre.apply(z))
+    U, Yp = np.array(U), np.array(Yp)
+    ell = U.shape[0]
+    dW = bern_dW(b)
+    dhat = (U * Yp).mean(axis=0)
+    g = 0.5 * (dW / W - dW / W ** 2 * dhat)
+    sv, _, _ = pcg(HF, pre.apply, Sigma_dagger_matvec(vif, g), solve_tol, max_iter)
+    v = sv / W
+    a = vif.Sigma_dagger_inv(b)
+    av = vif.Sigma_dagger_inv(v)
+
+    def forms(vf):
+        Sa = Sigma_dagger_matvec(vf, a)
+        SY = np.array([Sigma_dagger_matvec(vf, yi) for yi in Yp])
+        pf = FITCPrecond(vf, W)
+        if vf.m:
+            lr = vf.lowrank
+            AY = Yp @ lr.Smn.T                        # rows Sigma_mn y_i
+            low = (AY * (Yp @ lr.SinvSmn.T)).sum(axis=1)
+        else:
+            low = np.zeros(ell)
+        return dict(aa=float(a @ Sa), va=float(av @ Sa), uy=(U * SY).sum(axis=1),
+                    yPy=(Yp * Yp * pf.DV[None, :]).sum(axis=1) + low, ldP=pf.logdet())
+
+    q = laplace_param_vector(theta).size
+    grad = np.empty(q)
+    S = np.empty((ell, q))
+    C = np.empty((ell, q))
+    tr_plain, c_opt, tau, trace = (np.empty(q) for _ in range(4))
+    for k, (h, vp, vm) in enumerate(_perturbed(X, Z, theta, N, rel_step)):
+        fp, fm = forms(vp), forms(vm)
+        d = {key: (fp[key] - fm[key]) / (2.0 * h) for key in fp}
+        S[:, k] = d["uy"]
+        C[:, k] = d["yPy"]
+        tau[k] = d["ldP"]
+        tr_plain[k] = S[:, k].mean()
+        dc = C[:, k] - tau[k]
+        den = float(dc @ dc)
+        c_opt[k] = float((S[:, k] - tr_plain[k]) @ dc) / den if den > 0 else 0.0
+        trace[k] = float((S[:, k] - c_opt[k] * C[:, k]).mean()) + c_opt[k] * tau[k]
+        grad[k] = -0.5 * d["aa"] + d["va"] + 0.5 * trace[k]
+    return dict(grad=grad, s=S, c=C, trace_plain=tr_plain, c_opt=c_opt, tau=tau, trace=trace, g=g, v=v,
+                dhat=dhat)
+
+
+def vifla_grad_exact_fitc(X, Z, theta, N, y, b, rel_step: float = 1e-4):
+    """vifla_grad_ste_fitc with every trace exact from dense matrices (small n): H_F^{-1} dense and
+    dSigma_k the central difference of the dense Sigma_dagger.  Equals vifla_grad_exact (the same
+    gradient through Sigma_dagger instead of its inverse)."""
+    vif = VIF(X, Z, theta, N)
+    _, W = bern_grad_W(y, b)
+    Sd = vif.dense_Sigma_dagger()
+    HFinv = np.linalg.inv(np.diag(1.0 / W) + Sd)
+    dW = bern_dW(b)
+    g = 0.5 * (dW / W - dW / W ** 2 * np.diag(HFinv))
+    v = (HFinv @ (Sd @ g)) / W
+    a = vif.Sigma_dagger_inv(b)
+    av = vif.Sigma_dagger_inv(v)
+    q = laplace_param_vector(theta).size
+    grad, trace = np.empty(q), np.empty(q)
+    for k, (h, vp, vm) in enumerate(_perturbed(X, Z, theta, N, rel_step)):
+        Dk = (vp.dense_Sigma_dagger() - vm.dense_Sigma_dagger()) / (2.0 * h)
+        trace[k] = float(np.sum(HFinv * Dk))
+        grad[k] = -0.5 * a @ Dk @ a + av @ Dk @ a + 0.5 * trace[k]
+    return dict(grad=grad, trace=trace, dHF=np.diag(HFinv), g=g, v=v)
 
 
 def dense_Sigma_dagger_inv(vif: VIF) -> np.ndarray:

@@ -496,6 +496,47 @@ def test_ste_gradient_is_unbiased_and_the_control_variate_reduces_its_variance()
     assert np.all(se_cv < 0.5 * se), (se_cv, se)
 
 
+def test_fitc_form_gradient_with_exact_traces_equals_the_vifdu_form():
+    """App. B / App. D second form: through Sigma_dagger and H_F = W^{-1} + Sigma_dagger (Eq. pcls2) the
+    assembled gradient is the same derivative of L^VIFLA as through Sigma_dagger^{-1} (pinned above to
+    finite differences of the likelihood)."""
+    P, N, vif, b = _lap_grad_problem()
+    ex = O.vifla_grad_exact(P.X, P.Z, P.theta, N, P.y, b)
+    exf = O.vifla_grad_exact_fitc(P.X, P.Z, P.theta, N, P.y, b)
+    np.testing.assert_allclose(exf["grad"], ex["grad"], rtol=2e-5, atol=1e-6)
+
+
+def test_fitc_ste_sums_are_exact_when_the_probes_span_the_preconditioner():
+    """FITC probes z = D_V^{1/2} eps2 + Sigma_mn^T L_m^{-T} eps1 with eps over the identity of R^(m+n):
+    sum z z^T = P exactly, so l times each STE average is the exact trace Tr(H_F^{-1} dSigma_k),
+    Tr(P^{-1} dP/dth_k) and diagonal (H_F^{-1})_jj."""
+    P, N, vif, b = _lap_grad_problem(n=40, m=5, mv=3, seed=23)
+    n, m = vif.n, vif.m
+    eps = np.eye(m + n)
+    ell = eps.shape[0]
+    r = O.vifla_grad_ste_fitc(P.X, P.Z, P.theta, N, P.y, b, eps, 1e-13, 1e-13)
+    exf = O.vifla_grad_exact_fitc(P.X, P.Z, P.theta, N, P.y, b)
+    np.testing.assert_allclose(ell * r["trace_plain"], exf["trace"], rtol=1e-8)
+    np.testing.assert_allclose(ell * r["c"].mean(axis=0), r["tau"], rtol=1e-8)
+    np.testing.assert_allclose(ell * r["dhat"], exf["dHF"], rtol=1e-9)
+
+
+def test_fitc_ste_gradient_is_unbiased_and_the_control_variate_reduces_its_variance():
+    P, N, vif, b = _lap_grad_problem()
+    n, m = vif.n, vif.m
+    ell = 200
+    eps = np.random.default_rng(9).standard_normal((ell, m + 2 * n))
+    r = O.vifla_grad_ste_fitc(P.X, P.Z, P.theta, N, P.y, b, eps, 1e-12, 1e-12)
+    exf = O.vifla_grad_exact_fitc(P.X, P.Z, P.theta, N, P.y, b)
+    se = r["s"].std(axis=0, ddof=1) / math.sqrt(ell)
+    se_c = r["c"].std(axis=0, ddof=1) / math.sqrt(ell)
+    se_cv = (r["s"] - r["c_opt"] * r["c"]).std(axis=0, ddof=1) / math.sqrt(ell)
+    assert np.all(np.abs(r["trace_plain"] - exf["trace"]) <= 4 * se), (r["trace_plain"], exf["trace"], se)
+    assert np.all(np.abs(r["c"].mean(axis=0) - r["tau"]) <= 4 * se_c)
+    assert np.all(np.abs(r["trace"] - exf["trace"]) <= 4 * se_cv), (r["trace"], exf["trace"], se_cv)
+    assert np.all(se_cv < 0.75 * se), (se_cv, se)
+
+
 def test_fd_gradient_with_full_conditioning_is_the_exact_gp_gradient():
     """m_v = n-1 makes the VIF likelihood the exact one, whose gradient is analytic."""
     P = small_problem(n=60, m=8, mv=59, nugget=0.1, kind="matern32", ls=0.2)
