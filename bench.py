@@ -316,14 +316,18 @@ def laplace_block(args, stream):
                   "q_std_over_mean": float(np.std(sl["q"]) / max(abs(np.mean(sl["q"])), 1e-300))}
     # its gradient in (sigma1^2, lambda) by stochastic trace estimation with the same 50 probes and the
     # preconditioner control variate (Sec. 4.1, App. B, App. D); standard errors of the plain and the
-    # control-variate trace estimates from the per-probe terms
+    # control-variate trace estimates from the per-probe terms.  The traces reuse the probes' CG
+    # solutions, which the gradient needs tighter than the log-determinant does: at the FITC form's
+    # delta = 0.01 the two forms' gradients differed by 30-40 %, so both run at 1e-4 here.
+    grad_tol = 1e-4
     t0 = time.perf_counter()
-    nll_g, grad, sg = ctx.laplace_nll_grad(P.theta, y, eps, slq_tol=slq_tol, rel_tol=1e-6)
+    nll_g, grad, sg = ctx.laplace_nll_grad(P.theta, y, eps, slq_tol=grad_tol, rel_tol=1e-6)
     wall_g = time.perf_counter() - t0
     pt, tr = sg["probe_terms"], sg["trace"]
     se_plain = pt[:, :, 0].std(axis=0, ddof=1) / np.sqrt(nprobe)
     se_cv = (pt[:, :, 0] - tr[None, :, 1] * pt[:, :, 1]).std(axis=0, ddof=1) / np.sqrt(nprobe)
-    out["grad"] = {"params": ["sigma1^2", "lambda"], "grad": grad.tolist(), "nll": nll_g, "wall_s": wall_g,
+    out["grad"] = {"params": ["sigma1^2", "lambda"], "cg_tol": grad_tol, "grad": grad.tolist(), "nll": nll_g,
+                   "wall_s": wall_g,
                    "ms_after_nll": sg["ms_grad"], "pcg_iters_v": sg["pcg_iters_v"],
                    "trace_plain": tr[:, 0].tolist(), "c_opt": tr[:, 1].tolist(), "tau": tr[:, 2].tolist(),
                    "trace_cv": tr[:, 3].tolist(), "se_plain": se_plain.tolist(), "se_cv": se_cv.tolist(),
@@ -342,6 +346,18 @@ def laplace_block(args, stream):
                            "logdet_exact_norm": slf["logdet_exact_norm"],
                            "pcg_iters_slq": slf["pcg_iters_slq"], "ms_slq": slf["ms_slq"],
                            "ms_per_probe": slf["ms_slq"] / nprobe}}
+    # the gradient in the FITC form (Eq. pcls2 / slq_v2, App. D second form), same normals
+    t0 = time.perf_counter()
+    nll_gf, grad_f, sgf = ctx.laplace_nll_grad(P.theta, y, eps, slq_tol=grad_tol, rel_tol=1e-6,
+                                               precond=V.PRECOND_FITC)
+    wall_gf = time.perf_counter() - t0
+    ptf, trf = sgf["probe_terms"], sgf["trace"]
+    out["fitc"]["grad"] = {
+        "cg_tol": grad_tol, "grad": grad_f.tolist(), "nll": nll_gf, "wall_s": wall_gf, "ms_after_nll": sgf["ms_grad"],
+        "diff_vs_vifdu_form": (grad_f - grad).tolist(),
+        "pcg_iters_v": sgf["pcg_iters_v"], "trace_cv": trf[:, 3].tolist(), "c_opt": trf[:, 1].tolist(),
+        "se_plain": (ptf[:, :, 0].std(axis=0, ddof=1) / np.sqrt(nprobe)).tolist(),
+        "se_cv": ((ptf[:, :, 0] - trf[None, :, 1] * ptf[:, :, 1]).std(axis=0, ddof=1) / np.sqrt(nprobe)).tolist()}
     # predictive means (Prop. 3.1) and SBPV variances (Alg. 1) at 1000 new points: 100 draws (the
     # paper's default), FITC solves at CG tolerance 0.01
     Xp = synth._rng(20250715).uniform(size=(1000, P.X.shape[1]))

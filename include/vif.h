@@ -194,7 +194,7 @@ vif_status vif_laplace_nll(vif_ctx *ctx, const vif_cov *theta, const double *y, 
 
 /* vif_laplace_nll_grad -- vif_laplace_nll (same arguments, same nll_out and stats->nll) and the
  * gradient of L with respect to (sigma1^2, lambda_1..lambda_{n_ls}) by stochastic trace estimation
- * (Sec. 4.1 after Eq. slq_v2; App. B "Gradients"; App. D), VIFDU form (opts->precond = 0 only):
+ * (Sec. 4.1 after Eq. slq_v2; App. B "Gradients"; App. D), in the VIFDU form (opts->precond = 0):
  *     dL/dth_k = b~^T Delta_k b~ / 2 + (dlog det Sigma_dagger/dth_k + T_k) / 2 - v^T Delta_k b~,
  * H = W + Sigma_dagger^{-1}, Delta_k = dSigma_dagger^{-1}/dth_k, the last term being dL/db~ . db~/dth_k
  * with db~/dth_k = -H^{-1} Delta_k b~ and v = H^{-1} dL/db~ (CG on Eq. pcls1 with the mode's rel_tol and
@@ -208,11 +208,18 @@ vif_status vif_laplace_nll(vif_ctx *ctx, const vif_cov *theta, const double *y, 
  * x^T Sigma_dagger^{-1} y and (B y)^T W (B y), of log det Sigma_dagger and of log det P) are central
  * differences with step 1e-4 |th_k|, holding N, Z, the mode b~ and W fixed: the factors are rebuilt
  * twice per parameter, and those of theta are restored before the call returns.
+ * FITC form (opts->precond = 2, Eq. pcls2 / slq_v2 and App. D's second form): with H_F = W^{-1} + Sigma_dagger,
+ * a = Sigma_dagger^{-1} b~, av = Sigma_dagger^{-1} v and dSigma_k = dSigma_dagger/dth_k,
+ *     dL/dth_k = -a^T dSigma_k a / 2 + av^T dSigma_k a + T_k / 2,   s_ik = u_i^T dSigma_k y_i,
+ *     dL/db~_j ~ (dW_jj/db_j / W_jj) (1 - (1/l) sum_i u_ij y_ij / W_jj) / 2,
+ * u_i = H_F^{-1} z_i, y_i = P^{-1} z_i with the FITC probes and P = D_V + Sigma_mn^T Sigma_m^{-1} Sigma_mn,
+ * c_ik = y_i^T (dP/dth_k) y_i, tau_k = dlog det P/dth_k, v = W^{-1} H_F^{-1} Sigma_dagger dL/db~ (CG on
+ * Eq. pcls2).
  *   grad_out: host, 1 + n_ls values (required).
  *   probe_terms: host, nprobe x (1 + n_ls) x 2 (s_ik, c_ik), or NULL.
  *   trace_out: host, (1 + n_ls) x 4 (mean_i s_ik, c_k, tau_k, T_k), or NULL.
  *   stats: host, may be NULL.
- * Errors as vif_laplace_nll; VIF_ERR_ARG for precond != 0. */
+ * Errors as vif_laplace_nll; VIF_ERR_ARG for precond = 1 (the learned correction). */
 typedef struct {
   vif_laplace_nll_stats nll;  /* as vif_laplace_nll */
   int32_t pcg_iters_v;        /* CG iterations of the solve v = H^{-1} dL/db~ */

@@ -63,6 +63,7 @@ struct vif_ctx {
   // gradient by stochastic trace estimation: probe solves U, P^{-1} z_i (g_cap x n each), dL/db~, v,
   // the bilinear forms of one perturbed theta (6 + 3 g_cap) and a three-way reduction scratch
   double *g_U = nullptr, *g_Y = nullptr, *g_g = nullptr, *g_v = nullptr, *g_sc = nullptr, *g_red = nullptr;
+  double *g_a = nullptr, *g_av = nullptr, *g_dv = nullptr;   // FITC form: Sigma_dagger^{-1} b~, .. v, D_V
   int64_t g_cap = 0;
   // block CG over up to mr_cap probes: n x L vectors, m x L and reduction scratch, per-column scalars
   double *mr_v = nullptr, *mr_x = nullptr, *mr_r = nullptr, *mr_z = nullptr, *mr_p = nullptr, *mr_Ap = nullptr,
@@ -294,7 +295,8 @@ void free_ctx(vif_ctx* c) {
                    c->l_x,    c->l_r,   c->l_z,    c->l_p,    c->l_Ap,   c->l_t,    c->l_t2,   c->l_x1,
                    c->l_sdi,  c->l_sm,  c->l_cm,   c->l_tm,   c->l_part, c->l_LinvC, c->l_G3,  c->l_LinvC3,
                    c->l_sc,   c->l_red, c->l_corr, c->sched_fwd, c->sched_rev, c->ord_fwd, c->ord_rev, c->ch_coef, c->slq_eps, c->l_Apad, c->l_anorm2, c->l_dvinv, c->l_pacc, c->l_counter, c->l_abort, c->m_feat,
-                   c->g_U,    c->g_Y,   c->g_g,    c->g_v,    c->g_sc,   c->g_red,
+                   c->g_U,    c->g_Y,   c->g_g,    c->g_v,    c->g_sc,   c->g_red,  c->g_a,    c->g_av,
+                   c->g_dv,
                    c->mr_v,   c->mr_x,  c->mr_r,   c->mr_z,   c->mr_p,   c->mr_Ap,  c->mr_t,   c->mr_t2,
                    c->mr_x1,  c->mr_sm, c->mr_cm,  c->mr_tm,  c->mr_part, c->mr_dpart, c->mr_sc, c->mr_active, c->mr_map,
                    c->m_gc,   c->m_part, c->m_grad};
@@ -1636,6 +1638,9 @@ vif_status grad_buffers(vif_ctx* ctx, int nprobe) {
   if (!ctx->g_g) {
     CKS(dalloc(ctx, &ctx->g_g, (size_t)n));
     CKS(dalloc(ctx, &ctx->g_v, (size_t)n));
+    CKS(dalloc(ctx, &ctx->g_a, (size_t)n));
+    CKS(dalloc(ctx, &ctx->g_av, (size_t)n));
+    CKS(dalloc(ctx, &ctx->g_dv, (size_t)n));
     CKS(dalloc(ctx, &ctx->g_red, 3 * 256));
   }
   return VIF_OK;
@@ -1682,6 +1687,57 @@ vif_status grad_forms(vif_ctx* ctx, const vif_cov* tk, LapOps& o, int nprobe, do
   return VIF_OK;
 }
 
+// The FITC form (Eq. pcls2) of grad_forms, at tk with N, Z, b~ and W fixed (out: 4 + 3 nprobe values):
+//   [0] log det D_V  [1] log det M_V  [2] a^T Sigma_dagger a  [3] av^T Sigma_dagger a
+//   [4 + i] u_i^T Sigma_dagger y_i  [4 + l + i] y_i^T D_V y_i  [4 + 2l + i] |A y_i|^2
+// (a = Sigma_dagger^{-1} b~ and av = Sigma_dagger^{-1} v at theta; y^T P y = y^T D_V y + |A y|^2).  The
+// probe terms are taken in blocks of up to LAP_MR_MAXL columns.
+vif_status grad_forms_fitc(vif_ctx* ctx, const vif_cov* tk, LapOps& o, int nprobe, double* out) {
+  cudaStream_t s = ctx->stream;
+  const int64_t n = ctx->n;
+  const int m = ctx->m;
+  CKS(lap_setup(ctx, tk, nullptr, &o));
+  o.kind = LAP_FITC;
+  CK(lap_pointwise(ctx->y, ctx->l_b, ctx->Dv, nullptr, n, ctx->l_W, ctx->l_v, ctx->l_Ginv, ctx->l_om, ctx->l_rsD,
+                   ctx->l_ll, s));
+  CKS(lap_fitc_setup(ctx, o, true, tk->variance));
+  double* gs = ctx->g_sc;
+  CK(lap_log_sum(ctx->l_dvinv, n, 1, -1.0, ctx->l_red, gs + 0, s));
+  if (m > 0) {
+    CK(lap_log_sum(ctx->l_G3, m, (int64_t)ctx->fpad + 1, 2.0, ctx->l_red, gs + 1, s));
+  } else {
+    CK(cudaMemsetAsync(gs + 1, 0, sizeof(double), s));
+  }
+  CK(lap_sigma_matvec(o, ctx->g_a, nullptr, ctx->l_sdi, s));
+  CK(lap_grad_forms(n, ctx->g_a, ctx->g_av, ctx->l_sdi, nullptr, nullptr, nullptr, ctx->g_red, gs + 2, gs + 3,
+                    nullptr, s));
+  CK(lap_recip(ctx->l_dvinv, n, ctx->g_dv, s));
+  for (int b0 = 0; b0 < nprobe; b0 += LAP_MR_MAXL) {
+    const int L = std::min(LAP_MR_MAXL, nprobe - b0);
+    LapMulti w;
+    CKS(mr_buffers(ctx, L, &w));
+    for (int j = 0; j < L; ++j) {
+      CK(lap_mr_column(n, L, j, ctx->mr_x, ctx->g_U + (size_t)(b0 + j) * n, false, s));
+      CK(lap_mr_column(n, L, j, ctx->mr_r, ctx->g_Y + (size_t)(b0 + j) * n, false, s));
+    }
+    CK(lap_mr_sigma_matvec(o, w, ctx->mr_r, ctx->mr_Ap, s, false));
+    CK(lap_mr_dot(w, n, ctx->mr_x, ctx->mr_Ap, gs + 4 + b0, s));
+    CK(lap_mr_scale2(w, n, ctx->g_dv, nullptr, ctx->mr_r, ctx->mr_z, s));
+    CK(lap_mr_dot(w, n, ctx->mr_z, ctx->mr_r, gs + 4 + nprobe + b0, s));
+    if (m > 0) {
+      CK(lap_mr_ftv(o, w, o.Apad, ctx->mr_r, w.sm, s));
+      CK(lap_mr_dot(w, m, w.sm, w.sm, gs + 4 + 2 * nprobe + b0, s));
+    } else {
+      CK(cudaMemsetAsync(gs + 4 + 2 * nprobe + b0, 0, L * sizeof(double), s));
+    }
+  }
+  CK(cudaMemcpyAsync(out, gs, (4 + 3 * (size_t)nprobe) * sizeof(double), cudaMemcpyDeviceToHost, s));
+  CK(cudaStreamSynchronize(s));
+  double dummy[1];
+  CKS(read_status(ctx, dummy, 0));
+  return VIF_OK;
+}
+
 }  // namespace
 
 extern "C" {
@@ -1705,8 +1761,9 @@ vif_status vif_laplace_nll_grad(vif_ctx* ctx, const vif_cov* theta, const double
   if (!ctx) return VIF_ERR_ARG;
   ctx->err[0] = 0;
   if (!theta || !lo || !grad_out) return set_err(ctx, VIF_ERR_ARG, "theta, opts and grad_out are required");
-  if (lo->precond != 0)
-    return set_err(ctx, VIF_ERR_ARG, "the gradient is implemented for the VIFDU preconditioner (precond 0)");
+  if (lo->precond != 0 && lo->precond != LAP_FITC)
+    return set_err(ctx, VIF_ERR_ARG, "the gradient takes the VIFDU (0) or the FITC (2) preconditioner");
+  const bool fitc = lo->precond == LAP_FITC;
   if (nprobe < 1) return set_err(ctx, VIF_ERR_ARG, "nprobe >= 1 is required");
   CKS(check_cov(ctx, theta, ctx->d));
   const int64_t n = ctx->n;
@@ -1719,19 +1776,32 @@ vif_status vif_laplace_nll_grad(vif_ctx* ctx, const vif_cov* theta, const double
   CKS(laplace_nll_core(ctx, theta, y, lo, nprobe, eps, slq_tol, slq_max_iter, nll_out, nullptr, nullptr, &st.nll,
                        &o, ctx->g_U, ctx->g_Y, &newton_ok, &cg_ok));
   const auto t0 = std::chrono::steady_clock::now();
-  // dL/db~_j = 1/2 Tr(H^{-1} dW/db_j) by the probe estimate, H = W + Sigma_dagger^{-1} (App. B), and
-  // v = H^{-1} dL/db~ by CG on Eq. pcls1 with the mode's options
-  CK(lap_ste_diag(n, nprobe, ctx->g_U, ctx->g_Y, ctx->l_b, ctx->l_v, s));
-  CK(cudaMemcpyAsync(ctx->g_g, ctx->l_v, n * sizeof(double), cudaMemcpyDeviceToDevice, s));
+  // dL/db~_j = 1/2 dlog det(Sigma_dagger W + I)/db_j by the probe estimate of the diagonal of
+  // (W + Sigma_dagger^{-1})^{-1} (VIFDU) or of (W^{-1} + Sigma_dagger)^{-1} (FITC) (App. B), and
+  // v = (W + Sigma_dagger^{-1})^{-1} dL/db~ by CG with the mode's options: on Eq. pcls1, or on Eq. pcls2
+  // as v = W^{-1} (W^{-1} + Sigma_dagger)^{-1} Sigma_dagger dL/db~
+  CK(lap_ste_diag(n, nprobe, ctx->g_U, ctx->g_Y, ctx->l_b, fitc ? 1 : 0, ctx->g_g, s));
+  if (fitc) {
+    CK(lap_sigma_matvec(o, ctx->g_g, nullptr, ctx->l_v, s));
+  } else {
+    CK(cudaMemcpyAsync(ctx->l_v, ctx->g_g, n * sizeof(double), cudaMemcpyDeviceToDevice, s));
+  }
   int vit = 0;
   double vrel = 0.0;
   bool vcap = false;
   CKS(lap_pcg(ctx, o, lo->rel_tol, lo->max_pcg, &vit, &vrel, &vcap));
   cg_ok = cg_ok && !vcap;
-  CK(cudaMemcpyAsync(ctx->g_v, ctx->l_x, n * sizeof(double), cudaMemcpyDeviceToDevice, s));
+  if (fitc) {
+    CK(lap_div(n, ctx->l_x, ctx->l_W, ctx->g_v, s));
+    // a = Sigma_dagger^{-1} b~ and av = Sigma_dagger^{-1} v at theta
+    CK(lap_matvec(o, ctx->l_b, nullptr, ctx->g_a, s));
+    CK(lap_matvec(o, ctx->g_v, nullptr, ctx->g_av, s));
+  } else {
+    CK(cudaMemcpyAsync(ctx->g_v, ctx->l_x, n * sizeof(double), cudaMemcpyDeviceToDevice, s));
+  }
   // central differences in each parameter (sigma1^2, lambda_1..), relative step 1e-4
   const int q = 1 + theta->n_ls;
-  const int nf = 6 + 3 * nprobe;
+  const int nf = (fitc ? 4 : 6) + 3 * nprobe;
   std::vector<double> fp((size_t)q * nf), fm((size_t)q * nf), hk(q);
   const std::vector<double> ls(theta->lengthscale, theta->lengthscale + theta->n_ls);
   for (int k = 0; k < q; ++k) {
@@ -1743,7 +1813,12 @@ vif_status vif_laplace_nll_grad(vif_ctx* ctx, const vif_cov* theta, const double
       const double h = 1e-4 * std::fabs(*par);
       hk[k] = h;
       *par += sgn ? -h : h;
-      CKS(grad_forms(ctx, &tk, o, nprobe, (sgn ? fm : fp).data() + (size_t)k * nf));
+      double* dst = (sgn ? fm : fp).data() + (size_t)k * nf;
+      if (fitc) {
+        CKS(grad_forms_fitc(ctx, &tk, o, nprobe, dst));
+      } else {
+        CKS(grad_forms(ctx, &tk, o, nprobe, dst));
+      }
     }
   }
   // leave the factors of theta (and the preconditioner pieces at the mode) in the context
@@ -1751,22 +1826,26 @@ vif_status vif_laplace_nll_grad(vif_ctx* ctx, const vif_cov* theta, const double
   CK(lap_pointwise(ctx->y, ctx->l_b, ctx->Dv, nullptr, n, ctx->l_W, ctx->l_v, ctx->l_Ginv, ctx->l_om, ctx->l_rsD,
                    ctx->l_ll, s));
   CK(cudaStreamSynchronize(s));
-  // assembly (App. B): dL/dth_k = 1/2 b~^T Delta_k b~ + 1/2 (dlogdet Sigma_dagger + T_k) - v^T Delta_k b~,
-  // T_k the control-variate estimate of Tr(H^{-1} Delta_k) (App. D)
+  // assembly (App. B, App. D), T_k the control-variate estimate of the trace:
+  //   VIFDU: dL/dth_k = 1/2 b~^T Delta_k b~ + 1/2 (dlog det Sigma_dagger + T_k) - v^T Delta_k b~,
+  //          s_ik = d(u_i^T Sigma_dagger^{-1} y_i), c_ik = d((B y_i)^T W (B y_i) + y_i^T Sigma_dagger^{-1} y_i)
+  //   FITC:  dL/dth_k = -1/2 a^T dSigma_k a + av^T dSigma_k a + 1/2 T_k,
+  //          s_ik = d(u_i^T Sigma_dagger y_i), c_ik = d(y_i^T D_V y_i + |A y_i|^2)
   for (int k = 0; k < q; ++k) {
     const double* P = fp.data() + (size_t)k * nf;
     const double* M = fm.data() + (size_t)k * nf;
     const double h2 = 2.0 * hk[k];
     auto d = [&](int j) { return (P[j] - M[j]) / h2; };
-    const double dlogdet_sigma = d(0) + d(1);
-    const double tau = d(2) - d(1) + d(3);   // dlogdet P = Tr(P^{-1} dP/dth_k)
+    const int o0 = fitc ? 4 : 6;
+    auto s_i = [&](int i) { return d(o0 + i); };
+    auto c_i = [&](int i) { return d(o0 + 2 * nprobe + i) + d(o0 + nprobe + i); };
+    const double tau = fitc ? d(0) + d(1) : d(2) - d(1) + d(3);   // dlog det P = Tr(P^{-1} dP/dth_k)
     double smean = 0.0;
-    for (int i = 0; i < nprobe; ++i) smean += d(6 + i);
+    for (int i = 0; i < nprobe; ++i) smean += s_i(i);
     smean /= nprobe;
     double num = 0.0, den = 0.0, cvmean = 0.0;
     for (int i = 0; i < nprobe; ++i) {
-      const double si = d(6 + i);
-      const double ci = d(6 + 2 * nprobe + i) + d(6 + nprobe + i);
+      const double si = s_i(i), ci = c_i(i);
       num += (si - smean) * (ci - tau);
       den += (ci - tau) * (ci - tau);
       if (probe_terms) {
@@ -1775,9 +1854,9 @@ vif_status vif_laplace_nll_grad(vif_ctx* ctx, const vif_cov* theta, const double
       }
     }
     const double copt = den > 0.0 ? num / den : 0.0;
-    for (int i = 0; i < nprobe; ++i) cvmean += d(6 + i) - copt * (d(6 + 2 * nprobe + i) + d(6 + nprobe + i));
+    for (int i = 0; i < nprobe; ++i) cvmean += s_i(i) - copt * c_i(i);
     const double T = cvmean / nprobe + copt * tau;
-    grad_out[k] = 0.5 * d(4) + 0.5 * (dlogdet_sigma + T) - d(5);
+    grad_out[k] = fitc ? -0.5 * d(2) + d(3) + 0.5 * T : 0.5 * d(4) + 0.5 * (d(0) + d(1) + T) - d(5);
     if (trace_out) {
       trace_out[(size_t)k * 4 + 0] = smean;
       trace_out[(size_t)k * 4 + 1] = copt;

@@ -224,6 +224,7 @@ cudaError_t lap_system_matvec(const LapOps& o, const double* x, double* out, cud
 cudaError_t lap_system_precond(const LapOps& o, const double* w, double* out, cudaStream_t s);
 cudaError_t lap_fitc_probe(const LapOps& o, const double* eps1, const double* eps2, double* z, cudaStream_t s);
 cudaError_t lap_div(int64_t n, const double* x, const double* d, double* out, cudaStream_t s);
+cudaError_t lap_recip(const double* a, int64_t n, double* out, cudaStream_t s);
 cudaError_t lap_bx_scaled(const LapOps& o, const double* x, double* t, cudaStream_t s);
 cudaError_t lap_ftv(const double* F, int fpad, int m, int64_t n, const double* v, double* partial, double* out,
                     cudaStream_t s);
@@ -250,7 +251,12 @@ struct LapMulti {
 };
 cudaError_t lap_mr_matvec(const LapOps& o, const LapMulti& w, const double* X, double* out, cudaStream_t s);
 cudaError_t lap_mr_precond(const LapOps& o, const LapMulti& w, const double* R, double* out, cudaStream_t s);
-cudaError_t lap_mr_sigma_matvec(const LapOps& o, const LapMulti& w, const double* X, double* out, cudaStream_t s);
+cudaError_t lap_mr_sigma_matvec(const LapOps& o, const LapMulti& w, const double* X, double* out, cudaStream_t s,
+                                bool add_winv);
+cudaError_t lap_mr_scale2(const LapMulti& w, int64_t n, const double* a, const double* b, const double* x,
+                          double* out, cudaStream_t s);
+cudaError_t lap_mr_ftv(const LapOps& o, const LapMulti& w, const double* F, const double* T, double* out,
+                       cudaStream_t s);
 cudaError_t lap_mr_precond_fitc(const LapOps& o, const LapMulti& w, const double* R, double* out, cudaStream_t s);
 cudaError_t lap_mr_system_matvec(const LapOps& o, const LapMulti& w, const double* X, double* out, cudaStream_t s);
 cudaError_t lap_mr_system_precond(const LapOps& o, const LapMulti& w, const double* R, double* out, cudaStream_t s);
@@ -269,7 +275,7 @@ cudaError_t lap_mr_gather(int64_t n, int Ls, int Ld, const int* map, const doubl
 cudaError_t lap_mr_copy_col(int64_t n, const double* src, int Ls, int js, double* dst, int Ld, int jd,
                             cudaStream_t s);
 // gradient of the VIF-Laplace likelihood (Sec. 4.1, App. B, App. D)
-cudaError_t lap_ste_diag(int64_t n, int l, const double* U, const double* Y, const double* b, double* g,
+cudaError_t lap_ste_diag(int64_t n, int l, const double* U, const double* Y, const double* b, int form, double* g,
                          cudaStream_t s);
 cudaError_t lap_grad_forms(int64_t n, const double* a, const double* c, const double* x, const double* t,
                            const double* w, const double* d, double* partial, double* out0, double* out1,

@@ -748,10 +748,12 @@ cudaError_t lap_beta(double* sc, cudaStream_t s) {
 // differences in theta give the traces.
 // ---------------------------------------------------------------------------
 
-// g_i = 1/2 dW_ii/db_i (1/l) sum_j U[j][i] Y[j][i]   (U, Y: l x n, probe-major), the Bernoulli-logit
-// dW/db = p (1 - p)(1 - 2p), p = sigmoid(b_i)
+// With dhat_i = (1/l) sum_j U[j][i] Y[j][i] (U, Y: l x n, probe-major) and the Bernoulli-logit
+// W = p (1 - p), dW/db = p (1 - p)(1 - 2p), p = sigmoid(b_i):
+//   form 0 (VIFDU, dhat ~ (W + Sigma_dagger^{-1})^{-1}_ii):  g_i = 1/2 dW/db dhat_i
+//   form 1 (FITC, dhat ~ (W^{-1} + Sigma_dagger)^{-1}_ii):   g_i = 1/2 dW/db (1 - dhat_i / W) / W
 __global__ void ste_diag_kernel(int64_t n, int l, const double* __restrict__ U, const double* __restrict__ Y,
-                                const double* __restrict__ b, double* g) {
+                                const double* __restrict__ b, int form, double* g) {
   const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n) return;
   double s0 = 0.0, s1 = 0.0;
@@ -762,7 +764,8 @@ __global__ void ste_diag_kernel(int64_t n, int l, const double* __restrict__ U, 
   }
   if (j < l) s0 = fma(U[(size_t)j * n + i], Y[(size_t)j * n + i], s0);
   const double p = 1.0 / (1.0 + exp(-b[i]));
-  g[i] = 0.5 * p * (1.0 - p) * (1.0 - 2.0 * p) * (s0 + s1) / l;
+  const double w = p * (1.0 - p), dw = w * (1.0 - 2.0 * p), dhat = (s0 + s1) / l;
+  g[i] = form == 0 ? 0.5 * dw * dhat : 0.5 * dw * (1.0 - dhat / w) / w;
 }
 
 // per block: sum a_i x_i, sum c_i x_i and (t != NULL) sum t_i^2 w_i d_i, into partial[k * 256 + block]
@@ -814,9 +817,9 @@ __global__ void forms_stage2(const double* partial, double* out0, double* out1, 
   if (threadIdx.x == 0) *out = sh[0];
 }
 
-cudaError_t lap_ste_diag(int64_t n, int l, const double* U, const double* Y, const double* b, double* g,
+cudaError_t lap_ste_diag(int64_t n, int l, const double* U, const double* Y, const double* b, int form, double* g,
                          cudaStream_t s) {
-  ste_diag_kernel<<<blocks(n, 256), 256, 0, s>>>(n, l, U, Y, b, g);
+  ste_diag_kernel<<<blocks(n, 256), 256, 0, s>>>(n, l, U, Y, b, form, g);
   return cudaGetLastError();
 }
 
@@ -1274,8 +1277,10 @@ __global__ void mr_add_div_kernel(int64_t n, int L, const double* __restrict__ t
   out[e] = t[e] + x[e] / d[e / L];
 }
 
-// FITC form (Eq. pcls2): out = (W^{-1} + Sigma_dagger) X = B^{-1} (D o B^{-T} X) + A^T (A X) + X / W
-cudaError_t lap_mr_sigma_matvec(const LapOps& o, const LapMulti& w, const double* X, double* out, cudaStream_t s) {
+// FITC form (Eq. pcls2): out = (W^{-1} + Sigma_dagger) X = B^{-1} (D o B^{-T} X) + A^T (A X) + X / W, or
+// Sigma_dagger X alone (add_winv = false)
+cudaError_t lap_mr_sigma_matvec(const LapOps& o, const LapMulti& w, const double* X, double* out, cudaStream_t s,
+                                bool add_winv) {
   const size_t bytes = (size_t)o.n * w.L * sizeof(double);
   cudaError_t e = cudaSuccess;
   if (o.mv > 0) {
@@ -1291,7 +1296,11 @@ cudaError_t lap_mr_sigma_matvec(const LapOps& o, const LapMulti& w, const double
   } else {
     mr_scale2_kernel<<<mr_blocks(o.n, w.L), 256, 0, s>>>(o.n, w.L, o.D, nullptr, X, w.t);
   }
-  mr_add_div_kernel<<<mr_blocks(o.n, w.L), 256, 0, s>>>(o.n, w.L, w.t, X, o.W, w.t2);
+  if (add_winv) {
+    mr_add_div_kernel<<<mr_blocks(o.n, w.L), 256, 0, s>>>(o.n, w.L, w.t, X, o.W, w.t2);
+  } else if ((e = cudaMemcpyAsync(w.t2, w.t, bytes, cudaMemcpyDeviceToDevice, s)) != cudaSuccess) {
+    return e;
+  }
   if (o.m > 0) {
     mr_ftv(o, w, o.Apad, X, w.sm, s);
     mr_f_dot(o, w, o.Apad, w.sm, w.t2, 1.0, nullptr, nullptr, out, s);
@@ -1315,11 +1324,23 @@ cudaError_t lap_mr_precond_fitc(const LapOps& o, const LapMulti& w, const double
 }
 
 cudaError_t lap_mr_system_matvec(const LapOps& o, const LapMulti& w, const double* X, double* out, cudaStream_t s) {
-  return o.kind == LAP_FITC ? lap_mr_sigma_matvec(o, w, X, out, s) : lap_mr_matvec(o, w, X, out, s);
+  return o.kind == LAP_FITC ? lap_mr_sigma_matvec(o, w, X, out, s, true) : lap_mr_matvec(o, w, X, out, s);
 }
 
 cudaError_t lap_mr_system_precond(const LapOps& o, const LapMulti& w, const double* R, double* out, cudaStream_t s) {
   return o.kind == LAP_FITC ? lap_mr_precond_fitc(o, w, R, out, s) : lap_mr_precond(o, w, R, out, s);
+}
+
+cudaError_t lap_mr_scale2(const LapMulti& w, int64_t n, const double* a, const double* b, const double* x,
+                          double* out, cudaStream_t s) {
+  mr_scale2_kernel<<<mr_blocks(n, w.L), 256, 0, s>>>(n, w.L, a, b, x, out);
+  return cudaGetLastError();
+}
+
+cudaError_t lap_mr_ftv(const LapOps& o, const LapMulti& w, const double* F, const double* T, double* out,
+                       cudaStream_t s) {
+  mr_ftv(o, w, F, T, out, s);
+  return cudaGetLastError();
 }
 
 cudaError_t lap_mr_dot(const LapMulti& w, int64_t n, const double* a, const double* b, double* out, cudaStream_t s) {

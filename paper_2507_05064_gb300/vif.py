@@ -359,13 +359,14 @@ class Context:
         return out.value, stats
 
     def laplace_nll_grad(self, theta, y, eps, slq_tol=1e-2, slq_max_iter=1000, rel_tol=1e-6, max_pcg=1000,
-                         max_newton=50, allow_not_converged=False):
-        """VIF-Laplace NLL (as laplace_nll, VIFDU) and its gradient in (sigma1^2, lambda...) by
-        stochastic trace estimation with the preconditioner control variate (Sec. 4.1, App. B, App. D).
+                         max_newton=50, precond=0, allow_not_converged=False):
+        """VIF-Laplace NLL (as laplace_nll; precond 0 = VIFDU, 2 = FITC) and its gradient in
+        (sigma1^2, lambda...) by stochastic trace estimation with the preconditioner control variate
+        (Sec. 4.1, App. B, App. D).
         Returns (nll, grad, stats dict with 'probe_terms' (nprobe, q, 2) = (s_ik, c_ik) and 'trace'
         (q, 4) = (plain mean, c_k, tau_k, T_k))."""
         cv, ls = make_cov(theta)
-        opts = LaplaceOpts(float(rel_tol), int(max_pcg), int(max_newton), 0, 0, None)
+        opts = LaplaceOpts(float(rel_tol), int(max_pcg), int(max_newton), int(precond), 0, None)
         e = _f64(eps)
         nprobe = int(e.shape[0])
         q = 1 + int(cv.n_ls)

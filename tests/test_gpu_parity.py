@@ -398,12 +398,41 @@ def test_vifla_gradient_degenerate_structures_match_oracle(m, mv):
     ctx.close()
 
 
-def test_vifla_gradient_rejects_fitc_and_learned_preconditioners():
+@pytest.mark.parametrize("ard", [False, True])
+def test_vifla_gradient_fitc_form_matches_oracle_probe_by_probe(ard):
+    """App. D second form (Eq. pcls2 / slq_v2): FITC probes and their CG solutions reused, bilinear
+    forms of Sigma_dagger at the perturbed theta (block solves), the FITC control variate; s_ik, c_ik,
+    the traces and the gradient agree with the oracle (isotropic and ARD ranges)."""
+    P = bern(1200, 20, 8, 47)
+    if ard:
+        P.theta.lengthscale = np.array([0.08, 0.13])
+    N = O.causal_neighbors(P.X, P.Z, P.theta, 8)
+    vif = O.VIF(P.X, P.Z, P.theta, N)
+    b_dense, _, _ = O.laplace_mode(vif, P.y, dense=True, psi_tol=1e-14)
+    ctx = V.Context(P.X, P.Z, 8, P.theta, likelihood=V.BERNOULLI_LOGIT, neighbor_search=False)
+    ctx.set_neighbors(N.astype(np.int32))
+    eps = synth.slq_normals(5, vif.m, vif.n, seed=7)
+    nll, grad, st = ctx.laplace_nll_grad(P.theta, P.y, eps, slq_tol=1e-10, rel_tol=1e-10, precond=V.PRECOND_FITC)
+    ref = O.vifla_grad_ste_fitc(P.X, P.Z, P.theta, N, P.y, b_dense, eps, 1e-10, 1e-10)
+    q = 1 + np.atleast_1d(P.theta.lengthscale).size
+    terms = st["probe_terms"]
+    for k in range(q):
+        sc = np.abs(ref["s"][:, k]).max()
+        cc = np.abs(ref["c"][:, k]).max()
+        np.testing.assert_allclose(terms[:, k, 0], ref["s"][:, k], rtol=1e-6, atol=1e-7 * sc)
+        np.testing.assert_allclose(terms[:, k, 1], ref["c"][:, k], rtol=1e-6, atol=1e-7 * cc)
+    np.testing.assert_allclose(st["trace"][:, 2], ref["tau"], rtol=1e-6)
+    np.testing.assert_allclose(st["trace"][:, 3], ref["trace"], rtol=1e-6, atol=1e-7 * np.abs(ref["s"]).max())
+    np.testing.assert_allclose(grad, ref["grad"], rtol=1e-5, atol=1e-6 * np.abs(ref["grad"]).max())
+    ctx.close()
+
+
+def test_vifla_gradient_rejects_the_learned_preconditioner():
     P, vif, b_dense, ctx = _vifla_case(300, 10, 5, 44)
     eps = synth.slq_normals(2, vif.m, vif.n, seed=8)
     cv, ls = V.make_cov(P.theta)
     import ctypes as C
-    for pre in (1, 2):
+    for pre in (1,):
         opts = V.LaplaceOpts(1e-6, 100, 20, pre, 0, None)
         g = np.zeros(2)
         out = C.c_double()
