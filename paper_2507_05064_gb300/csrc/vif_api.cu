@@ -847,7 +847,7 @@ vif_status vif_nll(vif_ctx* ctx, const vif_cov* theta, const double* y, double* 
   CKS(upload(ctx, ctx->y, y, (size_t)ctx->n * sizeof(double)));
   if (grad_out) {
     // central differences of the float64 likelihood, one parameter at a time
-    double *A64, *F64, *LT64;
+    double *A64 = nullptr, *F64 = nullptr, *LT64 = nullptr;
     CKS(fp64_buffers(ctx, &A64, &F64, &LT64));
     const int q = theta->n_ls + 2;
     std::vector<double> ls(theta->lengthscale, theta->lengthscale + theta->n_ls);
@@ -895,7 +895,7 @@ vif_status vif_predict(vif_ctx* ctx, const vif_cov* theta, const double* y, cons
   if (ctx->mv > 48) return set_err(ctx, VIF_ERR_ARG, "m_v too large for prediction");
   const int64_t n = ctx->n;
   const int d = ctx->d, m = ctx->m, mpad = ctx->mpad, fpad = ctx->fpad, mv = ctx->mv;
-  double *A64, *F64, *LT64;
+  double *A64 = nullptr, *F64 = nullptr, *LT64 = nullptr;
   CKS(fp64_buffers(ctx, &A64, &F64, &LT64));
   CKS(predict_buffers(ctx, np));
   CovParams cp = cov_params(theta);
@@ -926,7 +926,7 @@ namespace {
 // (y: host or device responses, or NULL to keep those already on the device).
 vif_status lap_setup(vif_ctx* ctx, const vif_cov* theta, const double* y, LapOps* o) {
   cudaStream_t s = ctx->stream;
-  double *A64, *F64, *LT64;
+  double *A64 = nullptr, *F64 = nullptr, *LT64 = nullptr;
   CKS(fp64_buffers(ctx, &A64, &F64, &LT64));
   CKS(lap_alloc(ctx));
   CovParams cp = cov_params(theta);
@@ -1512,7 +1512,7 @@ vif_status laplace_nll_core(vif_ctx* ctx, const vif_cov* theta, const double* y,
   CK(cudaStreamSynchronize(s));
   memcpy(h, ctx->h_pin + 32, sizeof(h));
   // probes
-  double *A64, *F64, *LT64;
+  double *A64 = nullptr, *F64 = nullptr, *LT64 = nullptr;
   CKS(fp64_buffers(ctx, &A64, &F64, &LT64));
   if (!ctx->slq_eps) CKS(dalloc(ctx, &ctx->slq_eps, (size_t)m + 2 * (size_t)n));
   const size_t per = (size_t)m + 2 * (size_t)n;
@@ -1889,7 +1889,7 @@ vif_status vif_laplace_predict(vif_ctx* ctx, const vif_cov* theta, const double*
   const int d = ctx->d, m = ctx->m, mpad = ctx->mpad, fpad = ctx->fpad, mv = ctx->mv;
   cudaStream_t s = ctx->stream;
   const bool fitc = lo->precond == LAP_FITC;
-  double *A64, *F64, *LT64;
+  double *A64 = nullptr, *F64 = nullptr, *LT64 = nullptr;
   CKS(fp64_buffers(ctx, &A64, &F64, &LT64));
   CKS(predict_buffers(ctx, np));
   if (!ctx->l_pacc) CKS(dalloc(ctx, &ctx->l_pacc, (size_t)np));
