@@ -157,7 +157,8 @@ vif_status vif_laplace_mode(vif_ctx *ctx, const vif_cov *theta, const double *y,
  * in closed form (App. E.1), T_i the Lanczos tridiagonal matrix defined by the coefficients
  * of preconditioned CG on (W + Sigma_dagger^{-1}) x = z_i (from x = 0, stopping at
  * ||z_i - (W + Sigma_dagger^{-1}) x||_2 <= slq_tol ||z_i||_2 or after slq_max_iter steps),
- * and z_i ~ N(0, P) drawn by the recipe of Sec. 4.3,
+ * and z_i ~ N(0, P) drawn by the recipe of Sec. 4.3 (the probes' CGs run side by side in blocks of up to
+ * 64, each with its own coefficients and stopping test, sharing the operator applications),
  *     z_i = B^T W'^{1/2} eps3 + Sigma_dagger^{-1} (B^{-1} D^{1/2} eps2 + Sigma_mn^T L_m^{-T} eps1)
  * (Sigma_m = L_m L_m^T), from the standard normal numbers the caller supplies.
  *   eps: nprobe x (m + 2n) row-major float64 (host or device); row i is (eps1 (m), eps2 (n),
