@@ -65,7 +65,7 @@ def config_dict(P, n_gpus):
     return {"workload": f"vif-nll-se-ard-n{P.X.shape[0]}-d8-m{P.Z.shape[0]}-mv{P.mv}",
             "n": int(P.X.shape[0]), "d": int(P.X.shape[1]), "m": int(P.Z.shape[0]), "m_v": int(P.mv),
             "kernel": "squared-exponential ARD", "nugget": P.theta.nugget,
-            "l2": "inputs larger than L2 (A alone is n*m*4 B = 1 GB)",
+            "l2": f"inputs larger than L2 (A alone is n*m*4 B = {P.X.shape[0] * P.Z.shape[0] * 4 / 1e9:.2f} GB)",
             "parallelism": f"replicas x{n_gpus}"}
 
 
