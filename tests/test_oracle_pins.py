@@ -496,6 +496,60 @@ def test_ste_gradient_is_unbiased_and_the_control_variate_reduces_its_variance()
     assert np.all(se_cv < 0.5 * se), (se_cv, se)
 
 
+def _gp_laplace_gradient_textbook(X, y, theta):
+    """Gradient of -log q(y | X, theta) of the exact-GP Laplace approximation for Bernoulli-logit
+    responses in the K form of Rasmussen & Williams (2006): the mode by the Newton step of Alg. 3.1,
+    the gradient with the structure of Alg. 5.1, i.e. the explicit part 1/2 a^T C a -
+    1/2 tr((W^{-1} + K)^{-1} C) (a = grad log p at the mode, C = dK/dth) plus s2^T df/dth with
+    df/dth = (I + K W)^{-1} C grad log p and s2_i = dlog q/df_i = -1/2 dlog|I + K W|/df_i
+    = 1/2 [(K^{-1} + W)^{-1}]_ii d^3 log p/df_i^3 (dW/df = -d^3 log p/df^3)."""
+    n = len(y)
+    K = O.exact_cov(X, theta)
+    f = np.zeros(n)
+    for _ in range(100):
+        p = 1.0 / (1.0 + np.exp(-f))
+        W = p * (1 - p)
+        g = y - p
+        f_new = K @ np.linalg.solve(np.eye(n) + W[:, None] * K, W * f + g)
+        if np.max(np.abs(f_new - f)) < 1e-13:
+            f = f_new
+            break
+        f = f_new
+    p = 1.0 / (1.0 + np.exp(-f))
+    W = p * (1 - p)
+    g = y - p
+    d3 = -W * (1 - 2 * p)                                      # third derivative of log p
+    R = np.linalg.inv(np.diag(1.0 / W) + K)                     # (W^{-1} + K)^{-1}
+    Sig = np.linalg.inv(np.linalg.inv(K) + np.diag(W))          # (K^{-1} + W)^{-1}
+    s2 = 0.5 * np.diag(Sig) * d3
+    Xs = O.scaled(X, theta)
+    r = O.dist(Xs, Xs)
+    dK = O.dcov_of_r(r, theta.kind, theta.variance)
+    lam = float(np.atleast_1d(theta.lengthscale)[0])
+    mats = [O.cov_of_r(r, theta.kind, theta.variance) / theta.variance, -dK * r / lam]
+    grad = []
+    for C in mats:
+        s1 = 0.5 * g @ C @ g - 0.5 * np.sum(R * C)
+        b = C @ g
+        s3 = b - K @ (R @ b)
+        grad.append(-(s1 + s2 @ s3))
+    return np.array(grad)
+
+
+def test_vifla_gradient_with_full_conditioning_is_the_textbook_gp_laplace_gradient():
+    """With m_v = n - 1 the VIF is the exact GP (Sigma_dagger = Sigma), so the App. B gradient with exact
+    traces must be the textbook GP-Laplace gradient (Rasmussen & Williams Alg. 5.1, a different
+    derivation: K form, its own Newton mode)."""
+    n = 40
+    P = small_problem(n=n, m=5, mv=n - 1, nugget=0.0, likelihood="bernoulli_logit", ls=0.2, seed=27)
+    N = O.causal_neighbors(P.X, P.Z, P.theta, n - 1)
+    vif = O.VIF(P.X, P.Z, P.theta, N)
+    b, _, _ = O.laplace_mode(vif, P.y, dense=True, psi_tol=1e-14)
+    ex = O.vifla_grad_exact(P.X, P.Z, P.theta, N, P.y, b)
+    tb = _gp_laplace_gradient_textbook(P.X, P.y, P.theta)
+    np.testing.assert_allclose(ex["grad"], tb, rtol=1e-5, atol=1e-7)
+
+
 def test_fitc_form_gradient_with_exact_traces_equals_the_vifdu_form():
     """App. B / App. D second form: through Sigma_dagger and H_F = W^{-1} + Sigma_dagger (Eq. pcls2) the
     assembled gradient is the same derivative of L^VIFLA as through Sigma_dagger^{-1} (pinned above to
