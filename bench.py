@@ -172,6 +172,22 @@ NCU_DRAM_BYTES_PER_POINT = {
 }
 
 
+def host_cpu() -> str:
+    """Architecture and CPU model of the host (lscpu's model name when lscpu is present)."""
+    import platform
+    import subprocess
+    model = ""
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for ln in out.splitlines():
+            if ln.lower().startswith("model name"):
+                model = ln.split(":", 1)[1].strip()
+                break
+    except (OSError, subprocess.SubprocessError):
+        pass
+    return f"{platform.machine()}, {model or platform.processor() or 'unknown model'}"
+
+
 def cpu_baseline(P, n_s, steps=1):
     """Oracle NLL on the first n_s points (same m, m_v, d, kernel) -> evals/s of the
     full workload by linear scaling in n (the per-eval cost is O(n))."""
@@ -190,7 +206,7 @@ def cpu_baseline(P, n_s, steps=1):
         O.VIF(Xs, P.Z, P.theta, N).nll(ys)
         ts.append(time.time() - t0)
     t = statistics.median(ts)
-    return {"value": 1.0 / (t * n / n_s), "unit": UNIT, "cores": os.cpu_count(), "kind": "oracle",
+    return {"value": 1.0 / (t * n / n_s), "unit": UNIT, "cores": os.cpu_count(), "kind": "oracle", "host": host_cpu(),
             "sample": f"oracle NLL on the first {n_s} of {n} points (m={P.Z.shape[0]}, m_v={P.mv}, d=8), "
                       f"{t:.2f} s per sample eval, scaled by n/{n_s}"}
 
@@ -403,7 +419,7 @@ def run_reference(args, rank, world):
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
             "data": "synthetic", "config": config_dict(P, 1),
             "cpu_baseline": {"value": v, "unit": UNIT, "cores": os.cpu_count(), "kind": "oracle",
-                             "sample": cb["sample"]},
+                             "host": cb["host"], "sample": cb["sample"]},
             "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
             "wall_s": wall}
     print(json.dumps(line), flush=True)

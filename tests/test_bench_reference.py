@@ -29,6 +29,7 @@ def test_reference_arm_prints_one_contract_line():
     assert d["steps"] == 1 and d["warmup"] == 1 and d["vs_baseline"] is None
     assert d["cpu_baseline"]["kind"] == "oracle" and d["cpu_baseline"]["value"] == d["value"]
     assert d["cpu_baseline"]["cores"] >= 1 and "2000" in d["cpu_baseline"]["sample"]
+    assert isinstance(d["cpu_baseline"].get("host"), str) and d["cpu_baseline"]["host"]
     assert d["e2e"] == {"value": d["value"], "unit": d["unit"], "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}
     assert d["config"]["workload"] == "vif-nll-se-ard-n20000-d8-m500-mv20"
 
