@@ -510,13 +510,16 @@ def run_vif(args, rank, world, dist):
             "algorithmic_flops_per_launch": flops, "algorithmic_bytes_per_launch": byts,
             "hbm_achieved_gbs": byts / (med[dom] * 1e-3) / 1e9,
             "hbm_peak_gbs_measured": pk.get("hbm_gbs")}
+    # the side blocks (Laplace rows, C1/C2, the oracle on the host cores) run at N = 1 only: at N > 1
+    # the other GPUs would idle meanwhile and the CPU baseline is a single-GPU-run figure
+    single = world == 1
     lap = None
-    if not args.no_laplace:
+    if not args.no_laplace and single:
         lap = laplace_block(args, stream)
     bat = batch_block(args, stream) if args.batch > 0 else None
-    small = None if args.no_small else small_configs_block(stream)
+    small = None if (args.no_small or not single) else small_configs_block(stream)
     cb = None
-    if not args.no_cpu_baseline:
+    if not args.no_cpu_baseline and single:
         cb = cpu_baseline(P, min(args.cpu_sample, P.X.shape[0]))
     scale = max(abs(nll64), 0.5 * P.X.shape[0] * math.log(2 * math.pi))
     line = {
