@@ -199,13 +199,6 @@ def causal_neighbors(X, Z, theta, mv: int, return_keys: bool = False):
     return N
 
 
-def query_keys(i: int, X, lowrank: LowRank, cr, theta, upto: int | None = None):
-    """Keys of point i against candidates 0..upto-1 (default: its predecessors)."""
-    upto = i if upto is None else upto
-    lr = (lowrank.Smn[:, :upto].T @ lowrank.SinvSmn[:, i]) if lowrank.m else np.zeros(upto)
-    return corr_keys(X[i], cr[i], X[:upto], cr[:upto], theta, lr)
-
-
 def causal_neighbors_sample(X, Z, theta, mv: int, queries, chunk: int = 65536):
     """N(i) and all keys of selected queries only, streaming over the predecessors
     in chunks (the same definition as causal_neighbors, for full-size checks)."""

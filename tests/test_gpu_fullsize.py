@@ -9,6 +9,7 @@ import pytest
 from oracle import vif_oracle as O
 from paper_2507_05064_gb300 import synth
 from paper_2507_05064_gb300 import vif as V
+from tolerance import nll_close
 
 pytestmark = pytest.mark.gpu
 TIE_TOL = 1e-9
@@ -24,10 +25,6 @@ def preceding_neighbors(n, mv):
     N[mv + 1:] = i[:, None] - mv + np.arange(mv)[None, :]
     N[mv, :] = np.arange(mv)
     return N
-
-
-def scale_close(got, ref, n, rtol):
-    return abs(got - ref) <= rtol * max(abs(ref), 0.5 * n * np.log(2 * np.pi))
 
 
 @pytest.fixture(scope="module", params=["c3", "c2"])
@@ -74,6 +71,6 @@ def test_sampled_factor_rows_and_full_likelihood(workload):
         nll = ctx.nll(P.theta, P.y)
         Ac, D = ctx.factors()
         ctx.close()
-        assert scale_close(nll, ref, n, rtol_nll), (name, prec, nll, ref)
+        assert nll_close(nll, ref, n, rtol_nll), (name, prec, nll, ref)
         np.testing.assert_allclose(D[rows], D_or, rtol=rtol_f)
         np.testing.assert_allclose(Ac[rows], A_or, rtol=rtol_f, atol=rtol_f * np.abs(A_or).max())

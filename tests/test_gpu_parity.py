@@ -1,7 +1,8 @@
 """GPU (CUDA path through the C ABI) against the FP64 oracle, element by element.
 
 Tolerances: float64 path 1e-8 relative on the likelihood; mixed path 1e-5
-relative; neighbour sets exact up to near-ties (two candidates whose oracle keys
+relative (plain relative error, except for likelihoods that cancel to below a
+tenth of n/2 log 2 pi: tests/tolerance.py); neighbour sets exact up to near-ties (two candidates whose oracle keys
 differ by less than TIE_TOL may be exchanged).
 """
 import json
@@ -13,6 +14,7 @@ import pytest
 from oracle import vif_oracle as O
 from paper_2507_05064_gb300 import synth
 from paper_2507_05064_gb300 import vif as V
+from tolerance import nll_close
 
 pytestmark = pytest.mark.gpu
 
@@ -20,14 +22,6 @@ GOLD = os.path.join(os.path.dirname(__file__), "golden")
 TIE_TOL = 1e-9
 RTOL64 = 1e-8
 RTOL_MIXED = 1e-5
-
-
-def nll_close(got, ref, n, rtol):
-    """|got - ref| <= rtol * max(|ref|, n/2 log 2 pi): relative to the likelihood's own
-    scale, which is a sum of n terms; this keeps the bound meaningful when the
-    terms cancel to a small total."""
-    scale = max(abs(ref), 0.5 * n * np.log(2 * np.pi))
-    return abs(got - ref) <= rtol * scale
 
 
 def prob(n, d, m, mv, kind, nugget, ls, seed, inducing="kmeans++"):

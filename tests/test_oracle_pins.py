@@ -114,6 +114,25 @@ def test_knn_matches_dense_residual_correlation_brute_force():
         assert list(N[i, :q]) == list(ref), i
 
 
+@pytest.mark.parametrize("m,kind,d", [(20, "matern32", 2), (0, "matern32", 2), (12, "se", 3)])
+def test_sampled_neighbor_search_equals_the_full_brute_force(m, kind, d):
+    """The streaming form used at full size (chunks of predecessors, low-rank terms of the
+    queries alone) returns the sets and keys of the pinned full brute force: queries at,
+    just before and just after chunk boundaries (chunk = 7), the first points (fewer than
+    m_v predecessors) and the last point; m = 0 (no low-rank part) included."""
+    ls = 0.2 if d == 2 else np.array([0.3, 0.6, 1.1])
+    P = synth.make_problem(300, d, m, 8, kind, 1.0, ls, 0.1, 11, inducing="kmeans++", lloyd=2)
+    th = P.theta
+    N, keys, _ = O.causal_neighbors(P.X, P.Z, th, 8, return_keys=True)
+    queries = [1, 2, 3, 6, 7, 8, 13, 14, 15, 20, 21, 22, 49, 133, 140, 141, 298, 299]
+    Ns, ks = O.causal_neighbors_sample(P.X, P.Z, th, 8, queries, chunk=7)
+    for a, i in enumerate(queries):
+        q = min(i, 8)
+        assert list(Ns[a]) == list(N[i, :q]), i
+        np.testing.assert_allclose(ks[a], keys[i - 1], rtol=0, atol=1e-13)
+        assert len(ks[a]) == i
+
+
 # --------------------------------------------------------------------------- factors
 def test_vecchia_factor_invariants():
     P = small_problem(n=300, m=25, mv=10, nugget=0.05)
@@ -130,6 +149,23 @@ def test_vecchia_factor_invariants():
     for i in range(300):
         assert set(N4[i][N4[i] >= 0]) <= set(N10[i][N10[i] >= 0])
     assert (D10 <= D4 + 1e-12).all()
+
+
+@pytest.mark.parametrize("m,nugget", [(25, 0.05), (0, 0.05), (25, 0.0)])
+def test_row_sampled_factors_equal_the_full_factors(m, nugget):
+    """The per-row form used at full size (low-rank terms rebuilt on the rows and their
+    neighbours only, indices remapped) gives the A_i, D_i of the pinned full form, for
+    rows with fewer than m_v predecessors (i < m_v), rows sharing neighbours, and the last
+    row; with and without inducing points and nugget."""
+    P = small_problem(n=300, m=m, mv=10, nugget=nugget)
+    th = P.theta
+    N = O.causal_neighbors(P.X, P.Z, th, 10)
+    Af, Df = O.vecchia_factors(P.X, P.Z, th, N)
+    rows = np.array([0, 1, 2, 5, 9, 10, 11, 57, 58, 150, 151, 299])
+    Ar, Dr = O.vecchia_factors_rows(P.X, P.Z, th, N, rows)
+    np.testing.assert_allclose(Ar, Af[rows], rtol=0, atol=1e-10 * max(1.0, np.abs(Af).max()))
+    np.testing.assert_allclose(Dr, Df[rows], rtol=1e-10)
+    assert (Ar[0] == 0).all() and (Ar[2, 2:] == 0).all()
 
 
 # --------------------------------------------------------------------------- likelihood
