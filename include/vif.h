@@ -70,7 +70,12 @@ typedef struct {
                                  and the caller supplies N(i) with vif_set_neighbors before vif_nll */
   int32_t stage_timing;       /* 1: record CUDA events around every stage of vif_nll (read them with
                                  vif_get_stage_times); 0: no events */
-  int32_t reserved[4];        /* must be zero */
+  int32_t simt_factor;        /* VIF_MIXED only.  0 (default): the residual products A_N^T A_N of the
+                                 Vecchia factors run on the tensor cores (groups of points sharing
+                                 one 128-row Gram) whenever m >= 1 and m_v + 1 <= 32; 1: every point
+                                 forms its own Gram on the CUDA cores (the choice does not change the
+                                 method, only how its float32 products are summed) */
+  int32_t reserved[3];        /* must be zero */
 } vif_opts;
 
 /* vif_build -- fix the data S = {s_i} (X, n x d), the inducing points S* (Z, m x d,
@@ -132,7 +137,12 @@ typedef struct {
   int32_t max_newton;         /* Newton step cap (e.g. 50) */
   int32_t precond;            /* 0 VIFDU (Eq. pcls1), 1 VIFDU with learned diagonal correction,
                                  2 FITC with the VIF's inducing points (App. E.2, Eq. pcls2) */
-  int32_t reserved;           /* must be zero */
+  int32_t wait_polls;         /* 0: the default bound on every wait of the level-scheduled triangular
+                                 solves (well over a second); > 0: give up a wait after this many polls
+                                 of a value that is not yet written.  A diagnosis and testing knob: a
+                                 small value makes the solves give up, the kernels return, and the call
+                                 reports VIF_ERR_TIMEOUT with the context still usable; it applies to
+                                 the solves of the Newton iterations.  < 0: VIF_ERR_ARG */
   const void *mlp_weights;    /* device pointer to the packed network weights when precond = 1 */
 } vif_laplace_opts;
 
@@ -356,8 +366,14 @@ vif_status vif_get_stage_times(const vif_ctx *ctx, double *ms);
  * cudaMalloc/cudaFree.  It needs no context and calls no allocating routine.
  * The paper has no counterpart to this entry point; it is an interface addition.
  *   X (n x d), Z (m x d), N (n x mv int32, rows as for vif_set_neighbors), y (n):
- *   DEVICE pointers.  theta: as for vif_nll.  stream: cudaStream_t (NULL = legacy
- *   default).  nll_out: HOST double, written when the call returns VIF_OK.
+ *   DEVICE (or managed) pointers, checked with cudaPointerGetAttributes: any other
+ *   pointer is refused with VIF_ERR_ARG before work is enqueued.  The element types
+ *   (float64, int32) cannot be checked from a pointer and are the caller's duty.
+ *   theta: as for vif_nll, with the same checks (VIF_ERR_ARG for non-finite or
+ *   non-positive values).  stream: cudaStream_t (NULL = legacy default).
+ *   nll_out: HOST double, written when the call returns VIF_OK.  Errors map as for
+ *   vif_nll (VIF_ERR_NOT_PD, VIF_ERR_STATE for an invalid neighbour table,
+ *   VIF_ERR_TIMEOUT for a device wait that gave up).
  * All intermediates live in one static device array of VIF_NOALLOC_SCRATCH_BYTES
  * inside the library; every GPU that loads the library holds that memory until
  * the process exits.  A problem whose intermediates do not fit (roughly

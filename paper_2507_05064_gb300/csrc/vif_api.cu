@@ -28,6 +28,15 @@ struct vif_ctx {
   double *hyp = nullptr;                      // [0..15] 1/lambda, [16..31] center
   int32_t* N = nullptr;                       // n x mv
   int32_t* order = nullptr;                   // processing order of the per-point kernels
+  std::vector<int32_t> h_order;               // the same order on the host
+  // float32 path: groups of points sharing one tensor-core Gram of their rows of A
+  int32_t *ug_rows = nullptr, *ug_ptr = nullptr;
+  unsigned char* ug_loc = nullptr;
+  float* gsub = nullptr;                      // per slot: Gram of the point's rows (packed triangle)
+  int64_t ug_ngroups = 0;
+  bool ug_ready = false;
+  bool simt_factor = false;                   // keep the per-point Gram on the CUDA cores
+  int nsm = 1;
   double *Sm = nullptr, *Linv = nullptr;      // m x ldm
   double* trw = nullptr;                      // triangular-inverse workspace
   void* LinvT = nullptr;                      // mpad x mpad (float or double)
@@ -85,6 +94,70 @@ struct vif_ctx {
   char err[1024] = {0};
 };
 
+namespace vif {
+
+bool is_device_ptr(const void* p) {
+  cudaPointerAttributes at;
+  if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  return at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged;
+}
+
+bool cov_valid(const vif_cov* cv, int d, char* why, size_t cap) {
+  const char* msg = nullptr;
+  if (!cv) {
+    msg = "covariance parameters are NULL";
+  } else if (cv->kind < 0 || cv->kind > 3) {
+    snprintf(why, cap, "unknown kernel kind %d", cv->kind);
+    return false;
+  } else if (!(cv->variance > 0.0) || !std::isfinite(cv->variance)) {
+    msg = "variance must be positive and finite";
+  } else if (!(cv->nugget >= 0.0) || !std::isfinite(cv->nugget)) {
+    msg = "nugget must be >= 0 and finite";
+  } else if (!cv->lengthscale || (cv->n_ls != 1 && cv->n_ls != d)) {
+    snprintf(why, cap, "lengthscale must hold 1 or d=%d values", d);
+    return false;
+  } else {
+    for (int t = 0; t < cv->n_ls; ++t)
+      if (!(cv->lengthscale[t] > 0.0) || !std::isfinite(cv->lengthscale[t]))
+        msg = "length scales must be positive and finite";
+  }
+  if (msg) snprintf(why, cap, "%s", msg);
+  return msg == nullptr;
+}
+
+CovParams cov_params(const vif_cov* cv) {
+  CovParams cp;
+  cp.kind = cv->kind;
+  cp.var = cv->variance;
+  // Sigma_m jitter and residual diagonal (nugget, or a jitter for latent processes)
+  cp.jitter = (cv->kind == VIF_SE ? 1e-8 : 1e-10) * cv->variance;
+  cp.tdiag = cv->nugget > 0.0 ? cv->nugget : 1e-10 * cv->variance;
+  return cp;
+}
+
+vif_status status_error(const int* st, char* why, size_t cap) {
+  if (st[0] == ST_OK) return VIF_OK;
+  if (st[0] == ST_TIMEOUT) {
+    snprintf(why, cap, "device wait timed out at %d", st[1]);
+    return VIF_ERR_TIMEOUT;
+  }
+  if (st[0] == ST_BAD_NEIGHBOR) {
+    snprintf(why, cap, "neighbour table row %d holds an index that is not a predecessor", st[1]);
+    return VIF_ERR_STATE;
+  }
+  const char* what = st[0] == ST_NOTPD_SIGMAM  ? "Sigma_m (inducing points)"
+                     : st[0] == ST_NOTPD_FACTOR ? "residual Vecchia block of point"
+                     : st[0] == ST_NOTPD_CAP    ? "capacitance matrix"
+                                                 : "preconditioner";
+  snprintf(why, cap, "Cholesky pivot not positive: %s, index %d", what, st[1]);
+  return VIF_ERR_NOT_PD;
+}
+
+}  // namespace vif
+
 namespace {
 
 // message of the last failed vif_build (the context is gone by then)
@@ -107,15 +180,6 @@ vif_status set_err(vif_ctx* c, vif_status st, const char* fmt, ...) {
       return set_err(ctx, e_ == cudaErrorMemoryAllocation ? VIF_ERR_NOMEM : VIF_ERR_CUDA,       \
                      "%s: %s (%s:%d)", #call, cudaGetErrorString(e_), __FILE__, __LINE__);       \
   } while (0)
-
-bool is_device_ptr(const void* p) {
-  cudaPointerAttributes at;
-  if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
-    cudaGetLastError();
-    return false;
-  }
-  return at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged;
-}
 
 template <typename T>
 vif_status dalloc(vif_ctx* ctx, T** p, size_t count) {
@@ -153,28 +217,9 @@ vif_status download(vif_ctx* ctx, void* dst, const void* src, size_t bytes) {
 }
 
 vif_status check_cov(vif_ctx* ctx, const vif_cov* cv, int d) {
-  if (!cv) return set_err(ctx, VIF_ERR_ARG, "covariance parameters are NULL");
-  if (cv->kind < 0 || cv->kind > 3) return set_err(ctx, VIF_ERR_ARG, "unknown kernel kind %d", cv->kind);
-  if (!(cv->variance > 0.0) || !std::isfinite(cv->variance))
-    return set_err(ctx, VIF_ERR_ARG, "variance must be positive and finite");
-  if (!(cv->nugget >= 0.0) || !std::isfinite(cv->nugget))
-    return set_err(ctx, VIF_ERR_ARG, "nugget must be >= 0 and finite");
-  if (!cv->lengthscale || (cv->n_ls != 1 && cv->n_ls != d))
-    return set_err(ctx, VIF_ERR_ARG, "lengthscale must hold 1 or d=%d values", d);
-  for (int t = 0; t < cv->n_ls; ++t)
-    if (!(cv->lengthscale[t] > 0.0) || !std::isfinite(cv->lengthscale[t]))
-      return set_err(ctx, VIF_ERR_ARG, "length scales must be positive and finite");
+  char why[160];
+  if (!cov_valid(cv, d, why, sizeof(why))) return set_err(ctx, VIF_ERR_ARG, "%s", why);
   return VIF_OK;
-}
-
-CovParams cov_params(const vif_cov* cv) {
-  CovParams cp;
-  cp.kind = cv->kind;
-  cp.var = cv->variance;
-  // Sigma_m jitter and residual diagonal (nugget, or a jitter for latent processes)
-  cp.jitter = (cv->kind == VIF_SE ? 1e-8 : 1e-10) * cv->variance;
-  cp.tdiag = cv->nugget > 0.0 ? cv->nugget : 1e-10 * cv->variance;
-  return cp;
 }
 
 // Scale X and Z by 1/lambda around the data centre (float64 and, if asked, float32).
@@ -246,8 +291,15 @@ vif_status run_pipeline(vif_ctx* ctx, const CovParams& cp, T* A, T* LinvT, T* F,
   if (ctx->timing) CK(cudaEventRecord(ctx->ev[k], ctx->stream))
   MARK(0);
   CKS(compute_lowrank_parts<T>(ctx, cp, A, LinvT, Xs, Zs));
-  CK(vecchia_factor<T>(A, Xs, ctx->N, ctx->order, ctx->y, ctx->n, ctx->d, ctx->m, ctx->mpad, ctx->mv, ctx->fpad,
-                       cp, F, ctx->Acoef, ctx->Dv, ctx->logD, ctx->status, ctx->stream));
+  const float* gsub = nullptr;
+  if (sizeof(T) == 4 && ctx->ug_ready) {
+    // the residual products A_N^T A_N on the tensor cores, one 128-row Gram per group
+    const UnionGroups ug{ctx->ug_rows, ctx->ug_ptr, ctx->ug_loc, ctx->ug_ngroups};
+    CK(union_gram_tc((const float*)A, ctx->mpad, ug, ctx->mv + 1, ctx->gsub, ctx->status, ctx->stream, ctx->nsm));
+    gsub = ctx->gsub;
+  }
+  CK(vecchia_factor_gs<T>(A, Xs, ctx->N, ctx->order, ctx->y, ctx->n, ctx->d, ctx->m, ctx->mpad, ctx->mv,
+                          ctx->fpad, cp, F, ctx->Acoef, ctx->Dv, ctx->logD, ctx->status, ctx->stream, gsub));
   MARK(3);
   CK(gram_FtF<T>(F, ctx->n, ctx->fpad, ctx->m, ctx->part, ctx->nsplit, ctx->G, ctx->fpad, ctx->stream, nullptr,
                  ctx->status));
@@ -269,14 +321,9 @@ vif_status read_status(vif_ctx* ctx, double* scal_out, int nscal) {
   CK(cudaStreamSynchronize(ctx->stream));
   const int* st = reinterpret_cast<const int*>(ctx->h_pin);
   if (st[0] != ST_OK) {
-    const char* what = st[0] == ST_NOTPD_SIGMAM  ? "Sigma_m (inducing points)"
-                       : st[0] == ST_NOTPD_FACTOR ? "residual Vecchia block of point"
-                       : st[0] == ST_NOTPD_CAP    ? "capacitance matrix"
-                                                   : "preconditioner";
-    if (st[0] == ST_TIMEOUT) return set_err(ctx, VIF_ERR_TIMEOUT, "device wait timed out at %d", st[1]);
-    if (st[0] == ST_BAD_NEIGHBOR)
-      return set_err(ctx, VIF_ERR_STATE, "neighbour table row %d holds an index that is not a predecessor", st[1]);
-    return set_err(ctx, VIF_ERR_NOT_PD, "Cholesky pivot not positive: %s, index %d", what, st[1]);
+    char why[200];
+    const vif_status e = status_error(st, why, sizeof(why));
+    return set_err(ctx, e, "%s", why);
   }
   for (int k = 0; k < nscal; ++k) scal_out[k] = ctx->h_pin[2 + k];
   return VIF_OK;
@@ -286,7 +333,7 @@ void free_ctx(vif_ctx* c) {
   if (!c) return;
   void* bufs[] = {c->X,    c->Z,     c->Xs, c->Zs,   c->Xs32, c->Zs32, c->hyp, c->N,   c->order, c->Sm, c->trw,
                   c->Linv, c->LinvT, c->A,  c->F,    c->Acoef, c->Dv,  c->logD, c->part, c->G,
-                  c->y,    c->red,   c->dscal, c->status};
+                  c->y,    c->red,   c->dscal, c->status, c->ug_rows, c->ug_ptr, c->ug_loc, c->gsub};
   for (void* b : bufs)
     if (b) cudaFree(b);
   void* pbufs[] = {c->pA,     c->pF,    c->pLinvT, c->pXp,    c->pXps,   c->pAp,    c->pcpp,   c->pmean,
@@ -474,6 +521,34 @@ vif_status fp64_buffers(vif_ctx* ctx, double** A64, double** F64, double** LT64)
 }
 
 
+// Groups of the float32 path's tensor-core Gram (vif_factor_tc.cu) from the neighbour sets
+// N (host copy) and the processing order; the context keeps the SIMT factor kernel when the
+// sets do not qualify (m = 0, m_v = 0, m_v + 1 > 32) or a group cannot be formed.
+vif_status build_groups(vif_ctx* ctx, const int32_t* hN) {
+  ctx->ug_ready = false;
+  if (ctx->precision != VIF_MIXED || ctx->simt_factor || ctx->mv < 1 || ctx->mv + 1 > 32 || ctx->m < 1 ||
+      (int64_t)ctx->h_order.size() != ctx->n)
+    return VIF_OK;
+  std::vector<int32_t> rows, ptr;
+  std::vector<unsigned char> loc;
+  if (!build_union_groups(hN, ctx->h_order.data(), ctx->n, ctx->mv, 128, rows, ptr, loc)) return VIF_OK;
+  for (void* b : {(void*)ctx->ug_rows, (void*)ctx->ug_ptr, (void*)ctx->ug_loc})
+    if (b) cudaFree(b);
+  ctx->ug_rows = nullptr;
+  ctx->ug_ptr = nullptr;
+  ctx->ug_loc = nullptr;
+  CKS(dalloc(ctx, &ctx->ug_rows, rows.size()));
+  CKS(dalloc(ctx, &ctx->ug_ptr, ptr.size()));
+  CKS(dalloc(ctx, &ctx->ug_loc, loc.size()));
+  if (!ctx->gsub) CKS(dalloc(ctx, &ctx->gsub, (size_t)ctx->n * ((ctx->mv + 1) * (ctx->mv + 2) / 2)));
+  CK(cudaMemcpy(ctx->ug_rows, rows.data(), rows.size() * sizeof(int32_t), cudaMemcpyHostToDevice));
+  CK(cudaMemcpy(ctx->ug_ptr, ptr.data(), ptr.size() * sizeof(int32_t), cudaMemcpyHostToDevice));
+  CK(cudaMemcpy(ctx->ug_loc, loc.data(), loc.size(), cudaMemcpyHostToDevice));
+  ctx->ug_ngroups = (int64_t)ptr.size() - 1;
+  ctx->ug_ready = true;
+  return VIF_OK;
+}
+
 // Children lists of the neighbour DAG (the transpose of N, by column), for B^T.
 // Slots {row, first term, end of terms, solo} of a sync-free triangular solve, rows
 // ordered by level: level[r] is 0 for a row that reads no other row, else one more
@@ -634,7 +709,7 @@ vif_status lap_alloc(vif_ctx* ctx) {
   CKS(dalloc(ctx, &ctx->l_sc, 16));
   CKS(dalloc(ctx, &ctx->l_red, 256));
   CKS(dalloc(ctx, &ctx->l_counter, 4));
-  CKS(dalloc(ctx, &ctx->l_abort, 1));
+  CKS(dalloc(ctx, &ctx->l_abort, 2));   // [0] abort flag, [1] poll bound of the waits (0: default)
   CK(cudaMemsetAsync(ctx->l_sm, 0, ctx->fpad * sizeof(double), ctx->stream));
   CK(cudaMemsetAsync(ctx->l_cm, 0, ctx->fpad * sizeof(double), ctx->stream));
   CK(cudaMemsetAsync(ctx->l_G3, 0, (size_t)(ctx->m + 1) * ctx->fpad * sizeof(double), ctx->stream));
@@ -688,8 +763,9 @@ vif_status vif_build(const double* X, int64_t n, int32_t d, const double* Z, int
     return VIF_ERR_ARG;
   if (opts->precision != VIF_FP64 && opts->precision != VIF_MIXED) return VIF_ERR_ARG;
   if (opts->likelihood != VIF_GAUSSIAN && opts->likelihood != VIF_BERNOULLI_LOGIT) return VIF_ERR_ARG;
-  for (int k = 0; k < 4; ++k)
+  for (int k = 0; k < 3; ++k)
     if (opts->reserved[k] != 0) return VIF_ERR_ARG;
+  if (opts->simt_factor != 0 && opts->simt_factor != 1) return VIF_ERR_ARG;
   int ndev = 0;
   if (cudaGetDeviceCount(&ndev) != cudaSuccess || ndev == 0) {
     cudaGetLastError();
@@ -713,6 +789,7 @@ vif_status vif_build(const double* X, int64_t n, int32_t d, const double* Z, int
   ctx->precision = opts->precision;
   ctx->likelihood = opts->likelihood;
   ctx->timing = opts->stage_timing != 0;
+  ctx->simt_factor = opts->simt_factor != 0;
   if (ctx->timing)
     for (auto& e : ctx->ev)
       if (cudaEventCreate(&e) != cudaSuccess) {
@@ -721,9 +798,14 @@ vif_status vif_build(const double* X, int64_t n, int32_t d, const double* Z, int
       }
   const bool mixed = ctx->precision == VIF_MIXED;
   const size_t esz = mixed ? sizeof(float) : sizeof(double);
+  if (cudaDeviceGetAttribute(&ctx->nsm, cudaDevAttrMultiProcessorCount, ctx->dev) != cudaSuccess) {
+    cudaGetLastError();
+    ctx->nsm = 1;
+  }
   if (mixed) {
     cudaError_t e = lowrank_A_tc_init();
     if (e == cudaSuccess) e = gram_tc_init();
+    if (e == cudaSuccess) e = union_gram_tc_init();
     if (e != cudaSuccess) {
       vif_internal_set_global_error(cudaGetErrorString(e));
       free_ctx(ctx);
@@ -802,8 +884,9 @@ vif_status vif_build(const double* X, int64_t n, int32_t d, const double* Z, int
     ctx->center[t] = 0.5 * (lo + hi);
   }
   {
-    std::vector<int32_t> ord = morton_order(hx, n, d, cov);
-    if (cudaMemcpy(ctx->order, ord.data(), (size_t)n * sizeof(int32_t), cudaMemcpyHostToDevice) != cudaSuccess) {
+    ctx->h_order = morton_order(hx, n, d, cov);
+    if (cudaMemcpy(ctx->order, ctx->h_order.data(), (size_t)n * sizeof(int32_t), cudaMemcpyHostToDevice) !=
+        cudaSuccess) {
       free_ctx(ctx);
       return VIF_ERR_CUDA;
     }
@@ -827,6 +910,15 @@ vif_status vif_build(const double* X, int64_t n, int32_t d, const double* Z, int
   if (e != cudaSuccess) {
     free_ctx(ctx);
     return VIF_ERR_CUDA;
+  }
+  if (mixed && mv > 0 && !opts->no_neighbor_search) {
+    std::vector<int32_t> hN((size_t)n * mv);
+    if (cudaMemcpy(hN.data(), ctx->N, hN.size() * sizeof(int32_t), cudaMemcpyDeviceToHost) != cudaSuccess ||
+        (st = build_groups(ctx, hN.data())) != VIF_OK) {
+      snprintf(g_build_err, sizeof(g_build_err), "%s", ctx->err[0] ? ctx->err : "group construction failed");
+      free_ctx(ctx);
+      return st != VIF_OK ? st : VIF_ERR_CUDA;
+    }
   }
   *out = ctx;
   return VIF_OK;
@@ -931,7 +1023,7 @@ vif_status lap_setup(vif_ctx* ctx, const vif_cov* theta, const double* y, LapOps
   CKS(lap_alloc(ctx));
   CovParams cp = cov_params(theta);
   CK(cudaMemsetAsync(ctx->status, 0, 4 * sizeof(int), s));
-  CK(cudaMemsetAsync(ctx->l_abort, 0, sizeof(int), s));
+  CK(cudaMemsetAsync(ctx->l_abort, 0, 2 * sizeof(int), s));
   if (y) CKS(upload(ctx, ctx->y, y, (size_t)ctx->n * sizeof(double)));   // NULL: y already resident
   CKS(apply_scaling(ctx, theta, false));
   CKS(run_pipeline<double>(ctx, cp, A64, LT64, F64, ctx->Xs, ctx->Zs));
@@ -1338,7 +1430,7 @@ vif_status laplace_run(vif_ctx* ctx, const vif_cov* theta, const double* y, cons
   if (ctx->likelihood != VIF_BERNOULLI_LOGIT)
     return set_err(ctx, VIF_ERR_STATE, "the Laplace approximation needs a context built for VIF_BERNOULLI_LOGIT");
   if (theta->nugget != 0.0) return set_err(ctx, VIF_ERR_ARG, "a latent GP has no nugget: set nugget = 0");
-  if (!(lo->rel_tol > 0.0) || lo->max_pcg < 1 || lo->max_newton < 1 || lo->reserved != 0)
+  if (!(lo->rel_tol > 0.0) || lo->max_pcg < 1 || lo->max_newton < 1 || lo->wait_polls < 0)
     return set_err(ctx, VIF_ERR_ARG, "invalid Laplace options");
   if (lo->precond != 0 && lo->precond != 1 && lo->precond != LAP_FITC)
     return set_err(ctx, VIF_ERR_ARG, "unknown preconditioner");
@@ -1359,6 +1451,7 @@ vif_status laplace_run(vif_ctx* ctx, const vif_cov* theta, const double* y, cons
   CK(cudaEventRecord(e0, s));
   LapOps& o = *op;
   CKS(lap_setup(ctx, theta, y, &o));
+  if (lo->wait_polls > 0) CK(lap_set_wait_polls(ctx->l_abort, lo->wait_polls, s));
   const bool fitc = lo->precond == LAP_FITC;
   if (fitc) o.kind = LAP_FITC;
   bool fresh = true;   // FITC: A's padded copy is due after lap_setup
@@ -2382,6 +2475,7 @@ vif_status vif_set_neighbors(vif_ctx* ctx, const int32_t* N) {
   CK(cudaMemcpyAsync(ctx->N, h.data(), cnt * sizeof(int32_t), cudaMemcpyHostToDevice, ctx->stream));
   CK(cudaStreamSynchronize(ctx->stream));
   if (ctx->lap_ready) CKS(build_children(ctx));
+  CKS(build_groups(ctx, h.data()));
   return VIF_OK;
 }
 

@@ -251,12 +251,19 @@ __global__ __launch_bounds__(GC_THREADS, 1) void gram_tc_kernel(const float* __r
     }
   }
   // every MMA issued by this CTA completes on `fin` (committed by the MMA warp)
-  if (!tc::mbar_wait(&sb.fin, 0)) failed = true;
+  // after a wait that gave up, MMAs may still be in flight: wait for them once more
+  // (bounded) and release the TMEM only once they have finished (results of a call that
+  // reports the timeout are discarded)
+  bool fin_ok = tc::mbar_wait(&sb.fin, 0);
+  if (!fin_ok) {
+    failed = true;
+    fin_ok = tc::mbar_wait(&sb.fin, 0);
+  }
   tc::fence_after_sync();
   if (__syncthreads_or(failed) && tid == 0 && status) flag_status(status, ST_TIMEOUT, p);
   tc::fence_before_sync();
-  __syncthreads();
-  if (warp == 0) {
+  const bool drained = __syncthreads_and(fin_ok);
+  if (warp == 0 && drained) {
     tc::fence_after_sync();
     tc::tmem_dealloc(tmem, GC_TMEM_COLS);
   }

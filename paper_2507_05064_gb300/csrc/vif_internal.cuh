@@ -6,6 +6,7 @@
 
 #include <cmath>
 #include <string>
+#include <vector>
 
 #include "../../include/vif.h"
 
@@ -102,6 +103,14 @@ struct CovParams {
   double jitter;  // diagonal added to Sigma_m
 };
 
+// Host-side checks and conversions shared by the context API (vif_api.cu) and the
+// allocation-free entry point (vif_noalloc.cu), so that both accept, reject and
+// report alike.
+bool is_device_ptr(const void* p);                              // device or managed memory
+bool cov_valid(const vif_cov* cv, int d, char* why, size_t cap);  // false: reason in why
+CovParams cov_params(const vif_cov* cv);                        // kernel form, with the R6 jitters
+vif_status status_error(const int* st, char* why, size_t cap);  // device status words -> vif_status
+
 // ---------------------------------------------------------------------------
 // Launchers (host side), grouped by translation unit.
 // ---------------------------------------------------------------------------
@@ -139,6 +148,28 @@ template <typename T>
 cudaError_t vecchia_factor(const T* A, const T* Xs, const int32_t* N, const int32_t* order, const double* y,
                            int64_t n, int d, int m, int mpad, int mv, int fpad, CovParams cp, T* F,
                            double* Acoef, double* Dv, double* logD, int* status, cudaStream_t s);
+// gsub (float32 path only): the Gram of each point's rows [A_N(i); a_i] from
+// union_gram_tc, slot-major in the processing order with stride (m_v + 1)(m_v + 2) / 2
+// (packed lower triangle); NULL: the kernel forms it itself.
+template <typename T>
+cudaError_t vecchia_factor_gs(const T* A, const T* Xs, const int32_t* N, const int32_t* order, const double* y,
+                              int64_t n, int d, int m, int mpad, int mv, int fpad, CovParams cp, T* F,
+                              double* Acoef, double* Dv, double* logD, int* status, cudaStream_t s,
+                              const float* gsub);
+// vif_factor_tc.cu: the residual products A_N^T A_N on the tensor cores (float32 path).
+// Groups of consecutive points of the processing order share one 128-row Gram.
+struct UnionGroups {
+  const int32_t* rows;        // ngroups x 128 rows of A (-1 padded)
+  const int32_t* ptr;         // ngroups + 1 offsets into the processing order
+  const unsigned char* loc;   // n x 32: group-local row of each of a slot's rows (0xFF beyond)
+  int64_t ngroups;
+};
+cudaError_t union_gram_tc_init();
+// nsm: SM count of the device (one persistent CTA per SM)
+cudaError_t union_gram_tc(const float* A, int mpad, const UnionGroups& ug, int Q, float* gsub, int* status,
+                          cudaStream_t s, int nsm);
+bool build_union_groups(const int32_t* N, const int32_t* order, int64_t n, int mv, int max_pts,
+                        std::vector<int32_t>& rows, std::vector<int32_t>& ptr, std::vector<unsigned char>& loc);
 // wrow: optional row weights (NULL = 1): G = F^T diag(wrow) F (+ identity on the first m).
 // The float32 Gram runs on the tensor cores (vif_gram_tc.cu) and may use fewer slices
 // than nsplit; status receives ST_TIMEOUT if one of its waits gives up.
@@ -170,6 +201,8 @@ cudaError_t predict_all(const double* A, const double* Xs, int64_t n, const doub
                         cudaStream_t s);
 
 // vif_laplace.cu
+// abort_flag[1] = polls: the bound on each wait of the level-scheduled solves (0: default)
+cudaError_t lap_set_wait_polls(int* abort_flag, int polls, cudaStream_t s);
 // rows of the level schedules of the two triangular solves are taken four at a time
 // (slots {row, first term, end of terms, solo}); each level is padded with
 // {-1, 0, 0, 0} to a multiple of this

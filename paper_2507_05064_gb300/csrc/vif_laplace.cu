@@ -41,14 +41,18 @@ __device__ __forceinline__ void st_relaxed_f64(double* p, double v) {
 // Value of *p once it has been written (NaN after an abort or a timeout).  Polls are
 // back to back: a row's inputs land one L2 round trip apart at best, and backing off
 // only lengthens the chain of levels (measured: 1.37 us per level of a pure chain with
-// back-to-back polls, 2.06 us with a 64-512 ns backoff).
+// back-to-back polls, 2.06 us with a 64-512 ns backoff).  abort_flag[0] is the abort
+// flag, abort_flag[1] the poll bound (0: SPIN_LIMIT); the flag is read every 64 polls,
+// the bound at every poll once it is below that.
 __device__ __noinline__ double wait_value(const double* p, int* abort_flag, int* status, int64_t row) {
+  const int lim0 = ld_volatile(abort_flag + 1);
+  const int lim = lim0 > 0 ? lim0 : SPIN_LIMIT;
   for (int it = 1;; ++it) {
     const unsigned long long b = ld_relaxed_u64(p);
     if (b != TR_PENDING) return __longlong_as_double((long long)b);
-    if ((it & 63) == 0) {
+    if ((it & 63) == 0 || it >= lim) {
       if (ld_volatile(abort_flag)) return NAN;
-      if (it > SPIN_LIMIT) {
+      if (it >= lim) {
         atomicExch(abort_flag, 1);
         flag_status(status, ST_TIMEOUT, row);
         return NAN;
@@ -168,6 +172,13 @@ __global__ void child_coef_kernel(const int32_t* __restrict__ ch_row, const int3
                                   const double* __restrict__ Acoef, int64_t nnz, int mv, double* ch_coef) {
   const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (p < nnz) ch_coef[p] = Acoef[(size_t)ch_row[p] * mv + ch_slot[p]];
+}
+
+__global__ void set_i32_kernel(int* p, int v) { *p = v; }
+
+cudaError_t lap_set_wait_polls(int* abort_flag, int polls, cudaStream_t s) {
+  set_i32_kernel<<<1, 1, 0, s>>>(abort_flag + 1, polls);
+  return cudaGetLastError();
 }
 
 // t_i = (x_i - sum_k A_i[k] x_{N_k}) / sqrt(D_i); thread per row, four gathers in flight

@@ -270,7 +270,15 @@ __global__ __launch_bounds__(AT_THREADS, 1) void lowrank_A_tc_kernel(
         ++copies_seen[s];
       }
   }
-  if (!tc::mbar_wait(&sb.fin, 0)) failed = true;
+  // a wait that gave up may leave MMAs in flight: wait for them once more (bounded) before
+  // the accumulators' TMEM is released; if they still have not finished, the TMEM is
+  // kept rather than freed under running MMAs (the call reports the timeout and its
+  // results are discarded)
+  bool fin_ok = tc::mbar_wait(&sb.fin, 0);
+  if (!fin_ok) {
+    failed = true;
+    fin_ok = tc::mbar_wait(&sb.fin, 0);
+  }
   if (__syncthreads_or(failed)) {
     if (tid == 0 && status) flag_status(status, ST_TIMEOUT, blockIdx.x);
   } else {
@@ -289,8 +297,8 @@ __global__ __launch_bounds__(AT_THREADS, 1) void lowrank_A_tc_kernel(
     }
   }
   tc::fence_before_sync();
-  __syncthreads();
-  if (warp == 0) {
+  const bool drained = __syncthreads_and(fin_ok);
+  if (warp == 0 && drained) {
     tc::fence_after_sync();
     tc::tmem_dealloc(tmem, AT_TMEM_COLS);
   }

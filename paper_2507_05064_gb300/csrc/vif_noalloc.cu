@@ -119,11 +119,17 @@ extern "C" vif_status vif_nll_noalloc(const double* X, int64_t n, int32_t d, con
   if (!X || !y || !nll_out || !theta || n < 1 || d < 1 || d > 16 || m < 0 || m > 2048 || mv < 0 || mv > 48 ||
       (m > 0 && !Z) || (mv > 0 && !N))
     return fail(VIF_ERR_ARG, "vif_nll_noalloc: invalid arguments");
-  if (theta->kind < 0 || theta->kind > 3 || !(theta->variance > 0.0) || !(theta->nugget >= 0.0) ||
-      !theta->lengthscale || (theta->n_ls != 1 && theta->n_ls != d))
-    return fail(VIF_ERR_ARG, "vif_nll_noalloc: invalid covariance parameters");
-  for (int t = 0; t < theta->n_ls; ++t)
-    if (!(theta->lengthscale[t] > 0.0)) return fail(VIF_ERR_ARG, "vif_nll_noalloc: length scales must be > 0");
+  char why[200];
+  if (!cov_valid(theta, d, why, sizeof(why))) {
+    char b[256];
+    snprintf(b, sizeof(b), "vif_nll_noalloc: %s", why);
+    return fail(VIF_ERR_ARG, b);
+  }
+  // the kernels read these arrays directly: a host pointer would become an illegal
+  // device access, so anything cudaPointerGetAttributes does not report as device or
+  // managed memory is refused before any work is enqueued
+  if (!is_device_ptr(X) || !is_device_ptr(y) || (m > 0 && !is_device_ptr(Z)) || (mv > 0 && !is_device_ptr(N)))
+    return fail(VIF_ERR_ARG, "vif_nll_noalloc: X, Z, N and y must be device (or managed) pointers");
   const int mpad = std::max(32, ((m + 31) / 32) * 32);
   const int fpad = ((m + 1 + 63) / 64) * 64;
   const int nsplit = gram_nsplit(n, fpad);
@@ -139,11 +145,7 @@ extern "C" vif_status vif_nll_noalloc(const double* X, int64_t n, int32_t d, con
   cudaStream_t s = (cudaStream_t)stream;
   const Layout L = layout((uintptr_t)base, n, d, m, mv, mpad, fpad, nsplit);
 
-  CovParams cp;
-  cp.kind = theta->kind;
-  cp.var = theta->variance;
-  cp.jitter = (theta->kind == VIF_SE ? 1e-8 : 1e-10) * theta->variance;
-  cp.tdiag = theta->nugget > 0.0 ? theta->nugget : 1e-10 * theta->variance;
+  const CovParams cp = cov_params(theta);
   double h[32];
   for (int t = 0; t < 16; ++t) {
     h[t] = (t < d) ? 1.0 / theta->lengthscale[theta->n_ls == 1 ? 0 : t] : 0.0;
@@ -173,10 +175,10 @@ extern "C" vif_status vif_nll_noalloc(const double* X, int64_t n, int32_t d, con
   NA_CK(cudaMemcpyAsync(&val, L.dscal + 1, sizeof(double), cudaMemcpyDeviceToHost, s));
   NA_CK(cudaStreamSynchronize(s));
   if (st[0] != ST_OK) {
+    const vif_status e = status_error(st, why, sizeof(why));
     char b[256];
-    snprintf(b, sizeof(b), "vif_nll_noalloc: device status %d at index %d (non-positive Cholesky pivot or "
-             "invalid neighbour table)", st[0], st[1]);
-    return fail(st[0] == ST_BAD_NEIGHBOR ? VIF_ERR_STATE : VIF_ERR_NOT_PD, b);
+    snprintf(b, sizeof(b), "vif_nll_noalloc: %s", why);
+    return fail(e, b);
   }
   *nll_out = val;
   return VIF_OK;

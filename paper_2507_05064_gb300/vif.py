@@ -40,12 +40,12 @@ class VifCov(C.Structure):
 
 class VifOpts(C.Structure):
     _fields_ = [("precision", C.c_int32), ("likelihood", C.c_int32), ("no_neighbor_search", C.c_int32),
-                ("stage_timing", C.c_int32), ("reserved", C.c_int32 * 4)]
+                ("stage_timing", C.c_int32), ("simt_factor", C.c_int32), ("reserved", C.c_int32 * 3)]
 
 
 class LaplaceOpts(C.Structure):
     _fields_ = [("rel_tol", C.c_double), ("max_pcg", C.c_int32), ("max_newton", C.c_int32),
-                ("precond", C.c_int32), ("reserved", C.c_int32), ("mlp_weights", C.c_void_p)]
+                ("precond", C.c_int32), ("wait_polls", C.c_int32), ("mlp_weights", C.c_void_p)]
 
 
 class LaplaceNllStats(C.Structure):
@@ -170,17 +170,37 @@ def make_cov(theta) -> tuple[VifCov, np.ndarray]:
 
 def nll_noalloc(X, Z, N, mv: int, theta, y, stream: int = 0) -> float:
     """vif_nll_noalloc: the float64 likelihood without any device allocation.
-    X, Z, N (int32), y must be device tensors; see include/vif.h for who needs this."""
+    X (n, d) and Z (m, d) float64, N (n, mv) int32 and y (n,) float64 must be contiguous
+    CUDA tensors; see include/vif.h for who needs this.  Anything else raises
+    VifError(VIF_ERR_ARG) before the library is called."""
     L = lib()
+    n = int(X.shape[0]) if getattr(X, "ndim", 0) == 2 else -1
+    d = int(X.shape[1]) if n >= 0 else -1
+    m = 0 if Z is None else int(Z.shape[0])
+    _check_device(X, "float64", (n, d), "X")
+    _check_device(y, "float64", (n,), "y")
+    if m:
+        _check_device(Z, "float64", (m, d), "Z")
+    if mv:
+        _check_device(N, "int32", (n, int(mv)), "N")
     cv, ls = make_cov(theta)
     out = C.c_double()
-    n, d = int(X.shape[0]), int(X.shape[1])
-    m = 0 if Z is None else int(Z.shape[0])
     st = L.vif_nll_noalloc(_ptr(X), n, d, _ptr(Z) if m else None, m, _ptr(N) if mv else None, int(mv),
                            C.byref(cv), _ptr(y), C.c_void_p(stream), C.byref(out))
     if st != VIF_OK:
         raise VifError(st, L.vif_last_error(None).decode())
     return out.value
+
+
+def _check_device(t, dtype: str, shape, name: str) -> None:
+    """A contiguous CUDA tensor of the given dtype and shape, else VifError(VIF_ERR_ARG)."""
+    ok = (hasattr(t, "is_cuda") and t.is_cuda and t.is_contiguous() and str(t.dtype) == "torch." + dtype
+          and tuple(t.shape) == tuple(shape))
+    if not ok:
+        desc = (f"{type(t).__name__} {getattr(t, 'dtype', None)} {tuple(getattr(t, 'shape', ()))}"
+                f"{' on ' + str(t.device) if hasattr(t, 'device') else ''}")
+        raise VifError(VIF_ERR_ARG, f"{name} must be a contiguous CUDA {dtype} tensor of shape {tuple(shape)}, "
+                                    f"got {desc}")
 
 
 class Network:
@@ -277,7 +297,8 @@ class Context:
     """One built VIF problem: data, inducing points and neighbour sets (vif_build)."""
 
     def __init__(self, X, Z, mv: int, theta, precision: int = FP64, likelihood: int = GAUSSIAN,
-                 stream: int = 0, neighbor_search: bool = True, stage_timing: bool = False):
+                 stream: int = 0, neighbor_search: bool = True, stage_timing: bool = False,
+                 simt_factor: bool = False):
         L = lib()
         X = _f64(X)
         Z = _f64(Z) if Z is not None and Z.shape[0] > 0 else None
@@ -287,7 +308,7 @@ class Context:
         self.precision = precision
         cv, ls = make_cov(theta)
         opts = VifOpts(precision, likelihood, 0 if neighbor_search else 1, 1 if stage_timing else 0,
-                       (C.c_int32 * 4)())
+                       1 if simt_factor else 0, (C.c_int32 * 3)())
         h = C.c_void_p()
         st = L.vif_build(_ptr(X), self.n, self.d, _ptr(Z), self.m, self.mv, C.byref(cv), C.byref(opts),
                          C.c_void_p(stream), C.byref(h))
@@ -321,11 +342,12 @@ class Context:
         return mean, var
 
     def laplace_mode(self, theta, y, rel_tol=1e-6, max_pcg=1000, max_newton=50, precond=0,
-                     mlp_weights=None, allow_not_converged=False):
-        """Laplace mode for Bernoulli-logit responses y; returns (mode, stats dict)."""
+                     mlp_weights=None, allow_not_converged=False, wait_polls=0):
+        """Laplace mode for Bernoulli-logit responses y; returns (mode, stats dict).
+        wait_polls > 0 bounds every wait of the triangular solves (see include/vif.h)."""
         cv, ls = make_cov(theta)
         wp = None if mlp_weights is None else _ptr(getattr(mlp_weights, "buf", mlp_weights)).value
-        opts = LaplaceOpts(float(rel_tol), int(max_pcg), int(max_newton), int(precond), 0, wp)
+        opts = LaplaceOpts(float(rel_tol), int(max_pcg), int(max_newton), int(precond), int(wait_polls), wp)
         st = LaplaceStats()
         mode = np.empty(self.n)
         rc = lib().vif_laplace_mode(self.h, C.byref(cv), _ptr(_f64(y)), C.byref(opts), _ptr(mode), C.byref(st))

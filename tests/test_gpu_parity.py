@@ -308,6 +308,32 @@ def test_laplace_solves_on_deep_and_wide_dependency_graphs(shape):
     ctx.close()
 
 
+def test_solve_waits_give_up_at_their_bound_and_the_context_recovers():
+    """The sync-free triangular solves wait on values other warps write; every wait is
+    bounded.  With the bound set to one poll (vif_laplace_opts.wait_polls) on the 700-level
+    chain, whose rows each wait on the previous one, the waits give up, the kernels return
+    and the call reports VIF_ERR_TIMEOUT; the same context then finds the dense-Newton mode
+    with the default bound."""
+    n = 700
+    P = bern(n, 12, 1, 35)
+    N = np.full((n, 1), -1, dtype=np.int64)
+    N[1:, 0] = np.arange(n - 1)
+    vif = O.VIF(P.X, P.Z, P.theta, N)
+    b_dense, _, _ = O.laplace_mode(vif, P.y, dense=True)
+    ctx = V.Context(P.X, P.Z, 1, P.theta, likelihood=V.BERNOULLI_LOGIT, neighbor_search=False)
+    ctx.set_neighbors(N.astype(np.int32))
+    with pytest.raises(V.VifError) as ei:
+        ctx.laplace_mode(P.theta, P.y, rel_tol=1e-8, wait_polls=1)
+    assert ei.value.status == V.VIF_ERR_TIMEOUT, str(ei.value)
+    assert "timed out" in str(ei.value)
+    with pytest.raises(V.VifError) as ei:
+        ctx.laplace_mode(P.theta, P.y, rel_tol=1e-8, wait_polls=-1)
+    assert ei.value.status == V.VIF_ERR_ARG
+    b, st = ctx.laplace_mode(P.theta, P.y, rel_tol=1e-8)
+    assert np.linalg.norm(b - b_dense) <= 1e-6 * np.linalg.norm(b_dense), st
+    ctx.close()
+
+
 # --------------------------------------------------------------------------- VIF-Laplace NLL with SLQ
 def _vifla_case(n, m, mv, seed):
     P = bern(n, m, mv, seed)
