@@ -135,18 +135,55 @@ def peaks():
 
 
 def stage_algorithmic(P, stage):
-    """Algorithmic FLOPs and bytes of one launch of a stage (float32 storage)."""
-    n, m, mv = P.X.shape[0], P.Z.shape[0], P.mv
+    """Algorithmic flops and HBM bytes of one launch of a stage of the mixed path (float32
+    storage), as the method counts them (2 flops per FMA; one pass over each array):
+      lowrank_A       m^2 n / 2 FMA (A = L_m^{-1} K_mn), write A (4 n m bytes)
+      vecchia_factor  n m [(q+1)(q+2)/2 + q] FMA (residual Gram of [A_N; a_i] and the F row)
+                      + n q^3 / 6 (the Cholesky), read A once and write [F z] (4 n fpad)
+      gram_FtF        n (m+1)(m+2) / 2 FMA, read [F z] once."""
+    n, m, q = P.X.shape[0], P.Z.shape[0], P.mv
     fpad = ((m + 1 + 63) // 64) * 64
     if stage == "lowrank_A":
         return 2.0 * n * m * (m + 1) / 2, 4.0 * n * m
     if stage == "vecchia_factor":
-        q = mv
-        fma = n * ((q + 1) * (q + 2) / 2 * m + q * m)
-        return 2.0 * fma, 4.0 * n * m * 2 + 4.0 * n * (m + 1)
+        fma = n * ((q + 1) * (q + 2) / 2 * m + q * m) + n * q ** 3 / 6
+        return 2.0 * fma, 4.0 * n * m + 4.0 * n * fpad
     if stage == "gram_FtF":
         return 2.0 * n * (m + 1) * (m + 2) / 2, 4.0 * n * fpad
     return 0.0, 0.0
+
+
+def roofline_block(P, med, ms_step, pk):
+    """Roofline of the dense contractions (tensor-core bound, TF32) and of HBM, per stage and
+    for the whole evaluation.  The TF32 peak is the measured dense bf16 burst peak times the
+    nominal tf32 : bf16 ratio of 1/2; HBM is the measured copy bandwidth."""
+    bf16 = pk.get("bf16_tflops")
+    tf32 = bf16 / 2.0 if bf16 else 1900.0 / 2.0
+    hbm = pk.get("hbm_gbs") or 6800.0
+    src = ("measured" if bf16 else "fallback")
+    stages = {}
+    tot_f = tot_b = 0.0
+    for st in ("lowrank_A", "vecchia_factor", "gram_FtF"):
+        f, b = stage_algorithmic(P, st)
+        tot_f += f
+        tot_b += b
+        t = med[st] * 1e-3
+        ff, fb = f / t / 1e12 / tf32, b / t / 1e9 / hbm
+        stages[st] = {"ms": med[st], "tflops": f / t / 1e12, "frac_tf32": ff, "gbs": b / t / 1e9, "frac_hbm": fb,
+                      "binding": "tensor" if ff >= fb else "hbm", "frac": max(ff, fb),
+                      "algorithmic_flops": f, "algorithmic_bytes": b}
+    roof_ms = max(tot_f / (tf32 * 1e12), tot_b / (hbm * 1e9)) * 1e3
+    dom = max(stages, key=lambda k: stages[k]["ms"])
+    d = stages[dom]
+    return {"kernel": dom, "bound": "tensor", "achieved": d["tflops"], "peak": tf32, "unit": "TFLOP/s",
+            "frac": d["frac_tf32"], "traffic": None,
+            "peak_source": f"tf32 = 1/2 of the {src} dense bf16 burst peak ({bf16 or 1900.0} TFLOP/s, nominal ratio)",
+            "hbm_achieved_gbs": d["gbs"], "hbm_peak_gbs": hbm, "frac_hbm": d["frac_hbm"],
+            "algorithmic_flops_per_launch": d["algorithmic_flops"],
+            "algorithmic_bytes_per_launch": d["algorithmic_bytes"],
+            "per_stage": stages,
+            "whole_eval": {"algorithmic_flops": tot_f, "algorithmic_bytes": tot_b, "roofline_ms": roof_ms,
+                           "ms": ms_step, "frac_whole_eval": roof_ms / ms_step}}
 
 
 def launches_per_eval(m):
@@ -159,17 +196,6 @@ def launches_per_eval(m):
     trtri = lambda t: 1 + 2 * (t - 1)  # diagonal tiles, then product + finish per block diagonal
     return (2 + 1 + chol(nt) + trtri(tr) + 1 + 1   # scaling x2, Sigma_m, Cholesky, inverse, L^-1 operand, A
             + 1 + 2 + 2 + chol(nt1) + 1)          # factor, Gram + reduce, logD sum, capacitance Cholesky, finish
-
-
-# DRAM bytes per point of a kernel, from one ncu capture of the kernel as it stands
-# (dram__bytes_read.sum + dram__bytes_write.sum at n = 100,000; traffic grows with n).
-NCU_DRAM_BYTES_PER_POINT = {
-    # factor_kernel<float, 3> as of 9ae5d38 (captured at 2ae5bb2): 380.2 MB read + 199.9 MB
-    # written for 100,000 points
-    "vecchia_factor": ((380.208384 + 199.875584) * 1e6 / 100_000,
-                       "ncu dram__bytes_read.sum + dram__bytes_write.sum, factor_kernel<float, 3>, n = 100,000, "
-                       "profiles/tc_A_factor_gram_n100k.md"),
-}
 
 
 def host_cpu() -> str:
@@ -451,6 +477,8 @@ def run_vif(args, rank, world, dist):
 
     for _ in range(args.warmup):
         ctx.nll(th, y_dev)
+    # the float32 factor stage's autotuned path (CUDA cores or tensor cores) and its timings
+    factor_tuning = ctx.factor_tuning()
     stage_ms = {k: [] for k in V.STAGES}
     clk = ClockSampler(int(os.environ.get("LOCAL_RANK", 0)))
     barrier()
@@ -479,6 +507,17 @@ def run_vif(args, rank, world, dist):
     e1.record(stream)
     torch.cuda.synchronize()
     ms64 = e0.elapsed_time(e1) / max(args.fp64_steps, 1)
+    # error of the mixed path against the float64 path, per output of the evaluation: the
+    # likelihood and the factors it is built from (A_i and D_i of every point)
+    A32, D32 = ctx.factors()
+    A64, D64 = c64.factors()
+    rD = (D32 - D64) / D64
+    per_output = {"D_i": {"max_rel": float(np.abs(rD).max()), "mean_rel": float(rD.mean()),
+                          "rms_rel": float(np.sqrt((rD ** 2).mean()))},
+                  "A_i": {"max_abs": float(np.abs(A32 - A64).max()),
+                          "rms_abs": float(np.sqrt(((A32 - A64) ** 2).mean()))},
+                  "predictions": "a mixed context predicts through the float64 path (vif_predict): same values"}
+    del A32, D32, A64, D64, rD
 
     # end to end through the C ABI with host buffers: y from pinned host memory, the
     # scalar back to the host, both inside the timed region
@@ -495,21 +534,7 @@ def run_vif(args, rank, world, dist):
     if rank != 0:
         return
     med = {k: statistics.median(v) for k, v in stage_ms.items()}
-    dom = max(("lowrank_A", "vecchia_factor", "gram_FtF"), key=lambda k: med[k])
-    flops, byts = stage_algorithmic(P, dom)
-    pk = peaks()
-    sm_max = pk.get("sm_max_mhz", 2070.0)
-    fp32_peak = 152 * 128 * 2 * sm_max * 1e6 / 1e12        # TFLOP/s, SIMT FP32 FMA at max clock
-    achieved = flops / (med[dom] * 1e-3) / 1e12
-    roof = {"kernel": dom, "bound": "alu", "achieved": achieved, "peak": fp32_peak, "unit": "TFLOP/s",
-            "frac": achieved / fp32_peak,
-            "traffic": (NCU_DRAM_BYTES_PER_POINT[dom][0] * P.X.shape[0] if dom in NCU_DRAM_BYTES_PER_POINT else None),
-            "traffic_source": (NCU_DRAM_BYTES_PER_POINT[dom][1] + " (scaled by n)" if dom in NCU_DRAM_BYTES_PER_POINT
-                               else None),
-            "peak_source": "152 SMs x 128 FP32 lanes x 2 flop x max SM clock (derived)",
-            "algorithmic_flops_per_launch": flops, "algorithmic_bytes_per_launch": byts,
-            "hbm_achieved_gbs": byts / (med[dom] * 1e-3) / 1e9,
-            "hbm_peak_gbs_measured": pk.get("hbm_gbs")}
+    roof = roofline_block(P, med, ms, peaks())
     # the side blocks (Laplace rows, C1/C2, the oracle on the host cores) run at N = 1 only: at N > 1
     # the other GPUs would idle meanwhile and the CPU baseline is a single-GPU-run figure
     single = world == 1
@@ -530,10 +555,11 @@ def run_vif(args, rank, world, dist):
         "fp64_path": {"value": world * 1000.0 / ms64, "unit": UNIT, "ms_per_step": ms64, "dtype": "f64"},
         "mixed_vs_fp64": {"nll_mixed": nll_mixed, "nll_fp64": nll64,
                           "abs_err": abs(nll_mixed - nll64), "rel_err": abs(nll_mixed - nll64) / abs(nll64),
-                          "rel_err_scale": abs(nll_mixed - nll64) / scale},
+                          "rel_err_scale": abs(nll_mixed - nll64) / scale, "per_output": per_output},
         "speedup_mixed_over_fp64": ms64 / ms,
         "stage_ms": med,
         "neighbor_search": {"build_s": build_s, "queries_rescored": rescored, "queries_fallback": fallback},
+        "factor_tuning": factor_tuning,
         "roofline": roof,
         "laplace": lap,
         "batch": bat,

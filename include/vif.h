@@ -70,11 +70,13 @@ typedef struct {
                                  and the caller supplies N(i) with vif_set_neighbors before vif_nll */
   int32_t stage_timing;       /* 1: record CUDA events around every stage of vif_nll (read them with
                                  vif_get_stage_times); 0: no events */
-  int32_t simt_factor;        /* VIF_MIXED only.  0 (default): the residual products A_N^T A_N of the
-                                 Vecchia factors run on the tensor cores (groups of points sharing
-                                 one 128-row Gram) whenever m >= 1 and m_v + 1 <= 32; 1: every point
-                                 forms its own Gram on the CUDA cores (the choice does not change the
-                                 method, only how its float32 products are summed) */
+  int32_t factor_path;        /* VIF_MIXED only: where the residual products A_N^T A_N of the Vecchia
+                                 factors are formed.  1: every point forms its own Gram on the CUDA
+                                 cores; 2: on the tensor cores, groups of points sharing one 128-row
+                                 Gram (when m >= 1 and m_v + 1 <= 32; else as 1); 0 (default):
+                                 autotuned, the first vif_nll times both and keeps the faster
+                                 (vif_get_factor_tuning reports the choice).  The choice changes
+                                 how the float32 products are summed, not the method. */
   int32_t reserved[3];        /* must be zero */
 } vif_opts;
 
@@ -387,6 +389,12 @@ vif_status vif_get_stage_times(const vif_ctx *ctx, double *ms);
 vif_status vif_nll_noalloc(const double *X, int64_t n, int32_t d, const double *Z, int32_t m,
                            const int32_t *N, int32_t mv, const vif_cov *theta, const double *y,
                            void *stream, double *nll_out);
+
+/* vif_get_factor_tuning -- the float32 factor stage's path and the autotuner's timings:
+ * *path = 1 (CUDA cores) or 2 (tensor cores) as used by vif_nll now, 0 while not yet tuned;
+ * ms[0], ms[1] (host, nullable): the CUDA-core and tensor-core times of the tuning run (0 if
+ * not timed).  VIF_ERR_ARG for a NULL context or path. */
+vif_status vif_get_factor_tuning(const vif_ctx *ctx, int32_t *path, double *ms);
 
 /* vif_last_error -- text of the last error on this context ("" if none), valid
  * until the next call on the context; with ctx == NULL, the message of the last

@@ -391,6 +391,31 @@ class VIF:
         quad = float(y @ self.Sigma_dagger_inv(y))
         return 0.5 * (self.n * LOG2PI + self.logdet() + quad)
 
+    def nll_whitened(self, y) -> float:
+        """The same likelihood (Woodbury and Sylvester, Sec. 2.2) evaluated in the basis that the
+        Cholesky factor L_m of Sigma_m whitens: with W = L_m^{-1} Sigma_mn (triangular solve),
+        F = D^{-1/2} B W^T, z = D^{-1/2} B y and u = F^T z,
+            log det M - log det Sigma_m = log det(I + F^T F)        (L_m^{-1} M L_m^{-T} = I + F^T F)
+            y^T Q y - (Sigma_mn Q y)^T M^{-1} Sigma_mn Q y = z^T z - u^T (I + F^T F)^{-1} u.
+        M itself has eigenvalues from those of Sigma_m (1e-4 at n = 5e5, d = 8, m = 500) up to
+        the data's weight (1e7), so its float64 Cholesky carries an error of ~1e-8 of the
+        likelihood at that size (two float64 platforms disagree by that much on the M form);
+        I + F^T F has eigenvalues >= 1.  Used as the reference for large problems, and pinned to
+        the M form and the dense definition on small ones."""
+        ld = float(np.log(self.D).sum())
+        rs = 1.0 / np.sqrt(self.D)
+        z = rs * (self.B @ y)
+        quad = float(z @ z)
+        if self.m:
+            W = sla.solve_triangular(self.lowrank.cf[0], self.lowrank.Smn, lower=True)   # m x n
+            F = (self.B @ W.T) * rs[:, None]                                            # n x m
+            C = np.eye(self.m) + F.T @ F
+            Lc = np.linalg.cholesky(C)
+            w = sla.solve_triangular(Lc, F.T @ z, lower=True)
+            ld += 2.0 * float(np.log(np.diag(Lc)).sum())
+            quad -= float(w @ w)
+        return 0.5 * (self.n * LOG2PI + ld + quad)
+
     def dense_Sigma_dagger(self) -> np.ndarray:
         """Sigma~_dagger = Sigma^l + (B^T D^{-1} B)^{-1}, formed explicitly (small n)."""
         Binv = np.linalg.inv(self.B.toarray())

@@ -35,7 +35,9 @@ struct vif_ctx {
   float* gsub = nullptr;                      // per slot: Gram of the point's rows (packed triangle)
   int64_t ug_ngroups = 0;
   bool ug_ready = false;
-  bool simt_factor = false;                   // keep the per-point Gram on the CUDA cores
+  int factor_mode = 0;                        // 0 autotuned, 1 CUDA cores, 2 tensor cores
+  int factor_choice = -1;                     // autotuned: -1 undecided, 0 CUDA cores, 1 tensor cores
+  float factor_ms[2] = {0.f, 0.f};            // the autotuner's timings (CUDA cores, tensor cores)
   int nsm = 1;
   double *Sm = nullptr, *Linv = nullptr;      // m x ldm
   double* trw = nullptr;                      // triangular-inverse workspace
@@ -282,6 +284,28 @@ vif_status compute_lowrank_parts(vif_ctx* ctx, const CovParams& cp, T* A, T* Lin
   return VIF_OK;
 }
 
+// Whether the float32 path forms the per-point Grams on the tensor cores: when the groups
+// exist and the build asked for it, or the autotuner found it faster.
+bool factor_on_tc(const vif_ctx* ctx) {
+  return ctx->ug_ready && (ctx->factor_mode == 2 || (ctx->factor_mode == 0 && ctx->factor_choice == 1));
+}
+
+// The residual Vecchia factors and the rows of [F z] (Sec. 2.1): on the float32 path with
+// the per-point Grams of A_N^T A_N from the tensor cores (tc), or all on the CUDA cores.
+template <typename T>
+vif_status run_factor(vif_ctx* ctx, const CovParams& cp, T* A, const T* Xs, T* F, bool tc) {
+  const float* gsub = nullptr;
+  if (sizeof(T) == 4 && tc && ctx->ug_ready) {
+    const UnionGroups ug{ctx->ug_rows, ctx->ug_ptr, ctx->ug_loc, ctx->ug_ngroups};
+    CK(union_gram_tc((const float*)A, ctx->mpad, ug, ctx->mv + 1, cp.var, ctx->gsub, ctx->status, ctx->stream,
+                     ctx->nsm));
+    gsub = ctx->gsub;
+  }
+  CK(vecchia_factor_gs<T>(A, Xs, ctx->N, ctx->order, ctx->y, ctx->n, ctx->d, ctx->m, ctx->mpad, ctx->mv,
+                          ctx->fpad, cp, F, ctx->Acoef, ctx->Dv, ctx->logD, ctx->status, ctx->stream, gsub));
+  return VIF_OK;
+}
+
 // The likelihood pipeline of Sec. 2.1-2.2 in precision T on the given buffers:
 // A, the residual Vecchia factors and rows of [F z], the Gram, the augmented
 // capacitance Cholesky and the scalar (left on the device in dscal[1..3]).
@@ -291,15 +315,7 @@ vif_status run_pipeline(vif_ctx* ctx, const CovParams& cp, T* A, T* LinvT, T* F,
   if (ctx->timing) CK(cudaEventRecord(ctx->ev[k], ctx->stream))
   MARK(0);
   CKS(compute_lowrank_parts<T>(ctx, cp, A, LinvT, Xs, Zs));
-  const float* gsub = nullptr;
-  if (sizeof(T) == 4 && ctx->ug_ready) {
-    // the residual products A_N^T A_N on the tensor cores, one 128-row Gram per group
-    const UnionGroups ug{ctx->ug_rows, ctx->ug_ptr, ctx->ug_loc, ctx->ug_ngroups};
-    CK(union_gram_tc((const float*)A, ctx->mpad, ug, ctx->mv + 1, ctx->gsub, ctx->status, ctx->stream, ctx->nsm));
-    gsub = ctx->gsub;
-  }
-  CK(vecchia_factor_gs<T>(A, Xs, ctx->N, ctx->order, ctx->y, ctx->n, ctx->d, ctx->m, ctx->mpad, ctx->mv,
-                          ctx->fpad, cp, F, ctx->Acoef, ctx->Dv, ctx->logD, ctx->status, ctx->stream, gsub));
+  CKS(run_factor<T>(ctx, cp, A, Xs, F, factor_on_tc(ctx)));
   MARK(3);
   CK(gram_FtF<T>(F, ctx->n, ctx->fpad, ctx->m, ctx->part, ctx->nsplit, ctx->G, ctx->fpad, ctx->stream, nullptr,
                  ctx->status));
@@ -526,12 +542,12 @@ vif_status fp64_buffers(vif_ctx* ctx, double** A64, double** F64, double** LT64)
 // sets do not qualify (m = 0, m_v = 0, m_v + 1 > 32) or a group cannot be formed.
 vif_status build_groups(vif_ctx* ctx, const int32_t* hN) {
   ctx->ug_ready = false;
-  if (ctx->precision != VIF_MIXED || ctx->simt_factor || ctx->mv < 1 || ctx->mv + 1 > 32 || ctx->m < 1 ||
+  if (ctx->precision != VIF_MIXED || ctx->factor_mode == 1 || ctx->mv < 1 || ctx->mv + 1 > 32 || ctx->m < 1 ||
       (int64_t)ctx->h_order.size() != ctx->n)
     return VIF_OK;
   std::vector<int32_t> rows, ptr;
   std::vector<unsigned char> loc;
-  if (!build_union_groups(hN, ctx->h_order.data(), ctx->n, ctx->mv, 128, rows, ptr, loc)) return VIF_OK;
+  if (!build_union_groups(hN, ctx->h_order.data(), ctx->n, ctx->mv, UG_MAX_POINTS, rows, ptr, loc)) return VIF_OK;
   for (void* b : {(void*)ctx->ug_rows, (void*)ctx->ug_ptr, (void*)ctx->ug_loc})
     if (b) cudaFree(b);
   ctx->ug_rows = nullptr;
@@ -546,6 +562,7 @@ vif_status build_groups(vif_ctx* ctx, const int32_t* hN) {
   CK(cudaMemcpy(ctx->ug_loc, loc.data(), loc.size(), cudaMemcpyHostToDevice));
   ctx->ug_ngroups = (int64_t)ptr.size() - 1;
   ctx->ug_ready = true;
+  ctx->factor_choice = -1;   // new groups: tune again
   return VIF_OK;
 }
 
@@ -765,7 +782,7 @@ vif_status vif_build(const double* X, int64_t n, int32_t d, const double* Z, int
   if (opts->likelihood != VIF_GAUSSIAN && opts->likelihood != VIF_BERNOULLI_LOGIT) return VIF_ERR_ARG;
   for (int k = 0; k < 3; ++k)
     if (opts->reserved[k] != 0) return VIF_ERR_ARG;
-  if (opts->simt_factor != 0 && opts->simt_factor != 1) return VIF_ERR_ARG;
+  if (opts->factor_path < 0 || opts->factor_path > 2) return VIF_ERR_ARG;
   int ndev = 0;
   if (cudaGetDeviceCount(&ndev) != cudaSuccess || ndev == 0) {
     cudaGetLastError();
@@ -789,7 +806,7 @@ vif_status vif_build(const double* X, int64_t n, int32_t d, const double* Z, int
   ctx->precision = opts->precision;
   ctx->likelihood = opts->likelihood;
   ctx->timing = opts->stage_timing != 0;
-  ctx->simt_factor = opts->simt_factor != 0;
+  ctx->factor_mode = opts->factor_path;
   if (ctx->timing)
     for (auto& e : ctx->ev)
       if (cudaEventCreate(&e) != cudaSuccess) {
@@ -924,6 +941,33 @@ vif_status vif_build(const double* X, int64_t n, int32_t d, const double* Z, int
   return VIF_OK;
 }
 
+// The autotuner of the float32 factor stage (first evaluation of a context whose groups
+// exist): time the stage once on the tensor cores and once on the CUDA cores, on the A just
+// formed, and keep the faster.  The CUDA-core run comes last, so the factors left in the
+// context are those the evaluation itself produced.
+vif_status tune_factor(vif_ctx* ctx, const CovParams& cp) {
+  cudaEvent_t ev[3];
+  for (auto& e : ev) CK(cudaEventCreate(&e));
+  struct G {
+    cudaEvent_t* e;
+    ~G() {
+      for (int k = 0; k < 3; ++k) cudaEventDestroy(e[k]);
+    }
+  } guard{ev};
+  float* A = (float*)ctx->A;
+  float* F = (float*)ctx->F;
+  CK(cudaEventRecord(ev[0], ctx->stream));
+  CKS(run_factor<float>(ctx, cp, A, ctx->Xs32, F, true));
+  CK(cudaEventRecord(ev[1], ctx->stream));
+  CKS(run_factor<float>(ctx, cp, A, ctx->Xs32, F, false));
+  CK(cudaEventRecord(ev[2], ctx->stream));
+  CK(cudaEventSynchronize(ev[2]));
+  CK(cudaEventElapsedTime(&ctx->factor_ms[1], ev[0], ev[1]));
+  CK(cudaEventElapsedTime(&ctx->factor_ms[0], ev[1], ev[2]));
+  ctx->factor_choice = ctx->factor_ms[1] < ctx->factor_ms[0] ? 1 : 0;
+  return VIF_OK;
+}
+
 vif_status vif_nll(vif_ctx* ctx, const vif_cov* theta, const double* y, double* nll_out, double* grad_out) {
   if (!ctx) return VIF_ERR_ARG;
   ctx->err[0] = 0;
@@ -966,6 +1010,7 @@ vif_status vif_nll(vif_ctx* ctx, const vif_cov* theta, const double* y, double* 
   CKS(apply_scaling(ctx, theta, mixed));
   if (mixed) {
     CKS(run_pipeline<float>(ctx, cp, (float*)ctx->A, (float*)ctx->LinvT, (float*)ctx->F, ctx->Xs32, ctx->Zs32));
+    if (ctx->ug_ready && ctx->factor_mode == 0 && ctx->factor_choice < 0) CKS(tune_factor(ctx, cp));
   } else {
     CKS(run_pipeline<double>(ctx, cp, (double*)ctx->A, (double*)ctx->LinvT, (double*)ctx->F, ctx->Xs, ctx->Zs));
   }
@@ -2511,6 +2556,20 @@ vif_status vif_get_stage_times(const vif_ctx* cctx, double* ms) {
     float t = 0.f;
     CK(cudaEventElapsedTime(&t, ctx->ev[k], ctx->ev[k + 1]));
     ms[k] = t;
+  }
+  return VIF_OK;
+}
+
+vif_status vif_get_factor_tuning(const vif_ctx* ctx, int32_t* path, double* ms) {
+  if (!ctx || !path) return VIF_ERR_ARG;
+  const bool tc = ctx->precision == VIF_MIXED && ctx->ug_ready &&
+                  (ctx->factor_mode == 2 || (ctx->factor_mode == 0 && ctx->factor_choice == 1));
+  const bool undecided = ctx->precision == VIF_MIXED && ctx->ug_ready && ctx->factor_mode == 0 &&
+                         ctx->factor_choice < 0;
+  *path = undecided ? 0 : (tc ? 2 : 1);
+  if (ms) {
+    ms[0] = ctx->factor_ms[0];
+    ms[1] = ctx->factor_ms[1];
   }
   return VIF_OK;
 }

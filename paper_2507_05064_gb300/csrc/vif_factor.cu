@@ -76,11 +76,12 @@ __device__ __forceinline__ double rsqrt_refined(double p) {
   return y;
 }
 
-template <typename T, int R>
+template <typename T, int R, bool GS = false>
 struct FactorSmem {
   // float32 with R = 3 (m_v = 14..20): seven-row blocks on 5 column groups of a
-  // 40-column window (see the kernel); otherwise R x R blocks on 128-byte windows
-  static constexpr bool BIG = (sizeof(T) == 4 && R == 3);
+  // 40-column window (see the kernel); otherwise R x R blocks on 128-byte windows.
+  // GS: the Gram comes from the tensor-core kernel, no windows are needed.
+  static constexpr bool BIG = (sizeof(T) == 4 && R == 3 && !GS);
   static constexpr int QM = FK_NB * R;
   static constexpr int V = Vec16<T>::n;       // elements per 16 bytes
   static constexpr int GK = 5;                // BIG: column groups
@@ -94,7 +95,7 @@ struct FactorSmem {
     T part[PL][PE];
   };
   union {
-    alignas(16) T buf[2][QM][LD];
+    alignas(16) T buf[2][GS ? 1 : QM][LD];
     Post post;
   };
   T G[QM][QM + 1];
@@ -123,13 +124,13 @@ __device__ __forceinline__ T sqdist_rows(const T* __restrict__ xa, const T* __re
 }
 
 // float32 m_v = 20 (R = 3): six CTAs of four warps per SM, as the shared memory allows
-template <typename T, int R>
+template <typename T, int R, bool GS>
 __global__ __launch_bounds__(FK_WARPS * 32) void factor_kernel(
     const T* __restrict__ A, const T* __restrict__ Xs, const int32_t* __restrict__ N,
     const int32_t* __restrict__ order, const double* __restrict__ y, int64_t n, int d, int m, int mpad, int mv,
     int fpad, CovParams cp, T* __restrict__ F, double* __restrict__ Acoef, double* __restrict__ Dv,
-    double* __restrict__ logD, int* status) {
-  using SM = FactorSmem<T, R>;
+    double* __restrict__ logD, int* status, const float* __restrict__ gsub) {
+  using SM = FactorSmem<T, R, GS>;
   constexpr int QM = SM::QM, V = SM::V, KC = SM::KC;
   using VT = typename Vec16<T>::type;
   extern __shared__ __align__(16) unsigned char smraw[];
@@ -148,6 +149,8 @@ __global__ __launch_bounds__(FK_WARPS * 32) void factor_kernel(
     }
     S.idx[t] = j;
   }
+  __syncwarp();
+  if constexpr (!GS) {
   // rows Q..QM-1 of both windows stay zero (none once i >= m_v)
   for (int e = lane; e < 2 * (QM - Q) * SM::LD; e += 32) {
     const int b = e / ((QM - Q) * SM::LD), r = e % ((QM - Q) * SM::LD);
@@ -280,6 +283,7 @@ __global__ __launch_bounds__(FK_WARPS * 32) void factor_kernel(
   }
   __syncwarp();
   }
+  }  // !GS: the Gram of the gathered rows is in S.G
   // coordinates of the rows (their space was the windows')
   for (int e = lane; e < Q * d; e += 32) {
     const int t = e / d, c = e % d;
@@ -301,7 +305,10 @@ __global__ __launch_bounds__(FK_WARPS * 32) void factor_kernel(
     }
     T kv = cov_r2<T>(sqdist_rows(&S.post.xc[a][0], &S.post.xc[b2][0], d), cp.kind, (T)cp.var);
     if (a == b2) kv += (T)cp.tdiag;
-    S.G[a][b2] = kv - S.G[a][b2];
+    if constexpr (GS)
+      S.G[a][b2] = kv - (T)gsub[(size_t)slot * ((mv + 1) * (mv + 2) / 2) + e];
+    else
+      S.G[a][b2] = kv - S.G[a][b2];
   }
   __syncwarp();
   T inv;   // 1 / sqrt(D_i)
@@ -445,27 +452,43 @@ __global__ __launch_bounds__(FK_WARPS * 32) void factor_kernel(
   if (lane == 0) F[(size_t)i * fpad + m] = (T)((y[i] + zt) * (double)inv);
 }
 
-template <typename T, int R>
+template <typename T, int R, bool GS>
 static cudaError_t launch_factor(const T* A, const T* Xs, const int32_t* N, const int32_t* order, const double* y,
                                  int64_t n, int d, int m, int mpad, int mv, int fpad, CovParams cp, T* F,
-                                 double* Acoef, double* Dv, double* logD, int* status, cudaStream_t s) {
-  size_t smem = sizeof(FactorSmem<T, R>) * FK_WARPS;
-  cudaError_t e = cudaFuncSetAttribute(factor_kernel<T, R>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 double* Acoef, double* Dv, double* logD, int* status, cudaStream_t s,
+                                 const float* gsub) {
+  size_t smem = sizeof(FactorSmem<T, R, GS>) * FK_WARPS;
+  cudaError_t e = cudaFuncSetAttribute(factor_kernel<T, R, GS>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        (int)smem);
   if (e != cudaSuccess) return e;
   unsigned grid = (unsigned)((n + FK_WARPS - 1) / FK_WARPS);
-  factor_kernel<T, R><<<grid, FK_WARPS * 32, smem, s>>>(A, Xs, N, order, y, n, d, m, mpad, mv, fpad, cp, F,
-                                                         Acoef, Dv, logD, status);
+  factor_kernel<T, R, GS><<<grid, FK_WARPS * 32, smem, s>>>(A, Xs, N, order, y, n, d, m, mpad, mv, fpad, cp, F,
+                                                             Acoef, Dv, logD, status, gsub);
   return cudaGetLastError();
 }
 
 template <typename T>
-cudaError_t vecchia_factor(const T* A, const T* Xs, const int32_t* N, const int32_t* order, const double* y,
-                           int64_t n, int d, int m, int mpad, int mv, int fpad, CovParams cp, T* F, double* Acoef,
-                           double* Dv, double* logD, int* status, cudaStream_t s) {
+cudaError_t vecchia_factor_gs(const T* A, const T* Xs, const int32_t* N, const int32_t* order, const double* y,
+                              int64_t n, int d, int m, int mpad, int mv, int fpad, CovParams cp, T* F,
+                              double* Acoef, double* Dv, double* logD, int* status, cudaStream_t s,
+                              const float* gsub) {
   if (d > FK_MAXD) return cudaErrorInvalidValue;
   const int Q = mv + 1;
-#define LF(RR) launch_factor<T, RR>(A, Xs, N, order, y, n, d, m, mpad, mv, fpad, cp, F, Acoef, Dv, logD, status, s)
+  if (gsub) {
+    // the Gram of each point's rows comes from the tensor cores (float32, Q <= 32)
+    if constexpr (sizeof(T) == 4) {
+#define LG(RR) launch_factor<T, RR, true>(A, Xs, N, order, y, n, d, m, mpad, mv, fpad, cp, F, Acoef, Dv, logD, \
+                                          status, s, gsub)
+      if (Q <= 14) return LG(2);
+      if (Q <= 21) return LG(3);
+      if (Q <= 28) return LG(4);
+      if (Q <= 32) return LG(5);
+#undef LG
+    }
+    return cudaErrorInvalidValue;
+  }
+#define LF(RR) launch_factor<T, RR, false>(A, Xs, N, order, y, n, d, m, mpad, mv, fpad, cp, F, Acoef, Dv, logD, \
+                                           status, s, nullptr)
   if (Q <= 14) return LF(2);
   if (Q <= 21) return LF(3);
   if (Q <= 28) return LF(4);
@@ -475,6 +498,21 @@ cudaError_t vecchia_factor(const T* A, const T* Xs, const int32_t* N, const int3
 #undef LF
   return cudaErrorInvalidValue;
 }
+
+template <typename T>
+cudaError_t vecchia_factor(const T* A, const T* Xs, const int32_t* N, const int32_t* order, const double* y,
+                           int64_t n, int d, int m, int mpad, int mv, int fpad, CovParams cp, T* F, double* Acoef,
+                           double* Dv, double* logD, int* status, cudaStream_t s) {
+  return vecchia_factor_gs<T>(A, Xs, N, order, y, n, d, m, mpad, mv, fpad, cp, F, Acoef, Dv, logD, status, s,
+                              nullptr);
+}
+template cudaError_t vecchia_factor_gs<float>(const float*, const float*, const int32_t*, const int32_t*,
+                                              const double*, int64_t, int, int, int, int, int, CovParams, float*,
+                                              double*, double*, double*, int*, cudaStream_t, const float*);
+template cudaError_t vecchia_factor_gs<double>(const double*, const double*, const int32_t*, const int32_t*,
+                                               const double*, int64_t, int, int, int, int, int, CovParams,
+                                               double*, double*, double*, double*, int*, cudaStream_t,
+                                               const float*);
 template cudaError_t vecchia_factor<float>(const float*, const float*, const int32_t*, const int32_t*,
                                            const double*, int64_t, int, int, int, int, int, CovParams, float*,
                                            double*, double*, double*, int*, cudaStream_t);

@@ -164,10 +164,12 @@ struct UnionGroups {
   const unsigned char* loc;   // n x 32: group-local row of each of a slot's rows (0xFF beyond)
   int64_t ngroups;
 };
+constexpr int UG_MAX_POINTS = 128;   // points per group (the kernel's table of local rows)
 cudaError_t union_gram_tc_init();
-// nsm: SM count of the device (one persistent CTA per SM)
-cudaError_t union_gram_tc(const float* A, int mpad, const UnionGroups& ug, int Q, float* gsub, int* status,
-                          cudaStream_t s, int nsm);
+// var: sigma_1^2 (bounds |A_ij| and so the float16 scaling); nsm: SM count of the device
+// (one persistent CTA per SM)
+cudaError_t union_gram_tc(const float* A, int mpad, const UnionGroups& ug, int Q, double var, float* gsub,
+                          int* status, cudaStream_t s, int nsm);
 bool build_union_groups(const int32_t* N, const int32_t* order, int64_t n, int mv, int max_pts,
                         std::vector<int32_t>& rows, std::vector<int32_t>& ptr, std::vector<unsigned char>& loc);
 // wrow: optional row weights (NULL = 1): G = F^T diag(wrow) F (+ identity on the first m).

@@ -28,7 +28,7 @@ EXPORTS = ["vif_build", "vif_nll", "vif_predict", "vif_laplace_mode", "vif_lapla
            "vif_tridiag_log_quadrature", "vif_batch_create", "vif_batch_run",
            "vif_batch_info", "vif_batch_destroy", "vif_mlp_bytes", "vif_mlp_init", "vif_mlp_set_params",
            "vif_mlp_get_params", "vif_mlp_forward", "vif_mlp_backward", "vif_mlp_features", "vif_mlp_train", "vif_set_neighbors", "vif_get_neighbors",
-           "vif_get_factors", "vif_get_knn_stats", "vif_get_stage_times", "vif_nll_noalloc",
+           "vif_get_factors", "vif_get_knn_stats", "vif_get_stage_times", "vif_get_factor_tuning", "vif_nll_noalloc",
            "vif_last_error", "vif_destroy"]
 NOALLOC_SCRATCH_BYTES = 32 << 20
 
@@ -40,7 +40,7 @@ class VifCov(C.Structure):
 
 class VifOpts(C.Structure):
     _fields_ = [("precision", C.c_int32), ("likelihood", C.c_int32), ("no_neighbor_search", C.c_int32),
-                ("stage_timing", C.c_int32), ("simt_factor", C.c_int32), ("reserved", C.c_int32 * 3)]
+                ("stage_timing", C.c_int32), ("factor_path", C.c_int32), ("reserved", C.c_int32 * 3)]
 
 
 class LaplaceOpts(C.Structure):
@@ -117,6 +117,7 @@ def lib() -> C.CDLL:
         L.vif_get_factors.argtypes = [vp, vp, vp]
         L.vif_get_knn_stats.argtypes = [vp, C.POINTER(i64), C.POINTER(i64)]
         L.vif_get_stage_times.argtypes = [vp, dp]
+        L.vif_get_factor_tuning.argtypes = [vp, C.POINTER(i32), dp]
         L.vif_nll_noalloc.argtypes = [vp, i64, i32, vp, i32, vp, i32, C.POINTER(VifCov), vp, vp, dp]
         L.vif_batch_create.argtypes = [C.POINTER(vp), i32, C.POINTER(VifCov), C.POINTER(vp), vp, C.POINTER(vp)]
         L.vif_batch_run.argtypes = [vp, dp]
@@ -298,7 +299,7 @@ class Context:
 
     def __init__(self, X, Z, mv: int, theta, precision: int = FP64, likelihood: int = GAUSSIAN,
                  stream: int = 0, neighbor_search: bool = True, stage_timing: bool = False,
-                 simt_factor: bool = False):
+                 factor_path: int = 0):
         L = lib()
         X = _f64(X)
         Z = _f64(Z) if Z is not None and Z.shape[0] > 0 else None
@@ -308,7 +309,7 @@ class Context:
         self.precision = precision
         cv, ls = make_cov(theta)
         opts = VifOpts(precision, likelihood, 0 if neighbor_search else 1, 1 if stage_timing else 0,
-                       1 if simt_factor else 0, (C.c_int32 * 3)())
+                       int(factor_path), (C.c_int32 * 3)())
         h = C.c_void_p()
         st = L.vif_build(_ptr(X), self.n, self.d, _ptr(Z), self.m, self.mv, C.byref(cv), C.byref(opts),
                          C.c_void_p(stream), C.byref(h))
@@ -461,6 +462,14 @@ class Context:
         a, b = C.c_int64(), C.c_int64()
         self._check(lib().vif_get_knn_stats(self.h, C.byref(a), C.byref(b)))
         return a.value, b.value
+
+    def factor_tuning(self) -> dict:
+        """The float32 factor stage's path (1 CUDA cores, 2 tensor cores, 0 not yet tuned)
+        and the autotuner's timings in ms."""
+        p = C.c_int32()
+        ms = (C.c_double * 2)()
+        self._check(lib().vif_get_factor_tuning(self.h, C.byref(p), ms))
+        return {"path": p.value, "ms_cuda_cores": ms[0], "ms_tensor_cores": ms[1]}
 
     def stage_times(self) -> dict:
         ms = (C.c_double * NSTAGES)()

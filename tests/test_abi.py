@@ -48,12 +48,12 @@ def test_build_rejects_bad_arguments_before_touching_the_gpu(lib):
     X = np.zeros((4, 2))
     ls = np.array([0.1])
     cv = V.VifCov(1, 1.0, ls.ctypes.data_as(C.POINTER(C.c_double)), 1, 0.1)
-    opts = V.VifOpts(0, 0, 0, 0, (C.c_int32 * 4)())
+    opts = V.VifOpts(0, 0, 0, 0, 0, (C.c_int32 * 3)())
     h = C.c_void_p()
     # d out of range, mv out of range, bad precision: rejected by argument checks
     assert lib.vif_build(V._ptr(X), 4, 17, None, 0, 2, C.byref(cv), C.byref(opts), None, C.byref(h)) == V.VIF_ERR_ARG
     assert lib.vif_build(V._ptr(X), 4, 2, None, 0, 99, C.byref(cv), C.byref(opts), None, C.byref(h)) == V.VIF_ERR_ARG
-    bad = V.VifOpts(7, 0, 0, 0, (C.c_int32 * 4)())
+    bad = V.VifOpts(7, 0, 0, 0, 0, (C.c_int32 * 3)())
     assert lib.vif_build(V._ptr(X), 4, 2, None, 0, 2, C.byref(cv), C.byref(bad), None, C.byref(h)) == V.VIF_ERR_ARG
     assert lib.vif_last_error(None) is not None
 

@@ -217,6 +217,21 @@ def test_no_inducing_points_is_classical_vecchia():
     assert O.vif_nll(P.X, P.Z, th, N, P.y) == pytest.approx(O.dense_nll(Sv, P.y), rel=1e-10)
 
 
+@pytest.mark.parametrize("m,mv,kind,nugget", [(30, 8, "matern32", 0.1), (0, 6, "matern52", 0.05),
+                                              (25, 0, "se", 0.02)])
+def test_whitened_evaluation_equals_the_m_form_and_the_dense_likelihood(m, mv, kind, nugget):
+    """nll_whitened (the Sylvester ratio det M / det Sigma_m as det(L_m^{-1} M L_m^{-T})) gives the
+    likelihood of the M form and of the explicitly formed Sigma~_dagger, with and without
+    inducing points and neighbours."""
+    P = small_problem(n=400, m=m, mv=mv, kind=kind, nugget=nugget, ls=0.25)
+    N = O.causal_neighbors(P.X, P.Z, P.theta, mv) if mv else np.zeros((400, 0), dtype=np.int64)
+    vif = O.VIF(P.X, P.Z, P.theta, N)
+    a, b = vif.nll_whitened(P.y), vif.nll(P.y)
+    dense = O.dense_nll(vif.dense_Sigma_dagger(), P.y)
+    assert a == pytest.approx(b, rel=1e-11)
+    assert a == pytest.approx(dense, rel=1e-10)
+
+
 def test_woodbury_sylvester_equals_dense_vif_likelihood():
     P = small_problem(n=250, m=25, mv=7, nugget=0.05, kind="se", ls=np.array([0.1, 0.2]))
     N = O.causal_neighbors(P.X, P.Z, P.theta, 7)
