@@ -13,14 +13,15 @@
 // accumulators alternate so that the MMAs of chunk c run while the partial of chunk
 // c-1 is read out.
 //
-// CTA: 128 points (one TMEM lane each) x 256 output columns, 16 warps.  Per chunk every
-// thread evaluates 8 kernel values of one point, splits them and writes them into the
-// swizzled A-operand tiles; thread 0 brings the matching L_m^{-1} tiles (packed once
-// per call, already in the swizzled image) with one bulk copy per tile and issues the
-// 12 MMAs.  Two operand stages let the kernel evaluation of chunk c+1 overlap the MMAs
-// of chunk c; the inducing points of chunk c+1 are prefetched into registers and the
-// L_m^{-1} tiles of chunk c+1 are requested as soon as their stage is free.  Chunks
-// above the tile's last column are skipped (L_m^{-1} is lower triangular).
+// CTA: 128 points (one TMEM lane each) x 256 output columns; 16 compute warps and one MMA
+// warp.  Per chunk every compute thread evaluates 8 kernel values of one point, splits
+// them and writes them into the swizzled A-operand tiles of the chunk's stage, then reads
+// out the previous chunk's accumulator; thread 0 also brings the L_m^{-1} tiles (packed once
+// per call, already in the swizzled image) of the next chunk with one bulk copy per tile.
+// The MMA warp issues a chunk's 12 MMAs as soon as its tiles are staged and its
+// accumulator read out, so the kernel evaluation and read-out of neighbouring chunks run
+// while the tensor core works (hand-offs through mbarriers, no CTA-wide barrier per chunk).
+// Chunks above the tile's last column are skipped (L_m^{-1} is lower triangular).
 #include "vif_internal.cuh"
 #include "vif_tc.cuh"
 
@@ -32,7 +33,8 @@ constexpr int AT_M = 128;                         // points per CTA
 constexpr int AT_N = 256;                         // output columns per CTA
 constexpr int AT_K = 32;                          // inducing points per chunk
 constexpr int AT_MAXD = 16;
-constexpr int AT_THREADS = 512;
+constexpr int AT_CT = 512;                        // compute threads
+constexpr int AT_THREADS = AT_CT + 32;            // + the MMA warp
 constexpr uint32_t AT_ATILE = AT_M * 128;         // bytes of one A-operand tile (hi or lo)
 constexpr uint32_t AT_BTILE = AT_N * 128;         // bytes of one B-operand tile (hi or lo)
 constexpr uint32_t AT_STAGE = 2 * AT_ATILE + 2 * AT_BTILE;
@@ -41,9 +43,12 @@ constexpr uint32_t AT_TMEM_COLS = 2 * AT_N;       // two accumulators
 
 struct __align__(16) AtBars {
   uint64_t full[2];    // B tiles of the stage have landed
+  uint64_t staged[2];  // A tiles of the stage written (one arrival per compute thread)
+  uint64_t drained[2]; // accumulator s read out (one arrival per compute thread)
   uint64_t done[2];    // MMAs of the stage's chunk are done: stage free, accumulator s ready
   uint64_t fin;        // every MMA of the CTA is done
   uint32_t tmem;
+  int abort;           // the MMA warp gave up waiting
   alignas(16) float zs[2][AT_K * AT_MAXD];   // 8-byte pairs are read from it
 };
 
@@ -83,8 +88,8 @@ __global__ __launch_bounds__(AT_THREADS, 1) void lowrank_A_tc_kernel(
   const int nchunk = min(nchunk_all, (h * AT_N + ncols - 1) / AT_K + 1);
   const uint32_t idesc = tc::idesc_tf32(AT_M, ncols);
   const float* pk_h = pk + (size_t)h * nchunk_all * 2 * (AT_N * AT_K);
-  // kernel evaluation: point krow, values 8 kq .. 8 kq + 7 of each chunk
-  const int krow = tid & (AT_M - 1), kq = tid >> 7;
+  // kernel evaluation: point krow, values 8 kq .. 8 kq + 7 of each chunk (compute threads)
+  const int krow = tid & (AT_M - 1), kq = (tid >> 7) & 3;
   const int64_t p = row0 + krow;
   // read-out: TMEM lanes dl .. dl + 31, columns dc .. dc + 63 of the accumulator
   const int dl = 32 * (warp & 3), dc = 64 * (warp >> 2);
@@ -94,9 +99,12 @@ __global__ __launch_bounds__(AT_THREADS, 1) void lowrank_A_tc_kernel(
   if (tid == 0) {
     for (int s = 0; s < 2; ++s) {
       tc::mbar_init(&sb.full[s], 1);
+      tc::mbar_init(&sb.staged[s], AT_CT);
+      tc::mbar_init(&sb.drained[s], AT_CT);
       tc::mbar_init(&sb.done[s], 1);
     }
     tc::mbar_init(&sb.fin, 1);
+    sb.abort = 0;
     tc::fence_mbar_init();
   }
   constexpr int DX = D > 0 ? D : AT_MAXD;
@@ -111,7 +119,7 @@ __global__ __launch_bounds__(AT_THREADS, 1) void lowrank_A_tc_kernel(
   auto zload = [&](int c, float (&zr)[1]) {
 #pragma unroll
     for (int j = 0; j < 1; ++j) {
-      const int e = tid + AT_THREADS * j;
+      const int e = tid + AT_CT * j;
       const int k = c * AT_K + e / max(d, 1);
       zr[j] = (c < nchunk && e < AT_K * d && k < m) ? Zs[(size_t)c * AT_K * d + e] : 0.f;
     }
@@ -136,19 +144,21 @@ __global__ __launch_bounds__(AT_THREADS, 1) void lowrank_A_tc_kernel(
     }
     tc::fence_after_sync();
     const uint32_t base = tmem + ((uint32_t)dl << 16) + (uint32_t)((j & 1) * AT_N + dc);
+    // 16-column pieces (few live registers); the accumulator is released once all are read
 #pragma unroll
-    for (int g = 0; g < 2; ++g) {
-      if (g < ngrp) {
-        float v[32];
-        tc::tmem_ld32(base + g * 32, v);
+    for (int g = 0; g < 4; ++g) {
+      if (g < 2 * ngrp) {
+        float v[16];
+        tc::tmem_ld16(base + g * 16, v);
 #pragma unroll
-        for (int i = 0; i < 16; ++i) acc2[g * 16 + i] = fadd2(acc2[g * 16 + i], pack_f2(v[2 * i], v[2 * i + 1]));
+        for (int i = 0; i < 8; ++i) acc2[g * 8 + i] = fadd2(acc2[g * 8 + i], pack_f2(v[2 * i], v[2 * i + 1]));
       }
     }
     tc::fence_before_sync();
+    tc::mbar_arrive(&sb.drained[j & 1]);
   };
   // L_m^{-1} tiles of chunk c into stage c % 2 (thread 0)
-  int copies_issued[2] = {0, 0}, copies_seen[2] = {0, 0};
+  int copies_issued[2] = {0, 0};
   auto fetch_b = [&](int c) {
     const int s = c & 1;
     unsigned char* st = smem + s * AT_STAGE;
@@ -160,83 +170,23 @@ __global__ __launch_bounds__(AT_THREADS, 1) void lowrank_A_tc_kernel(
   };
   if (tid == 0 && nchunk > 0) fetch_b(0);
 
-  for (int c = 0; c < nchunk; ++c) {
-    const int s = c & 1;
-    unsigned char* st = smem + s * AT_STAGE;
-    unsigned char* a_hi = st;
-    unsigned char* a_lo = st + AT_ATILE;
-    unsigned char* b_hi = st + 2 * AT_ATILE;
-    unsigned char* b_lo = st + 2 * AT_ATILE + AT_BTILE;
-    // stage s was last read by the MMAs of chunk c-2, read out at iteration c-1
-#pragma unroll
-    for (int j = 0; j < 1; ++j) {
-      const int e = tid + AT_THREADS * j;
-      if (e < AT_K * AT_MAXD) sb.zs[s][e] = zpre[j];
-    }
-    zload(c + 1, zpre);
-    if (__syncthreads_or(failed)) {
-      failed = true;
-      break;
-    }
-    // 8 kernel values of this thread's point, split into tf32 hi + lo
-    const int kmax = min(AT_K, m - c * AT_K);
-#pragma unroll
-    for (int q = 0; q < 2; ++q) {
-      float hv[4], lv[4];
-#pragma unroll
-      for (int u = 0; u < 4; ++u) {
-        const int kk = kq * 8 + q * 4 + u;
-        float kv = 0.f;
-        if (kk < kmax && p < n) {
-          float r2 = 0.f;
-          if constexpr (D > 0 && D % 2 == 0) {
-            const float2* z2 = reinterpret_cast<const float2*>(&sb.zs[s][kk * D]);
-            unsigned long long a2 = 0ull;
-#pragma unroll
-            for (int j = 0; j < DP; ++j) {
-              const float2 zz = z2[j];
-              const unsigned long long df = fsub2(xp[j], pack_f2(zz.x, zz.y));
-              a2 = ffma2(df, df, a2);
-            }
-            const float2 h2 = unpack_f2(a2);
-            r2 = h2.x + h2.y;
-          } else if constexpr (D > 0) {
-            const float* z = &sb.zs[s][kk * D];
-#pragma unroll
-            for (int t = 0; t < D; ++t) {
-              const float df = x[t] - z[t];
-              r2 = fmaf(df, df, r2);
-            }
-          } else {
-            const float* z = &sb.zs[s][kk * d];
-#pragma unroll
-            for (int t = 0; t < AT_MAXD; ++t)
-              if (t < d) {
-                const float df = x[t] - z[t];
-                r2 = fmaf(df, df, r2);
-              }
-          }
-          kv = cov_r2_fast(r2, kind, var);
+  if (warp == AT_CT / 32) {
+    // ------------------------------------------------------------ MMA warp (one lane)
+    if (lane == 0) {
+      for (int c = 0; c < nchunk; ++c) {
+        const int s = c & 1;
+        const uint32_t ph = (uint32_t)(c >> 1) & 1u;
+        if (!tc::mbar_wait(&sb.staged[s], ph) || !tc::mbar_wait(&sb.full[s], ph) ||
+            (c >= 2 && !tc::mbar_wait(&sb.drained[s], ph ^ 1u))) {
+          failed = true;
+          sb.abort = 1;
+          break;
         }
-        hv[u] = tc::to_tf32(kv);
-        lv[u] = tc::to_tf32(kv - hv[u]);
-      }
-      const uint32_t off = tc::sw128_off32(krow, kq * 8 + q * 4);
-      *reinterpret_cast<float4*>(a_hi + off) = make_float4(hv[0], hv[1], hv[2], hv[3]);
-      *reinterpret_cast<float4*>(a_lo + off) = make_float4(lv[0], lv[1], lv[2], lv[3]);
-    }
-    tc::fence_proxy_async();
-    tc::fence_before_sync();
-    __syncthreads();
-    if (tid == 0) {
-      tc::fence_after_sync();
-      if (!tc::mbar_wait(&sb.full[s], copies_seen[s] & 1)) {
-        failed = true;
-      } else {
-        ++copies_seen[s];
+        tc::fence_after_sync();
+        unsigned char* st = smem + s * AT_STAGE;
         const uint32_t dt = tmem + (uint32_t)(s * AT_N);
-        const uint32_t ah = tc::smem_addr(a_hi), al = tc::smem_addr(a_lo);
-        const uint32_t bh = tc::smem_addr(b_hi), bl = tc::smem_addr(b_lo);
+        const uint32_t ah = tc::smem_addr(st), al = ah + AT_ATILE;
+        const uint32_t bh = ah + 2 * AT_ATILE, bl = bh + AT_BTILE;
         // the small cross terms first, the hi x hi products last: every accumulation
         // step truncates relative to the running sum, so the steps taken once the sum
         // is large are kept to the four hi x hi ones
@@ -251,24 +201,93 @@ __global__ __launch_bounds__(AT_THREADS, 1) void lowrank_A_tc_kernel(
           const uint32_t o = ks * 32;
           tc::mma_tf32(dt, tc::desc_k_sw128(ah + o), tc::desc_k_sw128(bh + o), idesc, 1u);
         }
+        tc::mma_commit(&sb.done[s]);
       }
-      tc::mma_commit(&sb.done[s]);
+      // every MMA issued by this CTA completes on `fin`
+      tc::mma_commit(&sb.fin);
     }
-    // read out chunk c-1 while chunk c multiplies; its MMAs were the last readers of
-    // stage (c+1) % 2, which then takes the L_m^{-1} tiles of chunk c+1
-    if (c >= 1 && !failed) drain(c - 1);
-    if (tid == 0 && !failed && c + 1 < nchunk) fetch_b(c + 1);
-  }
-  if (!failed && nchunk > 0) drain(nchunk - 1);
-  // every MMA issued by this CTA completes on `fin`
-  if (tid == 0) {
-    tc::mma_commit(&sb.fin);
-    // copies issued but never waited for (after a failure, or prefetched past a break)
-    for (int s = 0; s < 2; ++s)
-      while (copies_seen[s] < copies_issued[s]) {
-        if (!tc::mbar_wait(&sb.full[s], copies_seen[s] & 1)) break;
-        ++copies_seen[s];
+    __syncwarp();
+  } else {
+    // ------------------------------------------------------------ compute warps
+    for (int c = 0; c < nchunk; ++c) {
+      const int s = c & 1;
+      unsigned char* st = smem + s * AT_STAGE;
+      unsigned char* a_hi = st;
+      unsigned char* a_lo = st + AT_ATILE;
+      // zs[s] was last read at iteration c-2; everyone passed the barrier of iteration c-1
+#pragma unroll
+      for (int j = 0; j < 1; ++j) {
+        const int e = tid + AT_CT * j;
+        if (e < AT_K * AT_MAXD) sb.zs[s][e] = zpre[j];
       }
+      zload(c + 1, zpre);
+      if (tc::bar_sync_or(1, AT_CT, failed || sb.abort)) {
+        failed = true;
+        break;
+      }
+      // stage s was last read by the MMAs of chunk c-2, which this thread saw finish when it
+      // read out chunk c-2 at iteration c-1
+      const int kmax = min(AT_K, m - c * AT_K);
+#pragma unroll
+      for (int q = 0; q < 2; ++q) {
+        float hv[4], lv[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+          const int kk = kq * 8 + q * 4 + u;
+          float kv = 0.f;
+          if (kk < kmax && p < n) {
+            float r2 = 0.f;
+            if constexpr (D > 0 && D % 2 == 0) {
+              const float2* z2 = reinterpret_cast<const float2*>(&sb.zs[s][kk * D]);
+              unsigned long long a2 = 0ull;
+#pragma unroll
+              for (int j = 0; j < DP; ++j) {
+                const float2 zz = z2[j];
+                const unsigned long long df = fsub2(xp[j], pack_f2(zz.x, zz.y));
+                a2 = ffma2(df, df, a2);
+              }
+              const float2 h2 = unpack_f2(a2);
+              r2 = h2.x + h2.y;
+            } else if constexpr (D > 0) {
+              const float* z = &sb.zs[s][kk * D];
+#pragma unroll
+              for (int t = 0; t < D; ++t) {
+                const float df = x[t] - z[t];
+                r2 = fmaf(df, df, r2);
+              }
+            } else {
+              const float* z = &sb.zs[s][kk * d];
+#pragma unroll
+              for (int t = 0; t < AT_MAXD; ++t)
+                if (t < d) {
+                  const float df = x[t] - z[t];
+                  r2 = fmaf(df, df, r2);
+                }
+            }
+            kv = cov_r2_fast(r2, kind, var);
+          }
+          hv[u] = tc::to_tf32(kv);
+          lv[u] = tc::to_tf32(kv - hv[u]);
+        }
+        const uint32_t off = tc::sw128_off32(krow, kq * 8 + q * 4);
+        *reinterpret_cast<float4*>(a_hi + off) = make_float4(hv[0], hv[1], hv[2], hv[3]);
+        *reinterpret_cast<float4*>(a_lo + off) = make_float4(lv[0], lv[1], lv[2], lv[3]);
+      }
+      tc::fence_proxy_async();
+      tc::fence_before_sync();
+      tc::mbar_arrive(&sb.staged[s]);
+      // read out chunk c-1 while chunk c multiplies; its MMAs were the last readers of
+      // stage (c+1) % 2, which then takes the L_m^{-1} tiles of chunk c+1
+      if (c >= 1 && !failed) drain(c - 1);
+      if (tid == 0 && !failed && c + 1 < nchunk) fetch_b(c + 1);
+    }
+    if (!failed && nchunk > 0) drain(nchunk - 1);
+    if (tid == 0) {
+      // copies issued but possibly not landed (after a failure): wait for the last one of
+      // each stage (bounded) so that none lands after the CTA has left
+      for (int s = 0; s < 2; ++s)
+        if (copies_issued[s] > 0) tc::mbar_wait(&sb.full[s], (uint32_t)(copies_issued[s] - 1) & 1u);
+    }
   }
   // a wait that gave up may leave MMAs in flight: wait for them once more (bounded) before
   // the accumulators' TMEM is released; if they still have not finished, the TMEM is
@@ -281,7 +300,7 @@ __global__ __launch_bounds__(AT_THREADS, 1) void lowrank_A_tc_kernel(
   }
   if (__syncthreads_or(failed)) {
     if (tid == 0 && status) flag_status(status, ST_TIMEOUT, blockIdx.x);
-  } else {
+  } else if (warp < AT_CT / 32) {
     const int64_t row = row0 + dl + lane;
     if (row < n) {
       float* dst = A + (size_t)row * mpad + h * AT_N + dc;
