@@ -153,31 +153,41 @@ def stage_algorithmic(P, stage):
     return 0.0, 0.0
 
 
-def roofline_block(P, med, ms_step, pk):
-    """Roofline of the dense contractions (tensor-core bound, TF32) and of HBM, per stage and
-    for the whole evaluation.  The TF32 peak is the measured dense bf16 burst peak times the
-    nominal tf32 : bf16 ratio of 1/2; HBM is the measured copy bandwidth."""
+def roofline_block(P, med, ms_step, pk, factor_path=1):
+    """Roofline of the dense contractions (tensor-core bound) and of HBM, per stage and for the
+    whole evaluation.  Each contraction is held to the tensor peak of the type it runs in:
+    A (float16 split) and the tensor-core factor path at the measured dense bf16 burst peak
+    (float16 has the same nominal rate), the Gram (tf32 split) at half of it (the nominal
+    tf32 : bf16 ratio); the CUDA-core factor path is also held to the tf32 figure.  HBM is the
+    measured copy bandwidth."""
     bf16 = pk.get("bf16_tflops")
-    tf32 = bf16 / 2.0 if bf16 else 1900.0 / 2.0
-    hbm = pk.get("hbm_gbs") or 6800.0
     src = ("measured" if bf16 else "fallback")
+    bf16 = bf16 or 1900.0
+    hbm = pk.get("hbm_gbs") or 6800.0
+    peak_of = {"lowrank_A": ("f16", bf16),
+               "vecchia_factor": ("f16", bf16) if factor_path == 2 else ("tf32", bf16 / 2.0),
+               "gram_FtF": ("tf32", bf16 / 2.0)}
     stages = {}
-    tot_f = tot_b = 0.0
+    tot_f = tot_b = t_tensor = 0.0
     for st in ("lowrank_A", "vecchia_factor", "gram_FtF"):
         f, b = stage_algorithmic(P, st)
+        dt, pkt = peak_of[st]
         tot_f += f
         tot_b += b
+        t_tensor += f / (pkt * 1e12)
         t = med[st] * 1e-3
-        ff, fb = f / t / 1e12 / tf32, b / t / 1e9 / hbm
-        stages[st] = {"ms": med[st], "tflops": f / t / 1e12, "frac_tf32": ff, "gbs": b / t / 1e9, "frac_hbm": fb,
+        ff, fb = f / t / 1e12 / pkt, b / t / 1e9 / hbm
+        stages[st] = {"ms": med[st], "tflops": f / t / 1e12, "tensor_dtype": dt, "peak_tflops": pkt,
+                      "frac_tensor": ff, "gbs": b / t / 1e9, "frac_hbm": fb,
                       "binding": "tensor" if ff >= fb else "hbm", "frac": max(ff, fb),
                       "algorithmic_flops": f, "algorithmic_bytes": b}
-    roof_ms = max(tot_f / (tf32 * 1e12), tot_b / (hbm * 1e9)) * 1e3
+    roof_ms = max(t_tensor, tot_b / (hbm * 1e9)) * 1e3
     dom = max(stages, key=lambda k: stages[k]["ms"])
     d = stages[dom]
-    return {"kernel": dom, "bound": "tensor", "achieved": d["tflops"], "peak": tf32, "unit": "TFLOP/s",
-            "frac": d["frac_tf32"], "traffic": None,
-            "peak_source": f"tf32 = 1/2 of the {src} dense bf16 burst peak ({bf16 or 1900.0} TFLOP/s, nominal ratio)",
+    return {"kernel": dom, "bound": "tensor", "achieved": d["tflops"], "peak": d["peak_tflops"], "unit": "TFLOP/s",
+            "frac": d["frac_tensor"], "traffic": None,
+            "peak_source": (f"{d['tensor_dtype']}: {src} dense bf16 burst peak {bf16} TFLOP/s"
+                            + (" x 1/2 (nominal tf32 : bf16)" if d["tensor_dtype"] == "tf32" else "")),
             "hbm_achieved_gbs": d["gbs"], "hbm_peak_gbs": hbm, "frac_hbm": d["frac_hbm"],
             "algorithmic_flops_per_launch": d["algorithmic_flops"],
             "algorithmic_bytes_per_launch": d["algorithmic_bytes"],
@@ -187,14 +197,15 @@ def roofline_block(P, med, ms_step, pk):
 
 
 def launches_per_eval(m):
-    """Kernel launches of one vif_nll call (counted from the launch sites; 168 for
+    """Kernel launches of one vif_nll call (counted from the launch sites; 169 for
     m = 500, as in the committed launch list)."""
     ch = lambda k: (k + 15) // 16      # 16 x 16 Cholesky tiles
     tr = (m + 31) // 32                # 32 x 32 triangular-inverse tiles
     nt, nt1 = ch(m), ch(m + 1)
     chol = lambda t: t + (t - 1)       # panel launches + trailing-update launches
     trtri = lambda t: 1 + 2 * (t - 1)  # diagonal tiles, then product + finish per block diagonal
-    return (2 + 1 + chol(nt) + trtri(tr) + 1 + 1   # scaling x2, Sigma_m, Cholesky, inverse, L^-1 operand, A
+    return (2 + 1 + chol(nt) + trtri(tr) + 2 + 1   # scaling x2, Sigma_m, Cholesky, inverse, L^-1 operand (row
+                                                  # scales, tiles), A
             + 1 + 2 + 2 + chol(nt1) + 1)          # factor, Gram + reduce, logD sum, capacitance Cholesky, finish
 
 
@@ -534,7 +545,7 @@ def run_vif(args, rank, world, dist):
     if rank != 0:
         return
     med = {k: statistics.median(v) for k, v in stage_ms.items()}
-    roof = roofline_block(P, med, ms, peaks())
+    roof = roofline_block(P, med, ms, peaks(), factor_tuning.get("path", 1) if factor_tuning else 1)
     # the side blocks (Laplace rows, C1/C2, the oracle on the host cores) run at N = 1 only: at N > 1
     # the other GPUs would idle meanwhile and the CPU baseline is a single-GPU-run figure
     single = world == 1
@@ -546,17 +557,20 @@ def run_vif(args, rank, world, dist):
     cb = None
     if not args.no_cpu_baseline and single:
         cb = cpu_baseline(P, min(args.cpu_sample, P.X.shape[0]))
-    scale = max(abs(nll64), 0.5 * P.X.shape[0] * math.log(2 * math.pi))
+    have64 = nll64 is not None
+    scale = max(abs(nll64), 0.5 * P.X.shape[0] * math.log(2 * math.pi)) if have64 else None
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f32+f64", "data": "synthetic",
         "config": config_dict(P, world),
-        "fp64_path": {"value": world * 1000.0 / ms64, "unit": UNIT, "ms_per_step": ms64, "dtype": "f64"},
-        "mixed_vs_fp64": {"nll_mixed": nll_mixed, "nll_fp64": nll64,
-                          "abs_err": abs(nll_mixed - nll64), "rel_err": abs(nll_mixed - nll64) / abs(nll64),
-                          "rel_err_scale": abs(nll_mixed - nll64) / scale, "per_output": per_output},
-        "speedup_mixed_over_fp64": ms64 / ms,
+        "fp64_path": ({"value": world * 1000.0 / ms64, "unit": UNIT, "ms_per_step": ms64, "dtype": "f64"}
+                      if have64 else None),
+        "mixed_vs_fp64": ({"nll_mixed": nll_mixed, "nll_fp64": nll64,
+                           "abs_err": abs(nll_mixed - nll64), "rel_err": abs(nll_mixed - nll64) / abs(nll64),
+                           "rel_err_scale": abs(nll_mixed - nll64) / scale, "per_output": per_output}
+                          if have64 else None),
+        "speedup_mixed_over_fp64": ms64 / ms if have64 else None,
         "stage_ms": med,
         "neighbor_search": {"build_s": build_s, "queries_rescored": rescored, "queries_fallback": fallback},
         "factor_tuning": factor_tuning,

@@ -4,17 +4,22 @@
 // Row p of A is sum_k K(s_p, z_k) Linv[j][k] over k <= j, i.e. a GEMM of the kernel
 // block K_nm (M = points, K = inducing points) with L_m^{-1} read as an N x K K-major
 // operand (row j of L_m^{-1} is contiguous in k).  Float32 accuracy is kept with the
-// three-term split x = hi + lo (hi, lo tf32, round to nearest): each product is
+// three-term split x = hi + lo (hi, lo float16, round to nearest): each product is
 //   Khi Lhi + Khi Llo + Klo Lhi,
-// which leaves an error of about 2^-21 relative per product.  The tensor core's float32
-// accumulation rounds toward zero at every step (a coherent bias), so a TMEM
-// accumulator never runs longer than one chunk of 32 inducing points (12 MMAs): each
-// chunk's partial is added into float32 registers (round to nearest), and two TMEM
-// accumulators alternate so that the MMAs of chunk c run while the partial of chunk
-// c-1 is read out.
+// which leaves an error of about 2^-21 relative per product.  Float16 has 11 significant
+// bits like tf32 but a narrow exponent range, so both operands are brought to the top of
+// it by powers of two: the kernel values are evaluated with variance 2^14 (correlations
+// times 2^14), and row j of L_m^{-1} is scaled by 2^e_j so that its largest entry lies in
+// [2^13, 2^14).  The read-out multiplies column j by var 2^-14 2^-e_j.  Entries below
+// 2^-24 of their scale flush to zero, an absolute error far under float32 rounding.
+// The tensor core's float32 accumulation rounds toward zero at every step (a coherent
+// bias), so a TMEM accumulator never runs longer than one chunk of 64 inducing points
+// (four hi x hi steps, eight cross-term steps): each chunk's partial is added into float32
+// registers (round to nearest), and two TMEM accumulators alternate so that the MMAs of
+// chunk c run while the partial of chunk c-1 is read out.
 //
 // CTA: 128 points (one TMEM lane each) x 256 output columns; 16 compute warps and one MMA
-// warp.  Per chunk every compute thread evaluates 8 kernel values of one point, splits
+// warp.  Per chunk every compute thread evaluates 16 kernel values of one point, splits
 // them and writes them into the swizzled A-operand tiles of the chunk's stage, then reads
 // out the previous chunk's accumulator; thread 0 also brings the L_m^{-1} tiles (packed once
 // per call, already in the swizzled image) of the next chunk with one bulk copy per tile.
@@ -22,6 +27,8 @@
 // accumulator read out, so the kernel evaluation and read-out of neighbouring chunks run
 // while the tensor core works (hand-offs through mbarriers, no CTA-wide barrier per chunk).
 // Chunks above the tile's last column are skipped (L_m^{-1} is lower triangular).
+#include <cuda_fp16.h>
+
 #include "vif_internal.cuh"
 #include "vif_tc.cuh"
 
@@ -31,15 +38,17 @@ namespace {
 
 constexpr int AT_M = 128;                         // points per CTA
 constexpr int AT_N = 256;                         // output columns per CTA
-constexpr int AT_K = 32;                          // inducing points per chunk
+constexpr int AT_K = 64;                          // inducing points per chunk (128 bytes of f16)
 constexpr int AT_MAXD = 16;
 constexpr int AT_CT = 512;                        // compute threads
 constexpr int AT_THREADS = AT_CT + 32;            // + the MMA warp
+constexpr int AT_ZPT = AT_K * AT_MAXD / AT_CT;    // inducing-point coordinates per thread and chunk
 constexpr uint32_t AT_ATILE = AT_M * 128;         // bytes of one A-operand tile (hi or lo)
 constexpr uint32_t AT_BTILE = AT_N * 128;         // bytes of one B-operand tile (hi or lo)
 constexpr uint32_t AT_STAGE = 2 * AT_ATILE + 2 * AT_BTILE;
 constexpr uint32_t AT_SMEM = 2 * AT_STAGE + 1024; // two stages + alignment slack
 constexpr uint32_t AT_TMEM_COLS = 2 * AT_N;       // two accumulators
+constexpr float AT_KSCALE = 16384.f;              // kernel values are evaluated with this variance
 
 struct __align__(16) AtBars {
   uint64_t full[2];    // B tiles of the stage have landed
@@ -49,35 +58,88 @@ struct __align__(16) AtBars {
   uint64_t fin;        // every MMA of the CTA is done
   uint32_t tmem;
   int abort;           // the MMA warp gave up waiting
-  alignas(16) float zs[2][AT_K * AT_MAXD];   // 8-byte pairs are read from it
+  alignas(16) float zs[2][AT_K * AT_MAXD];   // 16- and 8-byte groups are read from it
 };
 
-// Packed L_m^{-1}: tile (h, c, part) holds rows j = 256 h + r (r < 256) and columns
-// k = 32 c + kk of L_m^{-1} (hi part = 0, lo part = 1) as a swizzled 256 x 32 tf32 image.
-__global__ void linv_pack_tc_kernel(const double* __restrict__ Linv, int m, int ldl, float* __restrict__ pk,
-                                    int nchunk, int64_t total) {
-  const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (e >= total) return;
-  const int kk = (int)(e % AT_K);
-  const int r = (int)((e / AT_K) % AT_N);
-  const int64_t t = e / ((int64_t)AT_K * AT_N);     // (h * nchunk + c)
-  const int c = (int)(t % nchunk), h = (int)(t / nchunk);
-  const int j = h * AT_N + r, k = c * AT_K + kk;
-  double v = 0.0;
-  if (j < m && k < m && k <= j) v = Linv[(size_t)j * ldl + k];
-  const float hi = tc::to_tf32((float)v);
-  const float lo = tc::to_tf32((float)(v - (double)hi));
-  float* tile = pk + (size_t)t * 2 * (AT_N * AT_K);
-  const uint32_t off = tc::sw128_off32(r, kk) / 4;
-  tile[off] = hi;
-  tile[AT_N * AT_K + off] = lo;
+// byte offset of element (r, k) of a K-major 128-byte-swizzled tile of 16-bit values
+__host__ __device__ constexpr uint32_t sw128_off16(uint32_t r, uint32_t k) {
+  return r * 128u + ((((k >> 3) ^ (r & 7u)) & 7u) << 4) + (k & 7u) * 2u;
 }
 
-// D > 0: compile-time input dimension; D = 0: any d <= AT_MAXD
-template <int D>
+__device__ __forceinline__ uint32_t h2_rn(float a, float b) {   // a in the low half
+  uint32_t r;
+  asm("cvt.rn.f16x2.f32 %0, %1, %2;" : "=r"(r) : "f"(b), "f"(a));
+  return r;
+}
+// float16 (hi, lo) pairs of two values: a = hi + lo + O(2^-22 a)
+__device__ __forceinline__ void split_h2(float a, float b, uint32_t& hi, uint32_t& lo) {
+  hi = h2_rn(a, b);
+  const float2 hf = __half22float2(*reinterpret_cast<const __half2*>(&hi));
+  lo = h2_rn(a - hf.x, b - hf.y);
+}
+
+// Scales of the rows of L_m^{-1} (one warp per row j < 256 nh): s_j = 2^e_j with the
+// row's largest |entry| s_j in [2^13, 2^14) (s_j = 1 for padding rows), and the read-out
+// factor colf[j] = var 2^-14 / s_j of column j of A.
+__global__ void linv_rowscale_kernel(const double* __restrict__ Linv, int m, int ldl, int rows, double var,
+                                     float* __restrict__ rs, float* __restrict__ colf) {
+  const int j = (int)(((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5), lane = threadIdx.x & 31;
+  if (j >= rows) return;
+  double mx = 0.0;
+  if (j < m)
+    for (int k = lane; k <= j; k += 32) mx = fmax(mx, fabs(Linv[(size_t)j * ldl + k]));
+#pragma unroll
+  for (int o = 16; o; o >>= 1) mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+  if (lane == 0) {
+    int e = 0;
+    if (mx > 0.0 && mx <= 1e300) {
+      int ex;
+      frexp(mx, &ex);                       // mx in [2^(ex-1), 2^ex)
+      e = min(100, max(-100, 14 - ex));
+    }
+    rs[j] = ldexpf(1.f, e);
+    colf[j] = (float)(var * ldexp(1.0, -14 - e));
+  }
+}
+
+// Packed L_m^{-1}: tile (h, c, part) holds rows j = 256 h + r (r < 256) and columns
+// k = 64 c + kk of diag(s) L_m^{-1} (hi part = 0, lo part = 1) as a swizzled 256 x 64
+// float16 image; one thread per 8 consecutive columns (16 bytes of each part).
+__global__ void linv_pack_tc_kernel(const double* __restrict__ Linv, int m, int ldl, const float* __restrict__ rs,
+                                    unsigned char* __restrict__ pk, int nchunk, int64_t total) {
+  const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= total) return;
+  const int g = (int)(e % (AT_K / 8));
+  const int r = (int)((e / (AT_K / 8)) % AT_N);
+  const int64_t t = e / ((int64_t)(AT_K / 8) * AT_N);     // (h * nchunk + c)
+  const int c = (int)(t % nchunk), h = (int)(t / nchunk);
+  const int j = h * AT_N + r, k0 = c * AT_K + 8 * g;
+  const double sj = j < m ? (double)rs[j] : 0.0;
+  uint32_t hi[4], lo[4];
+#pragma unroll
+  for (int u = 0; u < 4; ++u) {
+    float v[2];
+#pragma unroll
+    for (int w = 0; w < 2; ++w) {
+      const int k = k0 + 2 * u + w;
+      v[w] = (j < m && k < m && k <= j) ? (float)(sj * Linv[(size_t)j * ldl + k]) : 0.f;
+    }
+    // the float32 value of s_j Linv carries 24 bits; hi + lo keeps 22 of them
+    split_h2(v[0], v[1], hi[u], lo[u]);
+  }
+  unsigned char* tile = pk + (size_t)t * 2 * AT_BTILE;
+  const uint32_t off = sw128_off16(r, 8 * g);
+  *reinterpret_cast<uint4*>(tile + off) = make_uint4(hi[0], hi[1], hi[2], hi[3]);
+  *reinterpret_cast<uint4*>(tile + AT_BTILE + off) = make_uint4(lo[0], lo[1], lo[2], lo[3]);
+}
+
+// D > 0: compile-time input dimension; D = 0: any d <= AT_MAXD.  KIND: the covariance
+// function (a compile-time constant, so that the evaluation loop holds one branch-free form)
+template <int D, int KIND>
 __global__ __launch_bounds__(AT_THREADS, 1) void lowrank_A_tc_kernel(
-    const float* __restrict__ Xs, const float* __restrict__ Zs, const float* __restrict__ pk, float* __restrict__ A,
-    int64_t n, int d, int m, int mpad, int nchunk_all, int kind, float var, int* status) {
+    const float* __restrict__ Xs, const float* __restrict__ Zs, const unsigned char* __restrict__ pk,
+    const float* __restrict__ colf, float* __restrict__ A, int64_t n, int d, int m, int mpad, int nchunk_all,
+    int* status) {
   extern __shared__ unsigned char smem_raw[];
   __shared__ AtBars sb;
   unsigned char* smem = (unsigned char*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
@@ -86,9 +148,9 @@ __global__ __launch_bounds__(AT_THREADS, 1) void lowrank_A_tc_kernel(
   const int64_t row0 = (int64_t)blockIdx.x * AT_M;
   const int ncols = min(AT_N, mpad - h * AT_N);                 // multiple of 32
   const int nchunk = min(nchunk_all, (h * AT_N + ncols - 1) / AT_K + 1);
-  const uint32_t idesc = tc::idesc_tf32(AT_M, ncols);
-  const float* pk_h = pk + (size_t)h * nchunk_all * 2 * (AT_N * AT_K);
-  // kernel evaluation: point krow, values 8 kq .. 8 kq + 7 of each chunk (compute threads)
+  const uint32_t idesc = tc::idesc_f16(AT_M, ncols);
+  const unsigned char* pk_h = pk + (size_t)h * nchunk_all * 2 * AT_BTILE;
+  // kernel evaluation: point krow, values 16 kq .. 16 kq + 15 of each chunk (compute threads)
   const int krow = tid & (AT_M - 1), kq = (tid >> 7) & 3;
   const int64_t p = row0 + krow;
   // read-out: TMEM lanes dl .. dl + 31, columns dc .. dc + 63 of the accumulator
@@ -115,16 +177,17 @@ __global__ __launch_bounds__(AT_THREADS, 1) void lowrank_A_tc_kernel(
   unsigned long long xp[DP];
 #pragma unroll
   for (int j = 0; j < DP; ++j) xp[j] = pack_f2(x[(2 * j) % DX], x[(2 * j + 1) % DX]);
-  // inducing points of chunk c, element e = tid + 512 j of the chunk's 32 x d block
-  auto zload = [&](int c, float (&zr)[1]) {
+  // inducing points of chunk c, element e = tid + 512 j of the chunk's 64 x d block
+  constexpr int ZPT = D > 0 ? (AT_K * D + AT_CT - 1) / AT_CT : AT_ZPT;
+  auto zload = [&](int c, float (&zr)[ZPT]) {
 #pragma unroll
-    for (int j = 0; j < 1; ++j) {
+    for (int j = 0; j < ZPT; ++j) {
       const int e = tid + AT_CT * j;
       const int k = c * AT_K + e / max(d, 1);
       zr[j] = (c < nchunk && e < AT_K * d && k < m) ? Zs[(size_t)c * AT_K * d + e] : 0.f;
     }
   };
-  float zpre[1];
+  float zpre[ZPT];
   zload(0, zpre);
   unsigned long long acc2[32];   // column pairs (2j, 2j+1) of this thread's read-out range
 #pragma unroll
@@ -162,16 +225,16 @@ __global__ __launch_bounds__(AT_THREADS, 1) void lowrank_A_tc_kernel(
   auto fetch_b = [&](int c) {
     const int s = c & 1;
     unsigned char* st = smem + s * AT_STAGE;
-    const float* src = pk_h + (size_t)c * 2 * (AT_N * AT_K);
+    const unsigned char* src = pk_h + (size_t)c * 2 * AT_BTILE;
     tc::mbar_arrive_expect_tx(&sb.full[s], 2u * ncols * 128u);
     tc::bulk_g2s(st + 2 * AT_ATILE, src, ncols * 128u, &sb.full[s]);
-    tc::bulk_g2s(st + 2 * AT_ATILE + AT_BTILE, src + AT_N * AT_K, ncols * 128u, &sb.full[s]);
+    tc::bulk_g2s(st + 2 * AT_ATILE + AT_BTILE, src + AT_BTILE, ncols * 128u, &sb.full[s]);
     ++copies_issued[s];
   };
   if (tid == 0 && nchunk > 0) fetch_b(0);
 
   if (warp == AT_CT / 32) {
-    // ------------------------------------------------------------ MMA warp (one lane)
+    // ------------------------------------------------------------ MMA warp
     if (lane == 0) {
       for (int c = 0; c < nchunk; ++c) {
         const int s = c & 1;
@@ -191,15 +254,15 @@ __global__ __launch_bounds__(AT_THREADS, 1) void lowrank_A_tc_kernel(
         // step truncates relative to the running sum, so the steps taken once the sum
         // is large are kept to the four hi x hi ones
 #pragma unroll
-        for (int ks = 0; ks < AT_K / 8; ++ks) {
+        for (int ks = 0; ks < AT_K / 16; ++ks) {
           const uint32_t o = ks * 32;
-          tc::mma_tf32(dt, tc::desc_k_sw128(al + o), tc::desc_k_sw128(bh + o), idesc, ks > 0);
-          tc::mma_tf32(dt, tc::desc_k_sw128(ah + o), tc::desc_k_sw128(bl + o), idesc, 1u);
+          tc::mma_f16(dt, tc::desc_k_sw128(al + o), tc::desc_k_sw128(bh + o), idesc, ks > 0);
+          tc::mma_f16(dt, tc::desc_k_sw128(ah + o), tc::desc_k_sw128(bl + o), idesc, 1u);
         }
 #pragma unroll
-        for (int ks = 0; ks < AT_K / 8; ++ks) {
+        for (int ks = 0; ks < AT_K / 16; ++ks) {
           const uint32_t o = ks * 32;
-          tc::mma_tf32(dt, tc::desc_k_sw128(ah + o), tc::desc_k_sw128(bh + o), idesc, 1u);
+          tc::mma_f16(dt, tc::desc_k_sw128(ah + o), tc::desc_k_sw128(bh + o), idesc, 1u);
         }
         tc::mma_commit(&sb.done[s]);
       }
@@ -207,8 +270,19 @@ __global__ __launch_bounds__(AT_THREADS, 1) void lowrank_A_tc_kernel(
       tc::mma_commit(&sb.fin);
     }
     __syncwarp();
-  } else {
-    // ------------------------------------------------------------ compute warps
+    // the closing barriers of the compute warps (ids 2 and 3 span the whole CTA)
+    bool fin_ok = tc::mbar_wait(&sb.fin, 0);
+    if (!fin_ok) {
+      failed = true;
+      fin_ok = tc::mbar_wait(&sb.fin, 0);
+    }
+    tc::bar_sync_or(2, AT_THREADS, failed);
+    tc::fence_before_sync();
+    tc::bar_sync_or(3, AT_THREADS, !fin_ok);
+    return;
+  }
+  // ------------------------------------------------------------ compute warps
+  {
     for (int c = 0; c < nchunk; ++c) {
       const int s = c & 1;
       unsigned char* st = smem + s * AT_STAGE;
@@ -216,7 +290,7 @@ __global__ __launch_bounds__(AT_THREADS, 1) void lowrank_A_tc_kernel(
       unsigned char* a_lo = st + AT_ATILE;
       // zs[s] was last read at iteration c-2; everyone passed the barrier of iteration c-1
 #pragma unroll
-      for (int j = 0; j < 1; ++j) {
+      for (int j = 0; j < ZPT; ++j) {
         const int e = tid + AT_CT * j;
         if (e < AT_K * AT_MAXD) sb.zs[s][e] = zpre[j];
       }
@@ -228,16 +302,31 @@ __global__ __launch_bounds__(AT_THREADS, 1) void lowrank_A_tc_kernel(
       // stage s was last read by the MMAs of chunk c-2, which this thread saw finish when it
       // read out chunk c-2 at iteration c-1
       const int kmax = min(AT_K, m - c * AT_K);
-#pragma unroll
-      for (int q = 0; q < 2; ++q) {
-        float hv[4], lv[4];
+      const bool pvalid = p < n;
+#pragma unroll 1
+      for (int q = 0; q < 4; ++q) {
+        float kv[4];
 #pragma unroll
         for (int u = 0; u < 4; ++u) {
-          const int kk = kq * 8 + q * 4 + u;
-          float kv = 0.f;
-          if (kk < kmax && p < n) {
+          const int kk = kq * 16 + q * 4 + u;
+          // evaluated for every slot (inducing points past m read zeros, points past n have
+          // x = 0) and masked afterwards: no branch in the loop
+          {
             float r2 = 0.f;
-            if constexpr (D > 0 && D % 2 == 0) {
+            if constexpr (D > 0 && D % 4 == 0) {
+              const float4* z4 = reinterpret_cast<const float4*>(&sb.zs[s][kk * D]);
+              unsigned long long a2 = 0ull;
+#pragma unroll
+              for (int j = 0; j < D / 4; ++j) {
+                const float4 zz = z4[j];
+                const unsigned long long d0 = fsub2(xp[2 * j], pack_f2(zz.x, zz.y));
+                const unsigned long long d1 = fsub2(xp[2 * j + 1], pack_f2(zz.z, zz.w));
+                a2 = ffma2(d0, d0, a2);
+                a2 = ffma2(d1, d1, a2);
+              }
+              const float2 h2 = unpack_f2(a2);
+              r2 = h2.x + h2.y;
+            } else if constexpr (D > 0 && D % 2 == 0) {
               const float2* z2 = reinterpret_cast<const float2*>(&sb.zs[s][kk * D]);
               unsigned long long a2 = 0ull;
 #pragma unroll
@@ -258,20 +347,20 @@ __global__ __launch_bounds__(AT_THREADS, 1) void lowrank_A_tc_kernel(
             } else {
               const float* z = &sb.zs[s][kk * d];
 #pragma unroll
-              for (int t = 0; t < AT_MAXD; ++t)
-                if (t < d) {
-                  const float df = x[t] - z[t];
-                  r2 = fmaf(df, df, r2);
-                }
+              for (int t = 0; t < AT_MAXD; ++t) {
+                const float df = t < d ? x[t] - z[t] : 0.f;
+                r2 = fmaf(df, df, r2);
+              }
             }
-            kv = cov_r2_fast(r2, kind, var);
+            kv[u] = (kk < kmax && pvalid) ? cov_r2_fast(r2, KIND, AT_KSCALE) : 0.f;
           }
-          hv[u] = tc::to_tf32(kv);
-          lv[u] = tc::to_tf32(kv - hv[u]);
         }
-        const uint32_t off = tc::sw128_off32(krow, kq * 8 + q * 4);
-        *reinterpret_cast<float4*>(a_hi + off) = make_float4(hv[0], hv[1], hv[2], hv[3]);
-        *reinterpret_cast<float4*>(a_lo + off) = make_float4(lv[0], lv[1], lv[2], lv[3]);
+        uint32_t hv[2], lv[2];
+#pragma unroll
+        for (int u = 0; u < 2; ++u) split_h2(kv[2 * u], kv[2 * u + 1], hv[u], lv[u]);
+        const uint32_t off = sw128_off16(krow, kq * 16 + q * 4);
+        *reinterpret_cast<uint2*>(a_hi + off) = make_uint2(hv[0], hv[1]);
+        *reinterpret_cast<uint2*>(a_lo + off) = make_uint2(lv[0], lv[1]);
       }
       tc::fence_proxy_async();
       tc::fence_before_sync();
@@ -298,66 +387,83 @@ __global__ __launch_bounds__(AT_THREADS, 1) void lowrank_A_tc_kernel(
     failed = true;
     fin_ok = tc::mbar_wait(&sb.fin, 0);
   }
-  if (__syncthreads_or(failed)) {
+  if (tc::bar_sync_or(2, AT_THREADS, failed)) {
     if (tid == 0 && status) flag_status(status, ST_TIMEOUT, blockIdx.x);
-  } else if (warp < AT_CT / 32) {
+  } else {
     const int64_t row = row0 + dl + lane;
+    const int c0 = h * AT_N + dc;
     if (row < n) {
-      float* dst = A + (size_t)row * mpad + h * AT_N + dc;
+      float* dst = A + (size_t)row * mpad + c0;
 #pragma unroll
       for (int g = 0; g < 2; ++g)
         if (g < ngrp) {
 #pragma unroll
           for (int j = 0; j < 16; j += 2) {
+            const float4 f = __ldg(reinterpret_cast<const float4*>(colf + c0 + g * 32 + 2 * j));
             const float2 a = unpack_f2(acc2[g * 16 + j]), b = unpack_f2(acc2[g * 16 + j + 1]);
-            *reinterpret_cast<float4*>(dst + g * 32 + 2 * j) = make_float4(a.x, a.y, b.x, b.y);
+            *reinterpret_cast<float4*>(dst + g * 32 + 2 * j) = make_float4(a.x * f.x, a.y * f.y, b.x * f.z, b.y * f.w);
           }
         }
     }
   }
   tc::fence_before_sync();
-  const bool drained = __syncthreads_and(fin_ok);
+  const bool drained = !tc::bar_sync_or(3, AT_THREADS, !fin_ok);
   if (warp == 0 && drained) {
     tc::fence_after_sync();
     tc::tmem_dealloc(tmem, AT_TMEM_COLS);
   }
 }
 
+using AKernel = void (*)(const float*, const float*, const unsigned char*, const float*, float*, int64_t, int, int,
+                        int, int, int*);
+
+template <int D>
+AKernel a_kernel_for_kind(int kind) {
+  switch (kind) {
+    case VIF_MATERN12: return lowrank_A_tc_kernel<D, VIF_MATERN12>;
+    case VIF_MATERN32: return lowrank_A_tc_kernel<D, VIF_MATERN32>;
+    case VIF_MATERN52: return lowrank_A_tc_kernel<D, VIF_MATERN52>;
+    default: return lowrank_A_tc_kernel<D, VIF_SE>;
+  }
+}
+AKernel a_kernel(int d, int kind) {
+  return d == 8 ? a_kernel_for_kind<8>(kind) : d == 5 ? a_kernel_for_kind<5>(kind)
+         : d == 2 ? a_kernel_for_kind<2>(kind) : a_kernel_for_kind<0>(kind);
+}
+
 }  // namespace
 
 cudaError_t lowrank_A_tc_init() {
-  cudaError_t e = cudaFuncSetAttribute(lowrank_A_tc_kernel<0>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                       (int)AT_SMEM);
-  if (e == cudaSuccess)
-    e = cudaFuncSetAttribute(lowrank_A_tc_kernel<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)AT_SMEM);
-  if (e == cudaSuccess)
-    e = cudaFuncSetAttribute(lowrank_A_tc_kernel<8>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)AT_SMEM);
+  cudaError_t e = cudaSuccess;
+  for (int d : {0, 2, 5, 8})
+    for (int kind : {VIF_MATERN12, VIF_MATERN32, VIF_MATERN52, VIF_SE})
+      if (e == cudaSuccess)
+        e = cudaFuncSetAttribute((const void*)a_kernel(d, kind), cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)AT_SMEM);
   return e;
 }
 
+// packed L_m^{-1} tiles, then the row scales (256 nh floats) and the read-out factors
 size_t lowrank_A_tc_pack_floats(int mpad) {
-  const int nh = (mpad + AT_N - 1) / AT_N, nchunk = mpad / AT_K;
-  return (size_t)nh * nchunk * 2 * AT_N * AT_K;
+  const int nh = (mpad + AT_N - 1) / AT_N, nchunk = (mpad + AT_K - 1) / AT_K;
+  return (size_t)nh * nchunk * 2 * AT_BTILE / sizeof(float) + 2 * (size_t)nh * AT_N;
 }
 
 cudaError_t lowrank_A_tc(const float* Xs, const float* Zs, const double* Linv, int ldl, float* pack, float* A,
                          int64_t n, int d, int m, int mpad, int kind, double var, int* status, cudaStream_t s) {
   if (m <= 0) return cudaMemsetAsync(A, 0, sizeof(float) * (size_t)n * mpad, s);
-  if (d > AT_MAXD || mpad % AT_K != 0 || mpad < m || mpad - m >= AT_K || n <= 0) return cudaErrorInvalidValue;
-  // mpad = 32 ceil(m / 32), so the packed chunks and the chunks of m coincide
-  const int nh = (mpad + AT_N - 1) / AT_N, nchunk = mpad / AT_K;
-  const int64_t total = (int64_t)nh * nchunk * AT_N * AT_K;
-  linv_pack_tc_kernel<<<(unsigned)((total + 255) / 256), 256, 0, s>>>(Linv, m, ldl, pack, nchunk, total);
+  if (d > AT_MAXD || mpad % 32 != 0 || mpad < m || mpad - m >= 32 || n <= 0) return cudaErrorInvalidValue;
+  // mpad = 32 ceil(m / 32): the last chunk of 64 may hold 32 padding columns, packed as zeros
+  const int nh = (mpad + AT_N - 1) / AT_N, nchunk = (mpad + AT_K - 1) / AT_K;
+  unsigned char* tiles = reinterpret_cast<unsigned char*>(pack);
+  float* rs = pack + (size_t)nh * nchunk * 2 * AT_BTILE / sizeof(float);
+  float* colf = rs + (size_t)nh * AT_N;
+  const int rows = nh * AT_N;
+  linv_rowscale_kernel<<<(unsigned)((rows * 32 + 255) / 256), 256, 0, s>>>(Linv, m, ldl, rows, var, rs, colf);
+  const int64_t total = (int64_t)nh * nchunk * AT_N * (AT_K / 8);
+  linv_pack_tc_kernel<<<(unsigned)((total + 255) / 256), 256, 0, s>>>(Linv, m, ldl, rs, tiles, nchunk, total);
   dim3 grid((unsigned)((n + AT_M - 1) / AT_M), (unsigned)nh);
-  if (d == 8)
-    lowrank_A_tc_kernel<8><<<grid, AT_THREADS, AT_SMEM, s>>>(Xs, Zs, pack, A, n, d, m, mpad, nchunk, kind,
-                                                             (float)var, status);
-  else if (d == 2)
-    lowrank_A_tc_kernel<2><<<grid, AT_THREADS, AT_SMEM, s>>>(Xs, Zs, pack, A, n, d, m, mpad, nchunk, kind,
-                                                             (float)var, status);
-  else
-    lowrank_A_tc_kernel<0><<<grid, AT_THREADS, AT_SMEM, s>>>(Xs, Zs, pack, A, n, d, m, mpad, nchunk, kind,
-                                                             (float)var, status);
+  a_kernel(d, kind)<<<grid, AT_THREADS, AT_SMEM, s>>>(Xs, Zs, tiles, colf, A, n, d, m, mpad, nchunk, status);
   return cudaGetLastError();
 }
 
