@@ -49,7 +49,7 @@ def parse():
     ap.add_argument("--no-small", action="store_true", help="skip the C1/C2 block")
     ap.add_argument("--laplace-only", action="store_true",
                     help="run only the C4 Laplace block and print its JSON (for profiling the PCG kernels)")
-    ap.add_argument("--batch", type=int, default=0,
+    ap.add_argument("--batch", type=int, default=256,
                     help="also time N independent C5-style problems per CUDA graph replay (0: skip)")
     return ap.parse_args()
 
@@ -552,7 +552,7 @@ def run_vif(args, rank, world, dist):
     lap = None
     if not args.no_laplace and single:
         lap = laplace_block(args, stream)
-    bat = batch_block(args, stream) if args.batch > 0 else None
+    bat = batch_block(args, stream) if (args.batch > 0 and single) else None
     small = None if (args.no_small or not single) else small_configs_block(stream)
     cb = None
     if not args.no_cpu_baseline and single:

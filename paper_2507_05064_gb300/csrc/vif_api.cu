@@ -2282,51 +2282,100 @@ struct vif_batch {
   double* hout = nullptr;      // pinned: NLL + status copy-back
   int branches = 8, split_div = 1;
   double best_ms = 0.0;
+  // the dense float64 stages of every problem, one launch per step for all problems
+  DenseBatch chol_sm, trtri_sm, chol_cap;
   char err[512] = {0};
 };
 
 namespace {
 
-// Capture-safe likelihood enqueue for one context on stream s (no host syncs): the
-// hyperparameters come from pinned staging, the result and status go to device slots.
+// Capture-safe likelihood enqueue for one context on stream s (no host syncs), in phases
+// around the batched dense stages: (pre) hyperparameters from pinned staging, scaled
+// coordinates, Sigma_m; [Cholesky and inverse of every Sigma_m]; (mid) A, the residual
+// Vecchia factors, the Gram and sum log D_i; [Cholesky of every augmented capacitance
+// matrix]; (post) the scalar and the status words into the batch's slots.
+struct CtxSwap {   // the context's stream, timing and Gram split for the duration of a phase
+  vif_ctx* c;
+  cudaStream_t keep;
+  bool keep_t;
+  int keep_split;
+  CtxSwap(vif_ctx* ctx, cudaStream_t s, int split_div, bool fp64) : c(ctx) {
+    keep = c->stream;
+    keep_t = c->timing;
+    keep_split = c->nsplit;
+    c->stream = s;
+    c->timing = false;
+    // the float64 Gram's row slices follow the tuned split; the float32 (tensor-core) Gram
+    // picks its own one-wave split, so a batched call sums its rows exactly as a single call
+    if (fp64) c->nsplit = std::max(1, keep_split / split_div);
+  }
+  ~CtxSwap() {
+    c->stream = keep;
+    c->timing = keep_t;
+    c->nsplit = keep_split;
+  }
+};
+
 template <typename T>
-vif_status enqueue_nll(vif_ctx* ctx, const vif_cov* th, const double* hyp_src, const double* ydev, double* nll_dst,
-                       int* st_dst, cudaStream_t s, int split_div) {
-  cudaStream_t keep = ctx->stream;
-  bool keep_t = ctx->timing;
-  int keep_split = ctx->nsplit;
-  ctx->stream = s;
-  ctx->timing = false;
-  // the float64 Gram's row slices follow the tuned split; the float32 (tensor-core) Gram
-  // picks its own one-wave split, so a batched call sums its rows exactly as a single call
-  if constexpr (sizeof(T) == 8) ctx->nsplit = std::max(1, keep_split / split_div);
-  vif_status st = VIF_OK;
-  do {
-    CovParams cp = cov_params(th);
-    const bool mixed = sizeof(T) == 4;
-    if (cudaMemsetAsync(ctx->status, 0, 4 * sizeof(int), s) != cudaSuccess ||
-        cudaMemcpyAsync(ctx->y, ydev, ctx->n * sizeof(double), cudaMemcpyDeviceToDevice, s) != cudaSuccess ||
-        cudaMemcpyAsync(ctx->hyp, hyp_src, 32 * sizeof(double), cudaMemcpyHostToDevice, s) != cudaSuccess ||
-        scale_coords(ctx->X, ctx->n, ctx->d, ctx->hyp, ctx->hyp + 16, ctx->Xs, mixed ? ctx->Xs32 : nullptr, s) !=
-            cudaSuccess ||
-        (ctx->m > 0 && scale_coords(ctx->Z, ctx->m, ctx->d, ctx->hyp, ctx->hyp + 16, ctx->Zs,
-                                    mixed ? ctx->Zs32 : nullptr, s) != cudaSuccess)) {
-      st = set_err(ctx, VIF_ERR_CUDA, "batch enqueue failed");
-      break;
-    }
-    if (mixed)
-      st = run_pipeline<float>(ctx, cp, (float*)ctx->A, (float*)ctx->LinvT, (float*)ctx->F, ctx->Xs32, ctx->Zs32);
-    else
-      st = run_pipeline<double>(ctx, cp, (double*)ctx->A, (double*)ctx->LinvT, (double*)ctx->F, ctx->Xs, ctx->Zs);
-    if (st != VIF_OK) break;
-    if (cudaMemcpyAsync(nll_dst, ctx->dscal + 1, sizeof(double), cudaMemcpyDeviceToDevice, s) != cudaSuccess ||
-        cudaMemcpyAsync(st_dst, ctx->status, 4 * sizeof(int), cudaMemcpyDeviceToDevice, s) != cudaSuccess)
-      st = set_err(ctx, VIF_ERR_CUDA, "batch enqueue failed");
-  } while (0);
-  ctx->stream = keep;
-  ctx->timing = keep_t;
-  ctx->nsplit = keep_split;
-  return st;
+vif_status enqueue_pre(vif_ctx* ctx, const vif_cov* th, const double* hyp_src, const double* ydev, cudaStream_t s,
+                       int split_div) {
+  CtxSwap sw(ctx, s, split_div, sizeof(T) == 8);
+  const bool mixed = sizeof(T) == 4;
+  if (cudaMemsetAsync(ctx->status, 0, 4 * sizeof(int), s) != cudaSuccess ||
+      cudaMemcpyAsync(ctx->y, ydev, ctx->n * sizeof(double), cudaMemcpyDeviceToDevice, s) != cudaSuccess ||
+      cudaMemcpyAsync(ctx->hyp, hyp_src, 32 * sizeof(double), cudaMemcpyHostToDevice, s) != cudaSuccess ||
+      scale_coords(ctx->X, ctx->n, ctx->d, ctx->hyp, ctx->hyp + 16, ctx->Xs, mixed ? ctx->Xs32 : nullptr, s) !=
+          cudaSuccess ||
+      (ctx->m > 0 && scale_coords(ctx->Z, ctx->m, ctx->d, ctx->hyp, ctx->hyp + 16, ctx->Zs,
+                                  mixed ? ctx->Zs32 : nullptr, s) != cudaSuccess))
+    return set_err(ctx, VIF_ERR_CUDA, "batch enqueue failed");
+  if (ctx->m <= 0) return VIF_OK;
+  const CovParams cp = cov_params(th);
+  CK(build_sigma_m(ctx->Zs, ctx->m, ctx->d, cp, ctx->Sm, ctx->ldm, s));
+  // the inverse's zeroed upper part and k-slice scratch (as dense_trtri_lower does)
+  CK(cudaMemset2DAsync(ctx->Linv, ctx->ldm * sizeof(double), 0, ctx->m * sizeof(double), ctx->m, s));
+  CK(cudaMemsetAsync(ctx->trw, 0, trtri_work_doubles(ctx->m) * sizeof(double), s));
+  return VIF_OK;
+}
+
+template <typename T>
+vif_status enqueue_mid(vif_ctx* ctx, const vif_cov* th, cudaStream_t s, int split_div) {
+  CtxSwap sw(ctx, s, split_div, sizeof(T) == 8);
+  const CovParams cp = cov_params(th);
+  const bool mixed = sizeof(T) == 4;
+  T* A = (T*)ctx->A;
+  T* LinvT = (T*)ctx->LinvT;
+  T* F = (T*)ctx->F;
+  const T* Xs = mixed ? (const T*)ctx->Xs32 : (const T*)ctx->Xs;
+  const T* Zs = mixed ? (const T*)ctx->Zs32 : (const T*)ctx->Zs;
+  if constexpr (sizeof(T) == 8)
+    if (ctx->m > 0) CK(linv_transpose<T>(ctx->Linv, ctx->m, ctx->ldm, LinvT, ctx->mpad, s));
+  CK(lowrank_A_any<T>(ctx, cp, A, LinvT, Xs, Zs));
+  CKS(run_factor<T>(ctx, cp, A, Xs, F, factor_on_tc(ctx)));
+  CK(gram_FtF<T>(F, ctx->n, ctx->fpad, ctx->m, ctx->part, ctx->nsplit, ctx->G, ctx->fpad, s, nullptr, ctx->status));
+  CK(reduce_sum(ctx->logD, ctx->n, ctx->red, ctx->dscal, s));
+  return VIF_OK;
+}
+
+vif_status enqueue_post(vif_ctx* ctx, double* nll_dst, int* st_dst, cudaStream_t s) {
+  CK(nll_finish(ctx->G, ctx->fpad, ctx->m, ctx->dscal, ctx->n, ctx->dscal + 1, s));
+  if (cudaMemcpyAsync(nll_dst, ctx->dscal + 1, sizeof(double), cudaMemcpyDeviceToDevice, s) != cudaSuccess ||
+      cudaMemcpyAsync(st_dst, ctx->status, 4 * sizeof(int), cudaMemcpyDeviceToDevice, s) != cudaSuccess)
+    return set_err(ctx, VIF_ERR_CUDA, "batch enqueue failed");
+  return VIF_OK;
+}
+
+// the dense stages of every problem as batched launches (jobs fixed for the batch's life)
+cudaError_t batch_dense_init(vif_batch* b) {
+  std::vector<DenseJob> sm, cap;
+  for (vif_ctx* c : b->ctx) {
+    if (c->m > 0) sm.push_back({c->Sm, c->Linv, c->trw, c->status, c->m, c->ldm, ST_NOTPD_SIGMAM});
+    cap.push_back({c->G, nullptr, nullptr, c->status, c->m + 1, c->fpad, ST_NOTPD_CAP});
+  }
+  cudaError_t e = dense_batch_init(sm, false, &b->chol_sm);
+  if (e == cudaSuccess) e = dense_batch_init(sm, true, &b->trtri_sm);
+  if (e == cudaSuccess) e = dense_batch_init(cap, false, &b->chol_cap);
+  return e;
 }
 
 vif_status batch_capture(vif_batch* b, int branches, int split_div, cudaGraphExec_t* exec) {
@@ -2334,21 +2383,44 @@ vif_status batch_capture(vif_batch* b, int branches, int split_div, cudaGraphExe
   cudaGraph_t g = nullptr;
   if (cudaStreamBeginCapture(b->origin, cudaStreamCaptureModeThreadLocal) != cudaSuccess) return VIF_ERR_CUDA;
   vif_status st = VIF_OK;
-  cudaEventRecord(b->ev[0], b->origin);
-  for (int k = 0; k < branches; ++k) cudaStreamWaitEvent(b->br[k], b->ev[0], 0);
-  for (int p = 0; p < np && st == VIF_OK; ++p) {
-    vif_ctx* c = b->ctx[p];
-    cudaStream_t s = b->br[p % branches];
-    if (c->precision == VIF_MIXED)
-      st = enqueue_nll<float>(c, &b->th[p], b->hpin + 32 * p, b->ys[p], b->dout + p, b->dst + 4 * p, s, split_div);
-    else
-      st = enqueue_nll<double>(c, &b->th[p], b->hpin + 32 * p, b->ys[p], b->dout + p, b->dst + 4 * p, s,
-                               split_div);
-  }
-  for (int k = 0; k < branches; ++k) {
-    cudaEventRecord(b->ev[1 + k], b->br[k]);
-    cudaStreamWaitEvent(b->origin, b->ev[1 + k], 0);
-  }
+  int nev = 0;
+  // origin -> every branch
+  auto fork = [&]() {
+    cudaEvent_t e = b->ev[nev++];
+    cudaEventRecord(e, b->origin);
+    for (int k = 0; k < branches; ++k) cudaStreamWaitEvent(b->br[k], e, 0);
+  };
+  // every branch -> origin
+  auto join = [&]() {
+    for (int k = 0; k < branches; ++k) {
+      cudaEvent_t e = b->ev[nev++];
+      cudaEventRecord(e, b->br[k]);
+      cudaStreamWaitEvent(b->origin, e, 0);
+    }
+  };
+  auto each = [&](auto&& fn) {
+    for (int p = 0; p < np && st == VIF_OK; ++p) st = fn(p, b->ctx[p], b->br[p % branches]);
+  };
+  fork();
+  each([&](int p, vif_ctx* c, cudaStream_t s) {
+    const double* h = b->hpin + 32 * p;
+    return c->precision == VIF_MIXED ? enqueue_pre<float>(c, &b->th[p], h, b->ys[p], s, split_div)
+                                     : enqueue_pre<double>(c, &b->th[p], h, b->ys[p], s, split_div);
+  });
+  join();
+  if (st == VIF_OK && (dense_batch_run(b->chol_sm, b->origin) != cudaSuccess ||
+                       dense_batch_run(b->trtri_sm, b->origin) != cudaSuccess))
+    st = VIF_ERR_CUDA;
+  fork();
+  each([&](int p, vif_ctx* c, cudaStream_t s) {
+    return c->precision == VIF_MIXED ? enqueue_mid<float>(c, &b->th[p], s, split_div)
+                                     : enqueue_mid<double>(c, &b->th[p], s, split_div);
+  });
+  join();
+  if (st == VIF_OK && dense_batch_run(b->chol_cap, b->origin) != cudaSuccess) st = VIF_ERR_CUDA;
+  fork();
+  each([&](int p, vif_ctx* c, cudaStream_t s) { return enqueue_post(c, b->dout + p, b->dst + 4 * p, s); });
+  join();
   cudaError_t e = cudaStreamEndCapture(b->origin, &g);
   if (st != VIF_OK || e != cudaSuccess) {
     if (g) cudaGraphDestroy(g);
@@ -2403,9 +2475,10 @@ vif_status vif_batch_create(vif_ctx* const* ctxs, int32_t nprob, const vif_cov* 
       h[16 + t] = c->center[t];
     }
   }
+  if (batch_dense_init(b) != cudaSuccess) return fail(VIF_ERR_NOMEM, "vif_batch_create: dense plan failed");
   const int maxbr = 32;
   b->br.resize(maxbr);
-  b->ev.resize(maxbr + 1);
+  b->ev.resize(3 * (maxbr + 1));   // three fork / join pairs per capture
   for (auto& s : b->br)
     if (cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking) != cudaSuccess)
       return fail(VIF_ERR_CUDA, "vif_batch_create: stream creation failed");
@@ -2491,6 +2564,9 @@ void vif_batch_destroy(vif_batch* b) {
     if (s) cudaStreamDestroy(s);
   for (auto e : b->ev)
     if (e) cudaEventDestroy(e);
+  dense_batch_free(&b->chol_sm);
+  dense_batch_free(&b->trtri_sm);
+  dense_batch_free(&b->chol_cap);
   if (b->hpin) cudaFreeHost(b->hpin);
   if (b->hout) cudaFreeHost(b->hout);
   if (b->dout) cudaFree(b->dout);

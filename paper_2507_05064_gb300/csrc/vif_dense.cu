@@ -10,6 +10,8 @@
 // with the tile below it in one column sweep held in registers (pivots by a Newton-
 // refined reciprocal square root, formed one column ahead), the next updates the
 // trailing tiles, one CTA per tile.
+#include <algorithm>
+
 #include "vif_internal.cuh"
 
 namespace vif {
@@ -62,13 +64,14 @@ __device__ __forceinline__ double rsqrt_newton(double p) {
 // columns are all done issues no float64 instruction.  CTA 0 writes L_kk, CTA b writes X.
 constexpr int CH = 16;
 
-__global__ __launch_bounds__(128) void chol_panel_kernel(double* A, int m, int lda, int k, int* status, int code) {
+__device__ __forceinline__ void chol_panel_body(double* A, int m, int lda, int k, int* status, int code,
+                                                const int blk) {
   __shared__ double col[2 * CH];
   __shared__ double rs[CH];
   const int t = threadIdx.x, r = t >> 2, g = t & 3;
   const int k0 = k * CH;
-  const bool has_t = blockIdx.x > 0;
-  const int r0 = (k + blockIdx.x) * CH;   // first row of T_b
+  const bool has_t = blk > 0;
+  const int r0 = (k + blk) * CH;   // first row of T_b
   const bool live = r < CH || has_t;
   double v[CH / 4];
 #pragma unroll
@@ -82,7 +85,7 @@ __global__ __launch_bounds__(128) void chol_panel_kernel(double* A, int m, int l
   auto pivot = [&](double& pv, int c) {
     double p = pv;
     if (!(p > 0.0)) {
-      if (blockIdx.x == 0 && status) flag_status(status, code, k0 + c);
+      if (blk == 0 && status) flag_status(status, code, k0 + c);
       p = nan("");
     }
     const double y = rsqrt_newton(p);
@@ -130,9 +133,12 @@ __global__ __launch_bounds__(128) void chol_panel_kernel(double* A, int m, int l
 // output per thread, summed in a fixed order: the capacitance matrix is ill-conditioned
 // enough (condition ~1e7-1e8) that a run-to-run change in the last bits of its factor shows
 // in the likelihood.
-__global__ __launch_bounds__(256) void chol_update_kernel(double* A, int m, int lda, int k, int T) {
-  // tile (i, j), k < j <= i < k+1+T, enumerated over the lower triangle
-  const int b = blockIdx.x;
+__global__ __launch_bounds__(128) void chol_panel_kernel(double* A, int m, int lda, int k, int* status, int code) {
+  chol_panel_body(A, m, lda, k, status, code, blockIdx.x);
+}
+
+__device__ __forceinline__ void chol_update_body(double* A, int m, int lda, int k, const int b) {
+  // tile (i, j), k < j <= i < nt, enumerated over the lower triangle
   int ii = (int)((sqrt(8.0 * b + 1.0) - 1.0) * 0.5);
   while ((ii + 1) * (ii + 2) / 2 <= b) ++ii;
   while (ii * (ii + 1) / 2 > b) --ii;
@@ -151,6 +157,10 @@ __global__ __launch_bounds__(256) void chol_update_kernel(double* A, int m, int 
   A[(size_t)(i0 + r) * lda + j0 + c] -= acc;
 }
 
+__global__ __launch_bounds__(256) void chol_update_kernel(double* A, int m, int lda, int k) {
+  chol_update_body(A, m, lda, k, blockIdx.x);
+}
+
 // k-slices of the triangular-inverse products (one CTA each, float64 atomics)
 constexpr int KS = 4;
 constexpr int KSW = NB / KS;
@@ -161,7 +171,7 @@ cudaError_t dense_cholesky(double* A, int m, int lda, int* status, int code, cud
   for (int k = 0; k < nt; ++k) {
     chol_panel_kernel<<<nt - k, 128, 0, s>>>(A, m, lda, k, status, code);
     const int T = nt - k - 1;
-    if (T > 0) chol_update_kernel<<<T * (T + 1) / 2, 256, 0, s>>>(A, m, lda, k, T);
+    if (T > 0) chol_update_kernel<<<T * (T + 1) / 2, 256, 0, s>>>(A, m, lda, k);
   }
   return cudaGetLastError();
 }
@@ -173,11 +183,11 @@ cudaError_t dense_cholesky(double* A, int m, int lda, int* status, int code, cud
 // k, each its own CTA adding into a per-(i,j) float64 tile with atomics, so a step costs
 // two quarter tile products of latency instead of s + 1 whole ones.
 // ---------------------------------------------------------------------------
-__global__ void trtri_diag_kernel(const double* L, double* Li, int m, int lda) {
+__device__ __forceinline__ void trtri_diag_body(const double* L, double* Li, int m, int lda, const int blk) {
   __shared__ double Lt[NB][NB + 1];
   __shared__ double X[NB][NB + 1];
   __shared__ double rinv[NB];
-  const int t0 = blockIdx.x * NB;
+  const int t0 = blk * NB;
   for (int idx = threadIdx.x; idx < NB * NB; idx += blockDim.x) {
     int r = idx / NB, c = idx % NB;
     Lt[r][c] = (c <= r) ? ld_lower(L, lda, m, t0 + r, t0 + c) : 0.0;
@@ -190,6 +200,10 @@ __global__ void trtri_diag_kernel(const double* L, double* Li, int m, int lda) {
     int r = idx / NB, c = idx % NB;
     if (t0 + r < m && t0 + c < m) Li[(size_t)(t0 + r) * lda + t0 + c] = X[r][c];
   }
+}
+
+__global__ void trtri_diag_kernel(const double* L, double* Li, int m, int lda) {
+  trtri_diag_body(L, Li, m, lda, blockIdx.x);
 }
 
 // acc += P[rows][kk0..kk0+KSW) Q[kk0..kk0+KSW)[cols] for the 2 x 2 outputs of thread (tx, ty)
@@ -207,8 +221,9 @@ __device__ void tile_prod_acc_k(const double (*P)[NB + 1], const double (*Q)[NB 
 }
 
 // tmp[j] += L_{j+s,k} Linv_{k,j},  k = j + kk; CTA b = (j * s + kk) * KS + slice
-__global__ void trtri_prod_kernel(const double* L, const double* Li, int m, int lda, int sdiag, double* tmp) {
-  const int pb = blockIdx.x / KS, ks = blockIdx.x % KS;
+__device__ __forceinline__ void trtri_prod_body(const double* L, const double* Li, int m, int lda, int sdiag,
+                                                double* tmp, const int blk) {
+  const int pb = blk / KS, ks = blk % KS;
   const int j = pb / sdiag, kk = pb % sdiag;
   const int i0 = (j + sdiag) * NB, j0 = j * NB, k0 = (j + kk) * NB;
   __shared__ double P[NB][NB + 1];
@@ -229,10 +244,14 @@ __global__ void trtri_prod_kernel(const double* L, const double* Li, int m, int 
     for (int v = 0; v < 2; ++v) atomicAdd(&Tm[(ty + 16 * u) * NB + tx + 16 * v], acc[u][v]);
 }
 
+__global__ void trtri_prod_kernel(const double* L, const double* Li, int m, int lda, int sdiag, double* tmp) {
+  trtri_prod_body(L, Li, m, lda, sdiag, tmp, blockIdx.x);
+}
+
 // Linv_{j+s,j} = -Linv_{j+s,j+s} tmp[j] (added over KS slices into the zeroed Linv);
 // each slice clears the rows of tmp[j] it read, for the next step.
-__global__ void trtri_fin_kernel(double* Li, int m, int lda, int sdiag, double* tmp) {
-  const int j = blockIdx.x / KS, ks = blockIdx.x % KS;
+__device__ __forceinline__ void trtri_fin_body(double* Li, int m, int lda, int sdiag, double* tmp, const int blk) {
+  const int j = blk / KS, ks = blk % KS;
   const int i0 = (j + sdiag) * NB, j0 = j * NB;
   __shared__ double P[NB][NB + 1];
   __shared__ double Q[NB][NB + 1];
@@ -256,6 +275,10 @@ __global__ void trtri_fin_kernel(double* Li, int m, int lda, int sdiag, double* 
     }
 }
 
+__global__ void trtri_fin_kernel(double* Li, int m, int lda, int sdiag, double* tmp) {
+  trtri_fin_body(Li, m, lda, sdiag, tmp, blockIdx.x);
+}
+
 size_t trtri_work_doubles(int m) { return (size_t)((m + NB - 1) / NB) * NB * NB; }
 
 cudaError_t dense_trtri_lower(const double* L, double* Linv, int m, int lda, double* work, cudaStream_t s) {
@@ -270,6 +293,137 @@ cudaError_t dense_trtri_lower(const double* L, double* Linv, int m, int lda, dou
   for (int sd = 1; sd < nt; ++sd) {
     trtri_prod_kernel<<<(nt - sd) * sd * KS, 256, 0, s>>>(L, Linv, m, lda, sd, work);
     trtri_fin_kernel<<<(nt - sd) * KS, 256, 0, s>>>(Linv, m, lda, sd, work);
+  }
+  return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
+// Many independent factorizations at once (the batched likelihoods): each launch runs the
+// same step of every job, its blocks split among the jobs by a prefix of per-job block
+// counts (block b belongs to the job p with off[p] <= b < off[p + 1]).  A job's blocks do
+// exactly what the single-problem launch of that step does, so the results are the same.
+// ---------------------------------------------------------------------------
+namespace {
+
+enum DenseOp { OP_PANEL = 0, OP_UPDATE = 1, OP_TDIAG = 2, OP_TPROD = 3, OP_TFIN = 4 };
+
+__device__ __forceinline__ int job_of(const int* __restrict__ off, int njobs, int b) {
+  int lo = 0, hi = njobs;   // largest p with off[p] <= b
+  while (hi - lo > 1) {
+    const int mid = (lo + hi) >> 1;
+    if (off[mid] <= b) lo = mid;
+    else hi = mid;
+  }
+  return lo;
+}
+
+__global__ __launch_bounds__(128) void chol_panel_batched(const DenseJob* __restrict__ jobs,
+                                                          const int* __restrict__ off, int njobs, int k) {
+  const int p = job_of(off, njobs, blockIdx.x);
+  const DenseJob J = jobs[p];
+  chol_panel_body(J.A, J.m, J.lda, k, J.status, J.code, blockIdx.x - off[p]);
+}
+__global__ __launch_bounds__(256) void chol_update_batched(const DenseJob* __restrict__ jobs,
+                                                           const int* __restrict__ off, int njobs, int k) {
+  const int p = job_of(off, njobs, blockIdx.x);
+  const DenseJob J = jobs[p];
+  chol_update_body(J.A, J.m, J.lda, k, blockIdx.x - off[p]);
+}
+__global__ void trtri_diag_batched(const DenseJob* __restrict__ jobs, const int* __restrict__ off, int njobs) {
+  const int p = job_of(off, njobs, blockIdx.x);
+  const DenseJob J = jobs[p];
+  trtri_diag_body(J.A, J.Li, J.m, J.lda, blockIdx.x - off[p]);
+}
+__global__ void trtri_prod_batched(const DenseJob* __restrict__ jobs, const int* __restrict__ off, int njobs,
+                                   int sd) {
+  const int p = job_of(off, njobs, blockIdx.x);
+  const DenseJob J = jobs[p];
+  trtri_prod_body(J.A, J.Li, J.m, J.lda, sd, J.work, blockIdx.x - off[p]);
+}
+__global__ void trtri_fin_batched(const DenseJob* __restrict__ jobs, const int* __restrict__ off, int njobs, int sd) {
+  const int p = job_of(off, njobs, blockIdx.x);
+  const DenseJob J = jobs[p];
+  trtri_fin_body(J.Li, J.m, J.lda, sd, J.work, blockIdx.x - off[p]);
+}
+
+// blocks of job J in launch (op, step)
+int dense_blocks(const DenseJob& J, int op, int step) {
+  if (J.m <= 0) return 0;
+  const int nt = (J.m + CH - 1) / CH, ntt = (J.m + NB - 1) / NB;
+  switch (op) {
+    case OP_PANEL: return step < nt ? nt - step : 0;
+    case OP_UPDATE: {
+      const int T = nt - step - 1;
+      return T > 0 ? T * (T + 1) / 2 : 0;
+    }
+    case OP_TDIAG: return ntt;
+    case OP_TPROD: return step < ntt ? (ntt - step) * step * KS : 0;
+    default: return step < ntt ? (ntt - step) * KS : 0;
+  }
+}
+
+}  // namespace
+
+void dense_batch_free(DenseBatch* b) {
+  if (b->djobs) cudaFree(b->djobs);
+  if (b->doff) cudaFree(b->doff);
+  *b = DenseBatch();
+}
+
+cudaError_t dense_batch_init(const std::vector<DenseJob>& jobs, bool trtri, DenseBatch* b) {
+  dense_batch_free(b);
+  b->njobs = (int)jobs.size();
+  b->trtri = trtri;
+  if (b->njobs == 0) return cudaSuccess;
+  int maxm = 0;
+  for (const auto& J : jobs) maxm = std::max(maxm, J.m);
+  std::vector<int> off;
+  auto add = [&](int op, int step) {
+    int tot = 0;
+    std::vector<int> o(b->njobs + 1);
+    for (int p = 0; p < b->njobs; ++p) {
+      o[p] = tot;
+      tot += dense_blocks(jobs[p], op, step);
+    }
+    o[b->njobs] = tot;
+    if (tot == 0) return;
+    b->launches.push_back({op, step, tot, (int)off.size()});
+    off.insert(off.end(), o.begin(), o.end());
+  };
+  if (!trtri) {
+    const int nt = (maxm + CH - 1) / CH;
+    for (int k = 0; k < nt; ++k) {
+      add(OP_PANEL, k);
+      add(OP_UPDATE, k);
+    }
+  } else {
+    const int ntt = (maxm + NB - 1) / NB;
+    add(OP_TDIAG, 0);
+    for (int sd = 1; sd < ntt; ++sd) {
+      add(OP_TPROD, sd);
+      add(OP_TFIN, sd);
+    }
+  }
+  cudaError_t e = cudaMalloc((void**)&b->djobs, sizeof(DenseJob) * jobs.size());
+  if (e == cudaSuccess) e = cudaMalloc((void**)&b->doff, sizeof(int) * std::max<size_t>(off.size(), 1));
+  if (e == cudaSuccess)
+    e = cudaMemcpy(b->djobs, jobs.data(), sizeof(DenseJob) * jobs.size(), cudaMemcpyHostToDevice);
+  if (e == cudaSuccess && !off.empty())
+    e = cudaMemcpy(b->doff, off.data(), sizeof(int) * off.size(), cudaMemcpyHostToDevice);
+  if (e != cudaSuccess) dense_batch_free(b);
+  return e;
+}
+
+cudaError_t dense_batch_run(const DenseBatch& b, cudaStream_t s) {
+  for (const auto& L : b.launches) {
+    const int* off = b.doff + L.off;
+    switch (L.op) {
+      case OP_PANEL: chol_panel_batched<<<L.blocks, 128, 0, s>>>(b.djobs, off, b.njobs, L.step); break;
+      case OP_UPDATE: chol_update_batched<<<L.blocks, 256, 0, s>>>(b.djobs, off, b.njobs, L.step); break;
+      case OP_TDIAG: trtri_diag_batched<<<L.blocks, 256, 0, s>>>(b.djobs, off, b.njobs); break;
+      case OP_TPROD: trtri_prod_batched<<<L.blocks, 256, 0, s>>>(b.djobs, off, b.njobs, L.step); break;
+      default: trtri_fin_batched<<<L.blocks, 256, 0, s>>>(b.djobs, off, b.njobs, L.step); break;
+    }
   }
   return cudaGetLastError();
 }

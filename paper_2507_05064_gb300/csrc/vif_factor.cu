@@ -358,6 +358,66 @@ __global__ __launch_bounds__(FK_WARPS * 32) void factor_kernel(
     if (lane < q) S.coef[lane] = xk;
     inv = __shfl_sync(0xffffffffu, my_rs, q);
     __syncwarp();
+  } else if constexpr (QM <= 64 && sizeof(T) == 4) {
+    // ---- float32: the same register sweep with two rows per lane, rows lane (ra) and
+    // lane + 32 (rb); float64 rows of this length would not fit the register file
+    T ra[QM], rb[QM];
+    const int lb = lane + 32;
+#pragma unroll
+    for (int c = 0; c < QM; ++c) {
+      T va = (lane < Q && c <= lane) ? S.G[lane][c] : T(0);
+      if (c == lane && lane >= Q) va = T(1);
+      T vb = (lb < Q && c <= lb) ? S.G[lb < QM ? lb : 0][c] : T(0);
+      if (c == lb && lb >= Q) vb = T(1);
+      ra[c] = va;
+      rb[c] = vb;
+    }
+    bool notpd = false;
+    T rsa = T(1), rsb = T(1);   // 1 / L[r][r] of the lane's two rows
+#pragma unroll
+    for (int c = 0; c < QM; ++c) {
+      const bool hi = c >= 32;
+      T piv = __shfl_sync(0xffffffffu, hi ? rb[c] : ra[c], c & 31);
+      if (!(piv > T(0))) {
+        notpd = true;
+        piv = T(NAN);
+      }
+      const T rs = rsqrt_refined(piv);
+      const T la = (!hi && lane == c) ? piv * rs : ra[c] * rs;
+      const T lbv = (hi && lb == c) ? piv * rs : rb[c] * rs;
+      if (!hi && lane == c) rsa = rs;
+      if (hi && lb == c) rsb = rs;
+      ra[c] = la;
+      rb[c] = lbv;
+#pragma unroll
+      for (int s2 = c + 1; s2 < QM; ++s2) {
+        const T ls = __shfl_sync(0xffffffffu, s2 < 32 ? la : lbv, s2 & 31);
+        ra[s2] = fma(-la, ls, ra[s2]);
+        rb[s2] = fma(-lbv, ls, rb[s2]);
+      }
+    }
+    if (notpd && lane == 0) flag_status(status, ST_NOTPD_FACTOR, i);
+#pragma unroll
+    for (int c = 0; c < QM; ++c) {
+      if (lane < Q && c <= lane) S.G[lane][c] = ra[c];
+      if (lb < Q && c <= lb) S.G[lb][c] = rb[c];
+    }
+    __syncwarp();
+    // ---- A_i: L_NN^T x = l column-oriented, rows t = lane and lane + 32 per lane
+    T ba = (lane < q) ? S.G[q][lane] : T(0);
+    T bb = (lb < q) ? S.G[q][lb] : T(0);
+    T xa = T(0), xb = T(0);
+    for (int k = q - 1; k >= 0; --k) {
+      const T x = __shfl_sync(0xffffffffu, k >= 32 ? bb * rsb : ba * rsa, k & 31);
+      if (lane == k) xa = x;
+      if (lb == k) xb = x;
+      if (lane < k) ba = fma(-S.G[k][lane], x, ba);
+      if (lb < k) bb = fma(-S.G[k][lb], x, bb);
+    }
+    if (lane < q) S.coef[lane] = xa;
+    if (lb < q) S.coef[lb] = xb;
+    inv = __shfl_sync(0xffffffffu, q >= 32 ? rsb : rsa, q & 31);
+    __syncwarp();
   } else {
     // ---- Cholesky of R (lower, in place)
     for (int c = 0; c < Q; ++c) {

@@ -121,6 +121,31 @@ size_t trtri_work_doubles(int m);
 cudaError_t dense_trtri_lower(const double* L, double* Linv, int m, int lda, double* work, cudaStream_t s);
 cudaError_t reduce_sum(const double* x, int64_t n, double* partial, double* out, cudaStream_t s);
 
+// Batched form for many independent problems: one launch per step for all jobs.  A job
+// is a Cholesky of A (m x m, leading dimension lda, non-PD pivots flagged with `code` in
+// status) or, with trtri, the inverse of the lower factor A into Li (zeroed beforehand,
+// work: trtri_work_doubles(m) zeroed doubles).
+struct DenseJob {
+  double* A;
+  double* Li;
+  double* work;
+  int* status;
+  int m, lda, code;
+};
+struct DenseLaunch {
+  int op, step, blocks, off;
+};
+struct DenseBatch {
+  DenseJob* djobs = nullptr;   // device copy of the jobs
+  int* doff = nullptr;         // device block offsets, njobs + 1 per launch
+  int njobs = 0;
+  bool trtri = false;
+  std::vector<DenseLaunch> launches;
+};
+cudaError_t dense_batch_init(const std::vector<DenseJob>& jobs, bool trtri, DenseBatch* b);   // allocates
+cudaError_t dense_batch_run(const DenseBatch& b, cudaStream_t s);
+void dense_batch_free(DenseBatch* b);
+
 // vif_lowrank_tc.cu: A = K_nm L_m^{-T} on the tensor cores for the float32 path.  init
 // (once per device, outside stream capture) raises the kernel's shared-memory limit;
 // pack holds lowrank_A_tc_pack_floats(mpad) floats; mpad = 32 ceil(m / 32).

@@ -164,6 +164,22 @@ def test_mv30_and_k64_candidate_lists():
     ctx.close()
 
 
+@pytest.mark.parametrize("mv", [33, 40, 47])
+def test_mixed_factors_with_more_than_32_neighbours(mv):
+    """Float32 factors for 32 < m_v + 1 <= 64: the register Cholesky with two rows per lane,
+    including the first points of the order (fewer than 32 predecessors)."""
+    P = prob(1500, 2, 90, mv, "matern32", 0.05, 0.1, 40 + mv)
+    Nor = O.causal_neighbors(P.X, P.Z, P.theta, mv)
+    vif = O.VIF(P.X, P.Z, P.theta, Nor)
+    ctx = V.Context(P.X, P.Z, mv, P.theta, precision=V.MIXED, neighbor_search=False)
+    ctx.set_neighbors(Nor.astype(np.int32))
+    assert nll_close(ctx.nll(P.theta, P.y), vif.nll(P.y), 1500, RTOL_MIXED)
+    Ac, D = ctx.factors()
+    ctx.close()
+    np.testing.assert_allclose(D, vif.D, rtol=2e-3)
+    np.testing.assert_allclose(Ac, vif.Acoef, rtol=2e-3, atol=2e-3 * np.abs(vif.Acoef).max())
+
+
 # --------------------------------------------------------------------------- failure paths (host-made)
 def test_nan_input_reports_not_pd():
     P = prob(300, 2, 20, 5, "matern32", 0.1, 0.2, 16)
@@ -614,11 +630,12 @@ def test_batch_graph_replay_matches_single_problem_calls():
         np.testing.assert_allclose(got, ref, rtol=1e-10)
     info = B.info()
     assert info["branches"] in (4, 8, 16, 32) and info["best_replay_ms"] > 0
-    # three problems against the oracle on the GPU's neighbour sets' definition
-    for k in (0, 2, 4):
+    # float64 and mixed problems against the oracle on the GPU's neighbour sets' definition
+    for k in (0, 1, 2, 3, 4, 5):
         P = probs[k]
         Nor = O.causal_neighbors(P.X, P.Z, P.theta, P.mv)
-        assert nll_close(got[k], O.vif_nll(P.X, P.Z, P.theta, Nor, P.y), P.X.shape[0], RTOL64)
+        tol = RTOL_MIXED if k % 2 else RTOL64
+        assert nll_close(got[k], O.vif_nll(P.X, P.Z, P.theta, Nor, P.y), P.X.shape[0], tol), (k, got[k])
     B.close()
     for c in ctxs:
         c.close()
