@@ -270,12 +270,12 @@ vif_status vif_laplace_predict(vif_ctx *ctx, const vif_cov *theta, const double 
 vif_status vif_tridiag_log_quadrature(const double *diag, const double *offdiag, int32_t k, double *out);
 
 /* Learned diagonal correction of the VIFDU preconditioner (the paper has none):
- * c_i = 4 tanh(o_i / 4), o_i from a tanh network 8 -> 64 -> 64 -> 1 on local features
+ * c_i = 4 tanh(o_i / 4), o_i from a tanh network 10 -> 64 -> 64 -> 1 on local features
  * of point i, and the preconditioner uses W'_i = W_i exp(c_i).  The network lives in a
  * caller-allocated DEVICE buffer of vif_mlp_bytes() bytes (float32 master weights, Adam
- * moments, the float16 copy the kernels read).  Parameters are packed as W1 (64 x 8,
+ * moments, the float16 copy the kernels read).  Parameters are packed as W1 (64 x 10,
  * row-major), b1 (64), W2 (64 x 64), b2 (64), w3 (64), b3 (1): VIF_MLP_NPARAM floats. */
-#define VIF_MLP_NIN 8
+#define VIF_MLP_NIN 10
 #define VIF_MLP_NH 64
 #define VIF_MLP_NPARAM (VIF_MLP_NH * VIF_MLP_NIN + VIF_MLP_NH + VIF_MLP_NH * VIF_MLP_NH + VIF_MLP_NH + VIF_MLP_NH + 1)
 size_t vif_mlp_bytes(void);
@@ -284,7 +284,7 @@ vif_status vif_mlp_init(void *net, uint64_t seed, void *stream);
 /* Set / read the float32 parameters (params: VIF_MLP_NPARAM floats, host or device). */
 vif_status vif_mlp_set_params(void *net, const float *params, void *stream);
 vif_status vif_mlp_get_params(const void *net, float *params);
-/* c = network(feats) for n feature rows (DEVICE n x 8 float in, DEVICE n float out). */
+/* c = network(feats) for n feature rows (DEVICE n x 10 float in, DEVICE n float out). */
 vif_status vif_mlp_forward(const void *net, const float *feats, int64_t n, float *c, void *stream);
 /* grad = d(sum_i gc_i c_i)/d(params) (DEVICE inputs, DEVICE VIF_MLP_NPARAM floats out). */
 vif_status vif_mlp_backward(const void *net, const float *feats, const float *gc, int64_t n, float *grad,
@@ -293,8 +293,11 @@ vif_status vif_mlp_backward(const void *net, const float *feats, const float *gc
  * residual Vecchia factors of the last vif_laplace_mode / vif_mlp_train call on ctx:
  *   0 (log W_i + 3)/2   1 (log D_i + 3)/2   2 log(1 + W_i D_i)   3 |N(i)|/m_v
  *   4 sum_k A_i[k]^2    5 sum of A_j[k]^2 over the points j that condition on i
- *   6 log(mean_k W_{N_k(i)} / W_i)   7 log(1 + sum_{j: N_k(j)=i} W_j A_j[k]^2 / W_i).
- * feats: n x 8 float (host or device). */
+ *   6 log(mean_k W_{N_k(i)} / W_i)   7 log(1 + sum_{j: N_k(j)=i} W_j A_j[k]^2 / W_i)
+ *   8 max_k |rho(i, N_k(i))|          9 mean_k |rho(i, N_k(i))|
+ * with rho the correlation of the residual process (Sec. 2.1: Sigma~ minus the predictive-
+ * process part, the jitter on the diagonal) between i and its neighbours, whose largest
+ * values chose N(i) (Sec. 6).  feats: n x 10 float (host or device). */
 vif_status vif_mlp_features(vif_ctx *ctx, const double *W, float *feats);
 
 typedef struct {

@@ -3,12 +3,13 @@
 TEST INFRASTRUCTURE ONLY (see vif_oracle).  The paper has no learned part; this
 module states, in plain numpy, what the CUDA network computes:
 
-  features f_i (8 per point, from the Laplace weight W and the residual Vecchia
-  factors A_i, D_i of the current Newton iterate) -> h1 = tanh(W1 f + b1) ->
+  features f_i (10 per point, from the Laplace weight W, the residual Vecchia
+  factors A_i, D_i of the current Newton iterate and the residual correlations of
+  each point with its neighbours) -> h1 = tanh(W1 f + b1) ->
   h2 = tanh(W2 h1 + b2) -> o = w3 . h2 + b3 -> c_i = 4 tanh(o / 4),
 
 and the preconditioner uses W'_i = W_i exp(c_i) in P = B^T W' B + Sigma_dagger^{-1}.
-Parameters are packed as W1 (64x8, row-major), b1 (64), W2 (64x64), b2 (64), w3 (64), b3 (1).
+Parameters are packed as W1 (64x10, row-major), b1 (64), W2 (64x64), b2 (64), w3 (64), b3 (1).
 
 The training loss is the Hutchinson estimate of ||P^{-1} A - I||_F^2 with
 A = W + Sigma_dagger^{-1}: L = mean_k ||P^{-1} A z_k - z_k||^2 over Rademacher z_k,
@@ -20,7 +21,7 @@ from __future__ import annotations
 
 import numpy as np
 
-NIN, NH = 8, 64
+NIN, NH = 10, 64
 NPARAM = NH * NIN + NH + NH * NH + NH + NH + 1
 
 
@@ -36,7 +37,7 @@ def unpack(p: np.ndarray):
 
 
 def forward(p: np.ndarray, F: np.ndarray) -> np.ndarray:
-    """Correction c for feature rows F (n x 8)."""
+    """Correction c for feature rows F (n x 10)."""
     W1, b1, W2, b2, w3, b3 = unpack(p)
     h1 = np.tanh(F @ W1.T + b1)
     h2 = np.tanh(h1 @ W2.T + b2)
@@ -62,12 +63,14 @@ def backward(p: np.ndarray, F: np.ndarray, gc: np.ndarray) -> np.ndarray:
     return np.concatenate([dW1.ravel(), db1, dW2.ravel(), db2, dw3, [db3]])
 
 
-def features(W, D, Acoef, N, mv: int) -> np.ndarray:
+def features(W, D, Acoef, N, mv: int, rho=None) -> np.ndarray:
     """Per-point network inputs (each a fixed affine map of a local quantity):
       0 log W_i            1 log D_i             2 log(1 + W_i D_i)
       3 |N(i)| / m_v       4 sum_k A_i[k]^2      5 sum over the points j that condition on i
                                                    of A_j[k]^2
       6 log(mean_{k} W_{N_k(i)} / W_i)           7 log(1 + sum_{j: N_k(j)=i} W_j A_j[k]^2 / W_i)
+      8 max_k |rho(i, N_k(i))|                   9 mean_k |rho(i, N_k(i))|
+    with rho (n x 2: the largest and the mean) from vif_oracle.residual_neighbor_corr.
     """
     n = W.shape[0]
     F = np.zeros((n, NIN))
@@ -91,6 +94,9 @@ def features(W, D, Acoef, N, mv: int) -> np.ndarray:
     F[:, 5] = s_ch
     F[:, 6] = np.where(q > 0, np.log(np.where(q > 0, mW / np.maximum(q, 1), 1.0) / W), 0.0)
     F[:, 7] = np.log1p(s_chw / W)
+    if rho is not None:
+        F[:, 8] = rho[:, 0]
+        F[:, 9] = rho[:, 1]
     return F
 
 

@@ -330,6 +330,29 @@ def vecchia_factors(X, Z, theta, N, lowrank: LowRank | None = None):
     return Acoef, D
 
 
+def residual_neighbor_corr(X, Z, theta, N) -> np.ndarray:
+    """Per point i: the largest and the mean |rho(i, j)| over its neighbours j in N(i), rho
+    the correlation of the residual process whose covariance the residual Vecchia blocks
+    hold (Sec. 2.1: Sigma~ - Sigma_mn^T Sigma_m^{-1} Sigma_mn, the nugget or the R7 jitter on
+    the diagonal); zeros for points without neighbours.  Inputs 8 and 9 of the learned
+    preconditioner correction."""
+    n = X.shape[0]
+    lowrank = LowRank(X, Z, theta)
+    tdiag = residual_diag(theta)
+    cdiag = theta.variance + tdiag - (lowrank.lr_diag() if lowrank.m else np.zeros(n))
+    out = np.zeros((n, 2))
+    for i in range(n):
+        nb = N[i][N[i] >= 0]
+        if len(nb) == 0:
+            continue
+        c = cov(X[i:i + 1], X[nb], theta)[0]
+        if lowrank.m:
+            c = c - lowrank.lr([i], nb)[0]
+        r = np.abs(c / np.sqrt(cdiag[i] * cdiag[nb]))
+        out[i] = r.max(), r.mean()
+    return out
+
+
 def B_matrix(N, Acoef) -> sp.csr_matrix:
     """Unit lower-triangular B with B_{i,N(i)} = -A_i (Sec. 2.1)."""
     n, mv = N.shape

@@ -89,6 +89,7 @@ struct vif_ctx {
          *l_sc = nullptr, *l_red = nullptr, *l_corr = nullptr;
   int *l_counter = nullptr, *l_abort = nullptr;
   float *m_feat = nullptr, *m_gc = nullptr, *m_part = nullptr, *m_grad = nullptr;
+  float* m_rho = nullptr;   // latent-GP contexts: max and mean |residual correlation| per point
   int64_t knn_rescored = 0, knn_fallback = 0;
   bool have_factors = false;
   bool timing = false;
@@ -302,7 +303,8 @@ vif_status run_factor(vif_ctx* ctx, const CovParams& cp, T* A, const T* Xs, T* F
     gsub = ctx->gsub;
   }
   CK(vecchia_factor_gs<T>(A, Xs, ctx->N, ctx->order, ctx->y, ctx->n, ctx->d, ctx->m, ctx->mpad, ctx->mv,
-                          ctx->fpad, cp, F, ctx->Acoef, ctx->Dv, ctx->logD, ctx->status, ctx->stream, gsub));
+                          ctx->fpad, cp, F, ctx->Acoef, ctx->Dv, ctx->logD, ctx->status, ctx->stream, gsub,
+                          ctx->m_rho));
   return VIF_OK;
 }
 
@@ -357,7 +359,7 @@ void free_ctx(vif_ctx* c) {
                    c->ch_slot, c->l_b,  c->l_W,    c->l_v,    c->l_Ginv, c->l_om,   c->l_rsD,  c->l_ll,
                    c->l_x,    c->l_r,   c->l_z,    c->l_p,    c->l_Ap,   c->l_t,    c->l_t2,   c->l_x1,
                    c->l_sdi,  c->l_sm,  c->l_cm,   c->l_tm,   c->l_part, c->l_LinvC, c->l_G3,  c->l_LinvC3,
-                   c->l_sc,   c->l_red, c->l_corr, c->sched_fwd, c->sched_rev, c->ord_fwd, c->ord_rev, c->ch_coef, c->slq_eps, c->l_Apad, c->l_anorm2, c->l_dvinv, c->l_pacc, c->l_counter, c->l_abort, c->m_feat,
+                   c->l_sc,   c->l_red, c->l_corr, c->sched_fwd, c->sched_rev, c->ord_fwd, c->ord_rev, c->ch_coef, c->slq_eps, c->l_Apad, c->l_anorm2, c->l_dvinv, c->l_pacc, c->l_counter, c->l_abort, c->m_feat, c->m_rho,
                    c->g_U,    c->g_Y,   c->g_g,    c->g_v,    c->g_sc,   c->g_red,  c->g_a,    c->g_av,
                    c->g_dv,
                    c->mr_v,   c->mr_x,  c->mr_r,   c->mr_z,   c->mr_p,   c->mr_Ap,  c->mr_t,   c->mr_t2,
@@ -864,6 +866,10 @@ vif_status vif_build(const double* X, int64_t n, int32_t d, const double* Z, int
     ctx->F = p;
   }
   ALLOC(ctx->Acoef, (size_t)n * std::max(mv, 1));
+  if (ctx->likelihood != VIF_GAUSSIAN) {
+    ALLOC(ctx->m_rho, 2 * (size_t)n);
+    cudaMemset(ctx->m_rho, 0, 2 * sizeof(float) * (size_t)n);   // read before the first factorization
+  }
   ALLOC(ctx->Dv, (size_t)n);
   ALLOC(ctx->logD, (size_t)n);
   ctx->nsplit = gram_nsplit(n, ctx->fpad);
@@ -1446,7 +1452,7 @@ bool tridiag_log_quadrature(std::vector<double> d, std::vector<double> e, double
   return true;
 }
 
-// mlp scratch: features (n x 8 float), gc (n float), backward partials, gradient
+// mlp scratch: features (n x 10 float), gc (n float), backward partials, gradient
 vif_status mlp_scratch(vif_ctx* ctx) {
   if (ctx->m_feat) return VIF_OK;
   CKS(dalloc(ctx, &ctx->m_feat, (size_t)ctx->n * VIF_MLP_NIN));
@@ -1459,8 +1465,8 @@ vif_status mlp_scratch(vif_ctx* ctx) {
 // c = network(features(W)) into l_corr.
 vif_status mlp_correction_c(vif_ctx* ctx, const void* net) {
   CKS(mlp_scratch(ctx));
-  CK(mlp_features(ctx->l_W, ctx->Dv, ctx->Acoef, ctx->N, ctx->ch_ptr, ctx->ch_row, ctx->ch_slot, ctx->n, ctx->mv,
-                  ctx->m_feat, ctx->stream));
+  CK(mlp_features(ctx->l_W, ctx->Dv, ctx->Acoef, ctx->m_rho, ctx->N, ctx->ch_ptr, ctx->ch_row, ctx->ch_slot,
+                  ctx->n, ctx->mv, ctx->m_feat, ctx->stream));
   CK(mlp_forward_f64(net, ctx->m_feat, ctx->n, ctx->l_corr, ctx->stream));
   return VIF_OK;
 }
@@ -2183,8 +2189,8 @@ vif_status vif_mlp_features(vif_ctx* ctx, const double* W, float* feats) {
   if (!ctx->lap_ready) return set_err(ctx, VIF_ERR_STATE, "call vif_laplace_mode or vif_mlp_train first");
   CKS(mlp_scratch(ctx));
   CKS(upload(ctx, ctx->l_t, W, (size_t)ctx->n * sizeof(double)));
-  CK(mlp_features(ctx->l_t, ctx->Dv, ctx->Acoef, ctx->N, ctx->ch_ptr, ctx->ch_row, ctx->ch_slot, ctx->n, ctx->mv,
-                  ctx->m_feat, ctx->stream));
+  CK(mlp_features(ctx->l_t, ctx->Dv, ctx->Acoef, ctx->m_rho, ctx->N, ctx->ch_ptr, ctx->ch_row, ctx->ch_slot,
+                  ctx->n, ctx->mv, ctx->m_feat, ctx->stream));
   return download(ctx, feats, ctx->m_feat, (size_t)ctx->n * VIF_MLP_NIN * sizeof(float));
 }
 

@@ -129,7 +129,7 @@ __global__ __launch_bounds__(FK_WARPS * 32) void factor_kernel(
     const T* __restrict__ A, const T* __restrict__ Xs, const int32_t* __restrict__ N,
     const int32_t* __restrict__ order, const double* __restrict__ y, int64_t n, int d, int m, int mpad, int mv,
     int fpad, CovParams cp, T* __restrict__ F, double* __restrict__ Acoef, double* __restrict__ Dv,
-    double* __restrict__ logD, int* status, const float* __restrict__ gsub) {
+    double* __restrict__ logD, int* status, const float* __restrict__ gsub, float* __restrict__ rho) {
   using SM = FactorSmem<T, R, GS>;
   constexpr int QM = SM::QM, V = SM::V, KC = SM::KC;
   using VT = typename Vec16<T>::type;
@@ -311,6 +311,25 @@ __global__ __launch_bounds__(FK_WARPS * 32) void factor_kernel(
       S.G[a][b2] = kv - S.G[a][b2];
   }
   __syncwarp();
+  if (rho) {
+    // residual correlations of i with its neighbours, R[q][k] / sqrt(R[q][q] R[k][k]): their
+    // largest and mean absolute value (inputs of the learned preconditioner correction)
+    float rmax = 0.f, rsum = 0.f;
+    for (int k = lane; k < q; k += 32) {
+      const float r = fabsf((float)((double)S.G[q][k] / sqrt((double)S.G[q][q] * (double)S.G[k][k])));
+      rmax = fmaxf(rmax, r);
+      rsum += r;
+    }
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) {
+      rmax = fmaxf(rmax, __shfl_xor_sync(0xffffffffu, rmax, off));
+      rsum += __shfl_xor_sync(0xffffffffu, rsum, off);
+    }
+    if (lane == 0) {
+      rho[2 * i] = rmax;
+      rho[2 * i + 1] = q > 0 ? rsum / (float)q : 0.f;
+    }
+  }
   T inv;   // 1 / sqrt(D_i)
   if constexpr (QM <= 32) {
     // ---- Cholesky of R in registers: lane r holds row r, columns broadcast by
@@ -516,14 +535,14 @@ template <typename T, int R, bool GS>
 static cudaError_t launch_factor(const T* A, const T* Xs, const int32_t* N, const int32_t* order, const double* y,
                                  int64_t n, int d, int m, int mpad, int mv, int fpad, CovParams cp, T* F,
                                  double* Acoef, double* Dv, double* logD, int* status, cudaStream_t s,
-                                 const float* gsub) {
+                                 const float* gsub, float* rho) {
   size_t smem = sizeof(FactorSmem<T, R, GS>) * FK_WARPS;
   cudaError_t e = cudaFuncSetAttribute(factor_kernel<T, R, GS>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        (int)smem);
   if (e != cudaSuccess) return e;
   unsigned grid = (unsigned)((n + FK_WARPS - 1) / FK_WARPS);
   factor_kernel<T, R, GS><<<grid, FK_WARPS * 32, smem, s>>>(A, Xs, N, order, y, n, d, m, mpad, mv, fpad, cp, F,
-                                                             Acoef, Dv, logD, status, gsub);
+                                                             Acoef, Dv, logD, status, gsub, rho);
   return cudaGetLastError();
 }
 
@@ -531,14 +550,14 @@ template <typename T>
 cudaError_t vecchia_factor_gs(const T* A, const T* Xs, const int32_t* N, const int32_t* order, const double* y,
                               int64_t n, int d, int m, int mpad, int mv, int fpad, CovParams cp, T* F,
                               double* Acoef, double* Dv, double* logD, int* status, cudaStream_t s,
-                              const float* gsub) {
+                              const float* gsub, float* rho) {
   if (d > FK_MAXD) return cudaErrorInvalidValue;
   const int Q = mv + 1;
   if (gsub) {
     // the Gram of each point's rows comes from the tensor cores (float32, Q <= 32)
     if constexpr (sizeof(T) == 4) {
 #define LG(RR) launch_factor<T, RR, true>(A, Xs, N, order, y, n, d, m, mpad, mv, fpad, cp, F, Acoef, Dv, logD, \
-                                          status, s, gsub)
+                                          status, s, gsub, rho)
       if (Q <= 14) return LG(2);
       if (Q <= 21) return LG(3);
       if (Q <= 28) return LG(4);
@@ -548,7 +567,7 @@ cudaError_t vecchia_factor_gs(const T* A, const T* Xs, const int32_t* N, const i
     return cudaErrorInvalidValue;
   }
 #define LF(RR) launch_factor<T, RR, false>(A, Xs, N, order, y, n, d, m, mpad, mv, fpad, cp, F, Acoef, Dv, logD, \
-                                           status, s, nullptr)
+                                           status, s, nullptr, rho)
   if (Q <= 14) return LF(2);
   if (Q <= 21) return LF(3);
   if (Q <= 28) return LF(4);
@@ -564,15 +583,15 @@ cudaError_t vecchia_factor(const T* A, const T* Xs, const int32_t* N, const int3
                            int64_t n, int d, int m, int mpad, int mv, int fpad, CovParams cp, T* F, double* Acoef,
                            double* Dv, double* logD, int* status, cudaStream_t s) {
   return vecchia_factor_gs<T>(A, Xs, N, order, y, n, d, m, mpad, mv, fpad, cp, F, Acoef, Dv, logD, status, s,
-                              nullptr);
+                              nullptr, nullptr);
 }
 template cudaError_t vecchia_factor_gs<float>(const float*, const float*, const int32_t*, const int32_t*,
                                               const double*, int64_t, int, int, int, int, int, CovParams, float*,
-                                              double*, double*, double*, int*, cudaStream_t, const float*);
+                                              double*, double*, double*, int*, cudaStream_t, const float*, float*);
 template cudaError_t vecchia_factor_gs<double>(const double*, const double*, const int32_t*, const int32_t*,
                                                const double*, int64_t, int, int, int, int, int, CovParams,
                                                double*, double*, double*, double*, int*, cudaStream_t,
-                                               const float*);
+                                               const float*, float*);
 template cudaError_t vecchia_factor<float>(const float*, const float*, const int32_t*, const int32_t*,
                                            const double*, int64_t, int, int, int, int, int, CovParams, float*,
                                            double*, double*, double*, int*, cudaStream_t);

@@ -175,12 +175,13 @@ cudaError_t vecchia_factor(const T* A, const T* Xs, const int32_t* N, const int3
                            double* Acoef, double* Dv, double* logD, int* status, cudaStream_t s);
 // gsub (float32 path only): the Gram of each point's rows [A_N(i); a_i] from
 // union_gram_tc, slot-major in the processing order with stride (m_v + 1)(m_v + 2) / 2
-// (packed lower triangle); NULL: the kernel forms it itself.
+// (packed lower triangle); NULL: the kernel forms it itself.  rho (optional, n x 2
+// floats): per point the largest and the mean |residual correlation| with its neighbours.
 template <typename T>
 cudaError_t vecchia_factor_gs(const T* A, const T* Xs, const int32_t* N, const int32_t* order, const double* y,
                               int64_t n, int d, int m, int mpad, int mv, int fpad, CovParams cp, T* F,
                               double* Acoef, double* Dv, double* logD, int* status, cudaStream_t s,
-                              const float* gsub);
+                              const float* gsub, float* rho = nullptr);
 // vif_factor_tc.cu: the residual products A_N^T A_N on the tensor cores (float32 path).
 // Groups of consecutive points of the processing order share one 128-row Gram.
 struct UnionGroups {
@@ -345,7 +346,8 @@ cudaError_t lap_grad_forms(int64_t n, const double* a, const double* c, const do
 size_t mlp_bytes();
 cudaError_t mlp_init(void* net, uint64_t seed, cudaStream_t s);
 cudaError_t mlp_set(void* net, const float* p, cudaStream_t s);
-cudaError_t mlp_features(const double* W, const double* D, const double* Acoef, const int32_t* N,
+// rho: n x 2 floats (largest and mean |residual correlation| with the neighbours) or NULL (zeros)
+cudaError_t mlp_features(const double* W, const double* D, const double* Acoef, const float* rho, const int32_t* N,
                          const int32_t* ch_ptr, const int32_t* ch_row, const int32_t* ch_slot, int64_t n, int mv,
                          float* F, cudaStream_t s);
 cudaError_t mlp_forward_f32(const void* net, const float* F, int64_t n, float* c, cudaStream_t s);

@@ -1,7 +1,8 @@
 // Learned diagonal correction of the VIFDU preconditioner (not part of the paper).
 //
-// A two-layer tanh network maps 8 local features of point i (Laplace weight W_i,
-// residual variance D_i, the Vecchia coefficients that touch i) to c_i =
+// A two-layer tanh network maps 10 local features of point i (Laplace weight W_i,
+// residual variance D_i, the Vecchia coefficients that touch i, the largest and mean
+// residual correlation with its neighbours) to c_i =
 // 4 tanh(o_i / 4); the preconditioner then uses W'_i = W_i exp(c_i) in
 // P = B^T W' B + Sigma_dagger^{-1} (the CG system keeps W).  c = 0 is the plain
 // VIFDU preconditioner, and a zero output layer gives exactly that, so an
@@ -81,10 +82,11 @@ __global__ void mlp_set_kernel(void* net, const float* p) {
 }
 
 // ---------------------------------------------------------------------------
-// Features (8 per point, fixed affine normalisation)
+// Features (10 per point, fixed affine normalisation)
 // ---------------------------------------------------------------------------
 __global__ void mlp_features_kernel(const double* __restrict__ W, const double* __restrict__ D,
-                                    const double* __restrict__ Acoef, const int32_t* __restrict__ N,
+                                    const double* __restrict__ Acoef, const float* __restrict__ rho,
+                                    const int32_t* __restrict__ N,
                                     const int32_t* __restrict__ ch_ptr, const int32_t* __restrict__ ch_row,
                                     const int32_t* __restrict__ ch_slot, int64_t n, int mv, float* F) {
   int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -114,6 +116,8 @@ __global__ void mlp_features_kernel(const double* __restrict__ W, const double* 
   f[5] = (float)s_ch;
   f[6] = (float)(q > 0 ? log(mW / q / wi) : 0.0);
   f[7] = (float)log1p(s_chw / wi);
+  f[8] = rho ? rho[2 * i] : 0.f;
+  f[9] = rho ? rho[2 * i + 1] : 0.f;
 }
 
 // ---------------------------------------------------------------------------
@@ -316,10 +320,10 @@ cudaError_t mlp_set(void* net, const float* p, cudaStream_t s) {
   mlp_set_kernel<<<nblk(NPP, 256), 256, 0, s>>>(net, p);
   return cudaGetLastError();
 }
-cudaError_t mlp_features(const double* W, const double* D, const double* Acoef, const int32_t* N,
+cudaError_t mlp_features(const double* W, const double* D, const double* Acoef, const float* rho, const int32_t* N,
                          const int32_t* ch_ptr, const int32_t* ch_row, const int32_t* ch_slot, int64_t n, int mv,
                          float* F, cudaStream_t s) {
-  mlp_features_kernel<<<nblk(n, 256), 256, 0, s>>>(W, D, Acoef, N, ch_ptr, ch_row, ch_slot, n, mv, F);
+  mlp_features_kernel<<<nblk(n, 256), 256, 0, s>>>(W, D, Acoef, rho, N, ch_ptr, ch_row, ch_slot, n, mv, F);
   return cudaGetLastError();
 }
 cudaError_t mlp_forward_f32(const void* net, const float* F, int64_t n, float* c, cudaStream_t s) {

@@ -75,7 +75,7 @@ class MlpTrainStats(C.Structure):
     _fields_ = [("systems", C.c_int32), ("loss_first", C.c_double), ("loss_last", C.c_double)]
 
 
-MLP_NIN, MLP_NH = 8, 64
+MLP_NIN, MLP_NH = 10, 64
 MLP_NPARAM = MLP_NH * MLP_NIN + MLP_NH + MLP_NH * MLP_NH + MLP_NH + MLP_NH + 1
 NSTAGES = 5
 STAGES = ["sigma_m_chol_inv", "lowrank_A", "vecchia_factor", "gram_FtF", "capacitance_nll"]

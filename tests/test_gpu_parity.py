@@ -20,6 +20,7 @@ pytestmark = pytest.mark.gpu
 
 GOLD = os.path.join(os.path.dirname(__file__), "golden")
 TIE_TOL = 1e-9
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 RTOL64 = 1e-8
 RTOL_MIXED = 1e-5
 
@@ -670,7 +671,7 @@ def test_mlp_features_match_oracle_and_untrained_network_is_plain_vifdu():
     b0, st0 = ctx.laplace_mode(P.theta, P.y, rel_tol=1e-6)
     _, W = O.bern_grad_W(P.y, b0)
     vif = O.VIF(P.X, P.Z, P.theta, Nor)
-    F_or = MO.features(W, vif.D, vif.Acoef, Nor, 8)
+    F_or = MO.features(W, vif.D, vif.Acoef, Nor, 8, O.residual_neighbor_corr(P.X, P.Z, P.theta, Nor))
     F_gpu = ctx.mlp_features(W)
     np.testing.assert_allclose(F_gpu, F_or, rtol=1e-4, atol=1e-5)
     net = V.Network(seed=3)                       # zero output layer: c = 0
@@ -678,6 +679,26 @@ def test_mlp_features_match_oracle_and_untrained_network_is_plain_vifdu():
     assert st1["pcg_iters_total"] == st0["pcg_iters_total"]
     np.testing.assert_allclose(b1, b0, rtol=1e-12, atol=1e-12)
     ctx.close()
+
+
+def test_trained_correction_needs_fewer_cg_iterations_on_a_held_out_problem():
+    """The committed weights (trained on 5000 Newton systems of n = 2e4 Bernoulli-logit
+    problems, Matern-3/2 ranges in [0.03, 0.1]) against the plain VIFDU preconditioner on a
+    problem of that shape whose seed no training problem used: both reach the same mode at
+    the same CG tolerance, the learned correction in fewer CG iterations."""
+    p = np.load(os.path.join(ROOT, "paper_2507_05064_gb300", "weights", "vifdu_mlp.npy"))
+    assert p.shape == (V.MLP_NPARAM,)
+    P = synth.make_problem(20_000, 2, 200, 20, "matern32", 1.0, 0.05, 0.0, 9_100_001,
+                           likelihood="bernoulli_logit", lloyd=2, rff=256)
+    ctx = V.Context(P.X, P.Z, 20, P.theta, likelihood=V.BERNOULLI_LOGIT)
+    net = V.Network(params=p.astype(np.float32))
+    b_p, s_p = ctx.laplace_mode(P.theta, P.y, rel_tol=1e-6)
+    b_l, s_l = ctx.laplace_mode(P.theta, P.y, rel_tol=1e-6, precond=1, mlp_weights=net)
+    ctx.close()
+    print("CG iterations plain", s_p["pcg_iters_total"], "learned", s_l["pcg_iters_total"],
+          "Newton", s_p["newton_iters"], s_l["newton_iters"])
+    assert np.linalg.norm(b_l - b_p) <= 1e-5 * np.linalg.norm(b_p)
+    assert s_l["pcg_iters_total"] <= 0.9 * s_p["pcg_iters_total"]
 
 
 def test_training_lowers_the_preconditioner_loss():

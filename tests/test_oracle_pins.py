@@ -114,6 +114,41 @@ def test_knn_matches_dense_residual_correlation_brute_force():
         assert list(N[i, :q]) == list(ref), i
 
 
+@pytest.mark.parametrize("m,nugget", [(15, 0.0), (0, 0.0), (15, 0.1)])
+def test_residual_neighbour_correlations_from_the_dense_residual_covariance(m, nugget):
+    """Inputs 8-9 of the learned correction against the dense residual covariance
+    Sigma~ - Sigma^l (a dense solve, not the oracle's Cholesky route) and, without a
+    nugget, against the keys the neighbour search ranked by: the chosen |rho| are the
+    largest ones, so their maximum is 1 - the smallest chosen key."""
+    P = small_problem(n=160, m=m, mv=6, kind="matern32", nugget=nugget, seed=7)
+    th = P.theta
+    N, keys, _ = O.causal_neighbors(P.X, P.Z, th, 6, return_keys=True)
+    rho = O.residual_neighbor_corr(P.X, P.Z, th, N)
+    R = O.cov(P.X, P.X, th) + O.residual_diag(th) * np.eye(160)
+    if m:
+        Snm = O.cov(P.X, P.Z, th)
+        R = R - Snm @ np.linalg.solve(O.sigma_m(P.Z, th), Snm.T)
+    C = np.abs(R / np.sqrt(np.outer(np.diag(R), np.diag(R))))
+    assert np.all(rho[0] == 0.0)
+    for i in range(1, 160):
+        nb = N[i][N[i] >= 0]
+        np.testing.assert_allclose(rho[i], [C[i, nb].max(), C[i, nb].mean()], rtol=1e-10, atol=1e-13)
+        assert 0.0 <= rho[i, 1] <= rho[i, 0] <= 1.0
+        if nugget == 0.0:
+            # the residual diagonal then carries only the jitter, which moves rho by at
+            # most about jitter / (smallest residual variance involved)
+            kk = keys[i - 1]
+            tol = 4.0 * O.residual_diag(th) / np.diag(R)[np.r_[i, nb]].min() + 1e-13
+            assert abs(rho[i, 0] - (1.0 - kk[nb].min())) <= tol
+            assert abs(rho[i, 1] - (1.0 - kk[nb]).mean()) <= tol
+    if m == 0:                 # no inducing points: rho is the correlation function itself
+        i = 100
+        nb = N[i][N[i] >= 0]
+        r = O.dist(O.scaled(P.X[i:i + 1], th), O.scaled(P.X[nb], th))[0]
+        corr = O.cov_of_r(r, th.kind, 1.0) / (1.0 + O.residual_diag(th) / th.variance)
+        np.testing.assert_allclose(rho[i], [corr.max(), corr.mean()], rtol=1e-12)
+
+
 @pytest.mark.parametrize("m,kind,d", [(20, "matern32", 2), (0, "matern32", 2), (12, "se", 3)])
 def test_sampled_neighbor_search_equals_the_full_brute_force(m, kind, d):
     """The streaming form used at full size (chunks of predecessors, low-rank terms of the
@@ -675,7 +710,7 @@ def test_mlp_forward_closed_form_special_case():
     W1[0, 0] = 1.0
     W2[...] = np.eye(M.NH)
     w3[0] = 2.0
-    F = np.array([[0.3, 5, 5, 5, 5, 5, 5, 5], [-1.2, 0, 0, 0, 0, 0, 0, 0]])
+    F = np.array([[0.3] + [5.0] * (M.NIN - 1), [-1.2] + [0.0] * (M.NIN - 1)])
     o = 2.0 * np.tanh(np.tanh(F[:, 0]))
     np.testing.assert_allclose(M.forward(p, F), 4.0 * np.tanh(o / 4.0), rtol=1e-14)
     assert np.all(M.forward(M.init_params(3), F) == 0.0)     # zero output layer: plain VIFDU
