@@ -23,6 +23,8 @@ dense solves, sparse products, sorting) as the only building blocks:
 * the FITC preconditioner (Sec. 4.3, App. E.2) with the system form of Eq. pcls2 and
   the SLQ form of Eq. slq_v2;
 * VIF-Laplace predictive distributions (Prop. 3.1) and their variances by Alg. 1 (SBPV);
+* the analytic gradient of the Gaussian VIF likelihood (Sec. 2.2 trace formula, App. A
+  derivatives of B and D), pinned against central differences and the exact GP;
 * the VIF-Laplace gradient by stochastic trace estimation with the preconditioner control
   variate (Sec. 4.1, App. B, App. D), in the VIFDU (Eq. pcls1) and the FITC (Eq. pcls2) form.
 
@@ -37,6 +39,8 @@ Readings of points the paper leaves open (all shared with the CUDA path):
   R9 prediction points condition on training points only (B_p = I); their
      neighbours are the m_v nearest training points by d_c (non-causal).
   R10 Newton from b=0; PCG from x=0 stops at ||v - A x||_2/||v||_2 <= tol.
+  R17 App. A's derivative of D_i is read as the product rule of D_i = c~_ii - A_i c_Ni: its
+      printed term in dA_i multiplies the cross covariance c_Ni (the printed c_ii is garbled).
   R16 derivatives in theta of Sigma_dagger^{-1}, log det Sigma_dagger, log det P^ and B^T W B are
       central differences (relative step 1e-4) with N, Z, W and the mode fixed; the control
       variate is applied to the theta traces, the traces for dL/db use the plain estimate.
@@ -1269,3 +1273,88 @@ def exact_gp_grad(X, y, theta) -> np.ndarray:
                 mats.append(np.where(r > 0, -dK * dk2 / r, 0.0))
     mats.append(np.eye(len(y)))
     return np.array([0.5 * np.sum(Sinv * M) - 0.5 * alpha @ M @ alpha for M in mats])
+
+
+
+def dcov(X1, X2, theta) -> list:
+    """Derivatives of the cross covariance cov(X1, X2) (no nugget) with respect to
+    (sigma1^2, lambda_1..lambda_k, sigma^2), in the order of theta_vector."""
+    ls = np.atleast_1d(theta.lengthscale)
+    r = dist(scaled(X1, theta), scaled(X2, theta))
+    K = cov_of_r(r, theta.kind, theta.variance)
+    dK = dcov_of_r(r, theta.kind, theta.variance)
+    mats = [K / theta.variance]
+    with np.errstate(divide="ignore", invalid="ignore"):
+        if ls.size == 1:
+            mats.append(np.where(r > 0, -dK * r / ls[0], 0.0))     # dr/dlambda = -r / lambda
+        else:
+            for t in range(ls.size):
+                dk2 = (X1[:, None, t] - X2[None, :, t]) ** 2 / ls[t] ** 3
+                mats.append(np.where(r > 0, -dK * dk2 / r, 0.0))
+    mats.append(np.zeros_like(K))
+    return mats
+
+
+def vif_nll_grad(X, Z, theta, N, y) -> np.ndarray:
+    """Analytic gradient of the VIF NLL in (sigma1^2, lambda_1..lambda_k, sigma^2) with N and Z
+    fixed, as Sec. 2.2 writes it: 1/2 Tr(Sigma~_dagger^{-1} dSigma~_dagger) - 1/2 alpha^T
+    dSigma~_dagger alpha (alpha = Sigma~_dagger^{-1} y), dSigma~_dagger = dSigma~^s + dSigma^l with
+      dSigma^l = dSigma_mn^T Sigma_m^{-1} Sigma_mn + Sigma_mn^T Sigma_m^{-1} dSigma_mn
+                 - Sigma_mn^T Sigma_m^{-1} dSigma_m Sigma_m^{-1} Sigma_mn,
+      dSigma~^s = B^{-1} dD B^{-T} - B^{-1} dB B^{-1} D B^{-T} - B^{-1} D B^{-T} dB^T B^{-T},
+    and dB, dD per point from App. A (D_i = c~_ii - A_i c_Ni differentiated by the product
+    rule, reading R17).  Sigma_m carries the R7 jitter eps sigma1^2 (derivative Sigma_m /
+    sigma1^2 in sigma1^2); the residual blocks' diagonal carries the nugget.  Dense n x n
+    algebra: small n only."""
+    n, mv = N.shape
+    m = Z.shape[0]
+    vif = VIF(X, Z, theta, N)
+    q_par = theta_vector(theta).size
+    Kx = dcov(X, X, theta)
+    tdiag = residual_diag(theta)
+    dtdiag = np.zeros(q_par)
+    if theta.nugget > 0:
+        dtdiag[-1] = 1.0
+    else:
+        dtdiag[0] = tdiag / theta.variance
+    if m:
+        Smn = vif.lowrank.Smn
+        W = vif.lowrank.SinvSmn                                   # Sigma_m^{-1} Sigma_mn
+        dSmn = dcov(Z, X, theta)
+        dSm = dcov(Z, Z, theta)
+        dSm[0] = sigma_m(Z, theta) / theta.variance               # jitter scales with sigma1^2
+        dLR = [dSmn[k].T @ W + W.T @ dSmn[k] - W.T @ dSm[k] @ W for k in range(q_par)]
+        LR = Smn.T @ W
+    else:
+        dLR = [np.zeros((n, n)) for _ in range(q_par)]
+        LR = np.zeros((n, n))
+    S_full = cov(X, X, theta)
+    Binv = np.linalg.inv(vif.B.toarray())
+    Ss = Binv @ np.diag(vif.D) @ Binv.T
+    Sdag = vif.dense_Sigma_dagger()
+    cf = sla.cho_factor(Sdag, lower=True)
+    Sdinv = sla.cho_solve(cf, np.eye(n))
+    alpha = Sdinv @ y
+    g = np.empty(q_par)
+    for k in range(q_par):
+        dB = np.zeros((n, n))
+        dD = np.zeros(n)
+        for i in range(n):
+            Ni = N[i][N[i] >= 0]
+            c_ii = theta.variance + tdiag - LR[i, i]
+            dc_ii = Kx[k][i, i] + dtdiag[k] - dLR[k][i, i]
+            if len(Ni) == 0:
+                dD[i] = dc_ii
+                continue
+            Mat = S_full[np.ix_(Ni, Ni)] + tdiag * np.eye(len(Ni)) - LR[np.ix_(Ni, Ni)]
+            dMat = Kx[k][np.ix_(Ni, Ni)] + dtdiag[k] * np.eye(len(Ni)) - dLR[k][np.ix_(Ni, Ni)]
+            c_iN = S_full[i, Ni] - LR[i, Ni]
+            dc_iN = Kx[k][i, Ni] - dLR[k][i, Ni]
+            Ai = np.linalg.solve(Mat, c_iN)
+            dAi = np.linalg.solve(Mat, dc_iN - dMat @ Ai)
+            dB[i, Ni] = -dAi
+            dD[i] = dc_ii - dAi @ c_iN - Ai @ dc_iN
+        dSs = Binv @ np.diag(dD) @ Binv.T - Binv @ dB @ Ss - Ss @ dB.T @ Binv.T
+        dS = dSs + dLR[k]
+        g[k] = 0.5 * np.sum(Sdinv * dS) - 0.5 * alpha @ dS @ alpha
+    return g

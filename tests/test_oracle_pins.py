@@ -686,6 +686,40 @@ def test_fd_gradient_with_full_conditioning_is_the_exact_gp_gradient():
     np.testing.assert_allclose(g_fd, g_ex, rtol=1e-6, atol=1e-6)
 
 
+@pytest.mark.parametrize("m,mv,kind,ls,step,tol", [
+    (20, 8, "matern32", 0.2, 1e-4, 1e-6),
+    (0, 5, "matern52", 0.3, 1e-4, 1e-6),
+    (12, 0, "matern12", 0.2, 1e-4, 1e-6),
+    (15, 6, "se", np.array([0.3, 0.6]), 3e-4, 2e-6)])
+def test_analytic_gradient_matches_central_differences_of_the_likelihood(m, mv, kind, ls, step, tol):
+    """The Sec. 2.2 / App. A gradient against central differences of the oracle's own NLL
+    (a different route: no derivative algebra).  The SE case is ill-conditioned (Sigma_m
+    jitter 1e-8), so its differences take a larger step to stay above rounding."""
+    P = small_problem(n=220, d=2, m=m, mv=mv, kind=kind, ls=ls, nugget=0.1, seed=3)
+    N = O.causal_neighbors(P.X, P.Z, P.theta, mv) if mv else -np.ones((220, 0), dtype=np.int64)
+    g = O.vif_nll_grad(P.X, P.Z, P.theta, N, P.y)
+    g_fd = O.vif_nll_grad_fd(P.X, P.Z, P.theta, N, P.y, rel_step=step)
+    np.testing.assert_allclose(g, g_fd, rtol=0, atol=tol * np.abs(g_fd).max())
+
+
+def test_analytic_gradient_with_full_conditioning_is_the_exact_gp_gradient():
+    P = small_problem(n=60, m=8, mv=59, nugget=0.1, kind="matern32", ls=0.2)
+    N = O.causal_neighbors(P.X, P.Z, P.theta, 59)
+    np.testing.assert_allclose(O.vif_nll_grad(P.X, P.Z, P.theta, N, P.y),
+                               O.exact_gp_grad(P.X, P.y, P.theta), rtol=1e-9, atol=1e-10)
+
+
+def test_analytic_gradient_of_the_independent_model_is_closed_form():
+    """m = 0 and m_v = 0: Sigma~_dagger = (sigma1^2 + sigma^2) I, so the NLL is
+    n/2 log(2 pi s) + |y|^2 / (2 s) with s = sigma1^2 + sigma^2, and the length scale has no
+    effect."""
+    P = small_problem(n=50, m=0, mv=0, nugget=0.3, kind="matern32", ls=0.2)
+    N = -np.ones((50, 0), dtype=np.int64)
+    s2 = P.theta.variance + P.theta.nugget
+    ds = 0.5 * 50 / s2 - 0.5 * (P.y @ P.y) / s2 ** 2
+    np.testing.assert_allclose(O.vif_nll_grad(P.X, P.Z, P.theta, N, P.y), [ds, 0.0, ds], rtol=1e-12, atol=1e-12)
+
+
 def test_exact_gp_gradient_ard_matches_its_own_finite_differences():
     P = small_problem(n=40, m=0, mv=0, nugget=0.05, kind="se", ls=np.array([0.2, 0.4]))
     g = O.exact_gp_grad(P.X, P.y, P.theta)
