@@ -101,10 +101,12 @@ vif_status vif_build(const double *X, int64_t n, int32_t d, const double *Z, int
  * with log det via Sylvester (det M det Sigma_m^{-1} det D) and the solve via
  * Woodbury (M of Eq. def_M), for the hyperparameters `theta` and the fixed
  * neighbour sets of the context.  y: n responses.  nll_out: HOST double.
- * grad_out: NULL, or a HOST array of n_ls + 2 doubles that receives the gradient of
- * the likelihood (Sec. 2.2) with respect to (sigma1^2, lambda_1..lambda_{n_ls}, sigma^2),
- * with N and Z held fixed, as central differences of the float64 likelihood with
- * relative steps of 1e-4 (2 (n_ls + 2) extra float64 evaluations; needs nugget > 0). */
+ * grad_out: NULL, or a HOST array of n_ls + 2 doubles that receives the analytic gradient
+ * of the likelihood (Sec. 2.2 with the derivatives of B and D of App. A) with respect to
+ * (sigma1^2, lambda_1..lambda_{n_ls}, sigma^2), with N and Z held fixed, in float64 (a
+ * mixed-precision context evaluates it from a float64 pass; its nll_out stays the mixed
+ * likelihood).  It is formed in reverse mode, at the cost of about one more likelihood
+ * evaluation whatever n_ls; needs nugget > 0, m_v <= 64 and n_ls <= 16. */
 vif_status vif_nll(vif_ctx *ctx, const vif_cov *theta, const double *y, double *nll_out,
                    double *grad_out);
 

@@ -10,7 +10,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 OBJ = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libvif.so")
-SOURCES = ["vif_dense.cu", "vif_lowrank.cu", "vif_factor.cu", "vif_knn.cu", "vif_api.cu", "vif_noalloc.cu", "vif_predict.cu", "vif_laplace.cu", "vif_mlp.cu", "vif_lowrank_tc.cu", "vif_gram_tc.cu", "vif_factor_tc.cu"]
+SOURCES = ["vif_dense.cu", "vif_lowrank.cu", "vif_factor.cu", "vif_knn.cu", "vif_api.cu", "vif_noalloc.cu", "vif_predict.cu", "vif_laplace.cu", "vif_mlp.cu", "vif_lowrank_tc.cu", "vif_gram_tc.cu", "vif_factor_tc.cu", "vif_grad.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "--expt-relaxed-constexpr"]
 

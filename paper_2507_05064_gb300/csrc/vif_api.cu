@@ -90,6 +90,7 @@ struct vif_ctx {
   int *l_counter = nullptr, *l_abort = nullptr;
   float *m_feat = nullptr, *m_gc = nullptr, *m_part = nullptr, *m_grad = nullptr;
   float* m_rho = nullptr;   // latent-GP contexts: max and mean |residual correlation| per point
+  double *gr_buf = nullptr, *gr_LinvC = nullptr, *gr_out = nullptr;   // analytic gradient scratch
   int64_t knn_rescored = 0, knn_fallback = 0;
   bool have_factors = false;
   bool timing = false;
@@ -359,7 +360,7 @@ void free_ctx(vif_ctx* c) {
                    c->ch_slot, c->l_b,  c->l_W,    c->l_v,    c->l_Ginv, c->l_om,   c->l_rsD,  c->l_ll,
                    c->l_x,    c->l_r,   c->l_z,    c->l_p,    c->l_Ap,   c->l_t,    c->l_t2,   c->l_x1,
                    c->l_sdi,  c->l_sm,  c->l_cm,   c->l_tm,   c->l_part, c->l_LinvC, c->l_G3,  c->l_LinvC3,
-                   c->l_sc,   c->l_red, c->l_corr, c->sched_fwd, c->sched_rev, c->ord_fwd, c->ord_rev, c->ch_coef, c->slq_eps, c->l_Apad, c->l_anorm2, c->l_dvinv, c->l_pacc, c->l_counter, c->l_abort, c->m_feat, c->m_rho,
+                   c->l_sc,   c->l_red, c->l_corr, c->sched_fwd, c->sched_rev, c->ord_fwd, c->ord_rev, c->ch_coef, c->slq_eps, c->l_Apad, c->l_anorm2, c->l_dvinv, c->l_pacc, c->l_counter, c->l_abort, c->m_feat, c->m_rho, c->gr_buf, c->gr_LinvC, c->gr_out,
                    c->g_U,    c->g_Y,   c->g_g,    c->g_v,    c->g_sc,   c->g_red,  c->g_a,    c->g_av,
                    c->g_dv,
                    c->mr_v,   c->mr_x,  c->mr_r,   c->mr_z,   c->mr_p,   c->mr_Ap,  c->mr_t,   c->mr_t2,
@@ -988,28 +989,49 @@ vif_status vif_nll(vif_ctx* ctx, const vif_cov* theta, const double* y, double* 
   CK(cudaMemsetAsync(ctx->status, 0, 4 * sizeof(int), ctx->stream));
   CKS(upload(ctx, ctx->y, y, (size_t)ctx->n * sizeof(double)));
   if (grad_out) {
-    // central differences of the float64 likelihood, one parameter at a time
+    // the analytic gradient (vif_grad.cu) from a float64 evaluation
     double *A64 = nullptr, *F64 = nullptr, *LT64 = nullptr;
     CKS(fp64_buffers(ctx, &A64, &F64, &LT64));
+    CKS(apply_scaling(ctx, theta, false));
+    CKS(run_pipeline<double>(ctx, cp, A64, LT64, F64, ctx->Xs, ctx->Zs));
+    double sc64[1];
+    CKS(read_status(ctx, sc64, 1));
     const int q = theta->n_ls + 2;
-    std::vector<double> ls(theta->lengthscale, theta->lengthscale + theta->n_ls);
-    for (int k = 0; k < q; ++k) {
-      double f[2];
-      for (int sgn = 0; sgn < 2; ++sgn) {
-        vif_cov tk = *theta;
-        std::vector<double> lk = ls;
-        tk.lengthscale = lk.data();
-        double* par = (k == 0) ? &tk.variance : (k == q - 1 ? &tk.nugget : &lk[k - 1]);
-        const double h = 1e-4 * std::fabs(*par);
-        *par += sgn ? -h : h;
-        CovParams ck = cov_params(&tk);
-        CKS(apply_scaling(ctx, &tk, false));
-        CKS(run_pipeline<double>(ctx, ck, A64, LT64, F64, ctx->Xs, ctx->Zs));
-        double sc[1];
-        CKS(read_status(ctx, sc, 1));
-        f[sgn] = sc[0];
-        if (sgn == 1) grad_out[k] = (f[0] - f[1]) / (2.0 * h);
-      }
+    if (!ctx->gr_buf) {
+      CKS(dalloc(ctx, &ctx->gr_buf, grad_scratch_doubles(ctx->n, ctx->m, ctx->mv, 18)));
+      CKS(dalloc(ctx, &ctx->gr_LinvC, (size_t)ctx->fpad * ctx->fpad));
+      CKS(dalloc(ctx, &ctx->gr_out, 64));
+    }
+    std::vector<double> hls(theta->lengthscale, theta->lengthscale + theta->n_ls);
+    GradInputs in{};
+    in.A = A64;
+    in.F = F64;
+    in.Xs = ctx->Xs;
+    in.Zs = ctx->Zs;
+    in.Acoef = ctx->Acoef;
+    in.Dv = ctx->Dv;
+    in.y = ctx->y;
+    in.G = ctx->G;
+    in.Linv = ctx->Linv;
+    in.ls = hls.data();
+    in.N = ctx->N;
+    in.n = ctx->n;
+    in.d = ctx->d;
+    in.m = ctx->m;
+    in.mpad = ctx->mpad;
+    in.fpad = ctx->fpad;
+    in.mv = ctx->mv;
+    in.ldl = ctx->ldm;
+    in.nls = theta->n_ls;
+    in.cp = cp;
+    CK(vif_grad_fp64(in, ctx->gr_buf, ctx->gr_LinvC, ctx->trw, ctx->gr_out, ctx->stream));
+    double g3[3 * 18];
+    CKS(download(ctx, g3, ctx->gr_out, sizeof(double) * 3 * q));
+    for (int k = 0; k < q; ++k) grad_out[k] = g3[k] + g3[q + k] + g3[2 * q + k];
+    if (!mixed) {   // the float64 evaluation above is the likelihood
+      ctx->have_factors = true;
+      *nll_out = sc64[0];
+      return VIF_OK;
     }
     CK(cudaMemsetAsync(ctx->status, 0, 4 * sizeof(int), ctx->stream));
   }

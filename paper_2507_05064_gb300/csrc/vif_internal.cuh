@@ -146,6 +146,22 @@ cudaError_t dense_batch_init(const std::vector<DenseJob>& jobs, bool trtri, Dens
 cudaError_t dense_batch_run(const DenseBatch& b, cudaStream_t s);
 void dense_batch_free(DenseBatch* b);
 
+// vif_grad.cu: analytic gradient of the Gaussian likelihood (float64) from the buffers a
+// float64 evaluation leaves: A (whitened rows, n x mpad), [F z] (n x fpad), A_i (n x mv),
+// D_i, the augmented capacitance factor G (lda fpad), L_m^{-1} (ldl), scaled coordinates.
+struct GradInputs {
+  const double *A, *F, *Xs, *Zs, *Acoef, *Dv, *y, *G, *Linv, *ls;
+  const int32_t* N;
+  int64_t n;
+  int d, m, mpad, fpad, mv, ldl, nls;
+  CovParams cp;
+};
+size_t grad_scratch_doubles(int64_t n, int m, int mv, int q);
+// grad_dev receives 3 q doubles (direct, cross and inducing-point sums; the gradient is their
+// sum); LinvC: fpad x fpad doubles; trw: trtri_work_doubles(m) doubles.
+cudaError_t vif_grad_fp64(const GradInputs& in, double* scratch, double* LinvC, double* trw, double* grad_dev,
+                          cudaStream_t s);
+
 // vif_lowrank_tc.cu: A = K_nm L_m^{-T} on the tensor cores for the float32 path.  init
 // (once per device, outside stream capture) raises the kernel's shared-memory limit;
 // pack holds lowrank_A_tc_pack_floats(mpad) floats; mpad = 32 ceil(m / 32).

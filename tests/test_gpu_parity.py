@@ -593,22 +593,50 @@ def test_laplace_rejects_a_nugget():
 
 # --------------------------------------------------------------------------- gradient (Sec. 2.2)
 def test_c1_gradient_matches_oracle(c1):
+    """The reverse-mode gradient against the oracle's Sec. 2.2 / App. A form (float64 on both
+    sides; a mixed context forms it from a float64 pass) and against central differences."""
     P, Nor, keys, vif = c1
-    g_or = O.vif_nll_grad_fd(P.X, P.Z, P.theta, Nor, P.y)
+    g_or = O.vif_nll_grad(P.X, P.Z, P.theta, Nor, P.y)
+    g_fd = O.vif_nll_grad_fd(P.X, P.Z, P.theta, Nor, P.y)
+    np.testing.assert_allclose(g_fd, g_or, rtol=1e-6, atol=1e-6 * np.abs(g_or).max())
     for prec in (V.FP64, V.MIXED):
         ctx = V.Context(P.X, P.Z, P.mv, P.theta, precision=prec, neighbor_search=False)
         ctx.set_neighbors(Nor.astype(np.int32))
         nll, g = ctx.nll(P.theta, P.y, grad=True)
-        np.testing.assert_allclose(g, g_or, rtol=1e-6, atol=1e-6 * np.abs(g_or).max())
+        np.testing.assert_allclose(g, g_or, rtol=1e-8, atol=1e-9 * np.abs(g_or).max())
         assert nll_close(nll, vif.nll(P.y), 2000, RTOL64 if prec == V.FP64 else RTOL_MIXED)
+        nll2 = ctx.nll(P.theta, P.y)
+        assert nll2 == nll
         ctx.close()
+
+
+@pytest.mark.parametrize("m,mv,kind,ls,d", [
+    (30, 12, "matern52", 0.15, 2),
+    (25, 8, "se", [0.3, 0.7, 1.2], 3),
+    (0, 9, "matern32", 0.2, 2),
+    (20, 0, "matern12", 0.2, 2),
+    (40, 36, "matern32", 0.1, 2)])
+def test_gradient_matches_oracle_across_structures(m, mv, kind, ls, d):
+    """ARD length scales, no inducing points (classical Vecchia), no neighbours (FITC) and
+    more than 32 neighbours, all kernel families."""
+    P = prob(700, d, m, mv, kind, 0.08, np.array(ls) if np.ndim(ls) else ls, 60 + mv)
+    Nor = O.causal_neighbors(P.X, P.Z, P.theta, mv) if mv else -np.ones((700, 0), dtype=np.int64)
+    g_or = O.vif_nll_grad(P.X, P.Z, P.theta, Nor, P.y)
+    ctx = V.Context(P.X, P.Z, mv, P.theta, precision=V.FP64, neighbor_search=False)
+    if mv:
+        ctx.set_neighbors(Nor.astype(np.int32))
+    nll, g = ctx.nll(P.theta, P.y, grad=True)
+    ctx.close()
+    assert g.shape == g_or.shape
+    np.testing.assert_allclose(g, g_or, rtol=1e-7, atol=1e-8 * np.abs(g_or).max())
+    assert nll == pytest.approx(O.vif_nll(P.X, P.Z, P.theta, Nor, P.y), rel=RTOL64)
 
 
 def test_gradient_with_full_conditioning_is_the_exact_gp_gradient():
     P = synth.make_problem(45, 2, 8, 45, "matern32", 1.0, 0.2, 0.1, 41, lloyd=3)
     ctx = V.Context(P.X, P.Z, 45, P.theta)
     _, g = ctx.nll(P.theta, P.y, grad=True)
-    np.testing.assert_allclose(g, O.exact_gp_grad(P.X, P.y, P.theta), rtol=1e-6, atol=1e-6)
+    np.testing.assert_allclose(g, O.exact_gp_grad(P.X, P.y, P.theta), rtol=1e-8, atol=1e-8)
     ctx.close()
 
 
