@@ -605,8 +605,10 @@ def test_c1_gradient_matches_oracle(c1):
         nll, g = ctx.nll(P.theta, P.y, grad=True)
         np.testing.assert_allclose(g, g_or, rtol=1e-8, atol=1e-9 * np.abs(g_or).max())
         assert nll_close(nll, vif.nll(P.y), 2000, RTOL64 if prec == V.FP64 else RTOL_MIXED)
+        # the same likelihood without the gradient (float64 atomics in the triangular inverse
+        # and the mixed path's autotuned factor stage may move the last bits)
         nll2 = ctx.nll(P.theta, P.y)
-        assert nll2 == nll
+        assert nll2 == pytest.approx(nll, rel=1e-12 if prec == V.FP64 else RTOL_MIXED)
         ctx.close()
 
 
