@@ -153,6 +153,22 @@ def stage_algorithmic(P, stage):
     return 0.0, 0.0
 
 
+# DRAM bytes per point of the CUDA-core factor kernel (factor_kernel<float, 3>) from one ncu
+# capture of this source at n = 100,000 (378.5 MB read + 203.4 MB written per launch); reported,
+# scaled by n, only while the kernel's source file still has this digest
+FACTOR_TRAFFIC = {"bytes_per_point": 5819.1, "source_sha256": "569efd6857046bab7bcd376c8a103318b545eb8cbcb423d89f0b9dd25207c19e"}
+
+
+def factor_traffic(n):
+    import hashlib
+    try:
+        with open(os.path.join(ROOT, "paper_2507_05064_gb300", "csrc", "vif_factor.cu"), "rb") as f:
+            digest = hashlib.sha256(f.read()).hexdigest()
+    except OSError:
+        return None
+    return FACTOR_TRAFFIC["bytes_per_point"] * n if digest == FACTOR_TRAFFIC["source_sha256"] else None
+
+
 def roofline_block(P, med, ms_step, pk, factor_path=1):
     """Roofline of the dense contractions (tensor-core bound) and of HBM, per stage and for the
     whole evaluation.  Each contraction is held to the tensor peak of the type it runs in:
@@ -184,8 +200,9 @@ def roofline_block(P, med, ms_step, pk, factor_path=1):
     roof_ms = max(t_tensor, tot_b / (hbm * 1e9)) * 1e3
     dom = max(stages, key=lambda k: stages[k]["ms"])
     d = stages[dom]
+    traffic = factor_traffic(P.X.shape[0]) if (dom == "vecchia_factor" and factor_path == 1) else None
     return {"kernel": dom, "bound": "tensor", "achieved": d["tflops"], "peak": d["peak_tflops"], "unit": "TFLOP/s",
-            "frac": d["frac_tensor"], "traffic": None,
+            "frac": d["frac_tensor"], "traffic": traffic,
             "peak_source": (f"{d['tensor_dtype']}: {src} dense bf16 burst peak {bf16} TFLOP/s"
                             + (" x 1/2 (nominal tf32 : bf16)" if d["tensor_dtype"] == "tf32" else "")),
             "hbm_achieved_gbs": d["gbs"], "hbm_peak_gbs": hbm, "frac_hbm": d["frac_hbm"],
