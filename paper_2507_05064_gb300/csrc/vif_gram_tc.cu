@@ -2,11 +2,12 @@
 // response column appended) on the fifth-generation tensor cores, for the float32 path.
 //
 // Split-K SYRK over 128 x 128 tile pairs (ti >= tj) of the fpad columns: CTA (pair,
-// slice) sums rows r0..r1 of F, 32 rows per chunk.  Warp specialisation: 8 compute
-// warps bring the rows of chunk c+1 into a raw shared-memory buffer with cp.async, split
-// every value of chunk c into tf32 hi + lo (round to nearest) and write them transposed
-// into K-major 128-byte-swizzled tiles (row = column of F, K = row of F), then read out
-// the previous chunk's accumulator; one more warp issues the chunk's 16 MMAs
+// slice) sums rows r0..r1 of F, 32 rows per chunk.  Warp specialisation: 8 staging warps
+// bring the rows of chunk c+1 into a raw shared-memory buffer with cp.async, split every
+// value of chunk c into tf32 hi + lo (round to nearest) and write them transposed into
+// K-major 128-byte-swizzled tiles (row = column of F, K = row of F); 8 read-out warps (two
+// per TMEM lane quarter) add each finished accumulator into the running sums while the
+// staging warps prepare the next chunk; one more warp issues the chunk's 16 MMAs
 //   Alo Blo + Alo Bhi + Ahi Blo + Ahi Bhi
 // into one of two TMEM accumulators as soon as the tiles are staged.  The tensor core's
 // float32 accumulation rounds toward zero at every step and C is ill-conditioned (its
@@ -26,8 +27,10 @@ namespace {
 
 constexpr int GC_T = 128;                       // tile edge (F columns per block)
 constexpr int GC_K = 32;                        // rows of F per chunk
-constexpr int GC_CW = 8;                        // compute warps
+constexpr int GC_CW = 16;                       // compute warps: 8 read-out, then 8 staging
 constexpr int GC_NC = GC_CW * 32;               // compute threads
+constexpr int GC_NS = 256;                      // staging threads (warps 8..15)
+constexpr int GC_ND = 256;                      // read-out threads (warps 0..7)
 constexpr int GC_THREADS = GC_NC + 32;          // + the MMA warp
 constexpr uint32_t GC_TILE = GC_T * 128;        // bytes of one swizzled operand tile
 constexpr uint32_t GC_STAGE = 4 * GC_TILE;      // Ahi, Alo, Bhi, Blo
@@ -37,8 +40,9 @@ constexpr uint32_t GC_TMEM_COLS = 4 * GC_T;     // accumulators 0, 1; running su
 constexpr int GT64 = 64;                        // sub-tile edge of the partial layout
 
 struct __align__(16) GcBars {
-  uint64_t staged[2];   // tiles of the stage written (one arrival per compute thread)
+  uint64_t staged[2];   // tiles of the stage written (one arrival per staging thread)
   uint64_t done[2];     // MMAs of the stage's chunk finished (stage and accumulator free)
+  uint64_t drained[2];  // accumulator read out (one arrival per read-out thread)
   uint64_t fin;         // every MMA of the CTA finished
   uint32_t tmem;
   int abort;            // the MMA warp gave up waiting
@@ -76,8 +80,9 @@ __global__ __launch_bounds__(GC_THREADS, 1) void gram_tc_kernel(const float* __r
   if (warp == 0) tc::tmem_alloc(&sb.tmem, GC_TMEM_COLS);
   if (tid == 0) {
     for (int s = 0; s < 2; ++s) {
-      tc::mbar_init(&sb.staged[s], GC_NC);
+      tc::mbar_init(&sb.staged[s], GC_NS);
       tc::mbar_init(&sb.done[s], 1);
+      tc::mbar_init(&sb.drained[s], GC_ND);
     }
     tc::mbar_init(&sb.fin, 1);
     sb.abort = 0;
@@ -94,7 +99,9 @@ __global__ __launch_bounds__(GC_THREADS, 1) void gram_tc_kernel(const float* __r
     if (lane == 0) {
       for (int c = 0; c < nchunk; ++c) {
         const int s = c & 1;
-        if (!tc::mbar_wait(&sb.staged[s], (c >> 1) & 1)) {
+        // the chunk's tiles are staged, and accumulator s was read out after chunk c-2
+        if (!tc::mbar_wait(&sb.staged[s], (c >> 1) & 1) ||
+            (c >= 2 && !tc::mbar_wait(&sb.drained[s], ((c - 2) >> 1) & 1))) {
           failed = true;
           sb.abort = 1;
           break;
@@ -122,14 +129,17 @@ __global__ __launch_bounds__(GC_THREADS, 1) void gram_tc_kernel(const float* __r
       tc::mma_commit(&sb.fin);
     }
     __syncwarp();
-  } else {
-    // ------------------------------------------------ compute warps
+  } else if (warp >= GC_CW / 2) {
+    // ------------------------------------------------ staging warps
+    const int stid = tid - GC_ND;
+    // column (stid & 127) of both blocks, rows (stid >> 7) * 16 .. + 15 of the chunk
+    const int scol = stid & (GC_T - 1), srow0 = (stid >> 7) * 16;
     // raw rows of chunk c into raw buffer c % 2: 16-byte segments, zeros past r1 / fpad
     auto fetch = [&](int c) {
       if (c < nchunk) {
         float* dst = raw + (size_t)(c & 1) * (2 * GC_K * GC_T);
         const int64_t rb = r0 + (int64_t)c * GC_K;
-        for (int e = tid; e < nblk * GC_K * (GC_T / 4); e += GC_NC) {
+        for (int e = stid; e < nblk * GC_K * (GC_T / 4); e += GC_NS) {
           const int blk = e / (GC_K * (GC_T / 4));
           const int rr = (e / (GC_T / 4)) % GC_K, seg = e % (GC_T / 4);
           const int col = (blk == 0 ? ti : tj) * GC_T + seg * 4;
@@ -141,49 +151,6 @@ __global__ __launch_bounds__(GC_THREADS, 1) void gram_tc_kernel(const float* __r
       }
       asm volatile("cp.async.commit_group;\n" ::: "memory");
     };
-    // staging: thread -> column (tid & 127) of the block, rows (tid >> 7) * 16 .. + 15
-    const int scol = tid & (GC_T - 1), srow0 = (tid >> 7) * 16;
-    // read-out: warp -> TMEM lanes 32 (warp % 4) .., columns 64 (warp / 4) .. + 63
-    const int dlane = 32 * (warp & 3), dcol = 64 * (warp >> 2);
-    const uint32_t lane_base = tmem + ((uint32_t)dlane << 16);
-    // add the partial of chunk j (accumulator j % 2) into the TMEM running sums
-    auto drain = [&](int j) {
-      // warp-uniform outcome: the TMEM loads below are warp-collective
-      if (!__all_sync(0xffffffffu, tc::mbar_wait(&sb.done[j & 1], (j >> 1) & 1))) {
-        failed = true;
-        return;
-      }
-      tc::fence_after_sync();
-#pragma unroll
-      for (int g = 0; g < 2; ++g) {
-        const uint32_t col = (uint32_t)(dcol + g * 32);
-        float v[32], hi[32], lo[32];
-        tc::tmem_ld32(lane_base + (uint32_t)((j & 1) * GC_T) + col, v);
-        if (j == 0) {
-#pragma unroll
-          for (int i = 0; i < 32; ++i) {
-            hi[i] = v[i];
-            lo[i] = 0.f;
-          }
-        } else {
-          tc::tmem_ld32(lane_base + 2 * GC_T + col, hi);
-          tc::tmem_ld32(lane_base + 3 * GC_T + col, lo);
-#pragma unroll
-          for (int i = 0; i < 32; ++i) {
-            const float s2 = hi[i] + v[i];
-            const float bb = s2 - hi[i];
-            const float err = (hi[i] - (s2 - bb)) + (v[i] - bb);
-            hi[i] = s2;
-            lo[i] += err;
-          }
-        }
-        tc::tmem_st32(lane_base + 2 * GC_T + col, hi);
-        tc::tmem_st32(lane_base + 3 * GC_T + col, lo);
-      }
-      tc::tmem_st_wait();
-      tc::fence_before_sync();
-    };
-
     fetch(0);
     for (int c = 0; c < nchunk; ++c) {
       const int s = c & 1;
@@ -193,9 +160,10 @@ __global__ __launch_bounds__(GC_THREADS, 1) void gram_tc_kernel(const float* __r
       unsigned char* b_hi = diag ? a_hi : st + 2 * GC_TILE;
       unsigned char* b_lo = diag ? a_lo : st + 3 * GC_TILE;
       asm volatile("cp.async.wait_group 0;\n" ::: "memory");   // raw rows of chunk c
-      // everyone's rows have landed and everyone is past chunk c-1's staging; stage s was
-      // last read by the MMAs of chunk c-2, read out at iteration c-1
-      if (tc::bar_sync_or(1, GC_NC, failed || sb.abort)) {
+      // stage s was last read by the MMAs of chunk c-2
+      if (c >= 2 && !failed && !tc::mbar_wait(&sb.done[s], ((c - 2) >> 1) & 1)) failed = true;
+      // everyone's rows of chunk c have landed and everyone is past chunk c-1's staging
+      if (tc::bar_sync_or(1, GC_NS, failed || sb.abort)) {
         failed = true;
         break;
       }
@@ -221,26 +189,66 @@ __global__ __launch_bounds__(GC_THREADS, 1) void gram_tc_kernel(const float* __r
       tc::fence_proxy_async();
       tc::fence_before_sync();
       tc::mbar_arrive(&sb.staged[s]);
-      if (c >= 1 && !failed) drain(c - 1);
     }
-    if (!failed && nchunk > 0) drain(nchunk - 1);
     asm volatile("cp.async.wait_group 0;\n" ::: "memory");
+  } else {
+    // ------------------------------------------------ read-out warps
+    // warp w: TMEM lanes 32 (w % 4) .. + 31, columns 64 (w / 4) .. + 63, in 16-column pieces
+    const int dlane = 32 * (warp & 3), dcol = 64 * (warp >> 2);
+    const uint32_t lane_base = tmem + ((uint32_t)dlane << 16);
+    for (int j = 0; j < nchunk; ++j) {
+      // warp-uniform outcome: the TMEM loads below are warp-collective
+      if (failed || !__all_sync(0xffffffffu, tc::mbar_wait(&sb.done[j & 1], (j >> 1) & 1))) {
+        failed = true;
+        break;
+      }
+      tc::fence_after_sync();
+#pragma unroll 1
+      for (int g = 0; g < 4; ++g) {
+        const uint32_t col = (uint32_t)(dcol + g * 16);
+        float v[16], hi[16], lo[16];
+        tc::tmem_ld16(lane_base + (uint32_t)((j & 1) * GC_T) + col, v);
+        if (j == 0) {
+#pragma unroll
+          for (int i = 0; i < 16; ++i) {
+            hi[i] = v[i];
+            lo[i] = 0.f;
+          }
+        } else {
+          tc::tmem_ld16(lane_base + 2 * GC_T + col, hi);
+          tc::tmem_ld16(lane_base + 3 * GC_T + col, lo);
+#pragma unroll
+          for (int i = 0; i < 16; ++i) {
+            const float s2 = hi[i] + v[i];
+            const float bb = s2 - hi[i];
+            const float err = (hi[i] - (s2 - bb)) + (v[i] - bb);
+            hi[i] = s2;
+            lo[i] += err;
+          }
+        }
+        tc::tmem_st16(lane_base + 2 * GC_T + col, hi);
+        tc::tmem_st16(lane_base + 3 * GC_T + col, lo);
+      }
+      tc::tmem_st_wait();
+      tc::fence_before_sync();
+      tc::mbar_arrive(&sb.drained[j & 1]);
+    }
     if (!failed) {
       const int np64 = (fpad / GT64) * (fpad / GT64 + 1) / 2;
       const int row = ti * GC_T + dlane + lane;
-#pragma unroll
-      for (int g = 0; g < 2; ++g) {
-        float hi[32], lo[32];
+#pragma unroll 1
+      for (int g = 0; g < 4; ++g) {
+        float hi[16], lo[16];
         if (nchunk > 0) {
-          tc::tmem_ld32(lane_base + 2 * GC_T + (uint32_t)(dcol + g * 32), hi);
-          tc::tmem_ld32(lane_base + 3 * GC_T + (uint32_t)(dcol + g * 32), lo);
+          tc::tmem_ld16(lane_base + 2 * GC_T + (uint32_t)(dcol + g * 16), hi);
+          tc::tmem_ld16(lane_base + 3 * GC_T + (uint32_t)(dcol + g * 16), lo);
         } else {
 #pragma unroll
-          for (int i = 0; i < 32; ++i) hi[i] = lo[i] = 0.f;
+          for (int i = 0; i < 16; ++i) hi[i] = lo[i] = 0.f;
         }
 #pragma unroll
-        for (int i = 0; i < 32; ++i) {
-          const int col = tj * GC_T + dcol + g * 32 + i;
+        for (int i = 0; i < 16; ++i) {
+          const int col = tj * GC_T + dcol + g * 16 + i;
           if (row >= fpad || col >= fpad || col > row) continue;
           const int a64 = row / GT64, b64 = col / GT64;
           const int p64 = a64 * (a64 + 1) / 2 + b64;
