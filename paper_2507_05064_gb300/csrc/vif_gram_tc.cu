@@ -207,16 +207,26 @@ __global__ __launch_bounds__(GC_THREADS, 1) void gram_tc_kernel(const float* __r
       for (int g = 0; g < 4; ++g) {
         const uint32_t col = (uint32_t)(dcol + g * 16);
         float v[16], hi[16], lo[16];
-        tc::tmem_ld16(lane_base + (uint32_t)((j & 1) * GC_T) + col, v);
+        // the partial and both running sums in flight together: one wait
         if (j == 0) {
+          tc::tmem_ld16(lane_base + (uint32_t)((j & 1) * GC_T) + col, v);
 #pragma unroll
           for (int i = 0; i < 16; ++i) {
             hi[i] = v[i];
             lo[i] = 0.f;
           }
         } else {
-          tc::tmem_ld16(lane_base + 2 * GC_T + col, hi);
-          tc::tmem_ld16(lane_base + 3 * GC_T + col, lo);
+          uint32_t rv[16], rh[16], rl[16];
+          tc::tmem_ld16_raw(lane_base + (uint32_t)((j & 1) * GC_T) + col, rv);
+          tc::tmem_ld16_raw(lane_base + 2 * GC_T + col, rh);
+          tc::tmem_ld16_raw(lane_base + 3 * GC_T + col, rl);
+          tc::tmem_ld_wait();
+#pragma unroll
+          for (int i = 0; i < 16; ++i) {
+            v[i] = __uint_as_float(rv[i]);
+            hi[i] = __uint_as_float(rh[i]);
+            lo[i] = __uint_as_float(rl[i]);
+          }
 #pragma unroll
           for (int i = 0; i < 16; ++i) {
             const float s2 = hi[i] + v[i];
