@@ -61,7 +61,14 @@ __device__ __forceinline__ double rsqrt_newton(double p) {
 // columns t % 4 + 4j.  Per column: the owner of the pivot has already formed it (a
 // look-ahead at the end of the previous column), the column below it is scaled and shared
 // through shared memory, and every later column takes its rank-1 update; a thread whose
-// columns are all done issues no float64 instruction.  CTA 0 writes L_kk, CTA b writes X.
+// columns are all done issues no float64 instruction.  CTA b writes X.  Every CTA reads the
+// unfactored A_kk, and nothing orders the CTAs of a launch (a CTA may start only after
+// another has finished, when the GPU is busy or the batched launch has more CTAs than fit),
+// so CTA 0 must not overwrite A_kk while others may still read it: when the step has more
+// than one CTA, CTA 0 parks L_kk in the upper triangle, which the factorisation never
+// reads (its strictly lower part transposed into the tile's upper part, its diagonal in
+// the column after the tile), and CTA 0 of the step's trailing update (the next launch)
+// moves it into place.
 constexpr int CH = 16;
 
 __device__ __forceinline__ void chol_panel_body(double* A, int m, int lda, int k, int* status, int code,
@@ -73,6 +80,7 @@ __device__ __forceinline__ void chol_panel_body(double* A, int m, int lda, int k
   const bool has_t = blk > 0;
   const int r0 = (k + blk) * CH;   // first row of T_b
   const bool live = r < CH || has_t;
+  const int nt = (m + CH - 1) / CH;
   double v[CH / 4];
 #pragma unroll
   for (int j = 0; j < CH / 4; ++j) {
@@ -121,7 +129,11 @@ __device__ __forceinline__ void chol_panel_body(double* A, int m, int lda, int k
   for (int j = 0; j < CH / 4; ++j) {
     const int sc = g + 4 * j;
     if (!has_t) {
-      if (r < CH && sc <= r && k0 + r < m && k0 + sc < m) A[(size_t)(k0 + r) * lda + k0 + sc] = v[j];
+      if (r < CH && sc <= r && k0 + r < m && k0 + sc < m) {
+        if (nt - k == 1) A[(size_t)(k0 + r) * lda + k0 + sc] = v[j];          // the only CTA
+        else if (sc < r) A[(size_t)(k0 + sc) * lda + k0 + r] = v[j];          // parked, transposed
+        else A[(size_t)(k0 + r) * lda + k0 + CH] = v[j];                      // parked diagonal
+      }
     } else if (r >= CH) {
       const int rr = r0 + r - CH;
       if (rr < m && k0 + sc < m) A[(size_t)rr * lda + k0 + sc] = v[j];
@@ -138,6 +150,16 @@ __global__ __launch_bounds__(128) void chol_panel_kernel(double* A, int m, int l
 }
 
 __device__ __forceinline__ void chol_update_body(double* A, int m, int lda, int k, const int b) {
+  if (b == 0) {
+    // L_kk from where the panel launch parked it (the step had two or more CTAs, so its
+    // tile is full and column k0 + 16 exists); no CTA of this launch touches tile k
+    const int k0 = k * CH;
+    for (int e = threadIdx.x; e < CH * CH; e += blockDim.x) {
+      const int rr = e / CH, cc = e % CH;
+      if (rr > cc) A[(size_t)(k0 + rr) * lda + k0 + cc] = A[(size_t)(k0 + cc) * lda + k0 + rr];
+      else if (rr == cc) A[(size_t)(k0 + rr) * lda + k0 + rr] = A[(size_t)(k0 + rr) * lda + k0 + CH];
+    }
+  }
   // tile (i, j), k < j <= i < nt, enumerated over the lower triangle
   int ii = (int)((sqrt(8.0 * b + 1.0) - 1.0) * 0.5);
   while ((ii + 1) * (ii + 2) / 2 <= b) ++ii;

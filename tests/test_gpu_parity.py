@@ -672,6 +672,27 @@ def test_batch_graph_replay_matches_single_problem_calls():
         c.close()
 
 
+def test_batch_with_more_cholesky_blocks_than_fit_at_once():
+    """200 problems with m = 256: the batched Cholesky's first panel launch has 3200 CTAs
+    (3400 for the capacitance matrices), more than the GPU holds at once, so CTAs of one
+    problem's panel start after others of it have finished.  The likelihoods equal the
+    single-problem calls'."""
+    torch = pytest.importorskip("torch")
+    probs = [synth.make_problem(300, 2, 256, 8, "matern32", 1.0, 0.2, 0.1, 9000 + k, lloyd=1) for k in range(200)]
+    ctxs, ys, ref = [], [], []
+    for P in probs:
+        c = V.Context(P.X, P.Z, P.mv, P.theta, precision=V.FP64)
+        ctxs.append(c)
+        ys.append(torch.from_numpy(P.y).cuda())
+        ref.append(c.nll(P.theta, P.y))
+    B = V.Batch(ctxs, [P.theta for P in probs], ys)
+    for _ in range(2):
+        np.testing.assert_allclose(B.run(), ref, rtol=1e-10)
+    B.close()
+    for c in ctxs:
+        c.close()
+
+
 # --------------------------------------------------------------------------- learned correction
 from oracle import mlp_oracle as MO
 
