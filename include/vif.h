@@ -337,6 +337,20 @@ vif_status vif_batch_create(vif_ctx *const *ctxs, int32_t nprob, const vif_cov *
 vif_status vif_batch_run(vif_batch *batch, double *nll_out);
 /* launch shape chosen by the autotuner: branches, Gram split divisor, best replay ms */
 vif_status vif_batch_info(const vif_batch *batch, int32_t *branches, int32_t *split_div, double *ms);
+/* vif_batch_set_shape -- replace the autotuner's choice: recapture the graph with the given
+ * number of concurrent branches (1..32), float64 Gram split divisor (>= 1) and factor stage
+ * of the bucketed problems (see vif_batch_factor_info): batched_factor = 0 in each problem's
+ * branch, 1 one persistent launch per bucket (warps take 32-point chunks from a device
+ * counter), 2 one flat launch per bucket (one warp per point).  VIF_ERR_ARG for values out
+ * of range or batched_factor > 0 with no bucket; the previous graph stays in use on any error. */
+vif_status vif_batch_set_shape(vif_batch *batch, int32_t branches, int32_t split_div, int32_t batched_factor);
+/* vif_batch_factor_info -- the factor stage's buckets.  A bucket holds the problems of one
+ * precision and one neighbour-block size class (m_v + 1 up to 14, 21, 28, 35, 42 or 49) whose
+ * factor stage runs on the CUDA cores; one launch can cover all their points.  batched_factor:
+ * how the graph in use runs them (the codes of vif_batch_set_shape); nbuckets: buckets built;
+ * nbucketed: problems in them.  Any output pointer may be NULL. */
+vif_status vif_batch_factor_info(const vif_batch *batch, int32_t *batched_factor, int32_t *nbuckets,
+                                 int32_t *nbucketed);
 void vif_batch_destroy(vif_batch *batch);
 
 /* vif_set_neighbors / vif_get_neighbors -- replace or read the neighbour table

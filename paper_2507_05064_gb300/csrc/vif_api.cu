@@ -2309,9 +2309,22 @@ struct vif_batch {
   int* dst = nullptr;          // device: status words per problem (4 each)
   double* hout = nullptr;      // pinned: NLL + status copy-back
   int branches = 8, split_div = 1;
+  int batched_factor = 0;   // factor stage of the bucketed problems: 0 per problem, 1 persistent, 2 flat
   double best_ms = 0.0;
   // the dense float64 stages of every problem, one launch per step for all problems
   DenseBatch chol_sm, trtri_sm, chol_cap;
+  // the factor stage of the problems in buckets (precision x block-size class), each one
+  // persistent launch over all its problems' points; in_bucket[p]: problem p belongs to one
+  struct FactorBucket {
+    bool fp32;
+    int mv_max, njobs;
+    int64_t total;
+    void* djobs = nullptr;
+    int64_t* doff = nullptr;
+    unsigned long long* queue = nullptr;
+  };
+  std::vector<FactorBucket> fbuckets;
+  std::vector<char> in_bucket;
   char err[512] = {0};
 };
 
@@ -2366,8 +2379,10 @@ vif_status enqueue_pre(vif_ctx* ctx, const vif_cov* th, const double* hyp_src, c
   return VIF_OK;
 }
 
+// with_factor = false: the factor stage runs in a bucket launch (enqueue_gram follows it)
 template <typename T>
-vif_status enqueue_mid(vif_ctx* ctx, const vif_cov* th, cudaStream_t s, int split_div) {
+vif_status enqueue_mid(vif_ctx* ctx, const vif_cov* th, cudaStream_t s, int split_div, bool with_factor = true,
+                       bool with_gram = true) {
   CtxSwap sw(ctx, s, split_div, sizeof(T) == 8);
   const CovParams cp = cov_params(th);
   const bool mixed = sizeof(T) == 4;
@@ -2379,10 +2394,91 @@ vif_status enqueue_mid(vif_ctx* ctx, const vif_cov* th, cudaStream_t s, int spli
   if constexpr (sizeof(T) == 8)
     if (ctx->m > 0) CK(linv_transpose<T>(ctx->Linv, ctx->m, ctx->ldm, LinvT, ctx->mpad, s));
   CK(lowrank_A_any<T>(ctx, cp, A, LinvT, Xs, Zs));
-  CKS(run_factor<T>(ctx, cp, A, Xs, F, factor_on_tc(ctx)));
-  CK(gram_FtF<T>(F, ctx->n, ctx->fpad, ctx->m, ctx->part, ctx->nsplit, ctx->G, ctx->fpad, s, nullptr, ctx->status));
+  if (with_factor) CKS(run_factor<T>(ctx, cp, A, Xs, F, factor_on_tc(ctx)));
+  if (with_gram) {
+    CK(gram_FtF<T>(F, ctx->n, ctx->fpad, ctx->m, ctx->part, ctx->nsplit, ctx->G, ctx->fpad, s, nullptr,
+                   ctx->status));
+    CK(reduce_sum(ctx->logD, ctx->n, ctx->red, ctx->dscal, s));
+  }
+  return VIF_OK;
+}
+
+template <typename T>
+vif_status enqueue_gram(vif_ctx* ctx, cudaStream_t s, int split_div) {
+  CtxSwap sw(ctx, s, split_div, sizeof(T) == 8);
+  CK(gram_FtF<T>((T*)ctx->F, ctx->n, ctx->fpad, ctx->m, ctx->part, ctx->nsplit, ctx->G, ctx->fpad, s, nullptr,
+                 ctx->status));
   CK(reduce_sum(ctx->logD, ctx->n, ctx->red, ctx->dscal, s));
   return VIF_OK;
+}
+
+// factor buckets: problems of one precision and block-size class (those on the CUDA-core
+// factor path), their points back to back; built once per batch
+template <typename T>
+FactorJob<T> factor_job(vif_ctx* c, const vif_cov* th) {
+  const bool mixed = sizeof(T) == 4;
+  FactorJob<T> J{};
+  J.A = (const T*)c->A;
+  J.Xs = mixed ? (const T*)c->Xs32 : (const T*)c->Xs;
+  J.N = c->N;
+  J.order = c->order;
+  J.y = c->y;
+  J.n = c->n;
+  J.d = c->d;
+  J.m = c->m;
+  J.mpad = c->mpad;
+  J.mv = c->mv;
+  J.fpad = c->fpad;
+  J.cp = cov_params(th);
+  J.F = (T*)c->F;
+  J.Acoef = c->Acoef;
+  J.Dv = c->Dv;
+  J.logD = c->logD;
+  J.status = c->status;
+  return J;
+}
+
+cudaError_t batch_factor_init(vif_batch* b) {
+  const int np = (int)b->ctx.size();
+  b->in_bucket.assign(np, 0);
+  for (int fp32 = 0; fp32 < 2; ++fp32)
+    for (int cls = 2; cls <= 7; ++cls) {
+      std::vector<int> members;
+      for (int p = 0; p < np; ++p) {
+        vif_ctx* c = b->ctx[p];
+        if ((c->precision == VIF_MIXED) != (fp32 == 1) || factor_block_class(c->mv) != cls) continue;
+        if (factor_on_tc(c)) continue;   // per-point Grams from the tensor cores: its own launches
+        members.push_back(p);
+      }
+      if (members.empty()) continue;
+      vif_batch::FactorBucket fb;
+      fb.fp32 = fp32 == 1;
+      fb.njobs = (int)members.size();
+      fb.mv_max = 0;
+      std::vector<int64_t> off(1, 0);
+      std::vector<FactorJob<float>> j32;
+      std::vector<FactorJob<double>> j64;
+      for (int p : members) {
+        vif_ctx* c = b->ctx[p];
+        fb.mv_max = std::max(fb.mv_max, c->mv);
+        off.push_back(off.back() + c->n);
+        if (fp32) j32.push_back(factor_job<float>(c, &b->th[p]));
+        else j64.push_back(factor_job<double>(c, &b->th[p]));
+        b->in_bucket[p] = 1;
+      }
+      const size_t jb = fp32 ? sizeof(FactorJob<float>) * j32.size() : sizeof(FactorJob<double>) * j64.size();
+      cudaError_t e = cudaMalloc(&fb.djobs, jb);
+      if (e == cudaSuccess) e = cudaMalloc((void**)&fb.doff, sizeof(int64_t) * off.size());
+      if (e == cudaSuccess) e = cudaMalloc((void**)&fb.queue, sizeof(unsigned long long));
+      if (e == cudaSuccess)
+        e = cudaMemcpy(fb.djobs, fp32 ? (const void*)j32.data() : (const void*)j64.data(), jb, cudaMemcpyHostToDevice);
+      if (e == cudaSuccess)
+        e = cudaMemcpy(fb.doff, off.data(), sizeof(int64_t) * off.size(), cudaMemcpyHostToDevice);
+      fb.total = off.back();
+      b->fbuckets.push_back(fb);
+      if (e != cudaSuccess) return e;
+    }
+  return cudaSuccess;
 }
 
 vif_status enqueue_post(vif_ctx* ctx, double* nll_dst, int* st_dst, cudaStream_t s) {
@@ -2406,7 +2502,9 @@ cudaError_t batch_dense_init(vif_batch* b) {
   return e;
 }
 
-vif_status batch_capture(vif_batch* b, int branches, int split_div, cudaGraphExec_t* exec) {
+// bf: the factor stage of the bucketed problems as bucket launches, 1 persistent (warps take
+// chunks from a device counter), 2 flat (one warp per point); 0 in each problem's branch
+vif_status batch_capture(vif_batch* b, int branches, int split_div, int bf, cudaGraphExec_t* exec) {
   const int np = (int)b->ctx.size();
   cudaGraph_t g = nullptr;
   if (cudaStreamBeginCapture(b->origin, cudaStreamCaptureModeThreadLocal) != cudaSuccess) return VIF_ERR_CUDA;
@@ -2441,9 +2539,28 @@ vif_status batch_capture(vif_batch* b, int branches, int split_div, cudaGraphExe
     st = VIF_ERR_CUDA;
   fork();
   each([&](int p, vif_ctx* c, cudaStream_t s) {
-    return c->precision == VIF_MIXED ? enqueue_mid<float>(c, &b->th[p], s, split_div)
-                                     : enqueue_mid<double>(c, &b->th[p], s, split_div);
+    const bool own = !(bf && b->in_bucket[p]);   // factor stage in this branch
+    return c->precision == VIF_MIXED ? enqueue_mid<float>(c, &b->th[p], s, split_div, own, own)
+                                     : enqueue_mid<double>(c, &b->th[p], s, split_div, own, own);
   });
+  if (bf) {
+    join();
+    for (const auto& fb : b->fbuckets) {
+      if (st != VIF_OK) break;
+      const cudaError_t e =
+          fb.fp32 ? vecchia_factor_batched<float>((const FactorJob<float>*)fb.djobs, fb.doff, fb.njobs, fb.total,
+                                                  fb.mv_max, bf == 2, fb.queue, b->ctx[0]->nsm, b->origin)
+                  : vecchia_factor_batched<double>((const FactorJob<double>*)fb.djobs, fb.doff, fb.njobs,
+                                                   fb.total, fb.mv_max, bf == 2, fb.queue, b->ctx[0]->nsm,
+                                                   b->origin);
+      if (e != cudaSuccess) st = VIF_ERR_CUDA;
+    }
+    fork();
+    each([&](int p, vif_ctx* c, cudaStream_t s) {
+      if (!b->in_bucket[p]) return VIF_OK;
+      return c->precision == VIF_MIXED ? enqueue_gram<float>(c, s, split_div) : enqueue_gram<double>(c, s, split_div);
+    });
+  }
   join();
   if (st == VIF_OK && dense_batch_run(b->chol_cap, b->origin) != cudaSuccess) st = VIF_ERR_CUDA;
   fork();
@@ -2506,7 +2623,7 @@ vif_status vif_batch_create(vif_ctx* const* ctxs, int32_t nprob, const vif_cov* 
   if (batch_dense_init(b) != cudaSuccess) return fail(VIF_ERR_NOMEM, "vif_batch_create: dense plan failed");
   const int maxbr = 32;
   b->br.resize(maxbr);
-  b->ev.resize(3 * (maxbr + 1));   // three fork / join pairs per capture
+  b->ev.resize(4 * (maxbr + 1));   // up to four fork / join pairs per capture
   for (auto& s : b->br)
     if (cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking) != cudaSuccess)
       return fail(VIF_ERR_CUDA, "vif_batch_create: stream creation failed");
@@ -2517,12 +2634,20 @@ vif_status vif_batch_create(vif_ctx* const* ctxs, int32_t nprob, const vif_cov* 
   cudaEvent_t t0, t1;
   cudaEventCreate(&t0);
   cudaEventCreate(&t1);
-  const int shapes[][2] = {{4, 1}, {8, 1}, {16, 1}, {32, 1}, {8, 2}, {16, 2}};
+  if (batch_factor_init(b) != cudaSuccess) {
+    cudaEventDestroy(t0);
+    cudaEventDestroy(t1);
+    return fail(VIF_ERR_NOMEM, "vif_batch_create: factor buckets failed");
+  }
+  // concurrent branches, float64 Gram split divisor, factor stage as bucket launches
+  const int shapes[][3] = {{4, 1, 0}, {8, 1, 0}, {16, 1, 0}, {32, 1, 0}, {8, 2, 0}, {16, 2, 0},
+                           {8, 1, 1}, {32, 1, 1}, {8, 1, 2}, {32, 1, 2}};
   double best = 1e30;
   for (const auto& sh : shapes) {
     if (sh[0] > nprob && sh[0] != 4) continue;
     cudaGraphExec_t ex = nullptr;
-    if (batch_capture(b, sh[0], sh[1], &ex) != VIF_OK) {
+    if (sh[2] && b->fbuckets.empty()) continue;
+    if (batch_capture(b, sh[0], sh[1], sh[2], &ex) != VIF_OK) {
       cudaEventDestroy(t0);
       cudaEventDestroy(t1);
       return fail(VIF_ERR_CUDA, "vif_batch_create: graph capture failed");
@@ -2540,6 +2665,7 @@ vif_status vif_batch_create(vif_ctx* const* ctxs, int32_t nprob, const vif_cov* 
       b->exec = ex;
       b->branches = sh[0];
       b->split_div = sh[1];
+      b->batched_factor = sh[2];
     } else {
       cudaGraphExecDestroy(ex);
     }
@@ -2580,6 +2706,35 @@ vif_status vif_batch_info(const vif_batch* b, int32_t* branches, int32_t* split_
   return VIF_OK;
 }
 
+vif_status vif_batch_set_shape(vif_batch* b, int32_t branches, int32_t split_div, int32_t batched_factor) {
+  if (!b || branches < 1 || branches > (int32_t)b->br.size() || split_div < 1 || batched_factor < 0 ||
+      batched_factor > 2)
+    return VIF_ERR_ARG;
+  if (batched_factor && b->fbuckets.empty()) return VIF_ERR_ARG;
+  if (cudaStreamSynchronize(b->user) != cudaSuccess) return VIF_ERR_CUDA;
+  cudaGraphExec_t ex = nullptr;
+  if (batch_capture(b, branches, split_div, batched_factor, &ex) != VIF_OK) return VIF_ERR_CUDA;
+  if (b->exec) cudaGraphExecDestroy(b->exec);
+  b->exec = ex;
+  b->branches = branches;
+  b->split_div = split_div;
+  b->batched_factor = batched_factor;
+  return VIF_OK;
+}
+
+vif_status vif_batch_factor_info(const vif_batch* b, int32_t* batched_factor, int32_t* nbuckets,
+                                 int32_t* nbucketed) {
+  if (!b) return VIF_ERR_ARG;
+  if (batched_factor) *batched_factor = b->batched_factor;
+  if (nbuckets) *nbuckets = (int32_t)b->fbuckets.size();
+  if (nbucketed) {
+    int32_t k = 0;
+    for (char c : b->in_bucket) k += c ? 1 : 0;
+    *nbucketed = k;
+  }
+  return VIF_OK;
+}
+
 void vif_batch_destroy(vif_batch* b) {
   if (!b) return;
   cudaStreamSynchronize(b->user);
@@ -2592,6 +2747,11 @@ void vif_batch_destroy(vif_batch* b) {
     if (s) cudaStreamDestroy(s);
   for (auto e : b->ev)
     if (e) cudaEventDestroy(e);
+  for (auto& fb : b->fbuckets) {
+    if (fb.djobs) cudaFree(fb.djobs);
+    if (fb.doff) cudaFree(fb.doff);
+    if (fb.queue) cudaFree(fb.queue);
+  }
   dense_batch_free(&b->chol_sm);
   dense_batch_free(&b->trtri_sm);
   dense_batch_free(&b->chol_cap);

@@ -123,21 +123,19 @@ __device__ __forceinline__ T sqdist_rows(const T* __restrict__ xa, const T* __re
   return sqdist(xa, xb, d);
 }
 
-// float32 m_v = 20 (R = 3): six CTAs of four warps per SM, as the shared memory allows
+// The factors and the row of [F z] of the point at position `slot` of the processing order,
+// by one warp with its shared-memory block S.
 template <typename T, int R, bool GS>
-__global__ __launch_bounds__(FK_WARPS * 32) void factor_kernel(
+__device__ __forceinline__ void factor_point(
     const T* __restrict__ A, const T* __restrict__ Xs, const int32_t* __restrict__ N,
     const int32_t* __restrict__ order, const double* __restrict__ y, int64_t n, int d, int m, int mpad, int mv,
-    int fpad, CovParams cp, T* __restrict__ F, double* __restrict__ Acoef, double* __restrict__ Dv,
-    double* __restrict__ logD, int* status, const float* __restrict__ gsub, float* __restrict__ rho) {
+    int fpad, const CovParams& cp, T* __restrict__ F, double* __restrict__ Acoef, double* __restrict__ Dv,
+    double* __restrict__ logD, int* status, const float* __restrict__ gsub, float* __restrict__ rho,
+    const int64_t slot, FactorSmem<T, R, GS>& S) {
   using SM = FactorSmem<T, R, GS>;
   constexpr int QM = SM::QM, V = SM::V, KC = SM::KC;
   using VT = typename Vec16<T>::type;
-  extern __shared__ __align__(16) unsigned char smraw[];
-  const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  SM& S = reinterpret_cast<SM*>(smraw)[w];
-  const int64_t slot = (int64_t)blockIdx.x * FK_WARPS + w;
-  if (slot >= n) return;
+  const int lane = threadIdx.x & 31;
   const int64_t i = order ? (int64_t)order[slot] : slot;
   const int q = (int)(i < (int64_t)mv ? i : (int64_t)mv);
   const int Q = q + 1;
@@ -531,6 +529,89 @@ __global__ __launch_bounds__(FK_WARPS * 32) void factor_kernel(
   if (lane == 0) F[(size_t)i * fpad + m] = (T)((y[i] + zt) * (double)inv);
 }
 
+// float32 m_v = 20 (R = 3): six CTAs of four warps per SM, as the shared memory allows
+template <typename T, int R, bool GS>
+__global__ __launch_bounds__(FK_WARPS * 32) void factor_kernel(
+    const T* __restrict__ A, const T* __restrict__ Xs, const int32_t* __restrict__ N,
+    const int32_t* __restrict__ order, const double* __restrict__ y, int64_t n, int d, int m, int mpad, int mv,
+    int fpad, CovParams cp, T* __restrict__ F, double* __restrict__ Acoef, double* __restrict__ Dv,
+    double* __restrict__ logD, int* status, const float* __restrict__ gsub, float* __restrict__ rho) {
+  extern __shared__ __align__(16) unsigned char smraw[];
+  const int w = threadIdx.x >> 5;
+  const int64_t slot = (int64_t)blockIdx.x * FK_WARPS + w;
+  if (slot >= n) return;
+  factor_point<T, R, GS>(A, Xs, N, order, y, n, d, m, mpad, mv, fpad, cp, F, Acoef, Dv, logD, status, gsub, rho,
+                         slot, reinterpret_cast<FactorSmem<T, R, GS>*>(smraw)[w]);
+}
+
+// Many problems' factors in one persistent launch (the batched likelihoods): the points of
+// all jobs of one block size R form one list (job p owns positions off[p] .. off[p+1]); each
+// warp takes the next 32 positions from a device work queue and factors them one by one.
+// one point of a job, compiled on its own: inlined into the work loop, the float32 kernels
+// for R >= 5 kept part of their register arrays in local memory
+template <typename T, int R>
+__device__ __noinline__ void factor_job_point(const FactorJob<T>* __restrict__ J, int64_t slot,
+                                              FactorSmem<T, R, false>* S) {
+  factor_point<T, R, false>(J->A, J->Xs, J->N, J->order, J->y, J->n, J->d, J->m, J->mpad, J->mv, J->fpad, J->cp,
+                            J->F, J->Acoef, J->Dv, J->logD, J->status, nullptr, nullptr, slot, *S);
+}
+
+template <typename T, int R>
+__global__ __launch_bounds__(FK_WARPS * 32) void factor_batched_kernel(const FactorJob<T>* __restrict__ jobs,
+                                                                       const int64_t* __restrict__ off, int njobs,
+                                                                       unsigned long long* __restrict__ queue) {
+  extern __shared__ __align__(16) unsigned char smraw[];
+  const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  auto& S = reinterpret_cast<FactorSmem<T, R, false>*>(smraw)[w];
+  const int64_t total = off[njobs];
+  constexpr int CHUNK = 32;
+  // one loop level: a fresh chunk whenever the warp's current one is used up
+  int64_t g = 0, end = 0;
+  int p = 0;
+#pragma unroll 1
+  for (;;) {
+    if (g == end) {
+      unsigned long long base = 0;
+      if (lane == 0) base = atomicAdd(queue, (unsigned long long)CHUNK);
+      base = __shfl_sync(0xffffffffu, base, 0);
+      if ((int64_t)base >= total) break;
+      g = (int64_t)base;
+      end = min(total, g + CHUNK);
+      int hi = njobs;                                 // the job of the chunk's first position
+      p = 0;
+      while (hi - p > 1) {
+        const int mid = (p + hi) >> 1;
+        if (off[mid] <= g) p = mid;
+        else hi = mid;
+      }
+    }
+    while (p + 1 < njobs && off[p + 1] <= g) ++p;     // positions ascend: the job only moves forward
+    factor_job_point<T, R>(jobs + p, g - off[p], &S);
+    __syncwarp();
+    ++g;
+  }
+}
+
+// the same work as one flat launch: warp g of the grid factors position g of the list
+template <typename T, int R>
+__global__ __launch_bounds__(FK_WARPS * 32) void factor_flat_kernel(const FactorJob<T>* __restrict__ jobs,
+                                                                    const int64_t* __restrict__ off, int njobs) {
+  extern __shared__ __align__(16) unsigned char smraw[];
+  const int w = threadIdx.x >> 5;
+  auto& S = reinterpret_cast<FactorSmem<T, R, false>*>(smraw)[w];
+  const int64_t g = (int64_t)blockIdx.x * FK_WARPS + w;
+  if (g >= off[njobs]) return;
+  int p = 0, hi = njobs;
+  while (hi - p > 1) {
+    const int mid = (p + hi) >> 1;
+    if (off[mid] <= g) p = mid;
+    else hi = mid;
+  }
+  const FactorJob<T>& J = jobs[p];
+  factor_point<T, R, false>(J.A, J.Xs, J.N, J.order, J.y, J.n, J.d, J.m, J.mpad, J.mv, J.fpad, J.cp, J.F, J.Acoef,
+                            J.Dv, J.logD, J.status, nullptr, nullptr, g - off[p], S);
+}
+
 template <typename T, int R, bool GS>
 static cudaError_t launch_factor(const T* A, const T* Xs, const int32_t* N, const int32_t* order, const double* y,
                                  int64_t n, int d, int m, int mpad, int mv, int fpad, CovParams cp, T* F,
@@ -577,6 +658,56 @@ cudaError_t vecchia_factor_gs(const T* A, const T* Xs, const int32_t* N, const i
 #undef LF
   return cudaErrorInvalidValue;
 }
+
+template <typename T, int R>
+static cudaError_t launch_factor_batched(const FactorJob<T>* jobs, const int64_t* off, int njobs,
+                                         unsigned long long* queue, int nsm, cudaStream_t s) {
+  const size_t smem = sizeof(FactorSmem<T, R, false>) * FK_WARPS;
+  cudaError_t e = cudaFuncSetAttribute(factor_batched_kernel<T, R>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)smem);
+  if (e != cudaSuccess) return e;
+  int per_sm = 0;
+  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, factor_batched_kernel<T, R>, FK_WARPS * 32, smem);
+  if (e != cudaSuccess) return e;
+  e = cudaMemsetAsync(queue, 0, sizeof(unsigned long long), s);
+  if (e != cudaSuccess) return e;
+  factor_batched_kernel<T, R><<<(unsigned)(std::max(per_sm, 1) * std::max(nsm, 1)), FK_WARPS * 32, smem, s>>>(
+      jobs, off, njobs, queue);
+  return cudaGetLastError();
+}
+
+template <typename T, int R>
+static cudaError_t launch_factor_flat(const FactorJob<T>* jobs, const int64_t* off, int njobs, int64_t total,
+                                      cudaStream_t s) {
+  const size_t smem = sizeof(FactorSmem<T, R, false>) * FK_WARPS;
+  cudaError_t e = cudaFuncSetAttribute(factor_flat_kernel<T, R>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)smem);
+  if (e != cudaSuccess) return e;
+  factor_flat_kernel<T, R><<<(unsigned)((total + FK_WARPS - 1) / FK_WARPS), FK_WARPS * 32, smem, s>>>(jobs, off,
+                                                                                                     njobs);
+  return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t vecchia_factor_batched(const FactorJob<T>* jobs, const int64_t* off, int njobs, int64_t total,
+                                   int mv_max, bool flat, unsigned long long* queue, int nsm, cudaStream_t s) {
+  if (njobs <= 0 || total <= 0) return cudaSuccess;
+  const int Q = mv_max + 1;
+#define LB(RR) (flat ? launch_factor_flat<T, RR>(jobs, off, njobs, total, s) \
+                     : launch_factor_batched<T, RR>(jobs, off, njobs, queue, nsm, s))
+  if (Q <= 14) return LB(2);
+  if (Q <= 21) return LB(3);
+  if (Q <= 28) return LB(4);
+  if (Q <= 35) return LB(5);
+  if (Q <= 42) return LB(6);
+  if (Q <= 49) return LB(7);
+#undef LB
+  return cudaErrorInvalidValue;
+}
+template cudaError_t vecchia_factor_batched<float>(const FactorJob<float>*, const int64_t*, int, int64_t, int, bool,
+                                                   unsigned long long*, int, cudaStream_t);
+template cudaError_t vecchia_factor_batched<double>(const FactorJob<double>*, const int64_t*, int, int64_t, int,
+                                                    bool, unsigned long long*, int, cudaStream_t);
 
 template <typename T>
 cudaError_t vecchia_factor(const T* A, const T* Xs, const int32_t* N, const int32_t* order, const double* y,

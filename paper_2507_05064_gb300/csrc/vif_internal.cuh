@@ -198,6 +198,33 @@ cudaError_t vecchia_factor_gs(const T* A, const T* Xs, const int32_t* N, const i
                               int64_t n, int d, int m, int mpad, int mv, int fpad, CovParams cp, T* F,
                               double* Acoef, double* Dv, double* logD, int* status, cudaStream_t s,
                               const float* gsub, float* rho = nullptr);
+// The factor stage of many problems in one persistent launch per neighbour-block size: jobs
+// (device array) whose points are listed back to back (job p owns positions off[p] ..
+// off[p+1], off has njobs + 1 entries, off[0] = 0), all with m_v + 1 in the same block-size
+// class as mv_max; warps take the next positions from the device counter `queue` (zeroed by
+// the call).
+template <typename T>
+struct FactorJob {
+  const T* A;
+  const T* Xs;
+  const int32_t* N;
+  const int32_t* order;
+  const double* y;
+  int64_t n;
+  int d, m, mpad, mv, fpad;
+  CovParams cp;
+  T* F;
+  double *Acoef, *Dv, *logD;
+  int* status;
+};
+// the block size class of m_v (jobs of one launch share it)
+inline int factor_block_class(int mv) {
+  const int Q = mv + 1;
+  return Q <= 14 ? 2 : Q <= 21 ? 3 : Q <= 28 ? 4 : Q <= 35 ? 5 : Q <= 42 ? 6 : Q <= 49 ? 7 : 0;
+}
+template <typename T>
+cudaError_t vecchia_factor_batched(const FactorJob<T>* jobs, const int64_t* off, int njobs, int64_t total,
+                                   int mv_max, bool flat, unsigned long long* queue, int nsm, cudaStream_t s);
 // vif_factor_tc.cu: the residual products A_N^T A_N on the tensor cores (float32 path).
 // Groups of consecutive points of the processing order share one 128-row Gram.
 struct UnionGroups {

@@ -26,7 +26,7 @@ GAUSSIAN, BERNOULLI_LOGIT = 0, 1
 EXPORTS = ["vif_build", "vif_nll", "vif_predict", "vif_laplace_mode", "vif_laplace_nll", "vif_laplace_nll_grad",
            "vif_laplace_predict",
            "vif_tridiag_log_quadrature", "vif_batch_create", "vif_batch_run",
-           "vif_batch_info", "vif_batch_destroy", "vif_mlp_bytes", "vif_mlp_init", "vif_mlp_set_params",
+           "vif_batch_info", "vif_batch_set_shape", "vif_batch_factor_info", "vif_batch_destroy", "vif_mlp_bytes", "vif_mlp_init", "vif_mlp_set_params",
            "vif_mlp_get_params", "vif_mlp_forward", "vif_mlp_backward", "vif_mlp_features", "vif_mlp_train", "vif_set_neighbors", "vif_get_neighbors",
            "vif_get_factors", "vif_get_knn_stats", "vif_get_stage_times", "vif_get_factor_tuning", "vif_nll_noalloc",
            "vif_last_error", "vif_destroy"]
@@ -122,6 +122,8 @@ def lib() -> C.CDLL:
         L.vif_batch_create.argtypes = [C.POINTER(vp), i32, C.POINTER(VifCov), C.POINTER(vp), vp, C.POINTER(vp)]
         L.vif_batch_run.argtypes = [vp, dp]
         L.vif_batch_info.argtypes = [vp, C.POINTER(i32), C.POINTER(i32), dp]
+        L.vif_batch_set_shape.argtypes = [vp, i32, i32, i32]
+        L.vif_batch_factor_info.argtypes = [vp, C.POINTER(i32), C.POINTER(i32), C.POINTER(i32)]
         L.vif_batch_destroy.argtypes = [vp]
         L.vif_batch_destroy.restype = None
         L.vif_mlp_bytes.argtypes = []
@@ -269,7 +271,15 @@ class Batch:
     def info(self):
         b, sd, ms = C.c_int32(), C.c_int32(), C.c_double()
         lib().vif_batch_info(self.h, C.byref(b), C.byref(sd), C.byref(ms))
-        return {"branches": b.value, "split_div": sd.value, "best_replay_ms": ms.value}
+        bf, nb, nbk = C.c_int32(), C.c_int32(), C.c_int32()
+        lib().vif_batch_factor_info(self.h, C.byref(bf), C.byref(nb), C.byref(nbk))
+        return {"branches": b.value, "split_div": sd.value, "best_replay_ms": ms.value,
+                "batched_factor": bf.value, "factor_buckets": nb.value, "bucketed_problems": nbk.value}
+
+    def set_shape(self, branches: int, split_div: int = 1, batched_factor: int = 0):
+        st = lib().vif_batch_set_shape(self.h, branches, split_div, int(batched_factor))
+        if st != VIF_OK:
+            raise VifError(st, "vif_batch_set_shape failed")
 
     def close(self):
         if getattr(self, "h", None):

@@ -661,6 +661,16 @@ def test_batch_graph_replay_matches_single_problem_calls():
         np.testing.assert_allclose(got, ref, rtol=1e-10)
     info = B.info()
     assert info["branches"] in (4, 8, 16, 32) and info["best_replay_ms"] > 0
+    # every float64 problem (m_v + 1 <= 49) has its factor stage in a bucket
+    assert info["bucketed_problems"] >= 5 and info["factor_buckets"] >= 1
+    # each shape, the bucket launches included, gives the single calls' likelihoods
+    for shape in ((8, 1, 0), (8, 1, 1), (16, 2, 1), (4, 1, 2), (32, 1, 2)):
+        B.set_shape(*shape)
+        assert B.info()["batched_factor"] == shape[2]
+        for _ in range(2):
+            np.testing.assert_allclose(B.run(), ref, rtol=1e-10)
+    with pytest.raises(V.VifError):
+        B.set_shape(8, 1, 3)
     # float64 and mixed problems against the oracle on the GPU's neighbour sets' definition
     for k in (0, 1, 2, 3, 4, 5):
         P = probs[k]
