@@ -156,7 +156,7 @@ def stage_algorithmic(P, stage):
 # DRAM bytes per point of the CUDA-core factor kernel (factor_kernel<float, 3>) from one ncu
 # capture of this source at n = 100,000 (378.5 MB read + 203.4 MB written per launch); reported,
 # scaled by n, only while the kernel's source file still has this digest
-FACTOR_TRAFFIC = {"bytes_per_point": 5819.1, "source_sha256": "569efd6857046bab7bcd376c8a103318b545eb8cbcb423d89f0b9dd25207c19e"}
+FACTOR_TRAFFIC = {"bytes_per_point": 5822.2, "source_sha256": "a2a00d066ed0383a23fbcf5457f82f3ab2960c3063d502e0247993d897bb3843"}
 
 
 def factor_traffic(n):
@@ -337,13 +337,28 @@ def batch_block(args, stream):
         B.run()
     ms = (time.perf_counter() - t0) * 1000.0 / reps
     info = B.info()
+    modes = {0: "per-problem launches", 1: "one persistent launch per bucket", 2: "one flat launch per bucket"}
+    # the factor stage's other forms at the chosen branch count, for the record
+    alt = {}
+    if info["factor_buckets"] > 0:
+        for mode in (0, 1, 2):
+            if mode == info["batched_factor"]:
+                continue
+            B.set_shape(info["branches"], info["split_div"], mode)
+            B.run()
+            t1 = time.perf_counter()
+            for _ in range(reps):
+                B.run()
+            alt[modes[mode]] = (time.perf_counter() - t1) * 1000.0 / reps
     npts = int(sum(P.X.shape[0] for P in probs))
     B.close()
     for c in ctxs:
         c.close()
     return {"workload": f"c5-{args.batch}-problems", "problems": args.batch, "points": npts,
             "ms_per_replay": ms, "problems_per_s": args.batch * 1000.0 / ms, "points_per_s": npts * 1000.0 / ms,
-            "branches": info["branches"], "split_div": info["split_div"], "generate_s": gen_s,
+            "branches": info["branches"], "split_div": info["split_div"],
+            "factor_stage": modes[info["batched_factor"]], "factor_buckets": info["factor_buckets"],
+            "ms_per_replay_other_factor_forms": alt, "generate_s": gen_s,
             "build_s": build_s, "timing": "wall clock around vif_batch_run (graph replay + result read-back)"}
 
 
