@@ -337,7 +337,8 @@ def batch_block(args, stream):
         B.run()
     ms = (time.perf_counter() - t0) * 1000.0 / reps
     info = B.info()
-    modes = {0: "per-problem launches", 1: "one persistent launch per bucket", 2: "one flat launch per bucket"}
+    modes = {0: "per-problem launches", 1: "one persistent launch per bucket",
+             2: "one flat launch per bucket (job records in the parameter bank)"}
     # the factor stage's other forms at the chosen branch count, for the record
     alt = {}
     if info["factor_buckets"] > 0:

@@ -341,7 +341,8 @@ vif_status vif_batch_info(const vif_batch *batch, int32_t *branches, int32_t *sp
  * number of concurrent branches (1..32), float64 Gram split divisor (>= 1) and factor stage
  * of the bucketed problems (see vif_batch_factor_info): batched_factor = 0 in each problem's
  * branch, 1 one persistent launch per bucket (warps take 32-point chunks from a device
- * counter), 2 one flat launch per bucket (one warp per point).  VIF_ERR_ARG for values out
+ * counter), 2 one flat launch per bucket (one warp per point, the problems' records in the
+ * kernel's parameter bank, 200 problems per launch).  VIF_ERR_ARG for values out
  * of range or batched_factor > 0 with no bucket; the previous graph stays in use on any error. */
 vif_status vif_batch_set_shape(vif_batch *batch, int32_t branches, int32_t split_div, int32_t batched_factor);
 /* vif_batch_factor_info -- the factor stage's buckets.  A bucket holds the problems of one

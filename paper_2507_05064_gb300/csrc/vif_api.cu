@@ -2319,6 +2319,8 @@ struct vif_batch {
     bool fp32;
     int mv_max, njobs;
     int64_t total;
+    std::vector<FactorTable<float>> t32;    // the jobs again, as parameter-bank tables
+    std::vector<FactorTable<double>> t64;
     void* djobs = nullptr;
     int64_t* doff = nullptr;
     unsigned long long* queue = nullptr;
@@ -2475,7 +2477,25 @@ cudaError_t batch_factor_init(vif_batch* b) {
       if (e == cudaSuccess)
         e = cudaMemcpy(fb.doff, off.data(), sizeof(int64_t) * off.size(), cudaMemcpyHostToDevice);
       fb.total = off.back();
-      b->fbuckets.push_back(fb);
+      for (size_t j0 = 0; j0 < members.size(); j0 += FT_MAXJ) {
+        const int nj = (int)std::min(members.size() - j0, (size_t)FT_MAXJ);
+        auto fill = [&](auto& tab, const auto& jobs) {
+          tab.njobs = nj;
+          tab.boff[0] = 0;
+          for (int k = 0; k < nj; ++k) {
+            tab.job[k] = jobs[j0 + k];
+            tab.boff[k + 1] = tab.boff[k] + (int)((jobs[j0 + k].n + FT_BLOCK_POINTS - 1) / FT_BLOCK_POINTS);
+          }
+        };
+        if (fp32) {
+          fb.t32.emplace_back();
+          fill(fb.t32.back(), j32);
+        } else {
+          fb.t64.emplace_back();
+          fill(fb.t64.back(), j64);
+        }
+      }
+      b->fbuckets.push_back(std::move(fb));
       if (e != cudaSuccess) return e;
     }
   return cudaSuccess;
@@ -2503,7 +2523,8 @@ cudaError_t batch_dense_init(vif_batch* b) {
 }
 
 // bf: the factor stage of the bucketed problems as bucket launches, 1 persistent (warps take
-// chunks from a device counter), 2 flat (one warp per point); 0 in each problem's branch
+// chunks from a device counter), 2 flat (one warp per point, the jobs in the parameter bank);
+// 0 in each problem's branch
 vif_status batch_capture(vif_batch* b, int branches, int split_div, int bf, cudaGraphExec_t* exec) {
   const int np = (int)b->ctx.size();
   cudaGraph_t g = nullptr;
@@ -2547,12 +2568,18 @@ vif_status batch_capture(vif_batch* b, int branches, int split_div, int bf, cuda
     join();
     for (const auto& fb : b->fbuckets) {
       if (st != VIF_OK) break;
-      const cudaError_t e =
-          fb.fp32 ? vecchia_factor_batched<float>((const FactorJob<float>*)fb.djobs, fb.doff, fb.njobs, fb.total,
-                                                  fb.mv_max, bf == 2, fb.queue, b->ctx[0]->nsm, b->origin)
-                  : vecchia_factor_batched<double>((const FactorJob<double>*)fb.djobs, fb.doff, fb.njobs,
-                                                   fb.total, fb.mv_max, bf == 2, fb.queue, b->ctx[0]->nsm,
-                                                   b->origin);
+      cudaError_t e = cudaSuccess;
+      if (bf == 2) {
+        for (const auto& t : fb.t32)
+          if (e == cudaSuccess) e = vecchia_factor_table<float>(t, fb.mv_max, b->origin);
+        for (const auto& t : fb.t64)
+          if (e == cudaSuccess) e = vecchia_factor_table<double>(t, fb.mv_max, b->origin);
+      } else {
+        e = fb.fp32 ? vecchia_factor_batched<float>((const FactorJob<float>*)fb.djobs, fb.doff, fb.njobs,
+                                                    fb.mv_max, fb.queue, b->ctx[0]->nsm, b->origin)
+                    : vecchia_factor_batched<double>((const FactorJob<double>*)fb.djobs, fb.doff, fb.njobs,
+                                                     fb.mv_max, fb.queue, b->ctx[0]->nsm, b->origin);
+      }
       if (e != cudaSuccess) st = VIF_ERR_CUDA;
     }
     fork();

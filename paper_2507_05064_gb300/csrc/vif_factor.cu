@@ -592,24 +592,37 @@ __global__ __launch_bounds__(FK_WARPS * 32) void factor_batched_kernel(const Fac
   }
 }
 
-// the same work as one flat launch: warp g of the grid factors position g of the list
+static_assert(FK_WARPS == FT_BLOCK_POINTS, "table block offsets count blocks of FK_WARPS points");
+static_assert(sizeof(FactorTable<float>) <= 32764 && sizeof(FactorTable<double>) <= 32764,
+              "a factor table must fit the 32764-byte kernel parameter limit");
+// the job records in the parameter bank: block b of the launch serves job p with
+// boff[p] <= b < boff[p + 1], so p and the job's fields are the same for the whole block
 template <typename T, int R>
-__global__ __launch_bounds__(FK_WARPS * 32) void factor_flat_kernel(const FactorJob<T>* __restrict__ jobs,
-                                                                    const int64_t* __restrict__ off, int njobs) {
+__global__ __launch_bounds__(FK_WARPS * 32) void factor_table_kernel(const __grid_constant__ FactorTable<T> tab) {
   extern __shared__ __align__(16) unsigned char smraw[];
   const int w = threadIdx.x >> 5;
   auto& S = reinterpret_cast<FactorSmem<T, R, false>*>(smraw)[w];
-  const int64_t g = (int64_t)blockIdx.x * FK_WARPS + w;
-  if (g >= off[njobs]) return;
-  int p = 0, hi = njobs;
+  const int b = (int)blockIdx.x;
+  int p = 0, hi = tab.njobs;
   while (hi - p > 1) {
     const int mid = (p + hi) >> 1;
-    if (off[mid] <= g) p = mid;
+    if (tab.boff[mid] <= b) p = mid;
     else hi = mid;
   }
-  const FactorJob<T>& J = jobs[p];
+  const FactorJob<T>& J = tab.job[p];
+  const int64_t slot = (int64_t)(b - tab.boff[p]) * FK_WARPS + w;
+  if (slot >= J.n) return;
   factor_point<T, R, false>(J.A, J.Xs, J.N, J.order, J.y, J.n, J.d, J.m, J.mpad, J.mv, J.fpad, J.cp, J.F, J.Acoef,
-                            J.Dv, J.logD, J.status, nullptr, nullptr, g - off[p], S);
+                            J.Dv, J.logD, J.status, nullptr, nullptr, slot, S);
+}
+template <typename T, int R>
+static cudaError_t launch_factor_table(const FactorTable<T>& tab, cudaStream_t s) {
+  const size_t smem = sizeof(FactorSmem<T, R, false>) * FK_WARPS;
+  cudaError_t e = cudaFuncSetAttribute(factor_table_kernel<T, R>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)smem);
+  if (e != cudaSuccess) return e;
+  factor_table_kernel<T, R><<<(unsigned)tab.boff[tab.njobs], FK_WARPS * 32, smem, s>>>(tab);
+  return cudaGetLastError();
 }
 
 template <typename T, int R, bool GS>
@@ -676,38 +689,38 @@ static cudaError_t launch_factor_batched(const FactorJob<T>* jobs, const int64_t
   return cudaGetLastError();
 }
 
-template <typename T, int R>
-static cudaError_t launch_factor_flat(const FactorJob<T>* jobs, const int64_t* off, int njobs, int64_t total,
-                                      cudaStream_t s) {
-  const size_t smem = sizeof(FactorSmem<T, R, false>) * FK_WARPS;
-  cudaError_t e = cudaFuncSetAttribute(factor_flat_kernel<T, R>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                       (int)smem);
-  if (e != cudaSuccess) return e;
-  factor_flat_kernel<T, R><<<(unsigned)((total + FK_WARPS - 1) / FK_WARPS), FK_WARPS * 32, smem, s>>>(jobs, off,
-                                                                                                     njobs);
-  return cudaGetLastError();
-}
-
 template <typename T>
-cudaError_t vecchia_factor_batched(const FactorJob<T>* jobs, const int64_t* off, int njobs, int64_t total,
-                                   int mv_max, bool flat, unsigned long long* queue, int nsm, cudaStream_t s) {
-  if (njobs <= 0 || total <= 0) return cudaSuccess;
+cudaError_t vecchia_factor_batched(const FactorJob<T>* jobs, const int64_t* off, int njobs, int mv_max,
+                                   unsigned long long* queue, int nsm, cudaStream_t s) {
+  if (njobs <= 0) return cudaSuccess;
   const int Q = mv_max + 1;
-#define LB(RR) (flat ? launch_factor_flat<T, RR>(jobs, off, njobs, total, s) \
-                     : launch_factor_batched<T, RR>(jobs, off, njobs, queue, nsm, s))
-  if (Q <= 14) return LB(2);
-  if (Q <= 21) return LB(3);
-  if (Q <= 28) return LB(4);
-  if (Q <= 35) return LB(5);
-  if (Q <= 42) return LB(6);
-  if (Q <= 49) return LB(7);
-#undef LB
+  if (Q <= 14) return launch_factor_batched<T, 2>(jobs, off, njobs, queue, nsm, s);
+  if (Q <= 21) return launch_factor_batched<T, 3>(jobs, off, njobs, queue, nsm, s);
+  if (Q <= 28) return launch_factor_batched<T, 4>(jobs, off, njobs, queue, nsm, s);
+  if (Q <= 35) return launch_factor_batched<T, 5>(jobs, off, njobs, queue, nsm, s);
+  if (Q <= 42) return launch_factor_batched<T, 6>(jobs, off, njobs, queue, nsm, s);
+  if (Q <= 49) return launch_factor_batched<T, 7>(jobs, off, njobs, queue, nsm, s);
   return cudaErrorInvalidValue;
 }
-template cudaError_t vecchia_factor_batched<float>(const FactorJob<float>*, const int64_t*, int, int64_t, int, bool,
+template cudaError_t vecchia_factor_batched<float>(const FactorJob<float>*, const int64_t*, int, int,
                                                    unsigned long long*, int, cudaStream_t);
-template cudaError_t vecchia_factor_batched<double>(const FactorJob<double>*, const int64_t*, int, int64_t, int,
-                                                    bool, unsigned long long*, int, cudaStream_t);
+
+template <typename T>
+cudaError_t vecchia_factor_table(const FactorTable<T>& tab, int mv_max, cudaStream_t s) {
+  if (tab.njobs <= 0 || tab.njobs > FT_MAXJ || tab.boff[tab.njobs] <= 0) return cudaSuccess;
+  const int Q = mv_max + 1;
+  if (Q <= 14) return launch_factor_table<T, 2>(tab, s);
+  if (Q <= 21) return launch_factor_table<T, 3>(tab, s);
+  if (Q <= 28) return launch_factor_table<T, 4>(tab, s);
+  if (Q <= 35) return launch_factor_table<T, 5>(tab, s);
+  if (Q <= 42) return launch_factor_table<T, 6>(tab, s);
+  if (Q <= 49) return launch_factor_table<T, 7>(tab, s);
+  return cudaErrorInvalidValue;
+}
+template cudaError_t vecchia_factor_table<float>(const FactorTable<float>&, int, cudaStream_t);
+template cudaError_t vecchia_factor_table<double>(const FactorTable<double>&, int, cudaStream_t);
+template cudaError_t vecchia_factor_batched<double>(const FactorJob<double>*, const int64_t*, int, int,
+                                                    unsigned long long*, int, cudaStream_t);
 
 template <typename T>
 cudaError_t vecchia_factor(const T* A, const T* Xs, const int32_t* N, const int32_t* order, const double* y,

@@ -223,8 +223,22 @@ inline int factor_block_class(int mv) {
   return Q <= 14 ? 2 : Q <= 21 ? 3 : Q <= 28 ? 4 : Q <= 35 ? 5 : Q <= 42 ? 6 : Q <= 49 ? 7 : 0;
 }
 template <typename T>
-cudaError_t vecchia_factor_batched(const FactorJob<T>* jobs, const int64_t* off, int njobs, int64_t total,
-                                   int mv_max, bool flat, unsigned long long* queue, int nsm, cudaStream_t s);
+cudaError_t vecchia_factor_batched(const FactorJob<T>* jobs, const int64_t* off, int njobs, int mv_max,
+                                   unsigned long long* queue, int nsm, cudaStream_t s);
+// The same work as one launch whose job records travel in the kernel's parameter bank (up to
+// FT_MAXJ jobs per table, 30 KB): block b serves job p with boff[p] <= b < boff[p+1], boff
+// counting blocks of 4 points (job p has ceil(n_p / 4) of them), so the job's fields are
+// block-uniform operands as in the single-problem kernel instead of per-thread registers.
+constexpr int FT_MAXJ = 200;
+constexpr int FT_BLOCK_POINTS = 4;   // points (one per warp) of a block of the table kernel
+template <typename T>
+struct FactorTable {
+  FactorJob<T> job[FT_MAXJ];
+  int boff[FT_MAXJ + 1];
+  int njobs;
+};
+template <typename T>
+cudaError_t vecchia_factor_table(const FactorTable<T>& tab, int mv_max, cudaStream_t s);
 // vif_factor_tc.cu: the residual products A_N^T A_N on the tensor cores (float32 path).
 // Groups of consecutive points of the processing order share one 128-row Gram.
 struct UnionGroups {
