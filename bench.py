@@ -156,7 +156,7 @@ def stage_algorithmic(P, stage):
 # DRAM bytes per point of the CUDA-core factor kernel (factor_kernel<float, 3>) from one ncu
 # capture of this source at n = 100,000 (378.5 MB read + 203.4 MB written per launch); reported,
 # scaled by n, only while the kernel's source file still has this digest
-FACTOR_TRAFFIC = {"bytes_per_point": 5822.2, "source_sha256": "a2a00d066ed0383a23fbcf5457f82f3ab2960c3063d502e0247993d897bb3843"}
+FACTOR_TRAFFIC = {"bytes_per_point": 5824.9, "source_sha256": "3296c39430878a27f9c9dcf496e5f641bad8211bc78080d9a5cdf87a68c997d4"}
 
 
 def factor_traffic(n):
