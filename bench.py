@@ -154,7 +154,7 @@ def stage_algorithmic(P, stage):
 
 
 # DRAM bytes per point of the CUDA-core factor kernel (factor_kernel<float, 3>) from one ncu
-# capture of this source at n = 100,000 (378.5 MB read + 203.4 MB written per launch); reported,
+# capture of this source at n = 100,000 (379.4 MB read + 203.1 MB written per launch); reported,
 # scaled by n, only while the kernel's source file still has this digest
 FACTOR_TRAFFIC = {"bytes_per_point": 5824.9, "source_sha256": "3296c39430878a27f9c9dcf496e5f641bad8211bc78080d9a5cdf87a68c997d4"}
 
