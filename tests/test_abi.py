@@ -120,3 +120,15 @@ def test_tridiagonal_log_quadrature_rejects_an_indefinite_matrix(lib):
         V.tridiag_log_quadrature(np.array([1.0, -2.0, 1.0]), np.array([0.1, 0.1]))
     assert ei.value.status == V.VIF_ERR_NOT_PD
 
+
+
+def test_batch_entry_points_reject_a_null_batch_without_a_gpu(lib):
+    """vif_batch_run / _info / _set_shape / _factor_info check their handle before any device work."""
+    import ctypes as C
+    i32 = C.c_int32()
+    d = C.c_double()
+    assert lib.vif_batch_run(None, C.byref(d)) == V.VIF_ERR_ARG
+    assert lib.vif_batch_info(None, C.byref(i32), C.byref(i32), C.byref(d)) == V.VIF_ERR_ARG
+    assert lib.vif_batch_set_shape(None, 8, 1, 0) == V.VIF_ERR_ARG
+    assert lib.vif_batch_factor_info(None, C.byref(i32), C.byref(i32), C.byref(i32)) == V.VIF_ERR_ARG
+    lib.vif_batch_destroy(None)   # a no-op
