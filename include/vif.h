@@ -326,7 +326,8 @@ vif_status vif_mlp_train(vif_ctx *ctx, const vif_cov *theta, const double *y, co
  * thetas[k] and fixed DEVICE response vectors ys[k] (each ctxs[k]->n long; the
  * graph reads them at every replay, so their contents may change between runs).
  * A project autotuner times a few launch shapes (number of concurrent branches, Gram
- * split factor) on the first capture and keeps the fastest.  vif_batch_run replays the
+ * split factor, factor stage per problem or per bucket: vif_batch_set_shape) on the first
+ * capture and keeps the fastest.  vif_batch_run replays the
  * graph and writes nprob likelihoods to nll_out (HOST).  The contexts must stay alive
  * and must not be used by other calls while the batch exists.  stream: cudaStream_t
  * the replays are ordered on.  The paper has no batched interface; this is the
