@@ -294,11 +294,15 @@ cudaError_t gram_tc_init() {
 }
 
 int gram_tc_nsplit(int64_t n, int fpad) {
-  // at most one wave of one CTA per SM
+  // at most one wave of one CTA per SM; slices of at least 64 chunks (2048 rows), so that a
+  // small problem's few CTAs leave room for other problems' Grams on concurrent streams, but
+  // no fewer than 8 CTAs while slices of 16 chunks allow it (the latency of a lone small call)
   const int nt = (fpad + GC_T - 1) / GC_T;
   const int npairs = nt * (nt + 1) / 2;
   int64_t want = 152 / npairs;
-  const int64_t maxs = (n + 16 * GC_K - 1) / (16 * GC_K);
+  const int64_t s64 = (n + 64 * GC_K - 1) / (64 * GC_K), s16 = (n + 16 * GC_K - 1) / (16 * GC_K);
+  const int64_t low = (8 + npairs - 1) / npairs;
+  const int64_t maxs = s64 > (s16 < low ? s16 : low) ? s64 : (s16 < low ? s16 : low);
   if (want > maxs) want = maxs;
   return (int)(want < 1 ? 1 : want);
 }
